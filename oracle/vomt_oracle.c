@@ -1,0 +1,995 @@
+/*
+ * FP64 CPU oracle for vector / matrix / scalar L1 optimal mass transport
+ * solved by PDHG (Ryu, Chen, Li, Osher, "Vector and Matrix Optimal Mass
+ * Transport: Theory, Algorithm, and Applications", arXiv:1712.10279).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously-correct
+ * restatement of the method that the CUDA library is checked against.  It is
+ * compiled into its own shared object and loaded only by the tests, by the
+ * smoke check and by the benchmark's CPU-baseline leg.  It shares no source,
+ * header, table or helper with the CUDA path, and the CUDA path never calls it.
+ *
+ * Conventions (Appendix A, "Discretization"):
+ *   - n x n grid on [0,1]^2, Delta x = h = 1/(n-1).
+ *   - Every grid field is stored plane by plane, [c][j][i], with the x index i
+ *     fastest: element (i, j) of plane c is at (c*n + j)*n + i, 0-based.
+ *   - u_x and u_y are n x n with ghost entries u_x(n-1, j) = u_y(i, n-1) = 0
+ *     (Appendix A, ghost cells); the iteration keeps them exactly zero.
+ *   - Densities are cell masses (the finite-volume average of Appendix A).
+ *
+ * Everything is double precision, single threaded, in plain loops.  No
+ * blocking, fusion or reordering beyond the order the paper's algorithm boxes
+ * state: per iteration first the u-shrink for every point, then the w-shrink
+ * for every point, then the extrapolated phi ascent for every point.
+ *
+ * Norm codes (Section 6.2):
+ *   u: 0 = ||u||_{1,2} (per channel Euclidean in space, summed over channels;
+ *          the reading of the garbled index ranges follows Section 8.3),
+ *      1 = ||u||_2    (joint Euclidean over all channels and both directions),
+ *      2 = ||u||_1    (entrywise).
+ *   w: 0 = ||w||_1 (entrywise), 1 = ||w||_2 (joint Euclidean over the edges).
+ * For matrices the same codes mean: u 1 = ||U||_2 (joint Frobenius over both
+ * directions), 2 = ||U||_1 (entrywise); w 0 = ||W||_1 (entrywise),
+ * 1 = ||W||_2 (joint Frobenius over the N components).
+ *
+ * Metrics written at every check (array of ORC_NMET doubles):
+ *   [0] P   primal objective  sum_ij ||u_ij||_u + alpha sum_ij ||w_ij||_w
+ *   [1] D   dual objective    sum <phi, rho1 - rho0>            (eq. vomt-dual)
+ *   [2] rel_gap  |P - D| / |P|                                   (Section 8.1)
+ *   [3] rel_res  ||div_x u + div_G w - (rho0 - rho1)|| / ||rho0 - rho1||
+ *   [4] R   fixed-point residual ||s^t - s^{t-1}||^2_M             (Section 6.1)
+ *   [5] dual_infeas  max_ij max(||grad phi||_{u*} - 1, ||grad_G phi||_{w*} - alpha, 0)
+ *   [6] t   iteration index the metrics belong to
+ *   [7] converged flag (1 if rel_gap <= tol_gap and rel_res <= tol_res)
+ * Section 6.1 prints the y-block weight of R as 1/mu; the metric of the PDHG
+ * proximal-point form makes it 1/nu, which is what is used here.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_NMET 8
+
+#define AT(c, j, i) (((size_t)(c) * (size_t)n + (size_t)(j)) * (size_t)n + (size_t)(i))
+
+/* ------------------------------------------------------------------------ */
+/* Shrink operators (Appendix B)                                             */
+/* ------------------------------------------------------------------------ */
+
+/* shrink_1(x; t) = argmin_z t|z| + (1/2)|z - x|^2 for real x. */
+double orc_shrink1(double x, double t)
+{
+    double a = fabs(x);
+    if (a <= t) return 0.0;
+    return (1.0 - t / a) * x;
+}
+
+/* shrink_2(x; t) = argmin_z t||z||_2 + (1/2)||z - x||_2^2 for x in R^m. */
+void orc_shrink2(int m, const double *x, double t, double *out)
+{
+    double s = 0.0;
+    for (int q = 0; q < m; ++q) s += x[q] * x[q];
+    s = sqrt(s);
+    double f = (s <= t) ? 0.0 : (1.0 - t / s);
+    for (int q = 0; q < m; ++q) out[q] = f * x[q];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Symmetric eigenvalues by the cyclic Jacobi method (used for the          */
+/* "standard eigenvalue routine" of Sections 7.2 and 7.3).                   */
+/* ------------------------------------------------------------------------ */
+
+static int cmp_double(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+/* Eigenvalues of the symmetric m x m row-major matrix A, ascending. */
+int orc_jacobi_eigvals(int m, const double *A_in, double *ev)
+{
+    if (m <= 0) return -1;
+    double *A = (double *)malloc(sizeof(double) * (size_t)m * (size_t)m);
+    if (!A) return -1;
+    memcpy(A, A_in, sizeof(double) * (size_t)m * (size_t)m);
+    double scale = 0.0;
+    for (int q = 0; q < m * m; ++q) scale += A[q] * A[q];
+    for (int sweep = 0; sweep < 200; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < m; ++p)
+            for (int q = p + 1; q < m; ++q) off += A[p * m + q] * A[p * m + q];
+        if (off <= 1e-32 * scale || off == 0.0) break;
+        for (int p = 0; p < m; ++p) {
+            for (int q = p + 1; q < m; ++q) {
+                double apq = A[p * m + q];
+                if (apq == 0.0) continue;
+                /* rotation angle that zeroes A[p][q]: cot(2 theta) = (aqq - app) / (2 apq) */
+                double th = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
+                double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int r = 0; r < m; ++r) {
+                    if (r == p || r == q) continue;
+                    double arp = A[r * m + p], arq = A[r * m + q];
+                    A[r * m + p] = A[p * m + r] = c * arp - s * arq;
+                    A[r * m + q] = A[q * m + r] = s * arp + c * arq;
+                }
+                A[p * m + p] -= t * apq;
+                A[q * m + q] += t * apq;
+                A[p * m + q] = A[q * m + p] = 0.0;
+            }
+        }
+    }
+    for (int p = 0; p < m; ++p) ev[p] = A[p * m + p];
+    qsort(ev, (size_t)m, sizeof(double), cmp_double);
+    free(A);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Graph operators (Section 3.1)                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Incidence matrix D (k x l, row-major).  Edge e = {a, b} is oriented from
+ * the smaller node to the larger one: D[min][e] = +1, D[max][e] = -1. */
+int orc_incidence(int k, int l, const int *ea, const int *eb, double *D)
+{
+    for (int q = 0; q < k * l; ++q) D[q] = 0.0;
+    for (int e = 0; e < l; ++e) {
+        int a = ea[e], b = eb[e];
+        if (a < 0 || b < 0 || a >= k || b >= k || a == b) return -1;
+        int lo = a < b ? a : b, hi = a < b ? b : a;
+        D[lo * l + e] = 1.0;
+        D[hi * l + e] = -1.0;
+    }
+    return 0;
+}
+
+static double edge_cost(const double *cost, int e) { return cost ? cost[e] : 1.0; }
+
+/* lambda_max(-Delta_G) with -Delta_G = D diag(1/c^2) D^T. */
+double orc_graph_lmax(int k, int l, const int *ea, const int *eb, const double *cost)
+{
+    if (l == 0) return 0.0;
+    double *D = (double *)malloc(sizeof(double) * (size_t)k * (size_t)l);
+    double *M = (double *)calloc((size_t)k * (size_t)k, sizeof(double));
+    double *ev = (double *)malloc(sizeof(double) * (size_t)k);
+    orc_incidence(k, l, ea, eb, D);
+    for (int a = 0; a < k; ++a)
+        for (int b = 0; b < k; ++b) {
+            double s = 0.0;
+            for (int e = 0; e < l; ++e) {
+                double c = edge_cost(cost, e);
+                s += D[a * l + e] * D[b * l + e] / (c * c);
+            }
+            M[a * k + b] = s;
+        }
+    orc_jacobi_eigvals(k, M, ev);
+    double lm = ev[k - 1];
+    free(D); free(M); free(ev);
+    return lm;
+}
+
+/* (grad_G phi)_e = (1/c_e) (D^T phi)_e at every grid point. g: [l][n][n]. */
+void orc_grad_G(int n, int k, int l, const int *ea, const int *eb, const double *cost,
+                const double *phi, double *g)
+{
+    (void)k;
+    for (int e = 0; e < l; ++e) {
+        int lo = ea[e] < eb[e] ? ea[e] : eb[e], hi = ea[e] < eb[e] ? eb[e] : ea[e];
+        double ic = 1.0 / edge_cost(cost, e);
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i)
+                g[AT(e, j, i)] = ic * (phi[AT(lo, j, i)] - phi[AT(hi, j, i)]);
+    }
+}
+
+/* div_G y = -D diag(1/c) y at every grid point. out: [k][n][n]. */
+void orc_div_G(int n, int k, int l, const int *ea, const int *eb, const double *cost,
+               const double *y, double *out)
+{
+    for (size_t q = 0; q < (size_t)k * n * n; ++q) out[q] = 0.0;
+    for (int e = 0; e < l; ++e) {
+        int lo = ea[e] < eb[e] ? ea[e] : eb[e], hi = ea[e] < eb[e] ? eb[e] : ea[e];
+        double ic = 1.0 / edge_cost(cost, e);
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                double v = ic * y[AT(e, j, i)];
+                out[AT(lo, j, i)] -= v;   /* D[lo][e] = +1 */
+                out[AT(hi, j, i)] += v;   /* D[hi][e] = -1 */
+            }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Spatial operators with ghost cells (Appendix A)                            */
+/* ------------------------------------------------------------------------ */
+
+/* Forward-difference gradient; the ghost entries (i = n-1 for x, j = n-1 for
+ * y) are zero.  planes: number of [n][n] planes (k for vectors, k*k for
+ * matrices). */
+void orc_grad(int n, int planes, const double *phi, double *gx, double *gy)
+{
+    double ih = (double)(n - 1);
+    for (int c = 0; c < planes; ++c)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                gx[AT(c, j, i)] = (i < n - 1) ? ih * (phi[AT(c, j, i + 1)] - phi[AT(c, j, i)]) : 0.0;
+                gy[AT(c, j, i)] = (j < n - 1) ? ih * (phi[AT(c, j + 1, i)] - phi[AT(c, j, i)]) : 0.0;
+            }
+}
+
+/* div_x(u)_ij = (1/h)(u_x,ij - u_x,(i-1)j + u_y,ij - u_y,i(j-1)), with
+ * u_x,-1j = u_y,i-1 = 0 and the ghost entries taken as stored (zero). */
+void orc_div(int n, int planes, const double *ux, const double *uy, double *out)
+{
+    double ih = (double)(n - 1);
+    for (int c = 0; c < planes; ++c)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                double xl = (i > 0) ? ux[AT(c, j, i - 1)] : 0.0;
+                double yl = (j > 0) ? uy[AT(c, j - 1, i)] : 0.0;
+                out[AT(c, j, i)] = ih * (ux[AT(c, j, i)] - xl + uy[AT(c, j, i)] - yl);
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Quantum gradient / divergence (Section 4.1), real matrices               */
+/* ------------------------------------------------------------------------ */
+
+/* C = A B for k x k row-major. */
+static void matmul(int k, const double *A, const double *B, double *C)
+{
+    for (int a = 0; a < k; ++a)
+        for (int b = 0; b < k; ++b) {
+            double s = 0.0;
+            for (int q = 0; q < k; ++q) s += A[a * k + q] * B[q * k + b];
+            C[a * k + b] = s;
+        }
+}
+
+/* Z_s = L_s X - X L_s for one k x k matrix X; Z: N consecutive k x k blocks. */
+void orc_grad_L_point(int k, int N, const double *L, const double *X, double *Z)
+{
+    double *t1 = (double *)malloc(sizeof(double) * (size_t)k * k);
+    double *t2 = (double *)malloc(sizeof(double) * (size_t)k * k);
+    for (int s = 0; s < N; ++s) {
+        matmul(k, L + (size_t)s * k * k, X, t1);
+        matmul(k, X, L + (size_t)s * k * k, t2);
+        for (int q = 0; q < k * k; ++q) Z[(size_t)s * k * k + q] = t1[q] - t2[q];
+    }
+    free(t1); free(t2);
+}
+
+/* Y = sum_s (-L_s Z_s + Z_s L_s) for one point. */
+void orc_div_L_point(int k, int N, const double *L, const double *Z, double *Y)
+{
+    double *t1 = (double *)malloc(sizeof(double) * (size_t)k * k);
+    double *t2 = (double *)malloc(sizeof(double) * (size_t)k * k);
+    for (int q = 0; q < k * k; ++q) Y[q] = 0.0;
+    for (int s = 0; s < N; ++s) {
+        matmul(k, L + (size_t)s * k * k, Z + (size_t)s * k * k, t1);
+        matmul(k, Z + (size_t)s * k * k, L + (size_t)s * k * k, t2);
+        for (int q = 0; q < k * k; ++q) Y[q] += -t1[q] + t2[q];
+    }
+    free(t1); free(t2);
+}
+
+/* Grid versions: X [k*k][n][n], Z [N*k*k][n][n] (component s, entry q at plane s*k*k+q). */
+void orc_grad_L(int n, int k, int N, const double *L, const double *X, double *Z)
+{
+    int kk = k * k;
+    double *x = (double *)malloc(sizeof(double) * (size_t)kk);
+    double *z = (double *)malloc(sizeof(double) * (size_t)kk * N);
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            for (int q = 0; q < kk; ++q) x[q] = X[AT(q, j, i)];
+            orc_grad_L_point(k, N, L, x, z);
+            for (int q = 0; q < kk * N; ++q) Z[AT(q, j, i)] = z[q];
+        }
+    free(x); free(z);
+}
+
+void orc_div_L(int n, int k, int N, const double *L, const double *Z, double *Y)
+{
+    int kk = k * k;
+    double *z = (double *)malloc(sizeof(double) * (size_t)kk * N);
+    double *y = (double *)malloc(sizeof(double) * (size_t)kk);
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            for (int q = 0; q < kk * N; ++q) z[q] = Z[AT(q, j, i)];
+            orc_div_L_point(k, N, L, z, y);
+            for (int q = 0; q < kk; ++q) Y[AT(q, j, i)] = y[q];
+        }
+    free(z); free(y);
+}
+
+/* The k^2 x k^2 matrix of -Delta_L = -div_L grad_L acting on vec(X) (row-major
+ * vec: index a*k+b), for real symmetric L_s:
+ *   -Delta_L X = sum_s (L_s^2 X - 2 L_s X L_s + X L_s^2).
+ * Section 7.3 forms exactly this matrix and takes its largest eigenvalue. */
+void orc_neg_quantum_laplacian(int k, int N, const double *L, double *M)
+{
+    int kk = k * k;
+    double *L2 = (double *)malloc(sizeof(double) * (size_t)kk);
+    for (int q = 0; q < kk * kk; ++q) M[q] = 0.0;
+    for (int s = 0; s < N; ++s) {
+        const double *Ls = L + (size_t)s * kk;
+        matmul(k, Ls, Ls, L2);
+        /* row (a,b), column (c,d):  (L^2)_{ac} d_{bd} + d_{ac} (L^2)_{db} - 2 L_{ac} L_{db} */
+        for (int a = 0; a < k; ++a)
+            for (int b = 0; b < k; ++b)
+                for (int c = 0; c < k; ++c)
+                    for (int d = 0; d < k; ++d) {
+                        double v = 0.0;
+                        if (b == d) v += L2[a * k + c];
+                        if (a == c) v += L2[d * k + b];
+                        v -= 2.0 * Ls[a * k + c] * Ls[d * k + b];
+                        M[(a * k + b) * kk + (c * k + d)] += v;
+                    }
+    }
+    free(L2);
+}
+
+double orc_quantum_lmax(int k, int N, const double *L)
+{
+    int kk = k * k;
+    double *M = (double *)malloc(sizeof(double) * (size_t)kk * kk);
+    double *ev = (double *)malloc(sizeof(double) * (size_t)kk);
+    orc_neg_quantum_laplacian(k, N, L, M);
+    orc_jacobi_eigvals(kk, M, ev);
+    double lm = ev[kk - 1];
+    free(M); free(ev);
+    return lm;
+}
+
+/* Second-smallest eigenvalue of -Delta_L restricted to symmetric matrices.
+ * The standing assumption of Section 4.1 (ker grad_L = span{I}) holds iff it
+ * is positive.  Orthonormal basis of Sym(k): E_aa and (E_ab + E_ba)/sqrt 2. */
+double orc_quantum_sym_gap(int k, int N, const double *L)
+{
+    int kk = k * k, m = k * (k + 1) / 2;
+    double *M = (double *)malloc(sizeof(double) * (size_t)kk * kk);
+    double *B = (double *)calloc((size_t)kk * m, sizeof(double));
+    double *S = (double *)malloc(sizeof(double) * (size_t)m * m);
+    double *ev = (double *)malloc(sizeof(double) * (size_t)m);
+    orc_neg_quantum_laplacian(k, N, L, M);
+    int col = 0;
+    for (int a = 0; a < k; ++a)
+        for (int b = a; b < k; ++b, ++col) {
+            if (a == b) B[(a * k + a) * m + col] = 1.0;
+            else {
+                B[(a * k + b) * m + col] = 1.0 / sqrt(2.0);
+                B[(b * k + a) * m + col] = 1.0 / sqrt(2.0);
+            }
+        }
+    for (int p = 0; p < m; ++p)
+        for (int q = 0; q < m; ++q) {
+            double s = 0.0;
+            for (int r = 0; r < kk; ++r)
+                for (int c = 0; c < kk; ++c) s += B[r * m + p] * M[r * kk + c] * B[c * m + q];
+            S[p * m + q] = s;
+        }
+    orc_jacobi_eigvals(m, S, ev);
+    double g = (m > 1) ? ev[1] : 0.0;
+    free(M); free(B); free(S); free(ev);
+    return g;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step sizes (Sections 7.1-7.3)                                              */
+/* ------------------------------------------------------------------------ */
+
+/* mu = 1/(32 tau (n-1)^2), nu = 1/(4 tau lambda_max); with no second operator
+ * (l = 0) the S-OMT rule mu = 1/(16 tau (n-1)^2) of Section 7.1 is used. */
+void orc_step_sizes(int n, double tau, double lmax_second, int has_second, double *mu, double *nu)
+{
+    double n1 = (double)(n - 1);
+    if (!has_second) {
+        *mu = 1.0 / (16.0 * tau * n1 * n1);
+        *nu = 0.0;
+    } else {
+        *mu = 1.0 / (32.0 * tau * n1 * n1);
+        *nu = 1.0 / (4.0 * tau * lmax_second);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Vector OMT (Section 7.2)                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* u-shrink at one point for all channels (Section 7.2, first line of the
+ * loop) given v = u + mu grad phi in vx[c], vy[c]. */
+static void shrink_u_point(int k, int u_norm, double t, double *vx, double *vy)
+{
+    if (u_norm == 0) {              /* ||.||_{1,2}: shrink_2 on each channel's 2-vector */
+        for (int c = 0; c < k; ++c) {
+            double v[2] = {vx[c], vy[c]}, o[2];
+            orc_shrink2(2, v, t, o);
+            vx[c] = o[0]; vy[c] = o[1];
+        }
+    } else if (u_norm == 1) {       /* ||.||_2: shrink_2 on the whole 2k-vector */
+        double v[64], o[64];
+        for (int c = 0; c < k; ++c) { v[c] = vx[c]; v[k + c] = vy[c]; }
+        orc_shrink2(2 * k, v, t, o);
+        for (int c = 0; c < k; ++c) { vx[c] = o[c]; vy[c] = o[k + c]; }
+    } else {                        /* ||.||_1: shrink_1 entry by entry */
+        for (int c = 0; c < k; ++c) { vx[c] = orc_shrink1(vx[c], t); vy[c] = orc_shrink1(vy[c], t); }
+    }
+}
+
+static void shrink_w_point(int l, int w_norm, double t, double *x)
+{
+    if (l == 0) return;
+    if (w_norm == 0) {
+        for (int e = 0; e < l; ++e) x[e] = orc_shrink1(x[e], t);
+    } else {
+        double o[64];
+        orc_shrink2(l, x, t, o);
+        for (int e = 0; e < l; ++e) x[e] = o[e];
+    }
+}
+
+static double norm_u_point(int k, int u_norm, const double *ux, const double *uy)
+{
+    double s = 0.0;
+    if (u_norm == 0) {
+        for (int c = 0; c < k; ++c) s += sqrt(ux[c] * ux[c] + uy[c] * uy[c]);
+    } else if (u_norm == 1) {
+        for (int c = 0; c < k; ++c) s += ux[c] * ux[c] + uy[c] * uy[c];
+        s = sqrt(s);
+    } else {
+        for (int c = 0; c < k; ++c) s += fabs(ux[c]) + fabs(uy[c]);
+    }
+    return s;
+}
+
+/* dual norm of ||.||_u at one point */
+static double dualnorm_u_point(int k, int u_norm, const double *gx, const double *gy)
+{
+    double s = 0.0;
+    if (u_norm == 0) {
+        for (int c = 0; c < k; ++c) { double v = sqrt(gx[c] * gx[c] + gy[c] * gy[c]); if (v > s) s = v; }
+    } else if (u_norm == 1) {
+        for (int c = 0; c < k; ++c) s += gx[c] * gx[c] + gy[c] * gy[c];
+        s = sqrt(s);
+    } else {
+        for (int c = 0; c < k; ++c) { if (fabs(gx[c]) > s) s = fabs(gx[c]); if (fabs(gy[c]) > s) s = fabs(gy[c]); }
+    }
+    return s;
+}
+
+static double norm_w_point(int l, int w_norm, const double *w)
+{
+    double s = 0.0;
+    if (w_norm == 0) { for (int e = 0; e < l; ++e) s += fabs(w[e]); }
+    else { for (int e = 0; e < l; ++e) s += w[e] * w[e]; s = sqrt(s); }
+    return s;
+}
+
+static double dualnorm_w_point(int l, int w_norm, const double *g)
+{
+    double s = 0.0;
+    if (w_norm == 0) { for (int e = 0; e < l; ++e) if (fabs(g[e]) > s) s = fabs(g[e]); }
+    else { for (int e = 0; e < l; ++e) s += g[e] * g[e]; s = sqrt(s); }
+    return s;
+}
+
+/* Metrics of the state (ux, uy, w, phi) (see the header comment).  R is
+ * computed from the previous state (pux, puy, pw, pphi) when those are given,
+ * else set to 0.  out[6], out[7] are left to the caller. */
+void orc_vomt_metrics(int n, int k, int l, const int *ea, const int *eb, const double *cost,
+                      const double *rho0, const double *rho1, double alpha, int u_norm, int w_norm,
+                      double mu, double nu, double tau,
+                      const double *ux, const double *uy, const double *w, const double *phi,
+                      const double *pux, const double *puy, const double *pw, const double *pphi,
+                      double *out)
+{
+    size_t nk = (size_t)k * n * n, nl = (size_t)l * n * n, nn = (size_t)n * n;
+    double *dv = (double *)malloc(sizeof(double) * nk);
+    double *dg = (double *)malloc(sizeof(double) * nk);
+    double *gx = (double *)malloc(sizeof(double) * nk);
+    double *gy = (double *)malloc(sizeof(double) * nk);
+    double *gg = (double *)malloc(sizeof(double) * (nl ? nl : 1));
+    double a[32], b[32], c3[64];
+
+    /* primal objective */
+    double P = 0.0;
+    for (size_t p = 0; p < nn; ++p) {
+        for (int c = 0; c < k; ++c) { a[c] = ux[c * nn + p]; b[c] = uy[c * nn + p]; }
+        P += norm_u_point(k, u_norm, a, b);
+        for (int e = 0; e < l; ++e) c3[e] = w[e * nn + p];
+        P += alpha * norm_w_point(l, w_norm, c3);
+    }
+    /* dual objective */
+    double D = 0.0;
+    for (size_t q = 0; q < nk; ++q) D += phi[q] * (rho1[q] - rho0[q]);
+    /* constraint residual */
+    orc_div(n, k, ux, uy, dv);
+    orc_div_G(n, k, l, ea, eb, cost, w, dg);
+    double rr = 0.0, bb = 0.0;
+    for (size_t q = 0; q < nk; ++q) {
+        double r = dv[q] + dg[q] - (rho0[q] - rho1[q]);
+        rr += r * r;
+        bb += (rho0[q] - rho1[q]) * (rho0[q] - rho1[q]);
+    }
+    /* dual infeasibility */
+    orc_grad(n, k, phi, gx, gy);
+    if (l) orc_grad_G(n, k, l, ea, eb, cost, phi, gg);
+    double di = 0.0;
+    for (size_t p = 0; p < nn; ++p) {
+        for (int c = 0; c < k; ++c) { a[c] = gx[c * nn + p]; b[c] = gy[c * nn + p]; }
+        double v = dualnorm_u_point(k, u_norm, a, b) - 1.0;
+        if (v > di) di = v;
+        if (l) {
+            for (int e = 0; e < l; ++e) c3[e] = gg[e * nn + p];
+            v = dualnorm_w_point(l, w_norm, c3) - alpha;
+            if (v > di) di = v;
+        }
+    }
+    /* fixed-point residual in the PDHG metric */
+    double R = 0.0;
+    if (pux) {
+        double *dux = (double *)malloc(sizeof(double) * nk), *duy = (double *)malloc(sizeof(double) * nk);
+        double *dw = (double *)malloc(sizeof(double) * (nl ? nl : 1));
+        double su = 0.0, sw = 0.0, sp = 0.0, cr = 0.0;
+        for (size_t q = 0; q < nk; ++q) {
+            dux[q] = ux[q] - pux[q]; duy[q] = uy[q] - puy[q];
+            su += dux[q] * dux[q] + duy[q] * duy[q];
+            sp += (phi[q] - pphi[q]) * (phi[q] - pphi[q]);
+        }
+        for (size_t q = 0; q < nl; ++q) { dw[q] = w[q] - pw[q]; sw += dw[q] * dw[q]; }
+        orc_div(n, k, dux, duy, dv);
+        orc_div_G(n, k, l, ea, eb, cost, dw, dg);
+        for (size_t q = 0; q < nk; ++q) cr += (phi[q] - pphi[q]) * (dv[q] + dg[q]);
+        R = su / mu + (l ? sw / nu : 0.0) + sp / tau - 2.0 * cr;
+        free(dux); free(duy); free(dw);
+    }
+    out[0] = P;
+    out[1] = D;
+    out[2] = fabs(P - D) / (fabs(P) > 1e-300 ? fabs(P) : 1e-300);
+    out[3] = sqrt(rr) / (bb > 0.0 ? sqrt(bb) : 1.0);
+    out[4] = R;
+    out[5] = di;
+    free(dv); free(dg); free(gx); free(gy); free(gg);
+}
+
+/*
+ * V-OMT by PDHG (Section 7.2):
+ *   u^{t+1}_ij = shrink_u(u^t_ij + mu (grad phi^t)_ij ; mu)
+ *   w^{t+1}_ij = shrink_w(w^t_ij + nu (grad_G phi^t_ij) ; alpha nu)
+ *   phi^{t+1}_ij = phi^t_ij + tau (div_x(2u^{t+1} - u^t)_ij + div_G(2w^{t+1} - w^t)_ij
+ *                                 + rho1_ij - rho0_ij)
+ * The state arrays hold the initial iterate on entry (zeros for a cold start)
+ * and the last iterate on return.  A check runs after iteration t when
+ * t % check_every == 0 or t == max_iters; it appends a metrics row to history
+ * (up to hist_cap rows) and stops the loop when tol_gap > 0 and both relative
+ * gap and relative residual are within tolerance.  Returns the number of
+ * iterations run; metrics gets the last check row.
+ */
+int orc_vomt_solve(int n, int k, int l, const int *ea, const int *eb, const double *cost,
+                   const double *rho0, const double *rho1, double alpha,
+                   double tau, double mu, double nu, int u_norm, int w_norm,
+                   int max_iters, int check_every, double tol_gap, double tol_res,
+                   double *ux, double *uy, double *w, double *phi,
+                   double *metrics, double *history, int hist_cap)
+{
+    size_t nk = (size_t)k * n * n, nl = (size_t)l * n * n, nn = (size_t)n * n;
+    double *gx = (double *)malloc(sizeof(double) * nk), *gy = (double *)malloc(sizeof(double) * nk);
+    double *nux = (double *)malloc(sizeof(double) * nk), *nuy = (double *)malloc(sizeof(double) * nk);
+    double *gg = (double *)malloc(sizeof(double) * (nl ? nl : 1));
+    double *nw = (double *)malloc(sizeof(double) * (nl ? nl : 1));
+    double *bx = (double *)malloc(sizeof(double) * nk), *by = (double *)malloc(sizeof(double) * nk);
+    double *bw = (double *)malloc(sizeof(double) * (nl ? nl : 1));
+    double *dv = (double *)malloc(sizeof(double) * nk), *dg = (double *)malloc(sizeof(double) * nk);
+    double *pphi = (double *)malloc(sizeof(double) * nk);
+    double a[32], b[32], x[64];
+    int nh = 0, t = 0;
+    if (check_every <= 0) check_every = max_iters > 0 ? max_iters : 1;
+
+    for (t = 1; t <= max_iters; ++t) {
+        /* u-update: shrink of u + mu grad phi with threshold mu */
+        orc_grad(n, k, phi, gx, gy);
+        for (size_t p = 0; p < nn; ++p) {
+            for (int c = 0; c < k; ++c) {
+                a[c] = ux[c * nn + p] + mu * gx[c * nn + p];
+                b[c] = uy[c * nn + p] + mu * gy[c * nn + p];
+            }
+            shrink_u_point(k, u_norm, mu, a, b);
+            for (int c = 0; c < k; ++c) { nux[c * nn + p] = a[c]; nuy[c * nn + p] = b[c]; }
+        }
+        /* w-update: shrink of w + nu grad_G phi with threshold alpha nu */
+        if (l) {
+            orc_grad_G(n, k, l, ea, eb, cost, phi, gg);
+            for (size_t p = 0; p < nn; ++p) {
+                for (int e = 0; e < l; ++e) x[e] = w[e * nn + p] + nu * gg[e * nn + p];
+                shrink_w_point(l, w_norm, alpha * nu, x);
+                for (int e = 0; e < l; ++e) nw[e * nn + p] = x[e];
+            }
+        }
+        /* extrapolation and dual ascent */
+        for (size_t q = 0; q < nk; ++q) { bx[q] = 2.0 * nux[q] - ux[q]; by[q] = 2.0 * nuy[q] - uy[q]; }
+        for (size_t q = 0; q < nl; ++q) bw[q] = 2.0 * nw[q] - w[q];
+        orc_div(n, k, bx, by, dv);
+        if (l) orc_div_G(n, k, l, ea, eb, cost, bw, dg);
+        else for (size_t q = 0; q < nk; ++q) dg[q] = 0.0;
+        memcpy(pphi, phi, sizeof(double) * nk);
+        for (size_t q = 0; q < nk; ++q) phi[q] = phi[q] + tau * (dv[q] + dg[q] + rho1[q] - rho0[q]);
+
+        int check = (t % check_every == 0) || (t == max_iters);
+        double m[ORC_NMET];
+        if (check) {
+            /* previous state: ux, uy, w (not yet overwritten), pphi */
+            orc_vomt_metrics(n, k, l, ea, eb, cost, rho0, rho1, alpha, u_norm, w_norm, mu, nu, tau,
+                             nux, nuy, nw, phi, ux, uy, w, pphi, m);
+            m[6] = (double)t;
+            m[7] = (tol_gap > 0.0 && m[2] <= tol_gap && m[3] <= tol_res) ? 1.0 : 0.0;
+            if (history && nh < hist_cap) { memcpy(history + (size_t)nh * ORC_NMET, m, sizeof m); ++nh; }
+            if (metrics) memcpy(metrics, m, sizeof m);
+        }
+        memcpy(ux, nux, sizeof(double) * nk);
+        memcpy(uy, nuy, sizeof(double) * nk);
+        if (l) memcpy(w, nw, sizeof(double) * nl);
+        if (check && m[7] != 0.0) break;
+    }
+    if (t > max_iters) t = max_iters;
+    free(gx); free(gy); free(nux); free(nuy); free(gg); free(nw);
+    free(bx); free(by); free(bw); free(dv); free(dg); free(pphi);
+    return t;
+}
+
+/*
+ * S-OMT by PDHG exactly as the box of Section 7.1 (scalar density, k = 1):
+ *   u^{t+1}_ij = shrink(u^t_ij + mu (grad phi^t)_ij ; mu)
+ *   phi^{t+1}_ij = phi^t_ij + tau (div_x(2u^{t+1} - u^t)_ij + rho1_ij - rho0_ij)
+ * u_norm: 0 = isotropic ||u||_2 of the 2-vector, 2 = ||u||_1.
+ */
+int orc_somt_run(int n, const double *rho0, const double *rho1, double tau, double mu, int u_norm,
+                 int iters, double *ux, double *uy, double *phi)
+{
+    size_t nn = (size_t)n * n;
+    double *gx = (double *)malloc(sizeof(double) * nn), *gy = (double *)malloc(sizeof(double) * nn);
+    double *nx = (double *)malloc(sizeof(double) * nn), *ny = (double *)malloc(sizeof(double) * nn);
+    double *dv = (double *)malloc(sizeof(double) * nn);
+    for (int t = 0; t < iters; ++t) {
+        orc_grad(n, 1, phi, gx, gy);
+        for (size_t p = 0; p < nn; ++p) {
+            double v[2] = {ux[p] + mu * gx[p], uy[p] + mu * gy[p]}, o[2];
+            if (u_norm == 2) { o[0] = orc_shrink1(v[0], mu); o[1] = orc_shrink1(v[1], mu); }
+            else orc_shrink2(2, v, mu, o);
+            nx[p] = o[0]; ny[p] = o[1];
+        }
+        for (size_t p = 0; p < nn; ++p) { gx[p] = 2.0 * nx[p] - ux[p]; gy[p] = 2.0 * ny[p] - uy[p]; }
+        orc_div(n, 1, gx, gy, dv);
+        for (size_t p = 0; p < nn; ++p) phi[p] += tau * (dv[p] + rho1[p] - rho0[p]);
+        memcpy(ux, nx, sizeof(double) * nn);
+        memcpy(uy, ny, sizeof(double) * nn);
+    }
+    free(gx); free(gy); free(nx); free(ny); free(dv);
+    return iters;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Matrix OMT (Section 7.3), real symmetric densities, full k x k storage    */
+/* ------------------------------------------------------------------------ */
+
+/* Fields: Phi, Ux, Uy, Lam0, Lam1 [k*k][n][n]; W [N*k*k][n][n]. */
+void orc_momt_metrics(int n, int k, int N, const double *L, const double *Lam0, const double *Lam1,
+                      double alpha, int u_norm, int w_norm, double mu, double nu, double tau,
+                      const double *Ux, const double *Uy, const double *W, const double *Phi,
+                      const double *pUx, const double *pUy, const double *pW, const double *pPhi,
+                      double *out)
+{
+    int kk = k * k;
+    size_t nn = (size_t)n * n, nk = (size_t)kk * nn, nw = (size_t)N * kk * nn;
+    double *dv = (double *)malloc(sizeof(double) * nk), *dl = (double *)malloc(sizeof(double) * nk);
+    double *gx = (double *)malloc(sizeof(double) * nk), *gy = (double *)malloc(sizeof(double) * nk);
+    double *gl = (double *)malloc(sizeof(double) * nw);
+    double P = 0.0, D = 0.0, rr = 0.0, bb = 0.0, di = 0.0;
+    for (size_t p = 0; p < nn; ++p) {
+        double su = 0.0, sw = 0.0;
+        for (int q = 0; q < kk; ++q) {
+            if (u_norm == 2) su += fabs(Ux[q * nn + p]) + fabs(Uy[q * nn + p]);
+            else su += Ux[q * nn + p] * Ux[q * nn + p] + Uy[q * nn + p] * Uy[q * nn + p];
+        }
+        for (int q = 0; q < N * kk; ++q) {
+            if (w_norm == 0) sw += fabs(W[q * nn + p]);
+            else sw += W[q * nn + p] * W[q * nn + p];
+        }
+        P += (u_norm == 2 ? su : sqrt(su)) + alpha * (w_norm == 0 ? sw : sqrt(sw));
+    }
+    for (size_t q = 0; q < nk; ++q) D += Phi[q] * (Lam1[q] - Lam0[q]);
+    orc_div(n, kk, Ux, Uy, dv);
+    orc_div_L(n, k, N, L, W, dl);
+    for (size_t q = 0; q < nk; ++q) {
+        double r = dv[q] + dl[q] - (Lam0[q] - Lam1[q]);
+        rr += r * r;
+        bb += (Lam0[q] - Lam1[q]) * (Lam0[q] - Lam1[q]);
+    }
+    orc_grad(n, kk, Phi, gx, gy);
+    orc_grad_L(n, k, N, L, Phi, gl);
+    for (size_t p = 0; p < nn; ++p) {
+        double s = 0.0, m = 0.0;
+        for (int q = 0; q < kk; ++q) {
+            if (u_norm == 2) { if (fabs(gx[q * nn + p]) > s) s = fabs(gx[q * nn + p]); if (fabs(gy[q * nn + p]) > s) s = fabs(gy[q * nn + p]); }
+            else s += gx[q * nn + p] * gx[q * nn + p] + gy[q * nn + p] * gy[q * nn + p];
+        }
+        if (u_norm != 2) s = sqrt(s);
+        for (int q = 0; q < N * kk; ++q) {
+            if (w_norm == 0) { if (fabs(gl[q * nn + p]) > m) m = fabs(gl[q * nn + p]); }
+            else m += gl[q * nn + p] * gl[q * nn + p];
+        }
+        if (w_norm != 0) m = sqrt(m);
+        if (s - 1.0 > di) di = s - 1.0;
+        if (m - alpha > di) di = m - alpha;
+    }
+    double R = 0.0;
+    if (pUx) {
+        double *dUx = (double *)malloc(sizeof(double) * nk), *dUy = (double *)malloc(sizeof(double) * nk);
+        double *dW = (double *)malloc(sizeof(double) * nw);
+        double su = 0.0, sw = 0.0, sp = 0.0, cr = 0.0;
+        for (size_t q = 0; q < nk; ++q) {
+            dUx[q] = Ux[q] - pUx[q]; dUy[q] = Uy[q] - pUy[q];
+            su += dUx[q] * dUx[q] + dUy[q] * dUy[q];
+            sp += (Phi[q] - pPhi[q]) * (Phi[q] - pPhi[q]);
+        }
+        for (size_t q = 0; q < nw; ++q) { dW[q] = W[q] - pW[q]; sw += dW[q] * dW[q]; }
+        orc_div(n, kk, dUx, dUy, dv);
+        orc_div_L(n, k, N, L, dW, dl);
+        for (size_t q = 0; q < nk; ++q) cr += (Phi[q] - pPhi[q]) * (dv[q] + dl[q]);
+        R = su / mu + sw / nu + sp / tau - 2.0 * cr;
+        free(dUx); free(dUy); free(dW);
+    }
+    out[0] = P;
+    out[1] = D;
+    out[2] = fabs(P - D) / (fabs(P) > 1e-300 ? fabs(P) : 1e-300);
+    out[3] = sqrt(rr) / (bb > 0.0 ? sqrt(bb) : 1.0);
+    out[4] = R;
+    out[5] = di;
+    free(dv); free(dl); free(gx); free(gy); free(gl);
+}
+
+/*
+ * M-OMT by PDHG (Section 7.3):
+ *   U^{t+1}_ij = shrink_u(U^t_ij + mu (grad Phi^t)_ij ; mu)
+ *   W^{t+1}_ij = shrink_w(W^t_ij + nu (grad_L Phi^t_ij) ; alpha nu)
+ *   Phi^{t+1}_ij = Phi^t_ij + tau (div_x(2U^{t+1} - U^t)_ij + div_L(2W^{t+1} - W^t)_ij
+ *                                 + Lam1_ij - Lam0_ij)
+ * on full k x k matrices; the Lemma of Appendix B (and its entrywise analogue
+ * for ||.||_1) is why the shrinks can act on all of R^{k x k}.
+ */
+int orc_momt_solve(int n, int k, int N, const double *L, const double *Lam0, const double *Lam1,
+                   double alpha, double tau, double mu, double nu, int u_norm, int w_norm,
+                   int max_iters, int check_every, double tol_gap, double tol_res,
+                   double *Ux, double *Uy, double *W, double *Phi,
+                   double *metrics, double *history, int hist_cap)
+{
+    int kk = k * k;
+    size_t nn = (size_t)n * n, nk = (size_t)kk * nn, nw = (size_t)N * kk * nn;
+    double *gx = (double *)malloc(sizeof(double) * nk), *gy = (double *)malloc(sizeof(double) * nk);
+    double *gl = (double *)malloc(sizeof(double) * nw);
+    double *nUx = (double *)malloc(sizeof(double) * nk), *nUy = (double *)malloc(sizeof(double) * nk);
+    double *nW = (double *)malloc(sizeof(double) * nw);
+    double *bx = (double *)malloc(sizeof(double) * nk), *by = (double *)malloc(sizeof(double) * nk);
+    double *bw = (double *)malloc(sizeof(double) * nw);
+    double *dv = (double *)malloc(sizeof(double) * nk), *dl = (double *)malloc(sizeof(double) * nk);
+    double *pPhi = (double *)malloc(sizeof(double) * nk);
+    double *v = (double *)malloc(sizeof(double) * 2 * kk), *o = (double *)malloc(sizeof(double) * 2 * kk);
+    double *xw = (double *)malloc(sizeof(double) * N * kk), *ow = (double *)malloc(sizeof(double) * N * kk);
+    int nh = 0, t = 0;
+    if (check_every <= 0) check_every = max_iters > 0 ? max_iters : 1;
+
+    for (t = 1; t <= max_iters; ++t) {
+        orc_grad(n, kk, Phi, gx, gy);
+        for (size_t p = 0; p < nn; ++p) {
+            for (int q = 0; q < kk; ++q) {
+                v[q] = Ux[q * nn + p] + mu * gx[q * nn + p];
+                v[kk + q] = Uy[q * nn + p] + mu * gy[q * nn + p];
+            }
+            if (u_norm == 2) for (int q = 0; q < 2 * kk; ++q) o[q] = orc_shrink1(v[q], mu);
+            else orc_shrink2(2 * kk, v, mu, o);
+            for (int q = 0; q < kk; ++q) { nUx[q * nn + p] = o[q]; nUy[q * nn + p] = o[kk + q]; }
+        }
+        orc_grad_L(n, k, N, L, Phi, gl);
+        for (size_t p = 0; p < nn; ++p) {
+            for (int q = 0; q < N * kk; ++q) xw[q] = W[q * nn + p] + nu * gl[q * nn + p];
+            if (w_norm == 0) for (int q = 0; q < N * kk; ++q) ow[q] = orc_shrink1(xw[q], alpha * nu);
+            else orc_shrink2(N * kk, xw, alpha * nu, ow);
+            for (int q = 0; q < N * kk; ++q) nW[q * nn + p] = ow[q];
+        }
+        for (size_t q = 0; q < nk; ++q) { bx[q] = 2.0 * nUx[q] - Ux[q]; by[q] = 2.0 * nUy[q] - Uy[q]; }
+        for (size_t q = 0; q < nw; ++q) bw[q] = 2.0 * nW[q] - W[q];
+        orc_div(n, kk, bx, by, dv);
+        orc_div_L(n, k, N, L, bw, dl);
+        memcpy(pPhi, Phi, sizeof(double) * nk);
+        for (size_t q = 0; q < nk; ++q) Phi[q] = Phi[q] + tau * (dv[q] + dl[q] + Lam1[q] - Lam0[q]);
+
+        int check = (t % check_every == 0) || (t == max_iters);
+        double m[ORC_NMET];
+        if (check) {
+            orc_momt_metrics(n, k, N, L, Lam0, Lam1, alpha, u_norm, w_norm, mu, nu, tau,
+                             nUx, nUy, nW, Phi, Ux, Uy, W, pPhi, m);
+            m[6] = (double)t;
+            m[7] = (tol_gap > 0.0 && m[2] <= tol_gap && m[3] <= tol_res) ? 1.0 : 0.0;
+            if (history && nh < hist_cap) { memcpy(history + (size_t)nh * ORC_NMET, m, sizeof m); ++nh; }
+            if (metrics) memcpy(metrics, m, sizeof m);
+        }
+        memcpy(Ux, nUx, sizeof(double) * nk);
+        memcpy(Uy, nUy, sizeof(double) * nk);
+        memcpy(W, nW, sizeof(double) * nw);
+        if (check && m[7] != 0.0) break;
+    }
+    if (t > max_iters) t = max_iters;
+    free(gx); free(gy); free(gl); free(nUx); free(nUy); free(nW); free(bx); free(by); free(bw);
+    free(dv); free(dl); free(pPhi); free(v); free(o); free(xw); free(ow);
+    return t;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gradients of the transport cost                                            */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Envelope gradient.  V(rho0, rho1) is the optimal value of the dual problem
+ * (eq. vomt-dual), the maximum over the feasible phi of the linear function
+ * <phi, rho1 - rho0>; the feasible set does not depend on the densities, so
+ * dV/drho1 = phi* and dV/drho0 = -phi*, up to the constant that the dual
+ * leaves free (grad and grad_G vanish on constants shared by all channels).
+ * The constant is fixed by making phi* zero-mean over all cells and channels.
+ * V is also the optimal value of the primal (eq. vomt), which is linear in
+ * alpha for fixed (u, w), so dV/dalpha = sum_ij ||w*_ij||_w.
+ */
+void orc_envelope_grad(int n, int k, int l, int w_norm, const double *phi, const double *w,
+                       double *g_rho1, double *g_rho0, double *g_alpha)
+{
+    size_t nk = (size_t)k * n * n, nn = (size_t)n * n;
+    double mean = 0.0;
+    for (size_t q = 0; q < nk; ++q) mean += phi[q];
+    mean /= (double)nk;
+    for (size_t q = 0; q < nk; ++q) { g_rho1[q] = phi[q] - mean; g_rho0[q] = -(phi[q] - mean); }
+    double s = 0.0, x[64];
+    for (size_t p = 0; p < nn; ++p) {
+        for (int e = 0; e < l; ++e) x[e] = w[e * nn + p];
+        s += norm_w_point(l, w_norm, x);
+    }
+    *g_alpha = s;
+}
+
+/* transpose of the Jacobian of shrink_2(.; t) at x, applied to g (symmetric):
+ * (1 - t/s) g + t (x.g) x / s^3 for s = ||x|| > t, else 0.  Also returns the
+ * derivative of the output with respect to the threshold t, dotted with g:
+ * -(x.g)/s for s > t, else 0. */
+static double shrink2_vjp(int m, const double *x, double t, const double *g, double *out)
+{
+    double s = 0.0, xg = 0.0;
+    for (int q = 0; q < m; ++q) { s += x[q] * x[q]; xg += x[q] * g[q]; }
+    s = sqrt(s);
+    if (s <= t) { for (int q = 0; q < m; ++q) out[q] = 0.0; return 0.0; }
+    for (int q = 0; q < m; ++q) out[q] = (1.0 - t / s) * g[q] + t * xg * x[q] / (s * s * s);
+    return -xg / s;
+}
+
+static double shrink1_vjp(double x, double t, double g, double *out)
+{
+    if (fabs(x) <= t) { *out = 0.0; return 0.0; }
+    *out = g;
+    return -(x > 0 ? 1.0 : -1.0) * g;
+}
+
+/*
+ * Unrolled gradient.  J_T = P(u^T, w^T), the primal objective after T
+ * iterations of Section 7.2 from the zero iterate, is a piecewise-smooth
+ * function of (rho0, rho1, alpha).  This routine stores every iterate and
+ * applies the chain rule backwards through the T iterations, step by step:
+ *   phi^{t+1} = phi^t + tau (div ubar + div_G wbar + rho1 - rho0)
+ *   u^{t+1} = shrink_u(u^t + mu grad phi^t ; mu),  w^{t+1} = shrink_w(w^t + nu grad_G phi^t ; alpha nu)
+ * using div_x^T = -grad_x (Appendix A) and div_G^T = -grad_G (Section 3.1).
+ * Supports u_norm 0 (||.||_{1,2}) and w_norm 0 / 1.  Returns J_T.
+ */
+double orc_vomt_unrolled_grad(int n, int k, int l, const int *ea, const int *eb, const double *cost,
+                              const double *rho0, const double *rho1, double alpha,
+                              double tau, double mu, double nu, int w_norm, int T,
+                              double *g_rho1, double *g_rho0, double *g_alpha)
+{
+    size_t nk = (size_t)k * n * n, nl = (size_t)l * n * n, nn = (size_t)n * n;
+    size_t st = 3 * nk + nl;  /* ux, uy, phi, w */
+    double *S = (double *)calloc(st * (size_t)(T + 1), sizeof(double));
+    double met[ORC_NMET];
+    /* forward, keeping every iterate */
+    for (int t = 0; t < T; ++t) {
+        double *cur = S + st * (size_t)t, *nxt = S + st * (size_t)(t + 1);
+        memcpy(nxt, cur, sizeof(double) * st);
+        orc_vomt_solve(n, k, l, ea, eb, cost, rho0, rho1, alpha, tau, mu, nu, 0, w_norm,
+                       1, 1, 0.0, 0.0, nxt, nxt + nk, nxt + 3 * nk, nxt + 2 * nk, met, NULL, 0);
+    }
+    double *fin = S + st * (size_t)T;
+    double J = 0.0;
+    /* adjoint of J wrt the final state */
+    double *Gux = (double *)calloc(nk, sizeof(double)), *Guy = (double *)calloc(nk, sizeof(double));
+    double *Gphi = (double *)calloc(nk, sizeof(double));
+    double *Gw = (double *)calloc(nl ? nl : 1, sizeof(double));
+    double ga = 0.0;
+    for (size_t p = 0; p < nn; ++p) {
+        for (int c = 0; c < k; ++c) {
+            double x = fin[c * nn + p], y = fin[nk + c * nn + p], s = sqrt(x * x + y * y);
+            J += s;
+            if (s > 0) { Gux[c * nn + p] = x / s; Guy[c * nn + p] = y / s; }
+        }
+        double wv[64], ws = 0.0;
+        for (int e = 0; e < l; ++e) wv[e] = fin[3 * nk + e * nn + p];
+        ws = norm_w_point(l, w_norm, wv);
+        J += alpha * ws;
+        ga += ws;
+        for (int e = 0; e < l; ++e) {
+            double g;
+            if (w_norm == 0) g = (wv[e] > 0) ? 1.0 : (wv[e] < 0 ? -1.0 : 0.0);
+            else g = ws > 0 ? wv[e] / ws : 0.0;
+            Gw[e * nn + p] = alpha * g;
+        }
+    }
+    for (size_t q = 0; q < nk; ++q) { g_rho1[q] = 0.0; g_rho0[q] = 0.0; }
+
+    double *gx = (double *)malloc(sizeof(double) * nk), *gy = (double *)malloc(sizeof(double) * nk);
+    double *ggG = (double *)malloc(sizeof(double) * (nl ? nl : 1));
+    double *Hx = (double *)malloc(sizeof(double) * nk), *Hy = (double *)malloc(sizeof(double) * nk);
+    double *Hw = (double *)malloc(sizeof(double) * (nl ? nl : 1));
+    double *gvx = (double *)malloc(sizeof(double) * nk), *gvy = (double *)malloc(sizeof(double) * nk);
+    double *gxw = (double *)malloc(sizeof(double) * (nl ? nl : 1));
+    double *dv = (double *)malloc(sizeof(double) * nk), *dg = (double *)malloc(sizeof(double) * nk);
+    double *pgx = (double *)malloc(sizeof(double) * nk), *pgy = (double *)malloc(sizeof(double) * nk);
+    double *pgG = (double *)malloc(sizeof(double) * (nl ? nl : 1));
+
+    for (int t = T - 1; t >= 0; --t) {
+        double *cur = S + st * (size_t)t;
+        const double *ux = cur, *uy = cur + nk, *phi = cur + 2 * nk, *w = cur + 3 * nk;
+        /* phi^{t+1} = phi^t + tau (div(2u' - u) + div_G(2w' - w) + rho1 - rho0) */
+        for (size_t q = 0; q < nk; ++q) { g_rho1[q] += tau * Gphi[q]; g_rho0[q] -= tau * Gphi[q]; }
+        orc_grad(n, k, Gphi, gx, gy);           /* div^T Gphi = -grad Gphi */
+        if (l) orc_grad_G(n, k, l, ea, eb, cost, Gphi, ggG);
+        for (size_t q = 0; q < nk; ++q) { Hx[q] = Gux[q] - 2.0 * tau * gx[q]; Hy[q] = Guy[q] - 2.0 * tau * gy[q]; }
+        for (size_t q = 0; q < nl; ++q) Hw[q] = Gw[q] - 2.0 * tau * ggG[q];
+        /* u' = shrink(u + mu grad phi; mu) per channel 2-vector */
+        orc_grad(n, k, phi, pgx, pgy);
+        for (size_t p = 0; p < nn; ++p)
+            for (int c = 0; c < k; ++c) {
+                size_t q = c * nn + p;
+                double x[2] = {ux[q] + mu * pgx[q], uy[q] + mu * pgy[q]}, g[2] = {Hx[q], Hy[q]}, o[2];
+                shrink2_vjp(2, x, mu, g, o);
+                gvx[q] = o[0]; gvy[q] = o[1];
+            }
+        /* w' = shrink_w(w + nu grad_G phi; alpha nu) */
+        if (l) {
+            orc_grad_G(n, k, l, ea, eb, cost, phi, pgG);
+            for (size_t p = 0; p < nn; ++p) {
+                if (w_norm == 0) {
+                    for (int e = 0; e < l; ++e) {
+                        size_t q = e * nn + p;
+                        double o;
+                        double dt = shrink1_vjp(w[q] + nu * pgG[q], alpha * nu, Hw[q], &o);
+                        gxw[q] = o;
+                        ga += nu * dt;
+                    }
+                } else {
+                    double x[64], g[64], o[64];
+                    for (int e = 0; e < l; ++e) { x[e] = w[e * nn + p] + nu * pgG[e * nn + p]; g[e] = Hw[e * nn + p]; }
+                    ga += nu * shrink2_vjp(l, x, alpha * nu, g, o);
+                    for (int e = 0; e < l; ++e) gxw[e * nn + p] = o[e];
+                }
+            }
+        }
+        /* adjoints of the state at t */
+        orc_div(n, k, gvx, gvy, dv);                       /* grad^T gv = -div gv */
+        if (l) orc_div_G(n, k, l, ea, eb, cost, gxw, dg);  /* grad_G^T gx = -div_G gx */
+        else for (size_t q = 0; q < nk; ++q) dg[q] = 0.0;
+        for (size_t q = 0; q < nk; ++q) {
+            Gux[q] = gvx[q] + tau * gx[q];
+            Guy[q] = gvy[q] + tau * gy[q];
+            Gphi[q] = Gphi[q] - mu * dv[q] - nu * dg[q];
+        }
+        for (size_t q = 0; q < nl; ++q) Gw[q] = gxw[q] + tau * ggG[q];
+    }
+    *g_alpha = ga;
+    free(S); free(Gux); free(Guy); free(Gphi); free(Gw); free(gx); free(gy); free(ggG);
+    free(Hx); free(Hy); free(Hw); free(gvx); free(gvy); free(gxw); free(dv); free(dg);
+    free(pgx); free(pgy); free(pgG);
+    return J;
+}
