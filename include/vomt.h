@@ -1,0 +1,168 @@
+/*
+ * vomt.h -- C ABI of the GB300 (sm_103a) solver for vector- and matrix-valued
+ * L1 optimal mass transport by the primal-dual hybrid gradient (PDHG) method of
+ * Ryu, Chen, Li and Osher, "Vector and Matrix Optimal Mass Transport: Theory,
+ * Algorithm, and Applications" (arXiv:1712.10279).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid.  An n x n grid on [0,1]^2 with spacing h = 1/(n-1) (Section 7 and
+ *   Appendix A).  Every grid field is FP32, stored plane by plane as
+ *   [plane][j][i] with the x index i fastest, densely packed (row pitch n):
+ *   element (i, j) of plane p sits at (p*n + j)*n + i.
+ * Densities.  Cell masses (the finite-volume averages of Appendix A).  For the
+ *   vector problem rho0 and rho1 are [k][n][n] and must be nonnegative with
+ *   equal totals over all cells and channels (the constraint of eq. (vomt)
+ *   sums to zero because div_x and div_G do).
+ * Flux and potential.  u is [2][k][n][n]: the x components u_x (plane c) then
+ *   the y components u_y (plane k + c).  Entries u_x(n-1, j) and u_y(i, n-1)
+ *   are the ghost cells of Appendix A: they are ignored on input and are zero
+ *   on output.  w is [l][n][n] (one plane per graph edge, in the order the
+ *   edges are given).  phi is [k][n][n].
+ * Memory.  "device" pointers are CUDA global memory of the context's device,
+ *   owned by the caller (for example torch tensors); the library never frees
+ *   or keeps them after the call returns.  "host" pointers are ordinary host
+ *   memory (pageable or pinned).
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  All device work of a call is ordered on that stream.  A solve
+ *   that stops on a tolerance reads its stopping flag back while it runs and
+ *   returns only after its last kernel finished, so outputs and *result are
+ *   valid when the call returns.
+ * Status.  Every entry point returns an int: VOMT_OK (0), VOMT_NOT_CONVERGED
+ *   (1, outputs valid, iteration cap reached before the tolerance) or a
+ *   negative VOMT_ERR_* code.  No entry point aborts the process or lets an
+ *   exception escape.  vomt_last_error() gives a message for the last error
+ *   on a context.
+ * Threads.  A context may be used by one host thread at a time.
+ */
+#ifndef VOMT_H
+#define VOMT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VOMT_OK                      0
+#define VOMT_NOT_CONVERGED           1
+#define VOMT_ERR_BAD_ARG            -1   /* a size, pointer or parameter is invalid */
+#define VOMT_ERR_MASS_MISMATCH      -2   /* |sum rho0 - sum rho1| > 1e-5 max(sum rho0, sum rho1) */
+#define VOMT_ERR_NEGATIVE_DENSITY   -3   /* some density entry < 0 */
+#define VOMT_ERR_GRAPH              -4   /* channel graph not connected, self loop or repeated edge */
+#define VOMT_ERR_L_KERNEL           -5   /* ker grad_L on symmetric matrices is larger than span{I} */
+#define VOMT_ERR_STEP_CONDITION     -6   /* user step sizes break 1 > tau mu 8(n-1)^2 + tau nu lmax */
+#define VOMT_ERR_NONFINITE          -7   /* an input or an iterate became NaN / Inf */
+#define VOMT_ERR_BARRIER_TIMEOUT    -8   /* a device-side wait ran out of its iteration budget */
+#define VOMT_ERR_CUDA               -9   /* a CUDA runtime call failed (see vomt_last_error) */
+#define VOMT_ERR_TOO_LARGE         -10   /* the problem exceeds a documented size limit */
+
+/* Norm choices (Section 6.2).  u: per-channel Euclidean summed over channels
+ * (||u||_{1,2}, the Table 1 setting), joint Euclidean (||u||_2) or entrywise
+ * (||u||_1).  w: entrywise (||w||_1) or joint Euclidean (||w||_2). */
+#define VOMT_U_L12 0
+#define VOMT_U_L2  1
+#define VOMT_U_L1  2
+#define VOMT_W_L1  0
+#define VOMT_W_L2  1
+
+/* Engines.  AUTO picks RESIDENT when the whole state fits in the SMs'
+ * registers and shared memory, else STREAM. */
+#define VOMT_ENGINE_AUTO      0
+#define VOMT_ENGINE_STREAM    1   /* one fused stencil launch per iteration, state in HBM */
+#define VOMT_ENGINE_RESIDENT  2   /* one persistent launch, state on chip for the whole solve */
+
+#define VOMT_MAX_CHANNELS 8        /* k <= 8, so l <= 28 */
+
+typedef struct vomt_ctx vomt_ctx;
+
+/* The channel graph of Section 3.1: k nodes, l undirected edges {tail[e], head[e]}
+ * (0-based, any order inside a pair; each edge is oriented from its smaller to
+ * its larger node).  cost[e] > 0 is the cost c_e of changing along edge e
+ * (edge weight 1/c_e^2); cost == NULL means every c_e = 1.  Host memory. */
+typedef struct {
+    int k;
+    int n_edges;
+    const int *tail;
+    const int *head;
+    const double *cost;
+} vomt_graph;
+
+typedef struct {
+    double tau;          /* dual step; <= 0 picks Table 1's value: 1 for n <= 64, else 3 */
+    double mu, nu;       /* primal steps; <= 0 picks Section 7.2's rule
+                            mu = 1/(32 tau (n-1)^2), nu = 1/(4 tau lambda_max(-Delta_G));
+                            for l = 0 the scalar rule mu = 1/(16 tau (n-1)^2) of Section 7.1 */
+    int u_norm, w_norm;  /* VOMT_U_*, VOMT_W_* */
+    int max_iters;       /* iteration cap (>= 0) */
+    int check_every;     /* iterations between FP64 convergence checks (>= 1) */
+    double tol_gap;      /* stop when rel_gap <= tol_gap and rel_res <= tol_res; tol_gap <= 0
+                            runs exactly max_iters iterations */
+    double tol_res;
+    int warm_start;      /* 1: u, w, phi hold the initial iterate; 0: start from zero (Section 7
+                            leaves the initial guess open; zero is this library's default) */
+    int engine;          /* VOMT_ENGINE_* */
+} vomt_params;
+
+typedef struct {
+    double primal;       /* P = sum_ij ||u_ij||_u + alpha sum_ij ||w_ij||_w (Appendix A) */
+    double dual;         /* D = sum_ij <phi_ij, rho1_ij - rho0_ij> (eq. vomt-dual) */
+    double rel_gap;      /* |P - D| / |P|, the measure of Section 8.1 */
+    double rel_res;      /* ||div_x u + div_G w - (rho0 - rho1)||_2 / ||rho0 - rho1||_2 */
+    double fp_resid;     /* R of Section 6.1 between the last two iterates, weights 1/mu, 1/nu, 1/tau */
+    double dual_infeas;  /* max_ij max(||grad phi||_{u*} - 1, ||grad_G phi||_{w*} - alpha, 0) */
+    double mu, nu, tau;  /* step sizes used */
+    int iters;           /* iterations run */
+    int status;          /* VOMT_OK or VOMT_NOT_CONVERGED */
+    int engine;          /* engine that ran */
+    int checks;          /* convergence checks run */
+    int launches;        /* CUDA kernels this call launched */
+} vomt_result;
+
+/* Create a context on CUDA device `device`.  The context owns the solver's
+ * scratch memory (double-buffered iterates, FP64 partial sums, status words),
+ * grown on demand and freed by vomt_destroy.  Returns VOMT_OK or an error. */
+int vomt_create(vomt_ctx **out, int device);
+void vomt_destroy(vomt_ctx *ctx);
+const char *vomt_status_str(int status);
+const char *vomt_last_error(const vomt_ctx *ctx);
+
+/* Fill *p with the defaults: tau, mu, nu from the paper's rules, ||u||_{1,2},
+ * ||w||_1, max_iters 2000, check_every 100, tol_gap = tol_res = 0, cold start,
+ * engine AUTO. */
+void vomt_default_params(vomt_params *p);
+
+/* Step sizes of Section 7.2 for an n x n grid and graph g (host only, no GPU):
+ * lambda_max(-Delta_G) by Householder tridiagonalisation and Sturm bisection,
+ * then mu, nu from tau (tau <= 0 picks the Table 1 value).  Any output pointer
+ * may be NULL.  Errors: VOMT_ERR_BAD_ARG, VOMT_ERR_GRAPH. */
+int vomt_step_sizes(int n, const vomt_graph *g, double tau,
+                    double *mu, double *nu, double *tau_used, double *lmax_graph);
+
+/* Solve vector OMT (eq. (vomt)) by the V-OMT iteration of Section 7.2:
+ *   u <- shrink_u(u + mu grad phi; mu), w <- shrink_w(w + nu grad_G phi; alpha nu),
+ *   phi <- phi + tau (div_x(2u' - u) + div_G(2w' - w) + rho1 - rho0).
+ * n >= 2.  rho0, rho1: device [k][n][n].  u, w, phi: device outputs (inputs too
+ * when p->warm_start).  alpha > 0.  p == NULL uses the defaults.  *result
+ * (host) receives the metrics of the last check; every run ends with a check.
+ * Errors: BAD_ARG, MASS_MISMATCH, NEGATIVE_DENSITY, GRAPH, STEP_CONDITION,
+ * NONFINITE, TOO_LARGE, CUDA. */
+int vomt_solve(vomt_ctx *ctx, int n, const float *rho0, const float *rho1,
+               const vomt_graph *g, double alpha, const vomt_params *p,
+               float *u, float *w, float *phi, vomt_result *result, void *stream);
+
+/* The same solve with every array in host memory: the call copies rho0, rho1
+ * (and the warm-start iterate) to the context's device memory, solves, and
+ * copies u, w, phi back before it returns. */
+int vomt_solve_host(vomt_ctx *ctx, int n, const float *rho0, const float *rho1,
+                    const vomt_graph *g, double alpha, const vomt_params *p,
+                    float *u, float *w, float *phi, vomt_result *result, void *stream);
+
+/* Metrics of every convergence check of the last solve on ctx, 8 doubles per
+ * row: primal, dual, rel_gap, rel_res, fp_resid, dual_infeas, iteration,
+ * converged flag.  Writes min(cap, checks) rows to host `out`; returns the
+ * number of rows available, or a negative error. */
+int vomt_history(vomt_ctx *ctx, double *out, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VOMT_H */

@@ -1,0 +1,128 @@
+"""GB300-native vector / matrix L1 optimal mass transport by PDHG.
+
+Implements the primal-dual method of Ryu, Chen, Li and Osher, "Vector and
+Matrix Optimal Mass Transport: Theory, Algorithm, and Applications"
+(arXiv:1712.10279), Section 7, as hand-written sm_103a CUDA behind the C ABI in
+``include/vomt.h``.  This package is the thin Python layer over that ABI:
+torch provides device memory and streams, the library does all the work.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _native
+from ._native import VomtError, ENGINES
+
+U_L12, U_L2, U_L1 = 0, 1, 2
+W_L1, W_L2 = 0, 1
+
+__all__ = ["solve", "solve_host", "step_sizes", "history", "VomtError", "U_L12", "U_L2", "U_L1", "W_L1", "W_L2"]
+
+
+@dataclass
+class Solution:
+    u: object        # [2, k, n, n]: u_x planes then u_y planes
+    w: object        # [l, n, n]
+    phi: object      # [k, n, n]
+    result: dict
+
+
+def _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, warm, engine):
+    p = _native.Params()
+    _native.load().vomt_default_params(ctypes.byref(p))
+    p.tau = 0.0 if tau is None else float(tau)
+    p.mu = 0.0 if mu is None else float(mu)
+    p.nu = 0.0 if nu is None else float(nu)
+    p.u_norm, p.w_norm = int(u_norm), int(w_norm)
+    p.max_iters, p.check_every = int(max_iters), int(check_every)
+    p.tol_gap, p.tol_res = float(tol_gap), float(tol_res)
+    p.warm_start = int(bool(warm))
+    p.engine = ENGINES[engine] if isinstance(engine, str) else int(engine)
+    return p
+
+
+def step_sizes(n: int, k: int, edges, tau=None, cost=None):
+    """(mu, nu, tau, lambda_max(-Delta_G)) from the rules of Section 7.2."""
+    g = _native.GraphArg(k, edges, cost)
+    out = [ctypes.c_double() for _ in range(4)]
+    _native.check(_native.load().vomt_step_sizes(int(n), g.ref, 0.0 if tau is None else float(tau),
+                                                 *[ctypes.byref(x) for x in out]))
+    return tuple(x.value for x in out)
+
+
+def solve(rho0, rho1, edges, alpha: float = 1.0, *, tau=None, mu=None, nu=None, cost=None,
+          u_norm: int = U_L12, w_norm: int = W_L1, max_iters: int = 2000, check_every: int = 100,
+          tol_gap: float = 0.0, tol_res: float = 0.0, init=None, engine="auto", stream=None) -> Solution:
+    """Vector OMT (Section 7.2) on the GPU.
+
+    rho0, rho1: CUDA float32 tensors [k, n, n] (cell masses, [c, j, i], x fastest).
+    edges: node pairs of the channel graph (empty for k = 1).  init: optional
+    (u, w, phi) tensors to warm-start from.  Returns the final iterate and the
+    metrics of the last FP64 convergence check.
+    """
+    import torch
+    if not (rho0.is_cuda and rho1.is_cuda):
+        raise ValueError("rho0 and rho1 must be CUDA tensors")
+    rho0 = rho0.contiguous().float()
+    rho1 = rho1.contiguous().float()
+    k, n = rho0.shape[0], rho0.shape[-1]
+    dev = rho0.device
+    g = _native.GraphArg(k, edges, cost)
+    l = g.tail.size
+    if init is not None:
+        u = init[0].detach().clone().contiguous().float()
+        w = init[1].detach().clone().contiguous().float()
+        phi = init[2].detach().clone().contiguous().float()
+    else:
+        u = torch.empty((2, k, n, n), device=dev, dtype=torch.float32)
+        w = torch.empty((max(l, 0), n, n), device=dev, dtype=torch.float32)
+        phi = torch.empty((k, n, n), device=dev, dtype=torch.float32)
+    p = _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, init is not None, engine)
+    res = _native.Result()
+    st = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
+    ctx = _native.context(dev.index if dev.index is not None else torch.cuda.current_device())
+    rc = _native.load().vomt_solve(ctx, int(n), rho0.data_ptr(), rho1.data_ptr(), g.ref, float(alpha),
+                                   ctypes.byref(p), u.data_ptr(), w.data_ptr() if l else None, phi.data_ptr(),
+                                   ctypes.byref(res), ctypes.c_void_p(st))
+    _native.check(rc, ctx)
+    return Solution(u, w, phi, res.as_dict())
+
+
+def solve_host(rho0, rho1, edges, alpha: float = 1.0, *, tau=None, mu=None, nu=None, cost=None,
+               u_norm: int = U_L12, w_norm: int = W_L1, max_iters: int = 2000, check_every: int = 100,
+               tol_gap: float = 0.0, tol_res: float = 0.0, engine="auto", device: int = 0,
+               out=None) -> Solution:
+    """The same solve through vomt_solve_host: numpy float32 inputs and outputs in host
+    memory; the library copies them to and from the GPU inside the call."""
+    rho0 = np.ascontiguousarray(rho0, dtype=np.float32)
+    rho1 = np.ascontiguousarray(rho1, dtype=np.float32)
+    k, n = rho0.shape[0], rho0.shape[-1]
+    g = _native.GraphArg(k, edges, cost)
+    l = g.tail.size
+    if out is None:
+        out = (np.empty((2, k, n, n), np.float32), np.empty((max(l, 0), n, n), np.float32),
+               np.empty((k, n, n), np.float32))
+    u, w, phi = out
+    p = _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, False, engine)
+    res = _native.Result()
+    ctx = _native.context(device)
+    rc = _native.load().vomt_solve_host(ctx, int(n), rho0.ctypes.data, rho1.ctypes.data, g.ref, float(alpha),
+                                        ctypes.byref(p), u.ctypes.data, w.ctypes.data if l else None,
+                                        phi.ctypes.data, ctypes.byref(res), None)
+    _native.check(rc, ctx)
+    return Solution(u, w, phi, res.as_dict())
+
+
+def history(device: int = 0):
+    """Rows (primal, dual, rel_gap, rel_res, fp_resid, dual_infeas, iter, converged) of every
+    convergence check of the last solve on `device`."""
+    ctx = _native.context(device)
+    lib = _native.load()
+    rows = _native.check(lib.vomt_history(ctx, None, 0), ctx)
+    out = np.zeros((rows, 8))
+    if rows:
+        _native.check(lib.vomt_history(ctx, out.ctypes.data_as(_native.P_double), rows), ctx)
+    return out

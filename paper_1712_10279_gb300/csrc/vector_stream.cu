@@ -1,0 +1,577 @@
+// Streaming engine for vector OMT: one fused launch per PDHG iteration
+// (Section 7.2), state double-buffered in HBM, FP64 convergence checks.
+//
+// One thread owns one grid point (i, j) and all k channels of it.  The phi
+// update at (i, j) needs ubar = 2u' - u at (i, j), (i-1, j) and (i, j-1); the
+// thread recomputes the two neighbouring shrinks from phi and u instead of
+// waiting for the threads that own them, so one launch does a whole iteration
+// and no grid-wide barrier is needed between the u/w and phi halves
+// (Section 7.4 puts a synchronisation there).
+#include <math.h>
+
+#include "internal.h"
+
+namespace vomt {
+namespace {
+
+constexpr int BX = 32, BY = 8, NT = BX * BY;
+
+struct StateIn {
+    const float *phi, *ux, *uy, *w;
+};
+struct StateOut {
+    float *phi, *ux, *uy, *w;
+};
+
+// factor of shrink_2 (Appendix B): 1 - t/s for s = sqrt(s2) > t, else 0
+__device__ __forceinline__ float shrink2_factor(float s2, float t)
+{
+    return (s2 > t * t) ? (1.0f - t * rsqrtf(s2)) : 0.0f;
+}
+
+// shrink_1 (Appendix B): soft threshold
+__device__ __forceinline__ float soft(float x, float t)
+{
+    return (fabsf(x) > t) ? (x - copysignf(t, x)) : 0.0f;
+}
+
+template <int K>
+__device__ __forceinline__ float pick(const float (&a)[K], int idx)
+{
+    float r = 0.0f;
+#pragma unroll
+    for (int c = 0; c < K; ++c) r = (c == idx) ? a[c] : r;
+    return r;
+}
+
+// shrink_u on one point, all channels, in place (Section 7.2, u-update)
+template <int K, int UN>
+__device__ __forceinline__ void shrink_u(float (&vx)[K], float (&vy)[K], float t)
+{
+    if (UN == VOMT_U_L12) {
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            float f = shrink2_factor(vx[c] * vx[c] + vy[c] * vy[c], t);
+            vx[c] *= f;
+            vy[c] *= f;
+        }
+    } else if (UN == VOMT_U_L2) {
+        float s2 = 0.0f;
+#pragma unroll
+        for (int c = 0; c < K; ++c) s2 += vx[c] * vx[c] + vy[c] * vy[c];
+        float f = shrink2_factor(s2, t);
+#pragma unroll
+        for (int c = 0; c < K; ++c) { vx[c] *= f; vy[c] *= f; }
+    } else {
+#pragma unroll
+        for (int c = 0; c < K; ++c) { vx[c] = soft(vx[c], t); vy[c] = soft(vy[c], t); }
+    }
+}
+
+// shrink_w on one point (Section 7.2, w-update), l <= LK edges
+template <int LK, int WN>
+__device__ __forceinline__ void shrink_w(float (&x)[LK], int l, float t)
+{
+    if (WN == VOMT_W_L1) {
+#pragma unroll
+        for (int e = 0; e < LK; ++e)
+            if (e < l) x[e] = soft(x[e], t);
+    } else {
+        float s2 = 0.0f;
+#pragma unroll
+        for (int e = 0; e < LK; ++e)
+            if (e < l) s2 += x[e] * x[e];
+        float f = shrink2_factor(s2, t);
+#pragma unroll
+        for (int e = 0; e < LK; ++e) x[e] *= f;
+    }
+}
+
+template <int K>
+struct LKOf {
+    static constexpr int v = K * (K - 1) / 2 > 0 ? K * (K - 1) / 2 : 1;
+};
+
+// ----------------------------------------------------------------- iteration
+template <int K, int UN, int WN>
+__global__ void __launch_bounds__(NT) k_step(StateIn in, StateOut out, const float *__restrict__ b,
+                                              GraphDev g, StepDev s, const DevStatus *__restrict__ st)
+{
+    if (st->stop) return;
+    constexpr int LK = LKOf<K>::v;
+    const int n = s.n;
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    if (i >= n || j >= n) return;
+    const size_t nn = (size_t)n * n;
+    const size_t p = (size_t)j * n + i;
+    const bool hR = i < n - 1, hU = j < n - 1, hL = i > 0, hD = j > 0;
+    const float mu = s.mu, ih = s.ih;
+
+    float pc[K], pr[K], pu[K], pl[K], plu[K], pd[K], prd[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        const float *P = in.phi + c * nn + p;
+        pc[c] = __ldg(P);
+        pr[c] = hR ? __ldg(P + 1) : 0.0f;
+        pu[c] = hU ? __ldg(P + n) : 0.0f;
+        pl[c] = hL ? __ldg(P - 1) : 0.0f;
+        plu[c] = (hL && hU) ? __ldg(P - 1 + n) : 0.0f;
+        pd[c] = hD ? __ldg(P - n) : 0.0f;
+        prd[c] = (hR && hD) ? __ldg(P + 1 - n) : 0.0f;
+    }
+    // u' at (i, j)
+    float ux0[K], uy0[K], vx[K], vy[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        ux0[c] = __ldg(in.ux + c * nn + p);
+        uy0[c] = __ldg(in.uy + c * nn + p);
+        vx[c] = ux0[c] + (hR ? mu * (ih * (pr[c] - pc[c])) : 0.0f);
+        vy[c] = uy0[c] + (hU ? mu * (ih * (pu[c] - pc[c])) : 0.0f);
+    }
+    shrink_u<K, UN>(vx, vy, mu);
+    // u' at (i-1, j): only its x component enters div at (i, j)
+    float lx[K], ly[K], lx0[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        lx0[c] = hL ? __ldg(in.ux + c * nn + p - 1) : 0.0f;
+        float ly0 = hL ? __ldg(in.uy + c * nn + p - 1) : 0.0f;
+        lx[c] = lx0[c] + (hL ? mu * (ih * (pc[c] - pl[c])) : 0.0f);
+        ly[c] = ly0 + ((hL && hU) ? mu * (ih * (plu[c] - pl[c])) : 0.0f);
+    }
+    shrink_u<K, UN>(lx, ly, mu);
+    // u' at (i, j-1): only its y component enters div at (i, j)
+    float dx[K], dy[K], dy0[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        float dx0 = hD ? __ldg(in.ux + c * nn + p - n) : 0.0f;
+        dy0[c] = hD ? __ldg(in.uy + c * nn + p - n) : 0.0f;
+        dx[c] = dx0 + ((hR && hD) ? mu * (ih * (prd[c] - pd[c])) : 0.0f);
+        dy[c] = dy0[c] + (hD ? mu * (ih * (pc[c] - pd[c])) : 0.0f);
+    }
+    shrink_u<K, UN>(dx, dy, mu);
+    // w' at (i, j)
+    float w0[LK], wx[LK];
+#pragma unroll
+    for (int e = 0; e < LK; ++e) {
+        if (e < g.l) {
+            w0[e] = __ldg(in.w + e * nn + p);
+            float ge = g.inv_c[e] * (pick<K>(pc, g.lo[e]) - pick<K>(pc, g.hi[e]));
+            wx[e] = w0[e] + s.nu * ge;
+        } else {
+            w0[e] = 0.0f;
+            wx[e] = 0.0f;
+        }
+    }
+    shrink_w<LK, WN>(wx, g.l, s.alpha * s.nu);
+    // phi' = phi + tau (div_x ubar + div_G wbar + rho1 - rho0)
+    float r[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        float bxc = 2.0f * vx[c] - ux0[c];
+        float byc = 2.0f * vy[c] - uy0[c];
+        float bxl = hL ? 2.0f * lx[c] - lx0[c] : 0.0f;
+        float byd = hD ? 2.0f * dy[c] - dy0[c] : 0.0f;
+        r[c] = ih * ((bxc - bxl) + (byc - byd)) + __ldg(b + c * nn + p);
+    }
+#pragma unroll
+    for (int e = 0; e < LK; ++e) {
+        if (e < g.l) {
+            float v = g.inv_c[e] * (2.0f * wx[e] - w0[e]);
+            const int lo = g.lo[e], hi = g.hi[e];
+#pragma unroll
+            for (int c = 0; c < K; ++c) r[c] += (c == hi ? v : 0.0f) - (c == lo ? v : 0.0f);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        out.phi[c * nn + p] = pc[c] + s.tau * r[c];
+        out.ux[c * nn + p] = vx[c];
+        out.uy[c * nn + p] = vy[c];
+    }
+#pragma unroll
+    for (int e = 0; e < LK; ++e)
+        if (e < g.l) out.w[e * nn + p] = wx[e];
+}
+
+// ----------------------------------------------------------------- metrics
+__device__ __forceinline__ void block_reduce_store(double (&v)[NRED], double *dst)
+{
+    __shared__ double sh[NT / 32][NRED];
+    const int lane = (threadIdx.y * BX + threadIdx.x) & 31, wid = (threadIdx.y * BX + threadIdx.x) >> 5;
+#pragma unroll
+    for (int q = 0; q < NRED; ++q) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            double o = __shfl_down_sync(0xffffffffu, v[q], off);
+            v[q] = (q == RED_MAX) ? fmax(v[q], o) : v[q] + o;
+        }
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NRED; ++q) sh[wid][q] = v[q];
+    __syncthreads();
+    if (wid == 0 && lane < NRED) {
+        double a = sh[0][lane];
+        for (int w = 1; w < NT / 32; ++w) a = (lane == RED_MAX) ? fmax(a, sh[w][lane]) : a + sh[w][lane];
+        dst[lane] = a;
+    }
+}
+
+template <int K, int UN, int WN>
+__global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const float *__restrict__ b,
+                                                 GraphDev g, StepDev s, double *__restrict__ partials,
+                                                 const DevStatus *__restrict__ st)
+{
+    if (st->stop) return;
+    constexpr int LK = LKOf<K>::v;
+    const int n = s.n;
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    double v[NRED];
+#pragma unroll
+    for (int q = 0; q < NRED; ++q) v[q] = 0.0;
+    if (i < n && j < n) {
+        const size_t nn = (size_t)n * n, p = (size_t)j * n + i;
+        const bool hR = i < n - 1, hU = j < n - 1, hL = i > 0, hD = j > 0;
+        const double ih = (double)(n - 1), alpha = s.alpha;
+        double ux[K], uy[K], ph[K], bb[K], dph[K], rdiv[K], ddiv[K];
+        double nu_pt = 0.0, dn_u = 0.0;
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            const size_t q = c * nn + p;
+            ux[c] = cur.ux[q];
+            uy[c] = cur.uy[q];
+            ph[c] = cur.phi[q];
+            bb[c] = b[q];
+            dph[c] = ph[c] - (double)prv.phi[q];
+            double xl = hL ? (double)cur.ux[q - 1] : 0.0, yd = hD ? (double)cur.uy[q - n] : 0.0;
+            rdiv[c] = ih * ((ux[c] - xl) + (uy[c] - yd));
+            double dux = ux[c] - (double)prv.ux[q], duy = uy[c] - (double)prv.uy[q];
+            double dxl = hL ? (double)cur.ux[q - 1] - (double)prv.ux[q - 1] : 0.0;
+            double dyd = hD ? (double)cur.uy[q - n] - (double)prv.uy[q - n] : 0.0;
+            ddiv[c] = ih * ((dux - dxl) + (duy - dyd));
+            v[RED_DU] += dux * dux + duy * duy;
+            v[RED_DP] += dph[c] * dph[c];
+            v[RED_D] += ph[c] * bb[c];
+            v[RED_BB] += bb[c] * bb[c];
+            // norms of u and of grad phi
+            double gx = hR ? ih * ((double)cur.phi[q + 1] - ph[c]) : 0.0;
+            double gy = hU ? ih * ((double)cur.phi[q + n] - ph[c]) : 0.0;
+            if (UN == VOMT_U_L12) {
+                nu_pt += sqrt(ux[c] * ux[c] + uy[c] * uy[c]);
+                dn_u = fmax(dn_u, sqrt(gx * gx + gy * gy));
+            } else if (UN == VOMT_U_L2) {
+                nu_pt += ux[c] * ux[c] + uy[c] * uy[c];
+                dn_u += gx * gx + gy * gy;
+            } else {
+                nu_pt += fabs(ux[c]) + fabs(uy[c]);
+                dn_u = fmax(dn_u, fmax(fabs(gx), fabs(gy)));
+            }
+        }
+        if (UN == VOMT_U_L2) { nu_pt = sqrt(nu_pt); dn_u = sqrt(dn_u); }
+        double nw_pt = 0.0, dn_w = 0.0;
+#pragma unroll
+        for (int e = 0; e < LK; ++e) {
+            if (e < g.l) {
+                const size_t q = e * nn + p;
+                const int lo = g.lo[e], hi = g.hi[e];
+                const double ic = (double)g.inv_c[e];
+                double we = cur.w[q], dwe = we - (double)prv.w[q];
+                v[RED_DW] += dwe * dwe;
+                double ge = 0.0;
+#pragma unroll
+                for (int c = 0; c < K; ++c) {
+                    double sgn = (c == lo) ? 1.0 : (c == hi ? -1.0 : 0.0);
+                    ge += sgn * ph[c];
+                    rdiv[c] -= sgn * ic * we;      // div_G w = -D diag(1/c) w
+                    ddiv[c] -= sgn * ic * dwe;
+                }
+                ge *= ic;
+                if (WN == VOMT_W_L1) { nw_pt += fabs(we); dn_w = fmax(dn_w, fabs(ge)); }
+                else { nw_pt += we * we; dn_w += ge * ge; }
+            }
+        }
+        if (WN == VOMT_W_L2) { nw_pt = sqrt(nw_pt); dn_w = sqrt(dn_w); }
+        v[RED_P] = nu_pt + alpha * nw_pt;
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            double rc = rdiv[c] + bb[c];
+            v[RED_RR] += rc * rc;
+            v[RED_X] += dph[c] * ddiv[c];
+        }
+        double di = fmax(dn_u - 1.0, 0.0);
+        if (g.l > 0) di = fmax(di, dn_w - alpha);
+        v[RED_MAX] = di;
+    }
+    const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+    block_reduce_store(v, partials + (size_t)blk * NRED);
+}
+
+// Fixed-order sum of the per-block partials, the stopping decision and the
+// history row.  One block of 256 threads.
+__global__ void k_finalize(const double *__restrict__ partials, int nblocks, SolveCfg cfg, int t,
+                           DevStatus *st, double *hist, int hist_cap)
+{
+    if (st->stop) return;
+    __shared__ double sh[256];
+    __shared__ double S[NRED];
+    for (int q = 0; q < NRED; ++q) {
+        double a = 0.0;
+        for (int bk = threadIdx.x; bk < nblocks; bk += blockDim.x) {
+            double x = partials[(size_t)bk * NRED + q];
+            a = (q == RED_MAX) ? fmax(a, x) : a + x;
+        }
+        sh[threadIdx.x] = a;
+        __syncthreads();
+        for (int off = 128; off > 0; off >>= 1) {
+            if (threadIdx.x < off)
+                sh[threadIdx.x] = (q == RED_MAX) ? fmax(sh[threadIdx.x], sh[threadIdx.x + off])
+                                                 : sh[threadIdx.x] + sh[threadIdx.x + off];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) S[q] = sh[0];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double P = S[RED_P], D = S[RED_D];
+        double m[NMET];
+        m[0] = P;
+        m[1] = D;
+        m[2] = fabs(P - D) / fmax(fabs(P), 1e-300);
+        m[3] = sqrt(S[RED_RR]) / (S[RED_BB] > 0.0 ? sqrt(S[RED_BB]) : 1.0);
+        m[4] = S[RED_DU] / cfg.mu + (cfg.has_w ? S[RED_DW] / cfg.nu : 0.0) + S[RED_DP] / cfg.tau - 2.0 * S[RED_X];
+        m[5] = S[RED_MAX];
+        m[6] = (double)t;
+        bool finite = true;
+        for (int q = 0; q < 6; ++q) finite = finite && isfinite(m[q]);
+        bool conv = cfg.tol_gap > 0.0 && m[2] <= cfg.tol_gap && m[3] <= cfg.tol_res;
+        m[7] = conv ? 1.0 : 0.0;
+        for (int q = 0; q < NMET; ++q) st->met[q] = m[q];
+        if (hist && st->checks < hist_cap)
+            for (int q = 0; q < NMET; ++q) hist[(size_t)st->checks * NMET + q] = m[q];
+        st->checks += 1;
+        st->iter = t;
+        if (!finite) { st->error = VOMT_ERR_NONFINITE; st->stop = 1; }
+        if (conv) st->stop = 1;
+    }
+}
+
+// ----------------------------------------------------------------- setup / copy
+__global__ void k_prepare(int n, int k, int l, const float *__restrict__ rho0, const float *__restrict__ rho1,
+                          float *__restrict__ b, int warm, const float *__restrict__ u_in,
+                          const float *__restrict__ w_in, const float *__restrict__ phi_in, StateOut s0)
+{
+    const size_t nn = (size_t)n * n;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nn; q += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(q % n), j = (int)(q / n);
+        for (int c = 0; c < k; ++c) {
+            b[c * nn + q] = rho1[c * nn + q] - rho0[c * nn + q];
+            s0.phi[c * nn + q] = warm ? phi_in[c * nn + q] : 0.0f;
+            s0.ux[c * nn + q] = (warm && i < n - 1) ? u_in[c * nn + q] : 0.0f;
+            s0.uy[c * nn + q] = (warm && j < n - 1) ? u_in[(k + c) * nn + q] : 0.0f;
+        }
+        for (int e = 0; e < l; ++e) s0.w[e * nn + q] = warm ? w_in[e * nn + q] : 0.0f;
+    }
+}
+
+__global__ void k_copy_out(int n, int k, int l, StateIn s0, StateIn s1, const DevStatus *__restrict__ st,
+                           float *__restrict__ u, float *__restrict__ w, float *__restrict__ phi)
+{
+    const StateIn s = (st->iter & 1) ? s1 : s0;
+    const size_t nn = (size_t)n * n;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nn; q += (size_t)gridDim.x * blockDim.x) {
+        for (int c = 0; c < k; ++c) {
+            phi[c * nn + q] = s.phi[c * nn + q];
+            u[c * nn + q] = s.ux[c * nn + q];
+            u[(k + c) * nn + q] = s.uy[c * nn + q];
+        }
+        for (int e = 0; e < l; ++e) w[e * nn + q] = s.w[e * nn + q];
+    }
+}
+
+// density validation: per block sum0, sum1, min0, min1, nonfinite count
+__global__ void k_validate(size_t count, const float *__restrict__ r0, const float *__restrict__ r1,
+                           double *__restrict__ out)
+{
+    double s0 = 0.0, s1 = 0.0, m0 = 1e300, m1 = 1e300, bad = 0.0;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < count; q += (size_t)gridDim.x * blockDim.x) {
+        float a = r0[q], c = r1[q];
+        if (!isfinite(a) || !isfinite(c)) { bad += 1.0; continue; }
+        s0 += a; s1 += c;
+        m0 = fmin(m0, (double)a);
+        m1 = fmin(m1, (double)c);
+    }
+    __shared__ double sh[5][256];
+    sh[0][threadIdx.x] = s0; sh[1][threadIdx.x] = s1; sh[2][threadIdx.x] = m0; sh[3][threadIdx.x] = m1;
+    sh[4][threadIdx.x] = bad;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + off];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + off];
+            sh[2][threadIdx.x] = fmin(sh[2][threadIdx.x], sh[2][threadIdx.x + off]);
+            sh[3][threadIdx.x] = fmin(sh[3][threadIdx.x], sh[3][threadIdx.x + off]);
+            sh[4][threadIdx.x] += sh[4][threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) out[blockIdx.x * 5 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// ----------------------------------------------------------------- dispatch
+struct Launchers {
+    void (*step)(StateIn, StateOut, const float *, GraphDev, StepDev, const DevStatus *);
+    void (*metrics)(StateIn, StateIn, const float *, GraphDev, StepDev, double *, const DevStatus *);
+};
+
+template <int K, int UN, int WN>
+Launchers make_launchers()
+{
+    return Launchers{k_step<K, UN, WN>, k_metrics<K, UN, WN>};
+}
+
+template <int K>
+Launchers pick_norms(int un, int wn)
+{
+    if (un == VOMT_U_L12) return wn == VOMT_W_L1 ? make_launchers<K, 0, 0>() : make_launchers<K, 0, 1>();
+    if (un == VOMT_U_L2) return wn == VOMT_W_L1 ? make_launchers<K, 1, 0>() : make_launchers<K, 1, 1>();
+    return wn == VOMT_W_L1 ? make_launchers<K, 2, 0>() : make_launchers<K, 2, 1>();
+}
+
+Launchers pick(int k, int un, int wn)
+{
+    switch (k) {
+        case 1: return pick_norms<1>(un, wn);
+        case 2: return pick_norms<2>(un, wn);
+        case 3: return pick_norms<3>(un, wn);
+        case 4: return pick_norms<4>(un, wn);
+        case 5: return pick_norms<5>(un, wn);
+        case 6: return pick_norms<6>(un, wn);
+        case 7: return pick_norms<7>(un, wn);
+        default: return pick_norms<8>(un, wn);
+    }
+}
+
+}  // namespace
+
+int validate_densities(vomt_ctx *ctx, int planes, int n, const float *rho0, const float *rho1,
+                       cudaStream_t st, double *sums)
+{
+    const size_t count = (size_t)planes * n * n;
+    const int blocks = (int)((count + 255) / 256 < 1024 ? (count + 255) / 256 : 1024);
+    int rc = ensure_buffer(ctx, (void **)&ctx->partials, &ctx->partials_cap,
+                           sizeof(double) * (size_t)blocks * 5, "partials");
+    if (rc) return rc;
+    k_validate<<<blocks, 256, 0, st>>>(count, rho0, rho1, ctx->partials);
+    ctx->launches += 1;
+    std::vector<double> h((size_t)blocks * 5);
+    cudaError_t e = cudaMemcpyAsync(h.data(), ctx->partials, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return set_cuda_error(ctx, e, "validate");
+    sums[0] = sums[1] = sums[4] = 0.0;
+    sums[2] = sums[3] = 1e300;
+    for (int q = 0; q < blocks; ++q) {
+        sums[0] += h[q * 5 + 0];
+        sums[1] += h[q * 5 + 1];
+        sums[2] = fmin(sums[2], h[q * 5 + 2]);
+        sums[3] = fmin(sums[3], h[q * 5 + 3]);
+        sums[4] += h[q * 5 + 4];
+    }
+    return VOMT_OK;
+}
+
+int stream_solve(vomt_ctx *ctx, const GraphDev &g, const StepDev &s, const SolveCfg &cfg,
+                 const vomt_params &p, const float *rho0, const float *rho1,
+                 float *u, float *w, float *phi, cudaStream_t st)
+{
+    const int n = s.n, k = g.k, l = g.l;
+    const size_t nn = (size_t)n * n;
+    // workspace: b, then two states {phi, ux, uy, w}
+    const size_t per_state = (size_t)(3 * k + l) * nn;
+    const size_t need = (size_t)k * nn + 2 * per_state;
+    int rc = ensure_buffer(ctx, (void **)&ctx->ws, &ctx->ws_floats, need * sizeof(float), "workspace");
+    if (rc) return rc;
+    float *b = ctx->ws;
+    StateOut so[2];
+    StateIn si[2];
+    for (int q = 0; q < 2; ++q) {
+        float *base = ctx->ws + (size_t)k * nn + q * per_state;
+        so[q] = StateOut{base, base + (size_t)k * nn, base + (size_t)2 * k * nn, base + (size_t)3 * k * nn};
+        si[q] = StateIn{so[q].phi, so[q].ux, so[q].uy, so[q].w};
+    }
+    const dim3 blk(BX, BY), grd((n + BX - 1) / BX, (n + BY - 1) / BY);
+    const int nblocks = (int)(grd.x * grd.y);
+    rc = ensure_buffer(ctx, (void **)&ctx->partials, &ctx->partials_cap, sizeof(double) * (size_t)nblocks * NRED,
+                       "partials");
+    if (rc) return rc;
+    const int max_checks = p.max_iters / p.check_every + 2;
+    if (ctx->hist_cap < max_checks) {
+        if (ctx->dhist) cudaFree(ctx->dhist);
+        ctx->dhist = nullptr;
+        ctx->hist_cap = 0;
+        cudaError_t e = cudaMalloc(&ctx->dhist, sizeof(double) * NMET * (size_t)max_checks);
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "history");
+        ctx->hist_cap = max_checks;
+    }
+    cudaError_t e = cudaMemsetAsync(ctx->dstatus, 0, sizeof(DevStatus), st);
+    if (e != cudaSuccess) return set_cuda_error(ctx, e, "status reset");
+    const int pblocks = (int)((nn + 255) / 256 < 2048 ? (nn + 255) / 256 : 2048);
+    k_prepare<<<pblocks, 256, 0, st>>>(n, k, l, rho0, rho1, b, p.warm_start, u, w, phi, so[0]);
+    ctx->launches += 1;
+
+    Launchers L = pick(k, p.u_norm, p.w_norm);
+    auto check = [&](int t, int cur) {
+        L.metrics<<<grd, blk, 0, st>>>(si[cur], si[cur ^ 1], b, g, s, ctx->partials, ctx->dstatus);
+        k_finalize<<<1, 256, 0, st>>>(ctx->partials, nblocks, cfg, t, ctx->dstatus, ctx->dhist, ctx->hist_cap);
+        ctx->launches += 2;
+    };
+    if (p.max_iters == 0) {
+        L.metrics<<<grd, blk, 0, st>>>(si[0], si[0], b, g, s, ctx->partials, ctx->dstatus);
+        k_finalize<<<1, 256, 0, st>>>(ctx->partials, nblocks, cfg, 0, ctx->dstatus, ctx->dhist, ctx->hist_cap);
+        ctx->launches += 2;
+    }
+    const bool tol_mode = cfg.tol_gap > 0.0;
+    int chunk = p.check_every * ((2048 + p.check_every - 1) / p.check_every);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (tol_mode) {
+        for (int q = 0; q < 2; ++q) cudaEventCreateWithFlags(&ev[q], cudaEventDisableTiming);
+    }
+    int t = 0, nchunk = 0;
+    bool stopped = false;
+    while (t < p.max_iters && !stopped) {
+        const int end = t + chunk < p.max_iters ? t + chunk : p.max_iters;
+        for (int tt = t + 1; tt <= end; ++tt) {
+            const int cur = tt & 1;
+            L.step<<<grd, blk, 0, st>>>(si[cur ^ 1], so[cur], b, g, s, ctx->dstatus);
+            ctx->launches += 1;
+            if (tt % p.check_every == 0 || tt == p.max_iters) check(tt, cur);
+        }
+        t = end;
+        if (tol_mode) {
+            const int slot = nchunk & 1;
+            cudaMemcpyAsync(&ctx->hstatus[slot], ctx->dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, st);
+            cudaEventRecord(ev[slot], st);
+            if (nchunk >= 1) {
+                // the previous chunk's flag: the GPU keeps running the chunk just queued
+                cudaEventSynchronize(ev[slot ^ 1]);
+                if (ctx->hstatus[slot ^ 1].stop) stopped = true;
+            }
+            ++nchunk;
+        }
+    }
+    k_copy_out<<<pblocks, 256, 0, st>>>(n, k, l, si[0], si[1], ctx->dstatus, u, w, phi);
+    ctx->launches += 1;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        for (int q = 0; q < 2; ++q) if (ev[q]) cudaEventDestroy(ev[q]);
+        return set_cuda_error(ctx, e, "launch");
+    }
+    e = cudaMemcpyAsync(&ctx->hstatus[0], ctx->dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    for (int q = 0; q < 2; ++q) if (ev[q]) cudaEventDestroy(ev[q]);
+    if (e != cudaSuccess) return set_cuda_error(ctx, e, "solve");
+    return VOMT_OK;
+}
+
+}  // namespace vomt

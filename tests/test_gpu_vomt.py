@@ -1,0 +1,175 @@
+"""GPU parity of the vector-OMT solver (Section 7.2) against the FP64 oracle,
+called through the C ABI.  Tolerances: relative L2 <= 1e-3 on phi and u and
+relative <= 1e-4 on the primal objective at a fixed iteration count."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1712_10279_gb300 import synthetic as S
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+V = pytest.importorskip("paper_1712_10279_gb300")
+
+K3 = S.COMPLETE_K3
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def _gpu(r0, r1, edges, alpha, **kw):
+    d = _dev()
+    sol = V.solve(torch.from_numpy(r0.astype(np.float32)).to(d), torch.from_numpy(r1.astype(np.float32)).to(d),
+                  edges, alpha, **kw)
+    torch.cuda.synchronize()
+    return sol
+
+
+def _oracle(r0, r1, edges, alpha, **kw):
+    return oracle.vomt_solve(r0.astype(np.float32).astype(np.float64), r1.astype(np.float32).astype(np.float64),
+                             edges, alpha, **kw)
+
+
+def _compare(sol, ref, tol_field=1e-3, tol_obj=1e-4, k=None):
+    phi = sol.phi.cpu().numpy().astype(np.float64)
+    u = sol.u.cpu().numpy().astype(np.float64)
+    ru = np.stack([ref["ux"], ref["uy"]])
+    e_phi, e_u = _rel(phi, ref["phi"]), _rel(u, ru)
+    e_p = abs(sol.result["primal"] - ref["metrics"]["primal"]) / max(abs(ref["metrics"]["primal"]), 1e-300)
+    assert e_phi <= tol_field, ("phi", e_phi)
+    assert e_u <= tol_field, ("u", e_u)
+    assert e_p <= tol_obj, ("primal", e_p)
+    if ref["w"].size:
+        assert _rel(sol.w.cpu().numpy().astype(np.float64), ref["w"]) <= 10 * tol_field
+    return e_phi, e_u, e_p
+
+
+def test_parity_blob_32_k3_2000_iterations():
+    r0, r1 = S.blob_pair(32, 3, seed=1001)
+    sol = _gpu(r0, r1, K3, 1.0, max_iters=2000, check_every=100)
+    ref = _oracle(r0, r1, K3, 1.0, max_iters=2000, check_every=100, history=True)
+    assert sol.result["iters"] == 2000 and sol.result["checks"] == 20
+    errs = _compare(sol, ref)
+    print("32x32 k=3 2000 it: rel err phi %.2e u %.2e P %.2e" % errs)
+    # every check row agrees with the oracle's
+    h = V.history()
+    assert h.shape == (20, 8)
+    np.testing.assert_allclose(h[:, 6], ref["history"][:, 6])
+    np.testing.assert_allclose(h[:, 0], ref["history"][:, 0], rtol=1e-4)
+    np.testing.assert_allclose(h[:, 3], ref["history"][:, 3], rtol=2e-2)
+    np.testing.assert_allclose(h[:, 2], ref["history"][:, 2], rtol=5e-2, atol=1e-5)
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 33, 47, 70])
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_parity_sizes_and_channels(n, k):
+    rng = np.random.default_rng(100 * n + k)
+    edges = S.random_connected_graph(rng, k, 0.6)
+    r0, r1 = S.blob_pair(n, k, seed=10 * n + k) if n >= 5 else (rng.uniform(0.1, 1, (k, n, n)), rng.uniform(0.1, 1, (k, n, n)))
+    r0 = r0 / r0.sum(); r1 = r1 / r1.sum()
+    sol = _gpu(r0, r1, edges, 0.7, max_iters=300, check_every=60)
+    ref = _oracle(r0, r1, edges, 0.7, max_iters=300, check_every=60)
+    _compare(sol, ref)
+
+
+@pytest.mark.parametrize("u_norm,w_norm", [(0, 1), (1, 0), (1, 1), (2, 0), (2, 1)])
+def test_parity_norms(u_norm, w_norm):
+    r0, r1 = S.blob_pair(40, 3, seed=77)
+    sol = _gpu(r0, r1, K3, 2.0, u_norm=u_norm, w_norm=w_norm, max_iters=500, check_every=100)
+    ref = _oracle(r0, r1, K3, 2.0, u_norm=u_norm, w_norm=w_norm, max_iters=500, check_every=100)
+    _compare(sol, ref)
+
+
+def test_parity_edge_costs_and_tau():
+    r0, r1 = S.blob_pair(36, 4, seed=5)
+    edges = [(0, 1), (1, 2), (2, 3), (0, 3)]
+    cost = [1.0, 0.5, 2.0, 1.5]
+    sol = _gpu(r0, r1, edges, 1.0, cost=cost, tau=4.0, max_iters=400, check_every=100)
+    ref = _oracle(r0, r1, edges, 1.0, cost=cost, tau=4.0, max_iters=400, check_every=100)
+    _compare(sol, ref)
+
+
+def test_one_step_from_gpu_state_at_256():
+    """At the full 256 x 256 colour-image size: one GPU iteration from a mid-run GPU state
+    against one FP64 oracle iteration from the same state."""
+    r0, r1 = S.color_image_pair(256, 3, seed=1002)
+    mid = _gpu(r0, r1, K3, 1.0, max_iters=300, check_every=100)
+    nxt = _gpu(r0, r1, K3, 1.0, max_iters=1, check_every=1, init=(mid.u, mid.w, mid.phi))
+    u0 = mid.u.cpu().numpy().astype(np.float64)
+    init = dict(ux=u0[0], uy=u0[1], w=mid.w.cpu().numpy().astype(np.float64),
+                phi=mid.phi.cpu().numpy().astype(np.float64))
+    ref = _oracle(r0, r1, K3, 1.0, max_iters=1, check_every=1, init=init)
+    u1 = nxt.u.cpu().numpy().astype(np.float64)
+    assert _rel(u1, np.stack([ref["ux"], ref["uy"]])) < 1e-5
+    assert _rel(nxt.w.cpu().numpy().astype(np.float64), ref["w"]) < 1e-5
+    dphi_g = nxt.phi.cpu().numpy().astype(np.float64) - init["phi"]
+    dphi_o = ref["phi"] - init["phi"]
+    assert _rel(dphi_g, dphi_o) < 2e-2
+    assert _rel(nxt.phi.cpu().numpy().astype(np.float64), ref["phi"]) < 1e-6
+
+
+def test_tolerance_stop_matches_oracle():
+    r0, r1 = S.blob_pair(32, 3, seed=1001)
+    kw = dict(max_iters=20000, check_every=100, tol_gap=1e-3, tol_res=1e-3)
+    sol = _gpu(r0, r1, K3, 1.0, **kw)
+    ref = _oracle(r0, r1, K3, 1.0, **kw)
+    assert sol.result["status"] == 0
+    assert abs(sol.result["iters"] - ref["iters"]) <= 100
+    assert sol.result["rel_gap"] <= 1e-3 and sol.result["rel_res"] <= 1e-3
+
+
+def test_invariants_on_gpu():
+    r0, r1 = S.color_image_pair(128, 3, seed=3)
+    sol = _gpu(r0, r1, K3, 1.0, max_iters=1000, check_every=250)
+    u = sol.u.cpu().numpy()
+    assert np.all(u[0, :, :, -1] == 0) and np.all(u[1, :, -1, :] == 0)   # ghost cells stay zero
+    phi = sol.phi.cpu().numpy().astype(np.float64)
+    assert abs(phi.sum()) < 1e-4 * np.abs(phi).sum()                     # Sum phi stays ~0
+    h = V.history()
+    assert np.all(np.diff(h[:, 4]) <= 1e-6 * h[0, 4])                    # R non-increasing
+
+
+def test_host_api_matches_device_api():
+    r0, r1 = S.blob_pair(48, 3, seed=9)
+    dsol = _gpu(r0, r1, K3, 1.0, max_iters=250, check_every=50)
+    hsol = V.solve_host(r0.astype(np.float32), r1.astype(np.float32), K3, 1.0, max_iters=250, check_every=50)
+    np.testing.assert_array_equal(hsol.phi, dsol.phi.cpu().numpy())
+    np.testing.assert_array_equal(hsol.u, dsol.u.cpu().numpy())
+    assert hsol.result["primal"] == dsol.result["primal"]
+
+
+def test_input_errors():
+    r0, r1 = S.blob_pair(16, 3, seed=2)
+    with pytest.raises(V.VomtError) as e:
+        _gpu(r0, 1.01 * r1, K3, 1.0, max_iters=5)
+    assert e.value.status == -2
+    bad = r1.copy(); bad[0, 3, 3] = -1e-3; bad[1, 2, 2] += 1e-3
+    with pytest.raises(V.VomtError) as e:
+        _gpu(r0, bad, K3, 1.0, max_iters=5)
+    assert e.value.status == -3
+    bad = r1.copy(); bad[0, 0, 0] = np.nan
+    with pytest.raises(V.VomtError) as e:
+        _gpu(r0, bad, K3, 1.0, max_iters=5)
+    assert e.value.status == -7
+    with pytest.raises(V.VomtError) as e:
+        _gpu(r0, r1, K3, 1.0, max_iters=5, mu=1.0, nu=1.0)
+    assert e.value.status == -6
+    with pytest.raises(V.VomtError) as e:
+        _gpu(r0, r1, K3, -1.0, max_iters=5)
+    assert e.value.status == -1
+
+
+def test_zero_iterations_and_identical_densities():
+    r0, _ = S.blob_pair(20, 3, seed=4)
+    sol = _gpu(r0, r0, K3, 1.0, max_iters=0)
+    assert sol.result["iters"] == 0 and sol.result["primal"] == 0.0
+    sol = _gpu(r0, r0, K3, 1.0, max_iters=50, check_every=10)
+    assert sol.result["primal"] == 0.0 and float(sol.phi.abs().max()) == 0.0
