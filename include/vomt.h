@@ -162,6 +162,41 @@ int vomt_solve_host(vomt_ctx *ctx, int n, const float *rho0, const float *rho1,
  * number of rows available, or a negative error. */
 int vomt_history(vomt_ctx *ctx, double *out, int cap);
 
+/* ------------------------------------------------------------------------ */
+/* Allocation-free solve.  The paper has no counterpart: this is a            */
+/* deployment feature of this library.                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Size of the fixed device scratch array behind vomt_solve_noalloc: 16 MiB,
+ * enough for n = 256 with k = 3 channels and 3 edges (the solve needs
+ * 4 (7k + 2l) n^2 bytes, plus 80 bytes per 256 grid points and 11 KB). */
+#define VOMT_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* The vomt_solve computation (streaming engine) for callers that cannot
+ * allocate device memory: code running during CUDA graph capture, where
+ * cudaMalloc is not allowed; applications whose device memory belongs to one
+ * custom pool; plug-ins that must not grow the process footprint after
+ * start-up.  It needs no context and never allocates or frees memory: its
+ * scratch is one fixed array of VOMT_NOALLOC_SCRATCH_BYTES in the library's
+ * device image, which every GPU that loads the library holds until the
+ * process exits.
+ *   - Runs on the calling thread's current CUDA device; `stream` must belong
+ *     to it.  The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call shares the one array and overwrites it (the status block is
+ *     cleared at the start of each call), so calls that overlap on the GPU --
+ *     from other streams or host threads -- race and give wrong results.
+ *     Serialise them.
+ *   - Arguments, layouts and results are those of vomt_solve; p->engine is
+ *     ignored (always the streaming engine), and vomt_history() does not see
+ *     these solves.  The call synchronises `stream` to read its results.
+ *   - Problems whose scratch would exceed the array return VOMT_ERR_TOO_LARGE
+ *     before any GPU work.  `error` (may be NULL) receives a static message.
+ */
+int vomt_solve_noalloc(int n, const float *rho0, const float *rho1, const vomt_graph *g,
+                       double alpha, const vomt_params *p, float *u, float *w, float *phi,
+                       vomt_result *result, void *stream, const char **error);
+
 #ifdef __cplusplus
 }
 #endif

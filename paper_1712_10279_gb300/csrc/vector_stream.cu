@@ -575,3 +575,205 @@ int stream_solve(vomt_ctx *ctx, const GraphDev &g, const StepDev &s, const Solve
 }
 
 }  // namespace vomt
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the streaming solve (vomt_solve_noalloc).
+//
+// Some callers cannot allocate device memory: code that runs while a CUDA
+// graph is being captured (cudaMalloc is not allowed then), applications whose
+// device memory is owned by one custom pool or allocator, and plug-ins that
+// must not grow the process's footprint after start-up.  For them this entry
+// point takes its scratch (double-buffered iterates, b = rho1 - rho0, FP64
+// partial sums, the status block) from one fixed array of
+// VOMT_NOALLOC_SCRATCH_BYTES bytes that is part of the library image: every
+// GPU that loads the library holds it until the process exits, and no call
+// ever allocates or frees memory.  Every call shares the array, so calls that
+// overlap on the GPU (other streams, other host threads) race with each other.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[VOMT_NOALLOC_SCRATCH_BYTES];
+
+namespace vomt {
+namespace {
+
+constexpr int kNoAllocMaxDevices = 256;
+std::mutex g_noalloc_mu;
+void *g_noalloc_base[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once per
+// device (the first call on a device does this set-up).
+int noalloc_base(void **out, const char **why)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) { *why = "cudaGetDevice failed"; return VOMT_ERR_CUDA; }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) { *why = "cudaGetSymbolAddress failed for the scratch array"; return VOMT_ERR_CUDA; }
+        g_noalloc_base[dev] = p;
+    }
+    *out = g_noalloc_base[dev];
+    return VOMT_OK;
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+}  // namespace vomt
+
+extern "C" int vomt_solve_noalloc(int n, const float *rho0, const float *rho1, const vomt_graph *graph, double alpha,
+                                  const vomt_params *pin, float *u, float *w, float *phi, vomt_result *result,
+                                  void *stream, const char **error)
+{
+    using namespace vomt;
+    const char *dummy = nullptr;
+    const char **why = error ? error : &dummy;
+    *why = "";
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n < 2 || n > 32768) { *why = "n must be in [2, 32768]"; return VOMT_ERR_BAD_ARG; }
+    if (!(alpha > 0.0) || !isfinite(alpha)) { *why = "alpha must be positive"; return VOMT_ERR_BAD_ARG; }
+    vomt_params p;
+    vomt_default_params(&p);
+    if (pin) p = *pin;
+    if (p.max_iters < 0 || p.check_every < 1) { *why = "max_iters >= 0, check_every >= 1"; return VOMT_ERR_BAD_ARG; }
+    if (p.u_norm < 0 || p.u_norm > 2 || p.w_norm < 0 || p.w_norm > 1) { *why = "bad norm code"; return VOMT_ERR_BAD_ARG; }
+    GraphDev g;
+    std::string gerr;
+    int rc = graph_to_dev(graph, &g, &gerr);
+    if (rc) { *why = "invalid channel graph"; return rc; }
+    if (!rho0 || !rho1 || !u || !phi || (g.l > 0 && !w)) { *why = "null array"; return VOMT_ERR_BAD_ARG; }
+    const double tau = p.tau > 0.0 ? p.tau : (n <= 64 ? 1.0 : 3.0);
+    const double lmax = graph_lmax(g, graph->cost);
+    const double n1 = (double)(n - 1);
+    double mu = p.mu, nu = p.nu;
+    const bool user = mu > 0.0 || nu > 0.0;
+    if (!(mu > 0.0)) mu = g.l > 0 ? 1.0 / (32.0 * tau * n1 * n1) : 1.0 / (16.0 * tau * n1 * n1);
+    if (!(nu > 0.0)) nu = g.l > 0 ? 1.0 / (4.0 * tau * lmax) : 1.0;
+    if (user && !(tau * mu * 8.0 * n1 * n1 + (g.l > 0 ? tau * nu * lmax : 0.0) < 1.0)) {
+        *why = "step sizes break the PDHG condition";
+        return VOMT_ERR_STEP_CONDITION;
+    }
+    StepDev s{n, (float)n1, (float)mu, (float)nu, (float)tau, (float)alpha};
+    SolveCfg cfg{p.tol_gap, p.tol_res, mu, nu, tau, g.l > 0};
+
+    // carve the scratch array
+    const int k = g.k, l = g.l;
+    const size_t nn = (size_t)n * n;
+    const dim3 blk(BX, BY), grd((n + BX - 1) / BX, (n + BY - 1) / BY);
+    const int nblocks = (int)(grd.x * grd.y);
+    const size_t count = (size_t)k * nn;
+    const int vblocks = (int)((count + 255) / 256 < 256 ? (count + 255) / 256 : 256);
+    const size_t off_status = 0;
+    const size_t off_vpart = align256(off_status + sizeof(DevStatus));
+    const size_t off_part = align256(off_vpart + sizeof(double) * 5 * (size_t)vblocks);
+    const size_t off_b = align256(off_part + sizeof(double) * NRED * (size_t)nblocks);
+    const size_t per_state = (size_t)(3 * k + l) * nn;
+    const size_t off_s0 = align256(off_b + sizeof(float) * (size_t)k * nn);
+    const size_t off_s1 = align256(off_s0 + sizeof(float) * per_state);
+    const size_t total = align256(off_s1 + sizeof(float) * per_state);
+    if (total > (size_t)VOMT_NOALLOC_SCRATCH_BYTES) {
+        *why = "problem needs more scratch than VOMT_NOALLOC_SCRATCH_BYTES";
+        return VOMT_ERR_TOO_LARGE;
+    }
+    void *basev = nullptr;
+    rc = noalloc_base(&basev, why);
+    if (rc) return rc;
+    unsigned char *base = (unsigned char *)basev;
+    DevStatus *dstatus = (DevStatus *)(base + off_status);
+    double *vpart = (double *)(base + off_vpart);
+    double *partials = (double *)(base + off_part);
+    float *b = (float *)(base + off_b);
+    StateOut so[2];
+    StateIn si[2];
+    for (int q = 0; q < 2; ++q) {
+        float *sb = (float *)(base + (q ? off_s1 : off_s0));
+        so[q] = StateOut{sb, sb + (size_t)k * nn, sb + (size_t)2 * k * nn, sb + (size_t)3 * k * nn};
+        si[q] = StateIn{so[q].phi, so[q].ux, so[q].uy, so[q].w};
+    }
+    int launches = 0;
+
+    // density checks (the scratch keeps the previous call's contents: every slot read below is written first)
+    k_validate<<<vblocks, 256, 0, st>>>(count, rho0, rho1, vpart);
+    ++launches;
+    double hv[5 * 256];
+    cudaError_t e = cudaMemcpyAsync(hv, vpart, sizeof(double) * 5 * (size_t)vblocks, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { *why = cudaGetErrorString(e); return VOMT_ERR_CUDA; }
+    double s0 = 0.0, s1 = 0.0, m0 = 1e300, m1 = 1e300, bad = 0.0;
+    for (int q = 0; q < vblocks; ++q) {
+        s0 += hv[q * 5 + 0];
+        s1 += hv[q * 5 + 1];
+        m0 = fmin(m0, hv[q * 5 + 2]);
+        m1 = fmin(m1, hv[q * 5 + 3]);
+        bad += hv[q * 5 + 4];
+    }
+    if (bad > 0.0) { *why = "density has NaN or Inf entries"; return VOMT_ERR_NONFINITE; }
+    if (m0 < 0.0 || m1 < 0.0) { *why = "density has negative entries"; return VOMT_ERR_NEGATIVE_DENSITY; }
+    if (fabs(s0 - s1) > 1e-5 * fmax(fabs(s0), fabs(s1))) { *why = "rho0 and rho1 have different total mass"; return VOMT_ERR_MASS_MISMATCH; }
+
+    // the status block must start at zero; iterates and b are written by k_prepare
+    e = cudaMemsetAsync(dstatus, 0, sizeof(DevStatus), st);
+    if (e != cudaSuccess) { *why = cudaGetErrorString(e); return VOMT_ERR_CUDA; }
+    const int pblocks = (int)((nn + 255) / 256 < 2048 ? (nn + 255) / 256 : 2048);
+    k_prepare<<<pblocks, 256, 0, st>>>(n, k, l, rho0, rho1, b, p.warm_start, u, w, phi, so[0]);
+    ++launches;
+    Launchers L = pick(k, p.u_norm, p.w_norm);
+    if (p.max_iters == 0) {
+        L.metrics<<<grd, blk, 0, st>>>(si[0], si[0], b, g, s, partials, dstatus);
+        k_finalize<<<1, 256, 0, st>>>(partials, nblocks, cfg, 0, dstatus, nullptr, 0);
+        launches += 2;
+    }
+    const bool tol_mode = cfg.tol_gap > 0.0;
+    const int chunk = p.check_every * ((2048 + p.check_every - 1) / p.check_every);
+    DevStatus hs;
+    int t = 0;
+    while (t < p.max_iters) {
+        const int end = t + chunk < p.max_iters ? t + chunk : p.max_iters;
+        for (int tt = t + 1; tt <= end; ++tt) {
+            const int cur = tt & 1;
+            L.step<<<grd, blk, 0, st>>>(si[cur ^ 1], so[cur], b, g, s, dstatus);
+            ++launches;
+            if (tt % p.check_every == 0 || tt == p.max_iters) {
+                L.metrics<<<grd, blk, 0, st>>>(si[cur], si[cur ^ 1], b, g, s, partials, dstatus);
+                k_finalize<<<1, 256, 0, st>>>(partials, nblocks, cfg, tt, dstatus, nullptr, 0);
+                launches += 2;
+            }
+        }
+        t = end;
+        if (tol_mode && t < p.max_iters) {
+            e = cudaMemcpyAsync(&hs, dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) { *why = cudaGetErrorString(e); return VOMT_ERR_CUDA; }
+            if (hs.stop) break;
+        }
+    }
+    k_copy_out<<<pblocks, 256, 0, st>>>(n, k, l, si[0], si[1], dstatus, u, w, phi);
+    ++launches;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { *why = cudaGetErrorString(e); return VOMT_ERR_CUDA; }
+    int status = VOMT_OK;
+    if (hs.error) { status = hs.error; *why = "iterate became non-finite"; }
+    else if (cfg.tol_gap > 0.0 && hs.met[7] == 0.0) status = VOMT_NOT_CONVERGED;
+    if (result) {
+        result->primal = hs.met[0];
+        result->dual = hs.met[1];
+        result->rel_gap = hs.met[2];
+        result->rel_res = hs.met[3];
+        result->fp_resid = hs.met[4];
+        result->dual_infeas = hs.met[5];
+        result->mu = mu;
+        result->nu = nu;
+        result->tau = tau;
+        result->iters = hs.iter;
+        result->status = status;
+        result->engine = VOMT_ENGINE_STREAM;
+        result->checks = hs.checks;
+        result->launches = launches;
+    }
+    return status;
+}
