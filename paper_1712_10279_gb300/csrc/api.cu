@@ -148,9 +148,21 @@ static int solve_device(vomt_ctx *ctx, int n, const float *rho0, const float *rh
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "cudaSetDevice");
     rc = check_densities(ctx, P.g.k, n, rho0, rho1, st);
     if (rc) return rc;
-    const int engine = VOMT_ENGINE_STREAM;
-    rc = stream_solve(ctx, P.g, P.s, P.cfg, P.p, rho0, rho1, u, w, phi, st);
-    if (rc) return rc;
+    int engine = VOMT_ENGINE_STREAM;
+    if (P.p.engine != VOMT_ENGINE_STREAM) {
+        ResidentPlan plan;
+        if (resident_plan(n, P.g.k, ctx->sm_count, &plan)) {
+            rc = resident_solve(ctx, P.g, P.s, P.cfg, P.p, plan, rho0, rho1, u, w, phi, st);
+            if (rc == VOMT_OK) engine = VOMT_ENGINE_RESIDENT;
+            else if (!(rc == VOMT_ERR_TOO_LARGE && P.p.engine == VOMT_ENGINE_AUTO)) return rc;
+        } else if (P.p.engine == VOMT_ENGINE_RESIDENT) {
+            return fail(ctx, VOMT_ERR_TOO_LARGE, "grid too large for the resident engine");
+        }
+    }
+    if (engine == VOMT_ENGINE_STREAM) {
+        rc = stream_solve(ctx, P.g, P.s, P.cfg, P.p, rho0, rho1, u, w, phi, st);
+        if (rc) return rc;
+    }
     int status = 0;
     fill_result(ctx, P, engine, result, &status);
     return status;

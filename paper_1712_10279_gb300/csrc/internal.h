@@ -101,6 +101,14 @@ int ensure_buffer(vomt_ctx *ctx, void **p, size_t *cap, size_t bytes, const char
 int stream_solve(vomt_ctx *ctx, const GraphDev &g, const StepDev &s, const SolveCfg &cfg,
                  const vomt_params &p, const float *rho0, const float *rho1,
                  float *u, float *w, float *phi, cudaStream_t st);
+// resident engine (vector_resident.cu)
+struct ResidentPlan {
+    int Gx, Gy, TXm, TYm, threads;
+};
+bool resident_plan(int n, int k, int max_blocks, ResidentPlan *out);
+int resident_solve(vomt_ctx *ctx, const GraphDev &g, const StepDev &s, const SolveCfg &cfg, const vomt_params &p,
+                   const ResidentPlan &plan, const float *rho0, const float *rho1, float *u, float *w, float *phi,
+                   cudaStream_t st);
 int validate_densities(vomt_ctx *ctx, int planes, int n, const float *rho0, const float *rho1,
                        cudaStream_t st, double *sums /* s0, s1, min0, min1, nonfinite */);
 }  // namespace vomt

@@ -1,0 +1,182 @@
+// Device helpers shared by the resident engines: the shrink operators of
+// Appendix B with the norm picked at run time (the branch is uniform across a
+// launch), tagged 64-bit exchange words and bounded waits.
+#pragma once
+
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace vomt {
+namespace dev {
+
+// factor of shrink_2 (Appendix B): 1 - t/s for s = sqrt(s2) > t, else 0
+__device__ __forceinline__ float shrink2_factor(float s2, float t)
+{
+    return (s2 > t * t) ? (1.0f - t * rsqrtf(s2)) : 0.0f;
+}
+
+// shrink_1 (Appendix B): soft threshold
+__device__ __forceinline__ float soft(float x, float t)
+{
+    return (fabsf(x) > t) ? (x - copysignf(t, x)) : 0.0f;
+}
+
+template <int K>
+__device__ __forceinline__ float pick(const float (&a)[K], int idx)
+{
+    float r = 0.0f;
+#pragma unroll
+    for (int c = 0; c < K; ++c) r = (c == idx) ? a[c] : r;
+    return r;
+}
+
+// shrink_u on one point (all channels), in place; un = VOMT_U_*
+template <int K>
+__device__ __forceinline__ void shrink_u(float (&vx)[K], float (&vy)[K], float t, int un)
+{
+    if (un == VOMT_U_L12) {
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            float f = shrink2_factor(vx[c] * vx[c] + vy[c] * vy[c], t);
+            vx[c] *= f;
+            vy[c] *= f;
+        }
+    } else if (un == VOMT_U_L2) {
+        float s2 = 0.0f;
+#pragma unroll
+        for (int c = 0; c < K; ++c) s2 += vx[c] * vx[c] + vy[c] * vy[c];
+        float f = shrink2_factor(s2, t);
+#pragma unroll
+        for (int c = 0; c < K; ++c) { vx[c] *= f; vy[c] *= f; }
+    } else {
+#pragma unroll
+        for (int c = 0; c < K; ++c) { vx[c] = soft(vx[c], t); vy[c] = soft(vy[c], t); }
+    }
+}
+
+// shrink_w on one point, l <= LK edges; wn = VOMT_W_*
+template <int LK>
+__device__ __forceinline__ void shrink_w(float (&x)[LK], int l, float t, int wn)
+{
+    if (wn == VOMT_W_L1) {
+#pragma unroll
+        for (int e = 0; e < LK; ++e)
+            if (e < l) x[e] = soft(x[e], t);
+    } else {
+        float s2 = 0.0f;
+#pragma unroll
+        for (int e = 0; e < LK; ++e)
+            if (e < l) s2 += x[e] * x[e];
+        float f = shrink2_factor(s2, t);
+#pragma unroll
+        for (int e = 0; e < LK; ++e) x[e] *= f;
+    }
+}
+
+// ---------------------------------------------------------------- exchange words
+// A 64-bit word carries one FP32 value in its low half and a 32-bit tag (the
+// iteration it belongs to, plus one) in its high half.  Aligned 64-bit stores
+// and loads are single-copy atomic, so a reader that sees the expected tag also
+// sees the value written with it: no separate flag, no fence.
+__device__ __forceinline__ void st_tagged(unsigned long long *p, float v, uint32_t tag)
+{
+    unsigned long long w = ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint(v);
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long *p)
+{
+    unsigned long long w;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+    return w;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed32(const uint32_t *p)
+{
+    uint32_t w;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(w) : "l"(p) : "memory");
+    return w;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire32(const uint32_t *p)
+{
+    uint32_t w;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(w) : "l"(p) : "memory");
+    return w;
+}
+
+__device__ __forceinline__ void st_release32(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ double ld_relaxed_f64(const double *p)
+{
+    double w;
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(w) : "l"(p) : "memory");
+    return w;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Control words of a resident launch (device memory, zeroed before the launch).
+struct ResCtl {
+    uint32_t abort;     // set by the first wait that runs out of time
+    uint32_t where;     // which wait gave up (diagnostics)
+};
+
+constexpr uint64_t kWaitBudgetNs = 2000000000ull;   // 2 s per wait
+
+// Spin until *p carries `tag`; returns false (and raises the abort flag) if the
+// wait exceeds its budget or another block already aborted.
+__device__ __forceinline__ bool wait_tagged(const unsigned long long *p, uint32_t tag, float *out, ResCtl *ctl,
+                                            uint32_t where)
+{
+    unsigned long long w = ld_relaxed64(p);
+    if ((uint32_t)(w >> 32) == tag) {
+        *out = __uint_as_float((uint32_t)w);
+        return true;
+    }
+    const uint64_t t0 = global_ns();
+    for (uint32_t polls = 1;; ++polls) {
+        w = ld_relaxed64(p);
+        if ((uint32_t)(w >> 32) == tag) break;
+        if ((polls & 255u) == 0u) {
+            if (ld_relaxed32(&ctl->abort)) return false;
+            if (global_ns() - t0 > kWaitBudgetNs) {
+                atomicExch(&ctl->abort, 1u);
+                atomicExch(&ctl->where, where);
+                return false;
+            }
+        }
+    }
+    *out = __uint_as_float((uint32_t)w);
+    return true;
+}
+
+// Spin until *flag >= v (acquire); false on timeout / abort.
+__device__ __forceinline__ bool wait_flag(const uint32_t *flag, uint32_t v, ResCtl *ctl, uint32_t where)
+{
+    if (ld_acquire32(flag) >= v) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t polls = 1;; ++polls) {
+        if (ld_acquire32(flag) >= v) return true;
+        if ((polls & 255u) == 0u) {
+            if (ld_relaxed32(&ctl->abort)) return false;
+            if (global_ns() - t0 > kWaitBudgetNs) {
+                atomicExch(&ctl->abort, 1u);
+                atomicExch(&ctl->where, where);
+                return false;
+            }
+        }
+    }
+}
+
+}  // namespace dev
+}  // namespace vomt

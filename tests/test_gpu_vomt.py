@@ -52,9 +52,14 @@ def _compare(sol, ref, tol_field=1e-3, tol_obj=1e-4, k=None):
     return e_phi, e_u, e_p
 
 
-def test_parity_blob_32_k3_2000_iterations():
+ENGINES = ["stream", "resident"]
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_parity_blob_32_k3_2000_iterations(engine):
     r0, r1 = S.blob_pair(32, 3, seed=1001)
-    sol = _gpu(r0, r1, K3, 1.0, max_iters=2000, check_every=100)
+    sol = _gpu(r0, r1, K3, 1.0, max_iters=2000, check_every=100, engine=engine)
+    assert sol.result["engine"] == engine
     ref = _oracle(r0, r1, K3, 1.0, max_iters=2000, check_every=100, history=True)
     assert sol.result["iters"] == 2000 and sol.result["checks"] == 20
     errs = _compare(sol, ref)
@@ -68,22 +73,25 @@ def test_parity_blob_32_k3_2000_iterations():
     np.testing.assert_allclose(h[:, 2], ref["history"][:, 2], rtol=5e-2, atol=1e-5)
 
 
-@pytest.mark.parametrize("n", [2, 3, 5, 33, 47, 70])
-@pytest.mark.parametrize("k", [1, 2, 3, 5])
-def test_parity_sizes_and_channels(n, k):
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("n", [2, 3, 5, 33, 47, 70, 130])
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 8])
+def test_parity_sizes_and_channels(n, k, engine):
     rng = np.random.default_rng(100 * n + k)
     edges = S.random_connected_graph(rng, k, 0.6)
     r0, r1 = S.blob_pair(n, k, seed=10 * n + k) if n >= 5 else (rng.uniform(0.1, 1, (k, n, n)), rng.uniform(0.1, 1, (k, n, n)))
     r0 = r0 / r0.sum(); r1 = r1 / r1.sum()
-    sol = _gpu(r0, r1, edges, 0.7, max_iters=300, check_every=60)
+    sol = _gpu(r0, r1, edges, 0.7, max_iters=300, check_every=60, engine=engine)
+    assert sol.result["engine"] == engine
     ref = _oracle(r0, r1, edges, 0.7, max_iters=300, check_every=60)
     _compare(sol, ref)
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("u_norm,w_norm", [(0, 1), (1, 0), (1, 1), (2, 0), (2, 1)])
-def test_parity_norms(u_norm, w_norm):
+def test_parity_norms(u_norm, w_norm, engine):
     r0, r1 = S.blob_pair(40, 3, seed=77)
-    sol = _gpu(r0, r1, K3, 2.0, u_norm=u_norm, w_norm=w_norm, max_iters=500, check_every=100)
+    sol = _gpu(r0, r1, K3, 2.0, u_norm=u_norm, w_norm=w_norm, max_iters=500, check_every=100, engine=engine)
     ref = _oracle(r0, r1, K3, 2.0, u_norm=u_norm, w_norm=w_norm, max_iters=500, check_every=100)
     _compare(sol, ref)
 
@@ -97,12 +105,15 @@ def test_parity_edge_costs_and_tau():
     _compare(sol, ref)
 
 
-def test_one_step_from_gpu_state_at_256():
-    """At the full 256 x 256 colour-image size: one GPU iteration from a mid-run GPU state
-    against one FP64 oracle iteration from the same state."""
+@pytest.mark.parametrize("engine", ENGINES)
+def test_one_step_from_gpu_state_at_256(engine):
+    """At the full 256 x 256 colour-image size, in the launch configuration the benchmark
+    uses: one GPU iteration from a mid-run GPU state against one FP64 oracle iteration from
+    the same state."""
     r0, r1 = S.color_image_pair(256, 3, seed=1002)
-    mid = _gpu(r0, r1, K3, 1.0, max_iters=300, check_every=100)
-    nxt = _gpu(r0, r1, K3, 1.0, max_iters=1, check_every=1, init=(mid.u, mid.w, mid.phi))
+    mid = _gpu(r0, r1, K3, 1.0, max_iters=300, check_every=100, engine=engine)
+    nxt = _gpu(r0, r1, K3, 1.0, max_iters=1, check_every=1, init=(mid.u, mid.w, mid.phi), engine=engine)
+    assert mid.result["engine"] == engine and nxt.result["engine"] == engine
     u0 = mid.u.cpu().numpy().astype(np.float64)
     init = dict(ux=u0[0], uy=u0[1], w=mid.w.cpu().numpy().astype(np.float64),
                 phi=mid.phi.cpu().numpy().astype(np.float64))
@@ -116,19 +127,21 @@ def test_one_step_from_gpu_state_at_256():
     assert _rel(nxt.phi.cpu().numpy().astype(np.float64), ref["phi"]) < 1e-6
 
 
-def test_tolerance_stop_matches_oracle():
+@pytest.mark.parametrize("engine", ENGINES)
+def test_tolerance_stop_matches_oracle(engine):
     r0, r1 = S.blob_pair(32, 3, seed=1001)
     kw = dict(max_iters=20000, check_every=100, tol_gap=1e-3, tol_res=1e-3)
-    sol = _gpu(r0, r1, K3, 1.0, **kw)
+    sol = _gpu(r0, r1, K3, 1.0, engine=engine, **kw)
     ref = _oracle(r0, r1, K3, 1.0, **kw)
     assert sol.result["status"] == 0
     assert abs(sol.result["iters"] - ref["iters"]) <= 100
     assert sol.result["rel_gap"] <= 1e-3 and sol.result["rel_res"] <= 1e-3
 
 
-def test_invariants_on_gpu():
+@pytest.mark.parametrize("engine", ENGINES)
+def test_invariants_on_gpu(engine):
     r0, r1 = S.color_image_pair(128, 3, seed=3)
-    sol = _gpu(r0, r1, K3, 1.0, max_iters=1000, check_every=250)
+    sol = _gpu(r0, r1, K3, 1.0, max_iters=1000, check_every=250, engine=engine)
     u = sol.u.cpu().numpy()
     assert np.all(u[0, :, :, -1] == 0) and np.all(u[1, :, -1, :] == 0)   # ghost cells stay zero
     phi = sol.phi.cpu().numpy().astype(np.float64)
@@ -167,9 +180,28 @@ def test_input_errors():
     assert e.value.status == -1
 
 
-def test_zero_iterations_and_identical_densities():
-    r0, _ = S.blob_pair(20, 3, seed=4)
-    sol = _gpu(r0, r0, K3, 1.0, max_iters=0)
+@pytest.mark.parametrize("engine", ENGINES)
+def test_zero_iterations_and_identical_densities(engine):
+    r0, _ = S.blob_pair(40, 3, seed=4)
+    sol = _gpu(r0, r0, K3, 1.0, max_iters=0, engine=engine)
     assert sol.result["iters"] == 0 and sol.result["primal"] == 0.0
-    sol = _gpu(r0, r0, K3, 1.0, max_iters=50, check_every=10)
+    sol = _gpu(r0, r0, K3, 1.0, max_iters=50, check_every=10, engine=engine)
     assert sol.result["primal"] == 0.0 and float(sol.phi.abs().max()) == 0.0
+
+
+def test_auto_engine_choice():
+    r0, r1 = S.blob_pair(64, 3, seed=12)
+    sol = _gpu(r0, r1, K3, 1.0, max_iters=10)
+    assert sol.result["engine"] == "resident"
+    r0, r1 = S.blob_pair(600, 1, seed=13)
+    sol = _gpu(r0, r1, [], 1.0, max_iters=10)
+    assert sol.result["engine"] == "stream"
+
+
+def test_resident_matches_stream_closely_at_256():
+    r0, r1 = S.color_image_pair(256, 3, seed=1002)
+    a = _gpu(r0, r1, K3, 1.0, max_iters=3000, check_every=100, engine="stream")
+    b = _gpu(r0, r1, K3, 1.0, max_iters=3000, check_every=100, engine="resident")
+    assert _rel(b.phi.cpu().numpy().astype(np.float64), a.phi.cpu().numpy().astype(np.float64)) < 1e-5
+    assert _rel(b.u.cpu().numpy().astype(np.float64), a.u.cpu().numpy().astype(np.float64)) < 1e-4
+    assert abs(a.result["primal"] - b.result["primal"]) <= 1e-5 * a.result["primal"]
