@@ -100,6 +100,8 @@ typedef struct {
     int warm_start;      /* 1: u, w, phi hold the initial iterate; 0: start from zero (Section 7
                             leaves the initial guess open; zero is this library's default) */
     int engine;          /* VOMT_ENGINE_* */
+    int halo;            /* resident engine: iterations between halo exchanges, 1..16 (0 = the
+                            plan's estimate; a one-tile grid never exchanges) */
 } vomt_params;
 
 typedef struct {
@@ -127,7 +129,7 @@ const char *vomt_last_error(const vomt_ctx *ctx);
 
 /* Fill *p with the defaults: tau, mu, nu from the paper's rules, ||u||_{1,2},
  * ||w||_1, max_iters 2000, check_every 100, tol_gap = tol_res = 0, cold start,
- * engine AUTO. */
+ * engine AUTO, halo 0. */
 void vomt_default_params(vomt_params *p);
 
 /* Step sizes of Section 7.2 for an n x n grid and graph g (host only, no GPU):

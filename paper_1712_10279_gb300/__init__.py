@@ -30,7 +30,7 @@ class Solution:
     result: dict
 
 
-def _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, warm, engine):
+def _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, warm, engine, halo=0):
     p = _native.Params()
     _native.load().vomt_default_params(ctypes.byref(p))
     p.tau = 0.0 if tau is None else float(tau)
@@ -41,6 +41,7 @@ def _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_re
     p.tol_gap, p.tol_res = float(tol_gap), float(tol_res)
     p.warm_start = int(bool(warm))
     p.engine = ENGINES[engine] if isinstance(engine, str) else int(engine)
+    p.halo = int(halo)
     return p
 
 
@@ -55,7 +56,8 @@ def step_sizes(n: int, k: int, edges, tau=None, cost=None):
 
 def solve(rho0, rho1, edges, alpha: float = 1.0, *, tau=None, mu=None, nu=None, cost=None,
           u_norm: int = U_L12, w_norm: int = W_L1, max_iters: int = 2000, check_every: int = 100,
-          tol_gap: float = 0.0, tol_res: float = 0.0, init=None, engine="auto", stream=None) -> Solution:
+          tol_gap: float = 0.0, tol_res: float = 0.0, init=None, engine="auto", halo: int = 0,
+          stream=None) -> Solution:
     """Vector OMT (Section 7.2) on the GPU.
 
     rho0, rho1: CUDA float32 tensors [k, n, n] (cell masses, [c, j, i], x fastest).
@@ -80,7 +82,8 @@ def solve(rho0, rho1, edges, alpha: float = 1.0, *, tau=None, mu=None, nu=None, 
         u = torch.empty((2, k, n, n), device=dev, dtype=torch.float32)
         w = torch.empty((max(l, 0), n, n), device=dev, dtype=torch.float32)
         phi = torch.empty((k, n, n), device=dev, dtype=torch.float32)
-    p = _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, init is not None, engine)
+    p = _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, init is not None, engine,
+                halo)
     res = _native.Result()
     st = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
     ctx = _native.context(dev.index if dev.index is not None else torch.cuda.current_device())
@@ -93,7 +96,7 @@ def solve(rho0, rho1, edges, alpha: float = 1.0, *, tau=None, mu=None, nu=None, 
 
 def solve_host(rho0, rho1, edges, alpha: float = 1.0, *, tau=None, mu=None, nu=None, cost=None,
                u_norm: int = U_L12, w_norm: int = W_L1, max_iters: int = 2000, check_every: int = 100,
-               tol_gap: float = 0.0, tol_res: float = 0.0, engine="auto", device: int = 0,
+               tol_gap: float = 0.0, tol_res: float = 0.0, engine="auto", halo: int = 0, device: int = 0,
                out=None) -> Solution:
     """The same solve through vomt_solve_host: numpy float32 inputs and outputs in host
     memory; the library copies them to and from the GPU inside the call."""
@@ -106,7 +109,7 @@ def solve_host(rho0, rho1, edges, alpha: float = 1.0, *, tau=None, mu=None, nu=N
         out = (np.empty((2, k, n, n), np.float32), np.empty((max(l, 0), n, n), np.float32),
                np.empty((k, n, n), np.float32))
     u, w, phi = out
-    p = _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, False, engine)
+    p = _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, False, engine, halo)
     res = _native.Result()
     ctx = _native.context(device)
     rc = _native.load().vomt_solve_host(ctx, int(n), rho0.ctypes.data, rho1.ctypes.data, g.ref, float(alpha),

@@ -62,6 +62,7 @@ static int prepare(vomt_ctx *ctx, int n, const vomt_graph *graph, double alpha, 
     if (p.max_iters < 0 || p.check_every < 1) return fail(ctx, VOMT_ERR_BAD_ARG, "max_iters >= 0, check_every >= 1");
     if (p.u_norm < 0 || p.u_norm > 2 || p.w_norm < 0 || p.w_norm > 1) return fail(ctx, VOMT_ERR_BAD_ARG, "bad norm code");
     if (p.engine < 0 || p.engine > 2) return fail(ctx, VOMT_ERR_BAD_ARG, "bad engine code");
+    if (p.halo < 0 || p.halo > 16) return fail(ctx, VOMT_ERR_BAD_ARG, "halo must be in [0, 16]");
     int rc = graph_to_dev(graph, &out->g, &ctx->err);
     if (rc) return rc;
     const double tau = p.tau > 0.0 ? p.tau : default_tau(n);
@@ -151,7 +152,7 @@ static int solve_device(vomt_ctx *ctx, int n, const float *rho0, const float *rh
     int engine = VOMT_ENGINE_STREAM;
     if (P.p.engine != VOMT_ENGINE_STREAM) {
         ResidentPlan plan;
-        if (resident_plan(n, P.g.k, ctx->sm_count, &plan)) {
+        if (resident_plan(n, P.g.k, ctx->sm_count, P.p.halo, &plan)) {
             rc = resident_solve(ctx, P.g, P.s, P.cfg, P.p, plan, rho0, rho1, u, w, phi, st);
             if (rc == VOMT_OK) engine = VOMT_ENGINE_RESIDENT;
             else if (!(rc == VOMT_ERR_TOO_LARGE && P.p.engine == VOMT_ENGINE_AUTO)) return rc;
@@ -246,6 +247,7 @@ void vomt_default_params(vomt_params *p)
     p->tol_res = 0.0;
     p->warm_start = 0;
     p->engine = VOMT_ENGINE_AUTO;
+    p->halo = 0;
 }
 
 int vomt_step_sizes(int n, const vomt_graph *g, double tau, double *mu, double *nu, double *tau_used, double *lmax_graph)

@@ -103,9 +103,10 @@ int stream_solve(vomt_ctx *ctx, const GraphDev &g, const StepDev &s, const Solve
                  float *u, float *w, float *phi, cudaStream_t st);
 // resident engine (vector_resident.cu)
 struct ResidentPlan {
-    int Gx, Gy, TXm, TYm, threads;
+    int Gx, Gy, TXm, TYm, H, threads, P;
+    double est_ns;
 };
-bool resident_plan(int n, int k, int max_blocks, ResidentPlan *out);
+bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out);
 int resident_solve(vomt_ctx *ctx, const GraphDev &g, const StepDev &s, const SolveCfg &cfg, const vomt_params &p,
                    const ResidentPlan &plan, const float *rho0, const float *rho1, float *u, float *w, float *phi,
                    cudaStream_t st);

@@ -1,25 +1,36 @@
 // Resident engine for vector OMT: one cooperative launch runs the whole PDHG
-// solve (Section 7.2) with the state on chip.
+// solve (Section 7.2) with the iterate on chip, exchanging tile halos through
+// L2 once every H iterations (temporal blocking).
 //
 // The n x n grid is cut into Gx x Gy rectangular tiles, one per thread block
-// (one block per SM).  Each thread owns one grid point and keeps its iterate
-// (phi, u_x, u_y, w for all channels and edges) and b = rho1 - rho0 in
-// registers for the whole solve; HBM is touched only to load the densities and
-// the initial iterate and to store the final iterate.  Within a tile the
-// stencils of Appendix A go through shared memory.  Across tiles, the values a
-// neighbour needs (phi on the four tile edges, u on the right column and top
-// row) are written to L2 as 64-bit words tagged with the iteration number;
-// the reader polls the words themselves, so one L2 round trip replaces the
-// grid-wide barrier that Section 7.4 places around the phi update.  The two
-// neighbouring shrinks that the divergence at a tile's left / bottom edge needs
-// are recomputed from the received u and phi (the halo recompute of the
-// streaming engine).
+// (one block per SM).  Each block works on its tile extended by a ring of
+// width H on every side that has a neighbour tile.  After a halo exchange the
+// block holds the full iterate (phi, u_x, u_y, w) on the extended region, and
+// it can run H iterations without hearing from its neighbours: iteration s of
+// a block updates the tile grown by H - s cells, because one iteration of
+// Section 7.2 at a point reads the previous iterate only at that point and at
+// neighbours one cell away (phi at (i+1,j), (i,j+1), (i-1,j+1), (i+1,j-1); u at
+// (i-1,j), (i,j-1)).  After H iterations the tile itself is exact and the ring
+// is refreshed from the neighbours.  The ring work is redundant arithmetic
+// that buys H-fold fewer L2 round trips, which bound small grids.
 //
-// Convergence checks (every check_every iterations and at the end) reduce
-// the FP64 metric terms per block, publish one row per block, and every block
-// sums all rows in the same fixed order, so all blocks take the same stopping
-// decision without a further exchange.
+// Points are owned by threads for the whole solve (up to P points per thread);
+// each thread keeps its points' iterate and b = rho1 - rho0 in registers.  The
+// stencils of Appendix A within a block read neighbouring phi and ubar through
+// shared memory.  Between blocks, every iterate value a neighbour needs is
+// written to L2 as a 64-bit word with the value in its low half and the
+// exchange number in its high half; a reader polls the words themselves, so a
+// halo exchange costs one L2 round trip and no fences or flags (aligned 64-bit
+// accesses are single-copy atomic).
+//
+// Convergence checks (every check_every iterations and at the end; a block of
+// iterations is cut short so that it ends on a check) reduce FP64 metric terms
+// per thread block, publish one row per block as tagged word pairs, and every
+// block sums all rows in the same fixed order, so all blocks take the same
+// stopping decision.  Every wait is bounded in time; a wait that runs out
+// raises a global abort word that makes every block return.
 #include <math.h>
+#include <string.h>
 
 #include "internal.h"
 #include "pdhg_device.cuh"
@@ -29,12 +40,12 @@ namespace {
 
 using namespace dev;
 
-constexpr int EMAX = 64;              // longest tile side
-constexpr int RES_THREADS = 512;      // most points per tile (one thread each)
-constexpr int NE = 8;                 // exchange edges: phi L,R,D,U; u_x,u_y right; u_x,u_y top
+constexpr int RES_THREADS = 512;
+constexpr int TMAX = 64;              // longest tile side
+constexpr int HMAX = 16;              // widest halo ring
 
 struct ResGeom {
-    int n, Gx, Gy, TXm, TYm;
+    int n, Gx, Gy, TXm, TYm, H, EWm, EHm;
 };
 
 struct ResArgs {
@@ -42,17 +53,16 @@ struct ResArgs {
     GraphDev g;
     StepDev s;
     SolveCfg cfg;
+    float Dt[KMAX][LMAX];      // D diag(1/c): +1/c_e at the lower node of edge e, -1/c_e at the upper
     int un, wn, max_iters, check_every, warm;
     const float *rho0, *rho1;
     float *u, *w, *phi;
-    unsigned long long *xch;
-    double *rows;          // [2][G][NRED]
-    uint32_t *flags;       // [G]
+    unsigned long long *xch;   // [G][2][F][TYm][TXm] tagged iterate words
+    unsigned long long *rows;  // [2][G][NRED][2] tagged halves of the FP64 partial sums
     ResCtl *ctl;
     DevStatus *st;
     double *hist;
     int hist_cap;
-    int recv_max;          // receive-table capacity per block
 };
 
 template <int K>
@@ -60,431 +70,402 @@ struct LK {
     static constexpr int v = K * (K - 1) / 2 > 0 ? K * (K - 1) / 2 : 1;
 };
 
-// Shared-memory layout (bytes), computed identically on host and device.
 struct SmemLayout {
-    int red, S, dec, tsrc, tdst, sphi, sux, suy, sdx, sdy, hux, huy, hdx, hdy, phux, phuy, phdx, phdy, total;
+    int red, S, dec, rtab, sphi, sux, suy, sdx, sdy, total;
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
-__host__ __device__ inline SmemLayout smem_layout(int K, int TXm, int TYm, int recv_max)
+__host__ __device__ inline SmemLayout smem_layout(int K, int EWm, int EHm, int G)
 {
     SmemLayout L;
     int o = 0;
+    const int plane = K * EWm * EHm * 4;
     L.red = o; o += align16((RES_THREADS / 32) * NRED * 8);
     L.S = o; o += align16(NRED * 8);
     L.dec = o; o += 16;
-    L.tsrc = o; o += align16(recv_max * 4);
-    L.tdst = o; o += align16(recv_max * 4);
-    L.sphi = o; o += align16(K * (TYm + 2) * (TXm + 2) * 4);
-    L.sux = o; o += align16(K * TYm * (TXm + 1) * 4);
-    L.suy = o; o += align16(K * (TYm + 1) * TXm * 4);
-    L.sdx = o; o += align16(K * TYm * (TXm + 1) * 4);
-    L.sdy = o; o += align16(K * (TYm + 1) * TXm * 4);
-    L.hux = o; o += align16(K * TYm * 4);
-    L.huy = o; o += align16(K * TYm * 4);
-    L.hdx = o; o += align16(K * TXm * 4);
-    L.hdy = o; o += align16(K * TXm * 4);
-    L.phux = o; o += align16(K * TYm * 4);
-    L.phuy = o; o += align16(K * TYm * 4);
-    L.phdx = o; o += align16(K * TXm * 4);
-    L.phdy = o; o += align16(K * TXm * 4);
+    L.rtab = o; o += align16(G * NRED * 8);
+    L.sphi = o; o += align16(plane);
+    L.sux = o; o += align16(plane);
+    L.suy = o; o += align16(plane);
+    L.sdx = o; o += align16(plane);
+    L.sdy = o; o += align16(plane);
     L.total = o;
     return L;
 }
 
-// number of words a tile receives per iteration (upper bound for a TXm x TYm tile)
-__host__ __device__ inline int recv_words(int K, int TX, int TY)
+// Poll `cnt` tagged words (addresses from `addr(j)`), handing each value to
+// `sink(j, bits)` once its tag matches.  All pending words of a batch are
+// re-read every round.  Returns false on timeout or abort.
+template <int BATCH, typename Addr, typename Sink>
+__device__ __forceinline__ bool poll_words(int cnt, uint32_t tag, ResCtl *ctl, Addr addr, Sink sink)
 {
-    return 3 * K * TY + K * TY + 3 * K * TX + K * TX + 2 * K;
+    for (int base = 0; base < cnt; base += BATCH) {
+        uint32_t pending = 0;
+#pragma unroll
+        for (int r = 0; r < BATCH; ++r)
+            if (base + r < cnt) pending |= 1u << r;
+        uint64_t t0 = 0;
+        for (uint32_t round = 0; pending; ++round) {
+            unsigned long long v[BATCH];
+#pragma unroll
+            for (int r = 0; r < BATCH; ++r) v[r] = (pending >> r & 1u) ? ld_relaxed64(addr(base + r)) : 0ull;
+#pragma unroll
+            for (int r = 0; r < BATCH; ++r) {
+                if ((pending >> r & 1u) && (uint32_t)(v[r] >> 32) == tag) {
+                    sink(base + r, (uint32_t)v[r]);
+                    pending &= ~(1u << r);
+                }
+            }
+            if (pending && (round & 63u) == 63u) {
+                if (t0 == 0) t0 = global_ns();
+                if (ld_relaxed32(&ctl->abort)) return false;
+                if (global_ns() - t0 > kWaitBudgetNs) {
+                    atomicExch(&ctl->abort, 1u);
+                    atomicExch(&ctl->where, 1u);
+                    return false;
+                }
+            }
+        }
+    }
+    return true;
 }
 
-template <int K>
+template <int K, int P>
 __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
 {
     constexpr int LKv = LK<K>::v;
+    constexpr int FMAX = 3 * K + LKv;
     extern __shared__ __align__(16) unsigned char smem[];
     const ResGeom G = a.geo;
-    const int n = G.n;
+    const int n = G.n, H = G.H;
     const size_t nn = (size_t)n * n;
-    const SmemLayout SL = smem_layout(K, G.TXm, G.TYm, a.recv_max);
+    const int NT = (int)gridDim.x;
+    const SmemLayout SL = smem_layout(K, G.EWm, G.EHm, NT);
     double *red = (double *)(smem + SL.red);
     double *S = (double *)(smem + SL.S);
     int *dec = (int *)(smem + SL.dec);
-    uint32_t *tsrc = (uint32_t *)(smem + SL.tsrc);
-    uint32_t *tdst = (uint32_t *)(smem + SL.tdst);
+    double *rtab = (double *)(smem + SL.rtab);
     float *sphi = (float *)(smem + SL.sphi), *sux = (float *)(smem + SL.sux), *suy = (float *)(smem + SL.suy);
     float *sdx = (float *)(smem + SL.sdx), *sdy = (float *)(smem + SL.sdy);
-    float *hux = (float *)(smem + SL.hux), *huy = (float *)(smem + SL.huy);
-    float *hdx = (float *)(smem + SL.hdx), *hdy = (float *)(smem + SL.hdy);
-    float *phux = (float *)(smem + SL.phux), *phuy = (float *)(smem + SL.phuy);
-    float *phdx = (float *)(smem + SL.phdx), *phdy = (float *)(smem + SL.phdy);
-    const int PW = G.TXm + 2, PH = G.TYm + 2, XW = G.TXm + 1, YW = G.TXm;
-#define SPHI(c, r, q) sphi[((c) * PH + (r)) * PW + (q)]
-#define SUX(c, r, q) sux[((c) * G.TYm + (r)) * XW + (q)]
-#define SUY(c, r, q) suy[((c) * (G.TYm + 1) + (r)) * YW + (q)]
-#define SDX(c, r, q) sdx[((c) * G.TYm + (r)) * XW + (q)]
-#define SDY(c, r, q) sdy[((c) * (G.TYm + 1) + (r)) * YW + (q)]
 
     const int tile = blockIdx.x, gx = tile % G.Gx, gy = tile / G.Gx;
     const int x0 = gx * n / G.Gx, x1 = (gx + 1) * n / G.Gx;
     const int y0 = gy * n / G.Gy, y1 = (gy + 1) * n / G.Gy;
-    const int TXa = x1 - x0, TYa = y1 - y0;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int lx = tid % TXa, ly = tid / TXa;
-    const bool act = ly < TYa;
-    const int x = x0 + lx, y = y0 + ly;
     const bool hasL = gx > 0, hasR = gx < G.Gx - 1, hasD = gy > 0, hasU = gy < G.Gy - 1;
-    const bool hasUL = hasL && hasU, hasDR = hasR && hasD;
-    const int k = a.g.k, l = a.g.l;
+    const int X0 = x0 - (hasL ? H : 0), X1 = x1 + (hasR ? H : 0);
+    const int Y0 = y0 - (hasD ? H : 0), Y1 = y1 + (hasU ? H : 0);
+    const int EW = X1 - X0, EH = Y1 - Y0, NP = EW * EH;
+    const int PLANE = G.EWm * G.EHm;
+#define SA(arr, c, ey, ex) arr[(c) * PLANE + (ey) * G.EWm + (ex)]
+
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int k = a.g.k, l = a.g.l, F = 3 * K + l;
     const float mu = a.s.mu, nu = a.s.nu, tau = a.s.tau, ih = a.s.ih, alpha = a.s.alpha;
     const float muih = mu * ih;
     const int T = a.max_iters, CE = a.check_every;
-    const size_t SLOT = (size_t)NE * K * EMAX;       // words per (tile, parity)
-    auto word = [&](int t_, int par, int E, int c, int idx) -> unsigned long long * {
-        return a.xch + ((size_t)t_ * 2 + par) * SLOT + ((size_t)E * K + c) * EMAX + idx;
+    const size_t TSZ = (size_t)G.TXm * G.TYm;
+    auto xword = [&](int t_, int par, int f, int ly, int lx) -> unsigned long long * {
+        return a.xch + (((size_t)t_ * 2 + par) * F + f) * TSZ + (size_t)ly * G.TXm + lx;
     };
 
-    // ---- receive table: every halo word this tile reads, with its shared-memory destination
-    // destinations: index into the float pool starting at sphi (all halo arrays follow it)
-    int nrecv = 0;
-    if (tid == 0) {
-        auto add = [&](int t_, int E, int c, int idx, float *dst) {
-            tsrc[nrecv] = (uint32_t)(((size_t)t_ * 2) * SLOT + ((size_t)E * K + c) * EMAX + idx);
-            tdst[nrecv] = (uint32_t)(dst - sphi);
-            ++nrecv;
-        };
-        for (int c = 0; c < K; ++c) {
-            if (hasL)
-                for (int r = 0; r < TYa; ++r) {
-                    add(tile - 1, 1, c, r, &SPHI(c, r + 1, 0));
-                    add(tile - 1, 4, c, r, &hux[c * G.TYm + r]);
-                    add(tile - 1, 5, c, r, &huy[c * G.TYm + r]);
-                }
-            if (hasR)
-                for (int r = 0; r < TYa; ++r) add(tile + 1, 0, c, r, &SPHI(c, r + 1, TXa + 1));
-            if (hasD)
-                for (int q = 0; q < TXa; ++q) {
-                    add(tile - G.Gx, 3, c, q, &SPHI(c, 0, q + 1));
-                    add(tile - G.Gx, 6, c, q, &hdx[c * G.TXm + q]);
-                    add(tile - G.Gx, 7, c, q, &hdy[c * G.TXm + q]);
-                }
-            if (hasU)
-                for (int q = 0; q < TXa; ++q) add(tile + G.Gx, 2, c, q, &SPHI(c, TYa + 1, q + 1));
-            if (hasUL) add(tile + G.Gx - 1, 1, c, 0, &SPHI(c, TYa + 1, 0));
-            if (hasDR) add(tile - G.Gx + 1, 3, c, 0, &SPHI(c, 0, TXa + 1));
-        }
-        dec[0] = 0;          // abort seen by a thread of this block
-        dec[1] = nrecv;
-        dec[2] = 0;          // stop decision of the last check
-    }
-    __syncthreads();
-    nrecv = dec[1];
-
-    // ---- own state
-    float ph[K], ux[K], uy[K], bb[K], w[LKv];
-    const size_t p = (size_t)y * n + x;
+    // ---- owned points: q = tid + r * nthreads over the extended region, x fastest
+    int pex[P], pey[P];
+    bool pv[P], ptile[P], pband[P];
 #pragma unroll
-    for (int c = 0; c < K; ++c) {
-        ph[c] = ux[c] = uy[c] = bb[c] = 0.0f;
-        if (act) {
-            bb[c] = a.rho1[c * nn + p] - a.rho0[c * nn + p];
-            if (a.warm) {
-                ph[c] = a.phi[c * nn + p];
-                ux[c] = (x < n - 1) ? a.u[c * nn + p] : 0.0f;
-                uy[c] = (y < n - 1) ? a.u[(k + c) * nn + p] : 0.0f;
-            }
-        }
+    for (int r = 0; r < P; ++r) {
+        const int q = tid + r * nthr;
+        pv[r] = q < NP;
+        pex[r] = pv[r] ? q % EW : 0;
+        pey[r] = pv[r] ? q / EW : 0;
+        const int x = X0 + pex[r], y = Y0 + pey[r];
+        ptile[r] = pv[r] && x >= x0 && x < x1 && y >= y0 && y < y1;
+        pband[r] = ptile[r] && ((hasL && x - x0 < H) || (hasR && x1 - 1 - x < H) || (hasD && y - y0 < H) ||
+                                (hasU && y1 - 1 - y < H));
     }
-#pragma unroll
-    for (int e = 0; e < LKv; ++e) w[e] = (act && a.warm && e < l) ? a.w[e * nn + p] : 0.0f;
 
-    auto publish = [&](int t) {
-        if (!act) return;
-        const uint32_t tag = (uint32_t)t + 1u;
-        const int par = t & 1;
+    float ph[P][K], ux[P][K], uy[P][K], bb[P][K], w[P][LKv];
+#pragma unroll
+    for (int r = 0; r < P; ++r) {
+        const int x = X0 + pex[r], y = Y0 + pey[r];
+        const size_t p = (size_t)y * n + x;
 #pragma unroll
         for (int c = 0; c < K; ++c) {
-            if (lx == 0 && hasL) st_tagged(word(tile, par, 0, c, ly), ph[c], tag);
-            if (lx == TXa - 1 && hasR) {
-                st_tagged(word(tile, par, 1, c, ly), ph[c], tag);
-                st_tagged(word(tile, par, 4, c, ly), ux[c], tag);
-                st_tagged(word(tile, par, 5, c, ly), uy[c], tag);
-            }
-            if (ly == 0 && hasD) st_tagged(word(tile, par, 2, c, lx), ph[c], tag);
-            if (ly == TYa - 1 && hasU) {
-                st_tagged(word(tile, par, 3, c, lx), ph[c], tag);
-                st_tagged(word(tile, par, 6, c, lx), ux[c], tag);
-                st_tagged(word(tile, par, 7, c, lx), uy[c], tag);
+            ph[r][c] = ux[r][c] = uy[r][c] = bb[r][c] = 0.0f;
+            if (pv[r]) bb[r][c] = a.rho1[c * nn + p] - a.rho0[c * nn + p];
+            if (ptile[r] && a.warm) {
+                ph[r][c] = a.phi[c * nn + p];
+                ux[r][c] = (x < n - 1) ? a.u[c * nn + p] : 0.0f;
+                uy[r][c] = (y < n - 1) ? a.u[(k + c) * nn + p] : 0.0f;
             }
         }
-    };
-    // Load every halo word this thread owns, keep re-polling the ones whose tag is
-    // not there yet (all of them per round, so a round costs one L2 round trip);
-    // false if the wait ran out of time or another block aborted.
-    auto receive = [&](int t) -> bool {
-        const uint32_t tag = (uint32_t)t + 1u;
-        const size_t par_off = (size_t)(t & 1) * SLOT;
-        for (int base = 0; base < nrecv; base += 4 * nthr) {
-            unsigned pending = 0;
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
-                if (base + tid + r * nthr < nrecv) pending |= 1u << r;
-            uint64_t t0 = 0;
-            for (uint32_t round = 0; pending; ++round) {
-                unsigned long long v[4];
+        for (int e = 0; e < LKv; ++e) w[r][e] = (ptile[r] && a.warm && e < l) ? a.w[e * nn + p] : 0.0f;
+    }
+    if (tid == 0) { dec[0] = 0; dec[2] = 0; }
+
+    // ---- halo exchange number e: publish the tile's band, receive the ring.  Before
+    // a check, the ring points also record u_new - u_old in sdx / sdy.
+    auto exchange = [&](int e, bool rec_delta) -> bool {
+        const uint32_t tag = (uint32_t)e + 1u;
+        const int par = e & 1;
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
-                    v[r] = (pending >> r & 1u) ? ld_relaxed64(a.xch + tsrc[base + tid + r * nthr] + par_off) : 0ull;
+        for (int r = 0; r < P; ++r) {
+            if (!pband[r]) continue;
+            const int lx = X0 + pex[r] - x0, ly = Y0 + pey[r] - y0;
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    if ((pending >> r & 1u) && (uint32_t)(v[r] >> 32) == tag) {
-                        sphi[tdst[base + tid + r * nthr]] = __uint_as_float((uint32_t)v[r]);
-                        pending &= ~(1u << r);
-                    }
-                }
-                if (pending && (round & 63u) == 63u) {
-                    if (t0 == 0) t0 = global_ns();
-                    if (ld_relaxed32(&a.ctl->abort)) return false;
-                    if (global_ns() - t0 > kWaitBudgetNs) {
-                        atomicExch(&a.ctl->abort, 1u);
-                        atomicExch(&a.ctl->where, 1u);
-                        return false;
-                    }
-                }
+            for (int c = 0; c < K; ++c) {
+                st_tagged(xword(tile, par, c, ly, lx), ph[r][c], tag);
+                st_tagged(xword(tile, par, K + c, ly, lx), ux[r][c], tag);
+                st_tagged(xword(tile, par, 2 * K + c, ly, lx), uy[r][c], tag);
             }
+#pragma unroll
+            for (int e2 = 0; e2 < LKv; ++e2)
+                if (e2 < l) st_tagged(xword(tile, par, 3 * K + e2, ly, lx), w[r][e2], tag);
         }
-        return true;
+        bool ok = true;
+#pragma unroll
+        for (int r = 0; r < P; ++r) {
+            if (!pv[r] || ptile[r] || !ok) continue;
+            const int x = X0 + pex[r], y = Y0 + pey[r];
+            const int sgx = x < x0 ? gx - 1 : (x >= x1 ? gx + 1 : gx);
+            const int sgy = y < y0 ? gy - 1 : (y >= y1 ? gy + 1 : gy);
+            const int src = sgy * G.Gx + sgx;
+            const int slx = x - sgx * n / G.Gx, sly = y - sgy * n / G.Gy;
+            float vals[FMAX];
+#pragma unroll
+            for (int q = 0; q < FMAX; ++q) vals[q] = 0.0f;
+            ok = poll_words<16>(
+                F, tag, a.ctl, [&](int f) { return xword(src, par, f, sly, slx); },
+                [&](int f, uint32_t bits) {
+#pragma unroll
+                    for (int q = 0; q < FMAX; ++q)
+                        if (q == f) vals[q] = __uint_as_float(bits);
+                });
+            if (!ok) continue;
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                if (rec_delta) {
+                    SA(sdx, c, pey[r], pex[r]) = vals[K + c] - ux[r][c];
+                    SA(sdy, c, pey[r], pex[r]) = vals[2 * K + c] - uy[r][c];
+                }
+                ph[r][c] = vals[c];
+                ux[r][c] = vals[K + c];
+                uy[r][c] = vals[2 * K + c];
+                SA(sphi, c, pey[r], pex[r]) = ph[r][c];
+            }
+#pragma unroll
+            for (int e2 = 0; e2 < LKv; ++e2)
+                if (e2 < l) w[r][e2] = vals[3 * K + e2];
+        }
+        return ok;
     };
 
-    // ---- initial halo exchange (state 0, tag 1)
-    publish(0);
-    if (act)
+    // initial iterate: own phi to shared memory, then the first exchange
 #pragma unroll
-        for (int c = 0; c < K; ++c) SPHI(c, ly + 1, lx + 1) = ph[c];
-    if (!receive(0)) dec[0] = 1;
+    for (int r = 0; r < P; ++r)
+        if (ptile[r])
+#pragma unroll
+            for (int c = 0; c < K; ++c) SA(sphi, c, pey[r], pex[r]) = ph[r][c];
+    if (!exchange(0, false)) dec[0] = 1;
     __syncthreads();
     bool aborted = dec[0] != 0;
-
-    float oph[K], oux[K], ouy[K], ow[LKv];
-    int checks = 0;
+    int nexch = 1, checks = 0, t = 0;
     bool stop = false;
-    for (int t = (T == 0 ? 0 : 1); t <= T && !aborted && !stop; ++t) {
-        const bool is_check = (T == 0) || (t % CE == 0) || (t == T);
-        if (t > 0) {
-            // ---- u', w' and ubar (Section 7.2, first two lines of the loop)
-            float vx[K], vy[K], wx[LKv];
-            if (act) {
+
+    float dph[P][K], dgw[P][K], racc[P][K];
+#pragma unroll
+    for (int r = 0; r < P; ++r)
+#pragma unroll
+        for (int c = 0; c < K; ++c) { dph[r][c] = 0.0f; dgw[r][c] = 0.0f; racc[r][c] = 0.0f; }
+    while (!aborted && !stop) {
+        // a block of iterations runs to the next check (or the end) or H iterations
+        int hb = 0;
+        if (T > 0) {
+            const int next_check = ((t / CE) + 1) * CE;
+            hb = H;
+            if (t + hb > next_check) hb = next_check - t;
+            if (t + hb > T) hb = T - t;
+        }
+        const int t_end = t + hb;
+        const bool check_after = (T == 0) || (t_end % CE == 0) || (t_end == T);
+        double v[NRED];
+#pragma unroll
+        for (int q = 0; q < NRED; ++q) v[q] = 0.0;
+        for (int s = 1; s <= hb; ++s) {
+            const int rr = hb - s;                 // ring width of the region this step updates
+            const bool last = (s == hb) && check_after;
+            const int rl = hasL ? rr : 0, rrt = hasR ? rr : 0, rd = hasD ? rr : 0, ru = hasU ? rr : 0;
+            const int rlp = hasL ? rr + 1 : 0, rdp = hasD ? rr + 1 : 0;
+            // phase 1: u' on the region plus one column left and one row below (their
+            // ubar enters the divergence); w' and the commit on the region itself
+#pragma unroll
+            for (int r = 0; r < P; ++r) {
+                const int x = X0 + pex[r], y = Y0 + pey[r];
+                const bool inRp = pv[r] && x >= x0 - rlp && x < x1 + rrt && y >= y0 - rdp && y < y1 + ru;
+                if (!inRp) continue;
+                const bool inR = x >= x0 - rl && y >= y0 - rd;
+                const int ex = pex[r], ey = pey[r];
+                float vx[K], vy[K];
 #pragma unroll
                 for (int c = 0; c < K; ++c) {
-                    const float pc = SPHI(c, ly + 1, lx + 1);
-                    vx[c] = ux[c] + ((x < n - 1) ? muih * (SPHI(c, ly + 1, lx + 2) - pc) : 0.0f);
-                    vy[c] = uy[c] + ((y < n - 1) ? muih * (SPHI(c, ly + 2, lx + 1) - pc) : 0.0f);
+                    const float pc = ph[r][c];
+                    vx[c] = ux[r][c] + ((x < n - 1) ? muih * (SA(sphi, c, ey, ex + 1) - pc) : 0.0f);
+                    vy[c] = uy[r][c] + ((y < n - 1) ? muih * (SA(sphi, c, ey + 1, ex) - pc) : 0.0f);
                 }
                 shrink_u<K>(vx, vy, mu, a.un);
 #pragma unroll
+                for (int c = 0; c < K; ++c) {
+                    SA(sux, c, ey, ex) = 2.0f * vx[c] - ux[r][c];
+                    SA(suy, c, ey, ex) = 2.0f * vy[c] - uy[r][c];
+                }
+                if (!inR) continue;
+                float wx[LKv];
+#pragma unroll
                 for (int e = 0; e < LKv; ++e) {
-                    if (e < l) {
-                        const float ge = a.g.inv_c[e] * (pick<K>(ph, a.g.lo[e]) - pick<K>(ph, a.g.hi[e]));
-                        wx[e] = w[e] + nu * ge;
-                    } else {
-                        wx[e] = 0.0f;
-                    }
+                    float ge = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < K; ++c) ge += a.Dt[c][e] * ph[r][c];
+                    wx[e] = (e < l) ? w[r][e] + nu * ge : 0.0f;
                 }
                 shrink_w<LKv>(wx, l, alpha * nu, a.wn);
 #pragma unroll
                 for (int c = 0; c < K; ++c) {
-                    SUX(c, ly, lx + 1) = 2.0f * vx[c] - ux[c];
-                    SUY(c, ly + 1, lx) = 2.0f * vy[c] - uy[c];
+                    float gw = 0.0f, gd = 0.0f;
+#pragma unroll
+                    for (int e = 0; e < LKv; ++e) {
+                        gw -= a.Dt[c][e] * (2.0f * wx[e] - w[r][e]);
+                        gd -= a.Dt[c][e] * (wx[e] - w[r][e]);
+                    }
+                    racc[r][c] = gw + bb[r][c];
+                    if (last) dgw[r][c] = gd;
                 }
-                if (lx == 0 && hasL) {           // u' at (x0-1, y) from the received halo
-                    float hx[K], hy[K];
+                if (last) {
 #pragma unroll
                     for (int c = 0; c < K; ++c) {
-                        const float pl = SPHI(c, ly + 1, 0);
-                        hx[c] = hux[c * G.TYm + ly] + muih * (SPHI(c, ly + 1, 1) - pl);
-                        hy[c] = huy[c * G.TYm + ly] + ((y < n - 1) ? muih * (SPHI(c, ly + 2, 0) - pl) : 0.0f);
+                        const float dux = vx[c] - ux[r][c], duy = vy[c] - uy[r][c];
+                        SA(sdx, c, ey, ex) = dux;
+                        SA(sdy, c, ey, ex) = duy;
+                        v[RED_DU] += (double)dux * dux + (double)duy * duy;
                     }
-                    shrink_u<K>(hx, hy, mu, a.un);
 #pragma unroll
-                    for (int c = 0; c < K; ++c) SUX(c, ly, 0) = 2.0f * hx[c] - hux[c * G.TYm + ly];
-                }
-                if (ly == 0 && hasD) {           // u' at (x, y0-1)
-                    float hx[K], hy[K];
-#pragma unroll
-                    for (int c = 0; c < K; ++c) {
-                        const float pd = SPHI(c, 0, lx + 1);
-                        hx[c] = hdx[c * G.TXm + lx] + ((x < n - 1) ? muih * (SPHI(c, 0, lx + 2) - pd) : 0.0f);
-                        hy[c] = hdy[c * G.TXm + lx] + muih * (SPHI(c, 1, lx + 1) - pd);
+                    for (int e = 0; e < LKv; ++e) {
+                        const float dw = wx[e] - w[r][e];
+                        v[RED_DW] += (double)dw * dw;
                     }
-                    shrink_u<K>(hx, hy, mu, a.un);
-#pragma unroll
-                    for (int c = 0; c < K; ++c) SUY(c, 0, lx) = 2.0f * hy[c] - hdy[c * G.TXm + lx];
                 }
-                if (is_check) {
-                    if (lx == 0 && hasL)
 #pragma unroll
-                        for (int c = 0; c < K; ++c) {
-                            phux[c * G.TYm + ly] = hux[c * G.TYm + ly];
-                            phuy[c * G.TYm + ly] = huy[c * G.TYm + ly];
-                        }
-                    if (ly == 0 && hasD)
+                for (int c = 0; c < K; ++c) { ux[r][c] = vx[c]; uy[r][c] = vy[c]; }
 #pragma unroll
-                        for (int c = 0; c < K; ++c) {
-                            phdx[c * G.TXm + lx] = hdx[c * G.TXm + lx];
-                            phdy[c * G.TXm + lx] = hdy[c * G.TXm + lx];
-                        }
+                for (int e = 0; e < LKv; ++e) w[r][e] = wx[e];
+            }
+            __syncthreads();
+            // phase 2: phi' = phi + tau (div_x ubar + div_G wbar + rho1 - rho0) on the region
+#pragma unroll
+            for (int r = 0; r < P; ++r) {
+                const int x = X0 + pex[r], y = Y0 + pey[r];
+                const bool inR = pv[r] && x >= x0 - rl && x < x1 + rrt && y >= y0 - rd && y < y1 + ru;
+                if (!inR) continue;
+                const int ex = pex[r], ey = pey[r];
+#pragma unroll
+                for (int c = 0; c < K; ++c) {
+                    const float xl = (x > 0) ? SA(sux, c, ey, ex - 1) : 0.0f;
+                    const float yd = (y > 0) ? SA(suy, c, ey - 1, ex) : 0.0f;
+                    const float d = ih * ((SA(sux, c, ey, ex) - xl) + (SA(suy, c, ey, ex) - yd)) + racc[r][c];
+                    const float np = ph[r][c] + tau * d;
+                    if (last) dph[r][c] = np - ph[r][c];
+                    ph[r][c] = np;
+                    SA(sphi, c, ey, ex) = np;
                 }
             }
             __syncthreads();
-            // ---- phi' = phi + tau (div_x ubar + div_G wbar + rho1 - rho0)
-            if (act) {
-                float r[K];
-#pragma unroll
-                for (int c = 0; c < K; ++c) {
-                    const float xl = (x > 0) ? SUX(c, ly, lx) : 0.0f;
-                    const float yd = (y > 0) ? SUY(c, ly, lx) : 0.0f;
-                    r[c] = ih * ((SUX(c, ly, lx + 1) - xl) + (SUY(c, ly + 1, lx) - yd)) + bb[c];
-                }
-#pragma unroll
-                for (int e = 0; e < LKv; ++e) {
-                    if (e < l) {
-                        const float v = a.g.inv_c[e] * (2.0f * wx[e] - w[e]);
-                        const int lo = a.g.lo[e], hi = a.g.hi[e];
-#pragma unroll
-                        for (int c = 0; c < K; ++c) r[c] += (c == hi ? v : 0.0f) - (c == lo ? v : 0.0f);
-                    }
-                }
-                if (is_check) {
-#pragma unroll
-                    for (int c = 0; c < K; ++c) { oph[c] = ph[c]; oux[c] = ux[c]; ouy[c] = uy[c]; }
-#pragma unroll
-                    for (int e = 0; e < LKv; ++e) ow[e] = w[e];
-                }
-#pragma unroll
-                for (int c = 0; c < K; ++c) {
-                    ph[c] = ph[c] + tau * r[c];
-                    ux[c] = vx[c];
-                    uy[c] = vy[c];
-                }
-#pragma unroll
-                for (int e = 0; e < LKv; ++e) w[e] = wx[e];
-            }
-            // nothing reads the phi tile again before the barrier below, so the own
-            // value and the received halo can be written right away
-            publish(t);
-            if (act)
-#pragma unroll
-                for (int c = 0; c < K; ++c) SPHI(c, ly + 1, lx + 1) = ph[c];
-            if (!receive(t)) dec[0] = 1;
+        }
+        t = t_end;
+        // ---- refresh the ring (and, before a check, record u_new - u_old on it)
+        if (hb > 0) {
+            if (!exchange(nexch, check_after)) dec[0] = 1;
+            ++nexch;
             __syncthreads();
             if (dec[0]) { aborted = true; break; }
-        } else {
-            // zero iterations: metrics of the initial state, no change
-#pragma unroll
-            for (int c = 0; c < K; ++c) { oph[c] = ph[c]; oux[c] = ux[c]; ouy[c] = uy[c]; }
-#pragma unroll
-            for (int e = 0; e < LKv; ++e) ow[e] = w[e];
-            if (act && lx == 0 && hasL)
-                for (int c = 0; c < K; ++c) { phux[c * G.TYm + ly] = hux[c * G.TYm + ly]; phuy[c * G.TYm + ly] = huy[c * G.TYm + ly]; }
-            if (act && ly == 0 && hasD)
-                for (int c = 0; c < K; ++c) { phdx[c * G.TXm + lx] = hdx[c * G.TXm + lx]; phdy[c * G.TXm + lx] = hdy[c * G.TXm + lx]; }
         }
-        if (!is_check) continue;
+        if (!check_after) continue;
 
-        // ---- FP64 convergence check on the state after iteration t
-        if (act) {
+        // ---- FP64 convergence check of the iterate after iteration t
+        if (T == 0) {
+#pragma unroll
+            for (int r = 0; r < P; ++r)
+                if (pv[r])
+#pragma unroll
+                    for (int c = 0; c < K; ++c) { SA(sdx, c, pey[r], pex[r]) = 0.0f; SA(sdy, c, pey[r], pex[r]) = 0.0f; }
+        }
+#pragma unroll
+        for (int r = 0; r < P; ++r) {
+            if (!pv[r]) continue;
 #pragma unroll
             for (int c = 0; c < K; ++c) {
-                SUX(c, ly, lx + 1) = ux[c];
-                SUY(c, ly + 1, lx) = uy[c];
-                SDX(c, ly, lx + 1) = ux[c] - oux[c];
-                SDY(c, ly + 1, lx) = uy[c] - ouy[c];
+                SA(sux, c, pey[r], pex[r]) = ux[r][c];
+                SA(suy, c, pey[r], pex[r]) = uy[r][c];
             }
-            if (lx == 0 && hasL)
-#pragma unroll
-                for (int c = 0; c < K; ++c) {
-                    SUX(c, ly, 0) = hux[c * G.TYm + ly];
-                    SDX(c, ly, 0) = hux[c * G.TYm + ly] - phux[c * G.TYm + ly];
-                }
-            if (ly == 0 && hasD)
-#pragma unroll
-                for (int c = 0; c < K; ++c) {
-                    SUY(c, 0, lx) = hdy[c * G.TXm + lx];
-                    SDY(c, 0, lx) = hdy[c * G.TXm + lx] - phdy[c * G.TXm + lx];
-                }
         }
         __syncthreads();
-        double v[NRED];
+        // per-point terms in FP32 accumulated in FP64; the residual and the dual
+        // objective's products in FP64
 #pragma unroll
-        for (int q = 0; q < NRED; ++q) v[q] = 0.0;
-        if (act) {
+        for (int r = 0; r < P; ++r) {
+            if (!ptile[r]) continue;
+            const int x = X0 + pex[r], y = Y0 + pey[r], ex = pex[r], ey = pey[r];
             const double dih = (double)(n - 1);
-            double rdiv[K], ddiv[K], dph[K];
-            double nu_pt = 0.0, dn_u = 0.0;
+            float nu_pt = 0.0f, dn_u = 0.0f;
 #pragma unroll
             for (int c = 0; c < K; ++c) {
-                const double uxc = ux[c], uyc = uy[c], phc = ph[c], bc = bb[c];
-                dph[c] = phc - (double)oph[c];
-                const double xl = (x > 0) ? (double)SUX(c, ly, lx) : 0.0;
-                const double yd = (y > 0) ? (double)SUY(c, ly, lx) : 0.0;
-                rdiv[c] = dih * ((uxc - xl) + (uyc - yd));
-                const double dux = uxc - (double)oux[c], duy = uyc - (double)ouy[c];
-                const double dxl = (x > 0) ? (double)SDX(c, ly, lx) : 0.0;
-                const double dyd = (y > 0) ? (double)SDY(c, ly, lx) : 0.0;
-                ddiv[c] = dih * ((dux - dxl) + (duy - dyd));
-                v[RED_DU] += dux * dux + duy * duy;
-                v[RED_DP] += dph[c] * dph[c];
-                v[RED_D] += phc * bc;
-                v[RED_BB] += bc * bc;
-                const double gxx = (x < n - 1) ? dih * ((double)SPHI(c, ly + 1, lx + 2) - phc) : 0.0;
-                const double gyy = (y < n - 1) ? dih * ((double)SPHI(c, ly + 2, lx + 1) - phc) : 0.0;
+                const float uxc = ux[r][c], uyc = uy[r][c], phc = ph[r][c], bc = bb[r][c];
+                const float xl = (x > 0) ? SA(sux, c, ey, ex - 1) : 0.0f;
+                const float yd = (y > 0) ? SA(suy, c, ey - 1, ex) : 0.0f;
+                double rdiv = dih * (((double)uxc - (double)xl) + ((double)uyc - (double)yd));
+                const float dxl = (x > 0) ? SA(sdx, c, ey, ex - 1) : 0.0f;
+                const float dyd = (y > 0) ? SA(sdy, c, ey - 1, ex) : 0.0f;
+                const float ddiv = ih * ((SA(sdx, c, ey, ex) - dxl) + (SA(sdy, c, ey, ex) - dyd)) + dgw[r][c];
+#pragma unroll
+                for (int e = 0; e < LKv; ++e) rdiv -= (double)a.Dt[c][e] * (double)w[r][e];
+                const double rc = rdiv + (double)bc;
+                v[RED_RR] += rc * rc;
+                v[RED_BB] += (double)(bc * bc);
+                v[RED_D] += (double)phc * (double)bc;
+                v[RED_DP] += (double)(dph[r][c] * dph[r][c]);
+                v[RED_X] += (double)(dph[r][c] * ddiv);
+                const float gxx = (x < n - 1) ? ih * (SA(sphi, c, ey, ex + 1) - phc) : 0.0f;
+                const float gyy = (y < n - 1) ? ih * (SA(sphi, c, ey + 1, ex) - phc) : 0.0f;
                 if (a.un == VOMT_U_L12) {
-                    nu_pt += sqrt(uxc * uxc + uyc * uyc);
-                    dn_u = fmax(dn_u, sqrt(gxx * gxx + gyy * gyy));
+                    nu_pt += sqrtf(uxc * uxc + uyc * uyc);
+                    dn_u = fmaxf(dn_u, sqrtf(gxx * gxx + gyy * gyy));
                 } else if (a.un == VOMT_U_L2) {
                     nu_pt += uxc * uxc + uyc * uyc;
                     dn_u += gxx * gxx + gyy * gyy;
                 } else {
-                    nu_pt += fabs(uxc) + fabs(uyc);
-                    dn_u = fmax(dn_u, fmax(fabs(gxx), fabs(gyy)));
+                    nu_pt += fabsf(uxc) + fabsf(uyc);
+                    dn_u = fmaxf(dn_u, fmaxf(fabsf(gxx), fabsf(gyy)));
                 }
             }
-            if (a.un == VOMT_U_L2) { nu_pt = sqrt(nu_pt); dn_u = sqrt(dn_u); }
-            double nw_pt = 0.0, dn_w = 0.0;
+            if (a.un == VOMT_U_L2) { nu_pt = sqrtf(nu_pt); dn_u = sqrtf(dn_u); }
+            float nw_pt = 0.0f, dn_w = 0.0f;
 #pragma unroll
             for (int e = 0; e < LKv; ++e) {
                 if (e < l) {
-                    const int lo = a.g.lo[e], hi = a.g.hi[e];
-                    const double ic = (double)a.g.inv_c[e];
-                    const double we = w[e], dwe = we - (double)ow[e];
-                    v[RED_DW] += dwe * dwe;
-                    double ge = 0.0;
+                    float ge = 0.0f;
 #pragma unroll
-                    for (int c = 0; c < K; ++c) {
-                        const double sgn = (c == lo) ? 1.0 : (c == hi ? -1.0 : 0.0);
-                        ge += sgn * (double)ph[c];
-                        rdiv[c] -= sgn * ic * we;
-                        ddiv[c] -= sgn * ic * dwe;
-                    }
-                    ge *= ic;
-                    if (a.wn == VOMT_W_L1) { nw_pt += fabs(we); dn_w = fmax(dn_w, fabs(ge)); }
+                    for (int c = 0; c < K; ++c) ge += a.Dt[c][e] * ph[r][c];
+                    const float we = w[r][e];
+                    if (a.wn == VOMT_W_L1) { nw_pt += fabsf(we); dn_w = fmaxf(dn_w, fabsf(ge)); }
                     else { nw_pt += we * we; dn_w += ge * ge; }
                 }
             }
-            if (a.wn == VOMT_W_L2) { nw_pt = sqrt(nw_pt); dn_w = sqrt(dn_w); }
-            v[RED_P] = nu_pt + (double)alpha * nw_pt;
-#pragma unroll
-            for (int c = 0; c < K; ++c) {
-                const double rc = rdiv[c] + (double)bb[c];
-                v[RED_RR] += rc * rc;
-                v[RED_X] += dph[c] * ddiv[c];
-            }
-            double di = fmax(dn_u - 1.0, 0.0);
-            if (l > 0) di = fmax(di, dn_w - (double)alpha);
-            v[RED_MAX] = di;
+            if (a.wn == VOMT_W_L2) { nw_pt = sqrtf(nw_pt); dn_w = sqrtf(dn_w); }
+            v[RED_P] += (double)nu_pt + (double)alpha * (double)nw_pt;
+            float di = fmaxf(dn_u - 1.0f, 0.0f);
+            if (l > 0) di = fmaxf(di, dn_w - alpha);
+            v[RED_MAX] = fmax(v[RED_MAX], (double)di);
         }
-        // block reduction in a fixed order
+        // block reduction (fixed order)
         const int lane = tid & 31, wid = tid >> 5, nw = (nthr + 31) >> 5;
 #pragma unroll
         for (int q = 0; q < NRED; ++q) {
@@ -499,30 +480,37 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
             for (int q = 0; q < NRED; ++q) red[wid * NRED + q] = v[q];
         __syncthreads();
         const int cpar = checks & 1;
-        const uint32_t cflag = (uint32_t)checks + 1u;
+        const uint32_t ctag = (uint32_t)checks + 1u;
+        const int words = NT * NRED * 2;
         if (tid < NRED) {
             double acc = red[tid];
             for (int q = 1; q < nw; ++q) acc = (tid == RED_MAX) ? fmax(acc, red[q * NRED + tid]) : acc + red[q * NRED + tid];
-            a.rows[((size_t)cpar * gridDim.x + tile) * NRED + tid] = acc;
-            __threadfence();
+            unsigned long long *dst = a.rows + (size_t)cpar * words + ((size_t)tile * NRED + tid) * 2;
+            st_tagged(dst, __int_as_float(__double2hiint(acc)), ctag);
+            st_tagged(dst + 1, __int_as_float(__double2loint(acc)), ctag);
         }
-        __syncthreads();
-        if (tid == 0) st_release32(&a.flags[tile], cflag);
-        // every block sums every row in block order (identical in all blocks)
-        if (tid < NRED) {
-            bool ok = true;
-            for (int b = 0; b < (int)gridDim.x && ok; ++b) ok = wait_flag(&a.flags[b], cflag, a.ctl, 2);
-            double acc = 0.0;
-            if (ok)
-                for (int b = 0; b < (int)gridDim.x; ++b) {
-                    const double x_ = ld_relaxed_f64(&a.rows[((size_t)cpar * gridDim.x + b) * NRED + tid]);
-                    acc = (tid == RED_MAX) ? fmax(acc, x_) : acc + x_;
-                }
-            S[tid] = acc;
+        // every block gathers every row (one L2 round trip), then sums them in block order
+        {
+            const int mine = tid < words ? (words - tid + nthr - 1) / nthr : 0;
+            const bool ok = poll_words<8>(
+                mine, ctag, a.ctl, [&](int j) { return a.rows + (size_t)cpar * words + (size_t)tid + (size_t)j * nthr; },
+                [&](int j, uint32_t bits) {
+                    const int widx = tid + j * nthr;
+                    ((uint32_t *)rtab)[(widx >> 1) * 2 + ((widx & 1) ? 0 : 1)] = bits;
+                });
             if (!ok) dec[0] = 1;
         }
         __syncthreads();
         if (dec[0]) { aborted = true; break; }
+        if (tid < NRED) {
+            double acc = 0.0;
+            for (int b = 0; b < NT; ++b) {
+                const double x_ = rtab[b * NRED + tid];
+                acc = (tid == RED_MAX) ? fmax(acc, x_) : acc + x_;
+            }
+            S[tid] = acc;
+        }
+        __syncthreads();
         if (tid == 0) {
             double m[NMET];
             m[0] = S[RED_P];
@@ -546,12 +534,11 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
                 if (!finite) a.st->error = VOMT_ERR_NONFINITE;
                 if (conv || !finite) a.st->stop = 1;
             }
-            dec[2] = (conv || !finite) ? 1 : 0;
+            dec[2] = (conv || !finite || t >= T) ? 1 : 0;
         }
         __syncthreads();
         ++checks;
         stop = dec[2] != 0;
-        if (T == 0) break;
     }
     if (aborted) {
         if (tid == 0 && tile == 0) {
@@ -560,71 +547,105 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
         }
         return;
     }
-    // ---- final iterate to the caller's arrays
-    if (act) {
+    // ---- final iterate of the tile to the caller's arrays
+#pragma unroll
+    for (int r = 0; r < P; ++r) {
+        if (!ptile[r]) continue;
+        const size_t p = (size_t)(Y0 + pey[r]) * n + (X0 + pex[r]);
 #pragma unroll
         for (int c = 0; c < K; ++c) {
-            a.phi[c * nn + p] = ph[c];
-            a.u[c * nn + p] = ux[c];
-            a.u[(k + c) * nn + p] = uy[c];
+            a.phi[c * nn + p] = ph[r][c];
+            a.u[c * nn + p] = ux[r][c];
+            a.u[(k + c) * nn + p] = uy[r][c];
         }
 #pragma unroll
         for (int e = 0; e < LKv; ++e)
-            if (e < l) a.w[e * nn + p] = w[e];
+            if (e < l) a.w[e * nn + p] = w[r][e];
     }
-#undef SPHI
-#undef SUX
-#undef SUY
-#undef SDX
-#undef SDY
+#undef SA
 }
 
 using ResKernel = void (*)(ResArgs);
 
-ResKernel pick_kernel(int k)
+template <int P>
+ResKernel pick_k(int k)
 {
     switch (k) {
-        case 1: return k_resident<1>;
-        case 2: return k_resident<2>;
-        case 3: return k_resident<3>;
-        case 4: return k_resident<4>;
-        case 5: return k_resident<5>;
-        case 6: return k_resident<6>;
-        case 7: return k_resident<7>;
-        default: return k_resident<8>;
+        case 1: return k_resident<1, P>;
+        case 2: return k_resident<2, P>;
+        case 3: return k_resident<3, P>;
+        case 4: return k_resident<4, P>;
+        case 5: return k_resident<5, P>;
+        case 6: return k_resident<6, P>;
+        case 7: return k_resident<7, P>;
+        default: return k_resident<8, P>;
     }
+}
+
+ResKernel pick_kernel(int k, int P) { return P <= 2 ? pick_k<2>(k) : pick_k<4>(k); }
+
+// Estimated nanoseconds per iteration (see resident_plan).  Constants fitted to
+// GB300 measurements of this kernel at k = 3: 3.5 ns per point of the region a
+// step updates (arithmetic, shared-memory traffic and the two barriers of a
+// step at 16 warps per SM), 3.1 us per halo exchange (one L2 round trip plus
+// the tagged stores and polls), and 30% more per point when a thread owns
+// four points (register spills).
+double plan_cost(int TX, int TY, int H, int G)
+{
+    const double per_pt = 3.5;
+    if (G == 1) return per_pt * TX * TY * (TX * TY > 2 * RES_THREADS ? 1.3 : 1.0);
+    double pts = 0.0;
+    for (int s = 1; s <= H; ++s) pts += (double)(TX + 2 * (H - s) + 1) * (TY + 2 * (H - s) + 1);
+    const int ext = (TX + 2 * H) * (TY + 2 * H);
+    return per_pt * (ext > 2 * RES_THREADS ? 1.3 : 1.0) * pts / H + 3100.0 / H;
 }
 
 }  // namespace
 
-// Tile plan.  Cost of a plan in point-equivalents: the points of the largest
-// tile (one thread each, so proportional to the time of one iteration's
-// arithmetic) plus, when there is more than one tile, the L2 exchange between
-// tiles (about 1000 points' worth of time per iteration).  Every grid of at
-// most `max_blocks` tiles with sides <= 64 and <= 512 points per tile is tried.
-bool resident_plan(int n, int k, int max_blocks, ResidentPlan *out)
+// Tile plan.  Tiles of at most 64 x 64 points, at most `max_blocks` of them; the
+// ring width H is at most the narrowest tile side; the extended tile
+// (TX + 2H) x (TY + 2H) must fit 4 points per thread of a 512-thread block.
+// Among those, the plan with the smallest estimated time per iteration
+// (plan_cost) wins.  `force_H` > 0 pins the ring width.
+bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out)
 {
     (void)k;
-    long best = -1, best_per = 0;
+    double best = -1.0;
     for (int Gx = 1; Gx <= n && Gx <= max_blocks; ++Gx) {
-        const int TX = (n + Gx - 1) / Gx;
-        if (TX > EMAX) continue;
+        const int TX = (n + Gx - 1) / Gx, TXmin = n / Gx;
+        if (TX > TMAX) continue;
         for (int Gy = 1; Gy <= n && Gx * Gy <= max_blocks; ++Gy) {
-            const int TY = (n + Gy - 1) / Gy;
-            if (TY > EMAX || TX * TY > RES_THREADS) continue;
-            const long cost = (long)TX * TY + (Gx * Gy > 1 ? 1000 : 0), per = TX + TY;
-            if (best < 0 || cost < best || (cost == best && per < best_per)) {
-                best = cost;
-                best_per = per;
-                out->Gx = Gx;
-                out->Gy = Gy;
-                out->TXm = TX;
-                out->TYm = TY;
+            const int TY = (n + Gy - 1) / Gy, TYmin = n / Gy;
+            if (TY > TMAX) continue;
+            const int G = Gx * Gy;
+            if (G == 1) {
+                if (TX * TY > 4 * RES_THREADS) continue;
+                const double cost = plan_cost(TX, TY, 0, 1);
+                if (best < 0 || cost < best) {
+                    best = cost;
+                    *out = ResidentPlan{Gx, Gy, TX, TY, 0, 0, 0, cost};
+                }
+                continue;
+            }
+            for (int H = 1; H <= HMAX; ++H) {
+                if (force_H > 0 && H != force_H) continue;
+                if (H > TXmin || H > TYmin) break;
+                const int EW = TX + 2 * H, EH = TY + 2 * H;
+                if (EW * EH > 4 * RES_THREADS) break;
+                const double cost = plan_cost(TX, TY, H, G);
+                if (best < 0 || cost < best) {
+                    best = cost;
+                    *out = ResidentPlan{Gx, Gy, TX, TY, H, 0, 0, cost};
+                }
             }
         }
     }
     if (best < 0) return false;
-    out->threads = ((out->TXm * out->TYm + 31) / 32) * 32;
+    const int EW = out->TXm + 2 * out->H, EH = out->TYm + 2 * out->H;
+    out->threads = RES_THREADS;
+    if (EW * EH <= RES_THREADS) out->threads = ((EW * EH + 31) / 32) * 32;
+    out->P = (EW * EH + out->threads - 1) / out->threads;
+    out->P = out->P <= 2 ? 2 : 4;
     return true;
 }
 
@@ -632,23 +653,32 @@ int resident_solve(vomt_ctx *ctx, const GraphDev &g, const StepDev &s, const Sol
                    const ResidentPlan &plan, const float *rho0, const float *rho1, float *u, float *w, float *phi,
                    cudaStream_t st)
 {
-    const int K = g.k;
+    const int K = g.k, F = 3 * K + g.l;
     const int G = plan.Gx * plan.Gy;
-    const int recv_max = recv_words(K, plan.TXm, plan.TYm);
-    const SmemLayout SL = smem_layout(K, plan.TXm, plan.TYm, recv_max);
-    // scratch: exchange words, check rows, flags, control words
-    const size_t xch_bytes = (size_t)G * 2 * NE * K * EMAX * sizeof(unsigned long long);
-    const size_t rows_bytes = (size_t)2 * G * NRED * sizeof(double);
-    const size_t flag_bytes = ((size_t)G * sizeof(uint32_t) + 255) & ~(size_t)255;
-    const size_t need = xch_bytes + rows_bytes + flag_bytes + 256;
+    const int EWm = plan.TXm + 2 * plan.H, EHm = plan.TYm + 2 * plan.H;
+    const SmemLayout SL = smem_layout(K, EWm, EHm, G);
+    if (SL.total > 227 * 1024) {
+        ctx->err = "resident plan needs too much shared memory";
+        return VOMT_ERR_TOO_LARGE;
+    }
+    const size_t xch_bytes = (size_t)G * 2 * F * plan.TXm * plan.TYm * sizeof(unsigned long long);
+    const size_t rows_bytes = (size_t)2 * G * NRED * 2 * sizeof(unsigned long long);
+    const size_t need = xch_bytes + rows_bytes + 256;
     int rc = ensure_buffer(ctx, &ctx->rscratch, &ctx->rscratch_bytes, need, "resident scratch");
     if (rc) return rc;
     unsigned char *base = (unsigned char *)ctx->rscratch;
     ResArgs a;
-    a.geo = ResGeom{s.n, plan.Gx, plan.Gy, plan.TXm, plan.TYm};
+    memset(&a, 0, sizeof a);
+    // a single tile never exchanges, so its blocks of iterations may be as long as a check interval
+    const int H = G == 1 ? (1 << 30) : plan.H;
+    a.geo = ResGeom{s.n, plan.Gx, plan.Gy, plan.TXm, plan.TYm, H, EWm, EHm};
     a.g = g;
     a.s = s;
     a.cfg = cfg;
+    for (int e = 0; e < g.l; ++e) {
+        a.Dt[g.lo[e]][e] = g.inv_c[e];
+        a.Dt[g.hi[e]][e] = -g.inv_c[e];
+    }
     a.un = p.u_norm;
     a.wn = p.w_norm;
     a.max_iters = p.max_iters;
@@ -660,11 +690,9 @@ int resident_solve(vomt_ctx *ctx, const GraphDev &g, const StepDev &s, const Sol
     a.w = w;
     a.phi = phi;
     a.xch = (unsigned long long *)base;
-    a.rows = (double *)(base + xch_bytes);
-    a.flags = (uint32_t *)(base + xch_bytes + rows_bytes);
-    a.ctl = (ResCtl *)(base + xch_bytes + rows_bytes + flag_bytes);
+    a.rows = (unsigned long long *)(base + xch_bytes);
+    a.ctl = (ResCtl *)(base + xch_bytes + rows_bytes);
     a.st = ctx->dstatus;
-    a.recv_max = recv_max;
     const int max_checks = p.max_iters / p.check_every + 2;
     if (ctx->hist_cap < max_checks) {
         if (ctx->dhist) cudaFree(ctx->dhist);
@@ -677,7 +705,7 @@ int resident_solve(vomt_ctx *ctx, const GraphDev &g, const StepDev &s, const Sol
     a.hist = ctx->dhist;
     a.hist_cap = ctx->hist_cap;
 
-    ResKernel kern = pick_kernel(K);
+    ResKernel kern = pick_kernel(K, plan.P);
     cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SL.total);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "resident smem attribute");
     int per_sm = 0;

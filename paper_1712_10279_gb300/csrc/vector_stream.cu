@@ -232,77 +232,78 @@ __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const 
 #pragma unroll
     for (int q = 0; q < NRED; ++q) v[q] = 0.0;
     if (i < n && j < n) {
+        // Per-point terms in FP32 (each rounding is relative 2^-24) accumulated in
+        // FP64; the constraint residual, which cancels several digits, and the dual
+        // objective's products are formed in FP64.
         const size_t nn = (size_t)n * n, p = (size_t)j * n + i;
         const bool hR = i < n - 1, hU = j < n - 1, hL = i > 0, hD = j > 0;
-        const double ih = (double)(n - 1), alpha = s.alpha;
-        double ux[K], uy[K], ph[K], bb[K], dph[K], rdiv[K], ddiv[K];
-        double nu_pt = 0.0, dn_u = 0.0;
+        const float ih = s.ih, alpha = s.alpha;
+        const double dih = (double)(n - 1);
+        float ph[K], dph[K], ddiv[K];
+        double rdiv[K];
+        float nu_pt = 0.0f, dn_u = 0.0f;
 #pragma unroll
         for (int c = 0; c < K; ++c) {
             const size_t q = c * nn + p;
-            ux[c] = cur.ux[q];
-            uy[c] = cur.uy[q];
+            const float uxc = cur.ux[q], uyc = cur.uy[q], bc = b[q];
             ph[c] = cur.phi[q];
-            bb[c] = b[q];
-            dph[c] = ph[c] - (double)prv.phi[q];
-            double xl = hL ? (double)cur.ux[q - 1] : 0.0, yd = hD ? (double)cur.uy[q - n] : 0.0;
-            rdiv[c] = ih * ((ux[c] - xl) + (uy[c] - yd));
-            double dux = ux[c] - (double)prv.ux[q], duy = uy[c] - (double)prv.uy[q];
-            double dxl = hL ? (double)cur.ux[q - 1] - (double)prv.ux[q - 1] : 0.0;
-            double dyd = hD ? (double)cur.uy[q - n] - (double)prv.uy[q - n] : 0.0;
+            dph[c] = ph[c] - prv.phi[q];
+            const float xl = hL ? cur.ux[q - 1] : 0.0f, yd = hD ? cur.uy[q - n] : 0.0f;
+            rdiv[c] = dih * (((double)uxc - (double)xl) + ((double)uyc - (double)yd)) + (double)bc;
+            const float dux = uxc - prv.ux[q], duy = uyc - prv.uy[q];
+            const float dxl = hL ? cur.ux[q - 1] - prv.ux[q - 1] : 0.0f;
+            const float dyd = hD ? cur.uy[q - n] - prv.uy[q - n] : 0.0f;
             ddiv[c] = ih * ((dux - dxl) + (duy - dyd));
-            v[RED_DU] += dux * dux + duy * duy;
-            v[RED_DP] += dph[c] * dph[c];
-            v[RED_D] += ph[c] * bb[c];
-            v[RED_BB] += bb[c] * bb[c];
-            // norms of u and of grad phi
-            double gx = hR ? ih * ((double)cur.phi[q + 1] - ph[c]) : 0.0;
-            double gy = hU ? ih * ((double)cur.phi[q + n] - ph[c]) : 0.0;
+            v[RED_DU] += (double)(dux * dux + duy * duy);
+            v[RED_DP] += (double)(dph[c] * dph[c]);
+            v[RED_D] += (double)ph[c] * (double)bc;
+            v[RED_BB] += (double)(bc * bc);
+            const float gx = hR ? ih * (cur.phi[q + 1] - ph[c]) : 0.0f;
+            const float gy = hU ? ih * (cur.phi[q + n] - ph[c]) : 0.0f;
             if (UN == VOMT_U_L12) {
-                nu_pt += sqrt(ux[c] * ux[c] + uy[c] * uy[c]);
-                dn_u = fmax(dn_u, sqrt(gx * gx + gy * gy));
+                nu_pt += sqrtf(uxc * uxc + uyc * uyc);
+                dn_u = fmaxf(dn_u, sqrtf(gx * gx + gy * gy));
             } else if (UN == VOMT_U_L2) {
-                nu_pt += ux[c] * ux[c] + uy[c] * uy[c];
+                nu_pt += uxc * uxc + uyc * uyc;
                 dn_u += gx * gx + gy * gy;
             } else {
-                nu_pt += fabs(ux[c]) + fabs(uy[c]);
-                dn_u = fmax(dn_u, fmax(fabs(gx), fabs(gy)));
+                nu_pt += fabsf(uxc) + fabsf(uyc);
+                dn_u = fmaxf(dn_u, fmaxf(fabsf(gx), fabsf(gy)));
             }
         }
-        if (UN == VOMT_U_L2) { nu_pt = sqrt(nu_pt); dn_u = sqrt(dn_u); }
-        double nw_pt = 0.0, dn_w = 0.0;
+        if (UN == VOMT_U_L2) { nu_pt = sqrtf(nu_pt); dn_u = sqrtf(dn_u); }
+        float nw_pt = 0.0f, dn_w = 0.0f;
 #pragma unroll
         for (int e = 0; e < LK; ++e) {
             if (e < g.l) {
                 const size_t q = e * nn + p;
                 const int lo = g.lo[e], hi = g.hi[e];
-                const double ic = (double)g.inv_c[e];
-                double we = cur.w[q], dwe = we - (double)prv.w[q];
-                v[RED_DW] += dwe * dwe;
-                double ge = 0.0;
+                const float ic = g.inv_c[e];
+                const float we = cur.w[q], dwe = we - prv.w[q];
+                v[RED_DW] += (double)(dwe * dwe);
+                float ge = 0.0f;
 #pragma unroll
                 for (int c = 0; c < K; ++c) {
-                    double sgn = (c == lo) ? 1.0 : (c == hi ? -1.0 : 0.0);
+                    const float sgn = (c == lo) ? 1.0f : (c == hi ? -1.0f : 0.0f);
                     ge += sgn * ph[c];
-                    rdiv[c] -= sgn * ic * we;      // div_G w = -D diag(1/c) w
+                    rdiv[c] -= (double)sgn * (double)ic * (double)we;   // div_G w = -D diag(1/c) w
                     ddiv[c] -= sgn * ic * dwe;
                 }
                 ge *= ic;
-                if (WN == VOMT_W_L1) { nw_pt += fabs(we); dn_w = fmax(dn_w, fabs(ge)); }
+                if (WN == VOMT_W_L1) { nw_pt += fabsf(we); dn_w = fmaxf(dn_w, fabsf(ge)); }
                 else { nw_pt += we * we; dn_w += ge * ge; }
             }
         }
-        if (WN == VOMT_W_L2) { nw_pt = sqrt(nw_pt); dn_w = sqrt(dn_w); }
-        v[RED_P] = nu_pt + alpha * nw_pt;
+        if (WN == VOMT_W_L2) { nw_pt = sqrtf(nw_pt); dn_w = sqrtf(dn_w); }
+        v[RED_P] = (double)nu_pt + (double)alpha * (double)nw_pt;
 #pragma unroll
         for (int c = 0; c < K; ++c) {
-            double rc = rdiv[c] + bb[c];
-            v[RED_RR] += rc * rc;
-            v[RED_X] += dph[c] * ddiv[c];
+            v[RED_RR] += rdiv[c] * rdiv[c];
+            v[RED_X] += (double)(dph[c] * ddiv[c]);
         }
-        double di = fmax(dn_u - 1.0, 0.0);
-        if (g.l > 0) di = fmax(di, dn_w - alpha);
-        v[RED_MAX] = di;
+        float di = fmaxf(dn_u - 1.0f, 0.0f);
+        if (g.l > 0) di = fmaxf(di, dn_w - alpha);
+        v[RED_MAX] = (double)di;
     }
     const int blk = blockIdx.y * gridDim.x + blockIdx.x;
     block_reduce_store(v, partials + (size_t)blk * NRED);

@@ -205,3 +205,18 @@ def test_resident_matches_stream_closely_at_256():
     assert _rel(b.phi.cpu().numpy().astype(np.float64), a.phi.cpu().numpy().astype(np.float64)) < 1e-5
     assert _rel(b.u.cpu().numpy().astype(np.float64), a.u.cpu().numpy().astype(np.float64)) < 1e-4
     assert abs(a.result["primal"] - b.result["primal"]) <= 1e-5 * a.result["primal"]
+
+
+@pytest.mark.parametrize("halo", [1, 2, 3, 5, 8])
+@pytest.mark.parametrize("n,k", [(64, 3), (130, 2), (256, 3), (97, 5)])
+def test_resident_halo_widths_match_oracle(halo, n, k):
+    """Temporal blocking: every ring width gives the same iterates (up to FP32 rounding)."""
+    rng = np.random.default_rng(n + 10 * k + halo)
+    edges = S.random_connected_graph(rng, k, 0.6)
+    r0, r1 = S.blob_pair(n, k, seed=n * 7 + k)
+    sol = _gpu(r0, r1, edges, 1.3, max_iters=210, check_every=70, engine="resident", halo=halo)
+    ref = _oracle(r0, r1, edges, 1.3, max_iters=210, check_every=70, history=True)
+    _compare(sol, ref)
+    h = V.history()
+    np.testing.assert_allclose(h[:, 0], ref["history"][:, 0], rtol=1e-4)
+    np.testing.assert_allclose(h[:, 4], ref["history"][:, 4], rtol=5e-2)
