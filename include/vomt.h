@@ -165,6 +165,50 @@ int vomt_solve_host(vomt_ctx *ctx, int n, const float *rho0, const float *rho1,
 int vomt_history(vomt_ctx *ctx, double *out, int cap);
 
 /* ------------------------------------------------------------------------ */
+/* Matrix OMT (Section 4, eq. (momt); algorithm of Section 7.3)               */
+/* ------------------------------------------------------------------------ */
+/* Densities are real symmetric k x k matrices per cell (k = 2 or 3), stored as
+ * full matrices: plane a*k + b of a [k*k][n][n] array holds entry (a, b).
+ * The quantum gradient of Section 4.1 is built from N real symmetric k x k
+ * matrices L (host, row-major, N*k*k doubles): grad_L X = (L_s X - X L_s)_s, and
+ * div_L = -grad_L^*.  The standing assumption ker grad_L = span{I} (Section 4.1)
+ * is checked; a violation returns VOMT_ERR_L_KERNEL.
+ *
+ * Norms (Section 6.2): u_norm VOMT_U_L2 is ||U||_2 (joint Frobenius over both
+ * directions) and VOMT_U_L1 is ||U||_1 (entrywise); the per-channel code
+ * VOMT_U_L12 (the vomt_default_params value) selects ||U||_2 here.  w_norm
+ * VOMT_W_L1 is ||W||_1 (entrywise), VOMT_W_L2 is ||W||_2 (joint Frobenius).
+ * Step sizes: tau <= 0 picks Table 3's value (10 for n <= 64, 30 for n <= 128,
+ * else 60); mu = 1/(32 tau (n-1)^2), nu = 1/(4 tau lambda_max(-Delta_L)) with
+ * lambda_max taken over all k x k matrices, as Section 7.3 forms it.
+ *
+ * Internally symmetric fields are stored as their k(k+1)/2 upper entries and
+ * skew ones as their k(k-1)/2 entries above the diagonal, with the off-diagonal
+ * entries weighted 2 in every inner product and norm, which reproduces the
+ * Hilbert-Schmidt geometry exactly (the shrinks stay exact by the Lemma of
+ * Appendix B and its entrywise analogue). */
+
+/* lambda_max(-Delta_L) over all k x k matrices, the second-smallest eigenvalue
+ * of -Delta_L on symmetric matrices (positive iff ker grad_L = span{I}), and the
+ * step sizes (host only).  Any output pointer may be NULL.
+ * Errors: BAD_ARG (k, N, L not symmetric), L_KERNEL. */
+int momt_step_sizes(int n, int k, int N, const double *L, double tau, double *mu, double *nu,
+                    double *tau_used, double *lmax, double *sym_gap);
+
+/* Solve matrix OMT by the M-OMT iteration of Section 7.3:
+ *   U <- shrink_u(U + mu grad Phi; mu), W <- shrink_w(W + nu grad_L Phi; alpha nu),
+ *   Phi <- Phi + tau (div_x(2U' - U) + div_L(2W' - W) + Lam1 - Lam0).
+ * Lam0, Lam1: device [k*k][n][n], symmetric (|X_ab - X_ba| <= 1e-5 max|X|),
+ * nonnegative diagonals, equal total trace.  U: device [2][k*k][n][n] (x then y
+ * components), W: device [N][k*k][n][n] (skew), Phi: device [k*k][n][n]
+ * (symmetric); outputs, and inputs when p->warm_start (symmetrised / made skew
+ * on the way in).  Metrics in *result use the Hilbert-Schmidt inner product.
+ * Errors: as vomt_solve, plus L_KERNEL. */
+int momt_solve(vomt_ctx *ctx, int n, int k, const float *Lam0, const float *Lam1, int N, const double *L,
+               double alpha, const vomt_params *p, float *U, float *W, float *Phi, vomt_result *result,
+               void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Allocation-free solve.  The paper has no counterpart: this is a            */
 /* deployment feature of this library.                                        */
 /* ------------------------------------------------------------------------ */

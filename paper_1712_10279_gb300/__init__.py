@@ -119,6 +119,62 @@ def solve_host(rho0, rho1, edges, alpha: float = 1.0, *, tau=None, mu=None, nu=N
     return Solution(u, w, phi, res.as_dict())
 
 
+def momt_step_sizes(n: int, L, tau=None):
+    """(mu, nu, tau, lambda_max(-Delta_L), second-smallest eigenvalue of -Delta_L on
+    symmetric matrices) from the rules of Section 7.3; L: [N, k, k] real symmetric."""
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    N, k = L.shape[0], L.shape[1]
+    out = [ctypes.c_double() for _ in range(5)]
+    _native.check(_native.load().momt_step_sizes(int(n), int(k), int(N), L.ctypes.data,
+                                                 0.0 if tau is None else float(tau),
+                                                 *[ctypes.byref(x) for x in out]))
+    return tuple(x.value for x in out)
+
+
+@dataclass
+class MatrixSolution:
+    U: object        # [2, k*k, n, n]: U_x then U_y, full symmetric matrices
+    W: object        # [N, k*k, n, n], full skew-symmetric matrices
+    Phi: object      # [k*k, n, n], full symmetric matrices
+    result: dict
+
+
+def momt_solve(Lam0, Lam1, L, alpha: float = 1.0, *, tau=None, mu=None, nu=None, u_norm: int = U_L2,
+               w_norm: int = W_L1, max_iters: int = 2000, check_every: int = 100, tol_gap: float = 0.0,
+               tol_res: float = 0.0, init=None, engine="auto", halo: int = 0, stream=None) -> MatrixSolution:
+    """Matrix OMT (Section 7.3) on the GPU.
+
+    Lam0, Lam1: CUDA float32 tensors [k*k, n, n] of real symmetric matrices (entry (a, b)
+    at plane a*k+b).  L: [N, k, k] real symmetric (numpy, host).  init: optional
+    (U, W, Phi) tensors to warm-start from.
+    """
+    import torch
+    Lam0 = Lam0.contiguous().float()
+    Lam1 = Lam1.contiguous().float()
+    Lh = np.ascontiguousarray(L, dtype=np.float64)
+    N, k = Lh.shape[0], Lh.shape[1]
+    kk, n = Lam0.shape[0], Lam0.shape[-1]
+    if kk != k * k:
+        raise ValueError("Lam0 must have k*k planes")
+    dev = Lam0.device
+    if init is not None:
+        U, W, Phi = (x.detach().clone().contiguous().float() for x in init)
+    else:
+        U = torch.empty((2, kk, n, n), device=dev, dtype=torch.float32)
+        W = torch.empty((N, kk, n, n), device=dev, dtype=torch.float32)
+        Phi = torch.empty((kk, n, n), device=dev, dtype=torch.float32)
+    p = _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, init is not None, engine,
+                halo)
+    res = _native.Result()
+    st = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
+    ctx = _native.context(dev.index if dev.index is not None else torch.cuda.current_device())
+    rc = _native.load().momt_solve(ctx, int(n), int(k), Lam0.data_ptr(), Lam1.data_ptr(), int(N), Lh.ctypes.data,
+                                   float(alpha), ctypes.byref(p), U.data_ptr(), W.data_ptr(), Phi.data_ptr(),
+                                   ctypes.byref(res), ctypes.c_void_p(st))
+    _native.check(rc, ctx)
+    return MatrixSolution(U, W, Phi, res.as_dict())
+
+
 def history(device: int = 0):
     """Rows (primal, dual, rel_gap, rel_res, fp_resid, dual_infeas, iter, converged) of every
     convergence check of the last solve on `device`."""

@@ -66,6 +66,10 @@ SIGNATURES = {
                                 ctypes.POINTER(Params), c_void_p, c_void_p, c_void_p, ctypes.POINTER(Result),
                                 c_void_p]),
     "vomt_history": (c_int, [c_void_p, P_double, c_int]),
+    "momt_step_sizes": (c_int, [c_int, c_int, c_int, c_void_p, c_double, P_double, P_double, P_double, P_double,
+                                P_double]),
+    "momt_solve": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int, c_void_p, c_double,
+                           ctypes.POINTER(Params), c_void_p, c_void_p, c_void_p, ctypes.POINTER(Result), c_void_p]),
     "vomt_solve_noalloc": (c_int, [c_int, c_void_p, c_void_p, ctypes.POINTER(Graph), c_double,
                                    ctypes.POINTER(Params), c_void_p, c_void_p, c_void_p, ctypes.POINTER(Result),
                                    c_void_p, ctypes.POINTER(ctypes.c_char_p)]),

@@ -32,7 +32,7 @@ int ensure_buffer(vomt_ctx *ctx, void **p, size_t *cap, size_t bytes, const char
     return VOMT_OK;
 }
 
-static int fail(vomt_ctx *ctx, int code, const char *msg)
+int fail(vomt_ctx *ctx, int code, const char *msg)
 {
     if (ctx) ctx->err = msg;
     return code;
@@ -42,7 +42,8 @@ static int fail(vomt_ctx *ctx, int code, const char *msg)
 static double default_tau(int n) { return n <= 64 ? 1.0 : 3.0; }
 
 struct Prepared {
-    GraphDev g;
+    GraphDev gd;
+    OpDev g;
     StepDev s;
     SolveCfg cfg;
     vomt_params p;
@@ -63,10 +64,11 @@ static int prepare(vomt_ctx *ctx, int n, const vomt_graph *graph, double alpha, 
     if (p.u_norm < 0 || p.u_norm > 2 || p.w_norm < 0 || p.w_norm > 1) return fail(ctx, VOMT_ERR_BAD_ARG, "bad norm code");
     if (p.engine < 0 || p.engine > 2) return fail(ctx, VOMT_ERR_BAD_ARG, "bad engine code");
     if (p.halo < 0 || p.halo > 16) return fail(ctx, VOMT_ERR_BAD_ARG, "halo must be in [0, 16]");
-    int rc = graph_to_dev(graph, &out->g, &ctx->err);
+    int rc = graph_to_dev(graph, &out->gd, &ctx->err);
     if (rc) return rc;
+    graph_to_op(out->gd, &out->g);
     const double tau = p.tau > 0.0 ? p.tau : default_tau(n);
-    const double lmax = graph_lmax(out->g, graph->cost);
+    const double lmax = graph_lmax(out->gd, graph->cost);
     const double n1 = (double)(n - 1);
     double mu = p.mu, nu = p.nu;
     const bool user = mu > 0.0 || nu > 0.0;
@@ -106,14 +108,14 @@ static int check_densities(vomt_ctx *ctx, int planes, int n, const float *rho0, 
     return VOMT_OK;
 }
 
-static void fill_result(vomt_ctx *ctx, const Prepared &P, int engine, vomt_result *r, int *status)
+void fill_result(vomt_ctx *ctx, const SolveCfg &cfg, int engine, vomt_result *r, int *status)
 {
     const DevStatus &h = ctx->hstatus[0];
     ctx->last_checks = h.checks;
     if (h.error) {
         *status = h.error;
         ctx->err = h.error == VOMT_ERR_NONFINITE ? "iterate became non-finite" : "device wait timed out";
-    } else if (P.cfg.tol_gap > 0.0) {
+    } else if (cfg.tol_gap > 0.0) {
         *status = h.met[7] != 0.0 ? VOMT_OK : VOMT_NOT_CONVERGED;
     } else {
         *status = VOMT_OK;
@@ -126,14 +128,36 @@ static void fill_result(vomt_ctx *ctx, const Prepared &P, int engine, vomt_resul
         r->fp_resid = h.met[4];
         r->dual_infeas = h.met[5];
         r->iters = h.iter;
-        r->mu = P.cfg.mu;
-        r->nu = P.cfg.nu;
-        r->tau = P.cfg.tau;
-        r->status = *status > 0 ? *status : (*status == 0 ? 0 : *status);
+        r->mu = cfg.mu;
+        r->nu = cfg.nu;
+        r->tau = cfg.tau;
+        r->status = *status;
         r->engine = engine;
         r->checks = h.checks;
         r->launches = ctx->launches;
     }
+}
+
+// Resident engine when the plan fits (AUTO / RESIDENT), else the streaming engine.
+int run_engine(vomt_ctx *ctx, const OpDev &op, const StepDev &s, const SolveCfg &cfg, const vomt_params &p,
+               const float *rho0, const float *rho1, float *u, float *w, float *phi, cudaStream_t st, int *engine)
+{
+    *engine = VOMT_ENGINE_STREAM;
+    int rc;
+    if (p.engine != VOMT_ENGINE_STREAM) {
+        ResidentPlan plan;
+        if (resident_plan(s.n, op.k, ctx->sm_count, p.halo, &plan)) {
+            rc = resident_solve(ctx, op, s, cfg, p, plan, rho0, rho1, u, w, phi, st);
+            if (rc == VOMT_OK) {
+                *engine = VOMT_ENGINE_RESIDENT;
+                return VOMT_OK;
+            }
+            if (!(rc == VOMT_ERR_TOO_LARGE && p.engine == VOMT_ENGINE_AUTO)) return rc;
+        } else if (p.engine == VOMT_ENGINE_RESIDENT) {
+            return fail(ctx, VOMT_ERR_TOO_LARGE, "grid too large for the resident engine");
+        }
+    }
+    return stream_solve(ctx, op, s, cfg, p, rho0, rho1, u, w, phi, st);
 }
 
 static int solve_device(vomt_ctx *ctx, int n, const float *rho0, const float *rho1, const vomt_graph *graph,
@@ -149,23 +173,11 @@ static int solve_device(vomt_ctx *ctx, int n, const float *rho0, const float *rh
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "cudaSetDevice");
     rc = check_densities(ctx, P.g.k, n, rho0, rho1, st);
     if (rc) return rc;
-    int engine = VOMT_ENGINE_STREAM;
-    if (P.p.engine != VOMT_ENGINE_STREAM) {
-        ResidentPlan plan;
-        if (resident_plan(n, P.g.k, ctx->sm_count, P.p.halo, &plan)) {
-            rc = resident_solve(ctx, P.g, P.s, P.cfg, P.p, plan, rho0, rho1, u, w, phi, st);
-            if (rc == VOMT_OK) engine = VOMT_ENGINE_RESIDENT;
-            else if (!(rc == VOMT_ERR_TOO_LARGE && P.p.engine == VOMT_ENGINE_AUTO)) return rc;
-        } else if (P.p.engine == VOMT_ENGINE_RESIDENT) {
-            return fail(ctx, VOMT_ERR_TOO_LARGE, "grid too large for the resident engine");
-        }
-    }
-    if (engine == VOMT_ENGINE_STREAM) {
-        rc = stream_solve(ctx, P.g, P.s, P.cfg, P.p, rho0, rho1, u, w, phi, st);
-        if (rc) return rc;
-    }
+    int engine = 0;
+    rc = run_engine(ctx, P.g, P.s, P.cfg, P.p, rho0, rho1, u, w, phi, st, &engine);
+    if (rc) return rc;
     int status = 0;
-    fill_result(ctx, P, engine, result, &status);
+    fill_result(ctx, P.cfg, engine, result, &status);
     return status;
 }
 
@@ -208,6 +220,7 @@ void vomt_destroy(vomt_ctx *c)
     if (c->hstatus) cudaFreeHost(c->hstatus);
     if (c->dhist) cudaFree(c->dhist);
     if (c->stage) cudaFree(c->stage);
+    if (c->mstage) cudaFree(c->mstage);
     if (c->rscratch) cudaFree(c->rscratch);
     delete c;
 }

@@ -59,9 +59,36 @@ static int sturm_count(int m, const double *d, const double *e, double x)
     return cnt;
 }
 
-double sym_lmax(int m, const double *Ain)
+// Householder reduction of a symmetric matrix to tridiagonal (d, e).
+static void tridiagonalise(int m, const double *Ain, std::vector<double> &d, std::vector<double> &e);
+
+double sym_lmax(int m, const double *Ain) { return sym_eig(m, Ain, m - 1); }
+
+double sym_eig(int m, const double *Ain, int idx)
 {
     if (m <= 0) return 0.0;
+    std::vector<double> d, e;
+    tridiagonalise(m, Ain, d, e);
+    // Gershgorin interval, then bisection for the smallest x with more than idx
+    // eigenvalues below it.
+    double lo = d[0], hi = d[0];
+    for (int i = 0; i < m; ++i) {
+        double rad = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
+        lo = std::min(lo, d[i] - rad);
+        hi = std::max(hi, d[i] + rad);
+    }
+    double scale = std::max(fabs(lo), fabs(hi));
+    lo -= 1e-12 * scale + 1e-300;
+    hi += 1e-12 * scale + 1e-300;
+    for (int it = 0; it < 400 && hi - lo > 1e-15 * scale; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (sturm_count(m, d.data(), e.data(), mid) > idx) hi = mid; else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+static void tridiagonalise(int m, const double *Ain, std::vector<double> &d, std::vector<double> &e)
+{
     std::vector<double> A(Ain, Ain + (size_t)m * m);
     std::vector<double> v(m), p(m);
     // Householder: zero column c below the sub-diagonal, for c = 0 .. m-3.
@@ -92,23 +119,10 @@ double sym_lmax(int m, const double *Ain)
         for (int r = 0; r < m; ++r)
             for (int t = 0; t < m; ++t) A[r * m + t] -= 2.0 * (v[r] * p[t] + p[r] * v[t]);
     }
-    std::vector<double> d(m), e(m > 1 ? m - 1 : 1);
+    d.assign(m, 0.0);
+    e.assign(m > 1 ? m - 1 : 1, 0.0);
     for (int i = 0; i < m; ++i) d[i] = A[i * m + i];
     for (int i = 0; i + 1 < m; ++i) e[i] = 0.5 * (A[(i + 1) * m + i] + A[i * m + i + 1]);
-    // Gershgorin interval, then bisection for the smallest x with all m eigenvalues below it.
-    double lo = d[0], hi = d[0];
-    for (int i = 0; i < m; ++i) {
-        double rad = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
-        lo = std::min(lo, d[i] - rad);
-        hi = std::max(hi, d[i] + rad);
-    }
-    double scale = std::max(fabs(lo), fabs(hi));
-    hi += 1e-12 * scale + 1e-300;
-    for (int it = 0; it < 400 && hi - lo > 1e-15 * scale; ++it) {
-        double mid = 0.5 * (lo + hi);
-        if (sturm_count(m, d.data(), e.data(), mid) >= m) hi = mid; else lo = mid;
-    }
-    return hi;
 }
 
 // lambda_max(-Delta_G), -Delta_G = D diag(1/c^2) D^T (Section 3.1): entry (a, b)
@@ -127,6 +141,131 @@ double graph_lmax(const GraphDev &g, const double *cost)
         M[b * g.k + a] -= wgt;
     }
     return sym_lmax(g.k, M.data());
+}
+
+}  // namespace vomt
+
+namespace vomt {
+
+void graph_to_op(const GraphDev &g, OpDev *op)
+{
+    memset(op, 0, sizeof(*op));
+    op->k = g.k;
+    op->l = g.l;
+    for (int c = 0; c < g.k; ++c) op->wc[c] = 1.0f;
+    for (int e = 0; e < g.l; ++e) {
+        op->we[e] = 1.0f;
+        op->G[e][g.lo[e]] = g.inv_c[e];     // grad_G = diag(1/c) D^T, D[lo][e] = +1, D[hi][e] = -1
+        op->G[e][g.hi[e]] = -g.inv_c[e];
+        op->Dv[g.lo[e]][e] = g.inv_c[e];    // div_G = -D diag(1/c)
+        op->Dv[g.hi[e]][e] = -g.inv_c[e];
+    }
+}
+
+// compact index of the symmetric entry (a, b): the diagonal first, then the entries
+// above it row by row ((0,1), (0,2), (1,2) for k = 3)
+static int sym_index(int k, int a, int b)
+{
+    if (a == b) return a;
+    if (a > b) { int t = a; a = b; b = t; }
+    int idx = k;
+    for (int r = 0; r < k; ++r)
+        for (int c = r + 1; c < k; ++c) {
+            if (r == a && c == b) return idx;
+            ++idx;
+        }
+    return -1;
+}
+
+int quantum_to_op(int k, int N, const double *L, OpDev *op, double *lmax, double *sym_gap, std::string *err)
+{
+    if (k < 2 || k > 3 || N < 1 || !L) { *err = "matrix OMT: need 2 <= k <= 3, N >= 1, L given"; return VOMT_ERR_BAD_ARG; }
+    const int K = k * (k + 1) / 2, ks = k * (k - 1) / 2;
+    if (N * ks > K * (K - 1) / 2) { *err = "matrix OMT: too many L matrices for this k"; return VOMT_ERR_BAD_ARG; }
+    double scale = 0.0;
+    for (int q = 0; q < N * k * k; ++q) {
+        if (!isfinite(L[q])) { *err = "matrix OMT: L has non-finite entries"; return VOMT_ERR_BAD_ARG; }
+        scale = std::max(scale, fabs(L[q]));
+    }
+    for (int s = 0; s < N; ++s)
+        for (int a = 0; a < k; ++a)
+            for (int b = 0; b < k; ++b)
+                if (fabs(L[(s * k + a) * k + b] - L[(s * k + b) * k + a]) > 1e-12 * std::max(scale, 1e-300)) {
+                    *err = "matrix OMT: every L_s must be symmetric";
+                    return VOMT_ERR_BAD_ARG;
+                }
+    memset(op, 0, sizeof(*op));
+    op->k = K;
+    op->l = N * ks;
+    for (int c = 0; c < K; ++c) op->wc[c] = c < k ? 1.0f : 2.0f;
+    // (grad_L Phi)_s = L_s Phi - Phi L_s; entry (a, b), a < b, of the skew result
+    int e = 0;
+    for (int s = 0; s < N; ++s) {
+        const double *Ls = L + (size_t)s * k * k;
+        for (int a = 0; a < k; ++a)
+            for (int b = a + 1; b < k; ++b, ++e) {
+                double row[KMAX] = {};
+                for (int m = 0; m < k; ++m) {
+                    row[sym_index(k, m, b)] += Ls[a * k + m];     // (L_s Phi)_ab
+                    row[sym_index(k, a, m)] -= Ls[m * k + b];     // (Phi L_s)_ab
+                }
+                op->we[e] = 2.0f;
+                for (int c = 0; c < K; ++c) {
+                    op->G[e][c] = (float)row[c];
+                    op->Dv[c][e] = (float)(2.0 / (c < k ? 1.0 : 2.0) * row[c]);
+                }
+            }
+    }
+    // -Delta_L X = sum_s [L_s, [L_s, X]] as a k^2 x k^2 matrix, column by column
+    const int kk = k * k;
+    std::vector<double> M((size_t)kk * kk, 0.0);
+    for (int col = 0; col < kk; ++col) {
+        double X[9] = {}, C1[9], C2[9];
+        X[col] = 1.0;
+        for (int s = 0; s < N; ++s) {
+            const double *Ls = L + (size_t)s * kk;
+            for (int a = 0; a < k; ++a)
+                for (int b = 0; b < k; ++b) {
+                    double v = 0.0;
+                    for (int m = 0; m < k; ++m) v += Ls[a * k + m] * X[m * k + b] - X[a * k + m] * Ls[m * k + b];
+                    C1[a * k + b] = v;
+                }
+            for (int a = 0; a < k; ++a)
+                for (int b = 0; b < k; ++b) {
+                    double v = 0.0;
+                    for (int m = 0; m < k; ++m) v += Ls[a * k + m] * C1[m * k + b] - C1[a * k + m] * Ls[m * k + b];
+                    C2[a * k + b] = v;
+                }
+            for (int r = 0; r < kk; ++r) M[(size_t)r * kk + col] += C2[r];
+        }
+    }
+    if (lmax) *lmax = sym_lmax(kk, M.data());
+    // restriction to symmetric matrices in an orthonormal basis (E_aa, (E_ab + E_ba)/sqrt 2)
+    std::vector<double> B((size_t)kk * K, 0.0), Sm((size_t)K * K, 0.0);
+    for (int a = 0; a < k; ++a)
+        for (int b = a; b < k; ++b) {
+            const int c = sym_index(k, a, b);
+            if (a == b) B[(size_t)(a * k + a) * K + c] = 1.0;
+            else {
+                B[(size_t)(a * k + b) * K + c] = 1.0 / sqrt(2.0);
+                B[(size_t)(b * k + a) * K + c] = 1.0 / sqrt(2.0);
+            }
+        }
+    for (int p = 0; p < K; ++p)
+        for (int q = 0; q < K; ++q) {
+            double v = 0.0;
+            for (int r = 0; r < kk; ++r)
+                for (int c = 0; c < kk; ++c) v += B[(size_t)r * K + p] * M[(size_t)r * kk + c] * B[(size_t)c * K + q];
+            Sm[(size_t)p * K + q] = v;
+        }
+    const double gap = sym_eig(K, Sm.data(), 1);
+    if (sym_gap) *sym_gap = gap;
+    const double lm = sym_lmax(kk, M.data());
+    if (!(gap > 1e-8 * lm)) {
+        *err = "matrix OMT: ker grad_L on symmetric matrices is larger than span{I}";
+        return VOMT_ERR_L_KERNEL;
+    }
+    return VOMT_OK;
 }
 
 }  // namespace vomt

@@ -22,6 +22,22 @@ struct GraphDev {
     float inv_c[LMAX];
 };
 
+// Per-point linear structure as the kernels see it (a kernel argument).  A
+// point carries k "channels" (vector OMT: the k colour channels; matrix OMT:
+// the k(k+1)/2 entries of a symmetric matrix, diagonal first) and l flux
+// entries (vector OMT: the graph edges; matrix OMT: the k(k-1)/2 entries above
+// the diagonal of each skew-symmetric W_s).  Inner products weigh channel c by
+// wc[c] and flux entry e by we[e] (2 for an off-diagonal entry, which stands for
+// itself and its mirror), so the compact coordinates reproduce the
+// Hilbert-Schmidt products of Section 4.
+struct OpDev {
+    int k, l;
+    float wc[KMAX];
+    float we[LMAX];
+    float G[LMAX][KMAX];     // (grad phi)_e = sum_c G[e][c] phi_c   (grad_G or grad_L)
+    float Dv[KMAX][LMAX];    // (div y)_c = -sum_e Dv[c][e] y_e,  Dv = (we / wc) G^T (div = -grad^*)
+};
+
 // Per-solve scalars.
 struct StepDev {
     int n;          // grid side
@@ -64,7 +80,14 @@ struct SolveCfg {
 // ----------------------------------------------------------------- host setup
 int graph_to_dev(const vomt_graph *g, GraphDev *out, std::string *err);
 double sym_lmax(int m, const double *A);     // largest eigenvalue of a symmetric m x m matrix
+double sym_eig(int m, const double *A, int idx);   // idx-th smallest eigenvalue (0-based)
 double graph_lmax(const GraphDev &g, const double *cost);
+void graph_to_op(const GraphDev &g, OpDev *op);
+// Quantum operator of Section 4.1 for N real symmetric k x k matrices L (row-major,
+// host): compact grad / div, lambda_max(-Delta_L) over all k x k matrices (the
+// k^2 x k^2 matrix of Section 7.3) and the second-smallest eigenvalue of -Delta_L on
+// symmetric matrices (positive iff ker grad_L = span{I}, the standing assumption).
+int quantum_to_op(int k, int N, const double *L, OpDev *op, double *lmax, double *sym_gap, std::string *err);
 
 }  // namespace vomt
 
@@ -88,6 +111,9 @@ struct vomt_ctx {
     float *stage = nullptr;
     size_t stage_floats = 0;
     int launches = 0;                        // kernels launched by the current call
+    // matrix-OMT compact staging (device)
+    float *mstage = nullptr;
+    size_t mstage_bytes = 0;
     // resident-engine scratch
     void *rscratch = nullptr;
     size_t rscratch_bytes = 0;
@@ -95,10 +121,14 @@ struct vomt_ctx {
 
 namespace vomt {
 int set_cuda_error(vomt_ctx *ctx, cudaError_t e, const char *what);
+int fail(vomt_ctx *ctx, int code, const char *msg);
+void fill_result(vomt_ctx *ctx, const SolveCfg &cfg, int engine, vomt_result *r, int *status);
+int run_engine(vomt_ctx *ctx, const OpDev &op, const StepDev &s, const SolveCfg &cfg, const vomt_params &p,
+               const float *rho0, const float *rho1, float *u, float *w, float *phi, cudaStream_t st, int *engine);
 int ensure_buffer(vomt_ctx *ctx, void **p, size_t *cap, size_t bytes, const char *what);
 
 // streaming engine (vector_stream.cu)
-int stream_solve(vomt_ctx *ctx, const GraphDev &g, const StepDev &s, const SolveCfg &cfg,
+int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg &cfg,
                  const vomt_params &p, const float *rho0, const float *rho1,
                  float *u, float *w, float *phi, cudaStream_t st);
 // resident engine (vector_resident.cu)
@@ -107,7 +137,7 @@ struct ResidentPlan {
     double est_ns;
 };
 bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out);
-int resident_solve(vomt_ctx *ctx, const GraphDev &g, const StepDev &s, const SolveCfg &cfg, const vomt_params &p,
+int resident_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg &cfg, const vomt_params &p,
                    const ResidentPlan &plan, const float *rho0, const float *rho1, float *u, float *w, float *phi,
                    cudaStream_t st);
 int validate_densities(vomt_ctx *ctx, int planes, int n, const float *rho0, const float *rho1,

@@ -31,9 +31,10 @@ __device__ __forceinline__ float pick(const float (&a)[K], int idx)
     return r;
 }
 
-// shrink_u on one point (all channels), in place; un = VOMT_U_*
+// shrink_u on one point (all channels), in place; un = VOMT_U_*; channel weights wc
+// enter the joint norm (2 for an off-diagonal matrix entry)
 template <int K>
-__device__ __forceinline__ void shrink_u(float (&vx)[K], float (&vy)[K], float t, int un)
+__device__ __forceinline__ void shrink_u(float (&vx)[K], float (&vy)[K], float t, int un, const float *wc)
 {
     if (un == VOMT_U_L12) {
 #pragma unroll
@@ -45,7 +46,7 @@ __device__ __forceinline__ void shrink_u(float (&vx)[K], float (&vy)[K], float t
     } else if (un == VOMT_U_L2) {
         float s2 = 0.0f;
 #pragma unroll
-        for (int c = 0; c < K; ++c) s2 += vx[c] * vx[c] + vy[c] * vy[c];
+        for (int c = 0; c < K; ++c) s2 += wc[c] * (vx[c] * vx[c] + vy[c] * vy[c]);
         float f = shrink2_factor(s2, t);
 #pragma unroll
         for (int c = 0; c < K; ++c) { vx[c] *= f; vy[c] *= f; }
@@ -55,9 +56,9 @@ __device__ __forceinline__ void shrink_u(float (&vx)[K], float (&vy)[K], float t
     }
 }
 
-// shrink_w on one point, l <= LK edges; wn = VOMT_W_*
+// shrink_w on one point, l <= LK flux entries with weights we; wn = VOMT_W_*
 template <int LK>
-__device__ __forceinline__ void shrink_w(float (&x)[LK], int l, float t, int wn)
+__device__ __forceinline__ void shrink_w(float (&x)[LK], int l, float t, int wn, const float *we)
 {
     if (wn == VOMT_W_L1) {
 #pragma unroll
@@ -67,7 +68,7 @@ __device__ __forceinline__ void shrink_w(float (&x)[LK], int l, float t, int wn)
         float s2 = 0.0f;
 #pragma unroll
         for (int e = 0; e < LK; ++e)
-            if (e < l) s2 += x[e] * x[e];
+            if (e < l) s2 += we[e] * x[e] * x[e];
         float f = shrink2_factor(s2, t);
 #pragma unroll
         for (int e = 0; e < LK; ++e) x[e] *= f;

@@ -50,10 +50,9 @@ struct ResGeom {
 
 struct ResArgs {
     ResGeom geo;
-    GraphDev g;
+    OpDev g;                   // per-point grad / div and inner-product weights
     StepDev s;
     SolveCfg cfg;
-    float Dt[KMAX][LMAX];      // D diag(1/c): +1/c_e at the lower node of edge e, -1/c_e at the upper
     int un, wn, max_iters, check_every, warm;
     const float *rho0, *rho1;
     float *u, *w, *phi;
@@ -313,7 +312,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
                     vx[c] = ux[r][c] + ((x < n - 1) ? muih * (SA(sphi, c, ey, ex + 1) - pc) : 0.0f);
                     vy[c] = uy[r][c] + ((y < n - 1) ? muih * (SA(sphi, c, ey + 1, ex) - pc) : 0.0f);
                 }
-                shrink_u<K>(vx, vy, mu, a.un);
+                shrink_u<K>(vx, vy, mu, a.un, a.g.wc);
 #pragma unroll
                 for (int c = 0; c < K; ++c) {
                     SA(sux, c, ey, ex) = 2.0f * vx[c] - ux[r][c];
@@ -325,17 +324,17 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
                 for (int e = 0; e < LKv; ++e) {
                     float ge = 0.0f;
 #pragma unroll
-                    for (int c = 0; c < K; ++c) ge += a.Dt[c][e] * ph[r][c];
+                    for (int c = 0; c < K; ++c) ge += a.g.G[e][c] * ph[r][c];
                     wx[e] = (e < l) ? w[r][e] + nu * ge : 0.0f;
                 }
-                shrink_w<LKv>(wx, l, alpha * nu, a.wn);
+                shrink_w<LKv>(wx, l, alpha * nu, a.wn, a.g.we);
 #pragma unroll
                 for (int c = 0; c < K; ++c) {
                     float gw = 0.0f, gd = 0.0f;
 #pragma unroll
                     for (int e = 0; e < LKv; ++e) {
-                        gw -= a.Dt[c][e] * (2.0f * wx[e] - w[r][e]);
-                        gd -= a.Dt[c][e] * (wx[e] - w[r][e]);
+                        gw -= a.g.Dv[c][e] * (2.0f * wx[e] - w[r][e]);
+                        gd -= a.g.Dv[c][e] * (wx[e] - w[r][e]);
                     }
                     racc[r][c] = gw + bb[r][c];
                     if (last) dgw[r][c] = gd;
@@ -346,12 +345,12 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
                         const float dux = vx[c] - ux[r][c], duy = vy[c] - uy[r][c];
                         SA(sdx, c, ey, ex) = dux;
                         SA(sdy, c, ey, ex) = duy;
-                        v[RED_DU] += (double)dux * dux + (double)duy * duy;
+                        v[RED_DU] += (double)(a.g.wc[c] * (dux * dux + duy * duy));
                     }
 #pragma unroll
                     for (int e = 0; e < LKv; ++e) {
                         const float dw = wx[e] - w[r][e];
-                        v[RED_DW] += (double)dw * dw;
+                        v[RED_DW] += (double)(a.g.we[e] * dw * dw);
                     }
                 }
 #pragma unroll
@@ -426,23 +425,23 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
                 const float dyd = (y > 0) ? SA(sdy, c, ey - 1, ex) : 0.0f;
                 const float ddiv = ih * ((SA(sdx, c, ey, ex) - dxl) + (SA(sdy, c, ey, ex) - dyd)) + dgw[r][c];
 #pragma unroll
-                for (int e = 0; e < LKv; ++e) rdiv -= (double)a.Dt[c][e] * (double)w[r][e];
-                const double rc = rdiv + (double)bc;
-                v[RED_RR] += rc * rc;
-                v[RED_BB] += (double)(bc * bc);
-                v[RED_D] += (double)phc * (double)bc;
-                v[RED_DP] += (double)(dph[r][c] * dph[r][c]);
-                v[RED_X] += (double)(dph[r][c] * ddiv);
+                for (int e = 0; e < LKv; ++e) rdiv -= (double)a.g.Dv[c][e] * (double)w[r][e];
+                const double rc = rdiv + (double)bc, wgt = (double)a.g.wc[c];
+                v[RED_RR] += wgt * rc * rc;
+                v[RED_BB] += wgt * (double)(bc * bc);
+                v[RED_D] += wgt * (double)phc * (double)bc;
+                v[RED_DP] += wgt * (double)(dph[r][c] * dph[r][c]);
+                v[RED_X] += wgt * (double)(dph[r][c] * ddiv);
                 const float gxx = (x < n - 1) ? ih * (SA(sphi, c, ey, ex + 1) - phc) : 0.0f;
                 const float gyy = (y < n - 1) ? ih * (SA(sphi, c, ey + 1, ex) - phc) : 0.0f;
                 if (a.un == VOMT_U_L12) {
                     nu_pt += sqrtf(uxc * uxc + uyc * uyc);
                     dn_u = fmaxf(dn_u, sqrtf(gxx * gxx + gyy * gyy));
                 } else if (a.un == VOMT_U_L2) {
-                    nu_pt += uxc * uxc + uyc * uyc;
-                    dn_u += gxx * gxx + gyy * gyy;
+                    nu_pt += a.g.wc[c] * (uxc * uxc + uyc * uyc);
+                    dn_u += a.g.wc[c] * (gxx * gxx + gyy * gyy);
                 } else {
-                    nu_pt += fabsf(uxc) + fabsf(uyc);
+                    nu_pt += a.g.wc[c] * (fabsf(uxc) + fabsf(uyc));
                     dn_u = fmaxf(dn_u, fmaxf(fabsf(gxx), fabsf(gyy)));
                 }
             }
@@ -453,10 +452,10 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
                 if (e < l) {
                     float ge = 0.0f;
 #pragma unroll
-                    for (int c = 0; c < K; ++c) ge += a.Dt[c][e] * ph[r][c];
-                    const float we = w[r][e];
-                    if (a.wn == VOMT_W_L1) { nw_pt += fabsf(we); dn_w = fmaxf(dn_w, fabsf(ge)); }
-                    else { nw_pt += we * we; dn_w += ge * ge; }
+                    for (int c = 0; c < K; ++c) ge += a.g.G[e][c] * ph[r][c];
+                    const float we = w[r][e], wgt = a.g.we[e];
+                    if (a.wn == VOMT_W_L1) { nw_pt += wgt * fabsf(we); dn_w = fmaxf(dn_w, fabsf(ge)); }
+                    else { nw_pt += wgt * we * we; dn_w += wgt * ge * ge; }
                 }
             }
             if (a.wn == VOMT_W_L2) { nw_pt = sqrtf(nw_pt); dn_w = sqrtf(dn_w); }
@@ -649,7 +648,7 @@ bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out)
     return true;
 }
 
-int resident_solve(vomt_ctx *ctx, const GraphDev &g, const StepDev &s, const SolveCfg &cfg, const vomt_params &p,
+int resident_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg &cfg, const vomt_params &p,
                    const ResidentPlan &plan, const float *rho0, const float *rho1, float *u, float *w, float *phi,
                    cudaStream_t st)
 {
@@ -675,10 +674,6 @@ int resident_solve(vomt_ctx *ctx, const GraphDev &g, const StepDev &s, const Sol
     a.g = g;
     a.s = s;
     a.cfg = cfg;
-    for (int e = 0; e < g.l; ++e) {
-        a.Dt[g.lo[e]][e] = g.inv_c[e];
-        a.Dt[g.hi[e]][e] = -g.inv_c[e];
-    }
     a.un = p.u_norm;
     a.wn = p.w_norm;
     a.max_iters = p.max_iters;

@@ -45,8 +45,9 @@ __device__ __forceinline__ float pick(const float (&a)[K], int idx)
 }
 
 // shrink_u on one point, all channels, in place (Section 7.2, u-update)
+// (channel weights wc enter the joint norm ||u||_2: 2 for an off-diagonal matrix entry)
 template <int K, int UN>
-__device__ __forceinline__ void shrink_u(float (&vx)[K], float (&vy)[K], float t)
+__device__ __forceinline__ void shrink_u(float (&vx)[K], float (&vy)[K], float t, const float *wc)
 {
     if (UN == VOMT_U_L12) {
 #pragma unroll
@@ -58,7 +59,7 @@ __device__ __forceinline__ void shrink_u(float (&vx)[K], float (&vy)[K], float t
     } else if (UN == VOMT_U_L2) {
         float s2 = 0.0f;
 #pragma unroll
-        for (int c = 0; c < K; ++c) s2 += vx[c] * vx[c] + vy[c] * vy[c];
+        for (int c = 0; c < K; ++c) s2 += wc[c] * (vx[c] * vx[c] + vy[c] * vy[c]);
         float f = shrink2_factor(s2, t);
 #pragma unroll
         for (int c = 0; c < K; ++c) { vx[c] *= f; vy[c] *= f; }
@@ -68,9 +69,9 @@ __device__ __forceinline__ void shrink_u(float (&vx)[K], float (&vy)[K], float t
     }
 }
 
-// shrink_w on one point (Section 7.2, w-update), l <= LK edges
+// shrink_w on one point (Section 7.2, w-update), l <= LK flux entries with weights we
 template <int LK, int WN>
-__device__ __forceinline__ void shrink_w(float (&x)[LK], int l, float t)
+__device__ __forceinline__ void shrink_w(float (&x)[LK], int l, float t, const float *we)
 {
     if (WN == VOMT_W_L1) {
 #pragma unroll
@@ -80,7 +81,7 @@ __device__ __forceinline__ void shrink_w(float (&x)[LK], int l, float t)
         float s2 = 0.0f;
 #pragma unroll
         for (int e = 0; e < LK; ++e)
-            if (e < l) s2 += x[e] * x[e];
+            if (e < l) s2 += we[e] * x[e] * x[e];
         float f = shrink2_factor(s2, t);
 #pragma unroll
         for (int e = 0; e < LK; ++e) x[e] *= f;
@@ -95,7 +96,7 @@ struct LKOf {
 // ----------------------------------------------------------------- iteration
 template <int K, int UN, int WN>
 __global__ void __launch_bounds__(NT) k_step(StateIn in, StateOut out, const float *__restrict__ b,
-                                              GraphDev g, StepDev s, const DevStatus *__restrict__ st)
+                                              OpDev g, StepDev s, const DevStatus *__restrict__ st)
 {
     if (st->stop) return;
     constexpr int LK = LKOf<K>::v;
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(NT) k_step(StateIn in, StateOut out, const flo
         vx[c] = ux0[c] + (hR ? mu * (ih * (pr[c] - pc[c])) : 0.0f);
         vy[c] = uy0[c] + (hU ? mu * (ih * (pu[c] - pc[c])) : 0.0f);
     }
-    shrink_u<K, UN>(vx, vy, mu);
+    shrink_u<K, UN>(vx, vy, mu, g.wc);
     // u' at (i-1, j): only its x component enters div at (i, j)
     float lx[K], ly[K], lx0[K];
 #pragma unroll
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(NT) k_step(StateIn in, StateOut out, const flo
         lx[c] = lx0[c] + (hL ? mu * (ih * (pc[c] - pl[c])) : 0.0f);
         ly[c] = ly0 + ((hL && hU) ? mu * (ih * (plu[c] - pl[c])) : 0.0f);
     }
-    shrink_u<K, UN>(lx, ly, mu);
+    shrink_u<K, UN>(lx, ly, mu, g.wc);
     // u' at (i, j-1): only its y component enters div at (i, j)
     float dx[K], dy[K], dy0[K];
 #pragma unroll
@@ -149,21 +150,23 @@ __global__ void __launch_bounds__(NT) k_step(StateIn in, StateOut out, const flo
         dx[c] = dx0 + ((hR && hD) ? mu * (ih * (prd[c] - pd[c])) : 0.0f);
         dy[c] = dy0[c] + (hD ? mu * (ih * (pc[c] - pd[c])) : 0.0f);
     }
-    shrink_u<K, UN>(dx, dy, mu);
+    shrink_u<K, UN>(dx, dy, mu, g.wc);
     // w' at (i, j)
     float w0[LK], wx[LK];
 #pragma unroll
     for (int e = 0; e < LK; ++e) {
         if (e < g.l) {
             w0[e] = __ldg(in.w + e * nn + p);
-            float ge = g.inv_c[e] * (pick<K>(pc, g.lo[e]) - pick<K>(pc, g.hi[e]));
+            float ge = 0.0f;
+#pragma unroll
+            for (int c = 0; c < K; ++c) ge += g.G[e][c] * pc[c];
             wx[e] = w0[e] + s.nu * ge;
         } else {
             w0[e] = 0.0f;
             wx[e] = 0.0f;
         }
     }
-    shrink_w<LK, WN>(wx, g.l, s.alpha * s.nu);
+    shrink_w<LK, WN>(wx, g.l, s.alpha * s.nu, g.we);
     // phi' = phi + tau (div_x ubar + div_G wbar + rho1 - rho0)
     float r[K];
 #pragma unroll
@@ -176,12 +179,9 @@ __global__ void __launch_bounds__(NT) k_step(StateIn in, StateOut out, const flo
     }
 #pragma unroll
     for (int e = 0; e < LK; ++e) {
-        if (e < g.l) {
-            float v = g.inv_c[e] * (2.0f * wx[e] - w0[e]);
-            const int lo = g.lo[e], hi = g.hi[e];
+        const float v = 2.0f * wx[e] - w0[e];     // zero for e >= l
 #pragma unroll
-            for (int c = 0; c < K; ++c) r[c] += (c == hi ? v : 0.0f) - (c == lo ? v : 0.0f);
-        }
+        for (int c = 0; c < K; ++c) r[c] -= g.Dv[c][e] * v;
     }
 #pragma unroll
     for (int c = 0; c < K; ++c) {
@@ -220,7 +220,7 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NRED], double *ds
 
 template <int K, int UN, int WN>
 __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const float *__restrict__ b,
-                                                 GraphDev g, StepDev s, double *__restrict__ partials,
+                                                 OpDev g, StepDev s, double *__restrict__ partials,
                                                  const DevStatus *__restrict__ st)
 {
     if (st->stop) return;
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const 
 #pragma unroll
         for (int c = 0; c < K; ++c) {
             const size_t q = c * nn + p;
-            const float uxc = cur.ux[q], uyc = cur.uy[q], bc = b[q];
+            const float uxc = cur.ux[q], uyc = cur.uy[q], bc = b[q], wgt = g.wc[c];
             ph[c] = cur.phi[q];
             dph[c] = ph[c] - prv.phi[q];
             const float xl = hL ? cur.ux[q - 1] : 0.0f, yd = hD ? cur.uy[q - n] : 0.0f;
@@ -254,20 +254,20 @@ __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const 
             const float dxl = hL ? cur.ux[q - 1] - prv.ux[q - 1] : 0.0f;
             const float dyd = hD ? cur.uy[q - n] - prv.uy[q - n] : 0.0f;
             ddiv[c] = ih * ((dux - dxl) + (duy - dyd));
-            v[RED_DU] += (double)(dux * dux + duy * duy);
-            v[RED_DP] += (double)(dph[c] * dph[c]);
-            v[RED_D] += (double)ph[c] * (double)bc;
-            v[RED_BB] += (double)(bc * bc);
+            v[RED_DU] += (double)(wgt * (dux * dux + duy * duy));
+            v[RED_DP] += (double)(wgt * dph[c] * dph[c]);
+            v[RED_D] += (double)wgt * (double)ph[c] * (double)bc;
+            v[RED_BB] += (double)(wgt * bc * bc);
             const float gx = hR ? ih * (cur.phi[q + 1] - ph[c]) : 0.0f;
             const float gy = hU ? ih * (cur.phi[q + n] - ph[c]) : 0.0f;
             if (UN == VOMT_U_L12) {
                 nu_pt += sqrtf(uxc * uxc + uyc * uyc);
                 dn_u = fmaxf(dn_u, sqrtf(gx * gx + gy * gy));
             } else if (UN == VOMT_U_L2) {
-                nu_pt += uxc * uxc + uyc * uyc;
-                dn_u += gx * gx + gy * gy;
+                nu_pt += wgt * (uxc * uxc + uyc * uyc);
+                dn_u += wgt * (gx * gx + gy * gy);
             } else {
-                nu_pt += fabsf(uxc) + fabsf(uyc);
+                nu_pt += wgt * (fabsf(uxc) + fabsf(uyc));
                 dn_u = fmaxf(dn_u, fmaxf(fabsf(gx), fabsf(gy)));
             }
         }
@@ -277,29 +277,25 @@ __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const 
         for (int e = 0; e < LK; ++e) {
             if (e < g.l) {
                 const size_t q = e * nn + p;
-                const int lo = g.lo[e], hi = g.hi[e];
-                const float ic = g.inv_c[e];
-                const float we = cur.w[q], dwe = we - prv.w[q];
-                v[RED_DW] += (double)(dwe * dwe);
+                const float we = cur.w[q], dwe = we - prv.w[q], wgt = g.we[e];
+                v[RED_DW] += (double)(wgt * dwe * dwe);
                 float ge = 0.0f;
 #pragma unroll
                 for (int c = 0; c < K; ++c) {
-                    const float sgn = (c == lo) ? 1.0f : (c == hi ? -1.0f : 0.0f);
-                    ge += sgn * ph[c];
-                    rdiv[c] -= (double)sgn * (double)ic * (double)we;   // div_G w = -D diag(1/c) w
-                    ddiv[c] -= sgn * ic * dwe;
+                    ge += g.G[e][c] * ph[c];
+                    rdiv[c] -= (double)g.Dv[c][e] * (double)we;   // div y = -Dv y
+                    ddiv[c] -= g.Dv[c][e] * dwe;
                 }
-                ge *= ic;
-                if (WN == VOMT_W_L1) { nw_pt += fabsf(we); dn_w = fmaxf(dn_w, fabsf(ge)); }
-                else { nw_pt += we * we; dn_w += ge * ge; }
+                if (WN == VOMT_W_L1) { nw_pt += wgt * fabsf(we); dn_w = fmaxf(dn_w, fabsf(ge)); }
+                else { nw_pt += wgt * we * we; dn_w += wgt * ge * ge; }
             }
         }
         if (WN == VOMT_W_L2) { nw_pt = sqrtf(nw_pt); dn_w = sqrtf(dn_w); }
         v[RED_P] = (double)nu_pt + (double)alpha * (double)nw_pt;
 #pragma unroll
         for (int c = 0; c < K; ++c) {
-            v[RED_RR] += rdiv[c] * rdiv[c];
-            v[RED_X] += (double)(dph[c] * ddiv[c]);
+            v[RED_RR] += (double)g.wc[c] * rdiv[c] * rdiv[c];
+            v[RED_X] += (double)(g.wc[c] * dph[c] * ddiv[c]);
         }
         float di = fmaxf(dn_u - 1.0f, 0.0f);
         if (g.l > 0) di = fmaxf(di, dn_w - alpha);
@@ -422,8 +418,8 @@ __global__ void k_validate(size_t count, const float *__restrict__ r0, const flo
 
 // ----------------------------------------------------------------- dispatch
 struct Launchers {
-    void (*step)(StateIn, StateOut, const float *, GraphDev, StepDev, const DevStatus *);
-    void (*metrics)(StateIn, StateIn, const float *, GraphDev, StepDev, double *, const DevStatus *);
+    void (*step)(StateIn, StateOut, const float *, OpDev, StepDev, const DevStatus *);
+    void (*metrics)(StateIn, StateIn, const float *, OpDev, StepDev, double *, const DevStatus *);
 };
 
 template <int K, int UN, int WN>
@@ -482,7 +478,7 @@ int validate_densities(vomt_ctx *ctx, int planes, int n, const float *rho0, cons
     return VOMT_OK;
 }
 
-int stream_solve(vomt_ctx *ctx, const GraphDev &g, const StepDev &s, const SolveCfg &cfg,
+int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg &cfg,
                  const vomt_params &p, const float *rho0, const float *rho1,
                  float *u, float *w, float *phi, cudaStream_t st)
 {
@@ -641,13 +637,15 @@ extern "C" int vomt_solve_noalloc(int n, const float *rho0, const float *rho1, c
     if (pin) p = *pin;
     if (p.max_iters < 0 || p.check_every < 1) { *why = "max_iters >= 0, check_every >= 1"; return VOMT_ERR_BAD_ARG; }
     if (p.u_norm < 0 || p.u_norm > 2 || p.w_norm < 0 || p.w_norm > 1) { *why = "bad norm code"; return VOMT_ERR_BAD_ARG; }
-    GraphDev g;
+    GraphDev gd;
     std::string gerr;
-    int rc = graph_to_dev(graph, &g, &gerr);
+    int rc = graph_to_dev(graph, &gd, &gerr);
     if (rc) { *why = "invalid channel graph"; return rc; }
+    OpDev g;
+    graph_to_op(gd, &g);
     if (!rho0 || !rho1 || !u || !phi || (g.l > 0 && !w)) { *why = "null array"; return VOMT_ERR_BAD_ARG; }
     const double tau = p.tau > 0.0 ? p.tau : (n <= 64 ? 1.0 : 3.0);
-    const double lmax = graph_lmax(g, graph->cost);
+    const double lmax = graph_lmax(gd, graph->cost);
     const double n1 = (double)(n - 1);
     double mu = p.mu, nu = p.nu;
     const bool user = mu > 0.0 || nu > 0.0;

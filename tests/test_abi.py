@@ -87,3 +87,30 @@ def test_status_strings():
     p = _native.Params()
     lib.vomt_default_params(p)
     assert p.max_iters == 2000 and p.check_every == 100 and p.u_norm == 0 and p.w_norm == 0
+
+
+def test_matrix_step_sizes_match_oracle():
+    L = S.paper_L()
+    mu, nu, tau, lm, gap = V.momt_step_sizes(128, L)
+    assert lm == pytest.approx(oracle.quantum_lmax(L), rel=1e-10)
+    assert gap == pytest.approx(oracle.quantum_sym_gap(L), rel=1e-8)
+    assert tau == oracle.default_tau_matrix(128)
+    mu_o, nu_o = oracle.step_sizes(128, tau, oracle.quantum_lmax(L), True)
+    assert mu == pytest.approx(mu_o, rel=1e-14) and nu == pytest.approx(nu_o, rel=1e-10)
+    for seed in range(5):
+        Lr = S.random_L(3, 3, seed=seed)
+        _, _, _, lm, gap = V.momt_step_sizes(64, Lr)
+        assert lm == pytest.approx(oracle.quantum_lmax(Lr), rel=1e-10)
+        assert gap == pytest.approx(oracle.quantum_sym_gap(Lr), rel=1e-7)
+    L2 = S.random_L(2, 2, seed=3)
+    _, _, _, lm, _ = V.momt_step_sizes(64, L2)
+    assert lm == pytest.approx(oracle.quantum_lmax(L2), rel=1e-10)
+
+
+def test_matrix_kernel_assumption_rejected():
+    with pytest.raises(V.VomtError) as e:
+        V.momt_step_sizes(32, np.diag([1.0, 1.0, 0.0])[None])
+    assert e.value.status == -5
+    with pytest.raises(V.VomtError) as e:
+        V.momt_step_sizes(32, np.array([[[1.0, 2.0, 0], [0, 1, 0], [0, 0, 3]]]))   # not symmetric
+    assert e.value.status == -1
