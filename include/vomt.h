@@ -165,6 +165,57 @@ int vomt_solve_host(vomt_ctx *ctx, int n, const float *rho0, const float *rho1,
 int vomt_history(vomt_ctx *ctx, double *out, int cap);
 
 /* ------------------------------------------------------------------------ */
+/* Batched vector OMT: many independent problems in one persistent launch     */
+/* ------------------------------------------------------------------------ */
+/* Each instance is a vector-OMT problem of its own grid side, channel count,
+ * channel graph and alpha (Section 7.2).  Its data lives in one FP32 arena in
+ * device memory, starting at float `offset`:
+ *   rho0 [k][n][n], rho1 [k][n][n], u [2][k][n][n], w [l][n][n], phi [k][n][n]
+ * i.e. (5k + l) n^2 floats.  rho0 / rho1 are inputs, u / w / phi outputs (and
+ * inputs when p->warm_start).  vomt_batch_layout assigns consecutive 64-byte
+ * aligned offsets. */
+typedef struct {
+    int n;               /* grid side (>= 2) */
+    vomt_graph graph;    /* channel graph (host memory) */
+    double alpha;        /* > 0 */
+    double tau;          /* <= 0: p->tau if > 0, else Table 1's value for this n */
+    size_t offset;       /* first float of this instance in the arena */
+} vomt_instance;
+
+#define VOMT_ENGINE_BATCHED 3   /* reported in vomt_result.engine by vomt_solve_batched */
+
+/* Fill inst[q].offset for consecutive, 16-float aligned instance blocks and
+ * return the arena size in floats.  Host only. */
+int vomt_batch_layout(int count, vomt_instance *inst, size_t *total_floats);
+
+/* Solve every instance by the iteration of Section 7.2 in one persistent
+ * launch: thread blocks take instances from a device queue (largest first) and
+ * iterate each to its own stopping point (tolerance or p->max_iters, checked
+ * every p->check_every iterations, as in vomt_solve).  mu and nu follow the
+ * paper's rule per instance; p->mu, p->nu, p->engine and p->halo are ignored.
+ * When `stream` is not the legacy default stream (NULL), the launch (queue
+ * reset, kernel, status read-back) is captured into a CUDA graph on the first
+ * call and replayed by later calls with the same instances, arena and
+ * parameters.  results: host array of `count` (may be NULL).  Returns VOMT_OK,
+ * VOMT_NOT_CONVERGED if some instance hit the cap, or the first error (the
+ * message names the instance).  The context keeps the scratch (two iterates
+ * and b per instance) between calls. */
+int vomt_solve_batched(vomt_ctx *ctx, int count, const vomt_instance *inst, float *arena,
+                       const vomt_params *p, vomt_result *results, void *stream);
+
+/* Launch-shape tuner of the batched engine: runs the batch for sample_iters
+ * iterations (no tolerance) with 128, 256 and 512 threads per block, keeps the
+ * fastest for later vomt_solve_batched calls on ctx, and returns it in
+ * *best_threads and the three times (milliseconds) in ms[0..2] (either may be
+ * NULL).  Overwrites the arena's u, w, phi. */
+int vomt_batch_tune(vomt_ctx *ctx, int count, const vomt_instance *inst, float *arena,
+                    const vomt_params *p, int sample_iters, int *best_threads, double *ms);
+
+/* Set the batched engine's threads per block (128, 256 or 512; 0 restores the
+ * default, 256), e.g. from a tuning result cached by the caller. */
+int vomt_batch_set_threads(vomt_ctx *ctx, int threads);
+
+/* ------------------------------------------------------------------------ */
 /* Matrix OMT (Section 4, eq. (momt); algorithm of Section 7.3)               */
 /* ------------------------------------------------------------------------ */
 /* Densities are real symmetric k x k matrices per cell (k = 2 or 3), stored as

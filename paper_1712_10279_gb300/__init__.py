@@ -185,3 +185,88 @@ def history(device: int = 0):
     if rows:
         _native.check(lib.vomt_history(ctx, out.ctypes.data_as(_native.P_double), rows), ctx)
     return out
+
+
+class Batch:
+    """A set of independent vector-OMT problems laid out in one device arena.
+
+    problems: sequence of dicts with keys n, k, edges (node pairs), alpha, and
+    optionally cost and tau.  `rho0`, `rho1`: per-problem arrays [k, n, n] (numpy or
+    torch), copied into the arena.  After solve(), `u(q)`, `w(q)`, `phi(q)` are views
+    of problem q's results in the arena.
+    """
+
+    def __init__(self, problems, rho0, rho1, device=0):
+        import torch
+        self.problems = list(problems)
+        cnt = len(self.problems)
+        self.graphs = [_native.GraphArg(p["k"], p.get("edges", []), p.get("cost")) for p in self.problems]
+        self.inst = (_native.Instance * cnt)()
+        for q, (p, g) in enumerate(zip(self.problems, self.graphs)):
+            self.inst[q].n = int(p["n"])
+            self.inst[q].graph = g.g
+            self.inst[q].alpha = float(p.get("alpha", 1.0))
+            self.inst[q].tau = float(p["tau"]) if p.get("tau") else 0.0
+        total = ctypes.c_size_t()
+        _native.check(_native.load().vomt_batch_layout(cnt, self.inst, ctypes.byref(total)))
+        self.device = torch.device("cuda", device)
+        self.arena = torch.zeros(int(total.value), dtype=torch.float32, device=self.device)
+        for q, p in enumerate(self.problems):
+            k, n = int(p["k"]), int(p["n"])
+            nn = n * n
+            off = int(self.inst[q].offset)
+            r0 = torch.as_tensor(rho0[q], dtype=torch.float32).reshape(-1)
+            r1 = torch.as_tensor(rho1[q], dtype=torch.float32).reshape(-1)
+            self.arena[off:off + k * nn].copy_(r0)
+            self.arena[off + k * nn:off + 2 * k * nn].copy_(r1)
+        self.results = None
+
+    def _view(self, q, start, planes):
+        p = self.problems[q]
+        n = int(p["n"])
+        off = int(self.inst[q].offset) + start * n * n
+        return self.arena[off:off + planes * n * n].view(planes, n, n)
+
+    def u(self, q):
+        k = int(self.problems[q]["k"])
+        return self._view(q, 2 * k, 2 * k).view(2, k, *self._view(q, 0, 1).shape[1:])
+
+    def w(self, q):
+        k, l = int(self.problems[q]["k"]), self.graphs[q].tail.size
+        return self._view(q, 4 * k, l)
+
+    def phi(self, q):
+        k, l = int(self.problems[q]["k"]), self.graphs[q].tail.size
+        return self._view(q, 4 * k + l, k)
+
+    def solve(self, *, max_iters=2000, check_every=100, tol_gap=0.0, tol_res=0.0, tau=None, u_norm=U_L12,
+              w_norm=W_L1, warm_start=False, stream=None):
+        """One persistent launch over all problems (vomt_solve_batched).  Returns the
+        overall status; per-problem results are in self.results."""
+        import torch
+        p = _params(tau, None, None, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, warm_start, "batched")
+        res = (_native.Result * len(self.problems))()
+        st = (torch.cuda.current_stream(self.device) if stream is None else stream).cuda_stream
+        ctx = _native.context(self.device.index)
+        rc = _native.load().vomt_solve_batched(ctx, len(self.problems), self.inst, self.arena.data_ptr(),
+                                               ctypes.byref(p), res, ctypes.c_void_p(st))
+        _native.check(rc, ctx)
+        self.results = [r.as_dict() for r in res]
+        return rc
+
+    def tune(self, sample_iters=50, **kw):
+        """Time 128 / 256 / 512 threads per block on `sample_iters` iterations, keep the
+        fastest on this device's context; returns (best, {threads: ms})."""
+        p = _params(kw.get("tau"), None, None, kw.get("u_norm", U_L12), kw.get("w_norm", W_L1), sample_iters,
+                    sample_iters, 0.0, 0.0, False, "batched")
+        best = ctypes.c_int()
+        ms = (ctypes.c_double * 3)()
+        ctx = _native.context(self.device.index)
+        _native.check(_native.load().vomt_batch_tune(ctx, len(self.problems), self.inst, self.arena.data_ptr(),
+                                                     ctypes.byref(p), int(sample_iters), ctypes.byref(best), ms), ctx)
+        return best.value, dict(zip((128, 256, 512), list(ms)))
+
+
+def set_batch_threads(threads: int, device: int = 0):
+    ctx = _native.context(device)
+    _native.check(_native.load().vomt_batch_set_threads(ctx, int(threads)), ctx)

@@ -20,12 +20,16 @@ STATUS_NAMES = {
     -4: "GRAPH", -5: "L_KERNEL", -6: "STEP_CONDITION", -7: "NONFINITE", -8: "BARRIER_TIMEOUT",
     -9: "CUDA", -10: "TOO_LARGE",
 }
-ENGINES = {"auto": 0, "stream": 1, "resident": 2}
+ENGINES = {"auto": 0, "stream": 1, "resident": 2, "batched": 3}
 ENGINE_NAMES = {v: k for k, v in ENGINES.items()}
 
 
 class Graph(ctypes.Structure):
     _fields_ = [("k", c_int), ("n_edges", c_int), ("tail", P_int), ("head", P_int), ("cost", P_double)]
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("n", c_int), ("graph", Graph), ("alpha", c_double), ("tau", c_double), ("offset", ctypes.c_size_t)]
 
 
 class Params(ctypes.Structure):
@@ -66,6 +70,12 @@ SIGNATURES = {
                                 ctypes.POINTER(Params), c_void_p, c_void_p, c_void_p, ctypes.POINTER(Result),
                                 c_void_p]),
     "vomt_history": (c_int, [c_void_p, P_double, c_int]),
+    "vomt_batch_layout": (c_int, [c_int, ctypes.POINTER(Instance), ctypes.POINTER(ctypes.c_size_t)]),
+    "vomt_solve_batched": (c_int, [c_void_p, c_int, ctypes.POINTER(Instance), c_void_p, ctypes.POINTER(Params),
+                                   ctypes.POINTER(Result), c_void_p]),
+    "vomt_batch_tune": (c_int, [c_void_p, c_int, ctypes.POINTER(Instance), c_void_p, ctypes.POINTER(Params), c_int,
+                                P_int, P_double]),
+    "vomt_batch_set_threads": (c_int, [c_void_p, c_int]),
     "momt_step_sizes": (c_int, [c_int, c_int, c_int, c_void_p, c_double, P_double, P_double, P_double, P_double,
                                 P_double]),
     "momt_solve": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int, c_void_p, c_double,

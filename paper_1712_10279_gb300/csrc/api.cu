@@ -221,6 +221,7 @@ void vomt_destroy(vomt_ctx *c)
     if (c->dhist) cudaFree(c->dhist);
     if (c->stage) cudaFree(c->stage);
     if (c->mstage) cudaFree(c->mstage);
+    if (c->batch) batch_state_free(c->batch);
     if (c->rscratch) cudaFree(c->rscratch);
     delete c;
 }

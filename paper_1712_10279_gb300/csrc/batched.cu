@@ -1,0 +1,694 @@
+// Batched engine: many independent vector-OMT problems of mixed grid size,
+// channel count and channel graph in one persistent launch.
+//
+// Each thread block takes whole problems ("instances") from a device-side
+// queue, largest first, and runs the PDHG iteration of Section 7.2 on each one
+// to its own stopping point (per-instance tolerance and iteration cap) before
+// taking the next.  Instances are independent, so a block needs no exchange
+// with other blocks: one block barrier per iteration (the fused stencil
+// recomputes the neighbouring shrinks, as the streaming engine does) and a
+// block-level FP64 reduction per convergence check.  Iterates ping-pong between
+// two buffers of a scratch arena in HBM; L1 and L2 keep the working set of an
+// instance close.  The queue order balances the load: the longest instances
+// start first and the small ones fill in at the end.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+#include "pdhg_device.cuh"
+
+namespace vomt {
+namespace {
+
+using namespace dev;
+
+constexpr int BK = 8;                      // channels per instance (vector OMT, k <= 8)
+constexpr int BL = BK * (BK - 1) / 2;
+
+struct InstDev {
+    int n, k, l, pad;
+    float mu, nu, tau, alpha, ih;
+    float wc[BK], we[BL];
+    float G[BL][BK];
+    float Dv[BK][BL];
+    size_t o_rho0, o_rho1, o_u, o_w, o_phi;   // offsets (floats) into the caller's arena
+    size_t o_b, o_s[2];                       // offsets (floats) into the scratch arena
+    double mu_d, nu_d, tau_d;
+};
+
+struct InstStatus {
+    int iter, checks, error, stop;
+    double met[NMET];
+};
+
+struct BatchArgs {
+    const InstDev *inst;
+    const int *order;          // queue order (largest first)
+    int count;
+    int un, wn, max_iters, check_every, warm;
+    double tol_gap, tol_res;
+    float *arena;
+    float *scratch;
+    InstStatus *status;
+    int *queue;                // next queue position
+};
+
+template <int K>
+struct BLK {
+    static constexpr int v = K * (K - 1) / 2 > 0 ? K * (K - 1) / 2 : 1;
+};
+
+// One fused iteration at point (i, j) of one instance (the streaming engine's
+// formulation): u' at (i,j), (i-1,j), (i,j-1), w' at (i,j), phi' at (i,j).
+template <int K>
+__device__ __forceinline__ void step_point(const InstDev &I, int i, int j, const float *__restrict__ S0,
+                                           float *__restrict__ S1, const float *__restrict__ b, int un, int wn)
+{
+    constexpr int LK = BLK<K>::v;
+    const int n = I.n, l = I.l;
+    const size_t nn = (size_t)n * n, p = (size_t)j * n + i;
+    const float *phi = S0, *ux = S0 + (size_t)K * nn, *uy = S0 + (size_t)2 * K * nn, *w = S0 + (size_t)3 * K * nn;
+    const bool hR = i < n - 1, hU = j < n - 1, hL = i > 0, hD = j > 0;
+    const float mu = I.mu, muih = I.mu * I.ih, ih = I.ih;
+    float pc[K], vx[K], vy[K], ux0[K], uy0[K], lx[K], ly[K], lx0[K], dx[K], dy[K], dy0[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        const float *P = phi + c * nn + p;
+        pc[c] = P[0];
+        const float pr = hR ? P[1] : 0.0f, pu = hU ? P[n] : 0.0f;
+        const float pl = hL ? P[-1] : 0.0f, plu = (hL && hU) ? P[n - 1] : 0.0f;
+        const float pd = hD ? P[-n] : 0.0f, prd = (hR && hD) ? P[1 - n] : 0.0f;
+        ux0[c] = ux[c * nn + p];
+        uy0[c] = uy[c * nn + p];
+        vx[c] = ux0[c] + (hR ? muih * (pr - pc[c]) : 0.0f);
+        vy[c] = uy0[c] + (hU ? muih * (pu - pc[c]) : 0.0f);
+        lx0[c] = hL ? ux[c * nn + p - 1] : 0.0f;
+        const float ly0 = hL ? uy[c * nn + p - 1] : 0.0f;
+        lx[c] = lx0[c] + (hL ? muih * (pc[c] - pl) : 0.0f);
+        ly[c] = ly0 + ((hL && hU) ? muih * (plu - pl) : 0.0f);
+        const float dx0 = hD ? ux[c * nn + p - n] : 0.0f;
+        dy0[c] = hD ? uy[c * nn + p - n] : 0.0f;
+        dx[c] = dx0 + ((hR && hD) ? muih * (prd - pd) : 0.0f);
+        dy[c] = dy0[c] + (hD ? muih * (pc[c] - pd) : 0.0f);
+    }
+    shrink_u<K>(vx, vy, mu, un, I.wc);
+    shrink_u<K>(lx, ly, mu, un, I.wc);
+    shrink_u<K>(dx, dy, mu, un, I.wc);
+    float w0[LK], wx[LK];
+#pragma unroll
+    for (int e = 0; e < LK; ++e) {
+        float ge = 0.0f;
+#pragma unroll
+        for (int c = 0; c < K; ++c) ge += I.G[e][c] * pc[c];
+        w0[e] = (e < l) ? w[e * nn + p] : 0.0f;
+        wx[e] = (e < l) ? w0[e] + I.nu * ge : 0.0f;
+    }
+    shrink_w<LK>(wx, l, I.alpha * I.nu, wn, I.we);
+    float *ophi = S1, *oux = S1 + (size_t)K * nn, *ouy = S1 + (size_t)2 * K * nn, *ow = S1 + (size_t)3 * K * nn;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        const float bxl = hL ? 2.0f * lx[c] - lx0[c] : 0.0f;
+        const float byd = hD ? 2.0f * dy[c] - dy0[c] : 0.0f;
+        float r = ih * (((2.0f * vx[c] - ux0[c]) - bxl) + ((2.0f * vy[c] - uy0[c]) - byd)) + b[c * nn + p];
+#pragma unroll
+        for (int e = 0; e < LK; ++e) r -= I.Dv[c][e] * (2.0f * wx[e] - w0[e]);
+        ophi[c * nn + p] = pc[c] + I.tau * r;
+        oux[c * nn + p] = vx[c];
+        ouy[c * nn + p] = vy[c];
+    }
+#pragma unroll
+    for (int e = 0; e < LK; ++e)
+        if (e < l) ow[e * nn + p] = wx[e];
+}
+
+// FP64 metric terms of point (i, j) for state S1 (after the iteration) and S0
+// (before), accumulated into v (see RED_*).
+template <int K>
+__device__ __forceinline__ void metric_point(const InstDev &I, int i, int j, const float *__restrict__ S1,
+                                             const float *__restrict__ S0, const float *__restrict__ b, int un,
+                                             int wn, double (&v)[NRED])
+{
+    constexpr int LK = BLK<K>::v;
+    const int n = I.n, l = I.l;
+    const size_t nn = (size_t)n * n, p = (size_t)j * n + i;
+    const bool hR = i < n - 1, hU = j < n - 1, hL = i > 0, hD = j > 0;
+    const float ih = I.ih;
+    const double dih = (double)(n - 1);
+    float ph[K], dph[K], ddiv[K];
+    double rdiv[K];
+    float nu_pt = 0.0f, dn_u = 0.0f;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        const size_t q = c * nn + p;
+        const float *cux = S1 + (size_t)K * nn, *cuy = S1 + (size_t)2 * K * nn;
+        const float *pux = S0 + (size_t)K * nn, *puy = S0 + (size_t)2 * K * nn;
+        const float uxc = cux[q], uyc = cuy[q], bc = b[q], wgt = I.wc[c];
+        ph[c] = S1[q];
+        dph[c] = ph[c] - S0[q];
+        const float xl = hL ? cux[q - 1] : 0.0f, yd = hD ? cuy[q - n] : 0.0f;
+        rdiv[c] = dih * (((double)uxc - (double)xl) + ((double)uyc - (double)yd)) + (double)bc;
+        const float dux = uxc - pux[q], duy = uyc - puy[q];
+        const float dxl = hL ? cux[q - 1] - pux[q - 1] : 0.0f;
+        const float dyd = hD ? cuy[q - n] - puy[q - n] : 0.0f;
+        ddiv[c] = ih * ((dux - dxl) + (duy - dyd));
+        v[RED_DU] += (double)(wgt * (dux * dux + duy * duy));
+        v[RED_DP] += (double)(wgt * dph[c] * dph[c]);
+        v[RED_D] += (double)wgt * (double)ph[c] * (double)bc;
+        v[RED_BB] += (double)(wgt * bc * bc);
+        const float gx = hR ? ih * (S1[q + 1] - ph[c]) : 0.0f;
+        const float gy = hU ? ih * (S1[q + n] - ph[c]) : 0.0f;
+        if (un == VOMT_U_L12) {
+            nu_pt += sqrtf(uxc * uxc + uyc * uyc);
+            dn_u = fmaxf(dn_u, sqrtf(gx * gx + gy * gy));
+        } else if (un == VOMT_U_L2) {
+            nu_pt += wgt * (uxc * uxc + uyc * uyc);
+            dn_u += wgt * (gx * gx + gy * gy);
+        } else {
+            nu_pt += wgt * (fabsf(uxc) + fabsf(uyc));
+            dn_u = fmaxf(dn_u, fmaxf(fabsf(gx), fabsf(gy)));
+        }
+    }
+    if (un == VOMT_U_L2) { nu_pt = sqrtf(nu_pt); dn_u = sqrtf(dn_u); }
+    float nw_pt = 0.0f, dn_w = 0.0f;
+    const float *cw = S1 + (size_t)3 * K * nn, *pw = S0 + (size_t)3 * K * nn;
+#pragma unroll
+    for (int e = 0; e < LK; ++e) {
+        if (e < l) {
+            const size_t q = e * nn + p;
+            const float we = cw[q], dwe = we - pw[q], wgt = I.we[e];
+            v[RED_DW] += (double)(wgt * dwe * dwe);
+            float ge = 0.0f;
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                ge += I.G[e][c] * ph[c];
+                rdiv[c] -= (double)I.Dv[c][e] * (double)we;
+                ddiv[c] -= I.Dv[c][e] * dwe;
+            }
+            if (wn == VOMT_W_L1) { nw_pt += wgt * fabsf(we); dn_w = fmaxf(dn_w, fabsf(ge)); }
+            else { nw_pt += wgt * we * we; dn_w += wgt * ge * ge; }
+        }
+    }
+    if (wn == VOMT_W_L2) { nw_pt = sqrtf(nw_pt); dn_w = sqrtf(dn_w); }
+    v[RED_P] += (double)nu_pt + (double)I.alpha * (double)nw_pt;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        v[RED_RR] += (double)I.wc[c] * rdiv[c] * rdiv[c];
+        v[RED_X] += (double)(I.wc[c] * dph[c] * ddiv[c]);
+    }
+    float di = fmaxf(dn_u - 1.0f, 0.0f);
+    if (l > 0) di = fmaxf(di, dn_w - I.alpha);
+    v[RED_MAX] = fmax(v[RED_MAX], (double)di);
+}
+
+// block-wide fixed-order reduction of v; the result is valid in thread 0
+__device__ __forceinline__ void block_reduce(double (&v)[NRED], double *red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < NRED; ++q) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double o = __shfl_down_sync(0xffffffffu, v[q], off);
+            v[q] = (q == RED_MAX) ? fmax(v[q], o) : v[q] + o;
+        }
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NRED; ++q) red[wid * NRED + q] = v[q];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < nw; ++w)
+#pragma unroll
+            for (int q = 0; q < NRED; ++q) v[q] = (q == RED_MAX) ? fmax(v[q], red[w * NRED + q]) : v[q] + red[w * NRED + q];
+}
+
+// Solve one instance with the whole block.  I lives in shared memory.
+template <int K>
+__device__ void solve_one(const InstDev &I, const BatchArgs &a, InstStatus *st, double *red, int *flag)
+{
+    const int n = I.n, l = I.l;
+    const int np = n * n;
+    const size_t nn = (size_t)np;
+    float *b = a.scratch + I.o_b;
+    float *S[2] = {a.scratch + I.o_s[0], a.scratch + I.o_s[1]};
+    const float *r0 = a.arena + I.o_rho0, *r1 = a.arena + I.o_rho1;
+    float *u = a.arena + I.o_u, *w = a.arena + I.o_w, *phi = a.arena + I.o_phi;
+    // b = rho1 - rho0; iterate 0 from zero or from the caller's arrays (ghost cells zeroed)
+    for (int q = threadIdx.x; q < np; q += blockDim.x) {
+        const int i = q % n, j = q / n;
+        for (int c = 0; c < K; ++c) {
+            b[c * nn + q] = r1[c * nn + q] - r0[c * nn + q];
+            S[0][c * nn + q] = a.warm ? phi[c * nn + q] : 0.0f;
+            S[0][(K + c) * nn + q] = (a.warm && i < n - 1) ? u[c * nn + q] : 0.0f;
+            S[0][(2 * K + c) * nn + q] = (a.warm && j < n - 1) ? u[(K + c) * nn + q] : 0.0f;
+        }
+        for (int e = 0; e < l; ++e) S[0][(3 * K + e) * nn + q] = a.warm ? w[e * nn + q] : 0.0f;
+    }
+    __syncthreads();
+    const int T = a.max_iters, CE = a.check_every;
+    int t = 0, checks = 0;
+    bool stop = false;
+    while (!stop) {
+        const bool do_step = t < T;
+        if (do_step) {
+            ++t;
+            const float *in = S[(t - 1) & 1];
+            float *out = S[t & 1];
+            for (int q = threadIdx.x; q < np; q += blockDim.x) step_point<K>(I, q % n, q / n, in, out, b, a.un, a.wn);
+            __syncthreads();
+        }
+        if (!do_step || t % CE == 0 || t == T) {
+            // convergence check on the iterate after iteration t
+            double v[NRED];
+#pragma unroll
+            for (int q = 0; q < NRED; ++q) v[q] = 0.0;
+            const float *cur = S[t & 1], *prv = t > 0 ? S[(t - 1) & 1] : S[t & 1];
+            for (int q = threadIdx.x; q < np; q += blockDim.x) metric_point<K>(I, q % n, q / n, cur, prv, b, a.un, a.wn, v);
+            block_reduce(v, red);
+            if (threadIdx.x == 0) {
+                double m[NMET];
+                m[0] = v[RED_P];
+                m[1] = v[RED_D];
+                m[2] = fabs(m[0] - m[1]) / fmax(fabs(m[0]), 1e-300);
+                m[3] = sqrt(v[RED_RR]) / (v[RED_BB] > 0.0 ? sqrt(v[RED_BB]) : 1.0);
+                m[4] = v[RED_DU] / I.mu_d + (l > 0 ? v[RED_DW] / I.nu_d : 0.0) + v[RED_DP] / I.tau_d - 2.0 * v[RED_X];
+                m[5] = v[RED_MAX];
+                m[6] = (double)t;
+                bool finite = true;
+                for (int q = 0; q < 6; ++q) finite = finite && isfinite(m[q]);
+                const bool conv = a.tol_gap > 0.0 && m[2] <= a.tol_gap && m[3] <= a.tol_res;
+                m[7] = conv ? 1.0 : 0.0;
+                for (int q = 0; q < NMET; ++q) st->met[q] = m[q];
+                st->iter = t;
+                st->checks = ++checks;
+                if (!finite) st->error = VOMT_ERR_NONFINITE;
+                const bool s_ = conv || !finite || t >= T;
+                st->stop = s_ ? 1 : 0;
+                *flag = s_ ? 1 : 0;
+            }
+            __syncthreads();
+            stop = *flag != 0;
+            __syncthreads();
+        }
+    }
+    // final iterate to the caller's arrays
+    const float *fin = S[t & 1];
+    for (int q = threadIdx.x; q < np; q += blockDim.x) {
+        for (int c = 0; c < K; ++c) {
+            phi[c * nn + q] = fin[c * nn + q];
+            u[c * nn + q] = fin[(K + c) * nn + q];
+            u[(K + c) * nn + q] = fin[(2 * K + c) * nn + q];
+        }
+        for (int e = 0; e < l; ++e) w[e * nn + q] = fin[(3 * K + e) * nn + q];
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(512) k_batch(BatchArgs a)
+{
+    __shared__ InstDev I;
+    __shared__ double red[32 * NRED];
+    __shared__ int slot, flag;
+    for (;;) {
+        if (threadIdx.x == 0) slot = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int s = slot;
+        if (s >= a.count) break;
+        const int idx = a.order[s];
+        // copy the instance record to shared memory (uniform, read by every point)
+        const int words = (int)(sizeof(InstDev) / 4);
+        for (int q = threadIdx.x; q < words; q += blockDim.x) ((int *)&I)[q] = ((const int *)&a.inst[idx])[q];
+        __syncthreads();
+        InstStatus *st = a.status + idx;
+        switch (I.k) {
+            case 1: solve_one<1>(I, a, st, red, &flag); break;
+            case 2: solve_one<2>(I, a, st, red, &flag); break;
+            case 3: solve_one<3>(I, a, st, red, &flag); break;
+            case 4: solve_one<4>(I, a, st, red, &flag); break;
+            case 5: solve_one<5>(I, a, st, red, &flag); break;
+            case 6: solve_one<6>(I, a, st, red, &flag); break;
+            case 7: solve_one<7>(I, a, st, red, &flag); break;
+            default: solve_one<8>(I, a, st, red, &flag); break;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+}  // namespace vomt
+
+namespace vomt {
+namespace {
+
+// per instance (one block each): sum rho0, sum rho1, min rho0, min rho1, non-finite count
+__global__ void k_batch_validate(const InstDev *inst, const float *arena, double *out)
+{
+    const InstDev &I = inst[blockIdx.x];
+    const size_t cnt = (size_t)I.k * I.n * I.n;
+    const float *r0 = arena + I.o_rho0, *r1 = arena + I.o_rho1;
+    double s0 = 0.0, s1 = 0.0, m0 = 1e300, m1 = 1e300, bad = 0.0;
+    for (size_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const float a = r0[q], c = r1[q];
+        if (!isfinite(a) || !isfinite(c)) { bad += 1.0; continue; }
+        s0 += a; s1 += c;
+        m0 = fmin(m0, (double)a);
+        m1 = fmin(m1, (double)c);
+    }
+    __shared__ double sh[5][256];
+    sh[0][threadIdx.x] = s0; sh[1][threadIdx.x] = s1; sh[2][threadIdx.x] = m0; sh[3][threadIdx.x] = m1;
+    sh[4][threadIdx.x] = bad;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            const int o = threadIdx.x + off;
+            sh[0][threadIdx.x] += sh[0][o];
+            sh[1][threadIdx.x] += sh[1][o];
+            sh[2][threadIdx.x] = fmin(sh[2][threadIdx.x], sh[2][o]);
+            sh[3][threadIdx.x] = fmin(sh[3][threadIdx.x], sh[3][o]);
+            sh[4][threadIdx.x] += sh[4][o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) out[blockIdx.x * 5 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+}  // namespace
+
+// Per-context state of the batched engine (device tables, scratch, captured graph).
+struct BatchState {
+    InstDev *dinst = nullptr;
+    int *dorder = nullptr, *dqueue = nullptr;
+    InstStatus *dstatus = nullptr, *hstatus = nullptr;
+    double *dval = nullptr;
+    int cap = 0;
+    float *scratch = nullptr;
+    size_t scratch_floats = 0;
+    cudaGraphExec_t exec = nullptr;
+    // what the captured graph was built for
+    int g_count = -1, g_threads = 0, g_blocks = 0;
+    const float *g_arena = nullptr;
+    cudaStream_t g_stream = nullptr;
+    BatchArgs g_args;
+    int tuned_threads = 0;
+};
+
+void batch_state_free(BatchState *b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    cudaFree(b->dinst);
+    cudaFree(b->dorder);
+    cudaFree(b->dqueue);
+    cudaFree(b->dstatus);
+    cudaFree(b->dval);
+    cudaFree(b->scratch);
+    if (b->hstatus) cudaFreeHost(b->hstatus);
+    delete b;
+}
+
+static int batch_reserve(vomt_ctx *ctx, BatchState *b, int count)
+{
+    if (b->cap >= count) return VOMT_OK;
+    cudaFree(b->dinst); cudaFree(b->dorder); cudaFree(b->dqueue); cudaFree(b->dstatus); cudaFree(b->dval);
+    if (b->hstatus) cudaFreeHost(b->hstatus);
+    b->dinst = nullptr; b->dorder = b->dqueue = nullptr; b->dstatus = b->hstatus = nullptr; b->dval = nullptr;
+    b->cap = 0;
+    cudaError_t e = cudaMalloc(&b->dinst, sizeof(InstDev) * count);
+    if (e == cudaSuccess) e = cudaMalloc(&b->dorder, sizeof(int) * count);
+    if (e == cudaSuccess) e = cudaMalloc(&b->dqueue, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->dstatus, sizeof(InstStatus) * count);
+    if (e == cudaSuccess) e = cudaMalloc(&b->dval, sizeof(double) * 5 * count);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->hstatus, sizeof(InstStatus) * count);
+    if (e != cudaSuccess) return set_cuda_error(ctx, e, "batch tables");
+    b->cap = count;
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    b->g_count = -1;
+    return VOMT_OK;
+}
+
+}  // namespace vomt
+
+using namespace vomt;
+
+static double table1_tau(int n) { return n <= 64 ? 1.0 : 3.0; }
+
+extern "C" int vomt_batch_layout(int count, vomt_instance *inst, size_t *total_floats)
+{
+    if (count < 0 || (count > 0 && !inst)) return VOMT_ERR_BAD_ARG;
+    size_t off = 0;
+    for (int q = 0; q < count; ++q) {
+        const int n = inst[q].n, k = inst[q].graph.k, l = inst[q].graph.n_edges;
+        if (n < 2 || k < 1 || k > KMAX || l < 0 || l > LMAX) return VOMT_ERR_BAD_ARG;
+        inst[q].offset = off;
+        off += (size_t)(5 * k + l) * n * n;
+        off = (off + 15) & ~(size_t)15;
+    }
+    if (total_floats) *total_floats = off;
+    return VOMT_OK;
+}
+
+static int batch_prepare(vomt_ctx *ctx, int count, const vomt_instance *inst, const vomt_params &p,
+                         std::vector<InstDev> &hinst, std::vector<int> &order, size_t *scratch_floats, int *bad_index)
+{
+    hinst.assign(count, InstDev());
+    order.resize(count);
+    size_t soff = 0;
+    std::vector<double> cost(count);
+    for (int q = 0; q < count; ++q) {
+        *bad_index = q;
+        const vomt_instance &in = inst[q];
+        const int n = in.n;
+        if (n < 2 || n > 32768) return fail(ctx, VOMT_ERR_BAD_ARG, "instance: n must be in [2, 32768]");
+        if (!(in.alpha > 0.0) || !isfinite(in.alpha)) return fail(ctx, VOMT_ERR_BAD_ARG, "instance: alpha must be positive");
+        GraphDev gd;
+        int rc = graph_to_dev(&in.graph, &gd, &ctx->err);
+        if (rc) return rc;
+        OpDev op;
+        graph_to_op(gd, &op);
+        InstDev &I = hinst[q];
+        memset(&I, 0, sizeof I);
+        const int k = gd.k, l = gd.l;
+        const size_t nn = (size_t)n * n;
+        const double tau = in.tau > 0.0 ? in.tau : (p.tau > 0.0 ? p.tau : table1_tau(n));
+        const double n1 = (double)(n - 1), lmax = graph_lmax(gd, in.graph.cost);
+        const double mu = l > 0 ? 1.0 / (32.0 * tau * n1 * n1) : 1.0 / (16.0 * tau * n1 * n1);
+        const double nu = l > 0 ? 1.0 / (4.0 * tau * lmax) : 1.0;
+        I.n = n; I.k = k; I.l = l;
+        I.mu = (float)mu; I.nu = (float)nu; I.tau = (float)tau; I.alpha = (float)in.alpha; I.ih = (float)n1;
+        I.mu_d = mu; I.nu_d = nu; I.tau_d = tau;
+        memcpy(I.wc, op.wc, sizeof I.wc);
+        memcpy(I.we, op.we, sizeof I.we);
+        memcpy(I.G, op.G, sizeof I.G);
+        memcpy(I.Dv, op.Dv, sizeof I.Dv);
+        I.o_rho0 = in.offset;
+        I.o_rho1 = in.offset + (size_t)k * nn;
+        I.o_u = in.offset + (size_t)2 * k * nn;
+        I.o_w = in.offset + (size_t)4 * k * nn;
+        I.o_phi = in.offset + (size_t)(4 * k + l) * nn;
+        I.o_b = soff;
+        I.o_s[0] = soff + (size_t)k * nn;
+        I.o_s[1] = I.o_s[0] + (size_t)(3 * k + l) * nn;
+        soff += (size_t)(7 * k + 2 * l) * nn;
+        soff = (soff + 15) & ~(size_t)15;
+        cost[q] = (double)nn * (7 * k + 2 * l);
+        order[q] = q;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    *scratch_floats = soff;
+    *bad_index = -1;
+    return VOMT_OK;
+}
+
+extern "C" int vomt_solve_batched(vomt_ctx *ctx, int count, const vomt_instance *inst, float *arena,
+                                  const vomt_params *pin, vomt_result *results, void *stream)
+{
+    try {
+        if (!ctx) return VOMT_ERR_BAD_ARG;
+        ctx->err.clear();
+        if (count < 1 || !inst || !arena) return fail(ctx, VOMT_ERR_BAD_ARG, "need count >= 1, instances and an arena");
+        vomt_params p;
+        vomt_default_params(&p);
+        if (pin) p = *pin;
+        if (p.max_iters < 0 || p.check_every < 1) return fail(ctx, VOMT_ERR_BAD_ARG, "max_iters >= 0, check_every >= 1");
+        if (p.u_norm < 0 || p.u_norm > 2 || p.w_norm < 0 || p.w_norm > 1) return fail(ctx, VOMT_ERR_BAD_ARG, "bad norm code");
+        cudaStream_t st = (cudaStream_t)stream;
+        cudaError_t e = cudaSetDevice(ctx->device);
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "cudaSetDevice");
+        if (!ctx->batch) ctx->batch = new BatchState();
+        BatchState *b = ctx->batch;
+        ctx->launches = 0;
+        std::vector<InstDev> hinst;
+        std::vector<int> order;
+        size_t sfl = 0;
+        int bad = -1;
+        int rc = batch_prepare(ctx, count, inst, p, hinst, order, &sfl, &bad);
+        if (rc) {
+            char buf[64];
+            snprintf(buf, sizeof buf, " (instance %d)", bad);
+            ctx->err += buf;
+            return rc;
+        }
+        rc = batch_reserve(ctx, b, count);
+        if (rc) return rc;
+        if (b->scratch_floats < sfl) {
+            cudaFree(b->scratch);
+            b->scratch = nullptr;
+            b->scratch_floats = 0;
+            e = cudaMalloc(&b->scratch, sizeof(float) * sfl);
+            if (e != cudaSuccess) return set_cuda_error(ctx, e, "batch scratch");
+            b->scratch_floats = sfl;
+            if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+        }
+        e = cudaMemcpyAsync(b->dinst, hinst.data(), sizeof(InstDev) * count, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b->dorder, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "batch table upload");
+        // density checks, one block per instance
+        k_batch_validate<<<count, 256, 0, st>>>(b->dinst, arena, b->dval);
+        ++ctx->launches;
+        std::vector<double> hv((size_t)5 * count);
+        e = cudaMemcpyAsync(hv.data(), b->dval, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "batch validate");
+        for (int q = 0; q < count; ++q) {
+            const double *h = &hv[(size_t)5 * q];
+            char buf[96];
+            int code = 0;
+            if (h[4] > 0.0) { code = VOMT_ERR_NONFINITE; snprintf(buf, sizeof buf, "instance %d: NaN or Inf density", q); }
+            else if (h[2] < 0.0 || h[3] < 0.0) { code = VOMT_ERR_NEGATIVE_DENSITY; snprintf(buf, sizeof buf, "instance %d: negative density", q); }
+            else if (fabs(h[0] - h[1]) > 1e-5 * fmax(fabs(h[0]), fabs(h[1]))) { code = VOMT_ERR_MASS_MISMATCH; snprintf(buf, sizeof buf, "instance %d: different total mass", q); }
+            if (code) return fail(ctx, code, buf);
+        }
+        // launch shape: the tuned block size, as many resident blocks as fit, at most one per instance
+        const int threads = b->tuned_threads > 0 ? b->tuned_threads : 256;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, threads, 0);
+        if (e != cudaSuccess || per_sm < 1) return set_cuda_error(ctx, e == cudaSuccess ? cudaErrorInvalidConfiguration : e, "batch occupancy");
+        const int blocks = std::min(count, per_sm * ctx->sm_count);
+        BatchArgs a;
+        memset(&a, 0, sizeof a);
+        a.inst = b->dinst;
+        a.order = b->dorder;
+        a.count = count;
+        a.un = p.u_norm;
+        a.wn = p.w_norm;
+        a.max_iters = p.max_iters;
+        a.check_every = p.check_every;
+        a.warm = p.warm_start;
+        a.tol_gap = p.tol_gap;
+        a.tol_res = p.tol_res;
+        a.arena = arena;
+        a.scratch = b->scratch;
+        a.status = b->dstatus;
+        a.queue = b->dqueue;
+        auto enqueue = [&]() -> cudaError_t {
+            cudaError_t r = cudaMemsetAsync(b->dqueue, 0, sizeof(int), st);
+            if (r == cudaSuccess) r = cudaMemsetAsync(b->dstatus, 0, sizeof(InstStatus) * count, st);
+            if (r != cudaSuccess) return r;
+            k_batch<<<blocks, threads, 0, st>>>(a);
+            r = cudaGetLastError();
+            if (r == cudaSuccess) r = cudaMemcpyAsync(b->hstatus, b->dstatus, sizeof(InstStatus) * count, cudaMemcpyDeviceToHost, st);
+            return r;
+        };
+        if (st != nullptr) {
+            // one captured graph per (tables, arena, launch shape, parameters); replayed while they repeat
+            const bool same = b->exec && b->g_count == count && b->g_threads == threads && b->g_blocks == blocks &&
+                              b->g_arena == arena && b->g_stream == st && memcmp(&b->g_args, &a, sizeof a) == 0;
+            if (!same) {
+                if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+                cudaGraph_t graph = nullptr;
+                e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    cudaError_t r = enqueue();
+                    e = cudaStreamEndCapture(st, &graph);
+                    if (r != cudaSuccess) e = r;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+                if (e != cudaSuccess) return set_cuda_error(ctx, e, "batch graph capture");
+                b->g_count = count; b->g_threads = threads; b->g_blocks = blocks; b->g_arena = arena; b->g_stream = st;
+                b->g_args = a;
+            }
+            e = cudaGraphLaunch(b->exec, st);
+        } else {
+            e = enqueue();
+        }
+        ++ctx->launches;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "batch solve");
+        int status = VOMT_OK;
+        for (int q = 0; q < count; ++q) {
+            const InstStatus &h = b->hstatus[q];
+            int s_ = VOMT_OK;
+            if (h.error) s_ = h.error;
+            else if (p.tol_gap > 0.0 && h.met[7] == 0.0) s_ = VOMT_NOT_CONVERGED;
+            if (s_ < 0 && status >= 0) status = s_;
+            else if (s_ == VOMT_NOT_CONVERGED && status == VOMT_OK) status = s_;
+            if (results) {
+                vomt_result &r = results[q];
+                r.primal = h.met[0]; r.dual = h.met[1]; r.rel_gap = h.met[2]; r.rel_res = h.met[3];
+                r.fp_resid = h.met[4]; r.dual_infeas = h.met[5];
+                r.mu = hinst[q].mu_d; r.nu = hinst[q].nu_d; r.tau = hinst[q].tau_d;
+                r.iters = h.iter; r.status = s_; r.engine = VOMT_ENGINE_BATCHED; r.checks = h.checks;
+                r.launches = ctx->launches;
+            }
+        }
+        if (status < 0) ctx->err = "an instance produced a non-finite iterate";
+        return status;
+    } catch (...) {
+        return fail(ctx, VOMT_ERR_BAD_ARG, "internal exception");
+    }
+}
+
+extern "C" int vomt_batch_tune(vomt_ctx *ctx, int count, const vomt_instance *inst, float *arena,
+                               const vomt_params *pin, int sample_iters, int *best_threads, double *ms)
+{
+    if (!ctx || sample_iters < 1) return VOMT_ERR_BAD_ARG;
+    vomt_params p;
+    vomt_default_params(&p);
+    if (pin) p = *pin;
+    p.max_iters = sample_iters;
+    p.check_every = sample_iters;
+    p.tol_gap = p.tol_res = 0.0;
+    p.warm_start = 0;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return set_cuda_error(ctx, e, "cudaSetDevice");
+    if (!ctx->batch) ctx->batch = new BatchState();
+    const int cands[3] = {128, 256, 512};
+    double best = 1e300;
+    int pick = 256;
+    for (int c = 0; c < 3; ++c) {
+        ctx->batch->tuned_threads = cands[c];
+        // one untimed pass (table upload, graph capture), then a timed pass
+        int rc = vomt_solve_batched(ctx, count, inst, arena, &p, nullptr, nullptr);
+        if (rc < 0) return rc;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, nullptr);
+        rc = vomt_solve_batched(ctx, count, inst, arena, &p, nullptr, nullptr);
+        cudaEventRecord(e1, nullptr);
+        cudaEventSynchronize(e1);
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc < 0) return rc;
+        if (ms) ms[c] = t;
+        if (t < best) { best = t; pick = cands[c]; }
+    }
+    ctx->batch->tuned_threads = pick;
+    if (best_threads) *best_threads = pick;
+    return VOMT_OK;
+}
+
+extern "C" int vomt_batch_set_threads(vomt_ctx *ctx, int threads)
+{
+    if (!ctx || !(threads == 0 || threads == 128 || threads == 256 || threads == 512)) return VOMT_ERR_BAD_ARG;
+    if (!ctx->batch) ctx->batch = new BatchState();
+    ctx->batch->tuned_threads = threads;
+    return VOMT_OK;
+}

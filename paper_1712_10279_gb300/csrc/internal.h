@@ -91,6 +91,11 @@ int quantum_to_op(int k, int N, const double *L, OpDev *op, double *lmax, double
 
 }  // namespace vomt
 
+namespace vomt {
+struct BatchState;
+void batch_state_free(BatchState *b);
+}  // namespace vomt
+
 // The opaque context.
 struct vomt_ctx {
     int device = 0;
@@ -114,6 +119,8 @@ struct vomt_ctx {
     // matrix-OMT compact staging (device)
     float *mstage = nullptr;
     size_t mstage_bytes = 0;
+    // batched engine (tables, scratch, captured graph)
+    vomt::BatchState *batch = nullptr;
     // resident-engine scratch
     void *rscratch = nullptr;
     size_t rscratch_bytes = 0;
