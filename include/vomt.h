@@ -165,6 +165,37 @@ int vomt_solve_host(vomt_ctx *ctx, int n, const float *rho0, const float *rho1,
 int vomt_history(vomt_ctx *ctx, double *out, int cap);
 
 /* ------------------------------------------------------------------------ */
+/* Gradients of the transport cost                                            */
+/* ------------------------------------------------------------------------ */
+
+/* Envelope gradient of V (the optimal value of eq. (vomt) / eq. (vomt-dual))
+ * for `batch` problems of one shape: the dual is a maximum over a feasible set
+ * independent of the densities of <phi, rho1 - rho0>, so dV/drho1 = phi* and
+ * dV/drho0 = -phi*, with the constant the dual leaves free fixed by making phi*
+ * zero-mean over all cells and channels; the primal is linear in alpha, so
+ * dV/dalpha = sum_ij ||w*_ij||_w.  phi: device [batch][k][n][n], w: device
+ * [batch][l][n][n] (a converged iterate, e.g. from vomt_solve).  grad_scale:
+ * device [batch] factors (the upstream gradient) or NULL for 1.  Outputs (any
+ * may be NULL): d_rho0, d_rho1 device [batch][k][n][n], d_alpha device [batch].
+ * Asynchronous on `stream`.  Errors: BAD_ARG, CUDA. */
+int vomt_backward(vomt_ctx *ctx, int batch, int n, int k, int n_edges, int w_norm, const float *phi,
+                  const float *w, const float *grad_scale, float *d_rho0, float *d_rho1, float *d_alpha,
+                  void *stream);
+
+/* Unrolled gradient: J_T = P(u^T, w^T), the primal objective after T
+ * iterations of Section 7.2 from the zero iterate (tau, mu, nu, norms from p;
+ * p->u_norm must be VOMT_U_L12), and its exact gradient by reverse mode through
+ * the T iterations.  The forward pass keeps the iterate every `ckpt`
+ * iterations; the reverse pass recomputes each segment from its checkpoint.
+ * rho0, rho1: device [k][n][n].  Outputs: d_rho0, d_rho1 device [k][n][n]
+ * (either may be NULL), *d_alpha and *J host (either may be NULL); every
+ * derivative is multiplied by `scale`.  Returns after the work finished.
+ * Errors: as vomt_solve. */
+int vomt_unrolled_grad(vomt_ctx *ctx, int n, const float *rho0, const float *rho1, const vomt_graph *g,
+                       double alpha, const vomt_params *p, int T, int ckpt, double scale, float *d_rho0,
+                       float *d_rho1, double *d_alpha, double *J, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Batched vector OMT: many independent problems in one persistent launch     */
 /* ------------------------------------------------------------------------ */
 /* Each instance is a vector-OMT problem of its own grid side, channel count,

@@ -70,6 +70,11 @@ SIGNATURES = {
                                 ctypes.POINTER(Params), c_void_p, c_void_p, c_void_p, ctypes.POINTER(Result),
                                 c_void_p]),
     "vomt_history": (c_int, [c_void_p, P_double, c_int]),
+    "vomt_backward": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
+                              c_void_p, c_void_p, c_void_p]),
+    "vomt_unrolled_grad": (c_int, [c_void_p, c_int, c_void_p, c_void_p, ctypes.POINTER(Graph), c_double,
+                                   ctypes.POINTER(Params), c_int, c_int, c_double, c_void_p, c_void_p, P_double,
+                                   P_double, c_void_p]),
     "vomt_batch_layout": (c_int, [c_int, ctypes.POINTER(Instance), ctypes.POINTER(ctypes.c_size_t)]),
     "vomt_solve_batched": (c_int, [c_void_p, c_int, ctypes.POINTER(Instance), c_void_p, ctypes.POINTER(Params),
                                    ctypes.POINTER(Result), c_void_p]),

@@ -108,6 +108,24 @@ static int check_densities(vomt_ctx *ctx, int planes, int n, const float *rho0, 
     return VOMT_OK;
 }
 
+int prepare_vector(vomt_ctx *ctx, int n, const vomt_graph *graph, double alpha, const vomt_params *pin, OpDev *op,
+                   StepDev *s, SolveCfg *cfg, vomt_params *p)
+{
+    Prepared P;
+    const int rc = prepare(ctx, n, graph, alpha, pin, &P);
+    if (rc) return rc;
+    *op = P.g;
+    *s = P.s;
+    *cfg = P.cfg;
+    *p = P.p;
+    return VOMT_OK;
+}
+
+int check_vector_densities(vomt_ctx *ctx, int k, int n, const float *rho0, const float *rho1, cudaStream_t st)
+{
+    return check_densities(ctx, k, n, rho0, rho1, st);
+}
+
 void fill_result(vomt_ctx *ctx, const SolveCfg &cfg, int engine, vomt_result *r, int *status)
 {
     const DevStatus &h = ctx->hstatus[0];
@@ -222,6 +240,8 @@ void vomt_destroy(vomt_ctx *c)
     if (c->stage) cudaFree(c->stage);
     if (c->mstage) cudaFree(c->mstage);
     if (c->batch) batch_state_free(c->batch);
+    if (c->gbuf) cudaFree(c->gbuf);
+    if (c->gpart) cudaFree(c->gpart);
     if (c->rscratch) cudaFree(c->rscratch);
     delete c;
 }

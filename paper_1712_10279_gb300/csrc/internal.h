@@ -119,6 +119,11 @@ struct vomt_ctx {
     // matrix-OMT compact staging (device)
     float *mstage = nullptr;
     size_t mstage_bytes = 0;
+    // gradient scratch (unrolled adjoint checkpoints, adjoints, partial sums)
+    float *gbuf = nullptr;
+    size_t gbuf_bytes = 0;
+    double *gpart = nullptr;
+    size_t gpart_bytes = 0;
     // batched engine (tables, scratch, captured graph)
     vomt::BatchState *batch = nullptr;
     // resident-engine scratch
@@ -129,6 +134,9 @@ struct vomt_ctx {
 namespace vomt {
 int set_cuda_error(vomt_ctx *ctx, cudaError_t e, const char *what);
 int fail(vomt_ctx *ctx, int code, const char *msg);
+int prepare_vector(vomt_ctx *ctx, int n, const vomt_graph *graph, double alpha, const vomt_params *pin, OpDev *op,
+                   StepDev *s, SolveCfg *cfg, vomt_params *p);
+int check_vector_densities(vomt_ctx *ctx, int k, int n, const float *rho0, const float *rho1, cudaStream_t st);
 void fill_result(vomt_ctx *ctx, const SolveCfg &cfg, int engine, vomt_result *r, int *status);
 int run_engine(vomt_ctx *ctx, const OpDev &op, const StepDev &s, const SolveCfg &cfg, const vomt_params &p,
                const float *rho0, const float *rho1, float *u, float *w, float *phi, cudaStream_t st, int *engine);
@@ -147,6 +155,8 @@ bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out)
 int resident_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg &cfg, const vomt_params &p,
                    const ResidentPlan &plan, const float *rho0, const float *rho1, float *u, float *w, float *phi,
                    cudaStream_t st);
+void launch_step(const OpDev &g, const StepDev &s, int un, int wn, const float *in, float *out, const float *b,
+                 const DevStatus *st, cudaStream_t stream);
 int validate_densities(vomt_ctx *ctx, int planes, int n, const float *rho0, const float *rho1,
                        cudaStream_t st, double *sums /* s0, s1, min0, min1, nonfinite */);
 }  // namespace vomt

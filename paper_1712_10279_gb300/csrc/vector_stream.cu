@@ -452,6 +452,19 @@ Launchers pick(int k, int un, int wn)
 
 }  // namespace
 
+// One fused iteration (Section 7.2) from the state at `in` to the state at
+// `out`; each state is contiguous planes phi [k], u_x [k], u_y [k], w [l].
+void launch_step(const OpDev &g, const StepDev &s, int un, int wn, const float *in, float *out, const float *b,
+                 const DevStatus *st, cudaStream_t stream)
+{
+    const size_t nn = (size_t)s.n * s.n;
+    const int k = g.k;
+    const StateIn si{in, in + (size_t)k * nn, in + (size_t)2 * k * nn, in + (size_t)3 * k * nn};
+    const StateOut so{out, out + (size_t)k * nn, out + (size_t)2 * k * nn, out + (size_t)3 * k * nn};
+    const dim3 blk(BX, BY), grd((s.n + BX - 1) / BX, (s.n + BY - 1) / BY);
+    pick(k, un, wn).step<<<grd, blk, 0, stream>>>(si, so, b, g, s, st);
+}
+
 int validate_densities(vomt_ctx *ctx, int planes, int n, const float *rho0, const float *rho1,
                        cudaStream_t st, double *sums)
 {
