@@ -11,6 +11,15 @@ grid-point iterations per second summed over the whole job.
 Prints one JSON line.  `--impl reference` times the FP64 CPU oracle (the
 reference implementation of this repository) on a bounded sample of the same
 workload on the host cores.
+
+Besides the headline number the line carries, measured after the timed region
+(N = 1 only, skipped with --no-extras): matrix OMT at 128 x 128 (3 x 3), the
+batched engine against a loop of plain solves on 512 mixed instances, the
+differentiable cost (64 pairs at 256 x 256, forward + backward, and the
+200-iteration unrolled gradient) against plain forward solves, and a
+2048 x 2048 k = 3 case whose state does not fit L2 (the HBM-bound cross-check of
+the streaming kernel).  --cap / --alphas shrink the timed workload for profiler
+runs only (the line then names the reduced workload).
 """
 from __future__ import annotations
 
@@ -32,8 +41,13 @@ N, K, ALPHAS, TOL, CAP = 256, 3, (0.1, 1.0, 10.0), 1e-5, 50000
 CHECK_EVERY = 100
 EDGES = [(0, 1), (0, 2), (1, 2)]
 BYTES_PER_GP_IT = 4 * (7 * K + 2 * len(EDGES))   # read phi,u_x,u_y,w,b; write phi,u_x,u_y,w (FP32)
-WORKLOAD = ("vector OMT, 256x256 grid, k=3 colour-image densities (seed 1002), complete graph K3, "
-            "alpha in {0.1,1,10}, ||u||_{1,2} ||w||_1, tau=3, to rel gap and rel res <= 1e-5, cap 50000 it")
+def workload_name(alphas=ALPHAS, cap=CAP):
+    return ("vector OMT, 256x256 grid, k=3 colour-image densities (seed 1002), complete graph K3, "
+            "alpha in {%s}, ||u||_{1,2} ||w||_1, tau=3, to rel gap and rel res <= 1e-5, cap %d it"
+            % (",".join("%g" % a for a in alphas), cap))
+
+
+WORKLOAD = workload_name()
 METRIC = "PDHG grid-point-iterations/s"
 UNIT = "grid-point-iterations/s"
 
@@ -149,6 +163,161 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _gpu_ms(fn):
+    """Run fn() between two CUDA events on the current stream; (result, milliseconds)."""
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = fn()
+    e1.record()
+    e1.synchronize()
+    return out, e0.elapsed_time(e1)
+
+
+def _summary(r):
+    return {"iters": r["iters"], "rel_gap": r["rel_gap"], "rel_res": r["rel_res"], "primal": r["primal"],
+            "converged": r["status"] == 0, "engine": r["engine"]}
+
+
+def extra_matrix(dev, peak):
+    """Matrix OMT, 128 x 128 grid of 3 x 3 SPD densities, N = 3 random symmetric L."""
+    import torch
+    import paper_1712_10279_gb300 as V
+    from paper_1712_10279_gb300 import synthetic as S
+    n, cap = 128, 50000
+    L0, L1 = S.tensor_field_pair(n, 3, seed=1003)
+    L = S.random_L(3, 3, seed=1003)
+    t0 = torch.from_numpy(L0.astype(np.float32)).to(dev)
+    t1 = torch.from_numpy(L1.astype(np.float32)).to(dev)
+    V.momt_solve(t0, t1, L, 1.0, max_iters=200, check_every=100)
+    sol, ms = _gpu_ms(lambda: V.momt_solve(t0, t1, L, 1.0, max_iters=cap, check_every=CHECK_EVERY, tol_gap=TOL,
+                                           tol_res=TOL))
+    r = sol.result
+    gp = n * n * r["iters"]
+    gbs = 240.0 * gp / (ms / 1e3) / 1e9
+    return dict(workload="matrix OMT 128x128 3x3 (tensor field seed 1003, random L seed 1003), alpha=1, "
+                         "||U||_2 ||W||_1, tau=30, to 1e-5, cap %d" % cap,
+                ms=ms, us_per_iter=1e3 * ms / max(r["iters"], 1), gp_it_per_s=gp / (ms / 1e3),
+                algorithmic_bytes_per_gp_it=240, achieved_GBps=gbs, frac_of_measured_hbm=gbs / peak, **_summary(r))
+
+
+def extra_batched(dev, cap=5000):
+    """512 mixed instances: one persistent batched launch against a host loop of plain
+    single-instance solves, both from zero, both stopped per instance at 1e-5 or `cap`."""
+    import torch
+    import paper_1712_10279_gb300 as V
+    from paper_1712_10279_gb300 import synthetic as S
+    inst = S.batched_instances(512, seed=1004)
+    probs = [dict(n=q["n"], k=q["k"], edges=q["edges"], alpha=1.0) for q in inst]
+    bt = V.Batch(probs, [q["rho0"] for q in inst], [q["rho1"] for q in inst], device=dev.index or 0)
+    threads, tune_ms = bt.tune(sample_iters=50)
+    bt.solve(max_iters=100, check_every=100)
+    _, ms_b = _gpu_ms(lambda: bt.solve(max_iters=cap, check_every=CHECK_EVERY, tol_gap=TOL, tol_res=TOL))
+    rb = bt.results
+    d0 = [torch.from_numpy(q["rho0"].astype(np.float32)).to(dev) for q in inst]
+    d1 = [torch.from_numpy(q["rho1"].astype(np.float32)).to(dev) for q in inst]
+
+    def loop():
+        return [V.solve(a, b, q["edges"], 1.0, max_iters=cap, check_every=CHECK_EVERY, tol_gap=TOL,
+                        tol_res=TOL).result for q, a, b in zip(inst, d0, d1)]
+
+    rp, ms_p = _gpu_ms(loop)
+    gp_b = sum(q["n"] ** 2 * r["iters"] for q, r in zip(inst, rb))
+    gp_p = sum(q["n"] ** 2 * r["iters"] for q, r in zip(inst, rp))
+    return dict(workload="512 instances, n in {32..256}, k in {1,3,5}, random connected graphs p=0.6 (seed 1004), "
+                         "alpha=1, to 1e-5 per instance, cap %d" % cap,
+                batched_ms=ms_b, batched_converged=sum(r["status"] == 0 for r in rb),
+                batched_gp_it_per_s=gp_b / (ms_b / 1e3), batched_threads=threads,
+                tune_ms={str(k_): v for k_, v in tune_ms.items()},
+                plain_ms=ms_p, plain_converged=sum(r["status"] == 0 for r in rp),
+                plain_gp_it_per_s=gp_p / (ms_p / 1e3), plain_over_batched_time=ms_p / ms_b,
+                max_cost_diff=max(abs(a["primal"] - b["primal"]) / max(abs(b["primal"]), 1e-30)
+                                  for a, b in zip(rb, rp)))
+
+
+def extra_differentiable(dev, count=64, cap=2000):
+    """64 colour-image pairs at 256 x 256: batched forward solve + envelope backward, and
+    the 200-iteration unrolled gradient, against plain forward solves of the same pairs."""
+    import torch
+    import paper_1712_10279_gb300 as V
+    from paper_1712_10279_gb300 import synthetic as S
+    from paper_1712_10279_gb300 import autograd as A
+    pairs = [S.color_image_pair(N, K, seed=2000 + q) for q in range(count)]
+    r0 = torch.from_numpy(np.stack([p[0] for p in pairs]).astype(np.float32)).to(dev)
+    r1 = torch.from_numpy(np.stack([p[1] for p in pairs]).astype(np.float32)).to(dev)
+    kw = dict(max_iters=cap, check_every=CHECK_EVERY, tol_gap=TOL, tol_res=TOL)
+
+    def fwd_bwd():
+        x1 = r1.clone().requires_grad_(True)
+        a = torch.tensor(1.0, dtype=torch.float64, device=dev, requires_grad=True)
+        c = A.transport_cost(r0, x1, EDGES, a, engine="batched", **kw)
+        c.sum().backward()
+        return c
+
+    def plain():
+        return [V.solve(r0[q], r1[q], EDGES, 1.0, **kw).result for q in range(count)]
+
+    def unrolled():
+        out = []
+        for q in range(count):
+            x1 = r1[q].clone().requires_grad_(True)
+            J = A.unrolled_cost(r0[q], x1, EDGES, 1.0, T=200, ckpt=20)
+            J.backward()
+            out.append(float(J))
+        return out
+
+    fwd_bwd()
+    costs, ms_fb = _gpu_ms(fwd_bwd)
+    rp, ms_p = _gpu_ms(plain)
+    _, ms_u = _gpu_ms(unrolled)
+    return dict(workload="%d colour-image pairs 256x256 k=3 (seeds 2000..), alpha=1, to 1e-5, cap %d; "
+                         "unrolled T=200, checkpoints every 20" % (count, cap),
+                forward_backward_batched_ms=ms_fb, plain_forward_loop_ms=ms_p,
+                fwd_bwd_over_plain_time=ms_fb / ms_p, unrolled_fwd_bwd_ms=ms_u,
+                plain_converged=sum(r["status"] == 0 for r in rp),
+                max_cost_diff=float(max(abs(float(c) - r["primal"]) / max(abs(r["primal"]), 1e-30)
+                                        for c, r in zip(costs.detach().cpu(), rp))))
+
+
+def extra_hbm_bound(dev, peak, n=2048, iters=300):
+    """k = 3 at 2048 x 2048 (about 200 MB of state, beyond L2): the streaming kernel
+    against the HBM roofline; and k = 1 at 1024 x 1024 (the scalar S-OMT size)."""
+    import torch
+    import paper_1712_10279_gb300 as V
+    from paper_1712_10279_gb300 import synthetic as S
+    out = {}
+    for name, nn_, k, edges, seed in (("k3_2048", n, 3, EDGES, 1006), ("k1_1024", 1024, 1, [], 1007)):
+        a, b = S.color_image_pair(nn_, k, seed=seed)
+        d0 = torch.from_numpy(a.astype(np.float32)).to(dev)
+        d1 = torch.from_numpy(b.astype(np.float32)).to(dev)
+        V.solve(d0, d1, edges, 1.0, max_iters=20, check_every=20, engine="stream")
+        sol, ms = _gpu_ms(lambda: V.solve(d0, d1, edges, 1.0, max_iters=iters, check_every=CHECK_EVERY,
+                                          engine="stream"))
+        it = sol.result["iters"]
+        bpg = 4 * (7 * k + 2 * len(edges))
+        gbs = bpg * nn_ * nn_ * it / (ms / 1e3) / 1e9
+        out[name] = dict(n=nn_, k=k, iters=it, us_per_iter=1e3 * ms / it, algorithmic_bytes_per_gp_it=bpg,
+                         achieved_GBps=gbs, frac_of_measured_hbm=gbs / peak,
+                         note="checks every %d iterations included" % CHECK_EVERY)
+    return out
+
+
+def extras(dev):
+    peak, _ = _peaks()
+    out = {}
+    for name, fn in (("matrix_128", lambda: extra_matrix(dev, peak)), ("batched_vs_plain", lambda: extra_batched(dev)),
+                     ("differentiable", lambda: extra_differentiable(dev)),
+                     ("hbm_bound", lambda: extra_hbm_bound(dev, peak))):
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as ex:      # reported, never hidden: the line says what failed
+            out[name] = {"error": "%s: %s" % (type(ex).__name__, ex)}
+        out[name]["wall_s"] = time.perf_counter() - t0
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1712_10279_gb300 as V
@@ -166,9 +335,11 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream(dev)
 
+    alphas, cap = args.alphas, args.cap
+
     def step(results):
-        for a in ALPHAS:
-            sol = V.solve(d0, d1, EDGES, a, max_iters=CAP, check_every=CHECK_EVERY, tol_gap=TOL, tol_res=TOL,
+        for a in alphas:
+            sol = V.solve(d0, d1, EDGES, a, max_iters=cap, check_every=CHECK_EVERY, tol_gap=TOL, tol_res=TOL,
                           engine=args.engine)
             results.append(sol.result)
 
@@ -205,20 +376,22 @@ def run_ours(args, rank, world, local_rank):
     value = gp_it / (total_ms / 1e3)
 
     # end to end through the host-buffer entry point: copies inside the timed region
-    e2e_ms = []
-    for _ in range(max(1, args.steps)):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        e2e_iters = 0
-        for a in ALPHAS:
-            sol = V.solve_host(h0, h1, EDGES, a, max_iters=CAP, check_every=CHECK_EVERY, tol_gap=TOL, tol_res=TOL,
-                               engine=args.engine, device=local_rank)
-            e2e_iters += sol.result["iters"]
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_value = world * N * N * e2e_iters / (statistics.mean(e2e_ms) / 1e3)
+    e2e_value = None
+    if not args.no_e2e:
+        e2e_ms = []
+        for _ in range(max(1, args.steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_iters = 0
+            for a in alphas:
+                sol = V.solve_host(h0, h1, EDGES, a, max_iters=cap, check_every=CHECK_EVERY, tol_gap=TOL,
+                                   tol_res=TOL, engine=args.engine, device=local_rank)
+                e2e_iters += sol.result["iters"]
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        e2e_value = world * N * N * e2e_iters / (statistics.mean(e2e_ms) / 1e3)
     l = len(EDGES)
-    h2d = len(ALPHAS) * 2 * K * N * N * 4
-    d2h = len(ALPHAS) * (3 * K + l) * N * N * 4
+    h2d = len(alphas) * 2 * K * N * N * 4
+    d2h = len(alphas) * (3 * K + l) * N * N * 4
 
     if rank != 0:
         if dist:
@@ -227,14 +400,16 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = _peaks()
     # dominant kernel: the PDHG iteration; its algorithmic bytes over the timed GPU time
     achieved = BYTES_PER_GP_IT * (gp_it / world) / (total_ms / 1e3) / 1e9
+    # ncu DRAM bytes of one launch of the dominant kernel, taken on this kernel source and
+    # this launch (the same iteration count); else null
     trec = _traffic_record()
     traffic = None
-    if trec and results:
-        traffic = float(trec["dram_bytes_per_iteration"]) * (sum(r["iters"] for r in results) / len(results))
+    if trec and results and all(r["iters"] == int(trec["iterations_per_launch"]) for r in results):
+        traffic = float(trec["dram_bytes_per_launch"])
     engine = results[0]["engine"] if results else args.engine
     per_alpha = {}
-    for q, a in enumerate(ALPHAS):
-        rs = [results[s * len(ALPHAS) + q] for s in range(args.steps)]
+    for q, a in enumerate(alphas):
+        rs = [results[s * len(alphas) + q] for s in range(args.steps)]
         per_alpha["alpha=%g" % a] = {"iters": rs[-1]["iters"], "rel_gap": rs[-1]["rel_gap"],
                                      "rel_res": rs[-1]["rel_res"], "primal": rs[-1]["primal"],
                                      "converged": rs[-1]["status"] == 0}
@@ -242,18 +417,25 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N, "k": K, "edges": l, "alphas": list(ALPHAS), "tol": TOL,
-                   "cap": CAP, "check_every": CHECK_EVERY, "engine": engine,
+        "config": {"workload": workload_name(alphas, cap), "n": N, "k": K, "edges": l, "alphas": list(alphas),
+                   "tol": TOL, "cap": cap, "check_every": CHECK_EVERY, "engine": engine,
                    "l2": "flushed (512 MB write) between timed steps",
                    "parallelism": "independent replicas, one per GPU" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": traffic,
+                     "kernel": "k_resident" if engine == "resident" else "k_step",
+                     "algorithmic_bytes_per_launch": BYTES_PER_GP_IT * N * N * (sum(r["iters"] for r in results)
+                                                                             / max(len(results), 1)),
+                     "launch_ms": total_ms / max(len(results), 1),
                      "algorithmic_bytes_per_grid_point_iteration": BYTES_PER_GP_IT},
         "time_to_tolerance": per_alpha,
         "gpu_launches": launches,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": None if e2e_value is None else {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                                               "d2h_bytes_per_step": d2h},
         "clocks": clocks,
     }
+    if world == 1 and not args.no_extras:
+        line["extras"] = extras(dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample()
         line["cpu_baseline"]["host_cores_available"] = _cpu_cores()
@@ -270,6 +452,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--engine", default="auto", choices=["auto", "stream", "resident"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cap", type=int, default=CAP, help="iteration cap per solve (profiler runs only)")
+    ap.add_argument("--alphas", type=float, nargs="+", default=list(ALPHAS), help="(profiler runs only)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

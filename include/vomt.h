@@ -117,6 +117,8 @@ typedef struct {
     int engine;          /* engine that ran */
     int checks;          /* convergence checks run */
     int launches;        /* CUDA kernels this call launched */
+    int blocks;          /* thread blocks of the main launch (resident: one tile each) */
+    int halo;            /* resident engine: iterations between halo exchanges (0 otherwise) */
 } vomt_result;
 
 /* Create a context on CUDA device `device`.  The context owns the solver's

@@ -153,6 +153,8 @@ void fill_result(vomt_ctx *ctx, const SolveCfg &cfg, int engine, vomt_result *r,
         r->engine = engine;
         r->checks = h.checks;
         r->launches = ctx->launches;
+        r->blocks = ctx->last_blocks;
+        r->halo = ctx->last_halo;
     }
 }
 
@@ -161,6 +163,8 @@ int run_engine(vomt_ctx *ctx, const OpDev &op, const StepDev &s, const SolveCfg 
                const float *rho0, const float *rho1, float *u, float *w, float *phi, cudaStream_t st, int *engine)
 {
     *engine = VOMT_ENGINE_STREAM;
+    ctx->last_blocks = 0;
+    ctx->last_halo = 0;
     int rc;
     if (p.engine != VOMT_ENGINE_STREAM) {
         ResidentPlan plan;

@@ -40,7 +40,9 @@ namespace {
 
 using namespace dev;
 
-constexpr int RES_THREADS = 512;
+constexpr int RES_THREADS = 512;      // most threads a block runs
+constexpr int RES_P4_POINTS = 1024;   // extended tiles above this size: four points per thread
+constexpr int RES_MAX_POINTS = 2048;  // largest extended tile (four points per thread, 512 threads)
 constexpr int TMAX = 64;              // longest tile side
 constexpr int HMAX = 16;              // widest halo ring
 
@@ -407,8 +409,12 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
             }
         }
         __syncthreads();
-        // per-point terms in FP32 accumulated in FP64; the residual and the dual
-        // objective's products in FP64
+        // Per-point terms in FP32, summed over this thread's few points in FP32
+        // and then over the grid in FP64 (FP64 arithmetic is scarce on this GPU).
+        // The constraint residual, which cancels several digits, is formed in FP64.
+        float fs[NRED];
+#pragma unroll
+        for (int q = 0; q < NRED; ++q) fs[q] = 0.0f;
 #pragma unroll
         for (int r = 0; r < P; ++r) {
             if (!ptile[r]) continue;
@@ -417,21 +423,21 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
             float nu_pt = 0.0f, dn_u = 0.0f;
 #pragma unroll
             for (int c = 0; c < K; ++c) {
-                const float uxc = ux[r][c], uyc = uy[r][c], phc = ph[r][c], bc = bb[r][c];
+                const float uxc = ux[r][c], uyc = uy[r][c], phc = ph[r][c], bc = bb[r][c], wgt = a.g.wc[c];
                 const float xl = (x > 0) ? SA(sux, c, ey, ex - 1) : 0.0f;
                 const float yd = (y > 0) ? SA(suy, c, ey - 1, ex) : 0.0f;
-                double rdiv = dih * (((double)uxc - (double)xl) + ((double)uyc - (double)yd));
                 const float dxl = (x > 0) ? SA(sdx, c, ey, ex - 1) : 0.0f;
                 const float dyd = (y > 0) ? SA(sdy, c, ey - 1, ex) : 0.0f;
                 const float ddiv = ih * ((SA(sdx, c, ey, ex) - dxl) + (SA(sdy, c, ey, ex) - dyd)) + dgw[r][c];
+                float gwb = bc;
 #pragma unroll
-                for (int e = 0; e < LKv; ++e) rdiv -= (double)a.g.Dv[c][e] * (double)w[r][e];
-                const double rc = rdiv + (double)bc, wgt = (double)a.g.wc[c];
-                v[RED_RR] += wgt * rc * rc;
-                v[RED_BB] += wgt * (double)(bc * bc);
-                v[RED_D] += wgt * (double)phc * (double)bc;
-                v[RED_DP] += wgt * (double)(dph[r][c] * dph[r][c]);
-                v[RED_X] += wgt * (double)(dph[r][c] * ddiv);
+                for (int e = 0; e < LKv; ++e) gwb -= a.g.Dv[c][e] * w[r][e];
+                const double rc = dih * (((double)uxc - (double)xl) + ((double)uyc - (double)yd)) + (double)gwb;
+                v[RED_RR] += (double)wgt * rc * rc;
+                fs[RED_BB] += wgt * bc * bc;
+                fs[RED_D] += wgt * phc * bc;
+                fs[RED_DP] += wgt * dph[r][c] * dph[r][c];
+                fs[RED_X] += wgt * dph[r][c] * ddiv;
                 const float gxx = (x < n - 1) ? ih * (SA(sphi, c, ey, ex + 1) - phc) : 0.0f;
                 const float gyy = (y < n - 1) ? ih * (SA(sphi, c, ey + 1, ex) - phc) : 0.0f;
                 if (a.un == VOMT_U_L12) {
@@ -459,11 +465,17 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
                 }
             }
             if (a.wn == VOMT_W_L2) { nw_pt = sqrtf(nw_pt); dn_w = sqrtf(dn_w); }
-            v[RED_P] += (double)nu_pt + (double)alpha * (double)nw_pt;
+            fs[RED_P] += nu_pt + alpha * nw_pt;
             float di = fmaxf(dn_u - 1.0f, 0.0f);
             if (l > 0) di = fmaxf(di, dn_w - alpha);
-            v[RED_MAX] = fmax(v[RED_MAX], (double)di);
+            fs[RED_MAX] = fmaxf(fs[RED_MAX], di);
         }
+        v[RED_P] += (double)fs[RED_P];
+        v[RED_D] += (double)fs[RED_D];
+        v[RED_BB] += (double)fs[RED_BB];
+        v[RED_DP] += (double)fs[RED_DP];
+        v[RED_X] += (double)fs[RED_X];
+        v[RED_MAX] = fmax(v[RED_MAX], (double)fs[RED_MAX]);
         // block reduction (fixed order)
         const int lane = tid & 31, wid = tid >> 5, nw = (nthr + 31) >> 5;
 #pragma unroll
@@ -581,29 +593,29 @@ ResKernel pick_k(int k)
     }
 }
 
-ResKernel pick_kernel(int k, int P) { return P <= 2 ? pick_k<2>(k) : pick_k<4>(k); }
+ResKernel pick_kernel(int k, int P) { return P == 1 ? pick_k<1>(k) : (P == 2 ? pick_k<2>(k) : pick_k<4>(k)); }
 
 // Estimated nanoseconds per iteration (see resident_plan).  Constants fitted to
 // GB300 measurements of this kernel at k = 3: 3.5 ns per point of the region a
 // step updates (arithmetic, shared-memory traffic and the two barriers of a
 // step at 16 warps per SM), 3.1 us per halo exchange (one L2 round trip plus
 // the tagged stores and polls), and 30% more per point when a thread owns
-// four points (register spills).
+// four points (register spills; extended tiles above RES_P4_POINTS).
 double plan_cost(int TX, int TY, int H, int G)
 {
     const double per_pt = 3.5;
-    if (G == 1) return per_pt * TX * TY * (TX * TY > 2 * RES_THREADS ? 1.3 : 1.0);
+    if (G == 1) return per_pt * TX * TY * (TX * TY > RES_P4_POINTS ? 1.3 : 1.0);
     double pts = 0.0;
     for (int s = 1; s <= H; ++s) pts += (double)(TX + 2 * (H - s) + 1) * (TY + 2 * (H - s) + 1);
     const int ext = (TX + 2 * H) * (TY + 2 * H);
-    return per_pt * (ext > 2 * RES_THREADS ? 1.3 : 1.0) * pts / H + 3100.0 / H;
+    return per_pt * (ext > RES_P4_POINTS ? 1.3 : 1.0) * pts / H + 3100.0 / H;
 }
 
 }  // namespace
 
 // Tile plan.  Tiles of at most 64 x 64 points, at most `max_blocks` of them; the
 // ring width H is at most the narrowest tile side; the extended tile
-// (TX + 2H) x (TY + 2H) must fit 4 points per thread of a 512-thread block.
+// (TX + 2H) x (TY + 2H) holds at most RES_MAX_POINTS points.
 // Among those, the plan with the smallest estimated time per iteration
 // (plan_cost) wins.  `force_H` > 0 pins the ring width.
 bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out)
@@ -618,7 +630,7 @@ bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out)
             if (TY > TMAX) continue;
             const int G = Gx * Gy;
             if (G == 1) {
-                if (TX * TY > 4 * RES_THREADS) continue;
+                if (TX * TY > RES_MAX_POINTS) continue;
                 const double cost = plan_cost(TX, TY, 0, 1);
                 if (best < 0 || cost < best) {
                     best = cost;
@@ -630,7 +642,7 @@ bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out)
                 if (force_H > 0 && H != force_H) continue;
                 if (H > TXmin || H > TYmin) break;
                 const int EW = TX + 2 * H, EH = TY + 2 * H;
-                if (EW * EH > 4 * RES_THREADS) break;
+                if (EW * EH > RES_MAX_POINTS) break;
                 const double cost = plan_cost(TX, TY, H, G);
                 if (best < 0 || cost < best) {
                     best = cost;
@@ -641,10 +653,11 @@ bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out)
     }
     if (best < 0) return false;
     const int EW = out->TXm + 2 * out->H, EH = out->TYm + 2 * out->H;
-    out->threads = RES_THREADS;
-    if (EW * EH <= RES_THREADS) out->threads = ((EW * EH + 31) / 32) * 32;
-    out->P = (EW * EH + out->threads - 1) / out->threads;
-    out->P = out->P <= 2 ? 2 : 4;
+    // P points per thread, the fewest that fit 512 threads, spread evenly over
+    // round_up(ext / P, 32) threads.
+    const int ext = EW * EH;
+    out->P = ext <= RES_THREADS ? 1 : (ext <= 2 * RES_THREADS ? 2 : 4);
+    out->threads = (((ext + out->P - 1) / out->P + 31) / 32) * 32;
     return true;
 }
 
@@ -717,6 +730,8 @@ int resident_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveC
     e = cudaLaunchCooperativeKernel((const void *)kern, dim3(G), dim3(plan.threads), args, SL.total, st);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "resident launch");
     ctx->launches += 1;
+    ctx->last_blocks = G;
+    ctx->last_halo = G > 1 ? plan.H : 0;
     e = cudaMemcpyAsync(&ctx->hstatus[0], ctx->dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "resident solve");

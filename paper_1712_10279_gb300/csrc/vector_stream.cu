@@ -232,16 +232,17 @@ __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const 
 #pragma unroll
     for (int q = 0; q < NRED; ++q) v[q] = 0.0;
     if (i < n && j < n) {
-        // Per-point terms in FP32 (each rounding is relative 2^-24) accumulated in
-        // FP64; the constraint residual, which cancels several digits, and the dual
-        // objective's products are formed in FP64.
+        // Per-point terms in FP32 (each rounding is relative 2^-24), converted once
+        // per point and accumulated in FP64 (FP64 arithmetic is scarce on this
+        // GPU).  The spatial part of the constraint residual, which cancels
+        // several digits, is formed in FP64.
         const size_t nn = (size_t)n * n, p = (size_t)j * n + i;
         const bool hR = i < n - 1, hU = j < n - 1, hL = i > 0, hD = j > 0;
         const float ih = s.ih, alpha = s.alpha;
         const double dih = (double)(n - 1);
-        float ph[K], dph[K], ddiv[K];
+        float ph[K], dph[K], ddiv[K], gwb[K];
         double rdiv[K];
-        float nu_pt = 0.0f, dn_u = 0.0f;
+        float nu_pt = 0.0f, dn_u = 0.0f, fdu = 0.0f, fdp = 0.0f, fd = 0.0f, fbb = 0.0f, fdw = 0.0f, fx = 0.0f;
 #pragma unroll
         for (int c = 0; c < K; ++c) {
             const size_t q = c * nn + p;
@@ -249,15 +250,16 @@ __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const 
             ph[c] = cur.phi[q];
             dph[c] = ph[c] - prv.phi[q];
             const float xl = hL ? cur.ux[q - 1] : 0.0f, yd = hD ? cur.uy[q - n] : 0.0f;
-            rdiv[c] = dih * (((double)uxc - (double)xl) + ((double)uyc - (double)yd)) + (double)bc;
+            rdiv[c] = dih * (((double)uxc - (double)xl) + ((double)uyc - (double)yd));
+            gwb[c] = bc;
             const float dux = uxc - prv.ux[q], duy = uyc - prv.uy[q];
             const float dxl = hL ? cur.ux[q - 1] - prv.ux[q - 1] : 0.0f;
             const float dyd = hD ? cur.uy[q - n] - prv.uy[q - n] : 0.0f;
             ddiv[c] = ih * ((dux - dxl) + (duy - dyd));
-            v[RED_DU] += (double)(wgt * (dux * dux + duy * duy));
-            v[RED_DP] += (double)(wgt * dph[c] * dph[c]);
-            v[RED_D] += (double)wgt * (double)ph[c] * (double)bc;
-            v[RED_BB] += (double)(wgt * bc * bc);
+            fdu += wgt * (dux * dux + duy * duy);
+            fdp += wgt * dph[c] * dph[c];
+            fd += wgt * ph[c] * bc;
+            fbb += wgt * bc * bc;
             const float gx = hR ? ih * (cur.phi[q + 1] - ph[c]) : 0.0f;
             const float gy = hU ? ih * (cur.phi[q + n] - ph[c]) : 0.0f;
             if (UN == VOMT_U_L12) {
@@ -278,12 +280,12 @@ __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const 
             if (e < g.l) {
                 const size_t q = e * nn + p;
                 const float we = cur.w[q], dwe = we - prv.w[q], wgt = g.we[e];
-                v[RED_DW] += (double)(wgt * dwe * dwe);
+                fdw += wgt * dwe * dwe;
                 float ge = 0.0f;
 #pragma unroll
                 for (int c = 0; c < K; ++c) {
                     ge += g.G[e][c] * ph[c];
-                    rdiv[c] -= (double)g.Dv[c][e] * (double)we;   // div y = -Dv y
+                    gwb[c] -= g.Dv[c][e] * we;      // div y = -Dv y
                     ddiv[c] -= g.Dv[c][e] * dwe;
                 }
                 if (WN == VOMT_W_L1) { nw_pt += wgt * fabsf(we); dn_w = fmaxf(dn_w, fabsf(ge)); }
@@ -291,12 +293,19 @@ __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const 
             }
         }
         if (WN == VOMT_W_L2) { nw_pt = sqrtf(nw_pt); dn_w = sqrtf(dn_w); }
-        v[RED_P] = (double)nu_pt + (double)alpha * (double)nw_pt;
 #pragma unroll
         for (int c = 0; c < K; ++c) {
-            v[RED_RR] += (double)g.wc[c] * rdiv[c] * rdiv[c];
-            v[RED_X] += (double)(g.wc[c] * dph[c] * ddiv[c]);
+            const double rc = rdiv[c] + (double)gwb[c];
+            v[RED_RR] += (double)g.wc[c] * rc * rc;
+            fx += g.wc[c] * dph[c] * ddiv[c];
         }
+        v[RED_P] = (double)(nu_pt + alpha * nw_pt);
+        v[RED_D] = (double)fd;
+        v[RED_BB] = (double)fbb;
+        v[RED_DU] = (double)fdu;
+        v[RED_DW] = (double)fdw;
+        v[RED_DP] = (double)fdp;
+        v[RED_X] = (double)fx;
         float di = fmaxf(dn_u - 1.0f, 0.0f);
         if (g.l > 0) di = fmaxf(di, dn_w - alpha);
         v[RED_MAX] = (double)di;
@@ -512,6 +521,7 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
     }
     const dim3 blk(BX, BY), grd((n + BX - 1) / BX, (n + BY - 1) / BY);
     const int nblocks = (int)(grd.x * grd.y);
+    ctx->last_blocks = nblocks;
     rc = ensure_buffer(ctx, (void **)&ctx->partials, &ctx->partials_cap, sizeof(double) * (size_t)nblocks * NRED,
                        "partials");
     if (rc) return rc;
