@@ -1,0 +1,15 @@
+// Instantiations of the resident kernel for K in {3} channels (compiled apart
+// from the other channel counts so that the units build in parallel).
+#include "resident_kernel.cuh"
+
+namespace vomt {
+namespace res {
+
+ResKernel res_kernel_k3(int K, int P, int NM)
+{
+    if (K == 3) return kernel_for<3>(P, NM);
+    return nullptr;
+}
+
+}  // namespace res
+}  // namespace vomt

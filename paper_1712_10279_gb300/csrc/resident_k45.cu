@@ -1,0 +1,16 @@
+// Instantiations of the resident kernel for K in {4, 5} channels (compiled apart
+// from the other channel counts so that the units build in parallel).
+#include "resident_kernel.cuh"
+
+namespace vomt {
+namespace res {
+
+ResKernel res_kernel_k45(int K, int P, int NM)
+{
+    if (K == 4) return kernel_for<4>(P, NM);
+    if (K == 5) return kernel_for<5>(P, NM);
+    return nullptr;
+}
+
+}  // namespace res
+}  // namespace vomt

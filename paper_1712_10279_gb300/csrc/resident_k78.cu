@@ -1,0 +1,16 @@
+// Instantiations of the resident kernel for K in {7, 8} channels (compiled apart
+// from the other channel counts so that the units build in parallel).
+#include "resident_kernel.cuh"
+
+namespace vomt {
+namespace res {
+
+ResKernel res_kernel_k78(int K, int P, int NM)
+{
+    if (K == 7) return kernel_for<7>(P, NM);
+    if (K == 8) return kernel_for<8>(P, NM);
+    return nullptr;
+}
+
+}  // namespace res
+}  // namespace vomt

@@ -1,0 +1,822 @@
+// Resident engine for vector OMT: one cooperative launch runs the whole PDHG
+// solve (Section 7.2) with the iterate on chip, exchanging tile halos through
+// L2 once every H iterations (temporal blocking).
+//
+// The n x n grid is cut into Gx x Gy rectangular tiles, one per thread block
+// (one block per SM).  Each block works on its tile extended by a ring of
+// width H on every side that has a neighbour tile.  After a halo exchange the
+// block holds the full iterate (phi, u_x, u_y, w) on the extended region, and
+// it can run H iterations without hearing from its neighbours: iteration s of
+// a block updates the tile grown by H - s cells, because one iteration of
+// Section 7.2 at a point reads the previous iterate only at that point and at
+// neighbours one cell away (phi at (i+1,j), (i,j+1), (i-1,j+1), (i+1,j-1); u at
+// (i-1,j), (i,j-1)).  After H iterations the tile itself is exact and the ring
+// is refreshed from the neighbours.  The ring work is redundant arithmetic
+// that buys H-fold fewer L2 round trips, which bound small grids.
+//
+// Points are owned by threads for the whole solve (up to P points per thread),
+// numbered tile first and then ring by ring (resident_order.h), so that the
+// shrinking region of every step is a prefix of the numbering: a step's idle
+// points are whole idle warps.  Each thread keeps its points' iterate and
+// b = rho1 - rho0 in registers.  The stencils of Appendix A within a block read
+// neighbouring phi and ubar from shared memory, where a point's channels sit
+// side by side (padded to 1, 2 or a multiple of 4 floats) so that one vector
+// load fetches them all.  At the edges of the grid the neighbour offsets are
+// zero (the forward difference then vanishes) and the backward neighbours are
+// masked, so the stencil has no branches.
+//
+// Between blocks, every iterate value a neighbour needs is written to L2 as a
+// 64-bit word with the value in its low half and the exchange number in its
+// high half; words go in pairs (one 16-byte vector access per two fields).  A
+// reader polls the words themselves, so a halo exchange costs one L2 round trip
+// and no fences or flags (each aligned 64-bit element of a vector access is
+// single-copy atomic).
+//
+// Convergence checks (every check_every iterations and at the end; a block of
+// iterations is cut short so that it ends on a check) form the metric terms of
+// each point in FP32 (the constraint residual with error-free transformations,
+// to about twice FP32 precision), sum them per thread in FP32 and per block in
+// FP64, publish one row per block as tagged word pairs, and every block sums
+// all rows in the same fixed order, so all blocks take the same stopping
+// decision.  Every wait is bounded in time; a wait that runs out raises a
+// global abort word that makes every block return.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "internal.h"
+#include "pdhg_device.cuh"
+#include "resident_order.h"
+
+namespace vomt {
+namespace res {
+
+using namespace dev;
+
+constexpr int RES_THREADS = 512;      // most threads a block runs
+constexpr int HMAX = 16;              // widest halo ring
+
+template <int K>
+struct LK {
+    static constexpr int v = K * (K - 1) / 2 > 0 ? K * (K - 1) / 2 : 1;
+};
+
+// floats per point in the shared-memory arrays: the channels padded to a vector width
+__host__ __device__ constexpr int kv_of(int K) { return K == 1 ? 1 : (K == 2 ? 2 : ((K + 3) / 4) * 4); }
+
+// padded row length (points) of the shared-memory arrays: odd, so that the
+// column segments of the ring fall in distinct banks
+__host__ __device__ inline int row_stride(int EWm) { return EWm | 1; }
+
+struct ResGeom {
+    int n, Gx, Gy, TXm, TYm;
+    int H;         // iterations per block of steps between exchanges
+    int R;         // ring width (H with neighbour tiles, 0 for a lone tile)
+    int EWs, EHm;  // shared-memory array rows: padded length, count
+};
+
+struct ResArgs {
+    ResGeom geo;
+    OpDev g;                   // per-point grad / div and inner-product weights
+    StepDev s;
+    SolveCfg cfg;
+    int un, wn, max_iters, check_every, warm;
+    const float *rho0, *rho1;
+    float *u, *w, *phi;
+    unsigned long long *xch;   // [G][2][F2][TYm][TXm][2] tagged words, pair j = fields 2j, 2j+1
+    unsigned long long *rows;  // [2][G][NRED][2] tagged halves of the FP64 partial sums
+    ResCtl *ctl;
+    DevStatus *st;
+    double *hist;
+    int hist_cap;
+};
+
+struct SmemLayout {
+    int red, S, dec, rtab, cnt, sphi, sux, suy, sdx, sdy, total;
+};
+
+__host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
+
+__host__ __device__ inline SmemLayout smem_layout(int K, int EWs, int EHm, int G)
+{
+    SmemLayout L;
+    int o = 0;
+    const int plane = EWs * EHm * kv_of(K) * 4;
+    L.red = o; o += align16((RES_THREADS / 32) * NRED * 8);
+    L.S = o; o += align16(NRED * 8);
+    L.dec = o; o += 16;
+    L.rtab = o; o += align16(G * NRED * 8);
+    L.cnt = o; o += align16(2 * (HMAX + 2) * 4);
+    L.sphi = o; o += align16(plane);
+    L.sux = o; o += align16(plane);
+    L.suy = o; o += align16(plane);
+    L.sdx = o; o += align16(plane);
+    L.sdy = o; o += align16(plane);
+    L.total = o;
+    return L;
+}
+
+// ---------------------------------------------------------------- small helpers
+// K channel values of one point from / to a shared-memory array (vector accesses)
+template <int K>
+__device__ __forceinline__ void lds(const float *p, float (&v)[K])
+{
+    constexpr int KV = kv_of(K);
+    float t[KV];
+    if constexpr (KV == 1) {
+        t[0] = p[0];
+    } else if constexpr (KV == 2) {
+        const float2 a = *reinterpret_cast<const float2 *>(p);
+        t[0] = a.x;
+        t[1] = a.y;
+    } else {
+#pragma unroll
+        for (int j = 0; j < KV / 4; ++j) {
+            const float4 a = *reinterpret_cast<const float4 *>(p + 4 * j);
+            t[4 * j] = a.x;
+            t[4 * j + 1] = a.y;
+            t[4 * j + 2] = a.z;
+            t[4 * j + 3] = a.w;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < K; ++c) v[c] = t[c];
+}
+
+template <int K>
+__device__ __forceinline__ void sts(float *p, const float (&v)[K])
+{
+    constexpr int KV = kv_of(K);
+    float t[KV];
+#pragma unroll
+    for (int c = 0; c < KV; ++c) t[c] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < K; ++c) t[c] = v[c];
+    if constexpr (KV == 1) {
+        p[0] = t[0];
+    } else if constexpr (KV == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(t[0], t[1]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < KV / 4; ++j)
+            *reinterpret_cast<float4 *>(p + 4 * j) = make_float4(t[4 * j], t[4 * j + 1], t[4 * j + 2], t[4 * j + 3]);
+    }
+}
+
+// Error-free sum (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ float two_sum(float a, float b, float &e)
+{
+    const float s = a + b;
+    const float bv = s - a;
+    e = (a - (s - bv)) + (b - bv);
+    return s;
+}
+
+// ih * ((ux - xl) + (uy - yd)) + gb with the rounding errors of the
+// differences, their sum, the product and the final sum carried along (the
+// compensated evaluation of Ogita, Rump and Oishi, "Accurate sum and dot
+// product", 2005): about twice FP32 precision for the constraint residual,
+// whose terms cancel as the iteration converges.
+__device__ __forceinline__ float residual_c(float ih, float ux, float xl, float uy, float yd, float gb)
+{
+    float e1, e2, e3, e4;
+    const float d1 = two_sum(ux, -xl, e1);
+    const float d2 = two_sum(uy, -yd, e2);
+    const float s = two_sum(d1, d2, e3);
+    const float p = ih * s;
+    const float pe = fmaf(ih, s, -p);
+    const float r = two_sum(p, gb, e4);
+    return r + (e4 + (pe + ih * ((e1 + e2) + e3)));
+}
+
+// Two tagged words (fields 2j and 2j+1 of one point) in one 16-byte access.
+__device__ __forceinline__ void st_tagged2(unsigned long long *p, float v0, float v1, uint32_t tag)
+{
+    const unsigned long long w0 = ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint(v0);
+    const unsigned long long w1 = ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint(v1);
+    asm volatile("st.relaxed.gpu.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(w0), "l"(w1) : "memory");
+}
+
+__device__ __forceinline__ void ld_relaxed64x2(const unsigned long long *p, unsigned long long &w0,
+                                               unsigned long long &w1)
+{
+    asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(w0), "=l"(w1) : "l"(p) : "memory");
+}
+
+// Poll `cnt` tagged words (addresses from `addr(j)`), handing each value to
+// `sink(j, bits)` once its tag matches.  All pending words of a batch are
+// re-read every round.  Returns false on timeout or abort.
+template <int BATCH, typename Addr, typename Sink>
+__device__ __forceinline__ bool poll_words(int cnt, uint32_t tag, ResCtl *ctl, Addr addr, Sink sink)
+{
+    for (int base = 0; base < cnt; base += BATCH) {
+        uint32_t pending = 0;
+#pragma unroll
+        for (int r = 0; r < BATCH; ++r)
+            if (base + r < cnt) pending |= 1u << r;
+        uint64_t t0 = 0;
+        for (uint32_t round = 0; pending; ++round) {
+            unsigned long long v[BATCH];
+#pragma unroll
+            for (int r = 0; r < BATCH; ++r) v[r] = (pending >> r & 1u) ? ld_relaxed64(addr(base + r)) : 0ull;
+#pragma unroll
+            for (int r = 0; r < BATCH; ++r) {
+                if ((pending >> r & 1u) && (uint32_t)(v[r] >> 32) == tag) {
+                    sink(base + r, (uint32_t)v[r]);
+                    pending &= ~(1u << r);
+                }
+            }
+            if (pending && (round & 63u) == 63u) {
+                if (t0 == 0) t0 = global_ns();
+                if (ld_relaxed32(&ctl->abort)) return false;
+                if (global_ns() - t0 > kWaitBudgetNs) {
+                    atomicExch(&ctl->abort, 1u);
+                    atomicExch(&ctl->where, 1u);
+                    return false;
+                }
+            }
+        }
+    }
+    return true;
+}
+
+// Poll `cnt` <= NP2 tagged word pairs (addresses from `addr(j)`) until both
+// tags of every pair match; the values land in vals[2j], vals[2j+1].  Pairs go
+// in batches of up to 8: every round issues the batch's pending loads first
+// (in-order issue would otherwise expose one L2 latency per pair), then checks
+// the tags.  Returns false on timeout or abort.
+template <int NP2, typename Addr>
+__device__ __forceinline__ bool poll_pairs(int cnt, uint32_t tag, ResCtl *ctl, Addr addr, float (&vals)[2 * NP2])
+{
+    constexpr int B = NP2 < 8 ? NP2 : 8;
+#pragma unroll
+    for (int base = 0; base < NP2; base += B) {
+        if (base >= cnt) break;
+        uint32_t pending = 0;
+#pragma unroll
+        for (int j = 0; j < B; ++j)
+            if (base + j < cnt && base + j < NP2) pending |= 1u << j;
+        uint64_t t0 = 0;
+        for (uint32_t round = 0; pending; ++round) {
+            unsigned long long w0[B], w1[B];
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                w0[j] = w1[j] = 0ull;
+                if (pending >> j & 1u) ld_relaxed64x2(addr(base + j), w0[j], w1[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                if ((pending >> j & 1u) && (uint32_t)(w0[j] >> 32) == tag && (uint32_t)(w1[j] >> 32) == tag) {
+                    if (base + j < NP2) {
+                        vals[2 * (base + j)] = __uint_as_float((uint32_t)w0[j]);
+                        vals[2 * (base + j) + 1] = __uint_as_float((uint32_t)w1[j]);
+                    }
+                    pending &= ~(1u << j);
+                }
+            }
+            if (pending && (round & 63u) == 63u) {
+                if (t0 == 0) t0 = global_ns();
+                if (ld_relaxed32(&ctl->abort)) return false;
+                if (global_ns() - t0 > kWaitBudgetNs) {
+                    atomicExch(&ctl->abort, 1u);
+                    atomicExch(&ctl->where, 2u);
+                    return false;
+                }
+            }
+        }
+    }
+    return true;
+}
+
+// ------------------------------------------------------------------ the kernel
+// NM = 1: the norms are the default pair (||u||_{1,2}, ||w||_1), fixed at compile
+// time; NM = 0: the norms are read from the arguments.
+template <int K, int P, int NM>
+__global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
+{
+    constexpr int LKv = LK<K>::v;
+    constexpr int FMAX = 3 * K + LKv;
+    constexpr int F2MAX = (FMAX + 1) / 2;
+    constexpr int KV = kv_of(K);
+    extern __shared__ __align__(16) unsigned char smem[];
+    const ResGeom G = a.geo;
+    const int n = G.n, H = G.H, R = G.R;
+    const size_t nn = (size_t)n * n;
+    const int NT = (int)gridDim.x;
+    const SmemLayout SL = smem_layout(K, G.EWs, G.EHm, NT);
+    double *red = (double *)(smem + SL.red);
+    double *S = (double *)(smem + SL.S);
+    int *dec = (int *)(smem + SL.dec);
+    double *rtab = (double *)(smem + SL.rtab);
+    int *cntR = (int *)(smem + SL.cnt), *cntRp = cntR + (HMAX + 2);
+    float *sphi = (float *)(smem + SL.sphi), *sux = (float *)(smem + SL.sux), *suy = (float *)(smem + SL.suy);
+    float *sdx = (float *)(smem + SL.sdx), *sdy = (float *)(smem + SL.sdy);
+
+    const int tile = blockIdx.x, gx = tile % G.Gx, gy = tile / G.Gx;
+    TileFrame fr;
+    fr.x0 = gx * n / G.Gx;
+    fr.x1 = (gx + 1) * n / G.Gx;
+    fr.y0 = gy * n / G.Gy;
+    fr.y1 = (gy + 1) * n / G.Gy;
+    fr.hL = gx > 0;
+    fr.hR = gx < G.Gx - 1;
+    fr.hD = gy > 0;
+    fr.hU = gy < G.Gy - 1;
+    fr.R = R;
+    const int X0 = fr.x0 - fr.hL * R, Y0 = fr.y0 - fr.hD * R;
+    const int NTILE = (fr.x1 - fr.x0) * (fr.y1 - fr.y0);
+    const int NP = region_count(fr, R);
+    const int RS = G.EWs * KV;             // one row of a shared array, in floats
+
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int k = a.g.k, l = a.g.l, F = 3 * K + l, F2 = (F + 1) / 2;
+    const int un = NM ? (int)VOMT_U_L12 : a.un;
+    const int wn = NM ? (int)VOMT_W_L1 : a.wn;
+    const float mu = a.s.mu, nu = a.s.nu, tau = a.s.tau, ih = a.s.ih, alpha = a.s.alpha;
+    const float muih = mu * ih;
+    const int T = a.max_iters, CE = a.check_every;
+    const size_t TSZ = (size_t)G.TXm * G.TYm;
+    auto xpair = [&](int t_, int par, int j, int ly, int lx) -> unsigned long long * {
+        return a.xch + ((((size_t)t_ * 2 + par) * F2 + j) * TSZ + (size_t)ly * G.TXm + lx) * 2;
+    };
+
+    // ---- owned points: number q = tid + r * nthreads in the tile-then-ring order
+    int pxy[P];               // x | y << 16
+    int sb[P];                // index of the point in the shared arrays
+    int nbf[P];               // 1: x < n-1, 2: y < n-1, 4: x > 0, 8: y > 0
+    bool pv[P], ptile[P], pband[P];
+#pragma unroll
+    for (int r = 0; r < P; ++r) {
+        const int q = tid + r * nthr;
+        int x = fr.x0, y = fr.y0;
+        pv[r] = q < NP && onion_point(fr, q, x, y);
+        ptile[r] = pv[r] && q < NTILE;
+        pxy[r] = x | (y << 16);
+        sb[r] = ((y - Y0) * G.EWs + (x - X0)) * KV;
+        nbf[r] = (x < n - 1 ? 1 : 0) | (y < n - 1 ? 2 : 0) | (x > 0 ? 4 : 0) | (y > 0 ? 8 : 0);
+        pband[r] = ptile[r] && R > 0 &&
+                   ((fr.hL && x - fr.x0 < R) || (fr.hR && fr.x1 - 1 - x < R) || (fr.hD && y - fr.y0 < R) ||
+                    (fr.hU && fr.y1 - 1 - y < R));
+    }
+
+    float ph[P][K], ux[P][K], uy[P][K], bb[P][K], w[P][LKv];
+#pragma unroll
+    for (int r = 0; r < P; ++r) {
+        const int x = pxy[r] & 0xffff, y = pxy[r] >> 16;
+        const size_t p = (size_t)y * n + x;
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            ph[r][c] = ux[r][c] = uy[r][c] = bb[r][c] = 0.0f;
+            if (pv[r]) bb[r][c] = a.rho1[c * nn + p] - a.rho0[c * nn + p];
+            if (ptile[r] && a.warm) {
+                ph[r][c] = a.phi[c * nn + p];
+                ux[r][c] = (x < n - 1) ? a.u[c * nn + p] : 0.0f;
+                uy[r][c] = (y < n - 1) ? a.u[(k + c) * nn + p] : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < LKv; ++e) w[r][e] = (ptile[r] && a.warm && e < l) ? a.w[e * nn + p] : 0.0f;
+    }
+    if (tid == 0) {
+        dec[0] = 0;
+        dec[2] = 0;
+    }
+    if (tid <= R) {
+        cntR[tid] = region_count(fr, tid);
+        cntRp[tid] = region_p_count(fr, tid);
+    }
+    __syncthreads();
+
+    // ---- halo exchange number e: publish the tile's band, receive the ring.  Before
+    // a check, the ring points also record u_new - u_old in sdx / sdy.
+    auto exchange = [&](int e, bool rec_delta) -> bool {
+        const uint32_t tag = (uint32_t)e + 1u;
+        const int par = e & 1;
+#pragma unroll
+        for (int r = 0; r < P; ++r) {
+            if (!pband[r]) continue;
+            const int lx = (pxy[r] & 0xffff) - fr.x0, ly = (pxy[r] >> 16) - fr.y0;
+            float vals[2 * F2MAX];
+#pragma unroll
+            for (int q = 0; q < 2 * F2MAX; ++q) vals[q] = 0.0f;
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                vals[c] = ph[r][c];
+                vals[K + c] = ux[r][c];
+                vals[2 * K + c] = uy[r][c];
+            }
+#pragma unroll
+            for (int e2 = 0; e2 < LKv; ++e2) vals[3 * K + e2] = w[r][e2];
+#pragma unroll
+            for (int j = 0; j < F2MAX; ++j)
+                if (j < F2) st_tagged2(xpair(tile, par, j, ly, lx), vals[2 * j], vals[2 * j + 1], tag);
+        }
+        bool ok = true;
+#pragma unroll
+        for (int r = 0; r < P; ++r) {
+            if (!pv[r] || ptile[r] || !ok) continue;
+            const int x = pxy[r] & 0xffff, y = pxy[r] >> 16;
+            const int sgx = x < fr.x0 ? gx - 1 : (x >= fr.x1 ? gx + 1 : gx);
+            const int sgy = y < fr.y0 ? gy - 1 : (y >= fr.y1 ? gy + 1 : gy);
+            const int src = sgy * G.Gx + sgx;
+            const int slx = x - sgx * n / G.Gx, sly = y - sgy * n / G.Gy;
+            float vals[2 * F2MAX];
+#pragma unroll
+            for (int q = 0; q < 2 * F2MAX; ++q) vals[q] = 0.0f;
+            ok = poll_pairs<F2MAX>(F2, tag, a.ctl, [&](int j) { return xpair(src, par, j, sly, slx); }, vals);
+            if (!ok) continue;
+            if (rec_delta) {
+                float dx[K], dy[K];
+#pragma unroll
+                for (int c = 0; c < K; ++c) {
+                    dx[c] = vals[K + c] - ux[r][c];
+                    dy[c] = vals[2 * K + c] - uy[r][c];
+                }
+                sts<K>(sdx + sb[r], dx);
+                sts<K>(sdy + sb[r], dy);
+            }
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                ph[r][c] = vals[c];
+                ux[r][c] = vals[K + c];
+                uy[r][c] = vals[2 * K + c];
+            }
+#pragma unroll
+            for (int e2 = 0; e2 < LKv; ++e2) w[r][e2] = (e2 < l) ? vals[3 * K + e2] : 0.0f;
+            sts<K>(sphi + sb[r], ph[r]);
+        }
+        return ok;
+    };
+
+    // initial iterate: own phi to shared memory, then the first exchange
+#pragma unroll
+    for (int r = 0; r < P; ++r)
+        if (ptile[r]) sts<K>(sphi + sb[r], ph[r]);
+    if (!exchange(0, false)) dec[0] = 1;
+    __syncthreads();
+    bool aborted = dec[0] != 0;
+    int nexch = 1, checks = 0, t = 0;
+    bool stop = false;
+
+    float dph[P][K], dgw[P][K], racc[P][K];
+#pragma unroll
+    for (int r = 0; r < P; ++r)
+#pragma unroll
+        for (int c = 0; c < K; ++c) { dph[r][c] = 0.0f; dgw[r][c] = 0.0f; racc[r][c] = 0.0f; }
+
+    // ---- one PDHG step on the points q < nRp (phase 1: u, and ubar for the
+    // divergence) and q < nR (w, the commit, phase 2: phi).  LAST: the step
+    // before a check, which also records the increments the check needs.
+    float fdu = 0.0f, fdw = 0.0f;
+    auto step = [&](auto last_tag, int nR, int nRp) {
+        constexpr bool LAST = decltype(last_tag)::value;
+#pragma unroll
+        for (int r = 0; r < P; ++r) {
+            const int q = tid + r * nthr;
+            if (q >= nRp) continue;
+            const int b = sb[r], f = nbf[r];
+            float fx[K], fy[K];
+            lds<K>(sphi + b + ((f & 1) ? KV : 0), fx);
+            lds<K>(sphi + b + ((f & 2) ? RS : 0), fy);
+            float vx[K], vy[K];
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                vx[c] = ux[r][c] + muih * (fx[c] - ph[r][c]);
+                vy[c] = uy[r][c] + muih * (fy[c] - ph[r][c]);
+            }
+            shrink_u<K>(vx, vy, mu, un, a.g.wc);
+            float ubx[K], uby[K];
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                ubx[c] = 2.0f * vx[c] - ux[r][c];
+                uby[c] = 2.0f * vy[c] - uy[r][c];
+            }
+            sts<K>(sux + b, ubx);
+            sts<K>(suy + b, uby);
+            if (q >= nR) continue;
+            float wx[LKv];
+#pragma unroll
+            for (int e = 0; e < LKv; ++e) {
+                float ge = 0.0f;
+#pragma unroll
+                for (int c = 0; c < K; ++c) ge += a.g.G[e][c] * ph[r][c];
+                wx[e] = (e < l) ? w[r][e] + nu * ge : 0.0f;
+            }
+            shrink_w<LKv>(wx, l, alpha * nu, wn, a.g.we);
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                float gw = 0.0f;
+#pragma unroll
+                for (int e = 0; e < LKv; ++e) gw -= a.g.Dv[c][e] * (2.0f * wx[e] - w[r][e]);
+                racc[r][c] = gw + bb[r][c];
+            }
+            if constexpr (LAST) {
+                float dux[K], duy[K];
+#pragma unroll
+                for (int c = 0; c < K; ++c) {
+                    float gd = 0.0f;
+#pragma unroll
+                    for (int e = 0; e < LKv; ++e) gd -= a.g.Dv[c][e] * (wx[e] - w[r][e]);
+                    dgw[r][c] = gd;
+                    dux[c] = vx[c] - ux[r][c];
+                    duy[c] = vy[c] - uy[r][c];
+                    fdu += a.g.wc[c] * (dux[c] * dux[c] + duy[c] * duy[c]);
+                }
+                sts<K>(sdx + b, dux);
+                sts<K>(sdy + b, duy);
+#pragma unroll
+                for (int e = 0; e < LKv; ++e) {
+                    const float dw = wx[e] - w[r][e];
+                    fdw += a.g.we[e] * dw * dw;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                ux[r][c] = vx[c];
+                uy[r][c] = vy[c];
+            }
+#pragma unroll
+            for (int e = 0; e < LKv; ++e) w[r][e] = wx[e];
+        }
+        __syncthreads();
+        // phase 2: phi' = phi + tau (div_x ubar + div_G wbar + rho1 - rho0); the
+        // backward neighbours outside the grid are masked (ubar = 0 there)
+#pragma unroll
+        for (int r = 0; r < P; ++r) {
+            const int q = tid + r * nthr;
+            if (q >= nR) continue;
+            const int b = sb[r], f = nbf[r];
+            float bxo[K], bxl[K], byo[K], byd[K];
+            lds<K>(sux + b, bxo);
+            lds<K>(sux + b - ((f & 4) ? KV : 0), bxl);
+            lds<K>(suy + b, byo);
+            lds<K>(suy + b - ((f & 8) ? RS : 0), byd);
+            const float mx = (f & 4) ? 1.0f : 0.0f, my = (f & 8) ? 1.0f : 0.0f;
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                const float d = ih * ((bxo[c] - mx * bxl[c]) + (byo[c] - my * byd[c])) + racc[r][c];
+                const float np = ph[r][c] + tau * d;
+                if constexpr (LAST) dph[r][c] = np - ph[r][c];
+                ph[r][c] = np;
+            }
+            sts<K>(sphi + b, ph[r]);
+        }
+        __syncthreads();
+    };
+
+    while (!aborted && !stop) {
+        // a block of iterations runs to the next check (or the end) or H iterations
+        int hb = 0;
+        if (T > 0) {
+            const int next_check = ((t / CE) + 1) * CE;
+            hb = H;
+            if (t + hb > next_check) hb = next_check - t;
+            if (t + hb > T) hb = T - t;
+        }
+        const int t_end = t + hb;
+        const bool check_after = (T == 0) || (t_end % CE == 0) || (t_end == T);
+        fdu = 0.0f;
+        fdw = 0.0f;
+        for (int s = 1; s <= hb; ++s) {
+            const int rr = min(hb - s, R);      // ring width of the region this step updates
+            const int nR = cntR[rr], nRp = cntRp[rr];
+            if (s == hb && check_after)
+                step(std::integral_constant<bool, true>(), nR, nRp);
+            else
+                step(std::integral_constant<bool, false>(), nR, nRp);
+        }
+        t = t_end;
+        // ---- refresh the ring (and, before a check, record u_new - u_old on it)
+        if (hb > 0) {
+            if (!exchange(nexch, check_after)) dec[0] = 1;
+            ++nexch;
+            __syncthreads();
+            if (dec[0]) { aborted = true; break; }
+        }
+        if (!check_after) continue;
+
+        // ---- convergence check of the iterate after iteration t
+        if (T == 0) {
+#pragma unroll
+            for (int r = 0; r < P; ++r)
+                if (pv[r]) {
+                    float z[K];
+#pragma unroll
+                    for (int c = 0; c < K; ++c) z[c] = 0.0f;
+                    sts<K>(sdx + sb[r], z);
+                    sts<K>(sdy + sb[r], z);
+                }
+        }
+#pragma unroll
+        for (int r = 0; r < P; ++r)
+            if (pv[r]) {
+                sts<K>(sux + sb[r], ux[r]);
+                sts<K>(suy + sb[r], uy[r]);
+            }
+        __syncthreads();
+        // Per-point terms in FP32, summed over this thread's few points in FP32
+        // and then over the grid in FP64 (FP64 arithmetic is scarce on this GPU).
+        float fs[NRED];
+#pragma unroll
+        for (int q = 0; q < NRED; ++q) fs[q] = 0.0f;
+        fs[RED_DU] = fdu;
+        fs[RED_DW] = fdw;
+#pragma unroll
+        for (int r = 0; r < P; ++r) {
+            if (!ptile[r]) continue;
+            const int b = sb[r], f = nbf[r];
+            const int oxm = (f & 4) ? KV : 0, oym = (f & 8) ? RS : 0;
+            const float mx = (f & 4) ? 1.0f : 0.0f, my = (f & 8) ? 1.0f : 0.0f;
+            float uxl[K], uyd[K], dxo[K], dxl[K], dyo[K], dyd[K], fx[K], fy[K];
+            lds<K>(sux + b - oxm, uxl);
+            lds<K>(suy + b - oym, uyd);
+            lds<K>(sdx + b, dxo);
+            lds<K>(sdx + b - oxm, dxl);
+            lds<K>(sdy + b, dyo);
+            lds<K>(sdy + b - oym, dyd);
+            lds<K>(sphi + b + ((f & 1) ? KV : 0), fx);
+            lds<K>(sphi + b + ((f & 2) ? RS : 0), fy);
+            float nu_pt = 0.0f, dn_u = 0.0f;
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                const float uxc = ux[r][c], uyc = uy[r][c], phc = ph[r][c], bc = bb[r][c], wgt = a.g.wc[c];
+                const float ddiv = ih * ((dxo[c] - mx * dxl[c]) + (dyo[c] - my * dyd[c])) + dgw[r][c];
+                float gwb = bc;
+#pragma unroll
+                for (int e = 0; e < LKv; ++e) gwb -= a.g.Dv[c][e] * w[r][e];
+                const float rc = residual_c(ih, uxc, mx * uxl[c], uyc, my * uyd[c], gwb);
+                fs[RED_RR] += wgt * rc * rc;
+                fs[RED_BB] += wgt * bc * bc;
+                fs[RED_D] += wgt * phc * bc;
+                fs[RED_DP] += wgt * dph[r][c] * dph[r][c];
+                fs[RED_X] += wgt * dph[r][c] * ddiv;
+                const float gxx = ih * (fx[c] - phc), gyy = ih * (fy[c] - phc);
+                if (un == VOMT_U_L12) {
+                    nu_pt += sqrtf(uxc * uxc + uyc * uyc);
+                    dn_u = fmaxf(dn_u, sqrtf(gxx * gxx + gyy * gyy));
+                } else if (un == VOMT_U_L2) {
+                    nu_pt += wgt * (uxc * uxc + uyc * uyc);
+                    dn_u += wgt * (gxx * gxx + gyy * gyy);
+                } else {
+                    nu_pt += wgt * (fabsf(uxc) + fabsf(uyc));
+                    dn_u = fmaxf(dn_u, fmaxf(fabsf(gxx), fabsf(gyy)));
+                }
+            }
+            if (un == VOMT_U_L2) {
+                nu_pt = sqrtf(nu_pt);
+                dn_u = sqrtf(dn_u);
+            }
+            float nw_pt = 0.0f, dn_w = 0.0f;
+#pragma unroll
+            for (int e = 0; e < LKv; ++e) {
+                if (e < l) {
+                    float ge = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < K; ++c) ge += a.g.G[e][c] * ph[r][c];
+                    const float we = w[r][e], wgt = a.g.we[e];
+                    if (wn == VOMT_W_L1) {
+                        nw_pt += wgt * fabsf(we);
+                        dn_w = fmaxf(dn_w, fabsf(ge));
+                    } else {
+                        nw_pt += wgt * we * we;
+                        dn_w += wgt * ge * ge;
+                    }
+                }
+            }
+            if (wn == VOMT_W_L2) {
+                nw_pt = sqrtf(nw_pt);
+                dn_w = sqrtf(dn_w);
+            }
+            fs[RED_P] += nu_pt + alpha * nw_pt;
+            float di = fmaxf(dn_u - 1.0f, 0.0f);
+            if (l > 0) di = fmaxf(di, dn_w - alpha);
+            fs[RED_MAX] = fmaxf(fs[RED_MAX], di);
+        }
+        // block reduction in FP64 (fixed order)
+        double v[NRED];
+#pragma unroll
+        for (int q = 0; q < NRED; ++q) v[q] = (double)fs[q];
+        const int lane = tid & 31, wid = tid >> 5, nw = (nthr + 31) >> 5;
+#pragma unroll
+        for (int q = 0; q < NRED; ++q) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const double o = __shfl_down_sync(0xffffffffu, v[q], off);
+                v[q] = (q == RED_MAX) ? fmax(v[q], o) : v[q] + o;
+            }
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < NRED; ++q) red[wid * NRED + q] = v[q];
+        __syncthreads();
+        const int cpar = checks & 1;
+        const uint32_t ctag = (uint32_t)checks + 1u;
+        const int words = NT * NRED * 2;
+        if (tid < NRED) {
+            double acc = red[tid];
+            for (int q = 1; q < nw; ++q) acc = (tid == RED_MAX) ? fmax(acc, red[q * NRED + tid]) : acc + red[q * NRED + tid];
+            unsigned long long *dst = a.rows + (size_t)cpar * words + ((size_t)tile * NRED + tid) * 2;
+            st_tagged(dst, __int_as_float(__double2hiint(acc)), ctag);
+            st_tagged(dst + 1, __int_as_float(__double2loint(acc)), ctag);
+        }
+        // every block gathers every row (one L2 round trip) ...
+        {
+            const int mine = tid < words ? (words - tid + nthr - 1) / nthr : 0;
+            const bool ok = poll_words<8>(
+                mine, ctag, a.ctl, [&](int j) { return a.rows + (size_t)cpar * words + (size_t)tid + (size_t)j * nthr; },
+                [&](int j, uint32_t bits) {
+                    const int widx = tid + j * nthr;
+                    ((uint32_t *)rtab)[(widx >> 1) * 2 + ((widx & 1) ? 0 : 1)] = bits;
+                });
+            if (!ok) dec[0] = 1;
+        }
+        __syncthreads();
+        if (dec[0]) { aborted = true; break; }
+        // ... and sums them in a fixed order: lane j takes rows j, j + 32, ..., then a
+        // butterfly over the lanes (every lane ends with the same sum, in every block)
+        for (int q = wid; q < NRED; q += nw) {
+            double acc = 0.0;
+            for (int b = lane; b < NT; b += 32) {
+                const double x_ = rtab[b * NRED + q];
+                acc = (q == RED_MAX) ? fmax(acc, x_) : acc + x_;
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const double o = __shfl_xor_sync(0xffffffffu, acc, off);
+                acc = (q == RED_MAX) ? fmax(acc, o) : acc + o;
+            }
+            if (lane == 0) S[q] = acc;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double m[NMET];
+            m[0] = S[RED_P];
+            m[1] = S[RED_D];
+            m[2] = fabs(m[0] - m[1]) / fmax(fabs(m[0]), 1e-300);
+            m[3] = sqrt(S[RED_RR]) / (S[RED_BB] > 0.0 ? sqrt(S[RED_BB]) : 1.0);
+            m[4] = S[RED_DU] / a.cfg.mu + (a.cfg.has_w ? S[RED_DW] / a.cfg.nu : 0.0) + S[RED_DP] / a.cfg.tau -
+                   2.0 * S[RED_X];
+            m[5] = S[RED_MAX];
+            m[6] = (double)t;
+            bool finite = true;
+            for (int q = 0; q < 6; ++q) finite = finite && isfinite(m[q]);
+            const bool conv = a.cfg.tol_gap > 0.0 && m[2] <= a.cfg.tol_gap && m[3] <= a.cfg.tol_res;
+            m[7] = conv ? 1.0 : 0.0;
+            if (tile == 0) {
+                for (int q = 0; q < NMET; ++q) a.st->met[q] = m[q];
+                if (a.hist && checks < a.hist_cap)
+                    for (int q = 0; q < NMET; ++q) a.hist[(size_t)checks * NMET + q] = m[q];
+                a.st->checks = checks + 1;
+                a.st->iter = t;
+                if (!finite) a.st->error = VOMT_ERR_NONFINITE;
+                if (conv || !finite) a.st->stop = 1;
+            }
+            dec[2] = (conv || !finite || t >= T) ? 1 : 0;
+        }
+        __syncthreads();
+        ++checks;
+        stop = dec[2] != 0;
+    }
+    if (aborted) {
+        if (tid == 0 && tile == 0) {
+            a.st->error = VOMT_ERR_BARRIER_TIMEOUT;
+            a.st->stop = 1;
+        }
+        return;
+    }
+    // ---- final iterate of the tile to the caller's arrays
+#pragma unroll
+    for (int r = 0; r < P; ++r) {
+        if (!ptile[r]) continue;
+        const int x = pxy[r] & 0xffff, y = pxy[r] >> 16;
+        const size_t p = (size_t)y * n + x;
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            a.phi[c * nn + p] = ph[r][c];
+            a.u[c * nn + p] = ux[r][c];
+            a.u[(k + c) * nn + p] = uy[r][c];
+        }
+#pragma unroll
+        for (int e = 0; e < LKv; ++e)
+            if (e < l) a.w[e * nn + p] = w[r][e];
+    }
+}
+
+using ResKernel = void (*)(ResArgs);
+
+// Kernel for K channels, P points per thread and the norm mode NM (one per
+// instantiation unit; the host picks through res_kernel).
+template <int K>
+ResKernel kernel_for(int P, int NM)
+{
+    if (NM) return P == 1 ? k_resident<K, 1, 1> : (P == 2 ? k_resident<K, 2, 1> : k_resident<K, 4, 1>);
+    return P == 1 ? k_resident<K, 1, 0> : (P == 2 ? k_resident<K, 2, 0> : k_resident<K, 4, 0>);
+}
+
+ResKernel res_kernel(int K, int P, int NM);
+
+}  // namespace res
+}  // namespace vomt
