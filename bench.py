@@ -322,6 +322,7 @@ def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1712_10279_gb300 as V
     from paper_1712_10279_gb300 import synthetic as S
+    from paper_1712_10279_gb300.replicas import aggregate_throughput
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
@@ -366,13 +367,7 @@ def run_ours(args, rank, world, local_rank):
     total_ms = sum(step_ms)
     gp_it = sum(N * N * r["iters"] for r in results)
     launches = sum(r["launches"] for r in results)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        g = torch.tensor([float(gp_it)], device=dev, dtype=torch.float64)
-        dist.all_reduce(g)
-        gp_it = float(g.item())
+    total_ms, gp_it = aggregate_throughput(total_ms, gp_it, dist, dev)
     value = gp_it / (total_ms / 1e3)
 
     # end to end through the host-buffer entry point: copies inside the timed region
@@ -457,9 +452,8 @@ def main():
     ap.add_argument("--cap", type=int, default=CAP, help="iteration cap per solve (profiler runs only)")
     ap.add_argument("--alphas", type=float, nargs="+", default=list(ALPHAS), help="(profiler runs only)")
     args = ap.parse_args()
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1712_10279_gb300.replicas import rank_world
+    rank, world, local_rank = rank_world()
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -166,6 +166,21 @@ int vomt_solve_host(vomt_ctx *ctx, int n, const float *rho0, const float *rho1,
  * number of rows available, or a negative error. */
 int vomt_history(vomt_ctx *ctx, double *out, int cap);
 
+/* Bounded waits of the resident engine (no counterpart in the paper; a test
+ * and tuning hook).  In the resident engine one thread block waits on another
+ * (halo words, check rows); every such wait gives up after a time limit, then
+ * all blocks return and the solve reports VOMT_ERR_BARRIER_TIMEOUT with the
+ * context still usable (the output arrays are not written).
+ *   budget_ms      limit of one wait in milliseconds; 0 restores the default
+ *                  (2000 ms).
+ *   drop_exchange  > 0: in the following resident solves on ctx, block 0 does
+ *                  not publish halo exchange number drop_exchange, so that its
+ *                  neighbours' waits run out (a message dropped on purpose);
+ *                  0 turns this off.
+ * Applies to later calls on ctx.  Returns VOMT_OK, or VOMT_ERR_BAD_ARG for a
+ * null ctx or a negative or non-finite argument. */
+int vomt_set_wait_policy(vomt_ctx *ctx, double budget_ms, int drop_exchange);
+
 /* ------------------------------------------------------------------------ */
 /* Gradients of the transport cost                                            */
 /* ------------------------------------------------------------------------ */

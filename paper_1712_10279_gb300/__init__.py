@@ -19,7 +19,7 @@ from ._native import VomtError, ENGINES
 U_L12, U_L2, U_L1 = 0, 1, 2
 W_L1, W_L2 = 0, 1
 
-__all__ = ["solve", "solve_host", "step_sizes", "history", "VomtError", "U_L12", "U_L2", "U_L1", "W_L1", "W_L2"]
+__all__ = ["solve", "solve_host", "step_sizes", "history", "set_wait_policy", "VomtError", "U_L12", "U_L2", "U_L1", "W_L1", "W_L2"]
 
 
 @dataclass
@@ -173,6 +173,14 @@ def momt_solve(Lam0, Lam1, L, alpha: float = 1.0, *, tau=None, mu=None, nu=None,
                                    ctypes.byref(res), ctypes.c_void_p(st))
     _native.check(rc, ctx)
     return MatrixSolution(U, W, Phi, res.as_dict())
+
+
+def set_wait_policy(budget_ms: float = 0.0, drop_exchange: int = 0, device: int = 0):
+    """Time limit of the resident engine's waits of one block on another (0: the
+    default, 2 s) and, for tests, a halo exchange that block 0 skips on purpose
+    (0: none); a wait that runs out ends the solve with BARRIER_TIMEOUT."""
+    ctx = _native.context(device)
+    _native.check(_native.load().vomt_set_wait_policy(ctx, float(budget_ms), int(drop_exchange)), ctx)
 
 
 def history(device: int = 0):

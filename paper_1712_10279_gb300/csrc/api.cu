@@ -350,6 +350,16 @@ int vomt_solve_host(vomt_ctx *ctx, int n, const float *rho0, const float *rho1, 
     }
 }
 
+extern "C" int vomt_set_wait_policy(vomt_ctx *ctx, double budget_ms, int drop_exchange)
+{
+    if (!ctx) return VOMT_ERR_BAD_ARG;
+    if (!(budget_ms >= 0.0) || !isfinite(budget_ms) || budget_ms > 3.6e6 || drop_exchange < 0)
+        return fail(ctx, VOMT_ERR_BAD_ARG, "budget_ms must be in [0, 3.6e6] and drop_exchange >= 0");
+    ctx->wait_ns = (unsigned long long)(budget_ms * 1e6);
+    ctx->drop_exchange = drop_exchange;
+    return VOMT_OK;
+}
+
 int vomt_history(vomt_ctx *ctx, double *out, int cap)
 {
     if (!ctx) return VOMT_ERR_BAD_ARG;

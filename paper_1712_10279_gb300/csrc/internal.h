@@ -130,6 +130,9 @@ struct vomt_ctx {
     // resident-engine scratch
     void *rscratch = nullptr;
     size_t rscratch_bytes = 0;
+    // bounded waits of the resident engine: limit (0 = default) and the test hook
+    unsigned long long wait_ns = 0;
+    int drop_exchange = 0;
 };
 
 namespace vomt {

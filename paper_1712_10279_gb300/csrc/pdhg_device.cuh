@@ -132,52 +132,8 @@ struct ResCtl {
     uint32_t where;     // which wait gave up (diagnostics)
 };
 
-constexpr uint64_t kWaitBudgetNs = 2000000000ull;   // 2 s per wait
+constexpr uint64_t kWaitBudgetNs = 2000000000ull;   // default limit of one wait: 2 s
 
-// Spin until *p carries `tag`; returns false (and raises the abort flag) if the
-// wait exceeds its budget or another block already aborted.
-__device__ __forceinline__ bool wait_tagged(const unsigned long long *p, uint32_t tag, float *out, ResCtl *ctl,
-                                            uint32_t where)
-{
-    unsigned long long w = ld_relaxed64(p);
-    if ((uint32_t)(w >> 32) == tag) {
-        *out = __uint_as_float((uint32_t)w);
-        return true;
-    }
-    const uint64_t t0 = global_ns();
-    for (uint32_t polls = 1;; ++polls) {
-        w = ld_relaxed64(p);
-        if ((uint32_t)(w >> 32) == tag) break;
-        if ((polls & 255u) == 0u) {
-            if (ld_relaxed32(&ctl->abort)) return false;
-            if (global_ns() - t0 > kWaitBudgetNs) {
-                atomicExch(&ctl->abort, 1u);
-                atomicExch(&ctl->where, where);
-                return false;
-            }
-        }
-    }
-    *out = __uint_as_float((uint32_t)w);
-    return true;
-}
-
-// Spin until *flag >= v (acquire); false on timeout / abort.
-__device__ __forceinline__ bool wait_flag(const uint32_t *flag, uint32_t v, ResCtl *ctl, uint32_t where)
-{
-    if (ld_acquire32(flag) >= v) return true;
-    const uint64_t t0 = global_ns();
-    for (uint32_t polls = 1;; ++polls) {
-        if (ld_acquire32(flag) >= v) return true;
-        if ((polls & 255u) == 0u) {
-            if (ld_relaxed32(&ctl->abort)) return false;
-            if (global_ns() - t0 > kWaitBudgetNs) {
-                atomicExch(&ctl->abort, 1u);
-                atomicExch(&ctl->where, where);
-                return false;
-            }
-        }
-    }
-}
 
 }  // namespace dev
 }  // namespace vomt

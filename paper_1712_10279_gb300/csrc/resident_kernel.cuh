@@ -92,6 +92,8 @@ struct ResArgs {
     DevStatus *st;
     double *hist;
     int hist_cap;
+    unsigned long long wait_ns;  // time limit of one wait of a block on another
+    int drop_exch;             // > 0: block 0 skips publishing this halo exchange (wait tests)
 };
 
 struct SmemLayout {
@@ -208,9 +210,10 @@ __device__ __forceinline__ void ld_relaxed64x2(const unsigned long long *p, unsi
 
 // Poll `cnt` tagged words (addresses from `addr(j)`), handing each value to
 // `sink(j, bits)` once its tag matches.  All pending words of a batch are
-// re-read every round.  Returns false on timeout or abort.
+// re-read every round.  Returns false once the wait exceeds `budget` ns (raising
+// the abort word) or another block has aborted.
 template <int BATCH, typename Addr, typename Sink>
-__device__ __forceinline__ bool poll_words(int cnt, uint32_t tag, ResCtl *ctl, Addr addr, Sink sink)
+__device__ __forceinline__ bool poll_words(int cnt, uint32_t tag, ResCtl *ctl, uint64_t budget, Addr addr, Sink sink)
 {
     for (int base = 0; base < cnt; base += BATCH) {
         uint32_t pending = 0;
@@ -232,7 +235,7 @@ __device__ __forceinline__ bool poll_words(int cnt, uint32_t tag, ResCtl *ctl, A
             if (pending && (round & 63u) == 63u) {
                 if (t0 == 0) t0 = global_ns();
                 if (ld_relaxed32(&ctl->abort)) return false;
-                if (global_ns() - t0 > kWaitBudgetNs) {
+                if (global_ns() - t0 > budget) {
                     atomicExch(&ctl->abort, 1u);
                     atomicExch(&ctl->where, 1u);
                     return false;
@@ -247,9 +250,10 @@ __device__ __forceinline__ bool poll_words(int cnt, uint32_t tag, ResCtl *ctl, A
 // tags of every pair match; the values land in vals[2j], vals[2j+1].  Pairs go
 // in batches of up to 8: every round issues the batch's pending loads first
 // (in-order issue would otherwise expose one L2 latency per pair), then checks
-// the tags.  Returns false on timeout or abort.
+// the tags.  Returns false on timeout (`budget` ns) or abort.
 template <int NP2, typename Addr>
-__device__ __forceinline__ bool poll_pairs(int cnt, uint32_t tag, ResCtl *ctl, Addr addr, float (&vals)[2 * NP2])
+__device__ __forceinline__ bool poll_pairs(int cnt, uint32_t tag, ResCtl *ctl, uint64_t budget, Addr addr,
+                                           float (&vals)[2 * NP2])
 {
     constexpr int B = NP2 < 8 ? NP2 : 8;
 #pragma unroll
@@ -280,7 +284,7 @@ __device__ __forceinline__ bool poll_pairs(int cnt, uint32_t tag, ResCtl *ctl, A
             if (pending && (round & 63u) == 63u) {
                 if (t0 == 0) t0 = global_ns();
                 if (ld_relaxed32(&ctl->abort)) return false;
-                if (global_ns() - t0 > kWaitBudgetNs) {
+                if (global_ns() - t0 > budget) {
                     atomicExch(&ctl->abort, 1u);
                     atomicExch(&ctl->where, 2u);
                     return false;
@@ -292,8 +296,9 @@ __device__ __forceinline__ bool poll_pairs(int cnt, uint32_t tag, ResCtl *ctl, A
 }
 
 // ------------------------------------------------------------------ the kernel
-// NM = 1: the norms are the default pair (||u||_{1,2}, ||w||_1), fixed at compile
-// time; NM = 0: the norms are read from the arguments.
+// NM = 1: the norms are the vector default pair (||u||_{1,2}, ||w||_1), fixed at
+// compile time; NM = 2: the matrix default pair (||U||_2, ||W||_1); NM = 0: the
+// norms are read from the arguments.
 template <int K, int P, int NM>
 __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
 {
@@ -333,7 +338,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int k = a.g.k, l = a.g.l, F = 3 * K + l, F2 = (F + 1) / 2;
-    const int un = NM ? (int)VOMT_U_L12 : a.un;
+    const int un = NM == 1 ? (int)VOMT_U_L12 : (NM == 2 ? (int)VOMT_U_L2 : a.un);
     const int wn = NM ? (int)VOMT_W_L1 : a.wn;
     const float mu = a.s.mu, nu = a.s.nu, tau = a.s.tau, ih = a.s.ih, alpha = a.s.alpha;
     const float muih = mu * ih;
@@ -395,9 +400,10 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
     auto exchange = [&](int e, bool rec_delta) -> bool {
         const uint32_t tag = (uint32_t)e + 1u;
         const int par = e & 1;
+        const bool publish = !(a.drop_exch > 0 && e == a.drop_exch && tile == 0);
 #pragma unroll
         for (int r = 0; r < P; ++r) {
-            if (!pband[r]) continue;
+            if (!pband[r] || !publish) continue;
             const int lx = (pxy[r] & 0xffff) - fr.x0, ly = (pxy[r] >> 16) - fr.y0;
             float vals[2 * F2MAX];
 #pragma unroll
@@ -426,7 +432,8 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
             float vals[2 * F2MAX];
 #pragma unroll
             for (int q = 0; q < 2 * F2MAX; ++q) vals[q] = 0.0f;
-            ok = poll_pairs<F2MAX>(F2, tag, a.ctl, [&](int j) { return xpair(src, par, j, sly, slx); }, vals);
+            ok = poll_pairs<F2MAX>(F2, tag, a.ctl, a.wait_ns, [&](int j) { return xpair(src, par, j, sly, slx); },
+                                   vals);
             if (!ok) continue;
             if (rec_delta) {
                 float dx[K], dy[K];
@@ -726,7 +733,8 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
         {
             const int mine = tid < words ? (words - tid + nthr - 1) / nthr : 0;
             const bool ok = poll_words<8>(
-                mine, ctag, a.ctl, [&](int j) { return a.rows + (size_t)cpar * words + (size_t)tid + (size_t)j * nthr; },
+                mine, ctag, a.ctl, a.wait_ns,
+                [&](int j) { return a.rows + (size_t)cpar * words + (size_t)tid + (size_t)j * nthr; },
                 [&](int j, uint32_t bits) {
                     const int widx = tid + j * nthr;
                     ((uint32_t *)rtab)[(widx >> 1) * 2 + ((widx & 1) ? 0 : 1)] = bits;
@@ -812,7 +820,10 @@ using ResKernel = void (*)(ResArgs);
 template <int K>
 ResKernel kernel_for(int P, int NM)
 {
-    if (NM) return P == 1 ? k_resident<K, 1, 1> : (P == 2 ? k_resident<K, 2, 1> : k_resident<K, 4, 1>);
+    if constexpr (K == 3 || K == 6) {     // compact 2 x 2 and 3 x 3 matrices
+        if (NM == 2) return P == 1 ? k_resident<K, 1, 2> : (P == 2 ? k_resident<K, 2, 2> : k_resident<K, 4, 2>);
+    }
+    if (NM == 1) return P == 1 ? k_resident<K, 1, 1> : (P == 2 ? k_resident<K, 2, 1> : k_resident<K, 4, 1>);
     return P == 1 ? k_resident<K, 1, 0> : (P == 2 ? k_resident<K, 2, 0> : k_resident<K, 4, 0>);
 }
 

@@ -157,8 +157,12 @@ int resident_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveC
     }
     a.hist = ctx->dhist;
     a.hist_cap = ctx->hist_cap;
+    a.wait_ns = ctx->wait_ns ? ctx->wait_ns : dev::kWaitBudgetNs;
+    a.drop_exch = ctx->drop_exchange;
 
-    const int nm = (p.u_norm == VOMT_U_L12 && p.w_norm == VOMT_W_L1) ? 1 : 0;
+    int nm = 0;
+    if (p.u_norm == VOMT_U_L12 && p.w_norm == VOMT_W_L1) nm = 1;
+    else if (p.u_norm == VOMT_U_L2 && p.w_norm == VOMT_W_L1 && (K == 3 || K == 6)) nm = 2;
     res::ResKernel kern = res::res_kernel(K, plan.P, nm);
     cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SL.total);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "resident smem attribute");
