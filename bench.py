@@ -215,6 +215,7 @@ def extra_batched(dev, cap=5000):
     bt.solve(max_iters=100, check_every=100)
     _, ms_b = _gpu_ms(lambda: bt.solve(max_iters=cap, check_every=CHECK_EVERY, tol_gap=TOL, tol_res=TOL))
     rb = bt.results
+    path = "grouped" if max(r["blocks"] for r in rb) > 1 or rb[0]["halo"] > 0 else "queue"
     d0 = [torch.from_numpy(q["rho0"].astype(np.float32)).to(dev) for q in inst]
     d1 = [torch.from_numpy(q["rho1"].astype(np.float32)).to(dev) for q in inst]
 
@@ -227,7 +228,7 @@ def extra_batched(dev, cap=5000):
     gp_p = sum(q["n"] ** 2 * r["iters"] for q, r in zip(inst, rp))
     return dict(workload="512 instances, n in {32..256}, k in {1,3,5}, random connected graphs p=0.6 (seed 1004), "
                          "alpha=1, to 1e-5 per instance, cap %d" % cap,
-                batched_ms=ms_b, batched_converged=sum(r["status"] == 0 for r in rb),
+                batched_path=path, batched_ms=ms_b, batched_converged=sum(r["status"] == 0 for r in rb),
                 batched_gp_it_per_s=gp_b / (ms_b / 1e3), batched_threads=threads,
                 tune_ms={str(k_): v for k_, v in tune_ms.items()},
                 plain_ms=ms_p, plain_converged=sum(r["status"] == 0 for r in rp),

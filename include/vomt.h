@@ -236,26 +236,39 @@ typedef struct {
  * return the arena size in floats.  Host only. */
 int vomt_batch_layout(int count, vomt_instance *inst, size_t *total_floats);
 
-/* Solve every instance by the iteration of Section 7.2 in one persistent
- * launch: thread blocks take instances from a device queue (largest first) and
- * iterate each to its own stopping point (tolerance or p->max_iters, checked
- * every p->check_every iterations, as in vomt_solve).  mu and nu follow the
- * paper's rule per instance; p->mu, p->nu, p->engine and p->halo are ignored.
- * When `stream` is not the legacy default stream (NULL), the launch (queue
- * reset, kernel, status read-back) is captured into a CUDA graph on the first
- * call and replayed by later calls with the same instances, arena and
- * parameters.  results: host array of `count` (may be NULL).  Returns VOMT_OK,
- * VOMT_NOT_CONVERGED if some instance hit the cap, or the first error (the
- * message names the instance).  The context keeps the scratch (two iterates
- * and b per instance) between calls. */
+/* Solve every instance by the iteration of Section 7.2, each to its own
+ * stopping point (tolerance or p->max_iters, checked every p->check_every
+ * iterations, as in vomt_solve).  mu and nu follow the paper's rule per
+ * instance; p->mu, p->nu and p->halo are ignored.  Two paths:
+ *   one block per instance (p->engine == VOMT_ENGINE_STREAM): one persistent
+ *     launch; thread blocks take instances from a device queue (largest first)
+ *     and run the fused streaming step on each.  When `stream` is not the
+ *     legacy default stream (NULL), the launch (queue reset, kernel, status
+ *     read-back) is captured into a CUDA graph on the first call and replayed
+ *     by later calls with the same instances, arena and parameters.
+ *   grouped (p->engine == VOMT_ENGINE_RESIDENT): instances of equal channel
+ *     count and side form a wave; one cooperative launch per wave splits the
+ *     SMs into groups of T tiles and each group runs the resident algorithm on
+ *     its share of the wave, one instance after another.  Needs k <= 5 and
+ *     p->max_iters < 2^20 - 2 (else VOMT_ERR_TOO_LARGE).
+ * VOMT_ENGINE_AUTO or VOMT_ENGINE_BATCHED: the path vomt_batch_tune found
+ * faster on ctx, else the one a cost model estimates faster.
+ * results: host array of `count` (may be NULL); results[q].blocks is the
+ * number of tiles instance q ran on and .halo its ring width.  Returns
+ * VOMT_OK, VOMT_NOT_CONVERGED if some instance hit the cap, or the first error
+ * (the message names the instance).  The context keeps the scratch between
+ * calls. */
 int vomt_solve_batched(vomt_ctx *ctx, int count, const vomt_instance *inst, float *arena,
                        const vomt_params *p, vomt_result *results, void *stream);
 
-/* Launch-shape tuner of the batched engine: runs the batch for sample_iters
- * iterations (no tolerance) with 128, 256 and 512 threads per block, keeps the
- * fastest for later vomt_solve_batched calls on ctx, and returns it in
- * *best_threads and the three times (milliseconds) in ms[0..2] (either may be
- * NULL).  Overwrites the arena's u, w, phi. */
+/* Tuner of the batched engine: runs the batch for sample_iters iterations (no
+ * tolerance) on the one-block-per-instance path with 128, 256 and 512 threads
+ * per block, and on the grouped path where it applies; keeps the fastest
+ * thread count and the faster path for later vomt_solve_batched calls on ctx
+ * with VOMT_ENGINE_AUTO / VOMT_ENGINE_BATCHED.  Returns the best thread count
+ * in *best_threads and the times (milliseconds) in ms[0..3] (128, 256, 512
+ * threads, then the grouped path or -1); either pointer may be NULL.
+ * Overwrites the arena's u, w, phi. */
 int vomt_batch_tune(vomt_ctx *ctx, int count, const vomt_instance *inst, float *arena,
                     const vomt_params *p, int sample_iters, int *best_threads, double *ms);
 

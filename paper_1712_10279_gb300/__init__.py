@@ -248,11 +248,15 @@ class Batch:
         return self._view(q, 4 * k + l, k)
 
     def solve(self, *, max_iters=2000, check_every=100, tol_gap=0.0, tol_res=0.0, tau=None, u_norm=U_L12,
-              w_norm=W_L1, warm_start=False, stream=None):
-        """One persistent launch over all problems (vomt_solve_batched).  Returns the
-        overall status; per-problem results are in self.results."""
+              w_norm=W_L1, warm_start=False, stream=None, path="auto"):
+        """All problems through vomt_solve_batched.  path: "auto" (the tuned or
+        estimated faster path), "queue" (one thread block per problem, one persistent
+        launch, CUDA-graph captured on a non-default stream) or "grouped" (waves of
+        equal-shape problems, each spread over a group of SMs).  Returns the overall
+        status; per-problem results are in self.results."""
         import torch
-        p = _params(tau, None, None, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, warm_start, "batched")
+        engine = {"auto": "batched", "queue": "stream", "grouped": "resident"}[path]
+        p = _params(tau, None, None, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, warm_start, engine)
         res = (_native.Result * len(self.problems))()
         st = (torch.cuda.current_stream(self.device) if stream is None else stream).cuda_stream
         ctx = _native.context(self.device.index)
@@ -263,16 +267,18 @@ class Batch:
         return rc
 
     def tune(self, sample_iters=50, **kw):
-        """Time 128 / 256 / 512 threads per block on `sample_iters` iterations, keep the
-        fastest on this device's context; returns (best, {threads: ms})."""
+        """Time the one-block-per-problem path with 128 / 256 / 512 threads per block and
+        the grouped path on `sample_iters` iterations; keep the fastest on this device's
+        context.  Returns (best thread count, {128: ms, 256: ms, 512: ms, "grouped": ms
+        or -1 where that path does not apply})."""
         p = _params(kw.get("tau"), None, None, kw.get("u_norm", U_L12), kw.get("w_norm", W_L1), sample_iters,
                     sample_iters, 0.0, 0.0, False, "batched")
         best = ctypes.c_int()
-        ms = (ctypes.c_double * 3)()
+        ms = (ctypes.c_double * 4)()
         ctx = _native.context(self.device.index)
         _native.check(_native.load().vomt_batch_tune(ctx, len(self.problems), self.inst, self.arena.data_ptr(),
                                                      ctypes.byref(p), int(sample_iters), ctypes.byref(best), ms), ctx)
-        return best.value, dict(zip((128, 256, 512), list(ms)))
+        return best.value, dict(zip((128, 256, 512, "grouped"), list(ms)))
 
 
 def set_batch_threads(threads: int, device: int = 0):

@@ -20,6 +20,7 @@
 
 #include "internal.h"
 #include "pdhg_device.cuh"
+#include "resident_kernel.cuh"
 
 namespace vomt {
 namespace {
@@ -394,6 +395,18 @@ struct BatchState {
     cudaStream_t g_stream = nullptr;
     BatchArgs g_args;
     int tuned_threads = 0;
+    int tuned_engine = 0;      // set by vomt_batch_tune: the faster path for AUTO solves (0: by estimate)
+    // grouped path: job tables, exchange scratch, control word, per-problem status
+    void *gjobs = nullptr;
+    size_t gjobs_bytes = 0;
+    void *gvalid = nullptr;
+    size_t gvalid_bytes = 0;
+    void *gscratch = nullptr;
+    size_t gscratch_bytes = 0;
+    void *gstat = nullptr;
+    size_t gstat_bytes = 0;
+    DevStatus *hgstat = nullptr;
+    int hgstat_cap = 0;
 };
 
 void batch_state_free(BatchState *b)
@@ -407,6 +420,11 @@ void batch_state_free(BatchState *b)
     cudaFree(b->dval);
     cudaFree(b->scratch);
     if (b->hstatus) cudaFreeHost(b->hstatus);
+    cudaFree(b->gjobs);
+    cudaFree(b->gvalid);
+    cudaFree(b->gscratch);
+    cudaFree(b->gstat);
+    if (b->hgstat) cudaFreeHost(b->hgstat);
     delete b;
 }
 
@@ -503,6 +521,206 @@ static int batch_prepare(vomt_ctx *ctx, int count, const vomt_instance *inst, co
     return VOMT_OK;
 }
 
+// ------------------------------------------------------------- grouped path
+// Problems with the same channel count and grid side form a wave.  In one
+// cooperative launch per wave the SMs split into groups of T blocks (T tiles of
+// one problem, resident_plan_wave); each group runs the resident algorithm on
+// its share of the wave's problems one after the other, the groups side by
+// side.  A large problem is thus spread over many SMs instead of one, and
+// small problems still fill the GPU.
+struct Wave {
+    int k, n;
+    std::vector<int> insts;
+    ResidentPlan plan;
+    int groups, per;
+};
+
+// The problems the grouped path can take: K <= 5 (grouped kernels exist), a tile
+// plan exists, and tags stay unique (iterations below 2^20 per problem).
+static bool grouped_plan(vomt_ctx *ctx, int count, const std::vector<InstDev> &h, const vomt_params &p,
+                         std::vector<Wave> &waves)
+{
+    waves.clear();
+    if (p.max_iters >= (1 << 20) - 2) return false;
+    std::vector<int> idx(count);
+    for (int q = 0; q < count; ++q) idx[q] = q;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+        return h[a].k != h[b].k ? h[a].k < h[b].k : h[a].n > h[b].n;
+    });
+    for (int q : idx) {
+        if (h[q].k > 5) return false;
+        if (waves.empty() || waves.back().k != h[q].k || waves.back().n != h[q].n) {
+            Wave w;
+            w.k = h[q].k;
+            w.n = h[q].n;
+            waves.push_back(w);
+        }
+        waves.back().insts.push_back(q);
+    }
+    for (Wave &w : waves) {
+        if (!resident_plan_wave(w.n, w.k, (int)w.insts.size(), ctx->sm_count, &w.plan)) return false;
+        const int T = w.plan.Gx * w.plan.Gy;
+        w.groups = std::min((int)w.insts.size(), ctx->sm_count / T);
+        w.per = ((int)w.insts.size() + w.groups - 1) / w.groups;
+        const int nm = (p.u_norm == VOMT_U_L12 && p.w_norm == VOMT_W_L1) ? 1 : 0;
+        if (!res::res_multi_kernel(w.k, w.plan.P, nm)) return false;
+    }
+    return true;
+}
+
+// Estimated time (ns) of the two paths at the iteration cap: the grouped waves
+// by their tile plans; one block per problem by the measured cost of its fused
+// step on one SM (about 14 ns per point and iteration at k = 3, scaled by the
+// bytes per point), limited by the largest problem or the total over the SMs.
+static double grouped_estimate(const std::vector<Wave> &waves, int iters)
+{
+    double t = 0.0;
+    for (const Wave &w : waves) {
+        const double rounds = (double)w.per;
+        t += rounds * w.plan.est_ns * (double)iters * (double)(7 * w.k + w.k * (w.k - 1)) / 27.0 + 20000.0;
+    }
+    return t;
+}
+
+static double queue_estimate(const std::vector<InstDev> &h, int iters, int sms)
+{
+    double total = 0.0, longest = 0.0;
+    for (const InstDev &I : h) {
+        const double c = 14.0 * (double)I.n * I.n * (double)(7 * I.k + 2 * I.l) / 27.0 * (double)iters;
+        total += c;
+        longest = std::max(longest, c);
+    }
+    return std::max(longest, total / sms);
+}
+
+static int grouped_solve(vomt_ctx *ctx, BatchState *b, int count, const std::vector<InstDev> &h, float *arena,
+                         const vomt_params &p, std::vector<Wave> &waves, cudaStream_t st)
+{
+    const int nm = (p.u_norm == VOMT_U_L12 && p.w_norm == VOMT_W_L1) ? 1 : 0;
+    // scratch: per wave, per group two job slots of exchange words and check rows
+    size_t jobs_total = 0, scratch_words = 0;
+    for (const Wave &w : waves) {
+        const int T = w.plan.Gx * w.plan.Gy;
+        const int F2 = (3 * w.k + w.k * (w.k - 1) / 2 + 1) / 2;
+        const size_t xw = (size_t)T * 2 * F2 * w.plan.TXm * w.plan.TYm * 2;
+        const size_t rw = (size_t)2 * T * NRED * 2;
+        scratch_words = std::max(scratch_words, (size_t)w.groups * 2 * (xw + rw));
+        jobs_total += (size_t)w.groups * w.per;
+    }
+    const size_t ctl_bytes = 256;
+    int rc = ensure_buffer(ctx, &b->gjobs, &b->gjobs_bytes, sizeof(res::ResArgs) * jobs_total, "grouped jobs");
+    if (!rc) rc = ensure_buffer(ctx, &b->gvalid, &b->gvalid_bytes, sizeof(int) * jobs_total, "grouped jobs");
+    if (!rc) rc = ensure_buffer(ctx, &b->gscratch, &b->gscratch_bytes, scratch_words * 8 + ctl_bytes, "grouped scratch");
+    if (!rc) rc = ensure_buffer(ctx, &b->gstat, &b->gstat_bytes, sizeof(DevStatus) * count, "grouped status");
+    if (rc) return rc;
+    if (b->hgstat_cap < count) {
+        if (b->hgstat) cudaFreeHost(b->hgstat);
+        b->hgstat = nullptr;
+        b->hgstat_cap = 0;
+        cudaError_t e = cudaMallocHost(&b->hgstat, sizeof(DevStatus) * count);
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "grouped status");
+        b->hgstat_cap = count;
+    }
+    unsigned long long *xbase = (unsigned long long *)b->gscratch;
+    dev::ResCtl *ctl = (dev::ResCtl *)((unsigned char *)b->gscratch + scratch_words * 8);
+    DevStatus *dstat = (DevStatus *)b->gstat;
+    std::vector<res::ResArgs> jobs(jobs_total);
+    std::vector<int> valid(jobs_total, 0);
+    size_t jbase = 0;
+    std::vector<size_t> wave_job0(waves.size());
+    for (size_t wi = 0; wi < waves.size(); ++wi) {
+        const Wave &w = waves[wi];
+        wave_job0[wi] = jbase;
+        const ResidentPlan &pl = w.plan;
+        const int T = pl.Gx * pl.Gy;
+        const int F2 = (3 * w.k + w.k * (w.k - 1) / 2 + 1) / 2;
+        const size_t xw = (size_t)T * 2 * F2 * pl.TXm * pl.TYm * 2;
+        const size_t rw = (size_t)2 * T * NRED * 2;
+        const int EWm = pl.TXm + 2 * pl.H, EHm = pl.TYm + 2 * pl.H;
+        for (size_t i = 0; i < w.insts.size(); ++i) {
+            const int q = w.insts[i];
+            const InstDev &I = h[q];
+            const int g = (int)(i % w.groups), j = (int)(i / w.groups);
+            res::ResArgs &a = jobs[jbase + (size_t)g * w.per + j];
+            memset(&a, 0, sizeof a);
+            a.geo = res::ResGeom{I.n, pl.Gx, pl.Gy, pl.TXm, pl.TYm, T == 1 ? (1 << 30) : pl.H, T == 1 ? 0 : pl.H,
+                                 res::row_stride(EWm), EHm};
+            a.g.k = I.k;
+            a.g.l = I.l;
+            memcpy(a.g.wc, I.wc, sizeof I.wc);
+            memcpy(a.g.we, I.we, sizeof I.we);
+            memcpy(a.g.G, I.G, sizeof I.G);
+            memcpy(a.g.Dv, I.Dv, sizeof I.Dv);
+            a.s = StepDev{I.n, I.ih, I.mu, I.nu, I.tau, I.alpha};
+            a.cfg = SolveCfg{p.tol_gap, p.tol_res, I.mu_d, I.nu_d, I.tau_d, I.l > 0 ? 1 : 0};
+            a.un = p.u_norm;
+            a.wn = p.w_norm;
+            a.max_iters = p.max_iters;
+            a.check_every = p.check_every;
+            a.warm = p.warm_start;
+            a.rho0 = arena + I.o_rho0;
+            a.rho1 = arena + I.o_rho1;
+            a.u = arena + I.o_u;
+            a.w = arena + I.o_w;
+            a.phi = arena + I.o_phi;
+            unsigned long long *slot = xbase + ((size_t)g * 2 + (j & 1)) * (xw + rw);
+            a.xch = slot;
+            a.rows = slot + xw;
+            a.ctl = ctl;
+            a.st = dstat + q;
+            a.hist = nullptr;
+            a.hist_cap = 0;
+            a.wait_ns = ctx->wait_ns ? ctx->wait_ns : dev::kWaitBudgetNs;
+            a.drop_exch = ctx->drop_exchange;
+            a.tag_hi = (uint32_t)(q % 4095 + 1) << 20;
+            valid[jbase + (size_t)g * w.per + j] = 1;
+        }
+        jbase += (size_t)w.groups * w.per;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->gjobs, jobs.data(), sizeof(res::ResArgs) * jobs_total, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->gvalid, valid.data(), sizeof(int) * jobs_total, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dstat, 0, sizeof(DevStatus) * count, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, ctl_bytes, st);
+    if (e != cudaSuccess) return set_cuda_error(ctx, e, "grouped setup");
+    for (size_t wi = 0; wi < waves.size(); ++wi) {
+        const Wave &w = waves[wi];
+        const ResidentPlan &pl = w.plan;
+        const int T = pl.Gx * pl.Gy;
+        const int EWm = pl.TXm + 2 * pl.H, EHm = pl.TYm + 2 * pl.H;
+        const res::SmemLayout SL = res::smem_layout(w.k, res::row_stride(EWm), EHm, T);
+        res::MultiKernel kern = res::res_multi_kernel(w.k, pl.P, nm);
+        e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SL.total);
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "grouped smem attribute");
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)kern, pl.threads, SL.total);
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "grouped occupancy");
+        const int blocks = w.groups * T;
+        if (per_sm < 1 || blocks > per_sm * ctx->sm_count) {
+            ctx->err = "grouped wave does not fit on the device";
+            return VOMT_ERR_TOO_LARGE;
+        }
+        // exchange words of an earlier wave must not match this wave's tags
+        e = cudaMemsetAsync(b->gscratch, 0, (size_t)w.groups * 2 *
+                                                ((size_t)T * 2 * ((3 * w.k + w.k * (w.k - 1) / 2 + 1) / 2) * pl.TXm * pl.TYm * 2 +
+                                                 (size_t)2 * T * NRED * 2) * 8, st);
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "grouped reset");
+        res::MultiArgs m;
+        m.jobs = (const res::ResArgs *)b->gjobs + wave_job0[wi];
+        m.valid = (const int *)b->gvalid + wave_job0[wi];
+        m.per = w.per;
+        m.T = T;
+        m.ctl = ctl;
+        void *args[] = {&m};
+        e = cudaLaunchCooperativeKernel((const void *)kern, dim3(blocks), dim3(pl.threads), args, SL.total, st);
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "grouped launch");
+        ++ctx->launches;
+    }
+    e = cudaMemcpyAsync(b->hgstat, dstat, sizeof(DevStatus) * count, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return set_cuda_error(ctx, e, "grouped solve");
+    return VOMT_OK;
+}
+
 extern "C" int vomt_solve_batched(vomt_ctx *ctx, int count, const vomt_instance *inst, float *arena,
                                   const vomt_params *pin, vomt_result *results, void *stream)
 {
@@ -561,6 +779,53 @@ extern "C" int vomt_solve_batched(vomt_ctx *ctx, int count, const vomt_instance 
             else if (h[2] < 0.0 || h[3] < 0.0) { code = VOMT_ERR_NEGATIVE_DENSITY; snprintf(buf, sizeof buf, "instance %d: negative density", q); }
             else if (fabs(h[0] - h[1]) > 1e-5 * fmax(fabs(h[0]), fabs(h[1]))) { code = VOMT_ERR_MASS_MISMATCH; snprintf(buf, sizeof buf, "instance %d: different total mass", q); }
             if (code) return fail(ctx, code, buf);
+        }
+        // path: grouped resident waves, or one block per problem from a queue
+        std::vector<Wave> waves;
+        bool grouped = false;
+        if (p.engine == VOMT_ENGINE_RESIDENT) {
+            if (!grouped_plan(ctx, count, hinst, p, waves))
+                return fail(ctx, VOMT_ERR_TOO_LARGE,
+                            "grouped batch path needs k <= 5, a resident tile plan and max_iters < 2^20 - 2");
+            grouped = true;
+        } else if (p.engine == VOMT_ENGINE_AUTO || p.engine == VOMT_ENGINE_BATCHED) {
+            if (b->tuned_engine == VOMT_ENGINE_RESIDENT)
+                grouped = grouped_plan(ctx, count, hinst, p, waves);
+            else if (b->tuned_engine == 0)
+                grouped = grouped_plan(ctx, count, hinst, p, waves) &&
+                          grouped_estimate(waves, std::max(p.max_iters, 1)) <
+                              queue_estimate(hinst, std::max(p.max_iters, 1), ctx->sm_count);
+        }
+        if (grouped) {
+            rc = grouped_solve(ctx, b, count, hinst, arena, p, waves, st);
+            if (rc) return rc;
+            std::vector<int> tiles(count, 1), halo(count, 0);
+            for (const Wave &w : waves)
+                for (int q : w.insts) {
+                    tiles[q] = w.plan.Gx * w.plan.Gy;
+                    halo[q] = tiles[q] > 1 ? w.plan.H : 0;
+                }
+            int status = VOMT_OK;
+            for (int q = 0; q < count; ++q) {
+                const DevStatus &h = b->hgstat[q];
+                int s_ = VOMT_OK;
+                if (h.error) s_ = h.error;
+                else if (h.checks == 0) s_ = VOMT_ERR_BARRIER_TIMEOUT;       // never started: the launch aborted
+                else if (p.tol_gap > 0.0 && h.met[7] == 0.0) s_ = VOMT_NOT_CONVERGED;
+                if (s_ < 0 && status >= 0) status = s_;
+                else if (s_ == VOMT_NOT_CONVERGED && status == VOMT_OK) status = s_;
+                if (results) {
+                    vomt_result &r = results[q];
+                    r.primal = h.met[0]; r.dual = h.met[1]; r.rel_gap = h.met[2]; r.rel_res = h.met[3];
+                    r.fp_resid = h.met[4]; r.dual_infeas = h.met[5];
+                    r.mu = hinst[q].mu_d; r.nu = hinst[q].nu_d; r.tau = hinst[q].tau_d;
+                    r.iters = h.iter; r.status = s_; r.engine = VOMT_ENGINE_BATCHED; r.checks = h.checks;
+                    r.launches = ctx->launches; r.blocks = tiles[q]; r.halo = halo[q];
+                }
+            }
+            if (status < 0) ctx->err = status == VOMT_ERR_BARRIER_TIMEOUT ? "device wait timed out"
+                                                                          : "a problem produced a non-finite iterate";
+            return status;
         }
         // launch shape: the tuned block size, as many resident blocks as fit, at most one per instance
         const int threads = b->tuned_threads > 0 ? b->tuned_threads : 256;
@@ -633,7 +898,7 @@ extern "C" int vomt_solve_batched(vomt_ctx *ctx, int count, const vomt_instance 
                 r.fp_resid = h.met[4]; r.dual_infeas = h.met[5];
                 r.mu = hinst[q].mu_d; r.nu = hinst[q].nu_d; r.tau = hinst[q].tau_d;
                 r.iters = h.iter; r.status = s_; r.engine = VOMT_ENGINE_BATCHED; r.checks = h.checks;
-                r.launches = ctx->launches;
+                r.launches = ctx->launches; r.blocks = 1; r.halo = 0;
             }
         }
         if (status < 0) ctx->err = "an instance produced a non-finite iterate";
@@ -657,31 +922,58 @@ extern "C" int vomt_batch_tune(vomt_ctx *ctx, int count, const vomt_instance *in
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "cudaSetDevice");
     if (!ctx->batch) ctx->batch = new BatchState();
-    const int cands[3] = {128, 256, 512};
-    double best = 1e300;
-    int pick = 256;
-    for (int c = 0; c < 3; ++c) {
-        ctx->batch->tuned_threads = cands[c];
-        // one untimed pass (table upload, graph capture), then a timed pass
-        int rc = vomt_solve_batched(ctx, count, inst, arena, &p, nullptr, nullptr);
+    BatchState *b = ctx->batch;
+    // time one pass of each candidate (after an untimed pass: table upload, graph capture)
+    auto timed = [&](vomt_params q, double *out) -> int {
+        int rc = vomt_solve_batched(ctx, count, inst, arena, &q, nullptr, nullptr);
         if (rc < 0) return rc;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         cudaEventRecord(e0, nullptr);
-        rc = vomt_solve_batched(ctx, count, inst, arena, &p, nullptr, nullptr);
+        rc = vomt_solve_batched(ctx, count, inst, arena, &q, nullptr, nullptr);
         cudaEventRecord(e1, nullptr);
         cudaEventSynchronize(e1);
         float t = 0.0f;
         cudaEventElapsedTime(&t, e0, e1);
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        *out = t;
+        return rc < 0 ? rc : VOMT_OK;
+    };
+    const int cands[3] = {128, 256, 512};
+    double best = 1e300;
+    int pick = 256;
+    vomt_params q = p;
+    q.engine = VOMT_ENGINE_STREAM;          // one block per problem
+    for (int c = 0; c < 3; ++c) {
+        b->tuned_threads = cands[c];
+        double t = 0.0;
+        int rc = timed(q, &t);
         if (rc < 0) return rc;
         if (ms) ms[c] = t;
         if (t < best) { best = t; pick = cands[c]; }
     }
-    ctx->batch->tuned_threads = pick;
+    b->tuned_threads = pick;
     if (best_threads) *best_threads = pick;
+    // the grouped resident path, where it can take the problems
+    b->tuned_engine = VOMT_ENGINE_STREAM;
+    if (ms) ms[3] = -1.0;
+    std::vector<InstDev> hinst;
+    std::vector<int> order;
+    size_t sfl = 0;
+    int bad = -1;
+    std::vector<Wave> waves;
+    if (batch_prepare(ctx, count, inst, p, hinst, order, &sfl, &bad) == VOMT_OK &&
+        grouped_plan(ctx, count, hinst, p, waves)) {
+        q.engine = VOMT_ENGINE_RESIDENT;
+        double t = 0.0;
+        int rc = timed(q, &t);
+        if (rc < 0) return rc;
+        if (ms) ms[3] = t;
+        if (t < best) b->tuned_engine = VOMT_ENGINE_RESIDENT;
+    }
+    ctx->err.clear();
     return VOMT_OK;
 }
 

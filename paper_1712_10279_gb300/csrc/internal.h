@@ -156,6 +156,7 @@ struct ResidentPlan {
     double est_ns;
 };
 bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out);
+bool resident_plan_wave(int n, int k, int count, int max_blocks, ResidentPlan *out);
 int resident_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg &cfg, const vomt_params &p,
                    const ResidentPlan &plan, const float *rho0, const float *rho1, float *u, float *w, float *phi,
                    cudaStream_t st);

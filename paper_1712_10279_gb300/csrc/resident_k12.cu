@@ -1,4 +1,4 @@
-// Instantiations of the resident kernel for K in {1, 2} channels (compiled apart
+// Instantiations of the resident kernels for K in {1, 2} channels (compiled apart
 // from the other channel counts so that the units build in parallel).
 #include "resident_kernel.cuh"
 
@@ -9,6 +9,13 @@ ResKernel res_kernel_k12(int K, int P, int NM)
 {
     if (K == 1) return kernel_for<1>(P, NM);
     if (K == 2) return kernel_for<2>(P, NM);
+    return nullptr;
+}
+
+MultiKernel res_multi_kernel_k12(int K, int P, int NM)
+{
+    if (K == 1) return multi_kernel_for<1>(P, NM);
+    if (K == 2) return multi_kernel_for<2>(P, NM);
     return nullptr;
 }
 

@@ -1,4 +1,4 @@
-// Instantiations of the resident kernel for K in {6} channels (compiled apart
+// Instantiations of the resident kernels for K in {6} channels (compiled apart
 // from the other channel counts so that the units build in parallel).
 #include "resident_kernel.cuh"
 
@@ -8,6 +8,12 @@ namespace res {
 ResKernel res_kernel_k6(int K, int P, int NM)
 {
     if (K == 6) return kernel_for<6>(P, NM);
+    return nullptr;
+}
+
+MultiKernel res_multi_kernel_k6(int K, int P, int NM)
+{
+    if (K == 6) return multi_kernel_for<6>(P, NM);
     return nullptr;
 }
 

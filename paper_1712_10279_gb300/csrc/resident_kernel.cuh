@@ -94,6 +94,7 @@ struct ResArgs {
     int hist_cap;
     unsigned long long wait_ns;  // time limit of one wait of a block on another
     int drop_exch;             // > 0: block 0 skips publishing this halo exchange (wait tests)
+    uint32_t tag_hi;           // added to every tag of a grouped job: (instance + 1) << 20
 };
 
 struct SmemLayout {
@@ -300,7 +301,7 @@ __device__ __forceinline__ bool poll_pairs(int cnt, uint32_t tag, ResCtl *ctl, u
 // compile time; NM = 2: the matrix default pair (||U||_2, ||W||_1); NM = 0: the
 // norms are read from the arguments.
 template <int K, int P, int NM>
-__global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
+__device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, const int NT, const uint32_t tag_hi)
 {
     constexpr int LKv = LK<K>::v;
     constexpr int FMAX = 3 * K + LKv;
@@ -310,7 +311,6 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
     const ResGeom G = a.geo;
     const int n = G.n, H = G.H, R = G.R;
     const size_t nn = (size_t)n * n;
-    const int NT = (int)gridDim.x;
     const SmemLayout SL = smem_layout(K, G.EWs, G.EHm, NT);
     double *red = (double *)(smem + SL.red);
     double *S = (double *)(smem + SL.S);
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
     float *sphi = (float *)(smem + SL.sphi), *sux = (float *)(smem + SL.sux), *suy = (float *)(smem + SL.suy);
     float *sdx = (float *)(smem + SL.sdx), *sdy = (float *)(smem + SL.sdy);
 
-    const int tile = blockIdx.x, gx = tile % G.Gx, gy = tile / G.Gx;
+    const int gx = tile % G.Gx, gy = tile / G.Gx;
     TileFrame fr;
     fr.x0 = gx * n / G.Gx;
     fr.x1 = (gx + 1) * n / G.Gx;
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
     // ---- halo exchange number e: publish the tile's band, receive the ring.  Before
     // a check, the ring points also record u_new - u_old in sdx / sdy.
     auto exchange = [&](int e, bool rec_delta) -> bool {
-        const uint32_t tag = (uint32_t)e + 1u;
+        const uint32_t tag = tag_hi + (uint32_t)e + 1u;
         const int par = e & 1;
         const bool publish = !(a.drop_exch > 0 && e == a.drop_exch && tile == 0);
 #pragma unroll
@@ -720,7 +720,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
             for (int q = 0; q < NRED; ++q) red[wid * NRED + q] = v[q];
         __syncthreads();
         const int cpar = checks & 1;
-        const uint32_t ctag = (uint32_t)checks + 1u;
+        const uint32_t ctag = tag_hi + (uint32_t)checks + 1u;
         const int words = NT * NRED * 2;
         if (tid < NRED) {
             double acc = red[tid];
@@ -813,7 +813,45 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_resident(ResArgs a)
     }
 }
 
+// One problem: the grid is its tiles.
+template <int K, int P, int NM>
+__global__ void __launch_bounds__(RES_THREADS, 1) k_resident(const __grid_constant__ ResArgs a)
+{
+    resident_body<K, P, NM>(a, (int)blockIdx.x, (int)gridDim.x, 0u);
+}
+
+// Many problems of one shape (grouped batch): the grid is `groups` groups of T
+// blocks; group g solves the problems of its job list one after the other, each
+// on its T tiles.  A job's arguments (problem, exchange region, status) are
+// copied to shared memory before the group starts it.  Consecutive jobs of a
+// group use alternate exchange regions and distinct tag prefixes, so no block
+// can mistake a word of the previous problem for one of the current problem.
+struct MultiArgs {
+    const ResArgs *jobs;       // [groups][per] arguments of each job
+    const int *valid;          // [groups][per] 1 where the job exists
+    int per, T;
+    ResCtl *ctl;
+};
+
+template <int K, int P, int NM>
+__global__ void __launch_bounds__(RES_THREADS, 1) k_resident_multi(const __grid_constant__ MultiArgs m)
+{
+    __shared__ __align__(16) ResArgs sa;
+    const int g = (int)blockIdx.x / m.T, t = (int)blockIdx.x % m.T;
+    for (int j = 0; j < m.per; ++j) {
+        if (!m.valid[g * m.per + j]) break;
+        const int *src = reinterpret_cast<const int *>(&m.jobs[(size_t)g * m.per + j]);
+        for (int q = threadIdx.x; q < (int)(sizeof(ResArgs) / sizeof(int)); q += blockDim.x)
+            reinterpret_cast<int *>(&sa)[q] = src[q];
+        __syncthreads();
+        resident_body<K, P, NM>(sa, t, m.T, sa.tag_hi);
+        __syncthreads();
+        if (ld_relaxed32(&m.ctl->abort)) break;
+    }
+}
+
 using ResKernel = void (*)(ResArgs);
+using MultiKernel = void (*)(MultiArgs);
 
 // Kernel for K channels, P points per thread and the norm mode NM (one per
 // instantiation unit; the host picks through res_kernel).
@@ -827,7 +865,25 @@ ResKernel kernel_for(int P, int NM)
     return P == 1 ? k_resident<K, 1, 0> : (P == 2 ? k_resident<K, 2, 0> : k_resident<K, 4, 0>);
 }
 
+// Grouped-batch kernel for K <= 5 channels, P in {2, 4}, NM in {0, 1}; nullptr otherwise.
+template <int K>
+MultiKernel multi_kernel_for(int P, int NM)
+{
+    if constexpr (K <= 5) {
+        if (NM == 1) return P == 2 ? k_resident_multi<K, 2, 1> : k_resident_multi<K, 4, 1>;
+        return P == 2 ? k_resident_multi<K, 2, 0> : k_resident_multi<K, 4, 0>;
+    } else {
+        (void)P;
+        (void)NM;
+        return nullptr;
+    }
+}
+
 ResKernel res_kernel(int K, int P, int NM);
+MultiKernel res_multi_kernel(int K, int P, int NM);
+
+// Shared memory of the grouped kernel beyond the dynamic layout (the job copy).
+constexpr int MULTI_STATIC_SMEM = (int)((sizeof(ResArgs) + 15) / 16 * 16);
 
 }  // namespace res
 }  // namespace vomt

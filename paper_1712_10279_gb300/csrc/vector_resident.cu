@@ -4,6 +4,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "internal.h"
 #include "resident_kernel.cuh"
 
@@ -15,6 +17,11 @@ ResKernel res_kernel_k3(int K, int P, int NM);
 ResKernel res_kernel_k45(int K, int P, int NM);
 ResKernel res_kernel_k6(int K, int P, int NM);
 ResKernel res_kernel_k78(int K, int P, int NM);
+MultiKernel res_multi_kernel_k12(int K, int P, int NM);
+MultiKernel res_multi_kernel_k3(int K, int P, int NM);
+MultiKernel res_multi_kernel_k45(int K, int P, int NM);
+MultiKernel res_multi_kernel_k6(int K, int P, int NM);
+MultiKernel res_multi_kernel_k78(int K, int P, int NM);
 
 ResKernel res_kernel(int K, int P, int NM)
 {
@@ -23,6 +30,15 @@ ResKernel res_kernel(int K, int P, int NM)
     if (K <= 5) return res_kernel_k45(K, P, NM);
     if (K == 6) return res_kernel_k6(K, P, NM);
     return res_kernel_k78(K, P, NM);
+}
+
+MultiKernel res_multi_kernel(int K, int P, int NM)
+{
+    if (K <= 2) return res_multi_kernel_k12(K, P, NM);
+    if (K == 3) return res_multi_kernel_k3(K, P, NM);
+    if (K <= 5) return res_multi_kernel_k45(K, P, NM);
+    if (K == 6) return res_multi_kernel_k6(K, P, NM);
+    return res_multi_kernel_k78(K, P, NM);
 }
 
 }  // namespace res
@@ -105,6 +121,54 @@ bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out)
     return true;
 }
 
+// Tile plan for a wave of `count` problems of side n on `max_blocks` SMs (the
+// grouped batch): each problem gets T = Gx x Gy tiles, floor(max_blocks / T)
+// problems run side by side, and the plan minimises the estimated time of the
+// whole wave (rounds of side-by-side problems x time per iteration of one).
+// Same tile rules as resident_plan; P is 2 or 4 (the grouped kernels).
+bool resident_plan_wave(int n, int k, int count, int max_blocks, ResidentPlan *out)
+{
+    auto smem_ok = [&](int EW, int EH, int G) {
+        return res::smem_layout(k, res::row_stride(EW), EH, G).total <= SMEM_MAX - res::MULTI_STATIC_SMEM;
+    };
+    double best = -1.0;
+    for (int Gx = 1; Gx <= n && Gx <= max_blocks; ++Gx) {
+        const int TX = (n + Gx - 1) / Gx, TXmin = n / Gx;
+        if (TX > TMAX) continue;
+        for (int Gy = 1; Gy <= n && Gx * Gy <= max_blocks; ++Gy) {
+            const int TY = (n + Gy - 1) / Gy, TYmin = n / Gy;
+            if (TY > TMAX) continue;
+            const int G = Gx * Gy;
+            const int side = std::min(count, max_blocks / G);
+            const double rounds = (double)((count + side - 1) / side);
+            if (G == 1) {
+                if (TX * TY > RES_MAX_POINTS || !smem_ok(TX, TY, 1)) continue;
+                const double cost = rounds * plan_cost(TX, TY, 0, 1);
+                if (best < 0 || cost < best) {
+                    best = cost;
+                    *out = ResidentPlan{Gx, Gy, TX, TY, 0, 0, 0, cost};
+                }
+                continue;
+            }
+            for (int H = 1; H <= HMAX; ++H) {
+                if (H > TXmin || H > TYmin) break;
+                const int EW = TX + 2 * H, EH = TY + 2 * H;
+                if (EW * EH > RES_MAX_POINTS || !smem_ok(EW, EH, G)) break;
+                const double cost = rounds * plan_cost(TX, TY, H, G);
+                if (best < 0 || cost < best) {
+                    best = cost;
+                    *out = ResidentPlan{Gx, Gy, TX, TY, H, 0, 0, cost};
+                }
+            }
+        }
+    }
+    if (best < 0) return false;
+    const int ext = (out->TXm + 2 * out->H) * (out->TYm + 2 * out->H);
+    out->P = ext <= 2 * RES_THREADS ? 2 : 4;
+    out->threads = (((ext + out->P - 1) / out->P + 31) / 32) * 32;
+    return true;
+}
+
 int resident_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg &cfg, const vomt_params &p,
                    const ResidentPlan &plan, const float *rho0, const float *rho1, float *u, float *w, float *phi,
                    cudaStream_t st)
@@ -159,6 +223,7 @@ int resident_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveC
     a.hist_cap = ctx->hist_cap;
     a.wait_ns = ctx->wait_ns ? ctx->wait_ns : dev::kWaitBudgetNs;
     a.drop_exch = ctx->drop_exchange;
+    a.tag_hi = 0u;
 
     int nm = 0;
     if (p.u_norm == VOMT_U_L12 && p.w_norm == VOMT_W_L1) nm = 1;

@@ -57,21 +57,26 @@ def _check_against_oracle(B, probs, r0s, r1s, **kw):
             assert res["primal"] == 0.0
 
 
-def test_batched_mixed_problems_match_oracle():
+PATHS = ["queue", "grouped"]
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_batched_mixed_problems_match_oracle(path):
     _dev()
     probs, r0s, r1s = _mixed(24, seed=1)
     B = V.Batch(probs, r0s, r1s)
-    rc = B.solve(max_iters=300, check_every=100)
+    rc = B.solve(max_iters=300, check_every=100, path=path)
     assert rc == 0
     assert all(r["engine"] == "batched" for r in B.results)
     _check_against_oracle(B, probs, r0s, r1s, max_iters=300, check_every=100)
 
 
-def test_batched_per_instance_stopping():
+@pytest.mark.parametrize("path", PATHS)
+def test_batched_per_instance_stopping(path):
     _dev()
     probs, r0s, r1s = _mixed(10, seed=2, sides=(12, 20, 28), ks=(1, 3))
     B = V.Batch(probs, r0s, r1s)
-    B.solve(max_iters=20000, check_every=100, tol_gap=5e-3, tol_res=5e-3)
+    B.solve(max_iters=20000, check_every=100, tol_gap=5e-3, tol_res=5e-3, path=path)
     for q, p in enumerate(probs):
         ref = oracle.vomt_solve(r0s[q].astype(np.float64), r1s[q].astype(np.float64), p["edges"], p["alpha"],
                                 max_iters=20000, check_every=100, tol_gap=5e-3, tol_res=5e-3)
@@ -88,18 +93,19 @@ def test_batched_graph_replay_and_tuner():
     probs, r0s, r1s = _mixed(12, seed=3)
     B = V.Batch(probs, r0s, r1s)
     s = torch.cuda.Stream(device=d)
-    B.solve(max_iters=200, check_every=50, stream=s)          # captured
+    B.solve(max_iters=200, check_every=50, stream=s, path="queue")          # captured
     first = [B.phi(q).clone() for q in range(len(probs))]
-    B.solve(max_iters=200, check_every=50, stream=s)          # replayed
+    B.solve(max_iters=200, check_every=50, stream=s, path="queue")          # replayed
     for q in range(len(probs)):
         assert torch.equal(first[q], B.phi(q))
     best, times = B.tune(sample_iters=30)
     assert best in (128, 256, 512) and all(t > 0 for t in times.values())
-    B.solve(max_iters=200, check_every=50, stream=s)          # new launch shape -> recaptured
+    B.solve(max_iters=200, check_every=50, stream=s, path="queue")          # new launch shape -> recaptured
     _check_against_oracle(B, probs, r0s, r1s, max_iters=200, check_every=50)
 
 
-def test_batched_matches_single_solves_at_config_sizes():
+@pytest.mark.parametrize("path", PATHS)
+def test_batched_matches_single_solves_at_config_sizes(path):
     """Problems drawn like the 512-problem mixed configuration (sides up to 256, k in {1, 3, 5},
     G(k, 0.6) graphs): each result equals the single-problem streaming solve on the GPU."""
     d = _dev()
@@ -109,7 +115,9 @@ def test_batched_matches_single_solves_at_config_sizes():
     r1s = [p["rho1"].astype(np.float32) for p in insts]
     assert max(p["n"] for p in probs) >= 128
     B = V.Batch(probs, r0s, r1s)
-    B.solve(max_iters=250, check_every=125)
+    B.solve(max_iters=250, check_every=125, path=path)
+    if path == "grouped":
+        assert max(r["blocks"] for r in B.results) > 1      # the large problems span several SMs
     for q, p in enumerate(probs):
         sol = V.solve(torch.from_numpy(r0s[q]).to(d), torch.from_numpy(r1s[q]).to(d), p["edges"], 1.0,
                       max_iters=250, check_every=125, engine="stream")
