@@ -98,7 +98,7 @@ struct ResArgs {
 };
 
 struct SmemLayout {
-    int red, S, dec, rtab, cnt, sphi, sux, suy, sdx, sdy, total;
+    int red, S, dec, rtab, cnt, sphi, sux, suy, sdx, sdy, sdg, total;
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
@@ -118,6 +118,7 @@ __host__ __device__ inline SmemLayout smem_layout(int K, int EWs, int EHm, int G
     L.suy = o; o += align16(plane);
     L.sdx = o; o += align16(plane);
     L.sdy = o; o += align16(plane);
+    L.sdg = o; o += align16(plane);
     L.total = o;
     return L;
 }
@@ -318,7 +319,7 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
     double *rtab = (double *)(smem + SL.rtab);
     int *cntR = (int *)(smem + SL.cnt), *cntRp = cntR + (HMAX + 2);
     float *sphi = (float *)(smem + SL.sphi), *sux = (float *)(smem + SL.sux), *suy = (float *)(smem + SL.suy);
-    float *sdx = (float *)(smem + SL.sdx), *sdy = (float *)(smem + SL.sdy);
+    float *sdx = (float *)(smem + SL.sdx), *sdy = (float *)(smem + SL.sdy), *sdg = (float *)(smem + SL.sdg);
 
     const int gx = tile % G.Gx, gy = tile / G.Gx;
     TileFrame fr;
@@ -395,9 +396,8 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
     }
     __syncthreads();
 
-    // ---- halo exchange number e: publish the tile's band, receive the ring.  Before
-    // a check, the ring points also record u_new - u_old in sdx / sdy.
-    auto exchange = [&](int e, bool rec_delta) -> bool {
+    // ---- halo exchange number e: publish the tile's band, receive the ring
+    auto exchange = [&](int e) -> bool {
         const uint32_t tag = tag_hi + (uint32_t)e + 1u;
         const int par = e & 1;
         const bool publish = !(a.drop_exch > 0 && e == a.drop_exch && tile == 0);
@@ -435,16 +435,6 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
             ok = poll_pairs<F2MAX>(F2, tag, a.ctl, a.wait_ns, [&](int j) { return xpair(src, par, j, sly, slx); },
                                    vals);
             if (!ok) continue;
-            if (rec_delta) {
-                float dx[K], dy[K];
-#pragma unroll
-                for (int c = 0; c < K; ++c) {
-                    dx[c] = vals[K + c] - ux[r][c];
-                    dy[c] = vals[2 * K + c] - uy[r][c];
-                }
-                sts<K>(sdx + sb[r], dx);
-                sts<K>(sdy + sb[r], dy);
-            }
 #pragma unroll
             for (int c = 0; c < K; ++c) {
                 ph[r][c] = vals[c];
@@ -462,22 +452,25 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
 #pragma unroll
     for (int r = 0; r < P; ++r)
         if (ptile[r]) sts<K>(sphi + sb[r], ph[r]);
-    if (!exchange(0, false)) dec[0] = 1;
+    if (!exchange(0)) dec[0] = 1;
     __syncthreads();
     bool aborted = dec[0] != 0;
     int nexch = 1, checks = 0, t = 0;
     bool stop = false;
 
-    float dph[P][K], dgw[P][K], racc[P][K];
+    float racc[P][K];
 #pragma unroll
     for (int r = 0; r < P; ++r)
 #pragma unroll
-        for (int c = 0; c < K; ++c) { dph[r][c] = 0.0f; dgw[r][c] = 0.0f; racc[r][c] = 0.0f; }
+        for (int c = 0; c < K; ++c) racc[r][c] = 0.0f;
 
     // ---- one PDHG step on the points q < nRp (phase 1: u, and ubar for the
     // divergence) and q < nR (w, the commit, phase 2: phi).  LAST: the step
-    // before a check, which also records the increments the check needs.
-    float fdu = 0.0f, fdw = 0.0f;
+    // before a check (its region is the tile), which also sums the terms of the
+    // fixed-point residual R of Section 6.1: ||du||^2, ||dw||^2, ||dphi||^2 and
+    // <dphi, div du + div_G dw>, where du on the points left of and below the tile
+    // comes from the same phase-1 arithmetic their own tile does.
+    float fdu = 0.0f, fdw = 0.0f, fdp = 0.0f, fdx = 0.0f;
     auto step = [&](auto last_tag, int nR, int nRp) {
         constexpr bool LAST = decltype(last_tag)::value;
 #pragma unroll
@@ -503,6 +496,17 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
             }
             sts<K>(sux + b, ubx);
             sts<K>(suy + b, uby);
+            if constexpr (LAST) {
+                float dux[K], duy[K];
+#pragma unroll
+                for (int c = 0; c < K; ++c) {
+                    dux[c] = vx[c] - ux[r][c];
+                    duy[c] = vy[c] - uy[r][c];
+                    if (q < nR) fdu += a.g.wc[c] * (dux[c] * dux[c] + duy[c] * duy[c]);
+                }
+                sts<K>(sdx + b, dux);
+                sts<K>(sdy + b, duy);
+            }
             if (q >= nR) continue;
             float wx[LKv];
 #pragma unroll
@@ -521,19 +525,15 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
                 racc[r][c] = gw + bb[r][c];
             }
             if constexpr (LAST) {
-                float dux[K], duy[K];
+                float dg[K];
 #pragma unroll
                 for (int c = 0; c < K; ++c) {
                     float gd = 0.0f;
 #pragma unroll
                     for (int e = 0; e < LKv; ++e) gd -= a.g.Dv[c][e] * (wx[e] - w[r][e]);
-                    dgw[r][c] = gd;
-                    dux[c] = vx[c] - ux[r][c];
-                    duy[c] = vy[c] - uy[r][c];
-                    fdu += a.g.wc[c] * (dux[c] * dux[c] + duy[c] * duy[c]);
+                    dg[c] = gd;
                 }
-                sts<K>(sdx + b, dux);
-                sts<K>(sdy + b, duy);
+                sts<K>(sdg + b, dg);
 #pragma unroll
                 for (int e = 0; e < LKv; ++e) {
                     const float dw = wx[e] - w[r][e];
@@ -562,14 +562,29 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
             lds<K>(suy + b, byo);
             lds<K>(suy + b - ((f & 8) ? RS : 0), byd);
             const float mx = (f & 4) ? 1.0f : 0.0f, my = (f & 8) ? 1.0f : 0.0f;
+            float dph[K];
 #pragma unroll
             for (int c = 0; c < K; ++c) {
                 const float d = ih * ((bxo[c] - mx * bxl[c]) + (byo[c] - my * byd[c])) + racc[r][c];
                 const float np = ph[r][c] + tau * d;
-                if constexpr (LAST) dph[r][c] = np - ph[r][c];
+                dph[c] = np - ph[r][c];
                 ph[r][c] = np;
             }
             sts<K>(sphi + b, ph[r]);
+            if constexpr (LAST) {
+                float dxo[K], dxl[K], dyo[K], dyd[K], dg[K];
+                lds<K>(sdx + b, dxo);
+                lds<K>(sdx + b - ((f & 4) ? KV : 0), dxl);
+                lds<K>(sdy + b, dyo);
+                lds<K>(sdy + b - ((f & 8) ? RS : 0), dyd);
+                lds<K>(sdg + b, dg);
+#pragma unroll
+                for (int c = 0; c < K; ++c) {
+                    const float ddiv = ih * ((dxo[c] - mx * dxl[c]) + (dyo[c] - my * dyd[c])) + dg[c];
+                    fdp += a.g.wc[c] * dph[c] * dph[c];
+                    fdx += a.g.wc[c] * dph[c] * ddiv;
+                }
+            }
         }
         __syncthreads();
     };
@@ -585,8 +600,7 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
         }
         const int t_end = t + hb;
         const bool check_after = (T == 0) || (t_end % CE == 0) || (t_end == T);
-        fdu = 0.0f;
-        fdw = 0.0f;
+        fdu = fdw = fdp = fdx = 0.0f;
         for (int s = 1; s <= hb; ++s) {
             const int rr = min(hb - s, R);      // ring width of the region this step updates
             const int nR = cntR[rr], nRp = cntRp[rr];
@@ -596,9 +610,9 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
                 step(std::integral_constant<bool, false>(), nR, nRp);
         }
         t = t_end;
-        // ---- refresh the ring (and, before a check, record u_new - u_old on it)
+        // ---- refresh the ring
         if (hb > 0) {
-            if (!exchange(nexch, check_after)) dec[0] = 1;
+            if (!exchange(nexch)) dec[0] = 1;
             ++nexch;
             __syncthreads();
             if (dec[0]) { aborted = true; break; }
@@ -606,17 +620,6 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
         if (!check_after) continue;
 
         // ---- convergence check of the iterate after iteration t
-        if (T == 0) {
-#pragma unroll
-            for (int r = 0; r < P; ++r)
-                if (pv[r]) {
-                    float z[K];
-#pragma unroll
-                    for (int c = 0; c < K; ++c) z[c] = 0.0f;
-                    sts<K>(sdx + sb[r], z);
-                    sts<K>(sdy + sb[r], z);
-                }
-        }
 #pragma unroll
         for (int r = 0; r < P; ++r)
             if (pv[r]) {
@@ -631,26 +634,23 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
         for (int q = 0; q < NRED; ++q) fs[q] = 0.0f;
         fs[RED_DU] = fdu;
         fs[RED_DW] = fdw;
+        fs[RED_DP] = fdp;
+        fs[RED_X] = fdx;
 #pragma unroll
         for (int r = 0; r < P; ++r) {
             if (!ptile[r]) continue;
             const int b = sb[r], f = nbf[r];
             const int oxm = (f & 4) ? KV : 0, oym = (f & 8) ? RS : 0;
             const float mx = (f & 4) ? 1.0f : 0.0f, my = (f & 8) ? 1.0f : 0.0f;
-            float uxl[K], uyd[K], dxo[K], dxl[K], dyo[K], dyd[K], fx[K], fy[K];
+            float uxl[K], uyd[K], fx[K], fy[K];
             lds<K>(sux + b - oxm, uxl);
             lds<K>(suy + b - oym, uyd);
-            lds<K>(sdx + b, dxo);
-            lds<K>(sdx + b - oxm, dxl);
-            lds<K>(sdy + b, dyo);
-            lds<K>(sdy + b - oym, dyd);
             lds<K>(sphi + b + ((f & 1) ? KV : 0), fx);
             lds<K>(sphi + b + ((f & 2) ? RS : 0), fy);
             float nu_pt = 0.0f, dn_u = 0.0f;
 #pragma unroll
             for (int c = 0; c < K; ++c) {
                 const float uxc = ux[r][c], uyc = uy[r][c], phc = ph[r][c], bc = bb[r][c], wgt = a.g.wc[c];
-                const float ddiv = ih * ((dxo[c] - mx * dxl[c]) + (dyo[c] - my * dyd[c])) + dgw[r][c];
                 float gwb = bc;
 #pragma unroll
                 for (int e = 0; e < LKv; ++e) gwb -= a.g.Dv[c][e] * w[r][e];
@@ -658,8 +658,6 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
                 fs[RED_RR] += wgt * rc * rc;
                 fs[RED_BB] += wgt * bc * bc;
                 fs[RED_D] += wgt * phc * bc;
-                fs[RED_DP] += wgt * dph[r][c] * dph[r][c];
-                fs[RED_X] += wgt * dph[r][c] * ddiv;
                 const float gxx = ih * (fx[c] - phc), gyy = ih * (fy[c] - phc);
                 if (un == VOMT_U_L12) {
                     nu_pt += sqrtf(uxc * uxc + uyc * uyc);
@@ -702,29 +700,45 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
             if (l > 0) di = fmaxf(di, dn_w - alpha);
             fs[RED_MAX] = fmaxf(fs[RED_MAX], di);
         }
-        // block reduction in FP64 (fixed order)
-        double v[NRED];
-#pragma unroll
-        for (int q = 0; q < NRED; ++q) v[q] = (double)fs[q];
+        // warp sums in FP32 with the rounding error carried (TwoSum at every level,
+        // fixed order), then the warps' (hi, lo) pairs summed in FP64 by one thread
+        // per slot: the FP64 pipe sees a few dozen instructions per check
         const int lane = tid & 31, wid = tid >> 5, nw = (nthr + 31) >> 5;
+        float lo[NRED];
+#pragma unroll
+        for (int q = 0; q < NRED; ++q) lo[q] = 0.0f;
 #pragma unroll
         for (int q = 0; q < NRED; ++q) {
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
-                const double o = __shfl_down_sync(0xffffffffu, v[q], off);
-                v[q] = (q == RED_MAX) ? fmax(v[q], o) : v[q] + o;
+                const float oh = __shfl_down_sync(0xffffffffu, fs[q], off);
+                const float ol = __shfl_down_sync(0xffffffffu, lo[q], off);
+                if (q == RED_MAX) {
+                    fs[q] = fmaxf(fs[q], oh);
+                } else {
+                    float e;
+                    fs[q] = two_sum(fs[q], oh, e);
+                    lo[q] = lo[q] + (ol + e);
+                }
             }
         }
+        float *redf = reinterpret_cast<float *>(red);
         if (lane == 0)
 #pragma unroll
-            for (int q = 0; q < NRED; ++q) red[wid * NRED + q] = v[q];
+            for (int q = 0; q < NRED; ++q) {
+                redf[(wid * NRED + q) * 2] = fs[q];
+                redf[(wid * NRED + q) * 2 + 1] = lo[q];
+            }
         __syncthreads();
         const int cpar = checks & 1;
         const uint32_t ctag = tag_hi + (uint32_t)checks + 1u;
         const int words = NT * NRED * 2;
         if (tid < NRED) {
-            double acc = red[tid];
-            for (int q = 1; q < nw; ++q) acc = (tid == RED_MAX) ? fmax(acc, red[q * NRED + tid]) : acc + red[q * NRED + tid];
+            double acc = tid == RED_MAX ? (double)redf[tid * 2] : (double)redf[tid * 2] + (double)redf[tid * 2 + 1];
+            for (int q = 1; q < nw; ++q) {
+                const double x_ = (double)redf[(q * NRED + tid) * 2], y_ = (double)redf[(q * NRED + tid) * 2 + 1];
+                acc = (tid == RED_MAX) ? fmax(acc, x_) : acc + (x_ + y_);
+            }
             unsigned long long *dst = a.rows + (size_t)cpar * words + ((size_t)tile * NRED + tid) * 2;
             st_tagged(dst, __int_as_float(__double2hiint(acc)), ctag);
             st_tagged(dst + 1, __int_as_float(__double2loint(acc)), ctag);
