@@ -304,11 +304,34 @@ def extra_hbm_bound(dev, peak, n=2048, iters=300):
     return out
 
 
+def extra_regularised(dev, peak, eps=5e4, cap=50000):
+    """The quadratically regularised problem (the paper's conclusions) on the benchmark
+    workload: eps (||u||_2^2 + ||w||_2^2) added, to rel gap and rel res <= 1e-5."""
+    import torch
+    import paper_1712_10279_gb300 as V
+    from paper_1712_10279_gb300 import synthetic as S
+    r0, r1 = S.color_image_pair(N, K, seed=1002)
+    d0 = torch.from_numpy(r0.astype(np.float32)).to(dev)
+    d1 = torch.from_numpy(r1.astype(np.float32)).to(dev)
+    V.solve(d0, d1, EDGES, 1.0, max_iters=200, check_every=100, eps=eps)
+    sol, ms = _gpu_ms(lambda: V.solve(d0, d1, EDGES, 1.0, max_iters=cap, check_every=CHECK_EVERY, tol_gap=TOL,
+                                      tol_res=TOL, eps=eps))
+    r = sol.result
+    gp = N * N * r["iters"]
+    gbs = BYTES_PER_GP_IT * gp / (ms / 1e3) / 1e9
+    q2 = float((sol.u.double() ** 2).sum() + (sol.w.double() ** 2).sum())
+    return dict(workload="256x256 k=3 colour-image densities, alpha=1, eps=%g, to 1e-5, cap %d" % (eps, cap),
+                ms=ms, us_per_iter=1e3 * ms / max(r["iters"], 1), gp_it_per_s=gp / (ms / 1e3),
+                achieved_GBps=gbs, frac_of_measured_hbm=gbs / peak,
+                regulariser_share_of_cost=eps * q2 / r["primal"] if r["primal"] else None, **_summary(r))
+
+
 def extras(dev):
     peak, _ = _peaks()
     out = {}
     for name, fn in (("matrix_128", lambda: extra_matrix(dev, peak)), ("batched_vs_plain", lambda: extra_batched(dev)),
                      ("differentiable", lambda: extra_differentiable(dev)),
+                     ("regularised", lambda: extra_regularised(dev, peak)),
                      ("hbm_bound", lambda: extra_hbm_bound(dev, peak))):
         t0 = time.perf_counter()
         try:

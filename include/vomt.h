@@ -102,11 +102,20 @@ typedef struct {
     int engine;          /* VOMT_ENGINE_* */
     int halo;            /* resident engine: iterations between halo exchanges, 1..16 (0 = the
                             plan's estimate; a one-tile grid never exchanges) */
+    double eps;          /* >= 0: quadratic regularisation of the paper's concluding section,
+                            eps (||u(x)||_2^2 + ||w(x)||_2^2) added at every point (Euclidean
+                            norms, so the problem is strictly convex); each primal step is then
+                            the shrink of v / (1 + 2 t eps) with threshold t / (1 + 2 t eps), P
+                            includes the term and D subtracts sum dist_2(., dual ball)^2 /
+                            (4 eps).  0 (default) is the plain problem.  Vector OMT, forward
+                            solves (vomt_unrolled_grad and momt_solve take eps = 0 only). */
 } vomt_params;
 
 typedef struct {
-    double primal;       /* P = sum_ij ||u_ij||_u + alpha sum_ij ||w_ij||_w (Appendix A) */
-    double dual;         /* D = sum_ij <phi_ij, rho1_ij - rho0_ij> (eq. vomt-dual) */
+    double primal;       /* P = sum_ij ||u_ij||_u + alpha sum_ij ||w_ij||_w (Appendix A), plus the
+                            eps term when regularised */
+    double dual;         /* D = sum_ij <phi_ij, rho1_ij - rho0_ij> (eq. vomt-dual), minus the
+                            conjugate terms of the regulariser when eps > 0 */
     double rel_gap;      /* |P - D| / |P|, the measure of Section 8.1 */
     double rel_res;      /* ||div_x u + div_G w - (rho0 - rho1)||_2 / ||rho0 - rho1||_2 */
     double fp_resid;     /* R of Section 6.1 between the last two iterates, weights 1/mu, 1/nu, 1/tau */

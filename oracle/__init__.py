@@ -67,9 +67,9 @@ def _load():
             "orc_quantum_sym_gap": (d, [i, i, p]),
             "orc_step_sizes": (None, [i, d, d, i, p, p]),
             "orc_vomt_metrics": (None, [i, i, i, p, p, p, p, p, d, i, i, d, d, d,
-                                        p, p, p, p, p, p, p, p, p]),
+                                        p, p, p, p, p, p, p, p, d, p]),
             "orc_vomt_solve": (i, [i, i, i, p, p, p, p, p, d, d, d, d, i, i, i, i, d, d,
-                                   p, p, p, p, p, p, i]),
+                                   p, p, p, p, p, p, i, d]),
             "orc_somt_run": (i, [i, p, p, d, d, i, i, p, p, p]),
             "orc_momt_metrics": (None, [i, i, i, p, p, p, d, i, i, d, d, d,
                                         p, p, p, p, p, p, p, p, p]),
@@ -227,7 +227,7 @@ def default_tau_matrix(n: int) -> float:
 
 # ---------------------------------------------------------------- solvers
 def vomt_metrics(state, prev, rho0, rho1, edges, alpha, mu, nu, tau, cost=None,
-                 u_norm=U_L12, w_norm=W_L1):
+                 u_norm=U_L12, w_norm=W_L1, eps=0.0):
     rho0, rho1 = _f64(rho0), _f64(rho1)
     k, n = rho0.shape[0], rho0.shape[-1]
     a, b = _edges(edges)
@@ -241,17 +241,19 @@ def vomt_metrics(state, prev, rho0, rho1, edges, alpha, mu, nu, tau, cost=None,
     _load().orc_vomt_metrics(n, k, a.size, _ptr(a), _ptr(b), _ptr(c), _ptr(rho0), _ptr(rho1),
                              float(alpha), u_norm, w_norm, float(mu), float(nu), float(tau),
                              _ptr(ux), _ptr(uy), _ptr(w), _ptr(phi),
-                             _ptr(pux), _ptr(puy), _ptr(pw), _ptr(pphi), _ptr(out))
+                             _ptr(pux), _ptr(puy), _ptr(pw), _ptr(pphi), float(eps), _ptr(out))
     return out
 
 
 def vomt_solve(rho0, rho1, edges, alpha=1.0, tau=None, mu=None, nu=None, cost=None,
                u_norm=U_L12, w_norm=W_L1, max_iters=2000, check_every=100,
-               tol_gap=0.0, tol_res=0.0, init=None, history=False):
+               tol_gap=0.0, tol_res=0.0, init=None, history=False, eps=0.0):
     """Run the V-OMT iteration of Section 7.2 in FP64.
 
     rho0, rho1: [k, n, n] cell masses.  edges: list of node pairs of the channel
-    graph (empty for k = 1).  tau/mu/nu default to the paper's rules.  Returns a
+    graph (empty for k = 1).  tau/mu/nu default to the paper's rules.  eps > 0 adds
+    the quadratic regulariser eps (||u||_2^2 + ||w||_2^2) of the paper's conclusions
+    (Euclidean norms per point).  Returns a
     dict with the final state (ux, uy, w, phi), the step sizes, the metrics of the
     last check and, if asked, every check row.
     """
@@ -278,7 +280,7 @@ def vomt_solve(rho0, rho1, edges, alpha=1.0, tau=None, mu=None, nu=None, cost=No
     it = _load().orc_vomt_solve(n, k, l, _ptr(a), _ptr(b), _ptr(c), _ptr(rho0), _ptr(rho1),
                                 float(alpha), float(tau), float(mu), float(nu), u_norm, w_norm,
                                 int(max_iters), int(check_every), float(tol_gap), float(tol_res),
-                                _ptr(ux), _ptr(uy), _ptr(w), _ptr(phi), _ptr(met), _ptr(hist), nchk)
+                                _ptr(ux), _ptr(uy), _ptr(w), _ptr(phi), _ptr(met), _ptr(hist), nchk, float(eps))
     out = dict(ux=ux, uy=uy, w=w, phi=phi, iters=it, mu=mu, nu=nu, tau=tau,
                metrics=dict(zip(MET_NAMES, met)))
     if history:

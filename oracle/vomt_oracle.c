@@ -43,6 +43,14 @@
  *   [7] converged flag (1 if rel_gap <= tol_gap and rel_res <= tol_res)
  * Section 6.1 prints the y-block weight of R as 1/mu; the metric of the PDHG
  * proximal-point form makes it 1/nu, which is what is used here.
+ *
+ * Quadratic regularisation (the paper's concluding section): with eps > 0 the
+ * objective gains eps (||u(x)||_2^2 + ||w(x)||_2^2) at every point, with
+ * Euclidean norms (the reading under which the regularised problem is
+ * strictly convex, as the paper states, for every choice of ||.||_u, ||.||_w).
+ * P then includes that term, and D subtracts sum_x dist_2(grad phi(x), B_u*)^2
+ * / (4 eps) + dist_2(grad_G phi(x), alpha B_w*)^2 / (4 eps), the conjugate of
+ * ||.|| + eps ||.||_2^2 (B* the unit ball of the dual norm).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -474,6 +482,43 @@ static double dualnorm_w_point(int l, int w_norm, const double *g)
     return s;
 }
 
+/* Squared Euclidean distance from g to the dual unit ball of ||.||_u at one
+ * point (the ball is a product of per-channel discs for ||.||_{1,2}, one ball
+ * for ||.||_2, a box for ||.||_1). */
+static double dist2_dualball_u_point(int k, int u_norm, const double *gx, const double *gy)
+{
+    double s = 0.0;
+    if (u_norm == 0) {
+        for (int c = 0; c < k; ++c) {
+            double v = sqrt(gx[c] * gx[c] + gy[c] * gy[c]) - 1.0;
+            if (v > 0.0) s += v * v;
+        }
+    } else if (u_norm == 1) {
+        double v = dualnorm_u_point(k, 1, gx, gy) - 1.0;
+        if (v > 0.0) s = v * v;
+    } else {
+        for (int c = 0; c < k; ++c) {
+            double v = fabs(gx[c]) - 1.0, q = fabs(gy[c]) - 1.0;
+            if (v > 0.0) s += v * v;
+            if (q > 0.0) s += q * q;
+        }
+    }
+    return s;
+}
+
+/* Squared Euclidean distance from g to the dual ball of radius alpha of ||.||_w. */
+static double dist2_dualball_w_point(int l, int w_norm, const double *g, double alpha)
+{
+    double s = 0.0;
+    if (w_norm == 0) {
+        for (int e = 0; e < l; ++e) { double v = fabs(g[e]) - alpha; if (v > 0.0) s += v * v; }
+    } else {
+        double v = dualnorm_w_point(l, 1, g) - alpha;
+        if (v > 0.0) s = v * v;
+    }
+    return s;
+}
+
 /* Metrics of the state (ux, uy, w, phi) (see the header comment).  R is
  * computed from the previous state (pux, puy, pw, pphi) when those are given,
  * else set to 0.  out[6], out[7] are left to the caller. */
@@ -482,7 +527,7 @@ void orc_vomt_metrics(int n, int k, int l, const int *ea, const int *eb, const d
                       double mu, double nu, double tau,
                       const double *ux, const double *uy, const double *w, const double *phi,
                       const double *pux, const double *puy, const double *pw, const double *pphi,
-                      double *out)
+                      double eps, double *out)
 {
     size_t nk = (size_t)k * n * n, nl = (size_t)l * n * n, nn = (size_t)n * n;
     double *dv = (double *)malloc(sizeof(double) * nk);
@@ -492,15 +537,22 @@ void orc_vomt_metrics(int n, int k, int l, const int *ea, const int *eb, const d
     double *gg = (double *)malloc(sizeof(double) * (nl ? nl : 1));
     double a[32], b[32], c3[64];
 
-    /* primal objective */
+    /* primal objective (with the regulariser eps (||u||_2^2 + ||w||_2^2) per point) */
     double P = 0.0;
     for (size_t p = 0; p < nn; ++p) {
         for (int c = 0; c < k; ++c) { a[c] = ux[c * nn + p]; b[c] = uy[c * nn + p]; }
         P += norm_u_point(k, u_norm, a, b);
         for (int e = 0; e < l; ++e) c3[e] = w[e * nn + p];
         P += alpha * norm_w_point(l, w_norm, c3);
+        if (eps > 0.0) {
+            double q2 = 0.0;
+            for (int c = 0; c < k; ++c) q2 += a[c] * a[c] + b[c] * b[c];
+            for (int e = 0; e < l; ++e) q2 += c3[e] * c3[e];
+            P += eps * q2;
+        }
     }
-    /* dual objective */
+    /* dual objective; with eps > 0 the conjugate of ||.|| + eps ||.||_2^2 is
+     * dist_2(., dual ball)^2 / (4 eps), subtracted at every point */
     double D = 0.0;
     for (size_t q = 0; q < nk; ++q) D += phi[q] * (rho1[q] - rho0[q]);
     /* constraint residual */
@@ -515,17 +567,20 @@ void orc_vomt_metrics(int n, int k, int l, const int *ea, const int *eb, const d
     /* dual infeasibility */
     orc_grad(n, k, phi, gx, gy);
     if (l) orc_grad_G(n, k, l, ea, eb, cost, phi, gg);
-    double di = 0.0;
+    double di = 0.0, dist2 = 0.0;
     for (size_t p = 0; p < nn; ++p) {
         for (int c = 0; c < k; ++c) { a[c] = gx[c * nn + p]; b[c] = gy[c * nn + p]; }
         double v = dualnorm_u_point(k, u_norm, a, b) - 1.0;
         if (v > di) di = v;
+        if (eps > 0.0) dist2 += dist2_dualball_u_point(k, u_norm, a, b);
         if (l) {
             for (int e = 0; e < l; ++e) c3[e] = gg[e * nn + p];
             v = dualnorm_w_point(l, w_norm, c3) - alpha;
             if (v > di) di = v;
+            if (eps > 0.0) dist2 += dist2_dualball_w_point(l, w_norm, c3, alpha);
         }
     }
+    if (eps > 0.0) D -= dist2 / (4.0 * eps);
     /* fixed-point residual in the PDHG metric */
     double R = 0.0;
     if (pux) {
@@ -571,7 +626,7 @@ int orc_vomt_solve(int n, int k, int l, const int *ea, const int *eb, const doub
                    double tau, double mu, double nu, int u_norm, int w_norm,
                    int max_iters, int check_every, double tol_gap, double tol_res,
                    double *ux, double *uy, double *w, double *phi,
-                   double *metrics, double *history, int hist_cap)
+                   double *metrics, double *history, int hist_cap, double eps)
 {
     size_t nk = (size_t)k * n * n, nl = (size_t)l * n * n, nn = (size_t)n * n;
     double *gx = (double *)malloc(sizeof(double) * nk), *gy = (double *)malloc(sizeof(double) * nk);
@@ -585,24 +640,32 @@ int orc_vomt_solve(int n, int k, int l, const int *ea, const int *eb, const doub
     double a[32], b[32], x[64];
     int nh = 0, t = 0;
     if (check_every <= 0) check_every = max_iters > 0 ? max_iters : 1;
+    /* With the regulariser eps ||.||_2^2 (conclusions of the paper), the primal
+     * steps are the proximal maps of mu (||.||_u + eps ||.||_2^2) and of
+     * nu (alpha ||.||_w + eps ||.||_2^2).  Completing the square,
+     *   t ||z|| + t eps ||z||^2 + |z - v|^2 / 2
+     *     = (1 + 2 t eps) (t' ||z|| + |z - v'|^2 / 2) + const,
+     * with v' = v / (1 + 2 t eps) and t' = t / (1 + 2 t eps), so each step is the
+     * shrink of v' with threshold t'.  eps = 0 gives the plain iteration. */
+    const double su = 1.0 / (1.0 + 2.0 * mu * eps), sw = 1.0 / (1.0 + 2.0 * nu * eps);
 
     for (t = 1; t <= max_iters; ++t) {
         /* u-update: shrink of u + mu grad phi with threshold mu */
         orc_grad(n, k, phi, gx, gy);
         for (size_t p = 0; p < nn; ++p) {
             for (int c = 0; c < k; ++c) {
-                a[c] = ux[c * nn + p] + mu * gx[c * nn + p];
-                b[c] = uy[c * nn + p] + mu * gy[c * nn + p];
+                a[c] = (ux[c * nn + p] + mu * gx[c * nn + p]) * su;
+                b[c] = (uy[c * nn + p] + mu * gy[c * nn + p]) * su;
             }
-            shrink_u_point(k, u_norm, mu, a, b);
+            shrink_u_point(k, u_norm, mu * su, a, b);
             for (int c = 0; c < k; ++c) { nux[c * nn + p] = a[c]; nuy[c * nn + p] = b[c]; }
         }
         /* w-update: shrink of w + nu grad_G phi with threshold alpha nu */
         if (l) {
             orc_grad_G(n, k, l, ea, eb, cost, phi, gg);
             for (size_t p = 0; p < nn; ++p) {
-                for (int e = 0; e < l; ++e) x[e] = w[e * nn + p] + nu * gg[e * nn + p];
-                shrink_w_point(l, w_norm, alpha * nu, x);
+                for (int e = 0; e < l; ++e) x[e] = (w[e * nn + p] + nu * gg[e * nn + p]) * sw;
+                shrink_w_point(l, w_norm, alpha * nu * sw, x);
                 for (int e = 0; e < l; ++e) nw[e * nn + p] = x[e];
             }
         }
@@ -620,7 +683,7 @@ int orc_vomt_solve(int n, int k, int l, const int *ea, const int *eb, const doub
         if (check) {
             /* previous state: ux, uy, w (not yet overwritten), pphi */
             orc_vomt_metrics(n, k, l, ea, eb, cost, rho0, rho1, alpha, u_norm, w_norm, mu, nu, tau,
-                             nux, nuy, nw, phi, ux, uy, w, pphi, m);
+                             nux, nuy, nw, phi, ux, uy, w, pphi, eps, m);
             m[6] = (double)t;
             m[7] = (tol_gap > 0.0 && m[2] <= tol_gap && m[3] <= tol_res) ? 1.0 : 0.0;
             if (history && nh < hist_cap) { memcpy(history + (size_t)nh * ORC_NMET, m, sizeof m); ++nh; }
@@ -899,7 +962,7 @@ double orc_vomt_unrolled_grad(int n, int k, int l, const int *ea, const int *eb,
         double *cur = S + st * (size_t)t, *nxt = S + st * (size_t)(t + 1);
         memcpy(nxt, cur, sizeof(double) * st);
         orc_vomt_solve(n, k, l, ea, eb, cost, rho0, rho1, alpha, tau, mu, nu, 0, w_norm,
-                       1, 1, 0.0, 0.0, nxt, nxt + nk, nxt + 3 * nk, nxt + 2 * nk, met, NULL, 0);
+                       1, 1, 0.0, 0.0, nxt, nxt + nk, nxt + 3 * nk, nxt + 2 * nk, met, NULL, 0, 0.0);
     }
     double *fin = S + st * (size_t)T;
     double J = 0.0;

@@ -30,7 +30,7 @@ class Solution:
     result: dict
 
 
-def _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, warm, engine, halo=0):
+def _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, warm, engine, halo=0, eps=0.0):
     p = _native.Params()
     _native.load().vomt_default_params(ctypes.byref(p))
     p.tau = 0.0 if tau is None else float(tau)
@@ -42,6 +42,7 @@ def _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_re
     p.warm_start = int(bool(warm))
     p.engine = ENGINES[engine] if isinstance(engine, str) else int(engine)
     p.halo = int(halo)
+    p.eps = float(eps)
     return p
 
 
@@ -57,13 +58,14 @@ def step_sizes(n: int, k: int, edges, tau=None, cost=None):
 def solve(rho0, rho1, edges, alpha: float = 1.0, *, tau=None, mu=None, nu=None, cost=None,
           u_norm: int = U_L12, w_norm: int = W_L1, max_iters: int = 2000, check_every: int = 100,
           tol_gap: float = 0.0, tol_res: float = 0.0, init=None, engine="auto", halo: int = 0,
-          stream=None) -> Solution:
+          stream=None, eps: float = 0.0) -> Solution:
     """Vector OMT (Section 7.2) on the GPU.
 
     rho0, rho1: CUDA float32 tensors [k, n, n] (cell masses, [c, j, i], x fastest).
     edges: node pairs of the channel graph (empty for k = 1).  init: optional
     (u, w, phi) tensors to warm-start from.  Returns the final iterate and the
-    metrics of the last FP64 convergence check.
+    metrics of the last FP64 convergence check.  eps > 0 solves the quadratically
+    regularised problem of the paper's conclusions (eps (||u||_2^2 + ||w||_2^2)).
     """
     import torch
     if not (rho0.is_cuda and rho1.is_cuda):
@@ -83,7 +85,7 @@ def solve(rho0, rho1, edges, alpha: float = 1.0, *, tau=None, mu=None, nu=None, 
         w = torch.empty((max(l, 0), n, n), device=dev, dtype=torch.float32)
         phi = torch.empty((k, n, n), device=dev, dtype=torch.float32)
     p = _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, init is not None, engine,
-                halo)
+                halo, eps)
     res = _native.Result()
     st = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
     ctx = _native.context(dev.index if dev.index is not None else torch.cuda.current_device())
@@ -97,7 +99,7 @@ def solve(rho0, rho1, edges, alpha: float = 1.0, *, tau=None, mu=None, nu=None, 
 def solve_host(rho0, rho1, edges, alpha: float = 1.0, *, tau=None, mu=None, nu=None, cost=None,
                u_norm: int = U_L12, w_norm: int = W_L1, max_iters: int = 2000, check_every: int = 100,
                tol_gap: float = 0.0, tol_res: float = 0.0, engine="auto", halo: int = 0, device: int = 0,
-               out=None) -> Solution:
+               out=None, eps: float = 0.0) -> Solution:
     """The same solve through vomt_solve_host: numpy float32 inputs and outputs in host
     memory; the library copies them to and from the GPU inside the call."""
     rho0 = np.ascontiguousarray(rho0, dtype=np.float32)
@@ -109,7 +111,7 @@ def solve_host(rho0, rho1, edges, alpha: float = 1.0, *, tau=None, mu=None, nu=N
         out = (np.empty((2, k, n, n), np.float32), np.empty((max(l, 0), n, n), np.float32),
                np.empty((k, n, n), np.float32))
     u, w, phi = out
-    p = _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, False, engine, halo)
+    p = _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, False, engine, halo, eps)
     res = _native.Result()
     ctx = _native.context(device)
     rc = _native.load().vomt_solve_host(ctx, int(n), rho0.ctypes.data, rho1.ctypes.data, g.ref, float(alpha),
@@ -248,7 +250,7 @@ class Batch:
         return self._view(q, 4 * k + l, k)
 
     def solve(self, *, max_iters=2000, check_every=100, tol_gap=0.0, tol_res=0.0, tau=None, u_norm=U_L12,
-              w_norm=W_L1, warm_start=False, stream=None, path="auto"):
+              w_norm=W_L1, warm_start=False, stream=None, path="auto", eps=0.0):
         """All problems through vomt_solve_batched.  path: "auto" (the tuned or
         estimated faster path), "queue" (one thread block per problem, one persistent
         launch, CUDA-graph captured on a non-default stream) or "grouped" (waves of
@@ -256,7 +258,8 @@ class Batch:
         status; per-problem results are in self.results."""
         import torch
         engine = {"auto": "batched", "queue": "stream", "grouped": "resident"}[path]
-        p = _params(tau, None, None, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, warm_start, engine)
+        p = _params(tau, None, None, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, warm_start, engine,
+                    eps=eps)
         res = (_native.Result * len(self.problems))()
         st = (torch.cuda.current_stream(self.device) if stream is None else stream).cuda_stream
         ctx = _native.context(self.device.index)

@@ -35,7 +35,7 @@ class Instance(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("tau", c_double), ("mu", c_double), ("nu", c_double), ("u_norm", c_int), ("w_norm", c_int),
                 ("max_iters", c_int), ("check_every", c_int), ("tol_gap", c_double), ("tol_res", c_double),
-                ("warm_start", c_int), ("engine", c_int), ("halo", c_int)]
+                ("warm_start", c_int), ("engine", c_int), ("halo", c_int), ("eps", c_double)]
 
 
 class Result(ctypes.Structure):

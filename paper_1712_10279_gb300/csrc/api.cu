@@ -64,6 +64,7 @@ static int prepare(vomt_ctx *ctx, int n, const vomt_graph *graph, double alpha, 
     if (p.u_norm < 0 || p.u_norm > 2 || p.w_norm < 0 || p.w_norm > 1) return fail(ctx, VOMT_ERR_BAD_ARG, "bad norm code");
     if (p.engine < 0 || p.engine > 2) return fail(ctx, VOMT_ERR_BAD_ARG, "bad engine code");
     if (p.halo < 0 || p.halo > 16) return fail(ctx, VOMT_ERR_BAD_ARG, "halo must be in [0, 16]");
+    if (!(p.eps >= 0.0) || !isfinite(p.eps)) return fail(ctx, VOMT_ERR_BAD_ARG, "eps must be finite and >= 0");
     int rc = graph_to_dev(graph, &out->gd, &ctx->err);
     if (rc) return rc;
     graph_to_op(out->gd, &out->g);
@@ -82,6 +83,7 @@ static int prepare(vomt_ctx *ctx, int n, const vomt_graph *graph, double alpha, 
     out->s.nu = (float)nu;
     out->s.tau = (float)tau;
     out->s.alpha = (float)alpha;
+    set_regularisation(&out->s, &out->cfg, p.eps, mu, nu);
     out->cfg.tol_gap = p.tol_gap;
     out->cfg.tol_res = p.tol_res;
     out->cfg.mu = mu;
@@ -286,6 +288,7 @@ void vomt_default_params(vomt_params *p)
     p->warm_start = 0;
     p->engine = VOMT_ENGINE_AUTO;
     p->halo = 0;
+    p->eps = 0.0;
 }
 
 int vomt_step_sizes(int n, const vomt_graph *g, double tau, double *mu, double *nu, double *tau_used, double *lmax_graph)

@@ -328,6 +328,7 @@ extern "C" int vomt_unrolled_grad(vomt_ctx *ctx, int n, const float *rho0, const
         vomt_params p;
         int rc = prepare_vector(ctx, n, graph, alpha, pin, &op, &s, &cfg, &p);
         if (rc) return rc;
+        if (p.eps != 0.0) return fail(ctx, VOMT_ERR_BAD_ARG, "the unrolled gradient takes eps = 0");
         if (p.u_norm != VOMT_U_L12) return fail(ctx, VOMT_ERR_BAD_ARG, "unrolled gradient: u_norm must be VOMT_U_L12");
         if (T < 1 || ckpt < 1) return fail(ctx, VOMT_ERR_BAD_ARG, "unrolled gradient: T >= 1 and ckpt >= 1");
         if (!rho0 || !rho1) return fail(ctx, VOMT_ERR_BAD_ARG, "null array");

@@ -39,6 +39,9 @@ struct InstDev {
     size_t o_rho0, o_rho1, o_u, o_w, o_phi;   // offsets (floats) into the caller's arena
     size_t o_b, o_s[2];                       // offsets (floats) into the scratch arena
     double mu_d, nu_d, tau_d;
+    int reg;                                  // quadratic regularisation (see StepDev)
+    float eps, su, sw;
+    double eps_d;
 };
 
 struct InstStatus {
@@ -75,6 +78,7 @@ __device__ __forceinline__ void step_point(const InstDev &I, int i, int j, const
     const float *phi = S0, *ux = S0 + (size_t)K * nn, *uy = S0 + (size_t)2 * K * nn, *w = S0 + (size_t)3 * K * nn;
     const bool hR = i < n - 1, hU = j < n - 1, hL = i > 0, hD = j > 0;
     const float mu = I.mu, muih = I.mu * I.ih, ih = I.ih;
+    const float su = I.reg ? I.su : 1.0f, tu = I.reg ? mu * I.su : mu;
     float pc[K], vx[K], vy[K], ux0[K], uy0[K], lx[K], ly[K], lx0[K], dx[K], dy[K], dy0[K];
 #pragma unroll
     for (int c = 0; c < K; ++c) {
@@ -95,10 +99,13 @@ __device__ __forceinline__ void step_point(const InstDev &I, int i, int j, const
         dy0[c] = hD ? uy[c * nn + p - n] : 0.0f;
         dx[c] = dx0 + ((hR && hD) ? muih * (prd - pd) : 0.0f);
         dy[c] = dy0[c] + (hD ? muih * (pc[c] - pd) : 0.0f);
+        if (I.reg) {
+            vx[c] *= su; vy[c] *= su; lx[c] *= su; ly[c] *= su; dx[c] *= su; dy[c] *= su;
+        }
     }
-    shrink_u<K>(vx, vy, mu, un, I.wc);
-    shrink_u<K>(lx, ly, mu, un, I.wc);
-    shrink_u<K>(dx, dy, mu, un, I.wc);
+    shrink_u<K>(vx, vy, tu, un, I.wc);
+    shrink_u<K>(lx, ly, tu, un, I.wc);
+    shrink_u<K>(dx, dy, tu, un, I.wc);
     float w0[LK], wx[LK];
 #pragma unroll
     for (int e = 0; e < LK; ++e) {
@@ -107,8 +114,9 @@ __device__ __forceinline__ void step_point(const InstDev &I, int i, int j, const
         for (int c = 0; c < K; ++c) ge += I.G[e][c] * pc[c];
         w0[e] = (e < l) ? w[e * nn + p] : 0.0f;
         wx[e] = (e < l) ? w0[e] + I.nu * ge : 0.0f;
+        if (I.reg) wx[e] *= I.sw;
     }
-    shrink_w<LK>(wx, l, I.alpha * I.nu, wn, I.we);
+    shrink_w<LK>(wx, l, I.reg ? I.alpha * I.nu * I.sw : I.alpha * I.nu, wn, I.we);
     float *ophi = S1, *oux = S1 + (size_t)K * nn, *ouy = S1 + (size_t)2 * K * nn, *ow = S1 + (size_t)3 * K * nn;
 #pragma unroll
     for (int c = 0; c < K; ++c) {
@@ -141,7 +149,7 @@ __device__ __forceinline__ void metric_point(const InstDev &I, int i, int j, con
     const double dih = (double)(n - 1);
     float ph[K], dph[K], ddiv[K];
     double rdiv[K];
-    float nu_pt = 0.0f, dn_u = 0.0f;
+    float nu_pt = 0.0f, dn_u = 0.0f, q2 = 0.0f, dist = 0.0f;
 #pragma unroll
     for (int c = 0; c < K; ++c) {
         const size_t q = c * nn + p;
@@ -162,18 +170,29 @@ __device__ __forceinline__ void metric_point(const InstDev &I, int i, int j, con
         v[RED_BB] += (double)(wgt * bc * bc);
         const float gx = hR ? ih * (S1[q + 1] - ph[c]) : 0.0f;
         const float gy = hU ? ih * (S1[q + n] - ph[c]) : 0.0f;
+        q2 += wgt * (uxc * uxc + uyc * uyc);
         if (un == VOMT_U_L12) {
             nu_pt += sqrtf(uxc * uxc + uyc * uyc);
-            dn_u = fmaxf(dn_u, sqrtf(gx * gx + gy * gy));
+            const float gn = sqrtf(gx * gx + gy * gy);
+            dn_u = fmaxf(dn_u, gn);
+            const float o = fmaxf(gn - 1.0f, 0.0f);
+            dist += o * o;
         } else if (un == VOMT_U_L2) {
             nu_pt += wgt * (uxc * uxc + uyc * uyc);
             dn_u += wgt * (gx * gx + gy * gy);
         } else {
             nu_pt += wgt * (fabsf(uxc) + fabsf(uyc));
             dn_u = fmaxf(dn_u, fmaxf(fabsf(gx), fabsf(gy)));
+            const float ox = fmaxf(fabsf(gx) - 1.0f, 0.0f), oy = fmaxf(fabsf(gy) - 1.0f, 0.0f);
+            dist += wgt * (ox * ox + oy * oy);
         }
     }
-    if (un == VOMT_U_L2) { nu_pt = sqrtf(nu_pt); dn_u = sqrtf(dn_u); }
+    if (un == VOMT_U_L2) {
+        nu_pt = sqrtf(nu_pt);
+        dn_u = sqrtf(dn_u);
+        const float o = fmaxf(dn_u - 1.0f, 0.0f);
+        dist += o * o;
+    }
     float nw_pt = 0.0f, dn_w = 0.0f;
     const float *cw = S1 + (size_t)3 * K * nn, *pw = S0 + (size_t)3 * K * nn;
 #pragma unroll
@@ -182,6 +201,7 @@ __device__ __forceinline__ void metric_point(const InstDev &I, int i, int j, con
             const size_t q = e * nn + p;
             const float we = cw[q], dwe = we - pw[q], wgt = I.we[e];
             v[RED_DW] += (double)(wgt * dwe * dwe);
+            q2 += wgt * we * we;
             float ge = 0.0f;
 #pragma unroll
             for (int c = 0; c < K; ++c) {
@@ -189,12 +209,28 @@ __device__ __forceinline__ void metric_point(const InstDev &I, int i, int j, con
                 rdiv[c] -= (double)I.Dv[c][e] * (double)we;
                 ddiv[c] -= I.Dv[c][e] * dwe;
             }
-            if (wn == VOMT_W_L1) { nw_pt += wgt * fabsf(we); dn_w = fmaxf(dn_w, fabsf(ge)); }
-            else { nw_pt += wgt * we * we; dn_w += wgt * ge * ge; }
+            if (wn == VOMT_W_L1) {
+                nw_pt += wgt * fabsf(we);
+                dn_w = fmaxf(dn_w, fabsf(ge));
+                const float o = fmaxf(fabsf(ge) - I.alpha, 0.0f);
+                dist += wgt * o * o;
+            } else {
+                nw_pt += wgt * we * we;
+                dn_w += wgt * ge * ge;
+            }
         }
     }
-    if (wn == VOMT_W_L2) { nw_pt = sqrtf(nw_pt); dn_w = sqrtf(dn_w); }
+    if (wn == VOMT_W_L2) {
+        nw_pt = sqrtf(nw_pt);
+        dn_w = sqrtf(dn_w);
+        const float o = fmaxf(dn_w - I.alpha, 0.0f);
+        if (l > 0) dist += o * o;
+    }
     v[RED_P] += (double)nu_pt + (double)I.alpha * (double)nw_pt;
+    if (I.reg) {
+        v[RED_P] += (double)(I.eps * q2);
+        v[RED_DIST] += (double)dist;
+    }
 #pragma unroll
     for (int c = 0; c < K; ++c) {
         v[RED_RR] += (double)I.wc[c] * rdiv[c] * rdiv[c];
@@ -273,7 +309,7 @@ __device__ void solve_one(const InstDev &I, const BatchArgs &a, InstStatus *st, 
             if (threadIdx.x == 0) {
                 double m[NMET];
                 m[0] = v[RED_P];
-                m[1] = v[RED_D];
+                m[1] = v[RED_D] - (I.reg ? v[RED_DIST] / (4.0 * I.eps_d) : 0.0);
                 m[2] = fabs(m[0] - m[1]) / fmax(fabs(m[0]), 1e-300);
                 m[3] = sqrt(v[RED_RR]) / (v[RED_BB] > 0.0 ? sqrt(v[RED_BB]) : 1.0);
                 m[4] = v[RED_DU] / I.mu_d + (l > 0 ? v[RED_DW] / I.nu_d : 0.0) + v[RED_DP] / I.tau_d - 2.0 * v[RED_X];
@@ -498,6 +534,11 @@ static int batch_prepare(vomt_ctx *ctx, int count, const vomt_instance *inst, co
         I.n = n; I.k = k; I.l = l;
         I.mu = (float)mu; I.nu = (float)nu; I.tau = (float)tau; I.alpha = (float)in.alpha; I.ih = (float)n1;
         I.mu_d = mu; I.nu_d = nu; I.tau_d = tau;
+        I.reg = p.eps > 0.0 ? 1 : 0;
+        I.eps = (float)p.eps;
+        I.eps_d = p.eps;
+        I.su = (float)(1.0 / (1.0 + 2.0 * mu * p.eps));
+        I.sw = (float)(1.0 / (1.0 + 2.0 * nu * p.eps));
         memcpy(I.wc, op.wc, sizeof I.wc);
         memcpy(I.we, op.we, sizeof I.we);
         memcpy(I.G, op.G, sizeof I.G);
@@ -653,6 +694,7 @@ static int grouped_solve(vomt_ctx *ctx, BatchState *b, int count, const std::vec
             memcpy(a.g.Dv, I.Dv, sizeof I.Dv);
             a.s = StepDev{I.n, I.ih, I.mu, I.nu, I.tau, I.alpha};
             a.cfg = SolveCfg{p.tol_gap, p.tol_res, I.mu_d, I.nu_d, I.tau_d, I.l > 0 ? 1 : 0};
+            set_regularisation(&a.s, &a.cfg, p.eps, I.mu_d, I.nu_d);
             a.un = p.u_norm;
             a.wn = p.w_norm;
             a.max_iters = p.max_iters;
@@ -733,6 +775,7 @@ extern "C" int vomt_solve_batched(vomt_ctx *ctx, int count, const vomt_instance 
         if (pin) p = *pin;
         if (p.max_iters < 0 || p.check_every < 1) return fail(ctx, VOMT_ERR_BAD_ARG, "max_iters >= 0, check_every >= 1");
         if (p.u_norm < 0 || p.u_norm > 2 || p.w_norm < 0 || p.w_norm > 1) return fail(ctx, VOMT_ERR_BAD_ARG, "bad norm code");
+        if (!(p.eps >= 0.0) || !isfinite(p.eps)) return fail(ctx, VOMT_ERR_BAD_ARG, "eps must be finite and >= 0");
         cudaStream_t st = (cudaStream_t)stream;
         cudaError_t e = cudaSetDevice(ctx->device);
         if (e != cudaSuccess) return set_cuda_error(ctx, e, "cudaSetDevice");

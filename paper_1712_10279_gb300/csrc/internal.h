@@ -43,6 +43,11 @@ struct StepDev {
     int n;          // grid side
     float ih;       // 1/h = n - 1
     float mu, nu, tau, alpha;
+    // quadratic regularisation eps (||u||_2^2 + ||w||_2^2): the primal steps shrink
+    // su * v with threshold su * mu (u) and sw * v with threshold sw * alpha * nu (w),
+    // su = 1 / (1 + 2 mu eps), sw = 1 / (1 + 2 nu eps); reg = 0 when eps = 0
+    int reg;
+    float eps, su, sw;
 };
 
 // Reduction slots of one convergence check (FP64).
@@ -55,6 +60,7 @@ enum {
     RED_DW,         // ||w^t - w^{t-1}||^2
     RED_DP,         // ||phi^t - phi^{t-1}||^2
     RED_X,          // <phi^t - phi^{t-1}, div(u^t - u^{t-1}) + div_G(w^t - w^{t-1})>
+    RED_DIST,       // sum of squared distances of grad phi, grad_G phi to the dual balls (eps > 0)
     RED_NSUM,       // number of summed slots
     RED_MAX = RED_NSUM,  // dual infeasibility (max)
     NRED
@@ -75,7 +81,18 @@ struct SolveCfg {
     double tol_gap, tol_res;
     double mu, nu, tau;
     int has_w;
+    double eps;     // regularisation weight (0: none)
 };
+
+// Fill the regularisation fields of the step constants and the check settings.
+inline void set_regularisation(StepDev *s, SolveCfg *cfg, double eps, double mu, double nu)
+{
+    s->reg = eps > 0.0 ? 1 : 0;
+    s->eps = (float)eps;
+    s->su = (float)(1.0 / (1.0 + 2.0 * mu * eps));
+    s->sw = (float)(1.0 / (1.0 + 2.0 * nu * eps));
+    cfg->eps = eps;
+}
 
 // ----------------------------------------------------------------- host setup
 int graph_to_dev(const vomt_graph *g, GraphDev *out, std::string *err);

@@ -193,6 +193,7 @@ extern "C" int momt_solve(vomt_ctx *ctx, int n, int k, const float *Lam0, const 
         if (p.max_iters < 0 || p.check_every < 1) return fail(ctx, VOMT_ERR_BAD_ARG, "max_iters >= 0, check_every >= 1");
         if (p.u_norm < 1 || p.u_norm > 2 || p.w_norm < 0 || p.w_norm > 1) return fail(ctx, VOMT_ERR_BAD_ARG, "bad norm code");
         if (p.engine < 0 || p.engine > 2 || p.halo < 0 || p.halo > 16) return fail(ctx, VOMT_ERR_BAD_ARG, "bad engine / halo");
+        if (p.eps != 0.0) return fail(ctx, VOMT_ERR_BAD_ARG, "matrix OMT takes eps = 0 (regularisation is for vector OMT)");
         OpDev op;
         double lmax = 0.0, gap = 0.0;
         int rc = quantum_to_op(k, N, L, &op, &lmax, &gap, &ctx->err);

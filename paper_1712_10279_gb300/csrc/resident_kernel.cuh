@@ -487,7 +487,16 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
                 vx[c] = ux[r][c] + muih * (fx[c] - ph[r][c]);
                 vy[c] = uy[r][c] + muih * (fy[c] - ph[r][c]);
             }
-            shrink_u<K>(vx, vy, mu, un, a.g.wc);
+            float tu = mu;
+            if (a.s.reg) {          // regularised prox: shrink v / (1 + 2 mu eps) by mu / (1 + 2 mu eps)
+                tu = mu * a.s.su;
+#pragma unroll
+                for (int c = 0; c < K; ++c) {
+                    vx[c] *= a.s.su;
+                    vy[c] *= a.s.su;
+                }
+            }
+            shrink_u<K>(vx, vy, tu, un, a.g.wc);
             float ubx[K], uby[K];
 #pragma unroll
             for (int c = 0; c < K; ++c) {
@@ -516,7 +525,13 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
                 for (int c = 0; c < K; ++c) ge += a.g.G[e][c] * ph[r][c];
                 wx[e] = (e < l) ? w[r][e] + nu * ge : 0.0f;
             }
-            shrink_w<LKv>(wx, l, alpha * nu, wn, a.g.we);
+            float tw = alpha * nu;
+            if (a.s.reg) {
+                tw *= a.s.sw;
+#pragma unroll
+                for (int e = 0; e < LKv; ++e) wx[e] *= a.s.sw;
+            }
+            shrink_w<LKv>(wx, l, tw, wn, a.g.we);
 #pragma unroll
             for (int c = 0; c < K; ++c) {
                 float gw = 0.0f;
@@ -647,10 +662,11 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
             lds<K>(suy + b - oym, uyd);
             lds<K>(sphi + b + ((f & 1) ? KV : 0), fx);
             lds<K>(sphi + b + ((f & 2) ? RS : 0), fy);
-            float nu_pt = 0.0f, dn_u = 0.0f;
+            float nu_pt = 0.0f, dn_u = 0.0f, q2 = 0.0f, dist = 0.0f;
 #pragma unroll
             for (int c = 0; c < K; ++c) {
                 const float uxc = ux[r][c], uyc = uy[r][c], phc = ph[r][c], bc = bb[r][c], wgt = a.g.wc[c];
+                q2 += wgt * (uxc * uxc + uyc * uyc);
                 float gwb = bc;
 #pragma unroll
                 for (int e = 0; e < LKv; ++e) gwb -= a.g.Dv[c][e] * w[r][e];
@@ -661,18 +677,25 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
                 const float gxx = ih * (fx[c] - phc), gyy = ih * (fy[c] - phc);
                 if (un == VOMT_U_L12) {
                     nu_pt += sqrtf(uxc * uxc + uyc * uyc);
-                    dn_u = fmaxf(dn_u, sqrtf(gxx * gxx + gyy * gyy));
+                    const float gn = sqrtf(gxx * gxx + gyy * gyy);
+                    dn_u = fmaxf(dn_u, gn);
+                    const float o = fmaxf(gn - 1.0f, 0.0f);
+                    dist += o * o;
                 } else if (un == VOMT_U_L2) {
                     nu_pt += wgt * (uxc * uxc + uyc * uyc);
                     dn_u += wgt * (gxx * gxx + gyy * gyy);
                 } else {
                     nu_pt += wgt * (fabsf(uxc) + fabsf(uyc));
                     dn_u = fmaxf(dn_u, fmaxf(fabsf(gxx), fabsf(gyy)));
+                    const float ox = fmaxf(fabsf(gxx) - 1.0f, 0.0f), oy = fmaxf(fabsf(gyy) - 1.0f, 0.0f);
+                    dist += wgt * (ox * ox + oy * oy);
                 }
             }
             if (un == VOMT_U_L2) {
                 nu_pt = sqrtf(nu_pt);
                 dn_u = sqrtf(dn_u);
+                const float o = fmaxf(dn_u - 1.0f, 0.0f);
+                dist += o * o;
             }
             float nw_pt = 0.0f, dn_w = 0.0f;
 #pragma unroll
@@ -682,9 +705,12 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
 #pragma unroll
                     for (int c = 0; c < K; ++c) ge += a.g.G[e][c] * ph[r][c];
                     const float we = w[r][e], wgt = a.g.we[e];
+                    q2 += wgt * we * we;
                     if (wn == VOMT_W_L1) {
                         nw_pt += wgt * fabsf(we);
                         dn_w = fmaxf(dn_w, fabsf(ge));
+                        const float o = fmaxf(fabsf(ge) - alpha, 0.0f);
+                        dist += wgt * o * o;
                     } else {
                         nw_pt += wgt * we * we;
                         dn_w += wgt * ge * ge;
@@ -694,8 +720,14 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
             if (wn == VOMT_W_L2) {
                 nw_pt = sqrtf(nw_pt);
                 dn_w = sqrtf(dn_w);
+                const float o = fmaxf(dn_w - alpha, 0.0f);
+                if (l > 0) dist += o * o;
             }
             fs[RED_P] += nu_pt + alpha * nw_pt;
+            if (a.s.reg) {
+                fs[RED_P] += a.s.eps * q2;
+                fs[RED_DIST] += dist;
+            }
             float di = fmaxf(dn_u - 1.0f, 0.0f);
             if (l > 0) di = fmaxf(di, dn_w - alpha);
             fs[RED_MAX] = fmaxf(fs[RED_MAX], di);
@@ -776,7 +808,7 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
         if (tid == 0) {
             double m[NMET];
             m[0] = S[RED_P];
-            m[1] = S[RED_D];
+            m[1] = S[RED_D] - (a.cfg.eps > 0.0 ? S[RED_DIST] / (4.0 * a.cfg.eps) : 0.0);
             m[2] = fabs(m[0] - m[1]) / fmax(fabs(m[0]), 1e-300);
             m[3] = sqrt(S[RED_RR]) / (S[RED_BB] > 0.0 ? sqrt(S[RED_BB]) : 1.0);
             m[4] = S[RED_DU] / a.cfg.mu + (a.cfg.has_w ? S[RED_DW] / a.cfg.nu : 0.0) + S[RED_DP] / a.cfg.tau -

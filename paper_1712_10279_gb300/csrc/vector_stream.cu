@@ -108,6 +108,8 @@ __global__ void __launch_bounds__(NT) k_step(StateIn in, StateOut out, const flo
     const size_t p = (size_t)j * n + i;
     const bool hR = i < n - 1, hU = j < n - 1, hL = i > 0, hD = j > 0;
     const float mu = s.mu, ih = s.ih;
+    // regularised prox (eps > 0): shrink su * v by su * mu, su = 1 / (1 + 2 mu eps)
+    const float su = s.reg ? s.su : 1.0f, tu = s.reg ? mu * s.su : mu;
 
     float pc[K], pr[K], pu[K], pl[K], plu[K], pd[K], prd[K];
 #pragma unroll
@@ -129,8 +131,9 @@ __global__ void __launch_bounds__(NT) k_step(StateIn in, StateOut out, const flo
         uy0[c] = __ldg(in.uy + c * nn + p);
         vx[c] = ux0[c] + (hR ? mu * (ih * (pr[c] - pc[c])) : 0.0f);
         vy[c] = uy0[c] + (hU ? mu * (ih * (pu[c] - pc[c])) : 0.0f);
+        if (s.reg) { vx[c] *= su; vy[c] *= su; }
     }
-    shrink_u<K, UN>(vx, vy, mu, g.wc);
+    shrink_u<K, UN>(vx, vy, tu, g.wc);
     // u' at (i-1, j): only its x component enters div at (i, j)
     float lx[K], ly[K], lx0[K];
 #pragma unroll
@@ -139,8 +142,9 @@ __global__ void __launch_bounds__(NT) k_step(StateIn in, StateOut out, const flo
         float ly0 = hL ? __ldg(in.uy + c * nn + p - 1) : 0.0f;
         lx[c] = lx0[c] + (hL ? mu * (ih * (pc[c] - pl[c])) : 0.0f);
         ly[c] = ly0 + ((hL && hU) ? mu * (ih * (plu[c] - pl[c])) : 0.0f);
+        if (s.reg) { lx[c] *= su; ly[c] *= su; }
     }
-    shrink_u<K, UN>(lx, ly, mu, g.wc);
+    shrink_u<K, UN>(lx, ly, tu, g.wc);
     // u' at (i, j-1): only its y component enters div at (i, j)
     float dx[K], dy[K], dy0[K];
 #pragma unroll
@@ -149,8 +153,9 @@ __global__ void __launch_bounds__(NT) k_step(StateIn in, StateOut out, const flo
         dy0[c] = hD ? __ldg(in.uy + c * nn + p - n) : 0.0f;
         dx[c] = dx0 + ((hR && hD) ? mu * (ih * (prd[c] - pd[c])) : 0.0f);
         dy[c] = dy0[c] + (hD ? mu * (ih * (pc[c] - pd[c])) : 0.0f);
+        if (s.reg) { dx[c] *= su; dy[c] *= su; }
     }
-    shrink_u<K, UN>(dx, dy, mu, g.wc);
+    shrink_u<K, UN>(dx, dy, tu, g.wc);
     // w' at (i, j)
     float w0[LK], wx[LK];
 #pragma unroll
@@ -161,12 +166,13 @@ __global__ void __launch_bounds__(NT) k_step(StateIn in, StateOut out, const flo
 #pragma unroll
             for (int c = 0; c < K; ++c) ge += g.G[e][c] * pc[c];
             wx[e] = w0[e] + s.nu * ge;
+            if (s.reg) wx[e] *= s.sw;
         } else {
             w0[e] = 0.0f;
             wx[e] = 0.0f;
         }
     }
-    shrink_w<LK, WN>(wx, g.l, s.alpha * s.nu, g.we);
+    shrink_w<LK, WN>(wx, g.l, s.reg ? s.alpha * s.nu * s.sw : s.alpha * s.nu, g.we);
     // phi' = phi + tau (div_x ubar + div_G wbar + rho1 - rho0)
     float r[K];
 #pragma unroll
@@ -243,6 +249,7 @@ __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const 
         float ph[K], dph[K], ddiv[K], gwb[K];
         double rdiv[K];
         float nu_pt = 0.0f, dn_u = 0.0f, fdu = 0.0f, fdp = 0.0f, fd = 0.0f, fbb = 0.0f, fdw = 0.0f, fx = 0.0f;
+        float q2 = 0.0f, dist = 0.0f;     // regularisation: squared norms, squared distances to the dual balls
 #pragma unroll
         for (int c = 0; c < K; ++c) {
             const size_t q = c * nn + p;
@@ -260,20 +267,31 @@ __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const 
             fdp += wgt * dph[c] * dph[c];
             fd += wgt * ph[c] * bc;
             fbb += wgt * bc * bc;
+            q2 += wgt * (uxc * uxc + uyc * uyc);
             const float gx = hR ? ih * (cur.phi[q + 1] - ph[c]) : 0.0f;
             const float gy = hU ? ih * (cur.phi[q + n] - ph[c]) : 0.0f;
             if (UN == VOMT_U_L12) {
                 nu_pt += sqrtf(uxc * uxc + uyc * uyc);
-                dn_u = fmaxf(dn_u, sqrtf(gx * gx + gy * gy));
+                const float gn = sqrtf(gx * gx + gy * gy);
+                dn_u = fmaxf(dn_u, gn);
+                const float o = fmaxf(gn - 1.0f, 0.0f);
+                dist += o * o;
             } else if (UN == VOMT_U_L2) {
                 nu_pt += wgt * (uxc * uxc + uyc * uyc);
                 dn_u += wgt * (gx * gx + gy * gy);
             } else {
                 nu_pt += wgt * (fabsf(uxc) + fabsf(uyc));
                 dn_u = fmaxf(dn_u, fmaxf(fabsf(gx), fabsf(gy)));
+                const float ox = fmaxf(fabsf(gx) - 1.0f, 0.0f), oy = fmaxf(fabsf(gy) - 1.0f, 0.0f);
+                dist += wgt * (ox * ox + oy * oy);
             }
         }
-        if (UN == VOMT_U_L2) { nu_pt = sqrtf(nu_pt); dn_u = sqrtf(dn_u); }
+        if (UN == VOMT_U_L2) {
+            nu_pt = sqrtf(nu_pt);
+            dn_u = sqrtf(dn_u);
+            const float o = fmaxf(dn_u - 1.0f, 0.0f);
+            dist += o * o;
+        }
         float nw_pt = 0.0f, dn_w = 0.0f;
 #pragma unroll
         for (int e = 0; e < LK; ++e) {
@@ -281,6 +299,7 @@ __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const 
                 const size_t q = e * nn + p;
                 const float we = cur.w[q], dwe = we - prv.w[q], wgt = g.we[e];
                 fdw += wgt * dwe * dwe;
+                q2 += wgt * we * we;
                 float ge = 0.0f;
 #pragma unroll
                 for (int c = 0; c < K; ++c) {
@@ -288,18 +307,31 @@ __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const 
                     gwb[c] -= g.Dv[c][e] * we;      // div y = -Dv y
                     ddiv[c] -= g.Dv[c][e] * dwe;
                 }
-                if (WN == VOMT_W_L1) { nw_pt += wgt * fabsf(we); dn_w = fmaxf(dn_w, fabsf(ge)); }
-                else { nw_pt += wgt * we * we; dn_w += wgt * ge * ge; }
+                if (WN == VOMT_W_L1) {
+                    nw_pt += wgt * fabsf(we);
+                    dn_w = fmaxf(dn_w, fabsf(ge));
+                    const float o = fmaxf(fabsf(ge) - alpha, 0.0f);
+                    dist += wgt * o * o;
+                } else {
+                    nw_pt += wgt * we * we;
+                    dn_w += wgt * ge * ge;
+                }
             }
         }
-        if (WN == VOMT_W_L2) { nw_pt = sqrtf(nw_pt); dn_w = sqrtf(dn_w); }
+        if (WN == VOMT_W_L2) {
+            nw_pt = sqrtf(nw_pt);
+            dn_w = sqrtf(dn_w);
+            const float o = fmaxf(dn_w - alpha, 0.0f);
+            if (g.l > 0) dist += o * o;
+        }
 #pragma unroll
         for (int c = 0; c < K; ++c) {
             const double rc = rdiv[c] + (double)gwb[c];
             v[RED_RR] += (double)g.wc[c] * rc * rc;
             fx += g.wc[c] * dph[c] * ddiv[c];
         }
-        v[RED_P] = (double)(nu_pt + alpha * nw_pt);
+        v[RED_P] = (double)(nu_pt + alpha * nw_pt) + (s.reg ? (double)(s.eps * q2) : 0.0);
+        v[RED_DIST] = s.reg ? (double)dist : 0.0;
         v[RED_D] = (double)fd;
         v[RED_BB] = (double)fbb;
         v[RED_DU] = (double)fdu;
@@ -340,7 +372,7 @@ __global__ void k_finalize(const double *__restrict__ partials, int nblocks, Sol
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        double P = S[RED_P], D = S[RED_D];
+        double P = S[RED_P], D = S[RED_D] - (cfg.eps > 0.0 ? S[RED_DIST] / (4.0 * cfg.eps) : 0.0);
         double m[NMET];
         m[0] = P;
         m[1] = D;
@@ -660,6 +692,7 @@ extern "C" int vomt_solve_noalloc(int n, const float *rho0, const float *rho1, c
     if (pin) p = *pin;
     if (p.max_iters < 0 || p.check_every < 1) { *why = "max_iters >= 0, check_every >= 1"; return VOMT_ERR_BAD_ARG; }
     if (p.u_norm < 0 || p.u_norm > 2 || p.w_norm < 0 || p.w_norm > 1) { *why = "bad norm code"; return VOMT_ERR_BAD_ARG; }
+    if (!(p.eps >= 0.0) || !isfinite(p.eps)) { *why = "eps must be finite and >= 0"; return VOMT_ERR_BAD_ARG; }
     GraphDev gd;
     std::string gerr;
     int rc = graph_to_dev(graph, &gd, &gerr);
@@ -680,6 +713,7 @@ extern "C" int vomt_solve_noalloc(int n, const float *rho0, const float *rho1, c
     }
     StepDev s{n, (float)n1, (float)mu, (float)nu, (float)tau, (float)alpha};
     SolveCfg cfg{p.tol_gap, p.tol_res, mu, nu, tau, g.l > 0};
+    set_regularisation(&s, &cfg, p.eps, mu, nu);
 
     // carve the scratch array
     const int k = g.k, l = g.l;
