@@ -63,6 +63,8 @@ extern "C" {
 #define VOMT_U_L1  2
 #define VOMT_W_L1  0
 #define VOMT_W_L2  1
+#define VOMT_U_NUC 3   /* matrix OMT: ||U||_{1,nuc} = ||U_x||_nuc + ||U_y||_nuc (Section 6.2) */
+#define VOMT_W_NUC 2   /* matrix OMT: ||W||_{1,nuc} = sum_s ||W_s||_nuc (Section 6.2) */
 
 /* Engines.  AUTO picks RESIDENT when the whole state fits in the SMs'
  * registers and shared memory, else STREAM. */
@@ -297,8 +299,13 @@ int vomt_batch_set_threads(vomt_ctx *ctx, int threads);
  *
  * Norms (Section 6.2): u_norm VOMT_U_L2 is ||U||_2 (joint Frobenius over both
  * directions) and VOMT_U_L1 is ||U||_1 (entrywise); the per-channel code
- * VOMT_U_L12 (the vomt_default_params value) selects ||U||_2 here.  w_norm
- * VOMT_W_L1 is ||W||_1 (entrywise), VOMT_W_L2 is ||W||_2 (joint Frobenius).
+ * VOMT_U_L12 (the vomt_default_params value) selects ||U||_2 here; VOMT_U_NUC
+ * is ||U||_{1,nuc} = ||U_x||_nuc + ||U_y||_nuc.  w_norm VOMT_W_L1 is ||W||_1
+ * (entrywise), VOMT_W_L2 is ||W||_2 (joint Frobenius), VOMT_W_NUC is
+ * ||W||_{1,nuc} = sum_s ||W_s||_nuc.  The nuclear shrink soft-thresholds the
+ * singular values (Appendix B): for symmetric U through a per-point Jacobi
+ * eigen-decomposition; for 3 x 3 skew W_s, whose two nonzero singular values
+ * are equal, it scales W_s by max(0, 1 - t / sigma).
  * Step sizes: tau <= 0 picks Table 3's value (10 for n <= 64, 30 for n <= 128,
  * else 60); mu = 1/(32 tau (n-1)^2), nu = 1/(4 tau lambda_max(-Delta_L)) with
  * lambda_max taken over all k x k matrices, as Section 7.3 forms it.

@@ -28,8 +28,8 @@ _lib = None
 NMET = 8
 MET_NAMES = ("primal", "dual", "rel_gap", "rel_res", "fp_resid", "dual_infeas", "iter", "converged")
 
-U_L12, U_L2, U_L1 = 0, 1, 2
-W_L1, W_L2 = 0, 1
+U_L12, U_L2, U_L1, U_NUC = 0, 1, 2, 3      # U_NUC: matrix OMT only (||U_x||_nuc + ||U_y||_nuc)
+W_L1, W_L2, W_NUC = 0, 1, 2                # W_NUC: matrix OMT only (sum_s ||W_s||_nuc)
 
 
 def build(force: bool = False) -> str:
@@ -76,6 +76,9 @@ def _load():
             "orc_momt_solve": (i, [i, i, i, p, p, p, d, d, d, d, i, i, i, i, d, d,
                                    p, p, p, p, p, p, i]),
             "orc_envelope_grad": (None, [i, i, i, i, p, p, p, p, p]),
+            "orc_nuc_norm": (d, [i, p]),
+            "orc_spectral_norm": (d, [i, p]),
+            "orc_shrink_nuc": (None, [i, p, d, p]),
             "orc_vomt_unrolled_grad": (d, [i, i, i, p, p, p, p, p, d, d, d, d, i, i, p, p, p]),
         }
         for name, (res, args) in sig.items():
@@ -115,6 +118,26 @@ def shrink2(x, t: float):
     _load().orc_shrink2(x.size, _ptr(x), float(t), _ptr(out))
     return out
 
+
+
+def nuc_norm(X):
+    """Sum of the singular values of the square matrix X."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    return float(_load().orc_nuc_norm(X.shape[0], _ptr(X)))
+
+
+def spectral_norm(X):
+    """Largest singular value of the square matrix X (the dual of the nuclear norm)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    return float(_load().orc_spectral_norm(X.shape[0], _ptr(X)))
+
+
+def shrink_nuc(X, t: float):
+    """argmin_Z t ||Z||_nuc + ||Z - X||_F^2 / 2 (singular values soft-thresholded by t)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    out = np.zeros_like(X)
+    _load().orc_shrink_nuc(X.shape[0], _ptr(X), float(t), _ptr(out))
+    return out
 
 def jacobi_eigvals(A):
     A = _f64(A)

@@ -29,8 +29,9 @@
  *      2 = ||u||_1    (entrywise).
  *   w: 0 = ||w||_1 (entrywise), 1 = ||w||_2 (joint Euclidean over the edges).
  * For matrices the same codes mean: u 1 = ||U||_2 (joint Frobenius over both
- * directions), 2 = ||U||_1 (entrywise); w 0 = ||W||_1 (entrywise),
- * 1 = ||W||_2 (joint Frobenius over the N components).
+ * directions), 2 = ||U||_1 (entrywise), 3 = ||U||_{1,nuc} (nuclear norms of U_x
+ * and U_y, summed); w 0 = ||W||_1 (entrywise), 1 = ||W||_2 (joint Frobenius over
+ * the N components), 2 = ||W||_{1,nuc} (nuclear norms of the W_s, summed).
  *
  * Metrics written at every check (array of ORC_NMET doubles):
  *   [0] P   primal objective  sum_ij ||u_ij||_u + alpha sum_ij ||w_ij||_w
@@ -736,6 +737,106 @@ int orc_somt_run(int n, const double *rho0, const double *rho1, double tau, doub
 /* ------------------------------------------------------------------------ */
 
 /* Fields: Phi, Ux, Uy, Lam0, Lam1 [k*k][n][n]; W [N*k*k][n][n]. */
+/* ------------------------------------------------------------------------ */
+/* Nuclear norm (Section 6.2; shrink of Appendix B)                           */
+/* ------------------------------------------------------------------------ */
+
+/* Cyclic Jacobi eigen-decomposition of a symmetric m x m matrix A (row-major,
+ * overwritten): on return ev holds the eigenvalues and column j of V the
+ * eigenvector of ev[j].  Rotations as in Golub and Van Loan, Section 8.5. */
+static void jacobi_eig_vectors(int m, double *A, double *V, double *ev)
+{
+    for (int i = 0; i < m * m; ++i) V[i] = 0.0;
+    for (int i = 0; i < m; ++i) V[i * m + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) {
+                tot += A[i * m + j] * A[i * m + j];
+                if (i != j) off += A[i * m + j] * A[i * m + j];
+            }
+        if (off <= 1e-30 * tot || off == 0.0) break;
+        for (int p = 0; p < m; ++p)
+            for (int q = p + 1; q < m; ++q) {
+                double apq = A[p * m + q];
+                if (apq == 0.0) continue;
+                double theta = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
+                double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s_ = t * c;
+                for (int r = 0; r < m; ++r) {           /* A <- A J */
+                    double arp = A[r * m + p], arq = A[r * m + q];
+                    A[r * m + p] = c * arp - s_ * arq;
+                    A[r * m + q] = s_ * arp + c * arq;
+                }
+                for (int r = 0; r < m; ++r) {           /* A <- J^T A */
+                    double apr = A[p * m + r], aqr = A[q * m + r];
+                    A[p * m + r] = c * apr - s_ * aqr;
+                    A[q * m + r] = s_ * apr + c * aqr;
+                }
+                for (int r = 0; r < m; ++r) {           /* V <- V J */
+                    double vrp = V[r * m + p], vrq = V[r * m + q];
+                    V[r * m + p] = c * vrp - s_ * vrq;
+                    V[r * m + q] = s_ * vrp + c * vrq;
+                }
+            }
+    }
+    for (int i = 0; i < m; ++i) ev[i] = A[i * m + i];
+}
+
+/* Singular values of the k x k matrix X (k <= 8): square roots of the
+ * eigenvalues of X^T X; V (optional) gets the right singular vectors. */
+static void singular_values(int k, const double *X, double *sv, double *V)
+{
+    double A[64], Vl[64], ev[8];
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) {
+            double v = 0.0;
+            for (int r = 0; r < k; ++r) v += X[r * k + i] * X[r * k + j];
+            A[i * k + j] = v;
+        }
+    jacobi_eig_vectors(k, A, Vl, ev);
+    for (int i = 0; i < k; ++i) sv[i] = ev[i] > 0.0 ? sqrt(ev[i]) : 0.0;
+    if (V) memcpy(V, Vl, sizeof(double) * k * k);
+}
+
+/* ||X||_nuc, the sum of the singular values, and the spectral norm (its dual). */
+double orc_nuc_norm(int k, const double *X)
+{
+    double sv[8], s = 0.0;
+    singular_values(k, X, sv, NULL);
+    for (int i = 0; i < k; ++i) s += sv[i];
+    return s;
+}
+
+double orc_spectral_norm(int k, const double *X)
+{
+    double sv[8], s = 0.0;
+    singular_values(k, X, sv, NULL);
+    for (int i = 0; i < k; ++i) if (sv[i] > s) s = sv[i];
+    return s;
+}
+
+/* shrink_nuc (Appendix B): argmin_Z t ||Z||_nuc + |Z - X|_F^2 / 2 = U diag((sigma - t)_+) V^T
+ * for X = U diag(sigma) V^T; computed as X V diag((sigma_i - t)_+ / sigma_i) V^T. */
+void orc_shrink_nuc(int k, const double *X, double t, double *out)
+{
+    double sv[8], V[64], f[8], XV[64];
+    singular_values(k, X, sv, V);
+    for (int i = 0; i < k; ++i) f[i] = sv[i] > t ? (sv[i] - t) / sv[i] : 0.0;
+    for (int r = 0; r < k; ++r)
+        for (int i = 0; i < k; ++i) {
+            double v = 0.0;
+            for (int m = 0; m < k; ++m) v += X[r * k + m] * V[m * k + i];
+            XV[r * k + i] = v * f[i];
+        }
+    for (int r = 0; r < k; ++r)
+        for (int c = 0; c < k; ++c) {
+            double v = 0.0;
+            for (int i = 0; i < k; ++i) v += XV[r * k + i] * V[c * k + i];
+            out[r * k + c] = v;
+        }
+}
+
 void orc_momt_metrics(int n, int k, int N, const double *L, const double *Lam0, const double *Lam1,
                       double alpha, int u_norm, int w_norm, double mu, double nu, double tau,
                       const double *Ux, const double *Uy, const double *W, const double *Phi,
@@ -748,17 +849,34 @@ void orc_momt_metrics(int n, int k, int N, const double *L, const double *Lam0, 
     double *gx = (double *)malloc(sizeof(double) * nk), *gy = (double *)malloc(sizeof(double) * nk);
     double *gl = (double *)malloc(sizeof(double) * nw);
     double P = 0.0, D = 0.0, rr = 0.0, bb = 0.0, di = 0.0;
+    double X[64];
     for (size_t p = 0; p < nn; ++p) {
         double su = 0.0, sw = 0.0;
-        for (int q = 0; q < kk; ++q) {
-            if (u_norm == 2) su += fabs(Ux[q * nn + p]) + fabs(Uy[q * nn + p]);
-            else su += Ux[q * nn + p] * Ux[q * nn + p] + Uy[q * nn + p] * Uy[q * nn + p];
+        if (u_norm == 3) {              /* ||U||_{1,nuc} = ||U_x||_nuc + ||U_y||_nuc */
+            for (int q = 0; q < kk; ++q) X[q] = Ux[q * nn + p];
+            su = orc_nuc_norm(k, X);
+            for (int q = 0; q < kk; ++q) X[q] = Uy[q * nn + p];
+            su += orc_nuc_norm(k, X);
+        } else {
+            for (int q = 0; q < kk; ++q) {
+                if (u_norm == 2) su += fabs(Ux[q * nn + p]) + fabs(Uy[q * nn + p]);
+                else su += Ux[q * nn + p] * Ux[q * nn + p] + Uy[q * nn + p] * Uy[q * nn + p];
+            }
+            if (u_norm != 2) su = sqrt(su);
         }
-        for (int q = 0; q < N * kk; ++q) {
-            if (w_norm == 0) sw += fabs(W[q * nn + p]);
-            else sw += W[q * nn + p] * W[q * nn + p];
+        if (w_norm == 2) {              /* ||W||_{1,nuc} = sum_s ||W_s||_nuc */
+            for (int s_ = 0; s_ < N; ++s_) {
+                for (int q = 0; q < kk; ++q) X[q] = W[(s_ * kk + q) * nn + p];
+                sw += orc_nuc_norm(k, X);
+            }
+        } else {
+            for (int q = 0; q < N * kk; ++q) {
+                if (w_norm == 0) sw += fabs(W[q * nn + p]);
+                else sw += W[q * nn + p] * W[q * nn + p];
+            }
+            if (w_norm != 0) sw = sqrt(sw);
         }
-        P += (u_norm == 2 ? su : sqrt(su)) + alpha * (w_norm == 0 ? sw : sqrt(sw));
+        P += su + alpha * sw;
     }
     for (size_t q = 0; q < nk; ++q) D += Phi[q] * (Lam1[q] - Lam0[q]);
     orc_div(n, kk, Ux, Uy, dv);
@@ -772,16 +890,32 @@ void orc_momt_metrics(int n, int k, int N, const double *L, const double *Lam0, 
     orc_grad_L(n, k, N, L, Phi, gl);
     for (size_t p = 0; p < nn; ++p) {
         double s = 0.0, m = 0.0;
-        for (int q = 0; q < kk; ++q) {
-            if (u_norm == 2) { if (fabs(gx[q * nn + p]) > s) s = fabs(gx[q * nn + p]); if (fabs(gy[q * nn + p]) > s) s = fabs(gy[q * nn + p]); }
-            else s += gx[q * nn + p] * gx[q * nn + p] + gy[q * nn + p] * gy[q * nn + p];
+        if (u_norm == 3) {              /* dual of ||.||_{1,nuc}: the larger spectral norm */
+            for (int q = 0; q < kk; ++q) X[q] = gx[q * nn + p];
+            s = orc_spectral_norm(k, X);
+            for (int q = 0; q < kk; ++q) X[q] = gy[q * nn + p];
+            double s2 = orc_spectral_norm(k, X);
+            if (s2 > s) s = s2;
+        } else {
+            for (int q = 0; q < kk; ++q) {
+                if (u_norm == 2) { if (fabs(gx[q * nn + p]) > s) s = fabs(gx[q * nn + p]); if (fabs(gy[q * nn + p]) > s) s = fabs(gy[q * nn + p]); }
+                else s += gx[q * nn + p] * gx[q * nn + p] + gy[q * nn + p] * gy[q * nn + p];
+            }
+            if (u_norm != 2) s = sqrt(s);
         }
-        if (u_norm != 2) s = sqrt(s);
-        for (int q = 0; q < N * kk; ++q) {
-            if (w_norm == 0) { if (fabs(gl[q * nn + p]) > m) m = fabs(gl[q * nn + p]); }
-            else m += gl[q * nn + p] * gl[q * nn + p];
+        if (w_norm == 2) {
+            for (int s_ = 0; s_ < N; ++s_) {
+                for (int q = 0; q < kk; ++q) X[q] = gl[(s_ * kk + q) * nn + p];
+                double v = orc_spectral_norm(k, X);
+                if (v > m) m = v;
+            }
+        } else {
+            for (int q = 0; q < N * kk; ++q) {
+                if (w_norm == 0) { if (fabs(gl[q * nn + p]) > m) m = fabs(gl[q * nn + p]); }
+                else m += gl[q * nn + p] * gl[q * nn + p];
+            }
+            if (w_norm != 0) m = sqrt(m);
         }
-        if (w_norm != 0) m = sqrt(m);
         if (s - 1.0 > di) di = s - 1.0;
         if (m - alpha > di) di = m - alpha;
     }
@@ -849,6 +983,7 @@ int orc_momt_solve(int n, int k, int N, const double *L, const double *Lam0, con
                 v[kk + q] = Uy[q * nn + p] + mu * gy[q * nn + p];
             }
             if (u_norm == 2) for (int q = 0; q < 2 * kk; ++q) o[q] = orc_shrink1(v[q], mu);
+            else if (u_norm == 3) { orc_shrink_nuc(k, v, mu, o); orc_shrink_nuc(k, v + kk, mu, o + kk); }
             else orc_shrink2(2 * kk, v, mu, o);
             for (int q = 0; q < kk; ++q) { nUx[q * nn + p] = o[q]; nUy[q * nn + p] = o[kk + q]; }
         }
@@ -856,6 +991,7 @@ int orc_momt_solve(int n, int k, int N, const double *L, const double *Lam0, con
         for (size_t p = 0; p < nn; ++p) {
             for (int q = 0; q < N * kk; ++q) xw[q] = W[q * nn + p] + nu * gl[q * nn + p];
             if (w_norm == 0) for (int q = 0; q < N * kk; ++q) ow[q] = orc_shrink1(xw[q], alpha * nu);
+            else if (w_norm == 2) for (int s_ = 0; s_ < N; ++s_) orc_shrink_nuc(k, xw + s_ * kk, alpha * nu, ow + s_ * kk);
             else orc_shrink2(N * kk, xw, alpha * nu, ow);
             for (int q = 0; q < N * kk; ++q) nW[q * nn + p] = ow[q];
         }

@@ -16,10 +16,11 @@ import numpy as np
 from . import _native
 from ._native import VomtError, ENGINES
 
-U_L12, U_L2, U_L1 = 0, 1, 2
-W_L1, W_L2 = 0, 1
+U_L12, U_L2, U_L1, U_NUC = 0, 1, 2, 3    # U_NUC: matrix OMT, ||U_x||_nuc + ||U_y||_nuc
+W_L1, W_L2, W_NUC = 0, 1, 2              # W_NUC: matrix OMT, sum_s ||W_s||_nuc
 
-__all__ = ["solve", "solve_host", "step_sizes", "history", "set_wait_policy", "VomtError", "U_L12", "U_L2", "U_L1", "W_L1", "W_L2"]
+__all__ = ["solve", "solve_host", "step_sizes", "history", "set_wait_policy", "VomtError", "U_L12", "U_L2", "U_L1", "U_NUC", "W_L1",
+           "W_L2", "W_NUC"]
 
 
 @dataclass

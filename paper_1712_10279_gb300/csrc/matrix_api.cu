@@ -191,7 +191,9 @@ extern "C" int momt_solve(vomt_ctx *ctx, int n, int k, const float *Lam0, const 
         if (pin) p = *pin;
         if (p.u_norm == VOMT_U_L12) p.u_norm = VOMT_U_L2;
         if (p.max_iters < 0 || p.check_every < 1) return fail(ctx, VOMT_ERR_BAD_ARG, "max_iters >= 0, check_every >= 1");
-        if (p.u_norm < 1 || p.u_norm > 2 || p.w_norm < 0 || p.w_norm > 1) return fail(ctx, VOMT_ERR_BAD_ARG, "bad norm code");
+        if (p.u_norm < 1 || p.u_norm > 3 || p.w_norm < 0 || p.w_norm > 2) return fail(ctx, VOMT_ERR_BAD_ARG, "bad norm code");
+        // 2 x 2 skew components have one entry a and ||W_s||_nuc = 2 |a|, the weighted ||.||_1
+        if (k == 2 && p.w_norm == VOMT_W_NUC) p.w_norm = VOMT_W_L1;
         if (p.engine < 0 || p.engine > 2 || p.halo < 0 || p.halo > 16) return fail(ctx, VOMT_ERR_BAD_ARG, "bad engine / halo");
         if (p.eps != 0.0) return fail(ctx, VOMT_ERR_BAD_ARG, "matrix OMT takes eps = 0 (regularisation is for vector OMT)");
         OpDev op;

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "internal.h"
+#include "matrix_norms.cuh"
 
 namespace vomt {
 namespace dev {
@@ -50,6 +51,10 @@ __device__ __forceinline__ void shrink_u(float (&vx)[K], float (&vy)[K], float t
         float f = shrink2_factor(s2, t);
 #pragma unroll
         for (int c = 0; c < K; ++c) { vx[c] *= f; vy[c] *= f; }
+    } else if (un == VOMT_U_NUC) {
+        // ||U_x||_nuc + ||U_y||_nuc: each direction's symmetric matrix on its own
+        mat::sym_shrink_nuc<K>(vx, t);
+        mat::sym_shrink_nuc<K>(vy, t);
     } else {
 #pragma unroll
         for (int c = 0; c < K; ++c) { vx[c] = soft(vx[c], t); vy[c] = soft(vy[c], t); }
@@ -64,6 +69,19 @@ __device__ __forceinline__ void shrink_w(float (&x)[LK], int l, float t, int wn,
 #pragma unroll
         for (int e = 0; e < LK; ++e)
             if (e < l) x[e] = soft(x[e], t);
+    } else if (wn == VOMT_W_NUC) {
+        // 3 x 3 skew components, entries (a, b, c) consecutive: Euclidean group shrink
+        if constexpr (LK % 3 == 0) {
+#pragma unroll
+            for (int g = 0; g < LK; g += 3) {
+                if (g < l) {
+                    const float f = shrink2_factor(x[g] * x[g] + x[g + 1] * x[g + 1] + x[g + 2] * x[g + 2], t);
+                    x[g] *= f;
+                    x[g + 1] *= f;
+                    x[g + 2] *= f;
+                }
+            }
+        }
     } else {
         float s2 = 0.0f;
 #pragma unroll

@@ -663,6 +663,7 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
             lds<K>(sphi + b + ((f & 1) ? KV : 0), fx);
             lds<K>(sphi + b + ((f & 2) ? RS : 0), fy);
             float nu_pt = 0.0f, dn_u = 0.0f, q2 = 0.0f, dist = 0.0f;
+            float gxs[K], gys[K];
 #pragma unroll
             for (int c = 0; c < K; ++c) {
                 const float uxc = ux[r][c], uyc = uy[r][c], phc = ph[r][c], bc = bb[r][c], wgt = a.g.wc[c];
@@ -675,7 +676,11 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
                 fs[RED_BB] += wgt * bc * bc;
                 fs[RED_D] += wgt * phc * bc;
                 const float gxx = ih * (fx[c] - phc), gyy = ih * (fy[c] - phc);
-                if (un == VOMT_U_L12) {
+                gxs[c] = gxx;
+                gys[c] = gyy;
+                if (un == VOMT_U_NUC) {
+                    // after the loop
+                } else if (un == VOMT_U_L12) {
                     nu_pt += sqrtf(uxc * uxc + uyc * uyc);
                     const float gn = sqrtf(gxx * gxx + gyy * gyy);
                     dn_u = fmaxf(dn_u, gn);
@@ -697,7 +702,16 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
                 const float o = fmaxf(dn_u - 1.0f, 0.0f);
                 dist += o * o;
             }
-            float nw_pt = 0.0f, dn_w = 0.0f;
+            if (un == VOMT_U_NUC) {          // sum of the nuclear norms, larger spectral norm
+                float n1, s1, n2, s2;
+                mat::sym_nuc_spec<K>(ux[r], n1, s1);
+                mat::sym_nuc_spec<K>(uy[r], n2, s2);
+                nu_pt = n1 + n2;
+                mat::sym_nuc_spec<K>(gxs, n1, s1);
+                mat::sym_nuc_spec<K>(gys, n2, s2);
+                dn_u = fmaxf(s1, s2);
+            }
+            float nw_pt = 0.0f, dn_w = 0.0f, wg2 = 0.0f, gg2 = 0.0f;
 #pragma unroll
             for (int e = 0; e < LKv; ++e) {
                 if (e < l) {
@@ -711,6 +725,15 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
                         dn_w = fmaxf(dn_w, fabsf(ge));
                         const float o = fmaxf(fabsf(ge) - alpha, 0.0f);
                         dist += wgt * o * o;
+                    } else if (wn == VOMT_W_NUC) {
+                        // 3 x 3 skew components (a, b, c): ||W_s||_nuc = 2 |(a,b,c)|, spectral |(a,b,c)|
+                        wg2 += we * we;
+                        gg2 += ge * ge;
+                        if (e % 3 == 2) {
+                            nw_pt += 2.0f * sqrtf(wg2);
+                            dn_w = fmaxf(dn_w, sqrtf(gg2));
+                            wg2 = gg2 = 0.0f;
+                        }
                     } else {
                         nw_pt += wgt * we * we;
                         dn_w += wgt * ge * ge;

@@ -10,6 +10,7 @@
 #include <math.h>
 
 #include "internal.h"
+#include "matrix_norms.cuh"
 
 namespace vomt {
 namespace {
@@ -63,6 +64,9 @@ __device__ __forceinline__ void shrink_u(float (&vx)[K], float (&vy)[K], float t
         float f = shrink2_factor(s2, t);
 #pragma unroll
         for (int c = 0; c < K; ++c) { vx[c] *= f; vy[c] *= f; }
+    } else if (UN == VOMT_U_NUC) {
+        mat::sym_shrink_nuc<K>(vx, t);
+        mat::sym_shrink_nuc<K>(vy, t);
     } else {
 #pragma unroll
         for (int c = 0; c < K; ++c) { vx[c] = soft(vx[c], t); vy[c] = soft(vy[c], t); }
@@ -77,6 +81,18 @@ __device__ __forceinline__ void shrink_w(float (&x)[LK], int l, float t, const f
 #pragma unroll
         for (int e = 0; e < LK; ++e)
             if (e < l) x[e] = soft(x[e], t);
+    } else if (WN == VOMT_W_NUC) {
+        if constexpr (LK % 3 == 0) {
+#pragma unroll
+            for (int g = 0; g < LK; g += 3) {
+                if (g < l) {
+                    const float f = shrink2_factor(x[g] * x[g] + x[g + 1] * x[g + 1] + x[g + 2] * x[g + 2], t);
+                    x[g] *= f;
+                    x[g + 1] *= f;
+                    x[g + 2] *= f;
+                }
+            }
+        }
     } else {
         float s2 = 0.0f;
 #pragma unroll
@@ -250,6 +266,7 @@ __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const 
         double rdiv[K];
         float nu_pt = 0.0f, dn_u = 0.0f, fdu = 0.0f, fdp = 0.0f, fd = 0.0f, fbb = 0.0f, fdw = 0.0f, fx = 0.0f;
         float q2 = 0.0f, dist = 0.0f;     // regularisation: squared norms, squared distances to the dual balls
+        float gxs[K], gys[K], uxs[K], uys[K];
 #pragma unroll
         for (int c = 0; c < K; ++c) {
             const size_t q = c * nn + p;
@@ -270,7 +287,13 @@ __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const 
             q2 += wgt * (uxc * uxc + uyc * uyc);
             const float gx = hR ? ih * (cur.phi[q + 1] - ph[c]) : 0.0f;
             const float gy = hU ? ih * (cur.phi[q + n] - ph[c]) : 0.0f;
-            if (UN == VOMT_U_L12) {
+            gxs[c] = gx;
+            gys[c] = gy;
+            uxs[c] = uxc;
+            uys[c] = uyc;
+            if (UN == VOMT_U_NUC) {
+                // after the loop
+            } else if (UN == VOMT_U_L12) {
                 nu_pt += sqrtf(uxc * uxc + uyc * uyc);
                 const float gn = sqrtf(gx * gx + gy * gy);
                 dn_u = fmaxf(dn_u, gn);
@@ -292,7 +315,16 @@ __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const 
             const float o = fmaxf(dn_u - 1.0f, 0.0f);
             dist += o * o;
         }
-        float nw_pt = 0.0f, dn_w = 0.0f;
+        if constexpr (UN == VOMT_U_NUC) {        // sum of the nuclear norms, larger spectral norm
+            float n1, s1, n2, s2;
+            mat::sym_nuc_spec<K>(uxs, n1, s1);
+            mat::sym_nuc_spec<K>(uys, n2, s2);
+            nu_pt = n1 + n2;
+            mat::sym_nuc_spec<K>(gxs, n1, s1);
+            mat::sym_nuc_spec<K>(gys, n2, s2);
+            dn_u = fmaxf(s1, s2);
+        }
+        float nw_pt = 0.0f, dn_w = 0.0f, wg2 = 0.0f, gg2 = 0.0f;
 #pragma unroll
         for (int e = 0; e < LK; ++e) {
             if (e < g.l) {
@@ -312,6 +344,15 @@ __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const 
                     dn_w = fmaxf(dn_w, fabsf(ge));
                     const float o = fmaxf(fabsf(ge) - alpha, 0.0f);
                     dist += wgt * o * o;
+                } else if (WN == VOMT_W_NUC) {
+                    // 3 x 3 skew components (a, b, c): ||W_s||_nuc = 2 |(a,b,c)|, spectral |(a,b,c)|
+                    wg2 += we * we;
+                    gg2 += ge * ge;
+                    if (e % 3 == 2) {
+                        nw_pt += 2.0f * sqrtf(wg2);
+                        dn_w = fmaxf(dn_w, sqrtf(gg2));
+                        wg2 = gg2 = 0.0f;
+                    }
                 } else {
                     nw_pt += wgt * we * we;
                     dn_w += wgt * ge * ge;
@@ -472,6 +513,12 @@ Launchers make_launchers()
 template <int K>
 Launchers pick_norms(int un, int wn)
 {
+    if constexpr (K == 3 || K == 6) {          // nuclear norms: compact 2 x 2 and 3 x 3 matrices
+        if (un == VOMT_U_NUC)
+            return wn == VOMT_W_L1 ? make_launchers<K, 3, 0>()
+                                   : (wn == VOMT_W_L2 ? make_launchers<K, 3, 1>() : make_launchers<K, 3, 2>());
+        if (wn == VOMT_W_NUC) return un == VOMT_U_L2 ? make_launchers<K, 1, 2>() : make_launchers<K, 2, 2>();
+    }
     if (un == VOMT_U_L12) return wn == VOMT_W_L1 ? make_launchers<K, 0, 0>() : make_launchers<K, 0, 1>();
     if (un == VOMT_U_L2) return wn == VOMT_W_L1 ? make_launchers<K, 1, 0>() : make_launchers<K, 1, 1>();
     return wn == VOMT_W_L1 ? make_launchers<K, 2, 0>() : make_launchers<K, 2, 1>();

@@ -143,3 +143,32 @@ def test_matrix_input_errors():
     with pytest.raises(V.VomtError) as e:
         V.momt_solve(t0, torch.from_numpy(asym.astype(np.float32)).to(d), S.paper_L(), 1.0, max_iters=5)
     assert e.value.status in (-1, -2)
+
+
+# ---- nuclear norms (Section 6.2: ||U||_{1,nuc}, ||W||_{1,nuc}; shrink of Appendix B)
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("k", [2, 3])
+@pytest.mark.parametrize("u_norm,w_norm", [(oracle.U_NUC, oracle.W_L1), (oracle.U_NUC, oracle.W_NUC),
+                                           (oracle.U_L2, oracle.W_NUC)])
+def test_matrix_parity_nuclear_norms(engine, k, u_norm, w_norm):
+    L = S.random_L(k, 3 if k == 3 else 2, seed=40 + k)
+    T0, T1 = S.tensor_field_pair(29, k, seed=41 + k)
+    sol, ref = _run(T0, T1, L, 0.7, max_iters=900, check_every=300, engine=engine, u_norm=u_norm, w_norm=w_norm)
+    assert sol.result["engine"] == engine
+    _compare(sol, ref)
+    m = ref["metrics"]
+    assert sol.result["dual_infeas"] == pytest.approx(m["dual_infeas"], rel=1e-3, abs=1e-6)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_matrix_nuclear_isotropic_shift_on_gpu(engine):
+    """||U||_{1,nuc}: an isotropic density moved s cells costs mass x shift (within the
+    tolerance reached)."""
+    n, k, s = 12, 3, 2
+    b0, b1 = S.shifted_blob_pair(n, 1, s, sigma=1.0, margin=2)
+    iso = lambda r: np.stack([(r / k if a == b else 0.0 * r) for a in range(k) for b in range(k)])
+    L = S.paper_L()
+    sol, _ = _run(iso(b0[0]), iso(b1[0]), L, 1.0, tau=10.0, max_iters=100000, check_every=200, tol_gap=1e-5,
+                  tol_res=1e-5, engine=engine, u_norm=oracle.U_NUC)
+    assert sol.result["status"] == 0
+    assert sol.result["primal"] == pytest.approx(s / (n - 1), rel=3e-5)
