@@ -11,6 +11,7 @@
 
 #include "internal.h"
 #include "matrix_norms.cuh"
+#include "stream_tma.h"
 
 namespace vomt {
 namespace {
@@ -620,6 +621,11 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
     ctx->launches += 1;
 
     Launchers L = pick(k, p.u_norm, p.w_norm);
+    // TMA tiles for the iteration where they apply (n a multiple of 4, k <= 4)
+    TmaPlan *tp = tma_step_supported(n, k, l, p.u_norm, p.w_norm)
+                      ? tma_plan_create(n, k, l, p.u_norm, p.w_norm, so[0].phi, so[1].phi, b)
+                      : nullptr;
+    if (tp) ctx->last_blocks = ((n + 63) / 64) * ((n + 15) / 16);    // the step's 64 x 16 tiles
     auto check = [&](int t, int cur) {
         L.metrics<<<grd, blk, 0, st>>>(si[cur], si[cur ^ 1], b, g, s, ctx->partials, ctx->dstatus);
         k_finalize<<<1, 256, 0, st>>>(ctx->partials, nblocks, cfg, t, ctx->dstatus, ctx->dhist, ctx->hist_cap);
@@ -642,7 +648,10 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
         const int end = t + chunk < p.max_iters ? t + chunk : p.max_iters;
         for (int tt = t + 1; tt <= end; ++tt) {
             const int cur = tt & 1;
-            L.step<<<grd, blk, 0, st>>>(si[cur ^ 1], so[cur], b, g, s, ctx->dstatus);
+            if (tp)
+                tma_launch_step(tp, cur ^ 1, so[cur].phi, g, s, ctx->dstatus, st);
+            else
+                L.step<<<grd, blk, 0, st>>>(si[cur ^ 1], so[cur], b, g, s, ctx->dstatus);
             ctx->launches += 1;
             if (tt % p.check_every == 0 || tt == p.max_iters) check(tt, cur);
         }
@@ -661,6 +670,7 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
     }
     k_copy_out<<<pblocks, 256, 0, st>>>(n, k, l, si[0], si[1], ctx->dstatus, u, w, phi);
     ctx->launches += 1;
+    tma_plan_destroy(tp);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         for (int q = 0; q < 2; ++q) if (ev[q]) cudaEventDestroy(ev[q]);
