@@ -238,6 +238,7 @@ void vomt_destroy(vomt_ctx *c)
 {
     if (!c) return;
     cudaSetDevice(c->device);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->ws) cudaFree(c->ws);
     if (c->partials) cudaFree(c->partials);
     if (c->dstatus) cudaFree(c->dstatus);

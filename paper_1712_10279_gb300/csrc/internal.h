@@ -147,6 +147,8 @@ struct vomt_ctx {
     // resident-engine scratch
     void *rscratch = nullptr;
     size_t rscratch_bytes = 0;
+    // stream on which the streaming engine captures its iteration graphs
+    cudaStream_t cap_stream = nullptr;
     // bounded waits of the resident engine: limit (0 = default) and the test hook
     unsigned long long wait_ns = 0;
     int drop_exchange = 0;

@@ -414,6 +414,7 @@ __global__ void k_finalize(const double *__restrict__ partials, int nblocks, Sol
         __syncthreads();
     }
     if (threadIdx.x == 0) {
+        if (t < 0) t = st->iter - t;       // in a replayed graph: the last check's iteration plus -t
         double P = S[RED_P], D = S[RED_D] - (cfg.eps > 0.0 ? S[RED_DIST] / (4.0 * cfg.eps) : 0.0);
         double m[NMET];
         m[0] = P;
@@ -638,6 +639,39 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
     }
     const bool tol_mode = cfg.tol_gap > 0.0;
     int chunk = p.check_every * ((2048 + p.check_every - 1) / p.check_every);
+    // Long solves replay a captured CUDA graph of G iterations (G = check_every, made
+    // even so that the ping-pong parity repeats, and its checks), cutting the launch
+    // gaps between the short kernels of mid-size grids.  Captured on the context's
+    // own stream, launched on the caller's.
+    const int G = (p.check_every % 2 == 0) ? p.check_every : 2 * p.check_every;
+    cudaGraphExec_t gexec = nullptr;
+    if (G <= 512 && p.max_iters >= 4 * G) {
+        if (!ctx->cap_stream) cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+        cudaGraph_t graph = nullptr;
+        if (ctx->cap_stream && cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            for (int tt = 1; tt <= G; ++tt) {
+                const int cur = tt & 1;
+                if (tp)
+                    tma_launch_step(tp, cur ^ 1, so[cur].phi, g, s, ctx->dstatus, ctx->cap_stream);
+                else
+                    L.step<<<grd, blk, 0, ctx->cap_stream>>>(si[cur ^ 1], so[cur], b, g, s, ctx->dstatus);
+                if (tt % p.check_every == 0) {
+                    L.metrics<<<grd, blk, 0, ctx->cap_stream>>>(si[cur], si[cur ^ 1], b, g, s, ctx->partials,
+                                                                 ctx->dstatus);
+                    k_finalize<<<1, 256, 0, ctx->cap_stream>>>(ctx->partials, nblocks, cfg, -p.check_every,
+                                                                ctx->dstatus, ctx->dhist, ctx->hist_cap);
+                }
+            }
+            if (cudaStreamEndCapture(ctx->cap_stream, &graph) != cudaSuccess ||
+                cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess)
+                gexec = nullptr;
+            if (graph) cudaGraphDestroy(graph);
+        }
+        cudaGetLastError();          // a failed capture leaves the plain launches below
+    }
+    const int per_graph_launches = G + 2 * (G / p.check_every);
+    // graph replays need an even starting iteration: chunks are whole multiples of G
+    if (gexec) chunk = G * ((2048 + G - 1) / G);
     cudaEvent_t ev[2] = {nullptr, nullptr};
     if (tol_mode) {
         for (int q = 0; q < 2; ++q) cudaEventCreateWithFlags(&ev[q], cudaEventDisableTiming);
@@ -646,6 +680,13 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
     bool stopped = false;
     while (t < p.max_iters && !stopped) {
         const int end = t + chunk < p.max_iters ? t + chunk : p.max_iters;
+        if (gexec) {
+            while (t + G <= end) {
+                cudaGraphLaunch(gexec, st);
+                ctx->launches += per_graph_launches;
+                t += G;
+            }
+        }
         for (int tt = t + 1; tt <= end; ++tt) {
             const int cur = tt & 1;
             if (tp)
@@ -670,6 +711,10 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
     }
     k_copy_out<<<pblocks, 256, 0, st>>>(n, k, l, si[0], si[1], ctx->dstatus, u, w, phi);
     ctx->launches += 1;
+    if (gexec) {
+        cudaStreamSynchronize(st);
+        cudaGraphExecDestroy(gexec);
+    }
     tma_plan_destroy(tp);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
