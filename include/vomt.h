@@ -171,6 +171,25 @@ int vomt_solve_host(vomt_ctx *ctx, int n, const float *rho0, const float *rho1,
                     const vomt_graph *g, double alpha, const vomt_params *p,
                     float *u, float *w, float *phi, vomt_result *result, void *stream);
 
+/* Vector OMT on an n x n x n grid: the finite-volume discretization of
+ * Appendix A with a third direction (gradient, backward-difference divergence
+ * and ghost faces in z as in x and y), iterated as in Section 7.2 with one
+ * fused launch per iteration.  2 <= n <= 1024.
+ *   rho0, rho1: device [k][n][n][n] cell masses (x fastest).
+ *   u: device [3][k][n][n][n], the planes u_x, u_y, u_z; each component's
+ *      ghost face (last index in its own direction) stays zero.
+ *   w: device [l][n][n][n]; phi: device [k][n][n][n].
+ * Outputs (inputs too when p->warm_start), like vomt_solve.  Norms: u_norm in
+ * {L12, L2, L1} (the 2-norm over the three directions at a point), w_norm in
+ * {L1, L2}; p->eps must be 0; p->engine and p->halo are ignored.  Default mu
+ * is 1/(48 tau (n-1)^2) (1/(24 tau (n-1)^2) without edges), since
+ * ||grad||^2 <= 12 (n-1)^2 in 3-D; user mu, nu must satisfy
+ * tau mu 12 (n-1)^2 + tau nu lambda_max(-Delta_G) < 1.  The history is that of
+ * vomt_history().  Errors: those of vomt_solve. */
+int vomt_solve3d(vomt_ctx *ctx, int n, const float *rho0, const float *rho1,
+                 const vomt_graph *g, double alpha, const vomt_params *p,
+                 float *u, float *w, float *phi, vomt_result *result, void *stream);
+
 /* Metrics of every convergence check of the last solve on ctx, 8 doubles per
  * row: primal, dual, rel_gap, rel_res, fp_resid, dual_infeas, iteration,
  * converged flag.  Writes min(cap, checks) rows to host `out`; returns the

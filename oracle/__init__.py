@@ -77,6 +77,13 @@ def _load():
                                    p, p, p, p, p, p, i]),
             "orc_envelope_grad": (None, [i, i, i, i, p, p, p, p, p]),
             "orc_nuc_norm": (d, [i, p]),
+            "orc_grad3": (None, [i, i, p, p, p, p]),
+            "orc_div3": (None, [i, i, p, p, p, p]),
+            "orc_step_mu3": (d, [i, d, i]),
+            "orc_vomt3_metrics": (None, [i, i, i, p, p, p, p, p, d, i, i, d, d, d,
+                                         p, p, p, p, p, p, p, p, p, p, p]),
+            "orc_vomt3_solve": (i, [i, i, i, p, p, p, p, p, d, d, d, d, i, i, i, i, d, d,
+                                    p, p, p, p, p, p, p, i]),
             "orc_spectral_norm": (d, [i, p]),
             "orc_shrink_nuc": (None, [i, p, d, p]),
             "orc_vomt_unrolled_grad": (d, [i, i, i, p, p, p, p, p, d, d, d, d, i, i, p, p, p]),
@@ -408,3 +415,55 @@ def unrolled_grad(rho0, rho1, edges, alpha, T, tau=None, mu=None, nu=None, cost=
                                        float(alpha), float(tau), float(mu), float(nu), int(w_norm),
                                        int(T), _ptr(g1), _ptr(g0), _ptr(ga))
     return J, g1, g0, float(ga[0])
+
+
+# ---------------------------------------------------------------- 3-D grids
+def grad3(phi):
+    """Forward differences on an n x n x n grid, [planes, z, y, x]; ghost entries zero."""
+    phi = _f64(phi)
+    planes, n = phi.shape[0], phi.shape[-1]
+    gx, gy, gz = (np.zeros_like(phi) for _ in range(3))
+    _load().orc_grad3(n, planes, _ptr(phi), _ptr(gx), _ptr(gy), _ptr(gz))
+    return gx, gy, gz
+
+
+def div3(ux, uy, uz):
+    ux, uy, uz = _f64(ux), _f64(uy), _f64(uz)
+    planes, n = ux.shape[0], ux.shape[-1]
+    out = np.zeros_like(ux)
+    _load().orc_div3(n, planes, _ptr(ux), _ptr(uy), _ptr(uz), _ptr(out))
+    return out
+
+
+def vomt3_solve(rho0, rho1, edges, alpha=1.0, tau=None, mu=None, nu=None, cost=None, u_norm=U_L12, w_norm=W_L1,
+                max_iters=2000, check_every=100, tol_gap=0.0, tol_res=0.0, init=None, history=False):
+    """V-OMT by PDHG on an n x n x n grid (the 3-D extension of Section 7.2).  rho0, rho1:
+    [k, n, n, n] cell masses.  mu defaults to 1/(48 tau (n-1)^2) (1/(24 ...) without edges)."""
+    rho0, rho1 = _f64(rho0), _f64(rho1)
+    k, n = rho0.shape[0], rho0.shape[-1]
+    a, b = _edges(edges)
+    l = a.size
+    c = _cost(cost, l)
+    if tau is None:
+        tau = default_tau_vector(n)
+    if mu is None:
+        mu = float(_load().orc_step_mu3(n, float(tau), int(l > 0)))
+    if nu is None:
+        nu = 1.0 / (4.0 * tau * graph_lmax(k, edges, cost)) if l else 0.0
+    if init is None:
+        ux, uy, uz = (np.zeros((k, n, n, n)) for _ in range(3))
+        w = np.zeros((l, n, n, n)); phi = np.zeros((k, n, n, n))
+    else:
+        ux, uy, uz, w, phi = (np.array(init[x], dtype=np.float64, copy=True) for x in ("ux", "uy", "uz", "w", "phi"))
+    nchk = max_iters // max(check_every, 1) + 2
+    hist = np.zeros((nchk, NMET))
+    met = np.zeros(NMET)
+    it = _load().orc_vomt3_solve(n, k, l, _ptr(a), _ptr(b), _ptr(c), _ptr(rho0), _ptr(rho1), float(alpha),
+                                 float(tau), float(mu), float(nu), u_norm, w_norm, int(max_iters), int(check_every),
+                                 float(tol_gap), float(tol_res), _ptr(ux), _ptr(uy), _ptr(uz), _ptr(w), _ptr(phi),
+                                 _ptr(met), _ptr(hist), nchk)
+    out = dict(ux=ux, uy=uy, uz=uz, w=w, phi=phi, iters=it, mu=mu, nu=nu, tau=tau,
+               metrics=dict(zip(MET_NAMES, met)))
+    if history:
+        out["history"] = hist[hist[:, 6] > 0]
+    return out

@@ -1192,3 +1192,276 @@ double orc_vomt_unrolled_grad(int n, int k, int l, const int *ea, const int *eb,
     free(pgx); free(pgy); free(pgG);
     return J;
 }
+
+/* ------------------------------------------------------------------------ */
+/* 3-D grids (the extension to volumes the paper points to for 3-D DTI,       */
+/* Section 8.2): the discretization of Appendix A with a third direction      */
+/* ------------------------------------------------------------------------ */
+/*
+ * n x n x n cells on [0,1]^3, h = 1/(n-1); fields [c][z][y][x] with x fastest.
+ * Flux components u_x, u_y, u_z per channel; u_x has its ghost entries at
+ * x = n-1, u_y at y = n-1, u_z at z = n-1 (kept zero by the iteration).
+ *   (grad phi)_d = (phi(. + e_d) - phi) / h, zero where . + e_d leaves the grid;
+ *   div u = (u_x - u_x(x-1) + u_y - u_y(y-1) + u_z - u_z(z-1)) / h, with the
+ *   terms before the first cell of a direction taken as zero.
+ * Norms per point as in 2-D with three spatial components per channel:
+ * ||u||_{1,2} = sum_c |(u_x, u_y, u_z)_c|_2, ||u||_2 joint, ||u||_1 entrywise.
+ * Step rule (reading of this build): ||grad||^2 <= 12 / h^2 in 3-D, so
+ * mu = 1 / (48 tau (n-1)^2) keeps the 2-D rule's share of the bound
+ * (8/32 = 12/48); nu as in 2-D.
+ */
+#define AT3(c, z, y, x) ((((size_t)(c) * (size_t)n + (size_t)(z)) * (size_t)n + (size_t)(y)) * (size_t)n + (size_t)(x))
+
+void orc_grad3(int n, int planes, const double *phi, double *gx, double *gy, double *gz)
+{
+    double ih = (double)(n - 1);
+    for (int c = 0; c < planes; ++c)
+        for (int z = 0; z < n; ++z)
+            for (int y = 0; y < n; ++y)
+                for (int x = 0; x < n; ++x) {
+                    double p = phi[AT3(c, z, y, x)];
+                    gx[AT3(c, z, y, x)] = (x < n - 1) ? ih * (phi[AT3(c, z, y, x + 1)] - p) : 0.0;
+                    gy[AT3(c, z, y, x)] = (y < n - 1) ? ih * (phi[AT3(c, z, y + 1, x)] - p) : 0.0;
+                    gz[AT3(c, z, y, x)] = (z < n - 1) ? ih * (phi[AT3(c, z + 1, y, x)] - p) : 0.0;
+                }
+}
+
+void orc_div3(int n, int planes, const double *ux, const double *uy, const double *uz, double *out)
+{
+    double ih = (double)(n - 1);
+    for (int c = 0; c < planes; ++c)
+        for (int z = 0; z < n; ++z)
+            for (int y = 0; y < n; ++y)
+                for (int x = 0; x < n; ++x) {
+                    double xl = (x > 0) ? ux[AT3(c, z, y, x - 1)] : 0.0;
+                    double yl = (y > 0) ? uy[AT3(c, z, y - 1, x)] : 0.0;
+                    double zl = (z > 0) ? uz[AT3(c, z - 1, y, x)] : 0.0;
+                    out[AT3(c, z, y, x)] =
+                        ih * (ux[AT3(c, z, y, x)] - xl + uy[AT3(c, z, y, x)] - yl + uz[AT3(c, z, y, x)] - zl);
+                }
+}
+
+/* graph gradient and divergence at every one of m points (planes of m values) */
+static void grad_G_pts(size_t m, int l, const int *ea, const int *eb, const double *cost, const double *phi,
+                       double *g)
+{
+    for (int e = 0; e < l; ++e) {
+        int lo = ea[e] < eb[e] ? ea[e] : eb[e], hi = ea[e] < eb[e] ? eb[e] : ea[e];
+        double ic = 1.0 / edge_cost(cost, e);
+        for (size_t p = 0; p < m; ++p) g[e * m + p] = ic * (phi[lo * m + p] - phi[hi * m + p]);
+    }
+}
+
+static void div_G_pts(size_t m, int k, int l, const int *ea, const int *eb, const double *cost, const double *y,
+                      double *out)
+{
+    for (size_t q = 0; q < (size_t)k * m; ++q) out[q] = 0.0;
+    for (int e = 0; e < l; ++e) {
+        int lo = ea[e] < eb[e] ? ea[e] : eb[e], hi = ea[e] < eb[e] ? eb[e] : ea[e];
+        double ic = 1.0 / edge_cost(cost, e);
+        for (size_t p = 0; p < m; ++p) {
+            double v = ic * y[e * m + p];
+            out[lo * m + p] -= v;
+            out[hi * m + p] += v;
+        }
+    }
+}
+
+static void shrink_u3_point(int k, int u_norm, double t, double *vx, double *vy, double *vz)
+{
+    if (u_norm == 0) {
+        for (int c = 0; c < k; ++c) {
+            double v[3] = {vx[c], vy[c], vz[c]}, o[3];
+            orc_shrink2(3, v, t, o);
+            vx[c] = o[0]; vy[c] = o[1]; vz[c] = o[2];
+        }
+    } else if (u_norm == 1) {
+        double v[96], o[96];
+        for (int c = 0; c < k; ++c) { v[c] = vx[c]; v[k + c] = vy[c]; v[2 * k + c] = vz[c]; }
+        orc_shrink2(3 * k, v, t, o);
+        for (int c = 0; c < k; ++c) { vx[c] = o[c]; vy[c] = o[k + c]; vz[c] = o[2 * k + c]; }
+    } else {
+        for (int c = 0; c < k; ++c) {
+            vx[c] = orc_shrink1(vx[c], t); vy[c] = orc_shrink1(vy[c], t); vz[c] = orc_shrink1(vz[c], t);
+        }
+    }
+}
+
+static double norm_u3_point(int k, int u_norm, const double *a, const double *b, const double *z)
+{
+    double s = 0.0;
+    if (u_norm == 0) {
+        for (int c = 0; c < k; ++c) s += sqrt(a[c] * a[c] + b[c] * b[c] + z[c] * z[c]);
+    } else if (u_norm == 1) {
+        for (int c = 0; c < k; ++c) s += a[c] * a[c] + b[c] * b[c] + z[c] * z[c];
+        s = sqrt(s);
+    } else {
+        for (int c = 0; c < k; ++c) s += fabs(a[c]) + fabs(b[c]) + fabs(z[c]);
+    }
+    return s;
+}
+
+static double dualnorm_u3_point(int k, int u_norm, const double *a, const double *b, const double *z)
+{
+    double s = 0.0;
+    if (u_norm == 0) {
+        for (int c = 0; c < k; ++c) {
+            double v = sqrt(a[c] * a[c] + b[c] * b[c] + z[c] * z[c]);
+            if (v > s) s = v;
+        }
+    } else if (u_norm == 1) {
+        for (int c = 0; c < k; ++c) s += a[c] * a[c] + b[c] * b[c] + z[c] * z[c];
+        s = sqrt(s);
+    } else {
+        for (int c = 0; c < k; ++c) {
+            if (fabs(a[c]) > s) s = fabs(a[c]);
+            if (fabs(b[c]) > s) s = fabs(b[c]);
+            if (fabs(z[c]) > s) s = fabs(z[c]);
+        }
+    }
+    return s;
+}
+
+double orc_step_mu3(int n, double tau, int has_w)
+{
+    double n1 = (double)(n - 1);
+    return has_w ? 1.0 / (48.0 * tau * n1 * n1) : 1.0 / (24.0 * tau * n1 * n1);
+}
+
+/* Metrics of a 3-D state (the same eight numbers as orc_vomt_metrics). */
+void orc_vomt3_metrics(int n, int k, int l, const int *ea, const int *eb, const double *cost,
+                       const double *rho0, const double *rho1, double alpha, int u_norm, int w_norm,
+                       double mu, double nu, double tau,
+                       const double *ux, const double *uy, const double *uz, const double *w, const double *phi,
+                       const double *pux, const double *puy, const double *puz, const double *pw,
+                       const double *pphi, double *out)
+{
+    size_t m = (size_t)n * n * n, nk = (size_t)k * m, nl = (size_t)l * m;
+    double *dv = (double *)malloc(sizeof(double) * nk), *dg = (double *)malloc(sizeof(double) * nk);
+    double *gx = (double *)malloc(sizeof(double) * nk), *gy = (double *)malloc(sizeof(double) * nk);
+    double *gz = (double *)malloc(sizeof(double) * nk);
+    double *gg = (double *)malloc(sizeof(double) * (nl ? nl : 1));
+    double a[32], b[32], z[32], c3[64];
+    double P = 0.0, D = 0.0, rr = 0.0, bb = 0.0, di = 0.0, R = 0.0;
+    for (size_t p = 0; p < m; ++p) {
+        for (int c = 0; c < k; ++c) { a[c] = ux[c * m + p]; b[c] = uy[c * m + p]; z[c] = uz[c * m + p]; }
+        P += norm_u3_point(k, u_norm, a, b, z);
+        for (int e = 0; e < l; ++e) c3[e] = w[e * m + p];
+        P += alpha * norm_w_point(l, w_norm, c3);
+    }
+    for (size_t q = 0; q < nk; ++q) D += phi[q] * (rho1[q] - rho0[q]);
+    orc_div3(n, k, ux, uy, uz, dv);
+    div_G_pts(m, k, l, ea, eb, cost, w, dg);
+    for (size_t q = 0; q < nk; ++q) {
+        double r = dv[q] + dg[q] - (rho0[q] - rho1[q]);
+        rr += r * r;
+        bb += (rho0[q] - rho1[q]) * (rho0[q] - rho1[q]);
+    }
+    orc_grad3(n, k, phi, gx, gy, gz);
+    if (l) grad_G_pts(m, l, ea, eb, cost, phi, gg);
+    for (size_t p = 0; p < m; ++p) {
+        for (int c = 0; c < k; ++c) { a[c] = gx[c * m + p]; b[c] = gy[c * m + p]; z[c] = gz[c * m + p]; }
+        double v = dualnorm_u3_point(k, u_norm, a, b, z) - 1.0;
+        if (v > di) di = v;
+        if (l) {
+            for (int e = 0; e < l; ++e) c3[e] = gg[e * m + p];
+            v = dualnorm_w_point(l, w_norm, c3) - alpha;
+            if (v > di) di = v;
+        }
+    }
+    if (pux) {
+        double *du[3], su = 0.0, sw = 0.0, sp = 0.0, cr = 0.0;
+        double *dw = (double *)malloc(sizeof(double) * (nl ? nl : 1));
+        const double *cu[3] = {ux, uy, uz}, *pu[3] = {pux, puy, puz};
+        for (int d = 0; d < 3; ++d) {
+            du[d] = (double *)malloc(sizeof(double) * nk);
+            for (size_t q = 0; q < nk; ++q) { du[d][q] = cu[d][q] - pu[d][q]; su += du[d][q] * du[d][q]; }
+        }
+        for (size_t q = 0; q < nk; ++q) sp += (phi[q] - pphi[q]) * (phi[q] - pphi[q]);
+        for (size_t q = 0; q < nl; ++q) { dw[q] = w[q] - pw[q]; sw += dw[q] * dw[q]; }
+        orc_div3(n, k, du[0], du[1], du[2], dv);
+        div_G_pts(m, k, l, ea, eb, cost, dw, dg);
+        for (size_t q = 0; q < nk; ++q) cr += (phi[q] - pphi[q]) * (dv[q] + dg[q]);
+        R = su / mu + (l ? sw / nu : 0.0) + sp / tau - 2.0 * cr;
+        for (int d = 0; d < 3; ++d) free(du[d]);
+        free(dw);
+    }
+    out[0] = P;
+    out[1] = D;
+    out[2] = fabs(P - D) / (fabs(P) > 1e-300 ? fabs(P) : 1e-300);
+    out[3] = sqrt(rr) / (bb > 0.0 ? sqrt(bb) : 1.0);
+    out[4] = R;
+    out[5] = di;
+    free(dv); free(dg); free(gx); free(gy); free(gz); free(gg);
+}
+
+/* V-OMT by PDHG on a 3-D grid: the loop of Section 7.2 with the 3-D operators. */
+int orc_vomt3_solve(int n, int k, int l, const int *ea, const int *eb, const double *cost,
+                    const double *rho0, const double *rho1, double alpha,
+                    double tau, double mu, double nu, int u_norm, int w_norm,
+                    int max_iters, int check_every, double tol_gap, double tol_res,
+                    double *ux, double *uy, double *uz, double *w, double *phi,
+                    double *metrics, double *history, int hist_cap)
+{
+    size_t m = (size_t)n * n * n, nk = (size_t)k * m, nl = (size_t)l * m;
+    double *gx = (double *)malloc(sizeof(double) * nk), *gy = (double *)malloc(sizeof(double) * nk);
+    double *gz = (double *)malloc(sizeof(double) * nk);
+    double *nux = (double *)malloc(sizeof(double) * nk), *nuy = (double *)malloc(sizeof(double) * nk);
+    double *nuz = (double *)malloc(sizeof(double) * nk);
+    double *gg = (double *)malloc(sizeof(double) * (nl ? nl : 1)), *nw = (double *)malloc(sizeof(double) * (nl ? nl : 1));
+    double *bx = (double *)malloc(sizeof(double) * nk), *by = (double *)malloc(sizeof(double) * nk);
+    double *bz = (double *)malloc(sizeof(double) * nk), *bw = (double *)malloc(sizeof(double) * (nl ? nl : 1));
+    double *dv = (double *)malloc(sizeof(double) * nk), *dg = (double *)malloc(sizeof(double) * nk);
+    double *pphi = (double *)malloc(sizeof(double) * nk);
+    double a[32], b[32], z[32], x[64];
+    int nh = 0, t = 0;
+    if (check_every <= 0) check_every = max_iters > 0 ? max_iters : 1;
+    for (t = 1; t <= max_iters; ++t) {
+        orc_grad3(n, k, phi, gx, gy, gz);
+        for (size_t p = 0; p < m; ++p) {
+            for (int c = 0; c < k; ++c) {
+                a[c] = ux[c * m + p] + mu * gx[c * m + p];
+                b[c] = uy[c * m + p] + mu * gy[c * m + p];
+                z[c] = uz[c * m + p] + mu * gz[c * m + p];
+            }
+            shrink_u3_point(k, u_norm, mu, a, b, z);
+            for (int c = 0; c < k; ++c) { nux[c * m + p] = a[c]; nuy[c * m + p] = b[c]; nuz[c * m + p] = z[c]; }
+        }
+        if (l) {
+            grad_G_pts(m, l, ea, eb, cost, phi, gg);
+            for (size_t p = 0; p < m; ++p) {
+                for (int e = 0; e < l; ++e) x[e] = w[e * m + p] + nu * gg[e * m + p];
+                shrink_w_point(l, w_norm, alpha * nu, x);
+                for (int e = 0; e < l; ++e) nw[e * m + p] = x[e];
+            }
+        }
+        for (size_t q = 0; q < nk; ++q) {
+            bx[q] = 2.0 * nux[q] - ux[q]; by[q] = 2.0 * nuy[q] - uy[q]; bz[q] = 2.0 * nuz[q] - uz[q];
+        }
+        for (size_t q = 0; q < nl; ++q) bw[q] = 2.0 * nw[q] - w[q];
+        orc_div3(n, k, bx, by, bz, dv);
+        if (l) div_G_pts(m, k, l, ea, eb, cost, bw, dg);
+        else for (size_t q = 0; q < nk; ++q) dg[q] = 0.0;
+        memcpy(pphi, phi, sizeof(double) * nk);
+        for (size_t q = 0; q < nk; ++q) phi[q] = phi[q] + tau * (dv[q] + dg[q] + rho1[q] - rho0[q]);
+        int check = (t % check_every == 0) || (t == max_iters);
+        double met[ORC_NMET];
+        if (check) {
+            orc_vomt3_metrics(n, k, l, ea, eb, cost, rho0, rho1, alpha, u_norm, w_norm, mu, nu, tau,
+                              nux, nuy, nuz, nw, phi, ux, uy, uz, w, pphi, met);
+            met[6] = (double)t;
+            met[7] = (tol_gap > 0.0 && met[2] <= tol_gap && met[3] <= tol_res) ? 1.0 : 0.0;
+            if (history && nh < hist_cap) { memcpy(history + (size_t)nh * ORC_NMET, met, sizeof met); ++nh; }
+            if (metrics) memcpy(metrics, met, sizeof met);
+        }
+        memcpy(ux, nux, sizeof(double) * nk);
+        memcpy(uy, nuy, sizeof(double) * nk);
+        memcpy(uz, nuz, sizeof(double) * nk);
+        if (l) memcpy(w, nw, sizeof(double) * nl);
+        if (check && met[7] != 0.0) break;
+    }
+    if (t > max_iters) t = max_iters;
+    free(gx); free(gy); free(gz); free(nux); free(nuy); free(nuz); free(gg); free(nw);
+    free(bx); free(by); free(bz); free(bw); free(dv); free(dg); free(pphi);
+    return t;
+}

@@ -19,7 +19,7 @@ from ._native import VomtError, ENGINES
 U_L12, U_L2, U_L1, U_NUC = 0, 1, 2, 3    # U_NUC: matrix OMT, ||U_x||_nuc + ||U_y||_nuc
 W_L1, W_L2, W_NUC = 0, 1, 2              # W_NUC: matrix OMT, sum_s ||W_s||_nuc
 
-__all__ = ["solve", "solve_host", "step_sizes", "history", "set_wait_policy", "VomtError", "U_L12", "U_L2", "U_L1", "U_NUC", "W_L1",
+__all__ = ["solve", "solve_host", "solve3d", "step_sizes", "history", "set_wait_policy", "VomtError", "U_L12", "U_L2", "U_L1", "U_NUC", "W_L1",
            "W_L2", "W_NUC"]
 
 
@@ -93,6 +93,43 @@ def solve(rho0, rho1, edges, alpha: float = 1.0, *, tau=None, mu=None, nu=None, 
     rc = _native.load().vomt_solve(ctx, int(n), rho0.data_ptr(), rho1.data_ptr(), g.ref, float(alpha),
                                    ctypes.byref(p), u.data_ptr(), w.data_ptr() if l else None, phi.data_ptr(),
                                    ctypes.byref(res), ctypes.c_void_p(st))
+    _native.check(rc, ctx)
+    return Solution(u, w, phi, res.as_dict())
+
+
+def solve3d(rho0, rho1, edges, alpha: float = 1.0, *, tau=None, mu=None, nu=None, cost=None,
+            u_norm: int = U_L12, w_norm: int = W_L1, max_iters: int = 2000, check_every: int = 100,
+            tol_gap: float = 0.0, tol_res: float = 0.0, init=None, stream=None) -> Solution:
+    """Vector OMT on an n x n x n grid (Appendix A's discretization with a third direction).
+
+    rho0, rho1: CUDA float32 tensors [k, n, n, n] (cell masses, [c, z, y, x]).  Returns u as
+    [3, k, n, n, n] (u_x, u_y, u_z), w [l, n, n, n], phi [k, n, n, n] and the metrics of the
+    last FP64 check.  Default mu = 1/(48 tau (n-1)^2) (1/(24 ...) without edges).
+    """
+    import torch
+    if not (rho0.is_cuda and rho1.is_cuda):
+        raise ValueError("rho0 and rho1 must be CUDA tensors")
+    rho0 = rho0.contiguous().float()
+    rho1 = rho1.contiguous().float()
+    if rho0.dim() != 4 or rho0.shape != rho1.shape or not (rho0.shape[1] == rho0.shape[2] == rho0.shape[3]):
+        raise ValueError("rho0 and rho1 must be [k, n, n, n] of one shape")
+    k, n = rho0.shape[0], rho0.shape[-1]
+    dev = rho0.device
+    g = _native.GraphArg(k, edges, cost)
+    l = g.tail.size
+    if init is not None:
+        u, w, phi = (x.detach().clone().contiguous().float() for x in init)
+    else:
+        u = torch.empty((3, k, n, n, n), device=dev, dtype=torch.float32)
+        w = torch.empty((max(l, 0), n, n, n), device=dev, dtype=torch.float32)
+        phi = torch.empty((k, n, n, n), device=dev, dtype=torch.float32)
+    p = _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, init is not None, "stream")
+    res = _native.Result()
+    st = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
+    ctx = _native.context(dev.index if dev.index is not None else torch.cuda.current_device())
+    rc = _native.load().vomt_solve3d(ctx, int(n), rho0.data_ptr(), rho1.data_ptr(), g.ref, float(alpha),
+                                     ctypes.byref(p), u.data_ptr(), w.data_ptr() if l else None, phi.data_ptr(),
+                                     ctypes.byref(res), ctypes.c_void_p(st))
     _native.check(rc, ctx)
     return Solution(u, w, phi, res.as_dict())
 

@@ -174,6 +174,12 @@ struct ResidentPlan {
     int Gx, Gy, TXm, TYm, H, threads, P;
     double est_ns;
 };
+// Fixed-order sum of per-block FP64 partials (NRED per block), the stopping
+// decision and the history row (one block of 256 threads; vector_stream.cu).
+// t < 0: the iteration is the last check's plus -t (replayed graphs).
+__global__ void k_finalize(const double *__restrict__ partials, int nblocks, SolveCfg cfg, int t, DevStatus *st,
+                           double *hist, int hist_cap);
+
 bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out);
 bool resident_plan_wave(int n, int k, int count, int max_blocks, ResidentPlan *out);
 int resident_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg &cfg, const vomt_params &p,

@@ -388,56 +388,6 @@ __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const 
     block_reduce_store(v, partials + (size_t)blk * NRED);
 }
 
-// Fixed-order sum of the per-block partials, the stopping decision and the
-// history row.  One block of 256 threads.
-__global__ void k_finalize(const double *__restrict__ partials, int nblocks, SolveCfg cfg, int t,
-                           DevStatus *st, double *hist, int hist_cap)
-{
-    if (st->stop) return;
-    __shared__ double sh[256];
-    __shared__ double S[NRED];
-    for (int q = 0; q < NRED; ++q) {
-        double a = 0.0;
-        for (int bk = threadIdx.x; bk < nblocks; bk += blockDim.x) {
-            double x = partials[(size_t)bk * NRED + q];
-            a = (q == RED_MAX) ? fmax(a, x) : a + x;
-        }
-        sh[threadIdx.x] = a;
-        __syncthreads();
-        for (int off = 128; off > 0; off >>= 1) {
-            if (threadIdx.x < off)
-                sh[threadIdx.x] = (q == RED_MAX) ? fmax(sh[threadIdx.x], sh[threadIdx.x + off])
-                                                 : sh[threadIdx.x] + sh[threadIdx.x + off];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) S[q] = sh[0];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        if (t < 0) t = st->iter - t;       // in a replayed graph: the last check's iteration plus -t
-        double P = S[RED_P], D = S[RED_D] - (cfg.eps > 0.0 ? S[RED_DIST] / (4.0 * cfg.eps) : 0.0);
-        double m[NMET];
-        m[0] = P;
-        m[1] = D;
-        m[2] = fabs(P - D) / fmax(fabs(P), 1e-300);
-        m[3] = sqrt(S[RED_RR]) / (S[RED_BB] > 0.0 ? sqrt(S[RED_BB]) : 1.0);
-        m[4] = S[RED_DU] / cfg.mu + (cfg.has_w ? S[RED_DW] / cfg.nu : 0.0) + S[RED_DP] / cfg.tau - 2.0 * S[RED_X];
-        m[5] = S[RED_MAX];
-        m[6] = (double)t;
-        bool finite = true;
-        for (int q = 0; q < 6; ++q) finite = finite && isfinite(m[q]);
-        bool conv = cfg.tol_gap > 0.0 && m[2] <= cfg.tol_gap && m[3] <= cfg.tol_res;
-        m[7] = conv ? 1.0 : 0.0;
-        for (int q = 0; q < NMET; ++q) st->met[q] = m[q];
-        if (hist && st->checks < hist_cap)
-            for (int q = 0; q < NMET; ++q) hist[(size_t)st->checks * NMET + q] = m[q];
-        st->checks += 1;
-        st->iter = t;
-        if (!finite) { st->error = VOMT_ERR_NONFINITE; st->stop = 1; }
-        if (conv) st->stop = 1;
-    }
-}
-
 // ----------------------------------------------------------------- setup / copy
 __global__ void k_prepare(int n, int k, int l, const float *__restrict__ rho0, const float *__restrict__ rho1,
                           float *__restrict__ b, int warm, const float *__restrict__ u_in,
@@ -541,6 +491,56 @@ Launchers pick(int k, int un, int wn)
 }
 
 }  // namespace
+
+// Fixed-order sum of the per-block partials, the stopping decision and the
+// history row.  One block of 256 threads.
+__global__ void k_finalize(const double *__restrict__ partials, int nblocks, SolveCfg cfg, int t,
+                           DevStatus *st, double *hist, int hist_cap)
+{
+    if (st->stop) return;
+    __shared__ double sh[256];
+    __shared__ double S[NRED];
+    for (int q = 0; q < NRED; ++q) {
+        double a = 0.0;
+        for (int bk = threadIdx.x; bk < nblocks; bk += blockDim.x) {
+            double x = partials[(size_t)bk * NRED + q];
+            a = (q == RED_MAX) ? fmax(a, x) : a + x;
+        }
+        sh[threadIdx.x] = a;
+        __syncthreads();
+        for (int off = 128; off > 0; off >>= 1) {
+            if (threadIdx.x < off)
+                sh[threadIdx.x] = (q == RED_MAX) ? fmax(sh[threadIdx.x], sh[threadIdx.x + off])
+                                                 : sh[threadIdx.x] + sh[threadIdx.x + off];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) S[q] = sh[0];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (t < 0) t = st->iter - t;       // in a replayed graph: the last check's iteration plus -t
+        double P = S[RED_P], D = S[RED_D] - (cfg.eps > 0.0 ? S[RED_DIST] / (4.0 * cfg.eps) : 0.0);
+        double m[NMET];
+        m[0] = P;
+        m[1] = D;
+        m[2] = fabs(P - D) / fmax(fabs(P), 1e-300);
+        m[3] = sqrt(S[RED_RR]) / (S[RED_BB] > 0.0 ? sqrt(S[RED_BB]) : 1.0);
+        m[4] = S[RED_DU] / cfg.mu + (cfg.has_w ? S[RED_DW] / cfg.nu : 0.0) + S[RED_DP] / cfg.tau - 2.0 * S[RED_X];
+        m[5] = S[RED_MAX];
+        m[6] = (double)t;
+        bool finite = true;
+        for (int q = 0; q < 6; ++q) finite = finite && isfinite(m[q]);
+        bool conv = cfg.tol_gap > 0.0 && m[2] <= cfg.tol_gap && m[3] <= cfg.tol_res;
+        m[7] = conv ? 1.0 : 0.0;
+        for (int q = 0; q < NMET; ++q) st->met[q] = m[q];
+        if (hist && st->checks < hist_cap)
+            for (int q = 0; q < NMET; ++q) hist[(size_t)st->checks * NMET + q] = m[q];
+        st->checks += 1;
+        st->iter = t;
+        if (!finite) { st->error = VOMT_ERR_NONFINITE; st->stop = 1; }
+        if (conv) st->stop = 1;
+    }
+}
 
 // One fused iteration (Section 7.2) from the state at `in` to the state at
 // `out`; each state is contiguous planes phi [k], u_x [k], u_y [k], w [l].

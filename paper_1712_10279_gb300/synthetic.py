@@ -23,6 +23,10 @@ same shapes and structure:
 * ``random_L``           N symmetric k x k matrices, Gaussian entries,
                          symmetrised and scaled to unit Frobenius norm.
 * ``random_connected_graph``  G(k, p) redrawn until connected.
+* ``blob_pair3``         the blob recipe on an n x n x n grid (three blobs per
+                         channel, sigma uniform in [n/12, n/5] cells, amplitude
+                         uniform in [0.5, 1], 1e-3 floor; total mass 1), the
+                         shape of a 3-D DTI volume's scalar channels.
 
 Densities come out as float64 arrays shaped [k, n, n] indexed [c, j, i] with the
 x index i fastest; matrix fields as [k*k, n, n] with entry (a, b) at plane a*k+b.
@@ -55,6 +59,25 @@ def _blobs(rng, n, k, nblob=3, floor=1e-3):
 def blob_pair(n: int = 32, k: int = 3, seed: int = 1001):
     rng = np.random.default_rng(seed)
     return _blobs(rng, n, k), _blobs(rng, n, k)
+
+
+def _blobs3(rng, n, k, nblob=3, floor=1e-3):
+    zz, yy, xx = np.mgrid[0:n, 0:n, 0:n].astype(np.float64)
+    out = np.zeros((k, n, n, n))
+    for c in range(k):
+        for _ in range(nblob):
+            cx, cy, cz = rng.uniform(0.0, n, size=3)
+            s = rng.uniform(max(n / 12.0, 0.5), max(n / 5.0, 1.0))
+            a = rng.uniform(0.5, 1.0)
+            out[c] += a * np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2 + (zz - cz) ** 2) / (2.0 * s * s))
+    out += floor
+    return out / out.sum()
+
+
+def blob_pair3(n: int = 32, k: int = 3, seed: int = 1006):
+    """[k, n, n, n] densities ([c, z, y, x], x fastest)."""
+    rng = np.random.default_rng(seed)
+    return _blobs3(rng, n, k), _blobs3(rng, n, k)
 
 
 def _smooth_noise(rng, n, sigma):
