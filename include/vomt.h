@@ -130,6 +130,8 @@ typedef struct {
     int launches;        /* CUDA kernels this call launched */
     int blocks;          /* thread blocks of the main launch (resident: one tile each) */
     int halo;            /* resident engine: iterations between halo exchanges (0 otherwise) */
+    int variant;         /* form of the main step kernel: 1 = inputs staged by TMA tiles,
+                            0 = per-thread loads (streaming and 3-D solves; 0 otherwise) */
 } vomt_result;
 
 /* Create a context on CUDA device `device`.  The context owns the solver's
@@ -181,7 +183,10 @@ int vomt_solve_host(vomt_ctx *ctx, int n, const float *rho0, const float *rho1,
  *   w: device [l][n][n][n]; phi: device [k][n][n][n].
  * Outputs (inputs too when p->warm_start), like vomt_solve.  Norms: u_norm in
  * {L12, L2, L1} (the 2-norm over the three directions at a point), w_norm in
- * {L1, L2}; p->eps must be 0; p->engine and p->halo are ignored.  Default mu
+ * {L1, L2}; p->eps must be 0; p->engine is ignored; p->halo > 0 sets the
+ * number of z planes each thread block marches through (0: the library's
+ * choice, about four blocks per SM).  result->variant tells whether the TMA
+ * form of the step ran (n a multiple of 4, n >= 40, k <= 4).  Default mu
  * is 1/(48 tau (n-1)^2) (1/(24 tau (n-1)^2) without edges), since
  * ||grad||^2 <= 12 (n-1)^2 in 3-D; user mu, nu must satisfy
  * tau mu 12 (n-1)^2 + tau nu lambda_max(-Delta_G) < 1.  The history is that of

@@ -99,12 +99,13 @@ def solve(rho0, rho1, edges, alpha: float = 1.0, *, tau=None, mu=None, nu=None, 
 
 def solve3d(rho0, rho1, edges, alpha: float = 1.0, *, tau=None, mu=None, nu=None, cost=None,
             u_norm: int = U_L12, w_norm: int = W_L1, max_iters: int = 2000, check_every: int = 100,
-            tol_gap: float = 0.0, tol_res: float = 0.0, init=None, stream=None) -> Solution:
+            tol_gap: float = 0.0, tol_res: float = 0.0, init=None, stream=None, zc: int = 0) -> Solution:
     """Vector OMT on an n x n x n grid (Appendix A's discretization with a third direction).
 
     rho0, rho1: CUDA float32 tensors [k, n, n, n] (cell masses, [c, z, y, x]).  Returns u as
     [3, k, n, n, n] (u_x, u_y, u_z), w [l, n, n, n], phi [k, n, n, n] and the metrics of the
-    last FP64 check.  Default mu = 1/(48 tau (n-1)^2) (1/(24 ...) without edges).
+    last FP64 check.  Default mu = 1/(48 tau (n-1)^2) (1/(24 ...) without edges).  zc > 0
+    sets the z planes each thread block marches through (0: the library's choice).
     """
     import torch
     if not (rho0.is_cuda and rho1.is_cuda):
@@ -123,7 +124,8 @@ def solve3d(rho0, rho1, edges, alpha: float = 1.0, *, tau=None, mu=None, nu=None
         u = torch.empty((3, k, n, n, n), device=dev, dtype=torch.float32)
         w = torch.empty((max(l, 0), n, n, n), device=dev, dtype=torch.float32)
         phi = torch.empty((k, n, n, n), device=dev, dtype=torch.float32)
-    p = _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, init is not None, "stream")
+    p = _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, init is not None, "stream",
+                halo=zc)
     res = _native.Result()
     st = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
     ctx = _native.context(dev.index if dev.index is not None else torch.cuda.current_device())

@@ -1,11 +1,13 @@
-"""Command line: one vector-OMT solve on seeded synthetic colour-image densities.
+"""Command line: one vector-OMT solve on seeded synthetic densities.
 
     python -m paper_1712_10279_gb300 --n 2048 --k 3 --iters 20 --engine stream
+    python -m paper_1712_10279_gb300 --dim 3 --n 128 --k 3 --iters 100
 
-Prints the result record as one JSON line.  The densities come from
-``synthetic.color_image_pair`` (Gaussian-filtered noise plus rectangles); the
-channel graph is the complete graph on k nodes.  Useful for profiling one
-engine on one size.
+Prints the result record as one JSON line, with the last solve's time in
+milliseconds (CUDA events).  2-D densities come from
+``synthetic.color_image_pair`` (Gaussian-filtered noise plus rectangles), 3-D
+ones from ``synthetic.blob_pair3``; the channel graph is the complete graph on
+k nodes.  Useful for profiling one engine on one size.
 """
 from __future__ import annotations
 
@@ -17,6 +19,7 @@ import numpy as np
 
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_1712_10279_gb300")
+    ap.add_argument("--dim", type=int, default=2, choices=[2, 3])
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--alpha", type=float, default=1.0)
@@ -24,27 +27,36 @@ def main(argv=None):
     ap.add_argument("--check-every", type=int, default=100)
     ap.add_argument("--tol", type=float, default=0.0)
     ap.add_argument("--engine", default="auto", choices=["auto", "stream", "resident"])
-    ap.add_argument("--halo", type=int, default=0)
+    ap.add_argument("--halo", type=int, default=0, help="2-D resident engine: halo; 3-D: z planes per block")
     ap.add_argument("--seed", type=int, default=1002)
     ap.add_argument("--repeat", type=int, default=1, help="solves in a row (the first warms up)")
     args = ap.parse_args(argv)
 
     import torch
-    from . import solve
+    from . import solve, solve3d
     from . import synthetic as S
 
-    r0, r1 = S.color_image_pair(args.n, args.k, seed=args.seed)
+    if args.dim == 3:
+        r0, r1 = S.blob_pair3(args.n, args.k, seed=args.seed)
+    else:
+        r0, r1 = S.color_image_pair(args.n, args.k, seed=args.seed)
     dev = torch.device("cuda", 0)
     d0 = torch.from_numpy(r0.astype(np.float32)).to(dev)
     d1 = torch.from_numpy(r1.astype(np.float32)).to(dev)
     edges = S.complete_graph(args.k)
-    res = None
+    res, ms = None, 0.0
+    kw = dict(max_iters=args.iters, check_every=args.check_every, tol_gap=args.tol, tol_res=args.tol)
     for _ in range(max(1, args.repeat)):
-        sol = solve(d0, d1, edges, args.alpha, max_iters=args.iters, check_every=args.check_every,
-                    tol_gap=args.tol, tol_res=args.tol, engine=args.engine, halo=args.halo)
-        res = sol.result
-    torch.cuda.synchronize()
-    print(json.dumps(dict(n=args.n, k=args.k, alpha=args.alpha, **res)), flush=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        if args.dim == 3:
+            sol = solve3d(d0, d1, edges, args.alpha, zc=args.halo, **kw)
+        else:
+            sol = solve(d0, d1, edges, args.alpha, engine=args.engine, halo=args.halo, **kw)
+        e1.record()
+        e1.synchronize()
+        res, ms = sol.result, e0.elapsed_time(e1)
+    print(json.dumps(dict(dim=args.dim, n=args.n, k=args.k, alpha=args.alpha, ms=ms, **res)), flush=True)
 
 
 if __name__ == "__main__":

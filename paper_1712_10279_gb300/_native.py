@@ -42,7 +42,7 @@ class Result(ctypes.Structure):
     _fields_ = [("primal", c_double), ("dual", c_double), ("rel_gap", c_double), ("rel_res", c_double),
                 ("fp_resid", c_double), ("dual_infeas", c_double), ("mu", c_double), ("nu", c_double),
                 ("tau", c_double), ("iters", c_int), ("status", c_int), ("engine", c_int), ("checks", c_int),
-                ("launches", c_int), ("blocks", c_int), ("halo", c_int)]
+                ("launches", c_int), ("blocks", c_int), ("halo", c_int), ("variant", c_int)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}

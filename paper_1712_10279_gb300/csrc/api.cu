@@ -157,6 +157,7 @@ void fill_result(vomt_ctx *ctx, const SolveCfg &cfg, int engine, vomt_result *r,
         r->launches = ctx->launches;
         r->blocks = ctx->last_blocks;
         r->halo = ctx->last_halo;
+        r->variant = ctx->last_variant;
     }
 }
 
@@ -167,6 +168,7 @@ int run_engine(vomt_ctx *ctx, const OpDev &op, const StepDev &s, const SolveCfg 
     *engine = VOMT_ENGINE_STREAM;
     ctx->last_blocks = 0;
     ctx->last_halo = 0;
+    ctx->last_variant = 0;
     int rc;
     if (p.engine != VOMT_ENGINE_STREAM) {
         ResidentPlan plan;

@@ -864,6 +864,7 @@ extern "C" int vomt_solve_batched(vomt_ctx *ctx, int count, const vomt_instance 
                     r.mu = hinst[q].mu_d; r.nu = hinst[q].nu_d; r.tau = hinst[q].tau_d;
                     r.iters = h.iter; r.status = s_; r.engine = VOMT_ENGINE_BATCHED; r.checks = h.checks;
                     r.launches = ctx->launches; r.blocks = tiles[q]; r.halo = halo[q];
+                    r.variant = 0;
                 }
             }
             if (status < 0) ctx->err = status == VOMT_ERR_BARRIER_TIMEOUT ? "device wait timed out"
@@ -942,6 +943,7 @@ extern "C" int vomt_solve_batched(vomt_ctx *ctx, int count, const vomt_instance 
                 r.mu = hinst[q].mu_d; r.nu = hinst[q].nu_d; r.tau = hinst[q].tau_d;
                 r.iters = h.iter; r.status = s_; r.engine = VOMT_ENGINE_BATCHED; r.checks = h.checks;
                 r.launches = ctx->launches; r.blocks = 1; r.halo = 0;
+                r.variant = 0;
             }
         }
         if (status < 0) ctx->err = "an instance produced a non-finite iterate";

@@ -133,7 +133,7 @@ struct vomt_ctx {
     float *stage = nullptr;
     size_t stage_floats = 0;
     int launches = 0;                        // kernels launched by the current call
-    int last_blocks = 0, last_halo = 0;      // launch shape of the current call
+    int last_blocks = 0, last_halo = 0, last_variant = 0;      // launch shape of the current call
     // matrix-OMT compact staging (device)
     float *mstage = nullptr;
     size_t mstage_bytes = 0;

@@ -5,203 +5,236 @@
 //
 // Grid n x n x n on [0,1]^3, h = 1/(n-1); every field is planar [c][z][y][x]
 // with x fastest; the flux has three components u_x, u_y, u_z per channel, with
-// ghost entries at the last index of their own direction (kept zero).  One
-// thread per point computes u' at its point and at its three upwind neighbours
-// (their components enter the backward-difference divergence at the point), w'
-// and phi'.  Step rule: ||grad||^2 <= 12 / h^2 in 3-D, so mu = 1/(48 tau (n-1)^2)
-// (1/(24 tau (n-1)^2) without edges) keeps the 2-D rule's share of the bound.
+// ghost entries at the last index of their own direction (kept zero).  The
+// backward-difference divergence at a point takes 2u' - u of its three upwind
+// neighbours, so the step marches blocks up z: u' is computed once per point,
+// the x and y components meet their neighbours through shared memory and the z
+// component is carried to the next plane.  Two forms of that step: inputs staged
+// by TMA tiles (vector3d_tma.cu; n a multiple of 4, n >= 40, k <= 4) and, for
+// every other case, the form below with per-thread loads.  Step rule:
+// ||grad||^2 <= 12 / h^2 in 3-D, so mu = 1/(48 tau (n-1)^2) (1/(24 tau (n-1)^2)
+// without edges) keeps the 2-D rule's share of the bound.
 #include <math.h>
 #include <string.h>
 
 #include "internal.h"
 #include "pdhg_device.cuh"
+#include "vector3d.cuh"
+#include "vector3d_tma.h"
 
 namespace vomt {
 namespace {
 
-using dev::shrink2_factor;
-using dev::soft;
+using namespace v3;
 
 constexpr int T3 = 256;
 
-struct S3In {
-    const float *phi, *ux, *uy, *uz, *w;
-};
-struct S3Out {
-    float *phi, *ux, *uy, *uz, *w;
+// z-marching form of the same iteration (2.5-D blocking).  A block owns a
+// TX x TY column of the grid over a chunk of z; per z plane it stages phi of
+// planes z and z+1 (with a one-cell halo in x and y) in shared memory, prefetches
+// plane z+2 into registers, computes u' once per point, and publishes the
+// x and y components of 2u' - u through shared memory (the tile's x0-1 column and
+// y0-1 row are recomputed by the block).  The z component of 2u' - u at z-1 is the
+// thread's own value from the previous plane, carried in a register; the chunk's
+// first plane recomputes it.
+constexpr int HX = MX + 2, HY = MY + 2, HP = HX * HY;
+
+template <int K>
+struct MarchSmem {
+    static constexpr int phi = 3 * K * HP;              // three plane slots
+    static constexpr int bx = K * MY * (MX + 1);        // 2u'_x - u_x, column 0 = x0-1
+    static constexpr int by = K * (MY + 1) * MX;        // 2u'_y - u_y, row 0 = y0-1
+    static constexpr size_t bytes = sizeof(float) * (phi + bx + by);
 };
 
 template <int K>
-struct LK3 {
-    static constexpr int v = K * (K - 1) / 2 > 0 ? K * (K - 1) / 2 : 1;
-};
-
-template <int K, int UN>
-__device__ __forceinline__ void shrink_u3(float (&a)[K], float (&b)[K], float (&c)[K], float t, const float *wc)
+__device__ __forceinline__ void load_plane(float *slot, const float *__restrict__ phi, size_t m, int n, int x0,
+                                           int y0, int zp)
 {
-    if (UN == VOMT_U_L12) {
+    const bool zin = zp >= 0 && zp < n;
+    for (int e = threadIdx.x; e < HP; e += MT) {
+        const int j = e / HX, i = e - j * HX;
+        const int x = x0 + i - 1, y = y0 + j - 1;
+        const bool in = zin && x >= 0 && x < n && y >= 0 && y < n;
+        const size_t q = in ? ((size_t)zp * n + y) * n + x : 0;
 #pragma unroll
-        for (int q = 0; q < K; ++q) {
-            const float f = shrink2_factor(a[q] * a[q] + b[q] * b[q] + c[q] * c[q], t);
-            a[q] *= f;
-            b[q] *= f;
-            c[q] *= f;
-        }
-    } else if (UN == VOMT_U_L2) {
-        float s2 = 0.0f;
-#pragma unroll
-        for (int q = 0; q < K; ++q) s2 += wc[q] * (a[q] * a[q] + b[q] * b[q] + c[q] * c[q]);
-        const float f = shrink2_factor(s2, t);
-#pragma unroll
-        for (int q = 0; q < K; ++q) { a[q] *= f; b[q] *= f; c[q] *= f; }
-    } else {
-#pragma unroll
-        for (int q = 0; q < K; ++q) { a[q] = soft(a[q], t); b[q] = soft(b[q], t); c[q] = soft(c[q], t); }
-    }
-}
-
-template <int LK, int WN>
-__device__ __forceinline__ void shrink_w3(float (&x)[LK], int l, float t, const float *we)
-{
-    if (WN == VOMT_W_L1) {
-#pragma unroll
-        for (int e = 0; e < LK; ++e)
-            if (e < l) x[e] = soft(x[e], t);
-    } else {
-        float s2 = 0.0f;
-#pragma unroll
-        for (int e = 0; e < LK; ++e)
-            if (e < l) s2 += we[e] * x[e] * x[e];
-        const float f = shrink2_factor(s2, t);
-#pragma unroll
-        for (int e = 0; e < LK; ++e) x[e] *= f;
+        for (int c = 0; c < K; ++c) slot[c * HP + e] = in ? __ldg(phi + c * m + q) : 0.0f;
     }
 }
 
 template <int K, int UN, int WN>
-__global__ void __launch_bounds__(T3) k_step3(S3In in, S3Out out, const float *__restrict__ b, OpDev g, StepDev s,
-                                              const DevStatus *__restrict__ st)
+__global__ void __launch_bounds__(MT, K <= 4 ? 2 : 1) k_step3m(S3In in, S3Out out, const float *__restrict__ b, OpDev g,
+                                                 StepDev s, const DevStatus *__restrict__ st, int zc)
 {
     if (st->stop) return;
     constexpr int LK = LK3<K>::v;
+    constexpr int PF = (HP + MT - 1) / MT;
+    extern __shared__ float smem[];
+    float *sphi = smem;
+    float *sbx = smem + MarchSmem<K>::phi;
+    float *sby = sbx + MarchSmem<K>::bx;
     const int n = s.n;
-    const size_t m = (size_t)n * n * n;
-    const size_t p = (size_t)blockIdx.x * T3 + threadIdx.x;
-    if (p >= m) return;
-    const int x = (int)(p % n), y = (int)((p / n) % n), z = (int)(p / ((size_t)n * n));
-    const long SX = 1, SY = n, SZ = (long)n * n;
-    const bool hx = x < n - 1, hy = y < n - 1, hz = z < n - 1, lx = x > 0, ly = y > 0, lz = z > 0;
+    const size_t m = (size_t)n * n * n, nn = (size_t)n * n;
+    const int tid = threadIdx.x, tx = tid % MX, ty = tid / MX;
+    const int x0 = blockIdx.x * MX, y0 = blockIdx.y * MY;
+    const int z0 = blockIdx.z * zc, z1 = min(n, z0 + zc);
+    const int x = x0 + tx, y = y0 + ty;
+    const bool inb = x < n && y < n;
+    const bool hx = x < n - 1, hy = y < n - 1, lx = x > 0, ly = y > 0;
     const float mi = s.mu * s.ih;
-    float pc[K], px[K], py[K], pz[K], mx[K], mxy[K], mxz[K], my[K], myx[K], myz[K], mz[K], mzx[K], mzy[K];
+    auto S = [&](int zp, int c, int j, int i) -> float & { return sphi[((zp % 3) * K + c) * HP + j * HX + i]; };
+
+    load_plane<K>(&S(z0, 0, 0, 0), in.phi, m, n, x0, y0, z0);
+    load_plane<K>(&S(z0 + 1, 0, 0, 0), in.phi, m, n, x0, y0, z0 + 1);
+    // 2u'_z - u_z at (x, y, z0 - 1)
+    float cz[K];
 #pragma unroll
-    for (int c = 0; c < K; ++c) {
-        const float *P = in.phi + c * m + p;
-        pc[c] = __ldg(P);
-        px[c] = hx ? __ldg(P + SX) : 0.0f;
-        py[c] = hy ? __ldg(P + SY) : 0.0f;
-        pz[c] = hz ? __ldg(P + SZ) : 0.0f;
-        mx[c] = lx ? __ldg(P - SX) : 0.0f;
-        mxy[c] = (lx && hy) ? __ldg(P - SX + SY) : 0.0f;
-        mxz[c] = (lx && hz) ? __ldg(P - SX + SZ) : 0.0f;
-        my[c] = ly ? __ldg(P - SY) : 0.0f;
-        myx[c] = (ly && hx) ? __ldg(P - SY + SX) : 0.0f;
-        myz[c] = (ly && hz) ? __ldg(P - SY + SZ) : 0.0f;
-        mz[c] = lz ? __ldg(P - SZ) : 0.0f;
-        mzx[c] = (lz && hx) ? __ldg(P - SZ + SX) : 0.0f;
-        mzy[c] = (lz && hy) ? __ldg(P - SZ + SY) : 0.0f;
-    }
-    // u' at the point
-    float ux0[K], uy0[K], uz0[K], vx[K], vy[K], vz[K];
+    for (int c = 0; c < K; ++c) cz[c] = 0.0f;
+    if (z0 > 0 && inb) {
+        const size_t p = (size_t)(z0 - 1) * nn + (size_t)y * n + x;
+        float ax[K], ay[K], az[K], az0[K];
 #pragma unroll
-    for (int c = 0; c < K; ++c) {
-        const size_t q = c * m + p;
-        ux0[c] = __ldg(in.ux + q);
-        uy0[c] = __ldg(in.uy + q);
-        uz0[c] = __ldg(in.uz + q);
-        vx[c] = ux0[c] + (hx ? mi * (px[c] - pc[c]) : 0.0f);
-        vy[c] = uy0[c] + (hy ? mi * (py[c] - pc[c]) : 0.0f);
-        vz[c] = uz0[c] + (hz ? mi * (pz[c] - pc[c]) : 0.0f);
-    }
-    shrink_u3<K, UN>(vx, vy, vz, s.mu, g.wc);
-    // u' at (x-1): its x component enters div at the point
-    float ax[K], ay[K], az[K], ax0[K];
-#pragma unroll
-    for (int c = 0; c < K; ++c) {
-        const size_t q = c * m + p;
-        ax0[c] = lx ? __ldg(in.ux + q - SX) : 0.0f;
-        const float ay0 = lx ? __ldg(in.uy + q - SX) : 0.0f, az0 = lx ? __ldg(in.uz + q - SX) : 0.0f;
-        ax[c] = ax0[c] + (lx ? mi * (pc[c] - mx[c]) : 0.0f);
-        ay[c] = ay0 + ((lx && hy) ? mi * (mxy[c] - mx[c]) : 0.0f);
-        az[c] = az0 + ((lx && hz) ? mi * (mxz[c] - mx[c]) : 0.0f);
-    }
-    shrink_u3<K, UN>(ax, ay, az, s.mu, g.wc);
-    // u' at (y-1): its y component
-    float bx[K], by[K], bz[K], by0[K];
-#pragma unroll
-    for (int c = 0; c < K; ++c) {
-        const size_t q = c * m + p;
-        by0[c] = ly ? __ldg(in.uy + q - SY) : 0.0f;
-        const float bx0 = ly ? __ldg(in.ux + q - SY) : 0.0f, bz0 = ly ? __ldg(in.uz + q - SY) : 0.0f;
-        bx[c] = bx0 + ((ly && hx) ? mi * (myx[c] - my[c]) : 0.0f);
-        by[c] = by0[c] + (ly ? mi * (pc[c] - my[c]) : 0.0f);
-        bz[c] = bz0 + ((ly && hz) ? mi * (myz[c] - my[c]) : 0.0f);
-    }
-    shrink_u3<K, UN>(bx, by, bz, s.mu, g.wc);
-    // u' at (z-1): its z component
-    float cx[K], cy[K], cz[K], cz0[K];
-#pragma unroll
-    for (int c = 0; c < K; ++c) {
-        const size_t q = c * m + p;
-        cz0[c] = lz ? __ldg(in.uz + q - SZ) : 0.0f;
-        const float cx0 = lz ? __ldg(in.ux + q - SZ) : 0.0f, cy0 = lz ? __ldg(in.uy + q - SZ) : 0.0f;
-        cx[c] = cx0 + ((lz && hx) ? mi * (mzx[c] - mz[c]) : 0.0f);
-        cy[c] = cy0 + ((lz && hy) ? mi * (mzy[c] - mz[c]) : 0.0f);
-        cz[c] = cz0[c] + (lz ? mi * (pc[c] - mz[c]) : 0.0f);
-    }
-    shrink_u3<K, UN>(cx, cy, cz, s.mu, g.wc);
-    // w' at the point
-    float w0[LK], wx[LK];
-#pragma unroll
-    for (int e = 0; e < LK; ++e) {
-        if (e < g.l) {
-            w0[e] = __ldg(in.w + e * m + p);
-            float ge = 0.0f;
-#pragma unroll
-            for (int c = 0; c < K; ++c) ge += g.G[e][c] * pc[c];
-            wx[e] = w0[e] + s.nu * ge;
-        } else {
-            w0[e] = 0.0f;
-            wx[e] = 0.0f;
+        for (int c = 0; c < K; ++c) {
+            const float *P = in.phi + c * m + p;
+            const float pc = __ldg(P), px = hx ? __ldg(P + 1) : 0.0f, py = hy ? __ldg(P + n) : 0.0f;
+            const float pz = __ldg(P + nn);
+            const size_t q = c * m + p;
+            az0[c] = __ldg(in.uz + q);
+            ax[c] = upre(__ldg(in.ux + q), px, pc, hx, mi);
+            ay[c] = upre(__ldg(in.uy + q), py, pc, hy, mi);
+            az[c] = upre(az0[c], pz, pc, true, mi);
         }
+        shrink_u3<K, UN>(ax, ay, az, s.mu, g.wc);
+#pragma unroll
+        for (int c = 0; c < K; ++c) cz[c] = 2.0f * az[c] - az0[c];
     }
-    shrink_w3<LK, WN>(wx, g.l, s.alpha * s.nu, g.we);
-    // phi' = phi + tau (div ubar + div_G wbar + rho1 - rho0)
-    float r[K];
+    __syncthreads();
+
+    for (int z = z0; z < z1; ++z) {
+        const bool hz = z < n - 1, lz = z > 0;
+        const size_t p = (size_t)z * nn + (size_t)(inb ? y : 0) * n + (inb ? x : 0);
+        // prefetch plane z + 2 (needed as the "+1" plane of step z + 1)
+        float pf[PF][K];
+        const int zn = z + 2;
+        const bool want = zn < n && zn <= z1;
 #pragma unroll
-    for (int c = 0; c < K; ++c) {
-        const float bxc = 2.0f * vx[c] - ux0[c], byc = 2.0f * vy[c] - uy0[c], bzc = 2.0f * vz[c] - uz0[c];
-        const float bxl = lx ? 2.0f * ax[c] - ax0[c] : 0.0f;
-        const float byl = ly ? 2.0f * by[c] - by0[c] : 0.0f;
-        const float bzl = lz ? 2.0f * cz[c] - cz0[c] : 0.0f;
-        r[c] = s.ih * ((bxc - bxl) + (byc - byl) + (bzc - bzl)) + __ldg(b + c * m + p);
+        for (int r = 0; r < PF; ++r) {
+            const int e = tid + r * MT;
+            const int j = e / HX, i = e - j * HX;
+            const int xx = x0 + i - 1, yy = y0 + j - 1;
+            const bool ok = want && e < HP && xx >= 0 && xx < n && yy >= 0 && yy < n;
+            const size_t q = ok ? ((size_t)zn * n + yy) * n + xx : 0;
+#pragma unroll
+            for (int c = 0; c < K; ++c) pf[r][c] = ok ? __ldg(in.phi + c * m + q) : 0.0f;
+        }
+        // own u' and 2u' - u
+        float pc[K], vx[K], vy[K], vz[K], ux0[K], uy0[K], uz0[K];
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            const size_t q = c * m + p;
+            ux0[c] = inb ? __ldg(in.ux + q) : 0.0f;
+            uy0[c] = inb ? __ldg(in.uy + q) : 0.0f;
+            uz0[c] = inb ? __ldg(in.uz + q) : 0.0f;
+            pc[c] = S(z, c, ty + 1, tx + 1);
+            vx[c] = upre(ux0[c], S(z, c, ty + 1, tx + 2), pc[c], hx, mi);
+            vy[c] = upre(uy0[c], S(z, c, ty + 2, tx + 1), pc[c], hy, mi);
+            vz[c] = upre(uz0[c], S(z + 1, c, ty + 1, tx + 1), pc[c], hz, mi);
+        }
+        shrink_u3<K, UN>(vx, vy, vz, s.mu, g.wc);
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            sbx[(c * MY + ty) * (MX + 1) + tx + 1] = 2.0f * vx[c] - ux0[c];
+            sby[(c * (MY + 1) + ty + 1) * MX + tx] = 2.0f * vy[c] - uy0[c];
+        }
+        // the tile's y0-1 row (threads 0..MX-1) and x0-1 column (threads MX..MX+MY-1)
+        {
+            int hxp = -1, hyp = -1, j = 0, i = 0;
+            if (tid < MX) {
+                if (y0 > 0 && x0 + tid < n) { hxp = x0 + tid; hyp = y0 - 1; j = 0; i = tid + 1; }
+            } else if (tid < MX + MY) {
+                if (x0 > 0 && y0 + tid - MX < n) { hxp = x0 - 1; hyp = y0 + tid - MX; j = tid - MX + 1; i = 0; }
+            }
+            if (hxp >= 0) {
+                const bool ax_in = hxp < n - 1, ay_in = hyp < n - 1;
+                const size_t ph = (size_t)z * nn + (size_t)hyp * n + hxp;
+                float ax[K], ay[K], az[K], a0x[K], a0y[K];
+#pragma unroll
+                for (int c = 0; c < K; ++c) {
+                    const size_t q = c * m + ph;
+                    a0x[c] = __ldg(in.ux + q);
+                    a0y[c] = __ldg(in.uy + q);
+                    const float here = S(z, c, j, i);
+                    ax[c] = upre(a0x[c], S(z, c, j, i + 1), here, ax_in, mi);
+                    ay[c] = upre(a0y[c], S(z, c, j + 1, i), here, ay_in, mi);
+                    az[c] = upre(__ldg(in.uz + q), S(z + 1, c, j, i), here, hz, mi);
+                }
+                shrink_u3<K, UN>(ax, ay, az, s.mu, g.wc);
+                if (tid < MX) {
+#pragma unroll
+                    for (int c = 0; c < K; ++c) sby[(c * (MY + 1)) * MX + tid] = 2.0f * ay[c] - a0y[c];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < K; ++c) sbx[(c * MY + (tid - MX)) * (MX + 1)] = 2.0f * ax[c] - a0x[c];
+                }
+            }
+        }
+        // w' at the point
+        float w0[LK], wx[LK];
+#pragma unroll
+        for (int e = 0; e < LK; ++e) {
+            if (e < g.l) {
+                w0[e] = inb ? __ldg(in.w + e * m + p) : 0.0f;
+                float ge = 0.0f;
+#pragma unroll
+                for (int c = 0; c < K; ++c) ge += g.G[e][c] * pc[c];
+                wx[e] = w0[e] + s.nu * ge;
+            } else {
+                w0[e] = 0.0f;
+                wx[e] = 0.0f;
+            }
+        }
+        shrink_w3<LK, WN>(wx, g.l, s.alpha * s.nu, g.we);
+        __syncthreads();
+        // phi' = phi + tau (div ubar + div_G wbar + rho1 - rho0)
+        float r[K];
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            const float bxc = 2.0f * vx[c] - ux0[c], byc = 2.0f * vy[c] - uy0[c], bzc = 2.0f * vz[c] - uz0[c];
+            const float bxl = lx ? sbx[(c * MY + ty) * (MX + 1) + tx] : 0.0f;
+            const float byl = ly ? sby[(c * (MY + 1) + ty) * MX + tx] : 0.0f;
+            const float bzl = lz ? cz[c] : 0.0f;
+            r[c] = s.ih * ((bxc - bxl) + (byc - byl) + (bzc - bzl)) + (inb ? __ldg(b + c * m + p) : 0.0f);
+            cz[c] = bzc;
+        }
+#pragma unroll
+        for (int e = 0; e < LK; ++e) {
+            const float v = 2.0f * wx[e] - w0[e];
+#pragma unroll
+            for (int c = 0; c < K; ++c) r[c] -= g.Dv[c][e] * v;
+        }
+        if (inb) {
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                const size_t q = c * m + p;
+                out.phi[q] = pc[c] + s.tau * r[c];
+                out.ux[q] = vx[c];
+                out.uy[q] = vy[c];
+                out.uz[q] = vz[c];
+            }
+#pragma unroll
+            for (int e = 0; e < LK; ++e)
+                if (e < g.l) out.w[e * m + p] = wx[e];
+        }
+        // plane z + 2 into the slot of plane z - 1 (every thread is past step z - 1)
+#pragma unroll
+        for (int r2 = 0; r2 < PF; ++r2) {
+            const int e = tid + r2 * MT;
+            if (e < HP)
+#pragma unroll
+                for (int c = 0; c < K; ++c) sphi[((zn % 3) * K + c) * HP + e] = pf[r2][c];
+        }
+        __syncthreads();
     }
-#pragma unroll
-    for (int e = 0; e < LK; ++e) {
-        const float v = 2.0f * wx[e] - w0[e];
-#pragma unroll
-        for (int c = 0; c < K; ++c) r[c] -= g.Dv[c][e] * v;
-    }
-#pragma unroll
-    for (int c = 0; c < K; ++c) {
-        const size_t q = c * m + p;
-        out.phi[q] = pc[c] + s.tau * r[c];
-        out.ux[q] = vx[c];
-        out.uy[q] = vy[c];
-        out.uz[q] = vz[c];
-    }
-#pragma unroll
-    for (int e = 0; e < LK; ++e)
-        if (e < g.l) out.w[e * m + p] = wx[e];
 }
 
 // FP64 block partials of one convergence check (slots RED_*): per-point terms in
@@ -352,14 +385,15 @@ __global__ void k_copy_out3(size_t m, int k, int l, S3In s0, S3In s1, const DevS
 }
 
 struct L3 {
-    void (*step)(S3In, S3Out, const float *, OpDev, StepDev, const DevStatus *);
+    void (*step)(S3In, S3Out, const float *, OpDev, StepDev, const DevStatus *, int);
     void (*metrics)(S3In, S3In, const float *, OpDev, StepDev, double *, const DevStatus *);
+    size_t smem;
 };
 
 template <int K, int UN, int WN>
 L3 make3()
 {
-    return L3{k_step3<K, UN, WN>, k_metrics3<K, UN, WN>};
+    return L3{k_step3m<K, UN, WN>, k_metrics3<K, UN, WN>, MarchSmem<K>::bytes};
 }
 
 template <int K>
@@ -399,6 +433,7 @@ extern "C" int vomt_solve3d(vomt_ctx *ctx, int n, const float *rho0, const float
         ctx->launches = 0;
         ctx->last_blocks = 0;
         ctx->last_halo = 0;
+        ctx->last_variant = 0;
         if (n < 2 || n > 1024) return fail(ctx, VOMT_ERR_BAD_ARG, "3-D grids: n must be in [2, 1024]");
         if (!rho0 || !rho1 || !u || !phi || !graph || (graph->n_edges > 0 && !w))
             return fail(ctx, VOMT_ERR_BAD_ARG, "null array");
@@ -409,8 +444,13 @@ extern "C" int vomt_solve3d(vomt_ctx *ctx, int n, const float *rho0, const float
         OpDev g;
         StepDev s;
         SolveCfg cfg;
-        vomt_params p;
-        int rc = prepare_vector(ctx, n, graph, alpha, pin, &g, &s, &cfg, &p);
+        vomt_params p, p3;
+        vomt_default_params(&p3);
+        if (pin) p3 = *pin;
+        const int zc_user = p3.halo;       // 3-D: planes each block marches through (0: the library's choice)
+        if (zc_user < 0) return fail(ctx, VOMT_ERR_BAD_ARG, "halo (the 3-D z chunk) must be >= 0");
+        p3.halo = 0;
+        int rc = prepare_vector(ctx, n, graph, alpha, &p3, &g, &s, &cfg, &p);
         if (rc) return rc;
         // the 3-D step rule: ||grad||^2 <= 12 (n-1)^2, so mu takes 1/(48 tau (n-1)^2)
         // (1/(24 ...) without edges), the 2-D rule's share of the bound
@@ -447,8 +487,7 @@ extern "C" int vomt_solve3d(vomt_ctx *ctx, int n, const float *rho0, const float
                           base + (size_t)4 * k * m};
             si[q] = S3In{so[q].phi, so[q].ux, so[q].uy, so[q].uz, so[q].w};
         }
-        const int nblocks = (int)((m + T3 - 1) / T3);
-        ctx->last_blocks = nblocks;
+        const int nblocks = (int)((m + T3 - 1) / T3);     // checks: one point per thread
         rc = ensure_buffer(ctx, (void **)&ctx->partials, &ctx->partials_cap, sizeof(double) * (size_t)nblocks * NRED,
                            "partials");
         if (rc) return rc;
@@ -467,6 +506,24 @@ extern "C" int vomt_solve3d(vomt_ctx *ctx, int n, const float *rho0, const float
         k_prepare3<<<pblocks, 256, 0, st>>>(m, k, l, rho0, rho1, b, p.warm_start, u, w, phi, so[0]);
         ctx->launches += 1;
         L3 L = pick3(k, p.u_norm, p.w_norm);
+        e = cudaFuncSetAttribute((const void *)L.step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "3-D step shared memory");
+        // inputs by TMA tiles where they apply (n a multiple of 4, n >= 40, k <= 4)
+        Tma3Plan *tp = tma3_supported(n, k, l, p.u_norm, p.w_norm)
+                           ? tma3_plan_create(n, k, l, p.u_norm, p.w_norm, so[0].phi, so[1].phi, b)
+                           : nullptr;
+        ctx->last_variant = tp ? 1 : 0;
+        // z chunk: the longest of 32, 16, 8, 4 planes that still gives 1.5 blocks per SM
+        // (TMA form; longer chunks amortise the pipeline fill, but fewer blocks than SMs
+        // leave HBM idle) or four blocks per SM (per-thread form, which needs the warps)
+        const int tiles = ((n + MX - 1) / MX) * ((n + MY - 1) / MY);
+        const size_t want = tp ? (size_t)(3 * ctx->sm_count / 2) : (size_t)(4 * ctx->sm_count);
+        int zc = 4;
+        for (int c : {32, 16, 8})
+            if ((size_t)tiles * ((n + c - 1) / c) >= want) { zc = c; break; }
+        if (zc_user > 0) zc = std::min(zc_user, n);
+        const dim3 mgrid((n + MX - 1) / MX, (n + MY - 1) / MY, (n + zc - 1) / zc);
+        ctx->last_blocks = (int)(mgrid.x * mgrid.y * mgrid.z);
         auto check = [&](int t, int cur) {
             L.metrics<<<nblocks, T3, 0, st>>>(si[cur], si[cur ^ 1], b, g, s, ctx->partials, ctx->dstatus);
             k_finalize<<<1, 256, 0, st>>>(ctx->partials, nblocks, cfg, t, ctx->dstatus, ctx->dhist, ctx->hist_cap);
@@ -484,7 +541,10 @@ extern "C" int vomt_solve3d(vomt_ctx *ctx, int n, const float *rho0, const float
             const int end = std::min(t + chunk, p.max_iters);
             for (int tt = t + 1; tt <= end; ++tt) {
                 const int cur = tt & 1;
-                L.step<<<nblocks, T3, 0, st>>>(si[cur ^ 1], so[cur], b, g, s, ctx->dstatus);
+                if (tp)
+                    tma3_launch_step(tp, cur ^ 1, so[cur], g, s, ctx->dstatus, zc, st);
+                else
+                    L.step<<<mgrid, MT, L.smem, st>>>(si[cur ^ 1], so[cur], b, g, s, ctx->dstatus, zc);
                 ctx->launches += 1;
                 if (tt % p.check_every == 0 || tt == p.max_iters) check(tt, cur);
             }
@@ -508,6 +568,7 @@ extern "C" int vomt_solve3d(vomt_ctx *ctx, int n, const float *rho0, const float
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         for (int q = 0; q < 2; ++q)
             if (ev[q]) cudaEventDestroy(ev[q]);
+        tma3_plan_destroy(tp);
         if (e != cudaSuccess) return set_cuda_error(ctx, e, "3-D solve");
         int status = VOMT_OK;
         fill_result(ctx, cfg, VOMT_ENGINE_STREAM, result, &status);

@@ -1,0 +1,82 @@
+// Pieces shared by the two forms of the 3-D fused iteration (vector3d.cu,
+// vector3d_tma.cu): the state views, the per-point shrinks and the tile shape.
+//
+// A 3-D state is five runs of volumes, each n x n x n with x fastest:
+// phi [k], u_x [k], u_y [k], u_z [k], w [l].  u_d's ghost face is the last index
+// in direction d (kept zero).
+#pragma once
+
+#include "internal.h"
+#include "pdhg_device.cuh"
+
+namespace vomt {
+namespace v3 {
+
+using dev::shrink2_factor;
+using dev::soft;
+
+// a block owns an MX x MY column of the grid and marches through a chunk of z
+constexpr int MX = 32, MY = 8, MT = MX * MY;
+
+struct S3In {
+    const float *phi, *ux, *uy, *uz, *w;
+};
+struct S3Out {
+    float *phi, *ux, *uy, *uz, *w;
+};
+
+template <int K>
+struct LK3 {
+    static constexpr int v = K * (K - 1) / 2 > 0 ? K * (K - 1) / 2 : 1;
+};
+
+template <int K, int UN>
+__device__ __forceinline__ void shrink_u3(float (&a)[K], float (&b)[K], float (&c)[K], float t, const float *wc)
+{
+    if (UN == VOMT_U_L12) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const float f = shrink2_factor(a[q] * a[q] + b[q] * b[q] + c[q] * c[q], t);
+            a[q] *= f;
+            b[q] *= f;
+            c[q] *= f;
+        }
+    } else if (UN == VOMT_U_L2) {
+        float s2 = 0.0f;
+#pragma unroll
+        for (int q = 0; q < K; ++q) s2 += wc[q] * (a[q] * a[q] + b[q] * b[q] + c[q] * c[q]);
+        const float f = shrink2_factor(s2, t);
+#pragma unroll
+        for (int q = 0; q < K; ++q) { a[q] *= f; b[q] *= f; c[q] *= f; }
+    } else {
+#pragma unroll
+        for (int q = 0; q < K; ++q) { a[q] = soft(a[q], t); b[q] = soft(b[q], t); c[q] = soft(c[q], t); }
+    }
+}
+
+template <int LK, int WN>
+__device__ __forceinline__ void shrink_w3(float (&x)[LK], int l, float t, const float *we)
+{
+    if (WN == VOMT_W_L1) {
+#pragma unroll
+        for (int e = 0; e < LK; ++e)
+            if (e < l) x[e] = soft(x[e], t);
+    } else {
+        float s2 = 0.0f;
+#pragma unroll
+        for (int e = 0; e < LK; ++e)
+            if (e < l) s2 += we[e] * x[e] * x[e];
+        const float f = shrink2_factor(s2, t);
+#pragma unroll
+        for (int e = 0; e < LK; ++e) x[e] *= f;
+    }
+}
+
+// u + mu grad phi along one direction (zero across a ghost face)
+__device__ __forceinline__ float upre(float u0, float ahead, float here, bool inside, float mi)
+{
+    return inside ? u0 + mi * (ahead - here) : u0;
+}
+
+}  // namespace v3
+}  // namespace vomt

@@ -626,7 +626,10 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
     TmaPlan *tp = tma_step_supported(n, k, l, p.u_norm, p.w_norm)
                       ? tma_plan_create(n, k, l, p.u_norm, p.w_norm, so[0].phi, so[1].phi, b)
                       : nullptr;
-    if (tp) ctx->last_blocks = ((n + 63) / 64) * ((n + 15) / 16);    // the step's 64 x 16 tiles
+    if (tp) {
+        ctx->last_blocks = ((n + 63) / 64) * ((n + 15) / 16);    // the step's 64 x 16 tiles
+        ctx->last_variant = 1;
+    }
     auto check = [&](int t, int cur) {
         L.metrics<<<grd, blk, 0, st>>>(si[cur], si[cur ^ 1], b, g, s, ctx->partials, ctx->dstatus);
         k_finalize<<<1, 256, 0, st>>>(ctx->partials, nblocks, cfg, t, ctx->dstatus, ctx->dhist, ctx->hist_cap);
@@ -932,6 +935,9 @@ extern "C" int vomt_solve_noalloc(int n, const float *rho0, const float *rho1, c
         result->engine = VOMT_ENGINE_STREAM;
         result->checks = hs.checks;
         result->launches = launches;
+        result->blocks = nblocks;
+        result->halo = 0;
+        result->variant = 0;
     }
     return status;
 }
