@@ -18,7 +18,8 @@ batched engine against a loop of plain solves on 512 mixed instances, the
 differentiable cost (64 pairs at 256 x 256, forward + backward, and the
 200-iteration unrolled gradient) against plain forward solves, and a
 2048 x 2048 k = 3 case whose state does not fit L2 (the HBM-bound cross-check of
-the streaming kernel).  --cap / --alphas shrink the timed workload for profiler
+the streaming kernel), the regularised problem, and 3-D grids of 128^3 and 256^3
+with k = 3 (the TMA z-marching step against the HBM roofline).  --cap / --alphas shrink the timed workload for profiler
 runs only (the line then names the reduced workload).
 """
 from __future__ import annotations
@@ -329,6 +330,31 @@ def extra_regularised(dev, peak, eps=5e4, cap=50000):
                 regulariser_share_of_cost=eps * q2 / r["primal"] if r["primal"] else None, **_summary(r))
 
 
+def extra_volume(dev, peak, iters=500):
+    """Vector OMT on 3-D grids, k = 3 (K3), 128^3 and 256^3 blob volumes: fixed iteration
+    counts (checks every CHECK_EVERY iterations included) against the HBM roofline."""
+    import torch
+    import paper_1712_10279_gb300 as V
+    from paper_1712_10279_gb300 import synthetic as S
+    out = {}
+    for name, n in (("k3_128", 128), ("k3_256", 256)):
+        a, b = S.blob_pair3(n, 3, seed=1008)
+        d0 = torch.from_numpy(a.astype(np.float32)).to(dev)
+        d1 = torch.from_numpy(b.astype(np.float32)).to(dev)
+        V.solve3d(d0, d1, EDGES, 1.0, max_iters=20, check_every=20)
+        sol, ms = _gpu_ms(lambda: V.solve3d(d0, d1, EDGES, 1.0, max_iters=iters, check_every=CHECK_EVERY))
+        r = sol.result
+        it = r["iters"]
+        bpg = 4 * (9 * 3 + 2 * len(EDGES))
+        gbs = bpg * n ** 3 * it / (ms / 1e3) / 1e9
+        out[name] = dict(n=n, k=3, iters=it, us_per_iter=1e3 * ms / it, gp_it_per_s=n ** 3 * it / (ms / 1e3),
+                         algorithmic_bytes_per_gp_it=bpg, achieved_GBps=gbs, frac_of_measured_hbm=gbs / peak,
+                         tma_form=bool(r["variant"]), blocks=r["blocks"],
+                         note="blob volumes seed 1008, alpha=1; checks every %d iterations included" % CHECK_EVERY)
+        del d0, d1, sol
+    return out
+
+
 def extras(dev):
     peak, _ = _peaks()
     out = {}
@@ -337,7 +363,8 @@ def extras(dev):
                      ("batched_vs_plain", lambda: extra_batched(dev)),
                      ("differentiable", lambda: extra_differentiable(dev)),
                      ("regularised", lambda: extra_regularised(dev, peak)),
-                     ("hbm_bound", lambda: extra_hbm_bound(dev, peak))):
+                     ("hbm_bound", lambda: extra_hbm_bound(dev, peak)),
+                     ("volume_3d", lambda: extra_volume(dev, peak))):
         t0 = time.perf_counter()
         try:
             out[name] = fn()

@@ -515,7 +515,8 @@ extern "C" int vomt_solve3d(vomt_ctx *ctx, int n, const float *rho0, const float
         ctx->last_variant = tp ? 1 : 0;
         // z chunk: the longest of 32, 16, 8, 4 planes that still gives 1.5 blocks per SM
         // (TMA form; longer chunks amortise the pipeline fill, but fewer blocks than SMs
-        // leave HBM idle) or four blocks per SM (per-thread form, which needs the warps)
+        // leave HBM idle; 32 measured best at 128^3 and 256^3) or four blocks per SM
+        // (per-thread form, which needs the warps)
         const int tiles = ((n + MX - 1) / MX) * ((n + MY - 1) / MY);
         const size_t want = tp ? (size_t)(3 * ctx->sm_count / 2) : (size_t)(4 * ctx->sm_count);
         int zc = 4;

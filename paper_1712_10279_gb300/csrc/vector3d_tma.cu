@@ -7,9 +7,9 @@
 // cp.async.bulk.tensor copies issued by one thread on the stage's mbarrier:
 // phi with a one-cell halo on every side (x0-4 .. x0+35 so that the box starts
 // on a 16-byte boundary, y0-1 .. y0+8), u_x, u_y and u_z with the x0-1 column
-// and the y0-1 row (the tile's upwind neighbours), w and b on the tile.  Plane
-// z + NS - 1 is issued while plane z is computed, so NS - 1 planes are in
-// flight per block without tying up registers.  Per plane each thread computes
+// and the y0-1 row (x0-4 .. x0+31, the tile's upwind neighbours), w and b on the
+// tile.  Plane z + NS - 1 is issued while plane z is computed, so NS - 2 planes
+// are in flight per block without tying up registers.  Per plane each thread computes
 // u' at its point once; the tile's x0-1 column and y0-1 row are recomputed;
 // the x and y components of 2u' - u meet their downwind neighbours through
 // shared memory, the z component is carried in a register to the next plane
@@ -38,7 +38,8 @@ namespace {
 
 using namespace v3;
 
-constexpr int BXH = MX + 8;          // halo boxes: x0-4 .. x0+35
+constexpr int BXH = MX + 8;          // phi box columns x0-4 .. x0+35 (x0+32 is the last x+1)
+constexpr int BXU = MX + 4;          // u box columns x0-4 .. x0+31 (x0-1 is the upwind column)
 constexpr int BYP = MY + 2;          // phi rows y0-1 .. y0+8
 constexpr int BYU = MY + 1;          // u rows y0-1 .. y0+7
 constexpr uint32_t kSpins = 1u << 22;
@@ -55,17 +56,20 @@ __host__ __device__ inline Stage3 stage3(int K, int l)
     Stage3 S;
     int o = 0;
     S.phi = o; o += al128(K * BYP * BXH * 4);
-    S.ux = o; o += al128(K * BYU * BXH * 4);
-    S.uy = o; o += al128(K * BYU * BXH * 4);
-    S.uz = o; o += al128(K * BYU * BXH * 4);
+    S.ux = o; o += al128(K * BYU * BXU * 4);
+    S.uy = o; o += al128(K * BYU * BXU * 4);
+    S.uz = o; o += al128(K * BYU * BXU * 4);
     S.w = o; o += al128((l > 0 ? l : 1) * MY * MX * 4);
     S.b = o; o += al128(K * MY * MX * 4);
     S.size = o;
     S.bytes_phi = (unsigned)(K * BYP * BXH * 4);
-    S.bytes_all = S.bytes_phi + (unsigned)(3 * K * BYU * BXH * 4 + l * MY * MX * 4 + K * MY * MX * 4);
+    S.bytes_all = S.bytes_phi + (unsigned)(3 * K * BYU * BXU * 4 + l * MY * MX * 4 + K * MY * MX * 4);
     return S;
 }
 
+// stages: planes z and z+1 in use, the rest in flight.  Four for k <= 3 (two
+// blocks per SM; three stages would fit three blocks per SM but measured slower,
+// the copies then land too late), three for k = 4.
 __host__ __device__ constexpr int nstages(int K) { return K <= 3 ? 4 : 3; }
 
 __host__ __device__ inline int smem3(int K, int l)
@@ -75,7 +79,7 @@ __host__ __device__ inline int smem3(int K, int l)
 
 struct Maps3 {
     CUtensorMap phi;    // state volumes, box BXH x BYP x 1 x K
-    CUtensorMap u;      // state volumes, box BXH x BYU x 1 x K (at volumes K, 2K, 3K)
+    CUtensorMap u;      // state volumes, box BXU x BYU x 1 x K (at volumes K, 2K, 3K)
     CUtensorMap w;      // state volumes, box MX x MY x 1 x l (at volume 4K)
     CUtensorMap b;      // rho1 - rho0, box MX x MY x 1 x K
 };
@@ -116,7 +120,7 @@ __global__ void __launch_bounds__(MT, 2) k_step3t(const __grid_constant__ Maps3 
 {
     if (st->stop) return;
     constexpr int NS = nstages(K), LK = LK3<K>::v;
-    constexpr int PL = BYP * BXH, UL = BYU * BXH, WL = MY * MX;
+    constexpr int PL = BYP * BXH, UL = BYU * BXU, WL = MY * MX;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) unsigned long long mbar[NS];
     __shared__ int abort_flag;
@@ -184,7 +188,8 @@ __global__ void __launch_bounds__(MT, 2) k_step3t(const __grid_constant__ Maps3 
         for (int c = 0; c < K; ++c) cz[c] = 2.0f * az[c] - az0[c];
     }
 
-    const int oP = (ty + 1) * BXH + tx + 4;     // (x, y) in the phi and u boxes
+    const int oP = (ty + 1) * BXH + tx + 4;     // (x, y) in the phi box
+    const int oU = (ty + 1) * BXU + tx + 4;     // (x, y) in the u boxes
     const int oT = ty * MX + tx;                // (x, y) in the w and b boxes
     for (int z = z0; z < z1; ++z) {
         const bool hz = z < n - 1, lz = z > 0;
@@ -203,9 +208,9 @@ __global__ void __launch_bounds__(MT, 2) k_step3t(const __grid_constant__ Maps3 
         for (int c = 0; c < K; ++c) {
             const float *P = P0 + c * PL + oP;
             pc[c] = P[0];
-            ux0[c] = Ux[c * UL + oP];
-            uy0[c] = Uy[c * UL + oP];
-            uz0[c] = Uz[c * UL + oP];
+            ux0[c] = Ux[c * UL + oU];
+            uy0[c] = Uy[c * UL + oU];
+            uz0[c] = Uz[c * UL + oU];
             vx[c] = upre(ux0[c], P[1], pc[c], hx, mi);
             vy[c] = upre(uy0[c], P[BXH], pc[c], hy, mi);
             vz[c] = upre(uz0[c], P1[c * PL + oP], pc[c], hz, mi);
@@ -219,11 +224,16 @@ __global__ void __launch_bounds__(MT, 2) k_step3t(const __grid_constant__ Maps3 
         }
         // the tile's y0-1 row (threads 0..MX-1) and x0-1 column (threads MX..MX+MY-1)
         {
-            int hxp = -1, hyp = -1, o = 0;
+            int hxp = -1, hyp = -1, o = 0, ou = 0;
             if (tid < MX) {
-                if (y0 > 0 && x0 + tid < n) { hxp = x0 + tid; hyp = y0 - 1; o = tid + 4; }
+                if (y0 > 0 && x0 + tid < n) { hxp = x0 + tid; hyp = y0 - 1; o = tid + 4; ou = tid + 4; }
             } else if (tid < MX + MY) {
-                if (x0 > 0 && y0 + tid - MX < n) { hxp = x0 - 1; hyp = y0 + tid - MX; o = (tid - MX + 1) * BXH + 3; }
+                if (x0 > 0 && y0 + tid - MX < n) {
+                    hxp = x0 - 1;
+                    hyp = y0 + tid - MX;
+                    o = (tid - MX + 1) * BXH + 3;
+                    ou = (tid - MX + 1) * BXU + 3;
+                }
             }
             if (hxp >= 0) {
                 const bool ax_in = hxp < n - 1, ay_in = hyp < n - 1;
@@ -231,11 +241,11 @@ __global__ void __launch_bounds__(MT, 2) k_step3t(const __grid_constant__ Maps3 
 #pragma unroll
                 for (int c = 0; c < K; ++c) {
                     const float *P = P0 + c * PL + o;
-                    a0x[c] = Ux[c * UL + o];
-                    a0y[c] = Uy[c * UL + o];
+                    a0x[c] = Ux[c * UL + ou];
+                    a0y[c] = Uy[c * UL + ou];
                     ax[c] = upre(a0x[c], P[1], P[0], ax_in, mi);
                     ay[c] = upre(a0y[c], P[BXH], P[0], ay_in, mi);
-                    az[c] = upre(Uz[c * UL + o], P1[c * PL + o], P[0], hz, mi);
+                    az[c] = upre(Uz[c * UL + ou], P1[c * PL + o], P[0], hz, mi);
                 }
                 shrink_u3<K, UN>(ax, ay, az, s.mu, g.wc);
                 if (tid < MX) {
@@ -377,7 +387,7 @@ bool tma3_supported(int n, int k, int l, int un, int wn)
 {
     if (n < BXH || n % 4 != 0 || n > 1024) return false;
     if (!pick3t(k, un, wn)) return false;
-    if (smem3(k, l) > 112 * 1024) return false;        // two blocks per SM
+    if (smem3(k, l) > 110 * 1024) return false;        // two blocks per SM at least
     return encode_fn3() != nullptr;
 }
 
@@ -391,7 +401,7 @@ Tma3Plan *tma3_plan_create(int n, int k, int l, int un, int wn, const float *sta
     for (int q = 0; q < 2 && ok; ++q) {
         pl->in[q] = st[q];
         ok = encode4(&pl->maps[q].phi, st[q], n, vols, BXH, BYP, k) &&
-             encode4(&pl->maps[q].u, st[q], n, vols, BXH, BYU, k) &&
+             encode4(&pl->maps[q].u, st[q], n, vols, BXU, BYU, k) &&
              (l == 0 || encode4(&pl->maps[q].w, st[q], n, vols, MX, MY, l)) &&
              encode4(&pl->maps[q].b, b, n, k, MX, MY, k);
         if (l == 0) memset(&pl->maps[q].w, 0, sizeof(CUtensorMap));
