@@ -84,6 +84,10 @@ def _load():
                                          p, p, p, p, p, p, p, p, p, p, p]),
             "orc_vomt3_solve": (i, [i, i, i, p, p, p, p, p, d, d, d, d, i, i, i, i, d, d,
                                     p, p, p, p, p, p, p, i]),
+            "orc_momt3_metrics": (None, [i, i, i, p, p, p, d, i, i, d, d, d,
+                                         p, p, p, p, p, p, p, p, p, p, p]),
+            "orc_momt3_solve": (i, [i, i, i, p, p, p, d, d, d, d, i, i, i, i, d, d,
+                                    p, p, p, p, p, p, p, i]),
             "orc_spectral_norm": (d, [i, p]),
             "orc_shrink_nuc": (None, [i, p, d, p]),
             "orc_vomt_unrolled_grad": (d, [i, i, i, p, p, p, p, p, d, d, d, d, i, i, p, p, p]),
@@ -463,6 +467,46 @@ def vomt3_solve(rho0, rho1, edges, alpha=1.0, tau=None, mu=None, nu=None, cost=N
                                  float(tol_gap), float(tol_res), _ptr(ux), _ptr(uy), _ptr(uz), _ptr(w), _ptr(phi),
                                  _ptr(met), _ptr(hist), nchk)
     out = dict(ux=ux, uy=uy, uz=uz, w=w, phi=phi, iters=it, mu=mu, nu=nu, tau=tau,
+               metrics=dict(zip(MET_NAMES, met)))
+    if history:
+        out["history"] = hist[hist[:, 6] > 0]
+    return out
+
+
+def momt3_solve(Lam0, Lam1, L, alpha=1.0, tau=None, mu=None, nu=None, u_norm=U_L2, w_norm=W_L1,
+                max_iters=2000, check_every=100, tol_gap=0.0, tol_res=0.0, init=None, history=False):
+    """The M-OMT iteration of Section 7.3 in FP64 on an n x n x n grid.
+
+    Lam0, Lam1: [k*k, n, n, n] full real symmetric matrices per cell.  L: [N, k, k].  U has
+    three directions Ux, Uy, Uz ([k*k, n, n, n] each); ||U||_2 is the Frobenius norm over the
+    three directions jointly, ||U||_{1,nuc} the sum of the three directions' nuclear norms.
+    mu defaults to 1/(48 tau (n-1)^2), nu to 1/(4 tau lambda_max(-Delta_L)).
+    """
+    Lam0, Lam1, L = _f64(Lam0), _f64(Lam1), _f64(L)
+    N, k = L.shape[0], L.shape[1]
+    n = Lam0.shape[-1]
+    if k > 8 or N * k * k > 512:
+        raise ValueError("k <= 8 and N k^2 <= 512")
+    if tau is None:
+        tau = default_tau_matrix(n)
+    if mu is None:
+        mu = float(_load().orc_step_mu3(n, float(tau), 1))
+    if nu is None:
+        nu = 1.0 / (4.0 * tau * quantum_lmax(L))
+    kk = k * k
+    if init is None:
+        Ux, Uy, Uz = (np.zeros((kk, n, n, n)) for _ in range(3))
+        W = np.zeros((N * kk, n, n, n)); Phi = np.zeros((kk, n, n, n))
+    else:
+        Ux, Uy, Uz, W, Phi = (np.array(init[x], dtype=np.float64, copy=True) for x in ("Ux", "Uy", "Uz", "W", "Phi"))
+    nchk = max_iters // max(check_every, 1) + 2
+    hist = np.zeros((nchk, NMET))
+    met = np.zeros(NMET)
+    it = _load().orc_momt3_solve(n, k, N, _ptr(L), _ptr(Lam0), _ptr(Lam1), float(alpha), float(tau),
+                                 float(mu), float(nu), u_norm, w_norm, int(max_iters), int(check_every),
+                                 float(tol_gap), float(tol_res), _ptr(Ux), _ptr(Uy), _ptr(Uz), _ptr(W), _ptr(Phi),
+                                 _ptr(met), _ptr(hist), nchk)
+    out = dict(Ux=Ux, Uy=Uy, Uz=Uz, W=W, Phi=Phi, iters=it, mu=mu, nu=nu, tau=tau,
                metrics=dict(zip(MET_NAMES, met)))
     if history:
         out["history"] = hist[hist[:, 6] > 0]

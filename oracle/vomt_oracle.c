@@ -1465,3 +1465,223 @@ int orc_vomt3_solve(int n, int k, int l, const int *ea, const int *eb, const dou
     free(bx); free(by); free(bz); free(bw); free(dv); free(dg); free(pphi);
     return t;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Matrix OMT on 3-D grids                                                    */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The matrix problem of Sections 4-5 and the iteration of Section 7.3 on an
+ * n x n x n grid: U has three directions U_x, U_y, U_z, each a full k x k
+ * matrix per point ([k*k][n][n][n] planes, the 3-D gradient and divergence of
+ * Appendix A applied entrywise), W and grad_L as in 2-D.  Norms:
+ * u_norm 1: ||U||_2, the Frobenius norm over the three directions jointly;
+ * 2: entrywise ||U||_1; 3: ||U||_{1,nuc} = sum_d ||U_d||_nuc.  w_norm as in
+ * orc_momt_metrics.
+ */
+static double momt3_norm_u(int k, int u_norm, const double *a, const double *b, const double *c)
+{
+    int kk = k * k;
+    double s = 0.0;
+    if (u_norm == 3) return orc_nuc_norm(k, a) + orc_nuc_norm(k, b) + orc_nuc_norm(k, c);
+    for (int q = 0; q < kk; ++q) {
+        if (u_norm == 2) s += fabs(a[q]) + fabs(b[q]) + fabs(c[q]);
+        else s += a[q] * a[q] + b[q] * b[q] + c[q] * c[q];
+    }
+    return u_norm == 2 ? s : sqrt(s);
+}
+
+static double momt3_dualnorm_u(int k, int u_norm, const double *a, const double *b, const double *c)
+{
+    int kk = k * k;
+    double s = 0.0;
+    if (u_norm == 3) {
+        double v = orc_spectral_norm(k, a), v2 = orc_spectral_norm(k, b), v3 = orc_spectral_norm(k, c);
+        if (v2 > v) v = v2;
+        if (v3 > v) v = v3;
+        return v;
+    }
+    for (int q = 0; q < kk; ++q) {
+        if (u_norm == 2) {
+            if (fabs(a[q]) > s) s = fabs(a[q]);
+            if (fabs(b[q]) > s) s = fabs(b[q]);
+            if (fabs(c[q]) > s) s = fabs(c[q]);
+        } else {
+            s += a[q] * a[q] + b[q] * b[q] + c[q] * c[q];
+        }
+    }
+    return u_norm == 2 ? s : sqrt(s);
+}
+
+static double momt_norm_w(int k, int N, int w_norm, const double *w)
+{
+    int kk = k * k;
+    double s = 0.0;
+    if (w_norm == 2) {
+        for (int s_ = 0; s_ < N; ++s_) s += orc_nuc_norm(k, w + s_ * kk);
+        return s;
+    }
+    for (int q = 0; q < N * kk; ++q) s += w_norm == 0 ? fabs(w[q]) : w[q] * w[q];
+    return w_norm == 0 ? s : sqrt(s);
+}
+
+static double momt_dualnorm_w(int k, int N, int w_norm, const double *g)
+{
+    int kk = k * k;
+    double m = 0.0;
+    if (w_norm == 2) {
+        for (int s_ = 0; s_ < N; ++s_) {
+            double v = orc_spectral_norm(k, g + s_ * kk);
+            if (v > m) m = v;
+        }
+        return m;
+    }
+    for (int q = 0; q < N * kk; ++q) {
+        if (w_norm == 0) { if (fabs(g[q]) > m) m = fabs(g[q]); }
+        else m += g[q] * g[q];
+    }
+    return w_norm == 0 ? m : sqrt(m);
+}
+
+void orc_momt3_metrics(int n, int k, int N, const double *L, const double *Lam0, const double *Lam1,
+                       double alpha, int u_norm, int w_norm, double mu, double nu, double tau,
+                       const double *Ux, const double *Uy, const double *Uz, const double *W, const double *Phi,
+                       const double *pUx, const double *pUy, const double *pUz, const double *pW,
+                       const double *pPhi, double *out)
+{
+    int kk = k * k;
+    size_t m = (size_t)n * n * n, nk = (size_t)kk * m, nw = (size_t)N * kk * m;
+    double *dv = (double *)malloc(sizeof(double) * nk), *dl = (double *)malloc(sizeof(double) * nk);
+    double *gx = (double *)malloc(sizeof(double) * nk), *gy = (double *)malloc(sizeof(double) * nk);
+    double *gz = (double *)malloc(sizeof(double) * nk), *gl = (double *)malloc(sizeof(double) * nw);
+    double A[64], B[64], C[64], X[8 * 64];
+    double P = 0.0, D = 0.0, rr = 0.0, bb = 0.0, di = 0.0, R = 0.0;
+    for (size_t p = 0; p < m; ++p) {
+        for (int q = 0; q < kk; ++q) { A[q] = Ux[q * m + p]; B[q] = Uy[q * m + p]; C[q] = Uz[q * m + p]; }
+        for (int q = 0; q < N * kk; ++q) X[q] = W[q * m + p];
+        P += momt3_norm_u(k, u_norm, A, B, C) + alpha * momt_norm_w(k, N, w_norm, X);
+    }
+    for (size_t q = 0; q < nk; ++q) D += Phi[q] * (Lam1[q] - Lam0[q]);
+    orc_div3(n, kk, Ux, Uy, Uz, dv);
+    for (size_t p = 0; p < m; ++p) {            /* div_L per point on the 3-D grid */
+        for (int q = 0; q < N * kk; ++q) X[q] = W[q * m + p];
+        orc_div_L_point(k, N, L, X, A);
+        for (int q = 0; q < kk; ++q) dl[q * m + p] = A[q];
+    }
+    for (size_t q = 0; q < nk; ++q) {
+        double r = dv[q] + dl[q] - (Lam0[q] - Lam1[q]);
+        rr += r * r;
+        bb += (Lam0[q] - Lam1[q]) * (Lam0[q] - Lam1[q]);
+    }
+    orc_grad3(n, kk, Phi, gx, gy, gz);
+    for (size_t p = 0; p < m; ++p) {
+        for (int q = 0; q < kk; ++q) { A[q] = gx[q * m + p]; B[q] = gy[q * m + p]; C[q] = gz[q * m + p]; }
+        double v = momt3_dualnorm_u(k, u_norm, A, B, C) - 1.0;
+        if (v > di) di = v;
+        for (int q = 0; q < kk; ++q) A[q] = Phi[q * m + p];
+        orc_grad_L_point(k, N, L, A, X);
+        v = momt_dualnorm_w(k, N, w_norm, X) - alpha;
+        if (v > di) di = v;
+    }
+    if (pUx) {
+        double su = 0.0, sw = 0.0, sp = 0.0, cr = 0.0;
+        double *du[3];
+        const double *cu[3] = {Ux, Uy, Uz}, *pu[3] = {pUx, pUy, pUz};
+        for (int d = 0; d < 3; ++d) {
+            du[d] = (double *)malloc(sizeof(double) * nk);
+            for (size_t q = 0; q < nk; ++q) { du[d][q] = cu[d][q] - pu[d][q]; su += du[d][q] * du[d][q]; }
+        }
+        for (size_t q = 0; q < nk; ++q) sp += (Phi[q] - pPhi[q]) * (Phi[q] - pPhi[q]);
+        for (size_t q = 0; q < nw; ++q) sw += (W[q] - pW[q]) * (W[q] - pW[q]);
+        orc_div3(n, kk, du[0], du[1], du[2], dv);
+        for (size_t p = 0; p < m; ++p) {
+            for (int q = 0; q < N * kk; ++q) X[q] = W[q * m + p] - pW[q * m + p];
+            orc_div_L_point(k, N, L, X, A);
+            for (int q = 0; q < kk; ++q) dl[q * m + p] = A[q];
+        }
+        for (size_t q = 0; q < nk; ++q) cr += (Phi[q] - pPhi[q]) * (dv[q] + dl[q]);
+        R = su / mu + sw / nu + sp / tau - 2.0 * cr;
+        for (int d = 0; d < 3; ++d) free(du[d]);
+    }
+    out[0] = P;
+    out[1] = D;
+    out[2] = fabs(P - D) / (fabs(P) > 1e-300 ? fabs(P) : 1e-300);
+    out[3] = sqrt(rr) / (bb > 0.0 ? sqrt(bb) : 1.0);
+    out[4] = R;
+    out[5] = di;
+    free(dv); free(dl); free(gx); free(gy); free(gz); free(gl);
+}
+
+/* The M-OMT iteration of Section 7.3 on the 3-D grid (the steps of orc_momt_solve
+ * with a third direction). */
+int orc_momt3_solve(int n, int k, int N, const double *L, const double *Lam0, const double *Lam1,
+                    double alpha, double tau, double mu, double nu, int u_norm, int w_norm,
+                    int max_iters, int check_every, double tol_gap, double tol_res,
+                    double *Ux, double *Uy, double *Uz, double *W, double *Phi,
+                    double *metrics, double *history, int hist_cap)
+{
+    int kk = k * k;
+    size_t m = (size_t)n * n * n, nk = (size_t)kk * m, nw = (size_t)N * kk * m;
+    double *g[3], *nU[3], *bu[3];
+    for (int d = 0; d < 3; ++d) {
+        g[d] = (double *)malloc(sizeof(double) * nk);
+        nU[d] = (double *)malloc(sizeof(double) * nk);
+        bu[d] = (double *)malloc(sizeof(double) * nk);
+    }
+    double *U[3] = {Ux, Uy, Uz};
+    double *nW = (double *)malloc(sizeof(double) * nw), *bw = (double *)malloc(sizeof(double) * nw);
+    double *dv = (double *)malloc(sizeof(double) * nk), *dl = (double *)malloc(sizeof(double) * nk);
+    double *pPhi = (double *)malloc(sizeof(double) * nk);
+    double v[3 * 64], o[3 * 64], xw[8 * 64], ow[8 * 64], A[64];
+    int nh = 0, t = 0;
+    if (check_every <= 0) check_every = max_iters > 0 ? max_iters : 1;
+    for (t = 1; t <= max_iters; ++t) {
+        orc_grad3(n, kk, Phi, g[0], g[1], g[2]);
+        for (size_t p = 0; p < m; ++p) {
+            for (int d = 0; d < 3; ++d)
+                for (int q = 0; q < kk; ++q) v[d * kk + q] = U[d][q * m + p] + mu * g[d][q * m + p];
+            if (u_norm == 2) for (int q = 0; q < 3 * kk; ++q) o[q] = orc_shrink1(v[q], mu);
+            else if (u_norm == 3) for (int d = 0; d < 3; ++d) orc_shrink_nuc(k, v + d * kk, mu, o + d * kk);
+            else orc_shrink2(3 * kk, v, mu, o);
+            for (int d = 0; d < 3; ++d)
+                for (int q = 0; q < kk; ++q) nU[d][q * m + p] = o[d * kk + q];
+        }
+        for (size_t p = 0; p < m; ++p) {
+            for (int q = 0; q < kk; ++q) A[q] = Phi[q * m + p];
+            orc_grad_L_point(k, N, L, A, xw);
+            for (int q = 0; q < N * kk; ++q) xw[q] = W[q * m + p] + nu * xw[q];
+            if (w_norm == 0) for (int q = 0; q < N * kk; ++q) ow[q] = orc_shrink1(xw[q], alpha * nu);
+            else if (w_norm == 2) for (int s_ = 0; s_ < N; ++s_) orc_shrink_nuc(k, xw + s_ * kk, alpha * nu, ow + s_ * kk);
+            else orc_shrink2(N * kk, xw, alpha * nu, ow);
+            for (int q = 0; q < N * kk; ++q) nW[q * m + p] = ow[q];
+        }
+        for (int d = 0; d < 3; ++d)
+            for (size_t q = 0; q < nk; ++q) bu[d][q] = 2.0 * nU[d][q] - U[d][q];
+        for (size_t q = 0; q < nw; ++q) bw[q] = 2.0 * nW[q] - W[q];
+        orc_div3(n, kk, bu[0], bu[1], bu[2], dv);
+        for (size_t p = 0; p < m; ++p) {
+            for (int q = 0; q < N * kk; ++q) xw[q] = bw[q * m + p];
+            orc_div_L_point(k, N, L, xw, A);
+            for (int q = 0; q < kk; ++q) dl[q * m + p] = A[q];
+        }
+        memcpy(pPhi, Phi, sizeof(double) * nk);
+        for (size_t q = 0; q < nk; ++q) Phi[q] = Phi[q] + tau * (dv[q] + dl[q] + Lam1[q] - Lam0[q]);
+        int check = (t % check_every == 0) || (t == max_iters);
+        double mm[ORC_NMET];
+        if (check) {
+            orc_momt3_metrics(n, k, N, L, Lam0, Lam1, alpha, u_norm, w_norm, mu, nu, tau, nU[0], nU[1], nU[2],
+                              nW, Phi, Ux, Uy, Uz, W, pPhi, mm);
+            mm[6] = (double)t;
+            mm[7] = (tol_gap > 0.0 && mm[2] <= tol_gap && mm[3] <= tol_res) ? 1.0 : 0.0;
+            if (history && nh < hist_cap) { memcpy(history + (size_t)nh * ORC_NMET, mm, sizeof mm); ++nh; }
+            if (metrics) memcpy(metrics, mm, sizeof mm);
+        }
+        for (int d = 0; d < 3; ++d) memcpy(U[d], nU[d], sizeof(double) * nk);
+        memcpy(W, nW, sizeof(double) * nw);
+        if (check && mm[7] != 0.0) break;
+    }
+    if (t > max_iters) t = max_iters;
+    for (int d = 0; d < 3; ++d) { free(g[d]); free(nU[d]); free(bu[d]); }
+    free(nW); free(bw); free(dv); free(dl); free(pPhi);
+    return t;
+}
