@@ -360,6 +360,23 @@ int momt_solve(vomt_ctx *ctx, int n, int k, const float *Lam0, const float *Lam1
                double alpha, const vomt_params *p, float *U, float *W, float *Phi, vomt_result *result,
                void *stream);
 
+/* Matrix OMT on an n x n x n grid (2 <= n <= 1024): the iteration of momt_solve
+ * with a third spatial direction (the discretization of vomt_solve3d), for
+ * volumes of matrix densities such as 3-D DTI.
+ *   Lam0, Lam1: device [k*k][n][n][n] (x fastest), the checks of momt_solve.
+ *   U: device [3][k*k][n][n][n] (U_x, U_y, U_z; ghost faces zero),
+ *   W: device [N][k*k][n][n][n], Phi: device [k*k][n][n][n].
+ * Norms: u_norm L2 (Frobenius over the three directions jointly), L1 or NUC
+ * (sum of the three directions' nuclear norms); w_norm as momt_solve.  Default
+ * mu = 1/(48 tau (n-1)^2); user steps must satisfy tau mu 12 (n-1)^2 + tau nu
+ * lambda_max(-Delta_L) < 1.  p->engine is ignored; p->halo > 0 sets the z planes
+ * each block marches through.  k = 2 runs the TMA form of the step where the
+ * grid allows (result->variant), k = 3 the per-thread form.
+ * Errors: as momt_solve. */
+int momt_solve3d(vomt_ctx *ctx, int n, int k, const float *Lam0, const float *Lam1, int N, const double *L,
+                 double alpha, const vomt_params *p, float *U, float *W, float *Phi, vomt_result *result,
+                 void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Allocation-free solve.  The paper has no counterpart: this is a            */
 /* deployment feature of this library.                                        */

@@ -217,6 +217,42 @@ def momt_solve(Lam0, Lam1, L, alpha: float = 1.0, *, tau=None, mu=None, nu=None,
     return MatrixSolution(U, W, Phi, res.as_dict())
 
 
+def momt_solve3d(Lam0, Lam1, L, alpha: float = 1.0, *, tau=None, mu=None, nu=None, u_norm: int = U_L2,
+                 w_norm: int = W_L1, max_iters: int = 2000, check_every: int = 100, tol_gap: float = 0.0,
+                 tol_res: float = 0.0, init=None, stream=None, zc: int = 0) -> MatrixSolution:
+    """Matrix OMT on an n x n x n grid (volumes of matrix densities, e.g. 3-D DTI).
+
+    Lam0, Lam1: CUDA float32 tensors [k*k, n, n, n] of real symmetric matrices.  L: [N, k, k]
+    (numpy, host).  Returns U [3, k*k, n, n, n] (U_x, U_y, U_z), W [N, k*k, n, n, n],
+    Phi [k*k, n, n, n].  Default mu = 1/(48 tau (n-1)^2); zc > 0 sets the z planes per block.
+    """
+    import torch
+    Lam0 = Lam0.contiguous().float()
+    Lam1 = Lam1.contiguous().float()
+    Lh = np.ascontiguousarray(L, dtype=np.float64)
+    N, k = Lh.shape[0], Lh.shape[1]
+    kk, n = Lam0.shape[0], Lam0.shape[-1]
+    if kk != k * k or Lam0.dim() != 4 or Lam0.shape != Lam1.shape:
+        raise ValueError("Lam0 and Lam1 must be [k*k, n, n, n] of one shape")
+    dev = Lam0.device
+    if init is not None:
+        U, W, Phi = (x.detach().clone().contiguous().float() for x in init)
+    else:
+        U = torch.empty((3, kk, n, n, n), device=dev, dtype=torch.float32)
+        W = torch.empty((N, kk, n, n, n), device=dev, dtype=torch.float32)
+        Phi = torch.empty((kk, n, n, n), device=dev, dtype=torch.float32)
+    p = _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, init is not None, "stream",
+                zc)
+    res = _native.Result()
+    st = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
+    ctx = _native.context(dev.index if dev.index is not None else torch.cuda.current_device())
+    rc = _native.load().momt_solve3d(ctx, int(n), int(k), Lam0.data_ptr(), Lam1.data_ptr(), int(N), Lh.ctypes.data,
+                                     float(alpha), ctypes.byref(p), U.data_ptr(), W.data_ptr(), Phi.data_ptr(),
+                                     ctypes.byref(res), ctypes.c_void_p(st))
+    _native.check(rc, ctx)
+    return MatrixSolution(U, W, Phi, res.as_dict())
+
+
 def set_wait_policy(budget_ms: float = 0.0, drop_exchange: int = 0, device: int = 0):
     """Time limit of the resident engine's waits of one block on another (0: the
     default, 2 s) and, for tests, a halo exchange that block 0 skips on purpose

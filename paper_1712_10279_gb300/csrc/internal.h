@@ -160,6 +160,9 @@ int fail(vomt_ctx *ctx, int code, const char *msg);
 int prepare_vector(vomt_ctx *ctx, int n, const vomt_graph *graph, double alpha, const vomt_params *pin, OpDev *op,
                    StepDev *s, SolveCfg *cfg, vomt_params *p);
 int check_vector_densities(vomt_ctx *ctx, int k, int n, const float *rho0, const float *rho1, cudaStream_t st);
+// 3-D solve after validation and step sizes (vector3d.cu); compact channels of g
+int solve3d_core(vomt_ctx *ctx, int n, const OpDev &g, const StepDev &s, const SolveCfg &cfg, const vomt_params &p,
+                 int zc_user, const float *rho0, const float *rho1, float *u, float *w, float *phi, cudaStream_t st);
 void fill_result(vomt_ctx *ctx, const SolveCfg &cfg, int engine, vomt_result *r, int *status);
 int run_engine(vomt_ctx *ctx, const OpDev &op, const StepDev &s, const SolveCfg &cfg, const vomt_params &p,
                const float *rho0, const float *rho1, float *u, float *w, float *phi, cudaStream_t st, int *engine);

@@ -45,10 +45,9 @@ PairTable make_pairs(int k)
 
 // per block: sum tr Lam0, sum tr Lam1, min diagonal entry, max |X_ab - X_ba|,
 // max |X_ab|, count of non-finite entries
-__global__ void k_mat_validate(int n, int k, const float *__restrict__ L0, const float *__restrict__ L1,
+__global__ void k_mat_validate(size_t nn, int k, const float *__restrict__ L0, const float *__restrict__ L1,
                                double *__restrict__ out)
 {
-    const size_t nn = (size_t)n * n;
     double t0 = 0.0, t1 = 0.0, mind = 1e300, asym = 0.0, mabs = 0.0, bad = 0.0;
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nn; q += (size_t)gridDim.x * blockDim.x) {
         for (int side = 0; side < 2; ++side) {
@@ -88,10 +87,9 @@ __global__ void k_mat_validate(int n, int k, const float *__restrict__ L0, const
 
 // full symmetric planes -> compact channels (the symmetric part), `groups` fields
 // of k*k planes each (e.g. 2 for U = (U_x, U_y))
-__global__ void k_sym_to_compact(int n, PairTable t, int groups, const float *__restrict__ full,
+__global__ void k_sym_to_compact(size_t nn, PairTable t, int groups, const float *__restrict__ full,
                                  float *__restrict__ comp)
 {
-    const size_t nn = (size_t)n * n;
     const int kk = t.k * t.k;
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nn; q += (size_t)gridDim.x * blockDim.x)
         for (int g = 0; g < groups; ++g)
@@ -103,9 +101,8 @@ __global__ void k_sym_to_compact(int n, PairTable t, int groups, const float *__
 }
 
 // full planes of N skew matrices -> compact entries above the diagonal (the skew part)
-__global__ void k_skew_to_compact(int n, PairTable t, int N, const float *__restrict__ full, float *__restrict__ comp)
+__global__ void k_skew_to_compact(size_t nn, PairTable t, int N, const float *__restrict__ full, float *__restrict__ comp)
 {
-    const size_t nn = (size_t)n * n;
     const int kk = t.k * t.k;
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nn; q += (size_t)gridDim.x * blockDim.x)
         for (int s = 0; s < N; ++s)
@@ -116,9 +113,8 @@ __global__ void k_skew_to_compact(int n, PairTable t, int N, const float *__rest
             }
 }
 
-__global__ void k_compact_to_sym(int n, PairTable t, int groups, const float *__restrict__ comp, float *__restrict__ full)
+__global__ void k_compact_to_sym(size_t nn, PairTable t, int groups, const float *__restrict__ comp, float *__restrict__ full)
 {
-    const size_t nn = (size_t)n * n;
     const int kk = t.k * t.k;
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nn; q += (size_t)gridDim.x * blockDim.x)
         for (int g = 0; g < groups; ++g)
@@ -131,9 +127,8 @@ __global__ void k_compact_to_sym(int n, PairTable t, int groups, const float *__
             }
 }
 
-__global__ void k_compact_to_skew(int n, PairTable t, int N, const float *__restrict__ comp, float *__restrict__ full)
+__global__ void k_compact_to_skew(size_t nn, PairTable t, int N, const float *__restrict__ comp, float *__restrict__ full)
 {
-    const size_t nn = (size_t)n * n;
     const int kk = t.k * t.k;
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nn; q += (size_t)gridDim.x * blockDim.x)
         for (int s = 0; s < N; ++s) {
@@ -175,15 +170,18 @@ extern "C" int momt_step_sizes(int n, int k, int N, const double *L, double tau,
     return VOMT_OK;
 }
 
-extern "C" int momt_solve(vomt_ctx *ctx, int n, int k, const float *Lam0, const float *Lam1, int N, const double *L,
-                          double alpha, const vomt_params *pin, float *U, float *W, float *Phi, vomt_result *result,
-                          void *stream)
+// Matrix OMT on a 2-D (dim 2) or 3-D (dim 3) grid: checks, compaction, the vector
+// engines (2-D) or the 3-D march, expansion.
+static int momt_any(int dim, vomt_ctx *ctx, int n, int k, const float *Lam0, const float *Lam1, int N,
+                    const double *L, double alpha, const vomt_params *pin, float *U, float *W, float *Phi,
+                    vomt_result *result, void *stream)
 {
     try {
         if (!ctx) return VOMT_ERR_BAD_ARG;
         ctx->err.clear();
         cudaStream_t st = (cudaStream_t)stream;
-        if (n < 2 || n > 32768) return fail(ctx, VOMT_ERR_BAD_ARG, "n must be in [2, 32768]");
+        if (dim == 2 && (n < 2 || n > 32768)) return fail(ctx, VOMT_ERR_BAD_ARG, "n must be in [2, 32768]");
+        if (dim == 3 && (n < 2 || n > 1024)) return fail(ctx, VOMT_ERR_BAD_ARG, "3-D grids: n must be in [2, 1024]");
         if (!(alpha > 0.0) || !isfinite(alpha)) return fail(ctx, VOMT_ERR_BAD_ARG, "alpha must be positive");
         if (!Lam0 || !Lam1 || !U || !W || !Phi) return fail(ctx, VOMT_ERR_BAD_ARG, "null array");
         vomt_params p;
@@ -194,7 +192,8 @@ extern "C" int momt_solve(vomt_ctx *ctx, int n, int k, const float *Lam0, const 
         if (p.u_norm < 1 || p.u_norm > 3 || p.w_norm < 0 || p.w_norm > 2) return fail(ctx, VOMT_ERR_BAD_ARG, "bad norm code");
         // 2 x 2 skew components have one entry a and ||W_s||_nuc = 2 |a|, the weighted ||.||_1
         if (k == 2 && p.w_norm == VOMT_W_NUC) p.w_norm = VOMT_W_L1;
-        if (p.engine < 0 || p.engine > 2 || p.halo < 0 || p.halo > 16) return fail(ctx, VOMT_ERR_BAD_ARG, "bad engine / halo");
+        if (p.engine < 0 || p.engine > 2 || p.halo < 0 || (dim == 2 && p.halo > 16))
+            return fail(ctx, VOMT_ERR_BAD_ARG, "bad engine / halo");
         if (p.eps != 0.0) return fail(ctx, VOMT_ERR_BAD_ARG, "matrix OMT takes eps = 0 (regularisation is for vector OMT)");
         OpDev op;
         double lmax = 0.0, gap = 0.0;
@@ -202,12 +201,16 @@ extern "C" int momt_solve(vomt_ctx *ctx, int n, int k, const float *Lam0, const 
         if (rc) return rc;
         const double tau = p.tau > 0.0 ? p.tau : default_tau_matrix(n);
         const double n1 = (double)(n - 1);
+        // ||grad||^2 <= 4 dim (n-1)^2; the default mu keeps tau mu ||grad||^2 at 1/4
+        const double gsq = 4.0 * dim;
         double mu = p.mu, nu = p.nu;
         const bool user = mu > 0.0 || nu > 0.0;
-        if (!(mu > 0.0)) mu = 1.0 / (32.0 * tau * n1 * n1);
+        if (!(mu > 0.0)) mu = 1.0 / (4.0 * gsq * tau * n1 * n1);
         if (!(nu > 0.0)) nu = 1.0 / (4.0 * tau * lmax);
-        if (user && !(tau * mu * 8.0 * n1 * n1 + tau * nu * lmax < 1.0))
-            return fail(ctx, VOMT_ERR_STEP_CONDITION, "step sizes break 1 > tau mu 8(n-1)^2 + tau nu lambda_max(-Delta_L)");
+        if (user && !(tau * mu * gsq * n1 * n1 + tau * nu * lmax < 1.0))
+            return fail(ctx, VOMT_ERR_STEP_CONDITION,
+                        dim == 2 ? "step sizes break 1 > tau mu 8(n-1)^2 + tau nu lambda_max(-Delta_L)"
+                                 : "step sizes break 1 > tau mu 12(n-1)^2 + tau nu lambda_max(-Delta_L)");
         p.tau = tau;
         p.mu = mu;
         p.nu = nu;
@@ -217,14 +220,14 @@ extern "C" int momt_solve(vomt_ctx *ctx, int n, int k, const float *Lam0, const 
         cudaError_t e = cudaSetDevice(ctx->device);
         if (e != cudaSuccess) return set_cuda_error(ctx, e, "cudaSetDevice");
         ctx->launches = 0;
-        const size_t nn = (size_t)n * n;
+        const size_t nn = dim == 2 ? (size_t)n * n : (size_t)n * n * n;
         const PairTable t = make_pairs(k);
         const int K = t.K, l = op.l, kk = k * k;
         // input checks
         const int vb = (int)((nn + 255) / 256 < 512 ? (nn + 255) / 256 : 512);
         rc = ensure_buffer(ctx, (void **)&ctx->partials, &ctx->partials_cap, sizeof(double) * 6 * (size_t)vb, "partials");
         if (rc) return rc;
-        k_mat_validate<<<vb, 256, 0, st>>>(n, k, Lam0, Lam1, ctx->partials);
+        k_mat_validate<<<vb, 256, 0, st>>>(nn, k, Lam0, Lam1, ctx->partials);
         ++ctx->launches;
         std::vector<double> hv((size_t)vb * 6);
         e = cudaMemcpyAsync(hv.data(), ctx->partials, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost, st);
@@ -244,28 +247,35 @@ extern "C" int momt_solve(vomt_ctx *ctx, int n, int k, const float *Lam0, const 
         if (asym > 1e-5 * mabs) return fail(ctx, VOMT_ERR_BAD_ARG, "densities must be symmetric matrices");
         if (fabs(tr0 - tr1) > 1e-5 * fmax(fabs(tr0), fabs(tr1)))
             return fail(ctx, VOMT_ERR_MASS_MISMATCH, "Lam0 and Lam1 have different total trace");
-        // compact staging: rho0, rho1 (K), u (2K), w (l), phi (K)
-        const size_t need = sizeof(float) * (size_t)(5 * K + l) * nn;
+        // compact staging: rho0, rho1 (K), u (dim K), w (l), phi (K)
+        const size_t need = sizeof(float) * (size_t)((3 + dim) * K + l) * nn;
         rc = ensure_buffer(ctx, (void **)&ctx->mstage, &ctx->mstage_bytes, need, "matrix staging");
         if (rc) return rc;
         float *c0 = ctx->mstage, *c1 = c0 + (size_t)K * nn, *cu = c1 + (size_t)K * nn;
-        float *cw = cu + (size_t)2 * K * nn, *cp = cw + (size_t)l * nn;
+        float *cw = cu + (size_t)dim * K * nn, *cp = cw + (size_t)l * nn;
         const int pb = (int)((nn + 255) / 256 < 2048 ? (nn + 255) / 256 : 2048);
-        k_sym_to_compact<<<pb, 256, 0, st>>>(n, t, 1, Lam0, c0);
-        k_sym_to_compact<<<pb, 256, 0, st>>>(n, t, 1, Lam1, c1);
+        k_sym_to_compact<<<pb, 256, 0, st>>>(nn, t, 1, Lam0, c0);
+        k_sym_to_compact<<<pb, 256, 0, st>>>(nn, t, 1, Lam1, c1);
         ctx->launches += 2;
         if (p.warm_start) {
-            k_sym_to_compact<<<pb, 256, 0, st>>>(n, t, 2, U, cu);
-            k_skew_to_compact<<<pb, 256, 0, st>>>(n, t, N, W, cw);
-            k_sym_to_compact<<<pb, 256, 0, st>>>(n, t, 1, Phi, cp);
+            k_sym_to_compact<<<pb, 256, 0, st>>>(nn, t, dim, U, cu);
+            k_skew_to_compact<<<pb, 256, 0, st>>>(nn, t, N, W, cw);
+            k_sym_to_compact<<<pb, 256, 0, st>>>(nn, t, 1, Phi, cp);
             ctx->launches += 3;
         }
-        int engine = 0;
-        rc = run_engine(ctx, op, s, cfg, p, c0, c1, cu, cw, cp, st, &engine);
+        int engine = VOMT_ENGINE_STREAM;
+        if (dim == 2) {
+            rc = run_engine(ctx, op, s, cfg, p, c0, c1, cu, cw, cp, st, &engine);
+        } else {
+            ctx->last_blocks = ctx->last_halo = ctx->last_variant = 0;
+            vomt_params p3 = p;
+            p3.halo = 0;
+            rc = solve3d_core(ctx, n, op, s, cfg, p3, p.halo, c0, c1, cu, cw, cp, st);
+        }
         if (rc) return rc;
-        k_compact_to_sym<<<pb, 256, 0, st>>>(n, t, 2, cu, U);
-        k_compact_to_skew<<<pb, 256, 0, st>>>(n, t, N, cw, W);
-        k_compact_to_sym<<<pb, 256, 0, st>>>(n, t, 1, cp, Phi);
+        k_compact_to_sym<<<pb, 256, 0, st>>>(nn, t, dim, cu, U);
+        k_compact_to_skew<<<pb, 256, 0, st>>>(nn, t, N, cw, W);
+        k_compact_to_sym<<<pb, 256, 0, st>>>(nn, t, 1, cp, Phi);
         ctx->launches += 3;
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -277,4 +287,18 @@ extern "C" int momt_solve(vomt_ctx *ctx, int n, int k, const float *Lam0, const 
     } catch (...) {
         return fail(ctx, VOMT_ERR_BAD_ARG, "internal exception");
     }
+}
+
+extern "C" int momt_solve(vomt_ctx *ctx, int n, int k, const float *Lam0, const float *Lam1, int N, const double *L,
+                          double alpha, const vomt_params *pin, float *U, float *W, float *Phi, vomt_result *result,
+                          void *stream)
+{
+    return momt_any(2, ctx, n, k, Lam0, Lam1, N, L, alpha, pin, U, W, Phi, result, stream);
+}
+
+extern "C" int momt_solve3d(vomt_ctx *ctx, int n, int k, const float *Lam0, const float *Lam1, int N,
+                            const double *L, double alpha, const vomt_params *pin, float *U, float *W, float *Phi,
+                            vomt_result *result, void *stream)
+{
+    return momt_any(3, ctx, n, k, Lam0, Lam1, N, L, alpha, pin, U, W, Phi, result, stream);
 }

@@ -259,6 +259,7 @@ __global__ void __launch_bounds__(T3) k_metrics3(S3In cur, S3In prv, const float
         const float ih = s.ih, alpha = s.alpha;
         const double dih = (double)(n - 1);
         float ph[K], dph[K], ddiv[K], gwb[K];
+        float uxs[K], uys[K], uzs[K], gxs[K], gys[K], gzs[K];     // nuclear norms only
         double rdiv[K];
         float nu_pt = 0.0f, dn_u = 0.0f, fdu = 0.0f, fdp = 0.0f, fd = 0.0f, fbb = 0.0f, fdw = 0.0f, fx = 0.0f;
 #pragma unroll
@@ -283,7 +284,10 @@ __global__ void __launch_bounds__(T3) k_metrics3(S3In cur, S3In prv, const float
             const float gx = hx ? ih * (cur.phi[q + SX] - ph[c]) : 0.0f;
             const float gy = hy ? ih * (cur.phi[q + SY] - ph[c]) : 0.0f;
             const float gz = hz ? ih * (cur.phi[q + SZ] - ph[c]) : 0.0f;
-            if (UN == VOMT_U_L12) {
+            if (UN == VOMT_U_NUC) {
+                uxs[c] = a; uys[c] = bq; uzs[c] = cq;
+                gxs[c] = gx; gys[c] = gy; gzs[c] = gz;
+            } else if (UN == VOMT_U_L12) {
                 nu_pt += sqrtf(a * a + bq * bq + cq * cq);
                 dn_u = fmaxf(dn_u, sqrtf(gx * gx + gy * gy + gz * gz));
             } else if (UN == VOMT_U_L2) {
@@ -295,7 +299,18 @@ __global__ void __launch_bounds__(T3) k_metrics3(S3In cur, S3In prv, const float
             }
         }
         if (UN == VOMT_U_L2) { nu_pt = sqrtf(nu_pt); dn_u = sqrtf(dn_u); }
-        float nw_pt = 0.0f, dn_w = 0.0f;
+        if constexpr (UN == VOMT_U_NUC) {        // sum of the nuclear norms, largest spectral norm
+            float n1, s1, n2, s2, n3, s3;
+            mat::sym_nuc_spec<K>(uxs, n1, s1);
+            mat::sym_nuc_spec<K>(uys, n2, s2);
+            mat::sym_nuc_spec<K>(uzs, n3, s3);
+            nu_pt = n1 + n2 + n3;
+            mat::sym_nuc_spec<K>(gxs, n1, s1);
+            mat::sym_nuc_spec<K>(gys, n2, s2);
+            mat::sym_nuc_spec<K>(gzs, n3, s3);
+            dn_u = fmaxf(s1, fmaxf(s2, s3));
+        }
+        float nw_pt = 0.0f, dn_w = 0.0f, wg2 = 0.0f, gg2 = 0.0f;
 #pragma unroll
         for (int e = 0; e < LK; ++e) {
             if (e < g.l) {
@@ -309,8 +324,22 @@ __global__ void __launch_bounds__(T3) k_metrics3(S3In cur, S3In prv, const float
                     gwb[c] -= g.Dv[c][e] * we;
                     ddiv[c] -= g.Dv[c][e] * dwe;
                 }
-                if (WN == VOMT_W_L1) { nw_pt += wgt * fabsf(we); dn_w = fmaxf(dn_w, fabsf(ge)); }
-                else { nw_pt += wgt * we * we; dn_w += wgt * ge * ge; }
+                if (WN == VOMT_W_L1) {
+                    nw_pt += wgt * fabsf(we);
+                    dn_w = fmaxf(dn_w, fabsf(ge));
+                } else if (WN == VOMT_W_NUC) {
+                    // 3 x 3 skew components (a, b, c): ||W_s||_nuc = 2 |(a,b,c)|, spectral |(a,b,c)|
+                    wg2 += we * we;
+                    gg2 += ge * ge;
+                    if (e % 3 == 2) {
+                        nw_pt += 2.0f * sqrtf(wg2);
+                        dn_w = fmaxf(dn_w, sqrtf(gg2));
+                        wg2 = gg2 = 0.0f;
+                    }
+                } else {
+                    nw_pt += wgt * we * we;
+                    dn_w += wgt * ge * ge;
+                }
             }
         }
         if (WN == VOMT_W_L2) { nw_pt = sqrtf(nw_pt); dn_w = sqrtf(dn_w); }
@@ -399,6 +428,11 @@ L3 make3()
 template <int K>
 L3 pick3_norms(int un, int wn)
 {
+    if constexpr (K == 3 || K == 6) {          // nuclear norms: compact 2 x 2 and 3 x 3 matrices
+        if (un == VOMT_U_NUC)
+            return wn == VOMT_W_L1 ? make3<K, 3, 0>() : (wn == VOMT_W_L2 ? make3<K, 3, 1>() : make3<K, 3, 2>());
+        if (wn == VOMT_W_NUC) return un == VOMT_U_L2 ? make3<K, 1, 2>() : make3<K, 2, 2>();
+    }
     if (un == VOMT_U_L12) return wn == VOMT_W_L1 ? make3<K, 0, 0>() : make3<K, 0, 1>();
     if (un == VOMT_U_L2) return wn == VOMT_W_L1 ? make3<K, 1, 0>() : make3<K, 1, 1>();
     return wn == VOMT_W_L1 ? make3<K, 2, 0>() : make3<K, 2, 1>();
@@ -419,6 +453,122 @@ L3 pick3(int k, int un, int wn)
 }
 
 }  // namespace
+}  // namespace vomt
+
+namespace vomt {
+
+// The 3-D solve after validation and step sizes: workspace, the z-marching
+// iterations with their checks, the copy-out; ctx->hstatus[0] holds the final
+// status block.  rho0, rho1, u, w, phi are [c][z][y][x] volumes (u: u_x, u_y,
+// u_z runs of k volumes each) in the compact channels of g.
+int solve3d_core(vomt_ctx *ctx, int n, const OpDev &g, const StepDev &s, const SolveCfg &cfg, const vomt_params &p,
+                 int zc_user, const float *rho0, const float *rho1, float *u, float *w, float *phi, cudaStream_t st)
+{
+    const int k = g.k, l = g.l;
+    const size_t m = (size_t)n * n * n;
+    cudaError_t e;
+    int rc;
+    // workspace: b, then two states {phi, u_x, u_y, u_z, w}
+    const size_t per_state = (size_t)(4 * k + l) * m;
+    rc = ensure_buffer(ctx, (void **)&ctx->ws, &ctx->ws_floats, ((size_t)k * m + 2 * per_state) * sizeof(float),
+                       "workspace");
+    if (rc) return rc;
+    float *b = ctx->ws;
+    S3Out so[2];
+    S3In si[2];
+    for (int q = 0; q < 2; ++q) {
+        float *base = ctx->ws + (size_t)k * m + q * per_state;
+        so[q] = S3Out{base, base + (size_t)k * m, base + (size_t)2 * k * m, base + (size_t)3 * k * m,
+                      base + (size_t)4 * k * m};
+        si[q] = S3In{so[q].phi, so[q].ux, so[q].uy, so[q].uz, so[q].w};
+    }
+    const int nblocks = (int)((m + T3 - 1) / T3);     // checks: one point per thread
+    rc = ensure_buffer(ctx, (void **)&ctx->partials, &ctx->partials_cap, sizeof(double) * (size_t)nblocks * NRED,
+                       "partials");
+    if (rc) return rc;
+    const int max_checks = p.max_iters / p.check_every + 2;
+    if (ctx->hist_cap < max_checks) {
+        if (ctx->dhist) cudaFree(ctx->dhist);
+        ctx->dhist = nullptr;
+        ctx->hist_cap = 0;
+        e = cudaMalloc(&ctx->dhist, sizeof(double) * NMET * (size_t)max_checks);
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "history");
+        ctx->hist_cap = max_checks;
+    }
+    e = cudaMemsetAsync(ctx->dstatus, 0, sizeof(DevStatus), st);
+    if (e != cudaSuccess) return set_cuda_error(ctx, e, "status reset");
+    const int pblocks = (int)std::min<size_t>((m + 255) / 256, 4096);
+    k_prepare3<<<pblocks, 256, 0, st>>>(m, k, l, rho0, rho1, b, p.warm_start, u, w, phi, so[0]);
+    ctx->launches += 1;
+    L3 L = pick3(k, p.u_norm, p.w_norm);
+    e = cudaFuncSetAttribute((const void *)L.step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+    if (e != cudaSuccess) return set_cuda_error(ctx, e, "3-D step shared memory");
+    // inputs by TMA tiles where they apply (n a multiple of 4, n >= 40, k <= 4)
+    Tma3Plan *tp = tma3_supported(n, k, l, p.u_norm, p.w_norm)
+                       ? tma3_plan_create(n, k, l, p.u_norm, p.w_norm, so[0].phi, so[1].phi, b)
+                       : nullptr;
+    ctx->last_variant = tp ? 1 : 0;
+    // z chunk: the longest of 32, 16, 8, 4 planes that still gives 1.5 blocks per SM
+    // (TMA form; longer chunks amortise the pipeline fill, but fewer blocks than SMs
+    // leave HBM idle; 32 measured best at 128^3 and 256^3) or four blocks per SM
+    // (per-thread form, which needs the warps)
+    const int tiles = ((n + MX - 1) / MX) * ((n + MY - 1) / MY);
+    const size_t want = tp ? (size_t)(3 * ctx->sm_count / 2) : (size_t)(4 * ctx->sm_count);
+    int zc = 4;
+    for (int c : {32, 16, 8})
+        if ((size_t)tiles * ((n + c - 1) / c) >= want) { zc = c; break; }
+    if (zc_user > 0) zc = std::min(zc_user, n);
+    const dim3 mgrid((n + MX - 1) / MX, (n + MY - 1) / MY, (n + zc - 1) / zc);
+    ctx->last_blocks = (int)(mgrid.x * mgrid.y * mgrid.z);
+    auto check = [&](int t, int cur) {
+        L.metrics<<<nblocks, T3, 0, st>>>(si[cur], si[cur ^ 1], b, g, s, ctx->partials, ctx->dstatus);
+        k_finalize<<<1, 256, 0, st>>>(ctx->partials, nblocks, cfg, t, ctx->dstatus, ctx->dhist, ctx->hist_cap);
+        ctx->launches += 2;
+    };
+    if (p.max_iters == 0) check(0, 0);
+    const bool tol_mode = cfg.tol_gap > 0.0;
+    const int chunk = p.check_every * ((2048 + p.check_every - 1) / p.check_every);
+    int t = 0, nchunk = 0;
+    bool stopped = false;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (tol_mode)
+        for (int q = 0; q < 2; ++q) cudaEventCreateWithFlags(&ev[q], cudaEventDisableTiming);
+    while (t < p.max_iters && !stopped) {
+        const int end = std::min(t + chunk, p.max_iters);
+        for (int tt = t + 1; tt <= end; ++tt) {
+            const int cur = tt & 1;
+            if (tp)
+                tma3_launch_step(tp, cur ^ 1, so[cur], g, s, ctx->dstatus, zc, st);
+            else
+                L.step<<<mgrid, MT, L.smem, st>>>(si[cur ^ 1], so[cur], b, g, s, ctx->dstatus, zc);
+            ctx->launches += 1;
+            if (tt % p.check_every == 0 || tt == p.max_iters) check(tt, cur);
+        }
+        t = end;
+        if (tol_mode) {
+            const int slot = nchunk & 1;
+            cudaMemcpyAsync(&ctx->hstatus[slot], ctx->dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, st);
+            cudaEventRecord(ev[slot], st);
+            if (nchunk >= 1) {
+                cudaEventSynchronize(ev[slot ^ 1]);
+                if (ctx->hstatus[slot ^ 1].stop) stopped = true;
+            }
+            ++nchunk;
+        }
+    }
+    k_copy_out3<<<pblocks, 256, 0, st>>>(m, k, l, si[0], si[1], ctx->dstatus, u, w, phi);
+    ctx->launches += 1;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ctx->hstatus[0], ctx->dstatus, sizeof(DevStatus),
+                                              cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    for (int q = 0; q < 2; ++q)
+        if (ev[q]) cudaEventDestroy(ev[q]);
+    tma3_plan_destroy(tp);
+    if (e != cudaSuccess) return set_cuda_error(ctx, e, "3-D solve");
+    return VOMT_OK;
+}
+
 }  // namespace vomt
 
 using namespace vomt;
@@ -469,108 +619,10 @@ extern "C" int vomt_solve3d(vomt_ctx *ctx, int n, const float *rho0, const float
         s.mu = (float)mu;
         cfg.mu = mu;
         p.mu = mu;
-        const int k = g.k, l = g.l;
-        const size_t m = (size_t)n * n * n;
-        rc = check_vector_densities(ctx, k * n, n, rho0, rho1, st);
+        rc = check_vector_densities(ctx, g.k * n, n, rho0, rho1, st);
         if (rc) return rc;
-        // workspace: b, then two states {phi, u_x, u_y, u_z, w}
-        const size_t per_state = (size_t)(4 * k + l) * m;
-        rc = ensure_buffer(ctx, (void **)&ctx->ws, &ctx->ws_floats, ((size_t)k * m + 2 * per_state) * sizeof(float),
-                           "workspace");
+        rc = solve3d_core(ctx, n, g, s, cfg, p, zc_user, rho0, rho1, u, w, phi, st);
         if (rc) return rc;
-        float *b = ctx->ws;
-        S3Out so[2];
-        S3In si[2];
-        for (int q = 0; q < 2; ++q) {
-            float *base = ctx->ws + (size_t)k * m + q * per_state;
-            so[q] = S3Out{base, base + (size_t)k * m, base + (size_t)2 * k * m, base + (size_t)3 * k * m,
-                          base + (size_t)4 * k * m};
-            si[q] = S3In{so[q].phi, so[q].ux, so[q].uy, so[q].uz, so[q].w};
-        }
-        const int nblocks = (int)((m + T3 - 1) / T3);     // checks: one point per thread
-        rc = ensure_buffer(ctx, (void **)&ctx->partials, &ctx->partials_cap, sizeof(double) * (size_t)nblocks * NRED,
-                           "partials");
-        if (rc) return rc;
-        const int max_checks = p.max_iters / p.check_every + 2;
-        if (ctx->hist_cap < max_checks) {
-            if (ctx->dhist) cudaFree(ctx->dhist);
-            ctx->dhist = nullptr;
-            ctx->hist_cap = 0;
-            e = cudaMalloc(&ctx->dhist, sizeof(double) * NMET * (size_t)max_checks);
-            if (e != cudaSuccess) return set_cuda_error(ctx, e, "history");
-            ctx->hist_cap = max_checks;
-        }
-        e = cudaMemsetAsync(ctx->dstatus, 0, sizeof(DevStatus), st);
-        if (e != cudaSuccess) return set_cuda_error(ctx, e, "status reset");
-        const int pblocks = (int)std::min<size_t>((m + 255) / 256, 4096);
-        k_prepare3<<<pblocks, 256, 0, st>>>(m, k, l, rho0, rho1, b, p.warm_start, u, w, phi, so[0]);
-        ctx->launches += 1;
-        L3 L = pick3(k, p.u_norm, p.w_norm);
-        e = cudaFuncSetAttribute((const void *)L.step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
-        if (e != cudaSuccess) return set_cuda_error(ctx, e, "3-D step shared memory");
-        // inputs by TMA tiles where they apply (n a multiple of 4, n >= 40, k <= 4)
-        Tma3Plan *tp = tma3_supported(n, k, l, p.u_norm, p.w_norm)
-                           ? tma3_plan_create(n, k, l, p.u_norm, p.w_norm, so[0].phi, so[1].phi, b)
-                           : nullptr;
-        ctx->last_variant = tp ? 1 : 0;
-        // z chunk: the longest of 32, 16, 8, 4 planes that still gives 1.5 blocks per SM
-        // (TMA form; longer chunks amortise the pipeline fill, but fewer blocks than SMs
-        // leave HBM idle; 32 measured best at 128^3 and 256^3) or four blocks per SM
-        // (per-thread form, which needs the warps)
-        const int tiles = ((n + MX - 1) / MX) * ((n + MY - 1) / MY);
-        const size_t want = tp ? (size_t)(3 * ctx->sm_count / 2) : (size_t)(4 * ctx->sm_count);
-        int zc = 4;
-        for (int c : {32, 16, 8})
-            if ((size_t)tiles * ((n + c - 1) / c) >= want) { zc = c; break; }
-        if (zc_user > 0) zc = std::min(zc_user, n);
-        const dim3 mgrid((n + MX - 1) / MX, (n + MY - 1) / MY, (n + zc - 1) / zc);
-        ctx->last_blocks = (int)(mgrid.x * mgrid.y * mgrid.z);
-        auto check = [&](int t, int cur) {
-            L.metrics<<<nblocks, T3, 0, st>>>(si[cur], si[cur ^ 1], b, g, s, ctx->partials, ctx->dstatus);
-            k_finalize<<<1, 256, 0, st>>>(ctx->partials, nblocks, cfg, t, ctx->dstatus, ctx->dhist, ctx->hist_cap);
-            ctx->launches += 2;
-        };
-        if (p.max_iters == 0) check(0, 0);
-        const bool tol_mode = cfg.tol_gap > 0.0;
-        const int chunk = p.check_every * ((2048 + p.check_every - 1) / p.check_every);
-        int t = 0, nchunk = 0;
-        bool stopped = false;
-        cudaEvent_t ev[2] = {nullptr, nullptr};
-        if (tol_mode)
-            for (int q = 0; q < 2; ++q) cudaEventCreateWithFlags(&ev[q], cudaEventDisableTiming);
-        while (t < p.max_iters && !stopped) {
-            const int end = std::min(t + chunk, p.max_iters);
-            for (int tt = t + 1; tt <= end; ++tt) {
-                const int cur = tt & 1;
-                if (tp)
-                    tma3_launch_step(tp, cur ^ 1, so[cur], g, s, ctx->dstatus, zc, st);
-                else
-                    L.step<<<mgrid, MT, L.smem, st>>>(si[cur ^ 1], so[cur], b, g, s, ctx->dstatus, zc);
-                ctx->launches += 1;
-                if (tt % p.check_every == 0 || tt == p.max_iters) check(tt, cur);
-            }
-            t = end;
-            if (tol_mode) {
-                const int slot = nchunk & 1;
-                cudaMemcpyAsync(&ctx->hstatus[slot], ctx->dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, st);
-                cudaEventRecord(ev[slot], st);
-                if (nchunk >= 1) {
-                    cudaEventSynchronize(ev[slot ^ 1]);
-                    if (ctx->hstatus[slot ^ 1].stop) stopped = true;
-                }
-                ++nchunk;
-            }
-        }
-        k_copy_out3<<<pblocks, 256, 0, st>>>(m, k, l, si[0], si[1], ctx->dstatus, u, w, phi);
-        ctx->launches += 1;
-        e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&ctx->hstatus[0], ctx->dstatus, sizeof(DevStatus),
-                                                  cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        for (int q = 0; q < 2; ++q)
-            if (ev[q]) cudaEventDestroy(ev[q]);
-        tma3_plan_destroy(tp);
-        if (e != cudaSuccess) return set_cuda_error(ctx, e, "3-D solve");
         int status = VOMT_OK;
         fill_result(ctx, cfg, VOMT_ENGINE_STREAM, result, &status);
         return status;

@@ -327,6 +327,11 @@ using Kern3 = void (*)(const Maps3, const float *, S3Out, OpDev, StepDev, DevSta
 template <int K>
 Kern3 pick_norms3t(int un, int wn)
 {
+    if constexpr (K == 3) {                    // nuclear norms: compact 2 x 2 matrices
+        if (un == VOMT_U_NUC)
+            return wn == VOMT_W_L1 ? k_step3t<K, 3, 0> : (wn == VOMT_W_L2 ? k_step3t<K, 3, 1> : k_step3t<K, 3, 2>);
+        if (wn == VOMT_W_NUC) return un == VOMT_U_L2 ? k_step3t<K, 1, 2> : k_step3t<K, 2, 2>;
+    }
     if (un == VOMT_U_L12) return wn == VOMT_W_L1 ? k_step3t<K, 0, 0> : k_step3t<K, 0, 1>;
     if (un == VOMT_U_L2) return wn == VOMT_W_L1 ? k_step3t<K, 1, 0> : k_step3t<K, 1, 1>;
     return wn == VOMT_W_L1 ? k_step3t<K, 2, 0> : k_step3t<K, 2, 1>;
@@ -334,7 +339,8 @@ Kern3 pick_norms3t(int un, int wn)
 
 Kern3 pick3t(int k, int un, int wn)
 {
-    if (un < 0 || un > 2 || wn < 0 || wn > 1) return nullptr;
+    if (un < 0 || un > 3 || wn < 0 || wn > 2) return nullptr;
+    if ((un == VOMT_U_NUC || wn == VOMT_W_NUC) && k != 3) return nullptr;
     switch (k) {
         case 1: return pick_norms3t<1>(un, wn);
         case 2: return pick_norms3t<2>(un, wn);

@@ -23,6 +23,9 @@ same shapes and structure:
 * ``random_L``           N symmetric k x k matrices, Gaussian entries,
                          symmetrised and scaled to unit Frobenius norm.
 * ``random_connected_graph``  G(k, p) redrawn until connected.
+* ``tensor_field_pair3`` the tensor-field recipe on an n x n x n grid (angle and
+                         eigenvalue fields smoothed with sigma max(1, n/12) cells),
+                         matrix densities of a 3-D DTI volume's shape.
 * ``blob_pair3``         the blob recipe on an n x n x n grid (three blobs per
                          channel, sigma uniform in [n/12, n/5] cells, amplitude
                          uniform in [0.5, 1], 1e-3 floor; total mass 1), the
@@ -130,6 +133,27 @@ def _tensor_field(rng, n, k, sigma=10.0):
 def tensor_field_pair(n: int = 128, k: int = 3, seed: int = 1003):
     rng = np.random.default_rng(seed)
     return _tensor_field(rng, n, k), _tensor_field(rng, n, k)
+
+
+def _tensor_field3(rng, n, k, sigma):
+    def smooth3():
+        return gaussian_filter(rng.uniform(0.0, 1.0, size=(n, n, n)), sigma, mode="reflect", truncate=4.0)
+    t = smooth3()
+    t = (t - t.min()) / max(t.max() - t.min(), 1e-300)
+    theta = 2.0 * np.pi * t
+    lam = np.stack([0.05 + smooth3() for _ in range(k)], axis=-1)                  # [n, n, n, k]
+    R = _rot_z(theta, k)                                                            # [n, n, n, k, k]
+    M = np.einsum("zjiab,zjib,zjicb->zjiac", R, lam, R)
+    M = M / np.trace(M, axis1=-2, axis2=-1).sum()
+    return np.ascontiguousarray(M.reshape(n, n, n, k * k).transpose(3, 0, 1, 2))
+
+
+def tensor_field_pair3(n: int = 32, k: int = 3, seed: int = 1009):
+    """[k*k, n, n, n] symmetric positive definite fields (the 2-D recipe on a volume,
+    smoothing sigma max(1, n/12) cells), total trace 1 each."""
+    rng = np.random.default_rng(seed)
+    sigma = max(1.0, n / 12.0)
+    return _tensor_field3(rng, n, k, sigma), _tensor_field3(rng, n, k, sigma)
 
 
 def random_L(k: int = 3, N: int = 3, seed: int = 1003):
