@@ -352,6 +352,26 @@ def extra_volume(dev, peak, iters=500):
                          tma_form=bool(r["variant"]), blocks=r["blocks"],
                          note="blob volumes seed 1008, alpha=1; checks every %d iterations included" % CHECK_EVERY)
         del d0, d1, sol
+    # matrix OMT on volumes (3-D DTI shape): 3 x 3 tensors (6 compact channels, 9 skew
+    # entries: 288 B / point) and 2 x 2 tensors (3 channels, 3 skew entries: 132 B / point)
+    for name, n, k in (("matrix_k3_128", 128, 3), ("matrix_k2_128", 128, 2)):
+        a, b = S.tensor_field_pair3(n, k, seed=1009)
+        L = S.random_L(k, 3, seed=1009)
+        d0 = torch.from_numpy(a.astype(np.float32)).to(dev)
+        d1 = torch.from_numpy(b.astype(np.float32)).to(dev)
+        V.momt_solve3d(d0, d1, L, 1.0, max_iters=20, check_every=20)
+        it_req = iters // 2
+        sol, ms = _gpu_ms(lambda: V.momt_solve3d(d0, d1, L, 1.0, max_iters=it_req, check_every=CHECK_EVERY))
+        r = sol.result
+        it = r["iters"]
+        K, l = k * (k + 1) // 2, 3 * k * (k - 1) // 2
+        bpg = 4 * (9 * K + 2 * l)
+        gbs = bpg * n ** 3 * it / (ms / 1e3) / 1e9
+        out[name] = dict(n=n, k=k, N=3, iters=it, us_per_iter=1e3 * ms / it, gp_it_per_s=n ** 3 * it / (ms / 1e3),
+                         algorithmic_bytes_per_gp_it=bpg, achieved_GBps=gbs, frac_of_measured_hbm=gbs / peak,
+                         tma_form=bool(r["variant"]), blocks=r["blocks"],
+                         note="tensor-field volumes seed 1009, random L seed 1009, alpha=1, ||U||_2 ||W||_1")
+        del d0, d1, sol
     return out
 
 

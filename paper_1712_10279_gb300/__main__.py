@@ -2,12 +2,14 @@
 
     python -m paper_1712_10279_gb300 --n 2048 --k 3 --iters 20 --engine stream
     python -m paper_1712_10279_gb300 --dim 3 --n 128 --k 3 --iters 100
+    python -m paper_1712_10279_gb300 --dim 3 --matrix --n 64 --k 3 --iters 100
 
 Prints the result record as one JSON line, with the last solve's time in
 milliseconds (CUDA events).  2-D densities come from
 ``synthetic.color_image_pair`` (Gaussian-filtered noise plus rectangles), 3-D
 ones from ``synthetic.blob_pair3``; the channel graph is the complete graph on
-k nodes.  Useful for profiling one engine on one size.
+k nodes.  --matrix solves matrix OMT instead (k x k tensor fields from
+``synthetic.tensor_field_pair(3)``, N = 3 random L).  Useful for profiling one engine on one size.
 """
 from __future__ import annotations
 
@@ -20,6 +22,7 @@ import numpy as np
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_1712_10279_gb300")
     ap.add_argument("--dim", type=int, default=2, choices=[2, 3])
+    ap.add_argument("--matrix", action="store_true", help="matrix OMT (k x k tensor fields, N = 3)")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--alpha", type=float, default=1.0)
@@ -33,10 +36,14 @@ def main(argv=None):
     args = ap.parse_args(argv)
 
     import torch
-    from . import solve, solve3d
+    from . import momt_solve, momt_solve3d, solve, solve3d
     from . import synthetic as S
 
-    if args.dim == 3:
+    if args.matrix:
+        gen = S.tensor_field_pair3 if args.dim == 3 else S.tensor_field_pair
+        r0, r1 = gen(args.n, args.k, seed=args.seed)
+        L = S.random_L(args.k, 3, seed=args.seed)
+    elif args.dim == 3:
         r0, r1 = S.blob_pair3(args.n, args.k, seed=args.seed)
     else:
         r0, r1 = S.color_image_pair(args.n, args.k, seed=args.seed)
@@ -49,14 +56,19 @@ def main(argv=None):
     for _ in range(max(1, args.repeat)):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        if args.dim == 3:
+        if args.matrix and args.dim == 3:
+            sol = momt_solve3d(d0, d1, L, args.alpha, zc=args.halo, **kw)
+        elif args.matrix:
+            sol = momt_solve(d0, d1, L, args.alpha, engine=args.engine, halo=args.halo, **kw)
+        elif args.dim == 3:
             sol = solve3d(d0, d1, edges, args.alpha, zc=args.halo, **kw)
         else:
             sol = solve(d0, d1, edges, args.alpha, engine=args.engine, halo=args.halo, **kw)
         e1.record()
         e1.synchronize()
         res, ms = sol.result, e0.elapsed_time(e1)
-    print(json.dumps(dict(dim=args.dim, n=args.n, k=args.k, alpha=args.alpha, ms=ms, **res)), flush=True)
+    print(json.dumps(dict(dim=args.dim, matrix=args.matrix, n=args.n, k=args.k, alpha=args.alpha, ms=ms, **res)),
+          flush=True)
 
 
 if __name__ == "__main__":

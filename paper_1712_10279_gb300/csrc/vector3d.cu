@@ -10,7 +10,7 @@
 // neighbours, so the step marches blocks up z: u' is computed once per point,
 // the x and y components meet their neighbours through shared memory and the z
 // component is carried to the next plane.  Two forms of that step: inputs staged
-// by TMA tiles (vector3d_tma.cu; n a multiple of 4, n >= 40, k <= 4) and, for
+// by TMA tiles (vector3d_tma.cu; n a multiple of 4, n >= 40, k <= 6) and, for
 // every other case, the form below with per-thread loads.  Step rule:
 // ||grad||^2 <= 12 / h^2 in 3-D, so mu = 1/(48 tau (n-1)^2) (1/(24 tau (n-1)^2)
 // without edges) keeps the 2-D rule's share of the bound.
@@ -503,7 +503,7 @@ int solve3d_core(vomt_ctx *ctx, int n, const OpDev &g, const StepDev &s, const S
     L3 L = pick3(k, p.u_norm, p.w_norm);
     e = cudaFuncSetAttribute((const void *)L.step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "3-D step shared memory");
-    // inputs by TMA tiles where they apply (n a multiple of 4, n >= 40, k <= 4)
+    // inputs by TMA tiles where they apply (n a multiple of 4, n >= 40, k <= 6)
     Tma3Plan *tp = tma3_supported(n, k, l, p.u_norm, p.w_norm)
                        ? tma3_plan_create(n, k, l, p.u_norm, p.w_norm, so[0].phi, so[1].phi, b)
                        : nullptr;

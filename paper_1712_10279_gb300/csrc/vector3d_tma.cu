@@ -67,10 +67,12 @@ __host__ __device__ inline Stage3 stage3(int K, int l)
     return S;
 }
 
-// stages: planes z and z+1 in use, the rest in flight.  Four for k <= 3 (two
-// blocks per SM; three stages would fit three blocks per SM but measured slower,
-// the copies then land too late), three for k = 4.
-__host__ __device__ constexpr int nstages(int K) { return K <= 3 ? 4 : 3; }
+// stages: planes z and z+1 in use, the rest in flight.  Four for K <= 3 channels
+// (two blocks per SM; three stages would fit three blocks per SM but measured
+// slower, the copies then land too late), three for K = 4 (two blocks per SM),
+// four for K = 5, 6 (one block per SM: 3 x 3 matrix fields are 6 channels).
+__host__ __device__ constexpr int nstages(int K) { return K == 4 ? 3 : 4; }
+__host__ __device__ constexpr int blocks_per_sm(int K) { return K <= 4 ? 2 : 1; }
 
 __host__ __device__ inline int smem3(int K, int l)
 {
@@ -115,7 +117,7 @@ __device__ __forceinline__ bool wait_phase(uint32_t mb, uint32_t parity, uint32_
 }
 
 template <int K, int UN, int WN>
-__global__ void __launch_bounds__(MT, 2) k_step3t(const __grid_constant__ Maps3 maps, const float *__restrict__ in,
+__global__ void __launch_bounds__(MT, blocks_per_sm(K)) k_step3t(const __grid_constant__ Maps3 maps, const float *__restrict__ in,
                                                  S3Out out, OpDev g, StepDev s, DevStatus *st, int zc)
 {
     if (st->stop) return;
@@ -327,7 +329,7 @@ using Kern3 = void (*)(const Maps3, const float *, S3Out, OpDev, StepDev, DevSta
 template <int K>
 Kern3 pick_norms3t(int un, int wn)
 {
-    if constexpr (K == 3) {                    // nuclear norms: compact 2 x 2 matrices
+    if constexpr (K == 3 || K == 6) {          // nuclear norms: compact 2 x 2 and 3 x 3 matrices
         if (un == VOMT_U_NUC)
             return wn == VOMT_W_L1 ? k_step3t<K, 3, 0> : (wn == VOMT_W_L2 ? k_step3t<K, 3, 1> : k_step3t<K, 3, 2>);
         if (wn == VOMT_W_NUC) return un == VOMT_U_L2 ? k_step3t<K, 1, 2> : k_step3t<K, 2, 2>;
@@ -340,12 +342,14 @@ Kern3 pick_norms3t(int un, int wn)
 Kern3 pick3t(int k, int un, int wn)
 {
     if (un < 0 || un > 3 || wn < 0 || wn > 2) return nullptr;
-    if ((un == VOMT_U_NUC || wn == VOMT_W_NUC) && k != 3) return nullptr;
+    if ((un == VOMT_U_NUC || wn == VOMT_W_NUC) && k != 3 && k != 6) return nullptr;
     switch (k) {
         case 1: return pick_norms3t<1>(un, wn);
         case 2: return pick_norms3t<2>(un, wn);
         case 3: return pick_norms3t<3>(un, wn);
         case 4: return pick_norms3t<4>(un, wn);
+        case 5: return pick_norms3t<5>(un, wn);
+        case 6: return pick_norms3t<6>(un, wn);
         default: return nullptr;
     }
 }
@@ -393,7 +397,8 @@ bool tma3_supported(int n, int k, int l, int un, int wn)
 {
     if (n < BXH || n % 4 != 0 || n > 1024) return false;
     if (!pick3t(k, un, wn)) return false;
-    if (smem3(k, l) > 110 * 1024) return false;        // two blocks per SM at least
+    // the ring fits blocks_per_sm blocks of one SM's 228 KB (1 KB reserved per block)
+    if (smem3(k, l) > (k <= 4 ? 110 : 224) * 1024) return false;
     return encode_fn3() != nullptr;
 }
 

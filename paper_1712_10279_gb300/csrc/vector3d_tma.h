@@ -9,10 +9,10 @@ namespace vomt {
 struct Tma3Plan;
 
 // True when the TMA form applies: 40 <= n <= 1024 with n a multiple of 4
-// (16-byte strides), k <= 4 channels, norms u in {L12, L2, L1} and w in
-// {L1, L2} (and the nuclear norms for the compact 2 x 2 matrices, k = 3
-// channels), the stage ring fits two blocks per SM, and the driver provides
-// cuTensorMapEncodeTiled.
+// (16-byte strides), k <= 6 channels, norms u in {L12, L2, L1} and w in
+// {L1, L2} (and the nuclear norms for compact 2 x 2 and 3 x 3 matrices, k = 3
+// and 6 channels), the stage ring fits the SM (two blocks for k <= 4, one for
+// k = 5, 6), and the driver provides cuTensorMapEncodeTiled.
 bool tma3_supported(int n, int k, int l, int un, int wn);
 
 // Tensor maps over the two ping-pong states (volumes phi[k], u_x[k], u_y[k],

@@ -93,16 +93,18 @@ def test_fixed_iterations_match_oracle(n, k, norms):
     assert r["rel_res"] == pytest.approx(o["metrics"]["rel_res"], rel=1e-2)
 
 
-@pytest.mark.parametrize("n,k,zc", [(40, 3, 0), (44, 3, 5), (44, 1, 1), (48, 2, 7), (44, 4, 0), (52, 3, 52)])
+@pytest.mark.parametrize("n,k,zc", [(40, 3, 0), (44, 3, 5), (44, 1, 1), (48, 2, 7), (44, 4, 0), (52, 3, 52),
+                                    (44, 5, 0), (40, 6, 3)])
 @pytest.mark.parametrize("norms", NORMS)
 def test_tma_form_matches_oracle(n, k, zc, norms):
-    """The TMA form (n a multiple of 4, n >= 40, k <= 4): ragged 32 x 8 tiles, z chunks of
+    """The TMA form (n a multiple of 4, n >= 40, k <= 6; k = 6 with the complete graph's 15
+    edges does not fit and takes a path graph here): ragged 32 x 8 tiles, z chunks of
     1 (every chunk ends on a phi-only plane), 5, 7, the default and the whole column, so the
     stage ring wraps at every offset."""
     un, wn = norms
     if k == 1 and wn != V.W_L1:
         pytest.skip("no edges at k = 1")
-    edges = S.complete_graph(k)
+    edges = S.complete_graph(k) if k <= 5 else [(c, c + 1) for c in range(k - 1)]
     r0, r1 = _unit_cells(*S.blob_pair3(n, k, seed=60 + n + k))
     iters = 100
     g = _gpu(r0, r1, edges, 0.7, u_norm=un, w_norm=wn, max_iters=iters, check_every=50, zc=zc)
