@@ -73,10 +73,18 @@ __host__ __device__ inline Stage3 stage3(int K, int l)
 // four for K = 5, 6 (one block per SM: 3 x 3 matrix fields are 6 channels).
 __host__ __device__ constexpr int nstages(int K) { return K == 4 ? 3 : 4; }
 __host__ __device__ constexpr int blocks_per_sm(int K) { return K <= 4 ? 2 : 1; }
+// double-buffered exchange arrays (one barrier per plane) where they fit: not at K = 4,
+// whose two blocks per SM leave no room
+__host__ __device__ constexpr bool dbuf(int K) { return K != 4; }
+// the tile's MT threads plus two halo warps: the y0-1 row (32 lanes) and the x0-1
+// column (MY lanes) of 2u' - u, computed beside the tile instead of by tile warps
+constexpr int HT = 64, NT3 = MT + HT;
+
+__host__ __device__ inline int sb_floats(int K) { return K * MY * (MX + 1) + K * (MY + 1) * MX; }
 
 __host__ __device__ inline int smem3(int K, int l)
 {
-    return nstages(K) * stage3(K, l).size + 4 * (K * MY * (MX + 1) + K * (MY + 1) * MX);
+    return nstages(K) * stage3(K, l).size + 4 * sb_floats(K) * (dbuf(K) ? 2 : 1);
 }
 
 struct Maps3 {
@@ -117,7 +125,7 @@ __device__ __forceinline__ bool wait_phase(uint32_t mb, uint32_t parity, uint32_
 }
 
 template <int K, int UN, int WN>
-__global__ void __launch_bounds__(MT, blocks_per_sm(K)) k_step3t(const __grid_constant__ Maps3 maps, const float *__restrict__ in,
+__global__ void __launch_bounds__(NT3, blocks_per_sm(K)) k_step3t(const __grid_constant__ Maps3 maps, const float *__restrict__ in,
                                                  S3Out out, OpDev g, StepDev s, DevStatus *st, int zc)
 {
     if (st->stop) return;
@@ -128,14 +136,15 @@ __global__ void __launch_bounds__(MT, blocks_per_sm(K)) k_step3t(const __grid_co
     __shared__ int abort_flag;
     const int n = s.n, l = g.l;
     const Stage3 SL = stage3(K, l);
-    float *sbx = (float *)(smem + NS * SL.size);
-    float *sby = sbx + K * MY * (MX + 1);
+    float *const sb0 = (float *)(smem + NS * SL.size);
     const size_t m = (size_t)n * n * n, nn = (size_t)n * n;
     const int tid = threadIdx.x, tx = tid % MX, ty = tid / MX;
+    const bool tile = tid < MT;                 // else a halo thread: ht < MX row, < MX + MY column
+    const int ht = tid - MT;
     const int x0 = blockIdx.x * MX, y0 = blockIdx.y * MY;
     const int z0 = blockIdx.z * zc, z1 = min(n, z0 + zc), zlast = min(z1, n - 1);
     const int x = x0 + tx, y = y0 + ty;
-    const bool inb = x < n && y < n;
+    const bool inb = tile && x < n && y < n;
     const bool hx = x < n - 1, hy = y < n - 1, lx = x > 0, ly = y > 0;
     const float mi = s.mu * s.ih;
     if (tid == 0) {
@@ -195,6 +204,8 @@ __global__ void __launch_bounds__(MT, blocks_per_sm(K)) k_step3t(const __grid_co
     const int oT = ty * MX + tx;                // (x, y) in the w and b boxes
     for (int z = z0; z < z1; ++z) {
         const bool hz = z < n - 1, lz = z > 0;
+        float *sbx = sb0 + (dbuf(K) ? (z & 1) * sb_floats(K) : 0);
+        float *sby = sbx + K * MY * (MX + 1);
         bool ok = wait_plane(z, kSpins);
         if (ok && hz) ok = wait_plane(z + 1, kSpins);
         if (!ok) abort_flag = 1;
@@ -204,8 +215,10 @@ __global__ void __launch_bounds__(MT, blocks_per_sm(K)) k_step3t(const __grid_co
         const float *Ux = (const float *)(S0 + SL.ux), *Uy = (const float *)(S0 + SL.uy);
         const float *Uz = (const float *)(S0 + SL.uz);
         const float *W0 = (const float *)(S0 + SL.w), *B0 = (const float *)(S0 + SL.b);
-        // own u' and 2u' - u
+        // tile threads: own u', 2u' - u and w'; halo threads: the upwind row and column
         float pc[K], vx[K], vy[K], vz[K], ux0[K], uy0[K], uz0[K], bb[K];
+        float w0[LK], wx[LK];
+        if (tile) {
 #pragma unroll
         for (int c = 0; c < K; ++c) {
             const float *P = P0 + c * PL + oP;
@@ -224,17 +237,32 @@ __global__ void __launch_bounds__(MT, blocks_per_sm(K)) k_step3t(const __grid_co
             sbx[(c * MY + ty) * (MX + 1) + tx + 1] = 2.0f * vx[c] - ux0[c];
             sby[(c * (MY + 1) + ty + 1) * MX + tx] = 2.0f * vy[c] - uy0[c];
         }
-        // the tile's y0-1 row (threads 0..MX-1) and x0-1 column (threads MX..MX+MY-1)
-        {
+        // w' at the point
+#pragma unroll
+        for (int e = 0; e < LK; ++e) {
+            if (e < l) {
+                w0[e] = W0[e * WL + oT];
+                float ge = 0.0f;
+#pragma unroll
+                for (int c = 0; c < K; ++c) ge += g.G[e][c] * pc[c];
+                wx[e] = w0[e] + s.nu * ge;
+            } else {
+                w0[e] = 0.0f;
+                wx[e] = 0.0f;
+            }
+        }
+        shrink_w3<LK, WN>(wx, l, s.alpha * s.nu, g.we);
+        } else {
+            // the tile's y0-1 row (halo lanes 0..MX-1) and x0-1 column (lanes MX..MX+MY-1)
             int hxp = -1, hyp = -1, o = 0, ou = 0;
-            if (tid < MX) {
-                if (y0 > 0 && x0 + tid < n) { hxp = x0 + tid; hyp = y0 - 1; o = tid + 4; ou = tid + 4; }
-            } else if (tid < MX + MY) {
-                if (x0 > 0 && y0 + tid - MX < n) {
+            if (ht < MX) {
+                if (y0 > 0 && x0 + ht < n) { hxp = x0 + ht; hyp = y0 - 1; o = ht + 4; ou = ht + 4; }
+            } else if (ht < MX + MY) {
+                if (x0 > 0 && y0 + ht - MX < n) {
                     hxp = x0 - 1;
-                    hyp = y0 + tid - MX;
-                    o = (tid - MX + 1) * BXH + 3;
-                    ou = (tid - MX + 1) * BXU + 3;
+                    hyp = y0 + ht - MX;
+                    o = (ht - MX + 1) * BXH + 3;
+                    ou = (ht - MX + 1) * BXU + 3;
                 }
             }
             if (hxp >= 0) {
@@ -250,31 +278,15 @@ __global__ void __launch_bounds__(MT, blocks_per_sm(K)) k_step3t(const __grid_co
                     az[c] = upre(Uz[c * UL + ou], P1[c * PL + o], P[0], hz, mi);
                 }
                 shrink_u3<K, UN>(ax, ay, az, s.mu, g.wc);
-                if (tid < MX) {
+                if (ht < MX) {
 #pragma unroll
-                    for (int c = 0; c < K; ++c) sby[(c * (MY + 1)) * MX + tid] = 2.0f * ay[c] - a0y[c];
+                    for (int c = 0; c < K; ++c) sby[(c * (MY + 1)) * MX + ht] = 2.0f * ay[c] - a0y[c];
                 } else {
 #pragma unroll
-                    for (int c = 0; c < K; ++c) sbx[(c * MY + (tid - MX)) * (MX + 1)] = 2.0f * ax[c] - a0x[c];
+                    for (int c = 0; c < K; ++c) sbx[(c * MY + (ht - MX)) * (MX + 1)] = 2.0f * ax[c] - a0x[c];
                 }
             }
         }
-        // w' at the point
-        float w0[LK], wx[LK];
-#pragma unroll
-        for (int e = 0; e < LK; ++e) {
-            if (e < l) {
-                w0[e] = W0[e * WL + oT];
-                float ge = 0.0f;
-#pragma unroll
-                for (int c = 0; c < K; ++c) ge += g.G[e][c] * pc[c];
-                wx[e] = w0[e] + s.nu * ge;
-            } else {
-                w0[e] = 0.0f;
-                wx[e] = 0.0f;
-            }
-        }
-        shrink_w3<LK, WN>(wx, l, s.alpha * s.nu, g.we);
         __syncthreads();
         if (abort_flag) {
             if (tid == 0) {
@@ -289,6 +301,7 @@ __global__ void __launch_bounds__(MT, blocks_per_sm(K)) k_step3t(const __grid_co
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue(z + NS - 1);
         }
+        if (tile) {
         // phi' = phi + tau (div ubar + div_G wbar + rho1 - rho0)
         float r[K];
 #pragma unroll
@@ -320,7 +333,9 @@ __global__ void __launch_bounds__(MT, blocks_per_sm(K)) k_step3t(const __grid_co
             for (int e = 0; e < LK; ++e)
                 if (e < l) out.w[e * m + p] = wx[e];
         }
-        __syncthreads();
+        }
+        // with one exchange buffer the next plane's writes wait for this plane's reads
+        if constexpr (!dbuf(K)) __syncthreads();
     }
 }
 
@@ -436,7 +451,7 @@ void tma3_launch_step(const Tma3Plan *pl, int in_state, S3Out out, const OpDev &
 {
     const int n = s.n;
     const dim3 grd((n + MX - 1) / MX, (n + MY - 1) / MY, (n + zc - 1) / zc);
-    pl->kern<<<grd, MT, pl->smem, stream>>>(pl->maps[in_state], pl->in[in_state], out, g, s, st, zc);
+    pl->kern<<<grd, NT3, pl->smem, stream>>>(pl->maps[in_state], pl->in[in_state], out, g, s, st, zc);
 }
 
 }  // namespace vomt
