@@ -57,6 +57,11 @@ namespace res {
 using namespace dev;
 
 constexpr int RES_THREADS = 512;      // most threads a block runs
+// Six and more channels: at most 384 threads (12 warps, three per SM
+// sub-partition), so that a thread may hold 170 registers; with 13 or more warps
+// some sub-partition holds four and a thread gets 128, under which their
+// per-point state spills.
+__host__ __device__ constexpr int res_threads(int K) { return K >= 6 ? 384 : RES_THREADS; }
 constexpr int HMAX = 16;              // widest halo ring
 
 template <int K>
@@ -884,7 +889,7 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
 
 // One problem: the grid is its tiles.
 template <int K, int P, int NM>
-__global__ void __launch_bounds__(RES_THREADS, 1) k_resident(const __grid_constant__ ResArgs a)
+__global__ void __launch_bounds__(res_threads(K), 1) k_resident(const __grid_constant__ ResArgs a)
 {
     resident_body<K, P, NM>(a, (int)blockIdx.x, (int)gridDim.x, 0u);
 }
@@ -903,7 +908,7 @@ struct MultiArgs {
 };
 
 template <int K, int P, int NM>
-__global__ void __launch_bounds__(RES_THREADS, 1) k_resident_multi(const __grid_constant__ MultiArgs m)
+__global__ void __launch_bounds__(res_threads(K), 1) k_resident_multi(const __grid_constant__ MultiArgs m)
 {
     __shared__ __align__(16) ResArgs sa;
     const int g = (int)blockIdx.x / m.T, t = (int)blockIdx.x % m.T;

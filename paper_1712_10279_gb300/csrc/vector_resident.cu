@@ -47,7 +47,6 @@ namespace {
 
 using res::RES_THREADS;
 using res::HMAX;
-constexpr int RES_P4_POINTS = 1024;   // extended tiles above this size: four points per thread
 constexpr int RES_MAX_POINTS = 2048;  // largest extended tile (four points per thread, 512 threads)
 constexpr int TMAX = 64;              // longest tile side
 constexpr int SMEM_MAX = 227 * 1024;
@@ -57,22 +56,28 @@ constexpr int SMEM_MAX = 227 * 1024;
 // step updates (arithmetic, shared-memory traffic and the two barriers of a
 // step at 16 warps per SM), 3.1 us per halo exchange (one L2 round trip plus
 // the tagged stores and polls), and 30% more per point when a thread owns
-// four points (register spills; extended tiles above RES_P4_POINTS).
-double plan_cost(int TX, int TY, int H, int G)
+// four points (register spills).  With six and more channels (`heavy`) two
+// points per thread already spill: 30% more there, 60% at four.
+double plan_cost(int TX, int TY, int H, int G, int rt = RES_THREADS, bool heavy = false)
 {
     const double per_pt = 3.5;
-    if (G == 1) return per_pt * TX * TY * (TX * TY > RES_P4_POINTS ? 1.3 : 1.0);
+    auto spill = [&](int ext) {
+        if (ext <= (heavy ? rt : 2 * rt)) return 1.0;
+        return heavy && ext > 2 * rt ? 1.6 : 1.3;
+    };
+    if (G == 1) return per_pt * TX * TY * spill(TX * TY);
     double pts = 0.0;
     for (int s = 1; s <= H; ++s) pts += (double)(TX + 2 * (H - s) + 1) * (TY + 2 * (H - s) + 1);
     const int ext = (TX + 2 * H) * (TY + 2 * H);
-    return per_pt * (ext > RES_P4_POINTS ? 1.3 : 1.0) * pts / H + 3100.0 / H;
+    return per_pt * spill(ext) * pts / H + 3100.0 / H;
 }
 
 }  // namespace
 
 // Tile plan.  Tiles of at most 64 x 64 points, at most `max_blocks` of them; the
 // ring width H is at most the narrowest tile side; the extended tile
-// (TX + 2H) x (TY + 2H) holds at most RES_MAX_POINTS points and its shared-memory
+// (TX + 2H) x (TY + 2H) holds at most four points per thread of res_threads(k)
+// (2048 points; 1536 for six and more channels) and its shared-memory
 // arrays fit one SM.
 // Among those, the plan with the smallest estimated time per iteration
 // (plan_cost) wins.  `force_H` > 0 pins the ring width.
@@ -81,6 +86,8 @@ bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out)
     auto smem_ok = [&](int EW, int EH, int G) {
         return res::smem_layout(k, res::row_stride(EW), EH, G).total <= SMEM_MAX;
     };
+    const int RT = res::res_threads(k), max_points = 4 * RT;
+    const bool heavy = k >= 6;
     double best = -1.0;
     for (int Gx = 1; Gx <= n && Gx <= max_blocks; ++Gx) {
         const int TX = (n + Gx - 1) / Gx, TXmin = n / Gx;
@@ -90,8 +97,8 @@ bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out)
             if (TY > TMAX) continue;
             const int G = Gx * Gy;
             if (G == 1) {
-                if (TX * TY > RES_MAX_POINTS || !smem_ok(TX, TY, 1)) continue;
-                const double cost = plan_cost(TX, TY, 0, 1);
+                if (TX * TY > max_points || !smem_ok(TX, TY, 1)) continue;
+                const double cost = plan_cost(TX, TY, 0, 1, RT, heavy);
                 if (best < 0 || cost < best) {
                     best = cost;
                     *out = ResidentPlan{Gx, Gy, TX, TY, 0, 0, 0, cost};
@@ -102,8 +109,8 @@ bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out)
                 if (force_H > 0 && H != force_H) continue;
                 if (H > TXmin || H > TYmin) break;
                 const int EW = TX + 2 * H, EH = TY + 2 * H;
-                if (EW * EH > RES_MAX_POINTS || !smem_ok(EW, EH, G)) break;
-                const double cost = plan_cost(TX, TY, H, G);
+                if (EW * EH > max_points || !smem_ok(EW, EH, G)) break;
+                const double cost = plan_cost(TX, TY, H, G, RT, heavy);
                 if (best < 0 || cost < best) {
                     best = cost;
                     *out = ResidentPlan{Gx, Gy, TX, TY, H, 0, 0, cost};
@@ -113,10 +120,10 @@ bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out)
     }
     if (best < 0) return false;
     const int EW = out->TXm + 2 * out->H, EH = out->TYm + 2 * out->H;
-    // P points per thread, the fewest that fit 512 threads, spread evenly over
+    // P points per thread, the fewest that fit RT threads, spread evenly over
     // round_up(ext / P, 32) threads.
     const int ext = EW * EH;
-    out->P = ext <= RES_THREADS ? 1 : (ext <= 2 * RES_THREADS ? 2 : 4);
+    out->P = ext <= RT ? 1 : (ext <= 2 * RT ? 2 : 4);
     out->threads = (((ext + out->P - 1) / out->P + 31) / 32) * 32;
     return true;
 }
