@@ -356,9 +356,13 @@ struct TmaPlan {
 bool tma_step_supported(int n, int k, int l, int un, int wn)
 {
     if (n < 64 || n % 4 != 0 || n >= (1 << 20) || k > 4) return false;
-    // below about 64 MB of iterate the state stays in L2 and the plain step, with
-    // four times the blocks, is as fast or faster
-    if ((double)n * n * (7 * k + 2 * l) * 4.0 < 64.0 * 1024 * 1024) return false;
+    // Below about 16 MB of iterate the plain step (four times the blocks) is as fast;
+    // so it is while the 64 x 16 tiles fill fewer than two blocks on each of the 152
+    // SMs (512^2 at k = 3: 256 tiles).  Measured on GB300, 3000 iterations: 1024^2 at
+    // k = 1 10.7 -> 10.0 us, 768^2 at k = 3 15.2 -> 14.2 us with TMA; 512^2 at k = 3
+    // 7.9 us either way.
+    if ((double)n * n * (7 * k + 2 * l) * 4.0 < 16.0 * 1024 * 1024) return false;
+    if (((n + TX - 1) / TX) * ((n + TY - 1) / TY) < 2 * 152) return false;
     if (tma_smem(k, l).total > 110 * 1024) return false;     // two blocks per SM at least
     if (!pick_tma(k, un, wn)) return false;
     return encode_fn() != nullptr;

@@ -8,8 +8,8 @@ namespace vomt {
 struct TmaPlan;
 
 // True when the TMA step applies: n a multiple of 4 (16-byte strides), k <= 4,
-// at least 64 MB of iterate (smaller states stay in L2, where the plain step is
-// as fast), the tile's shared memory fits two blocks per SM, and the driver
+// at least 16 MB of iterate and 304 tiles (below either the plain step is as
+// fast), the tile's shared memory fits two blocks per SM, and the driver
 // provides cuTensorMapEncodeTiled.
 bool tma_step_supported(int n, int k, int l, int un, int wn);
 

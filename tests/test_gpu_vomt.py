@@ -222,10 +222,12 @@ def test_resident_halo_widths_match_oracle(halo, n, k):
     np.testing.assert_allclose(h[:, 4], ref["history"][:, 4], rtol=5e-2)
 
 
-@pytest.mark.parametrize("n,k,edges", [(1024, 3, K3), (1028, 3, K3), (1436, 2, [(0, 1)]), (2048, 1, [])])
+@pytest.mark.parametrize("n,k,edges", [(1024, 3, K3), (1028, 3, K3), (1436, 2, [(0, 1)]), (2048, 1, []),
+                                       (1024, 1, []), (772, 3, K3)])
 def test_tma_streaming_step_matches_oracle(n, k, edges):
-    """Grids whose iterate exceeds 64 MB with n a multiple of 4 take the TMA form of the
-    streaming step (64 x 16 tiles; 1028 and 1436 leave ragged tiles in x and y).  Cell masses
+    """Grids whose iterate is at least 16 MB over at least 304 tiles, with n a multiple of 4,
+    take the TMA form of the streaming step (64 x 16 tiles; 1028, 1436 and 772 leave ragged
+    tiles in x and y).  Cell masses
     of order one (equal totals), so that the flux moves within the few iterations run: a few
     iterations from zero, then one from the GPU state, against the FP64 oracle."""
     rng = np.random.default_rng(n)
