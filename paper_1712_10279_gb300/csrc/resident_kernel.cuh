@@ -57,11 +57,11 @@ namespace res {
 using namespace dev;
 
 constexpr int RES_THREADS = 512;      // most threads a block runs
-// Six and more channels: at most 384 threads (12 warps, three per SM
+// Five and more channels: at most 384 threads (12 warps, three per SM
 // sub-partition), so that a thread may hold 170 registers; with 13 or more warps
 // some sub-partition holds four and a thread gets 128, under which their
 // per-point state spills.
-__host__ __device__ constexpr int res_threads(int K) { return K >= 6 ? 384 : RES_THREADS; }
+__host__ __device__ constexpr int res_threads(int K) { return K >= 5 ? 384 : RES_THREADS; }
 constexpr int HMAX = 16;              // widest halo ring
 
 template <int K>

@@ -47,7 +47,6 @@ namespace {
 
 using res::RES_THREADS;
 using res::HMAX;
-constexpr int RES_MAX_POINTS = 2048;  // largest extended tile (four points per thread, 512 threads)
 constexpr int TMAX = 64;              // longest tile side
 constexpr int SMEM_MAX = 227 * 1024;
 
@@ -56,8 +55,8 @@ constexpr int SMEM_MAX = 227 * 1024;
 // step updates (arithmetic, shared-memory traffic and the two barriers of a
 // step at 16 warps per SM), 3.1 us per halo exchange (one L2 round trip plus
 // the tagged stores and polls), and 30% more per point when a thread owns
-// four points (register spills).  With six and more channels (`heavy`) two
-// points per thread already spill: 30% more there, 60% at four.
+// four points (register spills).  With five and more channels (`heavy`, 384
+// threads) two points per thread already spill: 30% more there, 60% at four.
 double plan_cost(int TX, int TY, int H, int G, int rt = RES_THREADS, bool heavy = false)
 {
     const double per_pt = 3.5;
@@ -77,7 +76,7 @@ double plan_cost(int TX, int TY, int H, int G, int rt = RES_THREADS, bool heavy 
 // Tile plan.  Tiles of at most 64 x 64 points, at most `max_blocks` of them; the
 // ring width H is at most the narrowest tile side; the extended tile
 // (TX + 2H) x (TY + 2H) holds at most four points per thread of res_threads(k)
-// (2048 points; 1536 for six and more channels) and its shared-memory
+// (2048 points; 1536 for five and more channels) and its shared-memory
 // arrays fit one SM.
 // Among those, the plan with the smallest estimated time per iteration
 // (plan_cost) wins.  `force_H` > 0 pins the ring width.
@@ -87,7 +86,7 @@ bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out)
         return res::smem_layout(k, res::row_stride(EW), EH, G).total <= SMEM_MAX;
     };
     const int RT = res::res_threads(k), max_points = 4 * RT;
-    const bool heavy = k >= 6;
+    const bool heavy = RT < RES_THREADS;
     double best = -1.0;
     for (int Gx = 1; Gx <= n && Gx <= max_blocks; ++Gx) {
         const int TX = (n + Gx - 1) / Gx, TXmin = n / Gx;
@@ -138,6 +137,8 @@ bool resident_plan_wave(int n, int k, int count, int max_blocks, ResidentPlan *o
     auto smem_ok = [&](int EW, int EH, int G) {
         return res::smem_layout(k, res::row_stride(EW), EH, G).total <= SMEM_MAX - res::MULTI_STATIC_SMEM;
     };
+    const int RT = res::res_threads(k), max_points = 4 * RT;
+    const bool heavy = res::res_threads(k) < RES_THREADS;
     double best = -1.0;
     for (int Gx = 1; Gx <= n && Gx <= max_blocks; ++Gx) {
         const int TX = (n + Gx - 1) / Gx, TXmin = n / Gx;
@@ -149,8 +150,8 @@ bool resident_plan_wave(int n, int k, int count, int max_blocks, ResidentPlan *o
             const int side = std::min(count, max_blocks / G);
             const double rounds = (double)((count + side - 1) / side);
             if (G == 1) {
-                if (TX * TY > RES_MAX_POINTS || !smem_ok(TX, TY, 1)) continue;
-                const double cost = rounds * plan_cost(TX, TY, 0, 1);
+                if (TX * TY > max_points || !smem_ok(TX, TY, 1)) continue;
+                const double cost = rounds * plan_cost(TX, TY, 0, 1, RT, heavy);
                 if (best < 0 || cost < best) {
                     best = cost;
                     *out = ResidentPlan{Gx, Gy, TX, TY, 0, 0, 0, cost};
@@ -160,8 +161,8 @@ bool resident_plan_wave(int n, int k, int count, int max_blocks, ResidentPlan *o
             for (int H = 1; H <= HMAX; ++H) {
                 if (H > TXmin || H > TYmin) break;
                 const int EW = TX + 2 * H, EH = TY + 2 * H;
-                if (EW * EH > RES_MAX_POINTS || !smem_ok(EW, EH, G)) break;
-                const double cost = rounds * plan_cost(TX, TY, H, G);
+                if (EW * EH > max_points || !smem_ok(EW, EH, G)) break;
+                const double cost = rounds * plan_cost(TX, TY, H, G, RT, heavy);
                 if (best < 0 || cost < best) {
                     best = cost;
                     *out = ResidentPlan{Gx, Gy, TX, TY, H, 0, 0, cost};
@@ -171,7 +172,7 @@ bool resident_plan_wave(int n, int k, int count, int max_blocks, ResidentPlan *o
     }
     if (best < 0) return false;
     const int ext = (out->TXm + 2 * out->H) * (out->TYm + 2 * out->H);
-    out->P = ext <= 2 * RES_THREADS ? 2 : 4;
+    out->P = ext <= 2 * RT ? 2 : 4;
     out->threads = (((ext + out->P - 1) / out->P + 31) / 32) * 32;
     return true;
 }
