@@ -88,6 +88,10 @@ def _load():
                                          p, p, p, p, p, p, p, p, p, p, p]),
             "orc_momt3_solve": (i, [i, i, i, p, p, p, d, d, d, d, i, i, i, i, d, d,
                                     p, p, p, p, p, p, p, i]),
+            "orc_zgrad_L_point": (None, [i, i, p, p, p]),
+            "orc_zdiv_L_point": (None, [i, i, p, p, p]),
+            "orc_zquantum_lmax": (d, [i, i, p]),
+            "orc_zmomt_solve": (i, [i, i, i, p, p, p, d, d, d, d, i, i, d, d, p, p, p, p, p, p, i]),
             "orc_spectral_norm": (d, [i, p]),
             "orc_shrink_nuc": (None, [i, p, d, p]),
             "orc_vomt_unrolled_grad": (d, [i, i, i, p, p, p, p, p, d, d, d, d, i, i, p, p, p]),
@@ -508,6 +512,71 @@ def momt3_solve(Lam0, Lam1, L, alpha=1.0, tau=None, mu=None, nu=None, u_norm=U_L
                                  _ptr(met), _ptr(hist), nchk)
     out = dict(Ux=Ux, Uy=Uy, Uz=Uz, W=W, Phi=Phi, iters=it, mu=mu, nu=nu, tau=tau,
                metrics=dict(zip(MET_NAMES, met)))
+    if history:
+        out["history"] = hist[hist[:, 6] > 0]
+    return out
+
+
+# ---------------------------------------------------------------- complex Hermitian matrix OMT
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def zgrad_L_point(X, L):
+    """[L_s X - X L_s]_s for one complex k x k X; L: [N, k, k] complex."""
+    X, L = _c128(X), _c128(L)
+    N, k = L.shape[0], L.shape[1]
+    Z = np.zeros((N, k, k), np.complex128)
+    _load().orc_zgrad_L_point(k, N, _ptr(L), _ptr(X), _ptr(Z))
+    return Z
+
+
+def zdiv_L_point(Z, L):
+    """sum_s (-L_s Z_s + Z_s L_s) for one point."""
+    Z, L = _c128(Z), _c128(L)
+    N, k = L.shape[0], L.shape[1]
+    Y = np.zeros((k, k), np.complex128)
+    _load().orc_zdiv_L_point(k, N, _ptr(L), _ptr(Z), _ptr(Y))
+    return Y
+
+
+def zquantum_lmax(L) -> float:
+    L = _c128(L)
+    return float(_load().orc_zquantum_lmax(L.shape[1], L.shape[0], _ptr(L)))
+
+
+def zmomt_solve(Lam0, Lam1, L, alpha=1.0, tau=None, mu=None, nu=None, max_iters=2000, check_every=100,
+                tol_gap=0.0, tol_res=0.0, init=None, history=False):
+    """The M-OMT iteration of Section 7.3 on complex Hermitian densities (Section 4's complex
+    setting), Frobenius norms ||U||_2 and ||W||_2, FP64.
+
+    Lam0, Lam1: [k*k, n, n] complex Hermitian matrices per cell.  L: [N, k, k] complex
+    Hermitian.  mu defaults to 1/(32 tau (n-1)^2), nu to 1/(4 tau lambda_max(-Delta_L)).
+    """
+    Lam0, Lam1, L = _c128(Lam0), _c128(Lam1), _c128(L)
+    N, k = L.shape[0], L.shape[1]
+    n = Lam0.shape[-1]
+    if k > 8 or N * k * k > 512:
+        raise ValueError("k <= 8 and N k^2 <= 512")
+    if tau is None:
+        tau = default_tau_matrix(n)
+    if mu is None:
+        mu = 1.0 / (32.0 * tau * (n - 1) ** 2)
+    if nu is None:
+        nu = 1.0 / (4.0 * tau * zquantum_lmax(L))
+    kk = k * k
+    if init is None:
+        Ux = np.zeros((kk, n, n), np.complex128); Uy = np.zeros((kk, n, n), np.complex128)
+        W = np.zeros((N * kk, n, n), np.complex128); Phi = np.zeros((kk, n, n), np.complex128)
+    else:
+        Ux, Uy, W, Phi = (np.array(init[x], dtype=np.complex128, copy=True) for x in ("Ux", "Uy", "W", "Phi"))
+    nchk = max_iters // max(check_every, 1) + 2
+    hist = np.zeros((nchk, NMET))
+    met = np.zeros(NMET)
+    it = _load().orc_zmomt_solve(n, k, N, _ptr(L), _ptr(Lam0), _ptr(Lam1), float(alpha), float(tau), float(mu),
+                                 float(nu), int(max_iters), int(check_every), float(tol_gap), float(tol_res),
+                                 _ptr(Ux), _ptr(Uy), _ptr(W), _ptr(Phi), _ptr(met), _ptr(hist), nchk)
+    out = dict(Ux=Ux, Uy=Uy, W=W, Phi=Phi, iters=it, mu=mu, nu=nu, tau=tau, metrics=dict(zip(MET_NAMES, met)))
     if history:
         out["history"] = hist[hist[:, 6] > 0]
     return out

@@ -53,6 +53,7 @@
  * / (4 eps) + dist_2(grad_G phi(x), alpha B_w*)^2 / (4 eps), the conjugate of
  * ||.|| + eps ||.||_2^2 (B* the unit ball of the dual norm).
  */
+#include <complex.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -1683,5 +1684,249 @@ int orc_momt3_solve(int n, int k, int N, const double *L, const double *Lam0, co
     if (t > max_iters) t = max_iters;
     for (int d = 0; d < 3; ++d) { free(g[d]); free(nU[d]); free(bu[d]); }
     free(nW); free(bw); free(dv); free(dl); free(pPhi);
+    return t;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Complex Hermitian matrix OMT (Section 4 in the complex setting)           */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Section 4 states matrix OMT for complex Hermitian densities: Lambda(x) is a
+ * positive semidefinite Hermitian k x k matrix, U_x, U_y are Hermitian,
+ * grad_L X = [L_l X - X L_l]_l with Hermitian L_l maps to skew-Hermitian
+ * matrices, div_L Z = sum_s (-L_s Z_s + Z_s L_s), and every inner product is
+ * the Hilbert-Schmidt one, <X, Y> = Re tr(X Y*) (the real inner product of
+ * C^{k x k} seen as R^{2k^2}).  Norms here: ||U||_2 and ||W||_2, the Frobenius
+ * norms (sum of |entry|^2 over everything, square root), whose shrink scales
+ * the whole point's flux.  The iteration is that of Section 7.3.  Arrays are
+ * complex planes [q][j][i] (q = a*k + b), C99 double complex.
+ */
+typedef double complex zdbl;
+
+static void zmatmul(int k, const zdbl *A, const zdbl *B, zdbl *C)
+{
+    for (int a = 0; a < k; ++a)
+        for (int b = 0; b < k; ++b) {
+            zdbl s = 0.0;
+            for (int q = 0; q < k; ++q) s += A[a * k + q] * B[q * k + b];
+            C[a * k + b] = s;
+        }
+}
+
+/* Z_s = L_s X - X L_s for one point. */
+void orc_zgrad_L_point(int k, int N, const zdbl *L, const zdbl *X, zdbl *Z)
+{
+    zdbl t1[64], t2[64];
+    for (int s = 0; s < N; ++s) {
+        zmatmul(k, L + (size_t)s * k * k, X, t1);
+        zmatmul(k, X, L + (size_t)s * k * k, t2);
+        for (int q = 0; q < k * k; ++q) Z[(size_t)s * k * k + q] = t1[q] - t2[q];
+    }
+}
+
+/* Y = sum_s (-L_s Z_s + Z_s L_s) for one point. */
+void orc_zdiv_L_point(int k, int N, const zdbl *L, const zdbl *Z, zdbl *Y)
+{
+    zdbl t1[64], t2[64];
+    for (int q = 0; q < k * k; ++q) Y[q] = 0.0;
+    for (int s = 0; s < N; ++s) {
+        zmatmul(k, L + (size_t)s * k * k, Z + (size_t)s * k * k, t1);
+        zmatmul(k, Z + (size_t)s * k * k, L + (size_t)s * k * k, t2);
+        for (int q = 0; q < k * k; ++q) Y[q] += -t1[q] + t2[q];
+    }
+}
+
+/* Appendix A's forward-difference gradient and backward-difference divergence,
+ * entrywise on complex planes (the same stencils as orc_grad / orc_div). */
+static void zgrad(int n, int planes, const zdbl *phi, zdbl *gx, zdbl *gy)
+{
+    double ih = (double)(n - 1);
+    for (int c = 0; c < planes; ++c)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                gx[AT(c, j, i)] = (i < n - 1) ? ih * (phi[AT(c, j, i + 1)] - phi[AT(c, j, i)]) : 0.0;
+                gy[AT(c, j, i)] = (j < n - 1) ? ih * (phi[AT(c, j + 1, i)] - phi[AT(c, j, i)]) : 0.0;
+            }
+}
+
+static void zdiv(int n, int planes, const zdbl *ux, const zdbl *uy, zdbl *out)
+{
+    double ih = (double)(n - 1);
+    for (int c = 0; c < planes; ++c)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                zdbl xl = (i > 0) ? ux[AT(c, j, i - 1)] : 0.0;
+                zdbl yl = (j > 0) ? uy[AT(c, j - 1, i)] : 0.0;
+                out[AT(c, j, i)] = ih * (ux[AT(c, j, i)] - xl + uy[AT(c, j, i)] - yl);
+            }
+}
+
+/* lambda_max(-Delta_L) with -Delta_L X = sum_s [L_s, [L_s, X]] acting on all of
+ * C^{k x k}, as a real symmetric 2k^2 x 2k^2 matrix (real parts, then imaginary
+ * parts) assembled column by column. */
+double orc_zquantum_lmax(int k, int N, const zdbl *L)
+{
+    int kk = k * k, m = 2 * kk;
+    double *M = (double *)calloc((size_t)m * m, sizeof(double));
+    double *ev = (double *)malloc(sizeof(double) * m);
+    zdbl X[64], Z[8 * 64], Y[64];
+    for (int col = 0; col < m; ++col) {
+        for (int q = 0; q < kk; ++q) X[q] = 0.0;
+        X[col % kk] = col < kk ? 1.0 : I;
+        orc_zgrad_L_point(k, N, L, X, Z);
+        orc_zdiv_L_point(k, N, L, Z, Y);            /* div grad = Delta_L */
+        for (int q = 0; q < kk; ++q) {
+            M[(size_t)q * m + col] = -creal(Y[q]);
+            M[(size_t)(kk + q) * m + col] = -cimag(Y[q]);
+        }
+    }
+    orc_jacobi_eigvals(m, M, ev);
+    double mx = ev[0];
+    for (int q = 1; q < m; ++q) if (ev[q] > mx) mx = ev[q];
+    free(M); free(ev);
+    return mx;
+}
+
+static double zsq(zdbl z) { return creal(z) * creal(z) + cimag(z) * cimag(z); }
+
+/* Frobenius shrink of m complex entries jointly (Appendix B, shrink_2). */
+static void zshrink2(int m, const zdbl *x, double t, zdbl *out)
+{
+    double s = 0.0;
+    for (int q = 0; q < m; ++q) s += zsq(x[q]);
+    s = sqrt(s);
+    double f = (s > t) ? 1.0 - t / s : 0.0;
+    for (int q = 0; q < m; ++q) out[q] = f * x[q];
+}
+
+void orc_zmomt_metrics(int n, int k, int N, const zdbl *L, const zdbl *Lam0, const zdbl *Lam1, double alpha,
+                       double mu, double nu, double tau, const zdbl *Ux, const zdbl *Uy, const zdbl *W,
+                       const zdbl *Phi, const zdbl *pUx, const zdbl *pUy, const zdbl *pW, const zdbl *pPhi,
+                       double *out)
+{
+    int kk = k * k;
+    size_t nn = (size_t)n * n, nk = (size_t)kk * nn;
+    zdbl *dv = (zdbl *)malloc(sizeof(zdbl) * nk), *dl = (zdbl *)malloc(sizeof(zdbl) * nk);
+    zdbl *gx = (zdbl *)malloc(sizeof(zdbl) * nk), *gy = (zdbl *)malloc(sizeof(zdbl) * nk);
+    zdbl X[64], Z[8 * 64], Y[64];
+    double P = 0.0, D = 0.0, rr = 0.0, bb = 0.0, di = 0.0, R = 0.0;
+    for (size_t p = 0; p < nn; ++p) {
+        double su = 0.0, sw = 0.0;
+        for (int q = 0; q < kk; ++q) su += zsq(Ux[q * nn + p]) + zsq(Uy[q * nn + p]);
+        for (int q = 0; q < N * kk; ++q) sw += zsq(W[q * nn + p]);
+        P += sqrt(su) + alpha * sqrt(sw);
+    }
+    for (size_t q = 0; q < nk; ++q) D += creal(Phi[q] * conj(Lam1[q] - Lam0[q]));
+    zdiv(n, kk, Ux, Uy, dv);
+    for (size_t p = 0; p < nn; ++p) {
+        for (int q = 0; q < N * kk; ++q) Z[q] = W[q * nn + p];
+        orc_zdiv_L_point(k, N, L, Z, Y);
+        for (int q = 0; q < kk; ++q) dl[q * nn + p] = Y[q];
+    }
+    for (size_t q = 0; q < nk; ++q) {
+        rr += zsq(dv[q] + dl[q] - (Lam0[q] - Lam1[q]));
+        bb += zsq(Lam0[q] - Lam1[q]);
+    }
+    zgrad(n, kk, Phi, gx, gy);
+    for (size_t p = 0; p < nn; ++p) {
+        double s = 0.0, w2 = 0.0;
+        for (int q = 0; q < kk; ++q) { s += zsq(gx[q * nn + p]) + zsq(gy[q * nn + p]); X[q] = Phi[q * nn + p]; }
+        orc_zgrad_L_point(k, N, L, X, Z);
+        for (int q = 0; q < N * kk; ++q) w2 += zsq(Z[q]);
+        if (sqrt(s) - 1.0 > di) di = sqrt(s) - 1.0;
+        if (sqrt(w2) - alpha > di) di = sqrt(w2) - alpha;
+    }
+    if (pUx) {
+        size_t nw = (size_t)N * kk * nn;
+        zdbl *dUx = (zdbl *)malloc(sizeof(zdbl) * nk), *dUy = (zdbl *)malloc(sizeof(zdbl) * nk);
+        zdbl *dW = (zdbl *)malloc(sizeof(zdbl) * nw);
+        double su = 0.0, sw = 0.0, sp = 0.0, cr = 0.0;
+        for (size_t q = 0; q < nk; ++q) {
+            dUx[q] = Ux[q] - pUx[q]; dUy[q] = Uy[q] - pUy[q];
+            su += zsq(dUx[q]) + zsq(dUy[q]);
+            sp += zsq(Phi[q] - pPhi[q]);
+        }
+        for (size_t q = 0; q < nw; ++q) { dW[q] = W[q] - pW[q]; sw += zsq(dW[q]); }
+        zdiv(n, kk, dUx, dUy, dv);
+        for (size_t p = 0; p < nn; ++p) {
+            for (int q = 0; q < N * kk; ++q) Z[q] = dW[q * nn + p];
+            orc_zdiv_L_point(k, N, L, Z, Y);
+            for (int q = 0; q < kk; ++q) dl[q * nn + p] = Y[q];
+        }
+        for (size_t q = 0; q < nk; ++q) cr += creal((Phi[q] - pPhi[q]) * conj(dv[q] + dl[q]));
+        R = su / mu + sw / nu + sp / tau - 2.0 * cr;
+        free(dUx); free(dUy); free(dW);
+    }
+    out[0] = P;
+    out[1] = D;
+    out[2] = fabs(P - D) / (fabs(P) > 1e-300 ? fabs(P) : 1e-300);
+    out[3] = sqrt(rr) / (bb > 0.0 ? sqrt(bb) : 1.0);
+    out[4] = R;
+    out[5] = di;
+    free(dv); free(dl); free(gx); free(gy);
+}
+
+/* The M-OMT iteration of Section 7.3 on complex Hermitian fields, Frobenius norms. */
+int orc_zmomt_solve(int n, int k, int N, const zdbl *L, const zdbl *Lam0, const zdbl *Lam1, double alpha,
+                    double tau, double mu, double nu, int max_iters, int check_every, double tol_gap,
+                    double tol_res, zdbl *Ux, zdbl *Uy, zdbl *W, zdbl *Phi, double *metrics, double *history,
+                    int hist_cap)
+{
+    int kk = k * k;
+    size_t nn = (size_t)n * n, nk = (size_t)kk * nn, nw = (size_t)N * kk * nn;
+    zdbl *gx = (zdbl *)malloc(sizeof(zdbl) * nk), *gy = (zdbl *)malloc(sizeof(zdbl) * nk);
+    zdbl *nUx = (zdbl *)malloc(sizeof(zdbl) * nk), *nUy = (zdbl *)malloc(sizeof(zdbl) * nk);
+    zdbl *nW = (zdbl *)malloc(sizeof(zdbl) * nw), *bw = (zdbl *)malloc(sizeof(zdbl) * nw);
+    zdbl *bx = (zdbl *)malloc(sizeof(zdbl) * nk), *by = (zdbl *)malloc(sizeof(zdbl) * nk);
+    zdbl *dv = (zdbl *)malloc(sizeof(zdbl) * nk), *dl = (zdbl *)malloc(sizeof(zdbl) * nk);
+    zdbl *pPhi = (zdbl *)malloc(sizeof(zdbl) * nk);
+    zdbl v[128], o[128], X[64], xw[8 * 64], ow[8 * 64], Y[64];
+    int nh = 0, t = 0;
+    if (check_every <= 0) check_every = max_iters > 0 ? max_iters : 1;
+    for (t = 1; t <= max_iters; ++t) {
+        zgrad(n, kk, Phi, gx, gy);
+        for (size_t p = 0; p < nn; ++p) {
+            for (int q = 0; q < kk; ++q) {
+                v[q] = Ux[q * nn + p] + mu * gx[q * nn + p];
+                v[kk + q] = Uy[q * nn + p] + mu * gy[q * nn + p];
+            }
+            zshrink2(2 * kk, v, mu, o);
+            for (int q = 0; q < kk; ++q) { nUx[q * nn + p] = o[q]; nUy[q * nn + p] = o[kk + q]; }
+        }
+        for (size_t p = 0; p < nn; ++p) {
+            for (int q = 0; q < kk; ++q) X[q] = Phi[q * nn + p];
+            orc_zgrad_L_point(k, N, L, X, xw);
+            for (int q = 0; q < N * kk; ++q) xw[q] = W[q * nn + p] + nu * xw[q];
+            zshrink2(N * kk, xw, alpha * nu, ow);
+            for (int q = 0; q < N * kk; ++q) nW[q * nn + p] = ow[q];
+        }
+        for (size_t q = 0; q < nk; ++q) { bx[q] = 2.0 * nUx[q] - Ux[q]; by[q] = 2.0 * nUy[q] - Uy[q]; }
+        for (size_t q = 0; q < nw; ++q) bw[q] = 2.0 * nW[q] - W[q];
+        zdiv(n, kk, bx, by, dv);
+        for (size_t p = 0; p < nn; ++p) {
+            for (int q = 0; q < N * kk; ++q) xw[q] = bw[q * nn + p];
+            orc_zdiv_L_point(k, N, L, xw, Y);
+            for (int q = 0; q < kk; ++q) dl[q * nn + p] = Y[q];
+        }
+        memcpy(pPhi, Phi, sizeof(zdbl) * nk);
+        for (size_t q = 0; q < nk; ++q) Phi[q] = Phi[q] + tau * (dv[q] + dl[q] + Lam1[q] - Lam0[q]);
+        int check = (t % check_every == 0) || (t == max_iters);
+        double m[ORC_NMET];
+        if (check) {
+            orc_zmomt_metrics(n, k, N, L, Lam0, Lam1, alpha, mu, nu, tau, nUx, nUy, nW, Phi, Ux, Uy, W, pPhi, m);
+            m[6] = (double)t;
+            m[7] = (tol_gap > 0.0 && m[2] <= tol_gap && m[3] <= tol_res) ? 1.0 : 0.0;
+            if (history && nh < hist_cap) { memcpy(history + (size_t)nh * ORC_NMET, m, sizeof m); ++nh; }
+            if (metrics) memcpy(metrics, m, sizeof m);
+        }
+        memcpy(Ux, nUx, sizeof(zdbl) * nk);
+        memcpy(Uy, nUy, sizeof(zdbl) * nk);
+        memcpy(W, nW, sizeof(zdbl) * nw);
+        if (check && m[7] != 0.0) break;
+    }
+    if (t > max_iters) t = max_iters;
+    free(gx); free(gy); free(nUx); free(nUy); free(nW); free(bw); free(bx); free(by); free(dv); free(dl);
+    free(pPhi);
     return t;
 }

@@ -23,6 +23,11 @@ same shapes and structure:
 * ``random_L``           N symmetric k x k matrices, Gaussian entries,
                          symmetrised and scaled to unit Frobenius norm.
 * ``random_connected_graph``  G(k, p) redrawn until connected.
+* ``hermitian_field_pair``, ``random_hermitian_L``  complex Hermitian positive
+                         definite fields (the tensor-field recipe with a smooth
+                         phase on the rotation's off-diagonal) and complex
+                         Hermitian L matrices, for matrix OMT in the complex
+                         setting of Section 4 (multivariate spectral densities).
 * ``tensor_field_pair3`` the tensor-field recipe on an n x n x n grid (angle and
                          eigenvalue fields smoothed with sigma max(1, n/12) cells),
                          matrix densities of a 3-D DTI volume's shape.
@@ -154,6 +159,41 @@ def tensor_field_pair3(n: int = 32, k: int = 3, seed: int = 1009):
     rng = np.random.default_rng(seed)
     sigma = max(1.0, n / 12.0)
     return _tensor_field3(rng, n, k, sigma), _tensor_field3(rng, n, k, sigma)
+
+
+def _hermitian_field(rng, n, k, sigma=10.0):
+    t = _smooth_noise(rng, n, sigma)
+    t = (t - t.min()) / max(t.max() - t.min(), 1e-300)
+    theta = 2.0 * np.pi * t
+    s = _smooth_noise(rng, n, sigma)
+    psi = 2.0 * np.pi * (s - s.min()) / max(s.max() - s.min(), 1e-300)
+    lam = np.stack([0.05 + _smooth_noise(rng, n, sigma) for _ in range(k)], axis=-1)   # [n, n, k]
+    Q = _rot_z(theta, k).astype(np.complex128)                                          # [n, n, k, k]
+    Q[..., 0, 1] *= np.exp(1j * psi)
+    Q[..., 1, 0] *= np.exp(-1j * psi)
+    M = np.einsum("jiab,jib,jicb->jiac", Q, lam, Q.conj())
+    M = M / np.trace(M, axis1=-2, axis2=-1).real.sum()
+    return np.ascontiguousarray(M.reshape(n, n, k * k).transpose(2, 0, 1))
+
+
+def hermitian_field_pair(n: int = 128, k: int = 2, seed: int = 1010):
+    """[k*k, n, n] complex Hermitian positive definite fields Q diag(lam) Q*, Q a rotation of
+    the first two coordinates by a smooth angle with a smooth phase on its off-diagonal
+    (sigma 10 px), lam = 0.05 + smooth fields; total trace 1 each."""
+    rng = np.random.default_rng(seed)
+    return _hermitian_field(rng, n, k), _hermitian_field(rng, n, k)
+
+
+def random_hermitian_L(k: int = 2, N: int = 3, seed: int = 1010):
+    """N complex Hermitian k x k matrices (G + G*) / 2, G with N(0,1) real and imaginary
+    parts, each scaled to unit Frobenius norm."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(N):
+        G = rng.standard_normal((k, k)) + 1j * rng.standard_normal((k, k))
+        H = (G + G.conj().T) / 2.0
+        out.append(H / np.linalg.norm(H))
+    return np.array(out)
 
 
 def random_L(k: int = 3, N: int = 3, seed: int = 1003):
