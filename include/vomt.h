@@ -360,6 +360,30 @@ int momt_solve(vomt_ctx *ctx, int n, int k, const float *Lam0, const float *Lam1
                double alpha, const vomt_params *p, float *U, float *W, float *Phi, vomt_result *result,
                void *stream);
 
+/* Complex Hermitian matrix OMT: Section 4's complex setting (Hermitian densities
+ * and L_l, skew-Hermitian W, the Hilbert-Schmidt product Re tr(X Y*)), iterated
+ * as in Section 7.3 with the Frobenius norms ||U||_2 and ||W||_2 (p->u_norm
+ * VOMT_U_L2 or the default, p->w_norm VOMT_W_L2; anything else is BAD_ARG).
+ *   k = 2 (a Hermitian 2 x 2 field is 4 real coordinates), 1 <= N <= 7.
+ *   L: host, N complex k x k Hermitian matrices as (re, im) double pairs,
+ *      row-major: L[((s*k + a)*k + b)*2 + {0, 1}].
+ *   Lam0, Lam1: device [2][k*k][n][n] floats, the real parts then the imaginary
+ *      parts of the k*k entries (entry (a, b) at plane a*k + b); Hermitian
+ *      (|X_ab - conj X_ba| and |Im X_aa| <= 1e-5 max|X|), nonnegative real
+ *      diagonals, equal total trace.
+ *   U: device [2][2][k*k][n][n] (direction x, y; then re, im), W: device
+ *      [N][2][k*k][n][n] (skew-Hermitian), Phi: device [2][k*k][n][n]; outputs,
+ *      and inputs when p->warm_start.
+ * Step sizes as momt_solve, with lambda_max(-Delta_L) over C^{k x k}; the
+ * kernel condition is checked on Hermitian matrices (L_KERNEL).  Internally a
+ * Hermitian field is its real diagonal and the real and imaginary parts of the
+ * entries above it (weights 1, 2, 2), a skew-Hermitian one the imaginary
+ * diagonal and the entries above it, which reproduces Re tr(X Y*) exactly.
+ * Errors: as momt_solve. */
+int momt_solve_complex(vomt_ctx *ctx, int n, int k, const float *Lam0, const float *Lam1, int N,
+                       const double *L, double alpha, const vomt_params *p, float *U, float *W, float *Phi,
+                       vomt_result *result, void *stream);
+
 /* Matrix OMT on an n x n x n grid (2 <= n <= 1024): the iteration of momt_solve
  * with a third spatial direction (the discretization of vomt_solve3d), for
  * volumes of matrix densities such as 3-D DTI.

@@ -217,6 +217,53 @@ def momt_solve(Lam0, Lam1, L, alpha: float = 1.0, *, tau=None, mu=None, nu=None,
     return MatrixSolution(U, W, Phi, res.as_dict())
 
 
+def momt_solve_complex(Lam0, Lam1, L, alpha: float = 1.0, *, tau=None, mu=None, nu=None, max_iters: int = 2000,
+                       check_every: int = 100, tol_gap: float = 0.0, tol_res: float = 0.0, init=None, engine="auto",
+                       halo: int = 0, stream=None) -> MatrixSolution:
+    """Complex Hermitian matrix OMT (Section 4's complex setting, Section 7.3 iteration) with
+    the Frobenius norms ||U||_2, ||W||_2, on the GPU.
+
+    Lam0, Lam1: CUDA complex tensors [k*k, n, n] (k = 2) of Hermitian matrices.  L: [N, k, k]
+    complex Hermitian (numpy, host).  Returns complex64 U [2, k*k, n, n], W [N, k*k, n, n],
+    Phi [k*k, n, n].  The complex tensors are split into real and imaginary planes for the
+    library and joined again on return (layout marshalling only).
+    """
+    import torch
+
+    def planes(x):
+        x = x.to(torch.complex64)
+        return torch.stack([x.real, x.imag], dim=-4 if x.dim() >= 4 else 0).contiguous()
+
+    def join(x):                                    # [..., 2, kk, n, n] -> complex [..., kk, n, n]
+        return torch.complex(x.select(-4, 0), x.select(-4, 1))
+
+    Lh = np.ascontiguousarray(np.asarray(L, dtype=np.complex128))
+    N, k = Lh.shape[0], Lh.shape[1]
+    kk, n = Lam0.shape[0], Lam0.shape[-1]
+    if kk != k * k or Lam0.shape != Lam1.shape or Lam0.dim() != 3:
+        raise ValueError("Lam0 and Lam1 must be [k*k, n, n] of one shape")
+    dev = Lam0.device
+    P0, P1 = planes(Lam0), planes(Lam1)
+    if init is not None:
+        U = torch.stack([planes(init[0][0]), planes(init[0][1])]).contiguous()
+        W = torch.stack([planes(init[1][s]) for s in range(N)]).contiguous()
+        Phi = planes(init[2])
+    else:
+        U = torch.empty((2, 2, kk, n, n), device=dev, dtype=torch.float32)
+        W = torch.empty((N, 2, kk, n, n), device=dev, dtype=torch.float32)
+        Phi = torch.empty((2, kk, n, n), device=dev, dtype=torch.float32)
+    p = _params(tau, mu, nu, U_L2, W_L2, max_iters, check_every, tol_gap, tol_res, init is not None, engine, halo)
+    res = _native.Result()
+    st = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
+    ctx = _native.context(dev.index if dev.index is not None else torch.cuda.current_device())
+    Lri = np.ascontiguousarray(np.stack([Lh.real, Lh.imag], axis=-1))
+    rc = _native.load().momt_solve_complex(ctx, int(n), int(k), P0.data_ptr(), P1.data_ptr(), int(N),
+                                           Lri.ctypes.data, float(alpha), ctypes.byref(p), U.data_ptr(),
+                                           W.data_ptr(), Phi.data_ptr(), ctypes.byref(res), ctypes.c_void_p(st))
+    _native.check(rc, ctx)
+    return MatrixSolution(join(U), join(W), join(Phi), res.as_dict())
+
+
 def momt_solve3d(Lam0, Lam1, L, alpha: float = 1.0, *, tau=None, mu=None, nu=None, u_norm: int = U_L2,
                  w_norm: int = W_L1, max_iters: int = 2000, check_every: int = 100, tol_gap: float = 0.0,
                  tol_res: float = 0.0, init=None, stream=None, zc: int = 0) -> MatrixSolution:

@@ -71,6 +71,9 @@ SIGNATURES = {
                                 c_void_p]),
     "vomt_solve3d": (c_int, [c_void_p, c_int, c_void_p, c_void_p, ctypes.POINTER(Graph), c_double,
                              ctypes.POINTER(Params), c_void_p, c_void_p, c_void_p, ctypes.POINTER(Result), c_void_p]),
+    "momt_solve_complex": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int, c_void_p, c_double,
+                                   ctypes.POINTER(Params), c_void_p, c_void_p, c_void_p, ctypes.POINTER(Result),
+                                   c_void_p]),
     "momt_solve3d": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int, c_void_p, c_double,
                              ctypes.POINTER(Params), c_void_p, c_void_p, c_void_p, ctypes.POINTER(Result), c_void_p]),
     "vomt_history": (c_int, [c_void_p, P_double, c_int]),

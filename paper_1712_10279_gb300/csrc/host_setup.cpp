@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <complex>
 #include <vector>
 
 #include "internal.h"
@@ -263,6 +264,122 @@ int quantum_to_op(int k, int N, const double *L, OpDev *op, double *lmax, double
     const double lm = sym_lmax(kk, M.data());
     if (!(gap > 1e-8 * lm)) {
         *err = "matrix OMT: ker grad_L on symmetric matrices is larger than span{I}";
+        return VOMT_ERR_L_KERNEL;
+    }
+    return VOMT_OK;
+}
+
+// Complex Hermitian fields (Section 4's complex setting) in real compact
+// coordinates: a Hermitian k x k matrix X is its diagonal (real), then Re and Im
+// of each entry above it (a, b), weights 1, 2, 2; a skew-Hermitian Z is Im of its
+// diagonal, then Re and Im of each entry above it, weights 1, 2, 2.  Both
+// reproduce Re tr(X Y*) exactly, so grad_L becomes a real-linear map G between
+// the two coordinate spaces and div_L its weighted adjoint, as in the real case.
+// k * k real channels must fit KMAX, so k = 2 (4 channels, 4 flux entries per
+// L_s); the channel count is padded to the smallest K >= 4 with
+// K(K-1)/2 >= 4N, the flux bound of the kernels' templates (padding channels
+// carry zero in every field and take no part in G).
+int hermitian_to_op(int k, int N, const double *L, OpDev *op, double *lmax, double *sym_gap, std::string *err)
+{
+    if (k != 2 || N < 1 || !L) { *err = "complex matrix OMT: k = 2 and N >= 1 with L given"; return VOMT_ERR_BAD_ARG; }
+    const int kk = k * k, ks = k * k;            // real coordinates of Hermitian / skew-Hermitian
+    int K = kk;
+    while (K * (K - 1) / 2 < N * ks) ++K;
+    if (K > KMAX) { *err = "complex matrix OMT: too many L matrices (N <= 7)"; return VOMT_ERR_BAD_ARG; }
+    typedef std::complex<double> cd;
+    double scale = 0.0;
+    for (int q = 0; q < 2 * N * kk; ++q) {
+        if (!isfinite(L[q])) { *err = "complex matrix OMT: L has non-finite entries"; return VOMT_ERR_BAD_ARG; }
+        scale = std::max(scale, fabs(L[q]));
+    }
+    auto Lz = [&](int s, int a, int b) { const double *p = L + 2 * ((size_t)(s * k + a) * k + b); return cd(p[0], p[1]); };
+    for (int s = 0; s < N; ++s)
+        for (int a = 0; a < k; ++a)
+            for (int b = 0; b < k; ++b)
+                if (std::abs(Lz(s, a, b) - std::conj(Lz(s, b, a))) > 1e-12 * std::max(scale, 1e-300)) {
+                    *err = "complex matrix OMT: every L_s must be Hermitian";
+                    return VOMT_ERR_BAD_ARG;
+                }
+    // basis X_c of the Hermitian coordinates, and the coordinate reader of skew-Hermitian matrices
+    std::vector<std::vector<cd>> Xc;
+    std::vector<double> wc;
+    for (int a = 0; a < k; ++a) {
+        std::vector<cd> X(kk, cd(0, 0));
+        X[a * k + a] = 1.0;
+        Xc.push_back(X);
+        wc.push_back(1.0);
+    }
+    for (int a = 0; a < k; ++a)
+        for (int b = a + 1; b < k; ++b) {
+            std::vector<cd> Xr(kk, cd(0, 0)), Xi(kk, cd(0, 0));
+            Xr[a * k + b] = 1.0;
+            Xr[b * k + a] = 1.0;
+            Xi[a * k + b] = cd(0, 1);
+            Xi[b * k + a] = cd(0, -1);
+            Xc.push_back(Xr);
+            Xc.push_back(Xi);
+            wc.push_back(2.0);
+            wc.push_back(2.0);
+        }
+    auto skew_coords = [&](const std::vector<cd> &Z, double *out) {
+        int e = 0;
+        for (int a = 0; a < k; ++a) out[e++] = Z[a * k + a].imag();
+        for (int a = 0; a < k; ++a)
+            for (int b = a + 1; b < k; ++b) {
+                out[e++] = Z[a * k + b].real();
+                out[e++] = Z[a * k + b].imag();
+            }
+    };
+    double we_one[64];
+    {
+        int e = 0;
+        for (int a = 0; a < k; ++a) we_one[e++] = 1.0;
+        for (int a = 0; a < k; ++a)
+            for (int b = a + 1; b < k; ++b) { we_one[e++] = 2.0; we_one[e++] = 2.0; }
+    }
+    memset(op, 0, sizeof(*op));
+    op->k = K;
+    op->l = N * ks;
+    for (int c = 0; c < K; ++c) op->wc[c] = c < kk ? (float)wc[c] : 1.0f;
+    std::vector<double> Gd((size_t)N * ks * kk, 0.0);
+    for (int s = 0; s < N; ++s)
+        for (int c = 0; c < kk; ++c) {
+            std::vector<cd> Z(kk, cd(0, 0));          // L_s X_c - X_c L_s
+            for (int a = 0; a < k; ++a)
+                for (int b = 0; b < k; ++b) {
+                    cd v(0, 0);
+                    for (int m = 0; m < k; ++m) v += Lz(s, a, m) * Xc[c][m * k + b] - Xc[c][a * k + m] * Lz(s, m, b);
+                    Z[a * k + b] = v;
+                }
+            double co[64];
+            skew_coords(Z, co);
+            for (int e = 0; e < ks; ++e) Gd[(size_t)(s * ks + e) * kk + c] = co[e];
+        }
+    for (int s = 0; s < N; ++s)
+        for (int e = 0; e < ks; ++e) {
+            const int ee = s * ks + e;
+            op->we[ee] = (float)we_one[e];
+            for (int c = 0; c < kk; ++c) {
+                op->G[ee][c] = (float)Gd[(size_t)ee * kk + c];
+                op->Dv[c][ee] = (float)(we_one[e] / wc[c] * Gd[(size_t)ee * kk + c]);
+            }
+        }
+    // -Delta_L = div^* ... in these coordinates M = Dv G, self-adjoint for the weights wc;
+    // its spectrum is that of W^(1/2) M W^(-1/2) (symmetric), the same on Hermitian
+    // matrices as on all of C^{k x k} since -Delta_L is complex-linear
+    std::vector<double> Sm((size_t)kk * kk, 0.0);
+    for (int c = 0; c < kk; ++c)
+        for (int d = 0; d < kk; ++d) {
+            double v = 0.0;
+            for (int e = 0; e < N * ks; ++e) v += (we_one[e % ks] / wc[c]) * Gd[(size_t)e * kk + c] * Gd[(size_t)e * kk + d];
+            Sm[(size_t)c * kk + d] = sqrt(wc[c]) * v / sqrt(wc[d]);
+        }
+    const double lm = sym_lmax(kk, Sm.data());
+    const double gap = sym_eig(kk, Sm.data(), 1);
+    if (lmax) *lmax = lm;
+    if (sym_gap) *sym_gap = gap;
+    if (!(gap > 1e-8 * lm)) {
+        *err = "complex matrix OMT: ker grad_L on Hermitian matrices is larger than span{I}";
         return VOMT_ERR_L_KERNEL;
     }
     return VOMT_OK;

@@ -105,6 +105,8 @@ void graph_to_op(const GraphDev &g, OpDev *op);
 // k^2 x k^2 matrix of Section 7.3) and the second-smallest eigenvalue of -Delta_L on
 // symmetric matrices (positive iff ker grad_L = span{I}, the standing assumption).
 int quantum_to_op(int k, int N, const double *L, OpDev *op, double *lmax, double *sym_gap, std::string *err);
+// complex Hermitian fields (k = 2); L: N complex k x k matrices, (re, im) pairs row-major
+int hermitian_to_op(int k, int N, const double *L, OpDev *op, double *lmax, double *sym_gap, std::string *err);
 
 }  // namespace vomt
 
