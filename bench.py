@@ -18,8 +18,9 @@ batched engine against a loop of plain solves on 512 mixed instances, the
 differentiable cost (64 pairs at 256 x 256, forward + backward, and the
 200-iteration unrolled gradient) against plain forward solves, and a
 2048 x 2048 k = 3 case whose state does not fit L2 (the HBM-bound cross-check of
-the streaming kernel), the regularised problem, and 3-D grids of 128^3 and 256^3
-with k = 3 (the TMA z-marching step against the HBM roofline).  --cap / --alphas shrink the timed workload for profiler
+the streaming kernel), the regularised problem, complex Hermitian matrix OMT at
+128 x 128, and 3-D grids of 128^3 and 256^3 (vector k = 3, 2 x 2 and 3 x 3
+matrices; the TMA z-marching step against the HBM roofline).  --cap / --alphas shrink the timed workload for profiler
 runs only (the line then names the reduced workload).
 """
 from __future__ import annotations
@@ -308,6 +309,31 @@ def extra_hbm_bound(dev, peak, n=2048, iters=300):
     return out
 
 
+def extra_complex(dev, peak, n=128, N=3, iters=20000):
+    """Complex Hermitian matrix OMT (Section 4's complex setting): 128 x 128 grid of 2 x 2
+    Hermitian densities, N = 3 complex Hermitian L, alpha = 1, Frobenius norms, fixed
+    iterations (checks every CHECK_EVERY)."""
+    import torch
+    import paper_1712_10279_gb300 as V
+    from paper_1712_10279_gb300 import synthetic as S
+    a, b = S.hermitian_field_pair(n, 2, seed=1010)
+    L = S.random_hermitian_L(2, N, seed=1010)
+    d0 = torch.from_numpy(a.astype(np.complex64)).to(dev)
+    d1 = torch.from_numpy(b.astype(np.complex64)).to(dev)
+    V.momt_solve_complex(d0, d1, L, 1.0, max_iters=200, check_every=100)
+    sol, ms = _gpu_ms(lambda: V.momt_solve_complex(d0, d1, L, 1.0, max_iters=iters, check_every=CHECK_EVERY))
+    r = sol.result
+    K, l = 4, 4 * N                     # real coordinates of a Hermitian / skew-Hermitian 2 x 2 field
+    bpg = 4 * (7 * K + 2 * l)
+    gp = n * n * r["iters"]
+    gbs = bpg * gp / (ms / 1e3) / 1e9
+    return dict(workload="complex Hermitian matrix OMT %dx%d 2x2 (Hermitian fields seed 1010, N=%d complex L), "
+                         "alpha=1, ||U||_2 ||W||_2, %d iterations" % (n, n, N, iters),
+                ms=ms, us_per_iter=1e3 * ms / max(r["iters"], 1), gp_it_per_s=gp / (ms / 1e3),
+                algorithmic_bytes_per_gp_it=bpg, achieved_GBps=gbs, frac_of_measured_hbm=gbs / peak,
+                engine=r["engine"], iters=r["iters"], primal=r["primal"], rel_gap=r["rel_gap"])
+
+
 def extra_regularised(dev, peak, eps=5e4, cap=50000):
     """The quadratically regularised problem (the paper's conclusions) on the benchmark
     workload: eps (||u||_2^2 + ||w||_2^2) added, to rel gap and rel res <= 1e-5."""
@@ -383,6 +409,7 @@ def extras(dev):
                      ("batched_vs_plain", lambda: extra_batched(dev)),
                      ("differentiable", lambda: extra_differentiable(dev)),
                      ("regularised", lambda: extra_regularised(dev, peak)),
+                     ("complex_hermitian_128", lambda: extra_complex(dev, peak)),
                      ("hbm_bound", lambda: extra_hbm_bound(dev, peak)),
                      ("volume_3d", lambda: extra_volume(dev, peak))):
         t0 = time.perf_counter()
