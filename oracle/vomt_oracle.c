@@ -1207,7 +1207,7 @@ double orc_vomt_unrolled_grad(int n, int k, int l, const int *ea, const int *eb,
  *   terms before the first cell of a direction taken as zero.
  * Norms per point as in 2-D with three spatial components per channel:
  * ||u||_{1,2} = sum_c |(u_x, u_y, u_z)_c|_2, ||u||_2 joint, ||u||_1 entrywise.
- * Step rule (reading of this build): ||grad||^2 <= 12 / h^2 in 3-D, so
+ * Step rule (a reading: the paper states the 2-D rule only): ||grad||^2 <= 12 / h^2 in 3-D, so
  * mu = 1 / (48 tau (n-1)^2) keeps the 2-D rule's share of the bound
  * (8/32 = 12/48); nu as in 2-D.
  */
