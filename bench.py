@@ -402,7 +402,7 @@ def extra_volume(dev, peak, iters=500):
     return out
 
 
-def extras(dev):
+def extras(dev, only=None):
     peak, _ = _peaks()
     out = {}
     for name, fn in (("matrix_128", lambda: extra_matrix(dev, peak)),
@@ -413,6 +413,8 @@ def extras(dev):
                      ("complex_hermitian_128", lambda: extra_complex(dev, peak)),
                      ("hbm_bound", lambda: extra_hbm_bound(dev, peak)),
                      ("volume_3d", lambda: extra_volume(dev, peak))):
+        if only is not None and name != only:
+            continue
         t0 = time.perf_counter()
         try:
             out[name] = fn()
@@ -555,10 +557,17 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cap", type=int, default=CAP, help="iteration cap per solve (profiler runs only)")
     ap.add_argument("--alphas", type=float, nargs="+", default=list(ALPHAS), help="(profiler runs only)")
+    ap.add_argument("--only-extra", default=None,
+                    help="run one named extra measurement alone and print it (profiler runs only)")
     args = ap.parse_args()
     from paper_1712_10279_gb300.replicas import rank_world
     rank, world, local_rank = rank_world()
-    if args.impl == "reference":
+    if args.only_extra:
+        import torch
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        print(json.dumps({"extras": extras(dev, only=args.only_extra)}), flush=True)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world, local_rank)

@@ -616,10 +616,8 @@ static bool grouped_plan(vomt_ctx *ctx, int count, const std::vector<InstDev> &h
 static double grouped_estimate(const std::vector<Wave> &waves, int iters)
 {
     double t = 0.0;
-    for (const Wave &w : waves) {
-        const double rounds = (double)w.per;
-        t += rounds * w.plan.est_ns * (double)iters * (double)(7 * w.k + w.k * (w.k - 1)) / 27.0 + 20000.0;
-    }
+    for (const Wave &w : waves)      // est_ns of a wave plan already covers its rounds
+        t += w.plan.est_ns * (double)iters * (double)(7 * w.k + w.k * (w.k - 1)) / 27.0 + 20000.0;
     return t;
 }
 

@@ -177,7 +177,7 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
 // resident engine (vector_resident.cu)
 struct ResidentPlan {
     int Gx, Gy, TXm, TYm, H, threads, P;
-    double est_ns;
+    double est_ns;      // estimated ns per iteration (a wave plan: of the whole wave, all its rounds)
 };
 // Fixed-order sum of per-block FP64 partials (NRED per block), the stopping
 // decision and the history row (one block of 256 threads; vector_stream.cu).
