@@ -233,3 +233,13 @@ def test_errors():
         _gpu(r0, r1, K3, 1.0, max_iters=1, mu=1.0 / (8.0 * (n - 1) ** 2))   # breaks the 3-D rule
     with pytest.raises(ValueError):
         V.solve3d(_t(r0[:, 0]), _t(r1[:, 0]), K3, 1.0)
+    # beyond the 3-D size limit (n <= 1024): refused before any allocation
+    big = torch.zeros((1, 2, 2, 2), device=_dev())
+    import ctypes
+    from paper_1712_10279_gb300 import _native
+    p = V._params(None, None, None, V.U_L12, V.W_L1, 1, 1, 0.0, 0.0, False, "stream")
+    g = _native.GraphArg(1, [], None)
+    rc = _native.load().vomt_solve3d(_native.context(0), 1025, big.data_ptr(), big.data_ptr(), g.ref, 1.0,
+                                     ctypes.byref(p), big.data_ptr(), None, big.data_ptr(),
+                                     ctypes.byref(_native.Result()), None)
+    assert rc < 0

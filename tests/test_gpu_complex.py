@@ -146,3 +146,7 @@ def test_errors():
     Lnh[0, 0, 1] += 0.3                                  # L not Hermitian
     with pytest.raises(V.VomtError):
         _gpu(A0, A1, Lnh, 1.0, max_iters=1)
+    # one L: its commutant on Hermitian matrices is span{I, L}, larger than span{I}
+    with pytest.raises(V.VomtError) as ex:
+        _gpu(A0, A1, L[:1], 1.0, max_iters=1)
+    assert ex.value.status == -5                          # VOMT_ERR_L_KERNEL
