@@ -308,7 +308,7 @@ int vomt_batch_tune(vomt_ctx *ctx, int count, const vomt_instance *inst, float *
                     const vomt_params *p, int sample_iters, int *best_threads, double *ms);
 
 /* Set the batched engine's threads per block (128, 256 or 512; 0 restores the
- * default, 256), e.g. from a tuning result cached by the caller. */
+ * default, 512), e.g. from a tuning result cached by the caller. */
 int vomt_batch_set_threads(vomt_ctx *ctx, int threads);
 
 /* ------------------------------------------------------------------------ */

@@ -869,8 +869,10 @@ extern "C" int vomt_solve_batched(vomt_ctx *ctx, int count, const vomt_instance 
                                                                           : "a problem produced a non-finite iterate";
             return status;
         }
-        // launch shape: the tuned block size, as many resident blocks as fit, at most one per instance
-        const int threads = b->tuned_threads > 0 ? b->tuned_threads : 256;
+        // launch shape: the tuned block size (untuned: 512, which the tuner picked for every
+        // mix measured on GB300, twice as fast as 256 on the 512-problem mix), as many
+        // resident blocks as fit, at most one per instance
+        const int threads = b->tuned_threads > 0 ? b->tuned_threads : 512;
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, threads, 0);
         if (e != cudaSuccess || per_sm < 1) return set_cuda_error(ctx, e == cudaSuccess ? cudaErrorInvalidConfiguration : e, "batch occupancy");
