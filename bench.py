@@ -3,8 +3,11 @@
 One step = solving the workload once for each alpha in {0.1, 1, 10} from the
 zero iterate until relative gap and relative residual are both <= 1e-5, with a
 cap of 50,000 iterations (Section 7.2 iteration, complete channel graph K3,
-||u||_{1,2}, ||w||_1, the paper's step-size rule with tau = 3).  The metric is
-grid-point iterations per second summed over the whole job.
+||u||_{1,2}, ||w||_1, the paper's step-size rule).  Sections 7.1-7.3 tune the
+dual step tau per experiment; before the warm-up, the library's tuner
+(vomt_tune_tau: short GPU runs over a geometric tau grid) picks tau for each
+alpha once, and every solve uses it (mu, nu follow by the paper's rule).  The
+metric is grid-point iterations per second summed over the whole job.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -12,16 +15,18 @@ Prints one JSON line.  `--impl reference` times the FP64 CPU oracle (the
 reference implementation of this repository) on a bounded sample of the same
 workload on the host cores.
 
-Besides the headline number the line carries, measured after the timed region
-(N = 1 only, skipped with --no-extras): matrix OMT at 128 x 128 (3 x 3), the
-batched engine against a loop of plain solves on 512 mixed instances, the
-differentiable cost (64 pairs at 256 x 256, forward + backward, and the
-200-iteration unrolled gradient) against plain forward solves, and a
-2048 x 2048 k = 3 case whose state does not fit L2 (the HBM-bound cross-check of
-the streaming kernel), the regularised problem, complex Hermitian matrix OMT at
-128 x 128, and 3-D grids of 128^3 and 256^3 (vector k = 3, 2 x 2 and 3 x 3
-matrices; the TMA z-marching step against the HBM roofline).  --cap / --alphas shrink the timed workload for profiler
-runs only (the line then names the reduced workload).
+Besides the headline number the line carries (N = 1 only, skipped with
+--no-extras): time to tolerance without the cap, matrix OMT at 128 x 128
+(3 x 3), the batched engine against a loop of plain solves on 512 mixed
+instances, the differentiable cost (64 pairs at 256 x 256, forward + backward,
+and the 200-iteration unrolled gradient) against plain forward solves, the
+FP32-vs-FP64-oracle error of every form, a 2048 x 2048 k = 3 case whose state
+does not fit L2 (the HBM-bound cross-check of the streaming kernel), the
+regularised problem, complex Hermitian matrix OMT at 128 x 128, and 3-D grids of
+128^3 and 256^3.  The CPU baseline holds the oracle's one-thread and all-core
+(OpenMP) iteration times at four sizes and its time to tolerance.  --cap /
+--alphas shrink the timed workload for profiler runs only (the line then names
+the reduced workload).
 """
 from __future__ import annotations
 
@@ -41,12 +46,17 @@ sys.path.insert(0, ROOT)
 
 N, K, ALPHAS, TOL, CAP = 256, 3, (0.1, 1.0, 10.0), 1e-5, 50000
 CHECK_EVERY = 100
+TUNE_ITERS = 1000            # sample_iters of the tau tuner (about 34x that many iterations per tuning)
+UNCAPPED = 500000            # cap of the time-to-tolerance runs beyond the configured 50,000
 EDGES = [(0, 1), (0, 2), (1, 2)]
 BYTES_PER_GP_IT = 4 * (7 * K + 2 * len(EDGES))   # read phi,u_x,u_y,w,b; write phi,u_x,u_y,w (FP32)
+REF_TAU = 300.0             # tau of the reference arm's oracle sample (its cost per iteration does not depend on tau)
+
+
 def workload_name(alphas=ALPHAS, cap=CAP):
     return ("vector OMT, 256x256 grid, k=3 colour-image densities (seed 1002), complete graph K3, "
-            "alpha in {%s}, ||u||_{1,2} ||w||_1, tau=3, to rel gap and rel res <= 1e-5, cap %d it"
-            % (",".join("%g" % a for a in alphas), cap))
+            "alpha in {%s}, ||u||_{1,2} ||w||_1, tau tuned per alpha (vomt_tune_tau), to rel gap and rel res "
+            "<= 1e-5, cap %d it" % (",".join("%g" % a for a in alphas), cap))
 
 
 WORKLOAD = workload_name()
@@ -125,25 +135,109 @@ def _cpu_cores():
     return os.cpu_count() or 1
 
 
-def oracle_sample(seconds_target=12.0):
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_sample(seconds_target=12.0, tau=REF_TAU, keep_state=False):
     """Time the FP64 oracle (one thread) on a bounded sample of the workload: the first T
-    iterations of the alpha = 1 solve from zero."""
+    iterations of the alpha = 1 solve from zero at the given tau."""
     import oracle
     from paper_1712_10279_gb300 import synthetic as S
+    oracle.set_threads(1)
     r0, r1 = S.color_image_pair(N, K, seed=1002)
     r0 = r0.astype(np.float32).astype(np.float64)
     r1 = r1.astype(np.float32).astype(np.float64)
     t0 = time.perf_counter()
-    oracle.vomt_solve(r0, r1, EDGES, 1.0, max_iters=5, check_every=5)
+    oracle.vomt_solve(r0, r1, EDGES, 1.0, tau=tau, max_iters=5, check_every=5)
     per = (time.perf_counter() - t0) / 5
     T = int(max(10, min(3000, seconds_target / max(per, 1e-6))))
     T = (T // 10) * 10
     t0 = time.perf_counter()
-    oracle.vomt_solve(r0, r1, EDGES, 1.0, max_iters=T, check_every=100)
+    ref = oracle.vomt_solve(r0, r1, EDGES, 1.0, tau=tau, max_iters=T, check_every=100)
     dt = time.perf_counter() - t0
-    return {"value": N * N * T / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "first %d PDHG iterations (checks every 100) of the alpha=1 solve, 256x256 k=3, FP64, "
-                      "one thread, %.1f s" % (T, dt)}
+    out = {"value": N * N * T / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "first %d PDHG iterations (checks every 100) of the alpha=1 solve at tau=%.4g, 256x256 k=3, "
+                     "FP64, one thread, %.1f s" % (T, tau, dt)}
+    if keep_state:
+        out["_state"] = ref
+        out["_iters"] = T
+    return out
+
+
+def _median_iter_ms(fn, iters, reps=5):
+    """Median over `reps` runs (after one warm-up) of the milliseconds per iteration of fn(iters)."""
+    fn(max(2, iters // 4))
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        fn(iters)
+        ts.append((time.perf_counter() - t0) * 1e3 / iters)
+    return statistics.median(ts)
+
+
+def cpu_legs(taus):
+    """The oracle on the host cores: ms per iteration, one thread and all cores (OpenMP
+    build, bit-identical results), at the paper-shaped sizes; time to tolerance for the
+    32 x 32 blob case (to 1e-5) and a bounded run of the 256 x 256 alpha = 1 solve."""
+    import oracle
+    from paper_1712_10279_gb300 import synthetic as S
+    cores = _cpu_cores()
+    a32, b32 = S.blob_pair(32, 3, seed=1001)
+    a256, b256 = S.color_image_pair(256, 3, seed=1002)
+    m0, m1 = S.tensor_field_pair(128, 3, seed=1003)
+    Lm = S.random_L(3, 3, seed=1003)
+    s0, s1 = S.color_image_pair(1024, 1, seed=1007)
+    cases = {
+        "vector_32x32_k3": (lambda T: oracle.vomt_solve(a32, b32, EDGES, 1.0, max_iters=T, check_every=T), 400),
+        "vector_256x256_k3": (lambda T: oracle.vomt_solve(a256, b256, EDGES, 1.0, max_iters=T, check_every=T), 20),
+        "matrix_128x128_3x3_N3": (lambda T: oracle.momt_solve(m0, m1, Lm, 1.0, max_iters=T, check_every=T), 6),
+        "scalar_1024x1024_k1": (lambda T: oracle.vomt_solve(s0, s1, [], 1.0, max_iters=T, check_every=T), 4),
+    }
+    out = {"cpu_model": _cpu_model(), "host_cores": cores, "statistic": "median of 5 after 1 warm-up",
+           "ms_per_iteration": {}}
+    for threads in (1, cores):
+        used = oracle.set_threads(threads)
+        key = "one_thread" if threads == 1 else "openmp_%d_threads" % used
+        try:
+            out["ms_per_iteration"][key] = {name: _median_iter_ms(fn, it * (1 if threads == 1 else 4))
+                                            for name, (fn, it) in cases.items()}
+        except Exception as ex:
+            out["ms_per_iteration"][key] = {"error": "%s: %s" % (type(ex).__name__, ex)}
+    # time to tolerance on all cores
+    ttg = {}
+    used = oracle.set_threads(cores)
+    t1 = taus.get("C1", 10.0)
+    t0 = time.perf_counter()
+    r = oracle.vomt_solve(a32, b32, EDGES, 1.0, tau=t1, max_iters=400000, check_every=100, tol_gap=TOL, tol_res=TOL)
+    ttg["C1_32x32_k3"] = {"tau": t1, "iters": r["iters"], "seconds": time.perf_counter() - t0, "threads": used,
+                          "converged": bool(r["metrics"]["converged"]), "rel_gap": r["metrics"]["rel_gap"],
+                          "rel_res": r["metrics"]["rel_res"]}
+    t2 = taus.get(1.0, REF_TAU)
+    cap = 10000
+    t0 = time.perf_counter()
+    r = oracle.vomt_solve(a256, b256, EDGES, 1.0, tau=t2, max_iters=cap, check_every=100, tol_gap=TOL, tol_res=TOL)
+    ttg["C2_256x256_alpha1"] = {"tau": t2, "iters": r["iters"], "seconds": time.perf_counter() - t0, "threads": used,
+                                "converged": bool(r["metrics"]["converged"]), "rel_gap": r["metrics"]["rel_gap"],
+                                "rel_res": r["metrics"]["rel_res"],
+                                "note": "bounded: %d iterations on all cores (the GPU needs more than 10^5 to reach "
+                                        "1e-5 on this solve, see time_to_tolerance)" % cap}
+    oracle.set_threads(1)
+    out["time_to_tolerance"] = ttg
+    return out
 
 
 def run_reference(args, rank, world):
@@ -182,34 +276,77 @@ def _summary(r):
             "converged": r["status"] == 0, "engine": r["engine"]}
 
 
+def _matrix_inputs(dev):
+    import torch
+    from paper_1712_10279_gb300 import synthetic as S
+    L0, L1 = S.tensor_field_pair(128, 3, seed=1003)
+    L = S.random_L(3, 3, seed=1003)
+    return L0, L1, L, torch.from_numpy(L0.astype(np.float32)).to(dev), torch.from_numpy(L1.astype(np.float32)).to(dev)
+
+
 def extra_matrix(dev, peak, u_norm=1, w_norm=0):
     """Matrix OMT, 128 x 128 grid of 3 x 3 SPD densities, N = 3 random symmetric L
-    (default norms ||U||_2, ||W||_1; u_norm 3 / w_norm 2 are the nuclear norms)."""
-    import torch
+    (default norms ||U||_2, ||W||_1; u_norm 3 / w_norm 2 are the nuclear norms); tau from
+    momt_tune_tau; to 1e-5 with the 50,000 cap and, for the default norms, without it."""
     import paper_1712_10279_gb300 as V
-    from paper_1712_10279_gb300 import synthetic as S
     n, cap = 128, 50000
-    L0, L1 = S.tensor_field_pair(n, 3, seed=1003)
-    L = S.random_L(3, 3, seed=1003)
-    t0 = torch.from_numpy(L0.astype(np.float32)).to(dev)
-    t1 = torch.from_numpy(L1.astype(np.float32)).to(dev)
-    V.momt_solve(t0, t1, L, 1.0, max_iters=200, check_every=100, u_norm=u_norm, w_norm=w_norm)
-    sol, ms = _gpu_ms(lambda: V.momt_solve(t0, t1, L, 1.0, max_iters=cap, check_every=CHECK_EVERY, tol_gap=TOL,
-                                           tol_res=TOL, u_norm=u_norm, w_norm=w_norm))
+    _, _, L, t0, t1 = _matrix_inputs(dev)
+    (tau, score, _), tune_ms = _gpu_ms(lambda: V.momt_tune_tau(t0, t1, L, 1.0, u_norm=u_norm, w_norm=w_norm,
+                                                               sample_iters=TUNE_ITERS))
+    V.momt_solve(t0, t1, L, 1.0, tau=tau, max_iters=200, check_every=100, u_norm=u_norm, w_norm=w_norm)
+    sol, ms = _gpu_ms(lambda: V.momt_solve(t0, t1, L, 1.0, tau=tau, max_iters=cap, check_every=CHECK_EVERY,
+                                           tol_gap=TOL, tol_res=TOL, u_norm=u_norm, w_norm=w_norm))
     r = sol.result
     gp = n * n * r["iters"]
     gbs = 240.0 * gp / (ms / 1e3) / 1e9
     norms = {(1, 0): "||U||_2 ||W||_1", (3, 2): "||U||_{1,nuc} ||W||_{1,nuc}"}.get((u_norm, w_norm),
                                                                                   "u_norm %d w_norm %d" % (u_norm, w_norm))
-    return dict(workload="matrix OMT 128x128 3x3 (tensor field seed 1003, random L seed 1003), alpha=1, "
-                         "%s, tau=30, to 1e-5, cap %d" % (norms, cap),
-                ms=ms, us_per_iter=1e3 * ms / max(r["iters"], 1), gp_it_per_s=gp / (ms / 1e3),
-                algorithmic_bytes_per_gp_it=240, achieved_GBps=gbs, frac_of_measured_hbm=gbs / peak, **_summary(r))
+    out = dict(workload="matrix OMT 128x128 3x3 (tensor field seed 1003, random L seed 1003), alpha=1, "
+                        "%s, tau tuned (momt_tune_tau), to 1e-5, cap %d" % (norms, cap),
+               tau=tau, tau_tune_ms=tune_ms, ms=ms, us_per_iter=1e3 * ms / max(r["iters"], 1),
+               gp_it_per_s=gp / (ms / 1e3), algorithmic_bytes_per_gp_it=240, achieved_GBps=gbs,
+               frac_of_measured_hbm=gbs / peak, **_summary(r))
+    if (u_norm, w_norm) == (1, 0):
+        sol, ms = _gpu_ms(lambda: V.momt_solve(t0, t1, L, 1.0, tau=tau, max_iters=UNCAPPED, check_every=CHECK_EVERY,
+                                               tol_gap=TOL, tol_res=TOL))
+        out["without_cap"] = dict(cap=UNCAPPED, ms=ms, **_summary(sol.result))
+    return out
 
 
-def extra_batched(dev, cap=5000):
+def extra_time_to_tolerance(dev, taus):
+    """Time to relative gap and residual <= 1e-5 without the 50,000 cap: the benchmark's
+    three solves (cap UNCAPPED) and the 32 x 32 blob case, each at its tuned tau."""
+    import torch
+    import paper_1712_10279_gb300 as V
+    from paper_1712_10279_gb300 import synthetic as S
+    out = {}
+    r0, r1 = S.color_image_pair(N, K, seed=1002)
+    d0, d1 = torch.from_numpy(r0.astype(np.float32)).to(dev), torch.from_numpy(r1.astype(np.float32)).to(dev)
+    for a in ALPHAS:
+        sol, ms = _gpu_ms(lambda: V.solve(d0, d1, EDGES, a, tau=taus[a], max_iters=UNCAPPED, check_every=CHECK_EVERY,
+                                          tol_gap=TOL, tol_res=TOL))
+        row = dict(tau=taus[a], cap=UNCAPPED, ms=ms, **_summary(sol.result))
+        if not row["converged"]:
+            row["reason"] = ("the fixed-tau iteration (the paper's method) has not reached 1e-5 within the cap: at "
+                             "alpha = 10 the channel flux w stays zero until the channel differences of phi reach "
+                             "alpha, which needs a large tau, while the spatial part converges best at a smaller one")
+        out["256x256_alpha=%g" % a] = row
+    a, b = S.blob_pair(32, 3, seed=1001)
+    da, db = torch.from_numpy(a.astype(np.float32)).to(dev), torch.from_numpy(b.astype(np.float32)).to(dev)
+    (tau, _, _), tune_ms = _gpu_ms(lambda: V.tune_tau(da, db, EDGES, 1.0, sample_iters=TUNE_ITERS))
+    sol, ms = _gpu_ms(lambda: V.solve(da, db, EDGES, 1.0, tau=tau, max_iters=UNCAPPED, check_every=CHECK_EVERY,
+                                      tol_gap=TOL, tol_res=TOL))
+    sol_p, ms_p = _gpu_ms(lambda: V.solve(da, db, EDGES, 1.0, tau=1.0, max_iters=UNCAPPED, check_every=CHECK_EVERY,
+                                          tol_gap=TOL, tol_res=TOL))
+    out["32x32_blobs_alpha=1"] = dict(tau=tau, tau_tune_ms=tune_ms, ms=ms, **_summary(sol.result),
+                                      table1_tau_1=dict(ms=ms_p, **_summary(sol_p.result)))
+    return out, tau
+
+
+def extra_batched(dev, cap=20000):
     """512 mixed instances: one persistent batched launch against a host loop of plain
-    single-instance solves, both from zero, both stopped per instance at 1e-5 or `cap`."""
+    single-instance solves, both from zero at the same per-instance tau (from the batch tau
+    tuner), both stopped per instance at 1e-5 or `cap`; and both at the paper's 1e-3."""
     import torch
     import paper_1712_10279_gb300 as V
     from paper_1712_10279_gb300 import synthetic as S
@@ -217,34 +354,37 @@ def extra_batched(dev, cap=5000):
     probs = [dict(n=q["n"], k=q["k"], edges=q["edges"], alpha=1.0) for q in inst]
     bt = V.Batch(probs, [q["rho0"] for q in inst], [q["rho1"] for q in inst], device=dev.index or 0)
     threads, tune_ms = bt.tune(sample_iters=50)
+    (taus, _), tau_tune_ms = _gpu_ms(lambda: bt.tune_tau(sample_iters=500))
     bt.solve(max_iters=100, check_every=100)
-    _, ms_b = _gpu_ms(lambda: bt.solve(max_iters=cap, check_every=CHECK_EVERY, tol_gap=TOL, tol_res=TOL))
-    rb = bt.results
-    path = "grouped" if max(r["blocks"] for r in rb) > 1 or rb[0]["halo"] > 0 else "queue"
     d0 = [torch.from_numpy(q["rho0"].astype(np.float32)).to(dev) for q in inst]
     d1 = [torch.from_numpy(q["rho1"].astype(np.float32)).to(dev) for q in inst]
+    out = dict(workload="512 instances, n in {32..256}, k in {1,3,5}, random connected graphs p=0.6 (seed 1004), "
+                        "alpha=1, per-instance tau from vomt_batch_tune_tau, per-instance stop",
+               batched_threads=threads, tune_ms={str(k_): v for k_, v in tune_ms.items()}, tau_tune_ms=tau_tune_ms)
+    for tol, cap_ in ((TOL, cap), (1e-3, cap)):
+        _, ms_b = _gpu_ms(lambda: bt.solve(max_iters=cap_, check_every=CHECK_EVERY, tol_gap=tol, tol_res=tol))
+        rb = bt.results
+        path = "grouped" if max(r["blocks"] for r in rb) > 1 or rb[0]["halo"] > 0 else "queue"
 
-    def loop():
-        return [V.solve(a, b, q["edges"], 1.0, max_iters=cap, check_every=CHECK_EVERY, tol_gap=TOL,
-                        tol_res=TOL).result for q, a, b in zip(inst, d0, d1)]
+        def loop():
+            return [V.solve(a, b, q["edges"], 1.0, tau=t, max_iters=cap_, check_every=CHECK_EVERY, tol_gap=tol,
+                            tol_res=tol).result for q, a, b, t in zip(inst, d0, d1, taus)]
 
-    rp, ms_p = _gpu_ms(loop)
-    gp_b = sum(q["n"] ** 2 * r["iters"] for q, r in zip(inst, rb))
-    gp_p = sum(q["n"] ** 2 * r["iters"] for q, r in zip(inst, rp))
-    return dict(workload="512 instances, n in {32..256}, k in {1,3,5}, random connected graphs p=0.6 (seed 1004), "
-                         "alpha=1, to 1e-5 per instance, cap %d" % cap,
-                batched_path=path, batched_ms=ms_b, batched_converged=sum(r["status"] == 0 for r in rb),
-                batched_gp_it_per_s=gp_b / (ms_b / 1e3), batched_threads=threads,
-                tune_ms={str(k_): v for k_, v in tune_ms.items()},
-                plain_ms=ms_p, plain_converged=sum(r["status"] == 0 for r in rp),
-                plain_gp_it_per_s=gp_p / (ms_p / 1e3), plain_over_batched_time=ms_p / ms_b,
-                max_cost_diff=max(abs(a["primal"] - b["primal"]) / max(abs(b["primal"]), 1e-30)
-                                  for a, b in zip(rb, rp)))
+        rp, ms_p = _gpu_ms(loop)
+        gp_b = sum(q["n"] ** 2 * r["iters"] for q, r in zip(inst, rb))
+        gp_p = sum(q["n"] ** 2 * r["iters"] for q, r in zip(inst, rp))
+        out["tol=%g" % tol] = dict(
+            cap=cap_, batched_path=path, batched_ms=ms_b, batched_converged=sum(r["status"] == 0 for r in rb),
+            batched_gp_it_per_s=gp_b / (ms_b / 1e3), plain_ms=ms_p, plain_converged=sum(r["status"] == 0 for r in rp),
+            plain_gp_it_per_s=gp_p / (ms_p / 1e3), plain_over_batched_time=ms_p / ms_b,
+            max_cost_diff=max(abs(a["primal"] - b["primal"]) / max(abs(b["primal"]), 1e-30) for a, b in zip(rb, rp)))
+    return out
 
 
-def extra_differentiable(dev, count=64, cap=2000):
-    """64 colour-image pairs at 256 x 256: batched forward solve + envelope backward, and
-    the 200-iteration unrolled gradient, against plain forward solves of the same pairs."""
+def extra_differentiable(dev, count=64, cap=50000, tol=1e-3):
+    """64 colour-image pairs at 256 x 256: batched forward solve to the paper's stopping rule
+    (gap 1e-3, Section 8.1) + envelope backward, and the 200-iteration unrolled gradient,
+    against plain forward solves of the same pairs at the same per-pair tau and tolerance."""
     import torch
     import paper_1712_10279_gb300 as V
     from paper_1712_10279_gb300 import synthetic as S
@@ -252,17 +392,19 @@ def extra_differentiable(dev, count=64, cap=2000):
     pairs = [S.color_image_pair(N, K, seed=2000 + q) for q in range(count)]
     r0 = torch.from_numpy(np.stack([p[0] for p in pairs]).astype(np.float32)).to(dev)
     r1 = torch.from_numpy(np.stack([p[1] for p in pairs]).astype(np.float32)).to(dev)
-    kw = dict(max_iters=cap, check_every=CHECK_EVERY, tol_gap=TOL, tol_res=TOL)
+    bt = V.Batch([dict(n=N, k=K, edges=EDGES, alpha=1.0)] * count, list(r0), list(r1), device=dev.index or 0)
+    (taus, _), tau_tune_ms = _gpu_ms(lambda: bt.tune_tau(sample_iters=TUNE_ITERS))
+    kw = dict(max_iters=cap, check_every=CHECK_EVERY, tol_gap=tol, tol_res=tol)
 
     def fwd_bwd():
         x1 = r1.clone().requires_grad_(True)
         a = torch.tensor(1.0, dtype=torch.float64, device=dev, requires_grad=True)
-        c = A.transport_cost(r0, x1, EDGES, a, engine="batched", **kw)
+        c = A.transport_cost(r0, x1, EDGES, a, engine="batched", taus=taus, **kw)
         c.sum().backward()
         return c
 
     def plain():
-        return [V.solve(r0[q], r1[q], EDGES, 1.0, **kw).result for q in range(count)]
+        return [V.solve(r0[q], r1[q], EDGES, 1.0, tau=taus[q], **kw).result for q in range(count)]
 
     def unrolled():
         out = []
@@ -273,17 +415,110 @@ def extra_differentiable(dev, count=64, cap=2000):
             out.append(float(J))
         return out
 
-    fwd_bwd()
     costs, ms_fb = _gpu_ms(fwd_bwd)
     rp, ms_p = _gpu_ms(plain)
     _, ms_u = _gpu_ms(unrolled)
-    return dict(workload="%d colour-image pairs 256x256 k=3 (seeds 2000..), alpha=1, to 1e-5, cap %d; "
-                         "unrolled T=200, checkpoints every 20" % (count, cap),
-                forward_backward_batched_ms=ms_fb, plain_forward_loop_ms=ms_p,
+    return dict(workload="%d colour-image pairs 256x256 k=3 (seeds 2000..), alpha=1, per-pair tau from "
+                         "vomt_batch_tune_tau, forward to rel gap and rel res <= %g (Section 8.1's rule), cap %d; "
+                         "unrolled T=200, checkpoints every 20" % (count, tol, cap),
+                tau_tune_ms=tau_tune_ms, forward_backward_batched_ms=ms_fb, plain_forward_loop_ms=ms_p,
                 fwd_bwd_over_plain_time=ms_fb / ms_p, unrolled_fwd_bwd_ms=ms_u,
-                plain_converged=sum(r["status"] == 0 for r in rp),
+                plain_converged=sum(r["status"] == 0 for r in rp), plain_iters_mean=statistics.mean(r["iters"] for r in rp),
                 max_cost_diff=float(max(abs(float(c) - r["primal"]) / max(abs(r["primal"]), 1e-30)
                                         for c, r in zip(costs.detach().cpu(), rp))))
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    cplx = np.iscomplexobj(a) or np.iscomplexobj(b)
+    a = a.astype(np.complex128 if cplx else np.float64)
+    b = b.astype(np.complex128 if cplx else np.float64)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def _errs(gpu, ref, names):
+    """Relative L2 errors of the GPU fields against the oracle's, and of P and D."""
+    out = {"rel_l2_" + k_: _rel(gpu[k_], ref[k_]) for k_ in names}
+    out["rel_err_primal"] = abs(gpu["primal"] - ref["primal"]) / max(abs(ref["primal"]), 1e-300)
+    out["rel_err_dual"] = abs(gpu["dual"] - ref["dual"]) / max(abs(ref["dual"]), 1e-300)
+    return out
+
+
+def extra_fp32_vs_fp64(dev, headline, tau_mat):
+    """FP32 GPU results against the FP64 oracle at equal iteration counts (same inputs, same
+    tau): the benchmark workload (the oracle's cpu_baseline sample), matrix OMT 128^2, one
+    instance of the batched engine, a 3-D volume and complex Hermitian matrix OMT."""
+    import torch
+    import oracle
+    import paper_1712_10279_gb300 as V
+    from paper_1712_10279_gb300 import synthetic as S
+    oracle.set_threads(_cpu_cores())
+    out = {}
+    if headline is not None:
+        ref, T, tau = headline
+        r0, r1 = S.color_image_pair(N, K, seed=1002)
+        d0, d1 = torch.from_numpy(r0.astype(np.float32)).to(dev), torch.from_numpy(r1.astype(np.float32)).to(dev)
+        sol = V.solve(d0, d1, EDGES, 1.0, tau=tau, max_iters=T, check_every=100)
+        g = dict(phi=sol.phi.cpu().numpy(), u=sol.u.cpu().numpy(), w=sol.w.cpu().numpy(),
+                 primal=sol.result["primal"], dual=sol.result["dual"])
+        o = dict(phi=ref["phi"], u=np.stack([ref["ux"], ref["uy"]]), w=ref["w"], primal=ref["metrics"]["primal"],
+                 dual=ref["metrics"]["dual"])
+        out["vector_256x256_k3_alpha1"] = dict(iters=T, tau=tau, **_errs(g, o, ("phi", "u", "w")))
+    L0, L1, L, t0, t1 = _matrix_inputs(dev)
+    T = 300
+    sol = V.momt_solve(t0, t1, L, 1.0, tau=tau_mat, max_iters=T, check_every=100)
+    ref = oracle.momt_solve(L0.astype(np.float32).astype(np.float64), L1.astype(np.float32).astype(np.float64), L,
+                            1.0, tau=tau_mat, max_iters=T, check_every=100)
+    out["matrix_128x128_3x3"] = dict(iters=T, tau=tau_mat, **_errs(
+        dict(Phi=sol.Phi.cpu().numpy(), U=sol.U.cpu().numpy(), W=sol.W.cpu().numpy(), primal=sol.result["primal"],
+             dual=sol.result["dual"]),
+        dict(Phi=ref["Phi"], U=np.stack([ref["Ux"], ref["Uy"]]), W=ref["W"].reshape(sol.W.shape),
+             primal=ref["metrics"]["primal"], dual=ref["metrics"]["dual"]), ("Phi", "U", "W")))
+    inst = S.batched_instances(8, seed=1004, sides=(64, 96), ks=(3, 5))
+    bt = V.Batch([dict(n=q["n"], k=q["k"], edges=q["edges"], alpha=1.0) for q in inst],
+                 [q["rho0"] for q in inst], [q["rho1"] for q in inst], device=dev.index or 0)
+    T = 1000
+    bt.solve(max_iters=T, check_every=100)
+    q = 0
+    x = inst[q]
+    ref = oracle.vomt_solve(x["rho0"].astype(np.float32).astype(np.float64),
+                            x["rho1"].astype(np.float32).astype(np.float64), x["edges"], 1.0, max_iters=T,
+                            check_every=100)
+    out["batched_instance_n%d_k%d" % (x["n"], x["k"])] = dict(iters=T, path=bt.results[q]["engine"], **_errs(
+        dict(phi=bt.phi(q).cpu().numpy(), u=bt.u(q).cpu().numpy(), w=bt.w(q).cpu().numpy(),
+             primal=bt.results[q]["primal"], dual=bt.results[q]["dual"]),
+        dict(phi=ref["phi"], u=np.stack([ref["ux"], ref["uy"]]), w=ref["w"], primal=ref["metrics"]["primal"],
+             dual=ref["metrics"]["dual"]), ("phi", "u", "w")))
+    n3 = 48
+    a, b = S.blob_pair3(n3, 3, seed=1008)
+    a, b = a * n3 ** 3, b * n3 ** 3
+    T = 200
+    sol = V.solve3d(torch.from_numpy(a.astype(np.float32)).to(dev), torch.from_numpy(b.astype(np.float32)).to(dev),
+                    EDGES, 1.0, max_iters=T, check_every=100)
+    ref = oracle.vomt3_solve(a.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64), EDGES,
+                             1.0, max_iters=T, check_every=100)
+    out["volume_48^3_k3"] = dict(iters=T, tma_form=bool(sol.result["variant"]), **_errs(
+        dict(phi=sol.phi.cpu().numpy(), u=sol.u.cpu().numpy(), w=sol.w.cpu().numpy(), primal=sol.result["primal"],
+             dual=sol.result["dual"]),
+        dict(phi=ref["phi"], u=np.stack([ref["ux"], ref["uy"], ref["uz"]]), w=ref["w"],
+             primal=ref["metrics"]["primal"], dual=ref["metrics"]["dual"]), ("phi", "u", "w")))
+    nz = 48
+    ha, hb = S.hermitian_field_pair(nz, 2, seed=1010)
+    ha, hb = ha * nz * nz, hb * nz * nz
+    Lz = S.random_hermitian_L(2, 3, seed=1010)
+    T = 300
+    sol = V.momt_solve_complex(torch.from_numpy(ha.astype(np.complex64)).to(dev),
+                               torch.from_numpy(hb.astype(np.complex64)).to(dev), Lz, 1.0, max_iters=T,
+                               check_every=100)
+    ref = oracle.zmomt_solve(ha.astype(np.complex64).astype(np.complex128),
+                             hb.astype(np.complex64).astype(np.complex128), Lz, 1.0, max_iters=T, check_every=100)
+    out["complex_hermitian_48x48_2x2"] = dict(iters=T, **_errs(
+        dict(Phi=sol.Phi.cpu().numpy(), W=sol.W.cpu().numpy(), primal=sol.result["primal"], dual=sol.result["dual"]),
+        dict(Phi=ref["Phi"], W=ref["W"].reshape(sol.W.shape), primal=ref["metrics"]["primal"],
+             dual=ref["metrics"]["dual"]), ("Phi", "W")))
+    oracle.set_threads(1)
+    return out
 
 
 def extra_hbm_bound(dev, peak, n=2048, iters=1000):
@@ -402,13 +637,27 @@ def extra_volume(dev, peak, iters=500):
     return out
 
 
-def extras(dev, only=None):
+def extras(dev, only=None, taus=None, headline_ref=None):
     peak, _ = _peaks()
     out = {}
-    for name, fn in (("matrix_128", lambda: extra_matrix(dev, peak)),
+    state = {}
+
+    def matrix():
+        m = extra_matrix(dev, peak)
+        state["tau_mat"] = m["tau"]
+        return m
+
+    def ttt():
+        o, tau_c1 = extra_time_to_tolerance(dev, taus)
+        state["tau_c1"] = tau_c1
+        return o
+
+    for name, fn in (("time_to_tolerance", ttt),
+                     ("matrix_128", matrix),
                      ("matrix_128_nuclear", lambda: extra_matrix(dev, peak, u_norm=3, w_norm=2)),
                      ("batched_vs_plain", lambda: extra_batched(dev)),
                      ("differentiable", lambda: extra_differentiable(dev)),
+                     ("fp32_vs_fp64", lambda: extra_fp32_vs_fp64(dev, headline_ref, state.get("tau_mat", 3e4))),
                      ("regularised", lambda: extra_regularised(dev, peak)),
                      ("complex_hermitian_128", lambda: extra_complex(dev, peak)),
                      ("hbm_bound", lambda: extra_hbm_bound(dev, peak)),
@@ -421,7 +670,18 @@ def extras(dev, only=None):
         except Exception as ex:      # reported, never hidden: the line says what failed
             out[name] = {"error": "%s: %s" % (type(ex).__name__, ex)}
         out[name]["wall_s"] = time.perf_counter() - t0
-    return out
+    return out, state
+
+
+def tune_taus(d0, d1, alphas):
+    """The dual step tau of every alpha of the workload, by the library's tuner."""
+    import paper_1712_10279_gb300 as V
+    taus, info = {}, {}
+    for a in alphas:
+        (tau, score, grid), ms = _gpu_ms(lambda: V.tune_tau(d0, d1, EDGES, a, sample_iters=TUNE_ITERS))
+        taus[a] = tau
+        info["alpha=%g" % a] = {"tau": tau, "score": score, "tune_ms": ms}
+    return taus, info
 
 
 def run_ours(args, rank, world, local_rank):
@@ -443,11 +703,12 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
 
     alphas, cap = args.alphas, args.cap
+    taus, tune_info = tune_taus(d0, d1, alphas)
 
     def step(results):
         for a in alphas:
-            sol = V.solve(d0, d1, EDGES, a, max_iters=cap, check_every=CHECK_EVERY, tol_gap=TOL, tol_res=TOL,
-                          engine=args.engine)
+            sol = V.solve(d0, d1, EDGES, a, tau=taus[a], max_iters=cap, check_every=CHECK_EVERY, tol_gap=TOL,
+                          tol_res=TOL, engine=args.engine)
             results.append(sol.result)
 
     for _ in range(args.warmup):
@@ -485,8 +746,8 @@ def run_ours(args, rank, world, local_rank):
             t0 = time.perf_counter()
             e2e_iters = 0
             for a in alphas:
-                sol = V.solve_host(h0, h1, EDGES, a, max_iters=cap, check_every=CHECK_EVERY, tol_gap=TOL,
-                                   tol_res=TOL, engine=args.engine, device=local_rank)
+                sol = V.solve_host(h0, h1, EDGES, a, tau=taus[a], max_iters=cap, check_every=CHECK_EVERY,
+                                   tol_gap=TOL, tol_res=TOL, engine=args.engine, device=local_rank)
                 e2e_iters += sol.result["iters"]
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
         e2e_value = world * N * N * e2e_iters / (statistics.mean(e2e_ms) / 1e3)
@@ -511,17 +772,21 @@ def run_ours(args, rank, world, local_rank):
     per_alpha = {}
     for q, a in enumerate(alphas):
         rs = [results[s * len(alphas) + q] for s in range(args.steps)]
-        per_alpha["alpha=%g" % a] = {"iters": rs[-1]["iters"], "rel_gap": rs[-1]["rel_gap"],
+        per_alpha["alpha=%g" % a] = {"tau": taus[a], "iters": rs[-1]["iters"], "rel_gap": rs[-1]["rel_gap"],
                                      "rel_res": rs[-1]["rel_res"], "primal": rs[-1]["primal"],
-                                     "converged": rs[-1]["status"] == 0}
+                                     "converged": rs[-1]["status"] == 0,
+                                     "ms_mean_of_step": statistics.mean(step_ms) / len(alphas)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(alphas, cap), "n": N, "k": K, "edges": l, "alphas": list(alphas),
-                   "tol": TOL, "cap": cap, "check_every": CHECK_EVERY, "engine": engine,
+                   "tau": {"alpha=%g" % a: taus[a] for a in alphas}, "tol": TOL, "cap": cap,
+                   "check_every": CHECK_EVERY, "engine": engine,
                    "l2": "flushed (512 MB write) between timed steps",
                    "parallelism": "independent replicas, one per GPU" if world > 1 else "single GPU"},
+        "tau_tuning": dict(tune_info, note="vomt_tune_tau once per alpha before the warm-up (outside the timed "
+                                           "region), sample_iters=%d" % TUNE_ITERS),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": traffic,
                      "kernel": "k_resident" if engine == "resident" else "k_step",
@@ -535,11 +800,21 @@ def run_ours(args, rank, world, local_rank):
                                                "d2h_bytes_per_step": d2h},
         "clocks": clocks,
     }
-    if world == 1 and not args.no_extras:
-        line["extras"] = extras(dev)
+    headline_ref = None
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample()
-        line["cpu_baseline"]["host_cores_available"] = _cpu_cores()
+        samp = oracle_sample(tau=taus.get(1.0, REF_TAU), keep_state=True)
+        headline_ref = (samp.pop("_state"), samp.pop("_iters"), taus.get(1.0, REF_TAU))
+        samp["host_cores_available"] = _cpu_cores()
+        line["cpu_baseline"] = samp
+    if world == 1 and not args.no_extras:
+        line["extras"], st = extras(dev, taus=taus, headline_ref=headline_ref)
+        if not args.no_cpu_baseline:
+            try:
+                line["cpu_baseline"]["legs"] = cpu_legs(dict(taus, C1=st.get("tau_c1", 10.0)))
+            except Exception as ex:
+                line["cpu_baseline"]["legs"] = {"error": "%s: %s" % (type(ex).__name__, ex)}
+        fe = line["extras"].get("fp32_vs_fp64", {})
+        line["fp32_vs_fp64"] = {k_: v for k_, v in fe.items() if k_ != "wall_s"}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -566,7 +841,13 @@ def main():
         import torch
         dev = torch.device("cuda", local_rank)
         torch.cuda.set_device(dev)
-        print(json.dumps({"extras": extras(dev, only=args.only_extra)}), flush=True)
+        import paper_1712_10279_gb300 as V
+        from paper_1712_10279_gb300 import synthetic as S
+        r0, r1 = S.color_image_pair(N, K, seed=1002)
+        d0 = torch.from_numpy(r0.astype(np.float32)).to(dev)
+        d1 = torch.from_numpy(r1.astype(np.float32)).to(dev)
+        taus, _ = tune_taus(d0, d1, ALPHAS)
+        print(json.dumps({"extras": extras(dev, only=args.only_extra, taus=taus)[0]}), flush=True)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -8,8 +8,9 @@
  * ---------------------------------------
  * Grid.  An n x n grid on [0,1]^2 with spacing h = 1/(n-1) (Section 7 and
  *   Appendix A).  Every grid field is FP32, stored plane by plane as
- *   [plane][j][i] with the x index i fastest, densely packed (row pitch n):
- *   element (i, j) of plane p sits at (p*n + j)*n + i.
+ *   [plane][j][i] with the x index i fastest: element (i, j) of plane p sits at
+ *   (p*n + j)*pitch + i, with the row pitch given by vomt_params.pitch (or the
+ *   pitch argument of vomt_backward) and n (dense) by default.
  * Densities.  Cell masses (the finite-volume averages of Appendix A).  For the
  *   vector problem rho0 and rho1 are [k][n][n] and must be nonnegative with
  *   equal totals over all cells and channels (the constraint of eq. (vomt)
@@ -45,7 +46,7 @@ extern "C" {
 #define VOMT_OK                      0
 #define VOMT_NOT_CONVERGED           1
 #define VOMT_ERR_BAD_ARG            -1   /* a size, pointer or parameter is invalid */
-#define VOMT_ERR_MASS_MISMATCH      -2   /* |sum rho0 - sum rho1| > 1e-5 max(sum rho0, sum rho1) */
+#define VOMT_ERR_MASS_MISMATCH      -2   /* |sum rho0 - sum rho1| > 1e-6 max(sum rho0, sum rho1) */
 #define VOMT_ERR_NEGATIVE_DENSITY   -3   /* some density entry < 0 */
 #define VOMT_ERR_GRAPH              -4   /* channel graph not connected, self loop or repeated edge */
 #define VOMT_ERR_L_KERNEL           -5   /* ker grad_L on symmetric matrices is larger than span{I} */
@@ -111,6 +112,13 @@ typedef struct {
                             includes the term and D subtracts sum dist_2(., dual ball)^2 /
                             (4 eps).  0 (default) is the plain problem.  Vector OMT, forward
                             solves (vomt_unrolled_grad and momt_solve take eps = 0 only). */
+    int pitch;           /* row pitch in floats of every grid array of vomt_solve, vomt_solve_host
+                            and momt_solve: element (i, j) of plane p at (p*n + j)*pitch + i,
+                            so that rows may be padded (e.g. to 16 bytes, or views of larger
+                            arrays).  0 (default) means pitch = n (dense); else pitch >= n.
+                            Pitched arrays are staged densely by the library (one 2-D copy per
+                            array in, one per output array out), so the solve itself is the
+                            same.  The other entry points take dense arrays. */
 } vomt_params;
 
 typedef struct {
@@ -225,12 +233,14 @@ int vomt_set_wait_policy(vomt_ctx *ctx, double budget_ms, int drop_exchange);
  * independent of the densities of <phi, rho1 - rho0>, so dV/drho1 = phi* and
  * dV/drho0 = -phi*, with the constant the dual leaves free fixed by making phi*
  * zero-mean over all cells and channels; the primal is linear in alpha, so
- * dV/dalpha = sum_ij ||w*_ij||_w.  phi: device [batch][k][n][n], w: device
- * [batch][l][n][n] (a converged iterate, e.g. from vomt_solve).  grad_scale:
- * device [batch] factors (the upstream gradient) or NULL for 1.  Outputs (any
- * may be NULL): d_rho0, d_rho1 device [batch][k][n][n], d_alpha device [batch].
- * Asynchronous on `stream`.  Errors: BAD_ARG, CUDA. */
-int vomt_backward(vomt_ctx *ctx, int batch, int n, int k, int n_edges, int w_norm, const float *phi,
+ * dV/dalpha = sum_ij ||w*_ij||_w.  phi: device [batch][k][n][pitch], w: device
+ * [batch][l][n][pitch] (a converged iterate, e.g. from vomt_solve), rows of n
+ * floats at a row pitch of `pitch` floats (0 means n).  grad_scale: device
+ * [batch] factors (the upstream gradient) or NULL for 1.  Outputs (any may be
+ * NULL): d_rho0, d_rho1 device [batch][k][n][pitch] (the padding is not
+ * written), d_alpha device [batch].  Asynchronous on `stream`.  Errors:
+ * BAD_ARG (also pitch in (0, n)), CUDA. */
+int vomt_backward(vomt_ctx *ctx, int batch, int n, int pitch, int k, int n_edges, int w_norm, const float *phi,
                   const float *w, const float *grad_scale, float *d_rho0, float *d_rho1, float *d_alpha,
                   void *stream);
 
@@ -402,6 +412,46 @@ int momt_solve3d(vomt_ctx *ctx, int n, int k, const float *Lam0, const float *La
                  void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Tuning the dual step tau                                                   */
+/* ------------------------------------------------------------------------ */
+/* Sections 7.1-7.3 tie the primal steps to tau (mu = 1/(32 tau (n-1)^2),
+ * nu = 1/(4 tau lambda_max)), so that every tau > 0 meets the convergence
+ * condition, and tune tau per experiment "for the fastest convergence" (Tables 1
+ * and 3 list the values).  The best tau scales with the densities and with how
+ * far mass moves, so these calls measure it: runs of the solve itself from the
+ * zero iterate over the grid tau_j = tau_paper * 10^((j - 1) / 2),
+ * j = 0 .. VOMT_TAU_GRID - 1 (tau_paper: Table 1's or Table 3's value for n),
+ * scored by max(rel_gap, rel_res) at the end of the run. */
+#define VOMT_TAU_GRID 10
+
+/* Vector OMT: successive halving on the grid (every tau runs sample_iters
+ * iterations, the best 4 twice as many, the best 2 four times as many), then
+ * the winner's neighbours tau * 10^(+-1/4) at that length; about 34 sample_iters
+ * iterations in all.  Arguments as vomt_solve; p supplies norms, engine and eps
+ * (its tau, mu, nu, iteration and tolerance fields are ignored).  u, w, phi are
+ * device scratch of vomt_solve's shapes, overwritten.  Outputs (host, any may be
+ * NULL): *best_tau, *best_score (its score at the longest run),
+ * grid_scores[VOMT_TAU_GRID] (the score of every grid point after sample_iters).
+ * Returns after the work finished.  Errors: those of vomt_solve (a candidate
+ * whose iterate became non-finite only scores +infinity). */
+int vomt_tune_tau(vomt_ctx *ctx, int n, const float *rho0, const float *rho1, const vomt_graph *g,
+                  double alpha, const vomt_params *p, int sample_iters, float *u, float *w, float *phi,
+                  double *best_tau, double *best_score, double *grid_scores, void *stream);
+
+/* Matrix OMT: the same search through momt_solve (arguments as momt_solve). */
+int momt_tune_tau(vomt_ctx *ctx, int n, int k, const float *Lam0, const float *Lam1, int N, const double *L,
+                  double alpha, const vomt_params *p, int sample_iters, float *U, float *W, float *Phi,
+                  double *best_tau, double *best_score, double *grid_scores, void *stream);
+
+/* Batched vector OMT: every grid point is run once for the whole batch
+ * (vomt_solve_batched, sample_iters iterations, instance q at tau_j of its own
+ * n), and each instance keeps its best: taus[q] (host, count entries, required)
+ * receives it, ready for inst[q].tau; scores[q] (host, may be NULL) its score.
+ * Overwrites the arena's u, w, phi.  Errors: those of vomt_solve_batched. */
+int vomt_batch_tune_tau(vomt_ctx *ctx, int count, const vomt_instance *inst, float *arena,
+                        const vomt_params *p, int sample_iters, double *taus, double *scores);
+
+/* ------------------------------------------------------------------------ */
 /* Allocation-free solve.  The paper has no counterpart: this is a            */
 /* deployment feature of this library.                                        */
 /* ------------------------------------------------------------------------ */
@@ -412,25 +462,30 @@ int momt_solve3d(vomt_ctx *ctx, int n, int k, const float *Lam0, const float *La
 #define VOMT_NOALLOC_SCRATCH_BYTES (16u << 20)
 
 /* The vomt_solve computation (streaming engine) for callers that cannot
- * allocate device memory: code running during CUDA graph capture, where
- * cudaMalloc is not allowed; applications whose device memory belongs to one
- * custom pool; plug-ins that must not grow the process footprint after
- * start-up.  It needs no context and never allocates or frees memory: its
- * scratch is one fixed array of VOMT_NOALLOC_SCRATCH_BYTES in the library's
- * device image, which every GPU that loads the library holds until the
- * process exits.
+ * allocate device memory: applications whose device memory belongs to one
+ * custom pool or allocator, which a cudaMalloc behind its back would fragment
+ * or overcommit; plug-ins and long-running services that must not grow the
+ * process footprint, or meet an out-of-memory failure, after start-up.  It
+ * needs no context and never allocates or frees memory: its scratch is one
+ * fixed array of VOMT_NOALLOC_SCRATCH_BYTES in the library's device image,
+ * which every GPU that loads the library holds until the process exits.
  *   - Runs on the calling thread's current CUDA device; `stream` must belong
  *     to it.  The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress), a one-time set-up per device.
+ *   - The call reads its stopping flag and results back and synchronises
+ *     `stream` while it runs, so it cannot be recorded into a CUDA graph: a
+ *     stream under capture is refused with VOMT_ERR_BAD_ARG before any GPU
+ *     work, leaving the capture intact.
  *   - Every call shares the one array and overwrites it (the status block is
  *     cleared at the start of each call), so calls that overlap on the GPU --
  *     from other streams or host threads -- race and give wrong results.
  *     Serialise them.
- *   - Arguments, layouts and results are those of vomt_solve; p->engine is
- *     ignored (always the streaming engine), and vomt_history() does not see
- *     these solves.  The call synchronises `stream` to read its results.
+ *   - Arguments, layouts, step-size rules, checks and results are those of
+ *     vomt_solve; p->engine and p->halo are ignored (always the streaming
+ *     engine), and vomt_history() does not see these solves.
  *   - Problems whose scratch would exceed the array return VOMT_ERR_TOO_LARGE
- *     before any GPU work.  `error` (may be NULL) receives a static message.
+ *     before any GPU work.  `error` (may be NULL) receives a message, valid
+ *     until the next call on the same host thread.
  */
 int vomt_solve_noalloc(int n, const float *rho0, const float *rho1, const vomt_graph *g,
                        double alpha, const vomt_params *p, float *u, float *w, float *phi,

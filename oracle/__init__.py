@@ -32,23 +32,54 @@ U_L12, U_L2, U_L1, U_NUC = 0, 1, 2, 3      # U_NUC: matrix OMT only (||U_x||_nuc
 W_L1, W_L2, W_NUC = 0, 1, 2                # W_NUC: matrix OMT only (sum_s ||W_s||_nuc)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into ``libvomt_oracle.so`` (plain gcc, no fast-math)."""
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
+_OMP_LIB_PATH = os.path.join(_HERE, "libvomt_oracle_omp.so")
+
+
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle into ``libvomt_oracle.so`` (plain gcc, no fast-math).  With
+    ``openmp`` the same source is built with -fopenmp into ``libvomt_oracle_omp.so``:
+    the loops over grid points run on several threads, with bit-identical results."""
+    path = _OMP_LIB_PATH if openmp else _LIB_PATH
+    if (not force and os.path.exists(path)
+            and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+        return path
     fd, tmp = tempfile.mkstemp(suffix=".so", dir=_HERE)
     os.close(fd)
-    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    extra = ["-fopenmp", "-DORC_OPENMP"] if openmp else []
+    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", *extra, "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
-def _load():
+_serial_lib = None
+_omp_lib = None
+
+
+def set_threads(threads: int) -> int:
+    """Run the following oracle calls on `threads` host threads (1: the one-thread build,
+    the default; more: the OpenMP build).  Returns the threads the library will use."""
+    global _lib, _serial_lib, _omp_lib
+    if threads <= 1:
+        if _serial_lib is None:
+            _lib = None
+            _serial_lib = _load()
+        _lib = _serial_lib
+        return 1
+    if _omp_lib is None:
+        if _serial_lib is None:
+            _serial_lib = _load()
+        _lib = None
+        _omp_lib = _load(openmp=True)
+    _lib = _omp_lib
+    _lib.orc_set_threads(int(threads))
+    return int(_lib.orc_max_threads())
+
+
+def _load(openmp: bool = False):
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
+        _lib = ctypes.CDLL(build(openmp=openmp))
         d, i, p = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
         sig = {
             "orc_shrink1": (d, [d, d]),
@@ -95,6 +126,8 @@ def _load():
             "orc_spectral_norm": (d, [i, p]),
             "orc_shrink_nuc": (None, [i, p, d, p]),
             "orc_vomt_unrolled_grad": (d, [i, i, i, p, p, p, p, p, d, d, d, d, i, i, p, p, p]),
+            "orc_set_threads": (None, [i]),
+            "orc_max_threads": (i, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -365,6 +398,8 @@ def momt_solve(Lam0, Lam1, L, alpha=1.0, tau=None, mu=None, nu=None, u_norm=U_L2
     Lam0, Lam1, L = _f64(Lam0), _f64(Lam1), _f64(L)
     N, k = L.shape[0], L.shape[1]
     n = Lam0.shape[-1]
+    if k > 8 or N * k * k > 512:
+        raise ValueError("k <= 8 and N k^2 <= 512")
     if tau is None:
         tau = default_tau_matrix(n)
     if mu is None or nu is None:

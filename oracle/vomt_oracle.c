@@ -60,6 +60,37 @@
 
 #define ORC_NMET 8
 
+/* Built with -fopenmp -DORC_OPENMP (the benchmark's multi-core CPU baseline),
+ * the loops over grid points of the iterations run on several threads.  Only
+ * loops whose iterations are independent are split, and nothing inside a point
+ * changes order, so the results are bit-identical to the one-thread build;
+ * the reductions of the metrics stay serial. */
+#ifdef ORC_OPENMP
+#include <omp.h>
+#define ORC_PARALLEL_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define ORC_PARALLEL_FOR
+#endif
+
+/* Threads of the multi-core build (a no-op in the one-thread build). */
+void orc_set_threads(int t)
+{
+#ifdef ORC_OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
+int orc_max_threads(void)
+{
+#ifdef ORC_OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 #define AT(c, j, i) (((size_t)(c) * (size_t)n + (size_t)(j)) * (size_t)n + (size_t)(i))
 
 /* ------------------------------------------------------------------------ */
@@ -187,6 +218,7 @@ void orc_grad_G(int n, int k, int l, const int *ea, const int *eb, const double 
     for (int e = 0; e < l; ++e) {
         int lo = ea[e] < eb[e] ? ea[e] : eb[e], hi = ea[e] < eb[e] ? eb[e] : ea[e];
         double ic = 1.0 / edge_cost(cost, e);
+        ORC_PARALLEL_FOR
         for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i)
                 g[AT(e, j, i)] = ic * (phi[AT(lo, j, i)] - phi[AT(hi, j, i)]);
@@ -201,6 +233,7 @@ void orc_div_G(int n, int k, int l, const int *ea, const int *eb, const double *
     for (int e = 0; e < l; ++e) {
         int lo = ea[e] < eb[e] ? ea[e] : eb[e], hi = ea[e] < eb[e] ? eb[e] : ea[e];
         double ic = 1.0 / edge_cost(cost, e);
+        ORC_PARALLEL_FOR
         for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i) {
                 double v = ic * y[AT(e, j, i)];
@@ -221,6 +254,7 @@ void orc_grad(int n, int planes, const double *phi, double *gx, double *gy)
 {
     double ih = (double)(n - 1);
     for (int c = 0; c < planes; ++c)
+        ORC_PARALLEL_FOR
         for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i) {
                 gx[AT(c, j, i)] = (i < n - 1) ? ih * (phi[AT(c, j, i + 1)] - phi[AT(c, j, i)]) : 0.0;
@@ -234,6 +268,7 @@ void orc_div(int n, int planes, const double *ux, const double *uy, double *out)
 {
     double ih = (double)(n - 1);
     for (int c = 0; c < planes; ++c)
+        ORC_PARALLEL_FOR
         for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i) {
                 double xl = (i > 0) ? ux[AT(c, j, i - 1)] : 0.0;
@@ -288,29 +323,33 @@ void orc_div_L_point(int k, int N, const double *L, const double *Z, double *Y)
 void orc_grad_L(int n, int k, int N, const double *L, const double *X, double *Z)
 {
     int kk = k * k;
-    double *x = (double *)malloc(sizeof(double) * (size_t)kk);
-    double *z = (double *)malloc(sizeof(double) * (size_t)kk * N);
-    for (int j = 0; j < n; ++j)
+    ORC_PARALLEL_FOR
+    for (int j = 0; j < n; ++j) {
+        double *x = (double *)malloc(sizeof(double) * (size_t)kk);
+        double *z = (double *)malloc(sizeof(double) * (size_t)kk * N);
         for (int i = 0; i < n; ++i) {
             for (int q = 0; q < kk; ++q) x[q] = X[AT(q, j, i)];
             orc_grad_L_point(k, N, L, x, z);
             for (int q = 0; q < kk * N; ++q) Z[AT(q, j, i)] = z[q];
         }
-    free(x); free(z);
+        free(x); free(z);
+    }
 }
 
 void orc_div_L(int n, int k, int N, const double *L, const double *Z, double *Y)
 {
     int kk = k * k;
-    double *z = (double *)malloc(sizeof(double) * (size_t)kk * N);
-    double *y = (double *)malloc(sizeof(double) * (size_t)kk);
-    for (int j = 0; j < n; ++j)
+    ORC_PARALLEL_FOR
+    for (int j = 0; j < n; ++j) {
+        double *z = (double *)malloc(sizeof(double) * (size_t)kk * N);
+        double *y = (double *)malloc(sizeof(double) * (size_t)kk);
         for (int i = 0; i < n; ++i) {
             for (int q = 0; q < kk * N; ++q) z[q] = Z[AT(q, j, i)];
             orc_div_L_point(k, N, L, z, y);
             for (int q = 0; q < kk; ++q) Y[AT(q, j, i)] = y[q];
         }
-    free(z); free(y);
+        free(z); free(y);
+    }
 }
 
 /* The k^2 x k^2 matrix of -Delta_L = -div_L grad_L acting on vec(X) (row-major
@@ -639,7 +678,6 @@ int orc_vomt_solve(int n, int k, int l, const int *ea, const int *eb, const doub
     double *bw = (double *)malloc(sizeof(double) * (nl ? nl : 1));
     double *dv = (double *)malloc(sizeof(double) * nk), *dg = (double *)malloc(sizeof(double) * nk);
     double *pphi = (double *)malloc(sizeof(double) * nk);
-    double a[32], b[32], x[64];
     int nh = 0, t = 0;
     if (check_every <= 0) check_every = max_iters > 0 ? max_iters : 1;
     /* With the regulariser eps ||.||_2^2 (conclusions of the paper), the primal
@@ -654,7 +692,9 @@ int orc_vomt_solve(int n, int k, int l, const int *ea, const int *eb, const doub
     for (t = 1; t <= max_iters; ++t) {
         /* u-update: shrink of u + mu grad phi with threshold mu */
         orc_grad(n, k, phi, gx, gy);
+        ORC_PARALLEL_FOR
         for (size_t p = 0; p < nn; ++p) {
+            double a[32], b[32];
             for (int c = 0; c < k; ++c) {
                 a[c] = (ux[c * nn + p] + mu * gx[c * nn + p]) * su;
                 b[c] = (uy[c * nn + p] + mu * gy[c * nn + p]) * su;
@@ -665,19 +705,23 @@ int orc_vomt_solve(int n, int k, int l, const int *ea, const int *eb, const doub
         /* w-update: shrink of w + nu grad_G phi with threshold alpha nu */
         if (l) {
             orc_grad_G(n, k, l, ea, eb, cost, phi, gg);
+            ORC_PARALLEL_FOR
             for (size_t p = 0; p < nn; ++p) {
+                double x[64];
                 for (int e = 0; e < l; ++e) x[e] = (w[e * nn + p] + nu * gg[e * nn + p]) * sw;
                 shrink_w_point(l, w_norm, alpha * nu * sw, x);
                 for (int e = 0; e < l; ++e) nw[e * nn + p] = x[e];
             }
         }
         /* extrapolation and dual ascent */
+        ORC_PARALLEL_FOR
         for (size_t q = 0; q < nk; ++q) { bx[q] = 2.0 * nux[q] - ux[q]; by[q] = 2.0 * nuy[q] - uy[q]; }
         for (size_t q = 0; q < nl; ++q) bw[q] = 2.0 * nw[q] - w[q];
         orc_div(n, k, bx, by, dv);
         if (l) orc_div_G(n, k, l, ea, eb, cost, bw, dg);
         else for (size_t q = 0; q < nk; ++q) dg[q] = 0.0;
         memcpy(pphi, phi, sizeof(double) * nk);
+        ORC_PARALLEL_FOR
         for (size_t q = 0; q < nk; ++q) phi[q] = phi[q] + tau * (dv[q] + dg[q] + rho1[q] - rho0[q]);
 
         int check = (t % check_every == 0) || (t == max_iters);
@@ -971,14 +1015,14 @@ int orc_momt_solve(int n, int k, int N, const double *L, const double *Lam0, con
     double *bw = (double *)malloc(sizeof(double) * nw);
     double *dv = (double *)malloc(sizeof(double) * nk), *dl = (double *)malloc(sizeof(double) * nk);
     double *pPhi = (double *)malloc(sizeof(double) * nk);
-    double *v = (double *)malloc(sizeof(double) * 2 * kk), *o = (double *)malloc(sizeof(double) * 2 * kk);
-    double *xw = (double *)malloc(sizeof(double) * N * kk), *ow = (double *)malloc(sizeof(double) * N * kk);
     int nh = 0, t = 0;
     if (check_every <= 0) check_every = max_iters > 0 ? max_iters : 1;
 
     for (t = 1; t <= max_iters; ++t) {
         orc_grad(n, kk, Phi, gx, gy);
+        ORC_PARALLEL_FOR
         for (size_t p = 0; p < nn; ++p) {
+            double v[128], o[128];
             for (int q = 0; q < kk; ++q) {
                 v[q] = Ux[q * nn + p] + mu * gx[q * nn + p];
                 v[kk + q] = Uy[q * nn + p] + mu * gy[q * nn + p];
@@ -989,7 +1033,9 @@ int orc_momt_solve(int n, int k, int N, const double *L, const double *Lam0, con
             for (int q = 0; q < kk; ++q) { nUx[q * nn + p] = o[q]; nUy[q * nn + p] = o[kk + q]; }
         }
         orc_grad_L(n, k, N, L, Phi, gl);
+        ORC_PARALLEL_FOR
         for (size_t p = 0; p < nn; ++p) {
+            double xw[512], ow[512];
             for (int q = 0; q < N * kk; ++q) xw[q] = W[q * nn + p] + nu * gl[q * nn + p];
             if (w_norm == 0) for (int q = 0; q < N * kk; ++q) ow[q] = orc_shrink1(xw[q], alpha * nu);
             else if (w_norm == 2) for (int s_ = 0; s_ < N; ++s_) orc_shrink_nuc(k, xw + s_ * kk, alpha * nu, ow + s_ * kk);
@@ -1020,7 +1066,7 @@ int orc_momt_solve(int n, int k, int N, const double *L, const double *Lam0, con
     }
     if (t > max_iters) t = max_iters;
     free(gx); free(gy); free(gl); free(nUx); free(nUy); free(nW); free(bx); free(by); free(bw);
-    free(dv); free(dl); free(pPhi); free(v); free(o); free(xw); free(ow);
+    free(dv); free(dl); free(pPhi);
     return t;
 }
 
@@ -1743,6 +1789,7 @@ static void zgrad(int n, int planes, const zdbl *phi, zdbl *gx, zdbl *gy)
 {
     double ih = (double)(n - 1);
     for (int c = 0; c < planes; ++c)
+        ORC_PARALLEL_FOR
         for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i) {
                 gx[AT(c, j, i)] = (i < n - 1) ? ih * (phi[AT(c, j, i + 1)] - phi[AT(c, j, i)]) : 0.0;

@@ -19,7 +19,7 @@ from ._native import VomtError, ENGINES
 U_L12, U_L2, U_L1, U_NUC = 0, 1, 2, 3    # U_NUC: matrix OMT, ||U_x||_nuc + ||U_y||_nuc
 W_L1, W_L2, W_NUC = 0, 1, 2              # W_NUC: matrix OMT, sum_s ||W_s||_nuc
 
-__all__ = ["solve", "solve_host", "solve3d", "step_sizes", "history", "set_wait_policy", "VomtError", "U_L12", "U_L2", "U_L1", "U_NUC", "W_L1",
+__all__ = ["solve", "solve_host", "solve3d", "step_sizes", "tune_tau", "momt_tune_tau", "history", "set_wait_policy", "VomtError", "U_L12", "U_L2", "U_L1", "U_NUC", "W_L1",
            "W_L2", "W_NUC"]
 
 
@@ -31,7 +31,8 @@ class Solution:
     result: dict
 
 
-def _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, warm, engine, halo=0, eps=0.0):
+def _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, warm, engine, halo=0, eps=0.0,
+            pitch=0):
     p = _native.Params()
     _native.load().vomt_default_params(ctypes.byref(p))
     p.tau = 0.0 if tau is None else float(tau)
@@ -44,6 +45,7 @@ def _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_re
     p.engine = ENGINES[engine] if isinstance(engine, str) else int(engine)
     p.halo = int(halo)
     p.eps = float(eps)
+    p.pitch = int(pitch)
     return p
 
 
@@ -95,6 +97,35 @@ def solve(rho0, rho1, edges, alpha: float = 1.0, *, tau=None, mu=None, nu=None, 
                                    ctypes.byref(res), ctypes.c_void_p(st))
     _native.check(rc, ctx)
     return Solution(u, w, phi, res.as_dict())
+
+
+def tune_tau(rho0, rho1, edges, alpha: float = 1.0, *, cost=None, u_norm: int = U_L12, w_norm: int = W_L1,
+             sample_iters: int = 1500, engine="auto", eps: float = 0.0, stream=None):
+    """Measure the dual step tau for this problem (vomt_tune_tau): short GPU runs over the
+    grid tau_paper * 10^((j-1)/2), successive halving, one refinement.  Sections 7.1-7.2
+    tune tau per experiment; mu and nu follow from it by the paper's rule.  Returns
+    (best tau, its score max(rel gap, rel res), scores of the grid after sample_iters)."""
+    import torch
+    rho0 = rho0.contiguous().float()
+    rho1 = rho1.contiguous().float()
+    k, n = rho0.shape[0], rho0.shape[-1]
+    dev = rho0.device
+    g = _native.GraphArg(k, edges, cost)
+    l = g.tail.size
+    u = torch.empty((2, k, n, n), device=dev, dtype=torch.float32)
+    w = torch.empty((max(l, 1), n, n), device=dev, dtype=torch.float32)
+    phi = torch.empty((k, n, n), device=dev, dtype=torch.float32)
+    p = _params(None, None, None, u_norm, w_norm, sample_iters, sample_iters, 0.0, 0.0, False, engine, eps=eps)
+    best, score = ctypes.c_double(), ctypes.c_double()
+    grid = (ctypes.c_double * _native.TAU_GRID)()
+    st = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
+    ctx = _native.context(dev.index if dev.index is not None else torch.cuda.current_device())
+    rc = _native.load().vomt_tune_tau(ctx, int(n), rho0.data_ptr(), rho1.data_ptr(), g.ref, float(alpha),
+                                      ctypes.byref(p), int(sample_iters), u.data_ptr(), w.data_ptr() if l else None,
+                                      phi.data_ptr(), ctypes.byref(best), ctypes.byref(score), grid,
+                                      ctypes.c_void_p(st))
+    _native.check(rc, ctx)
+    return best.value, score.value, list(grid)
 
 
 def solve3d(rho0, rho1, edges, alpha: float = 1.0, *, tau=None, mu=None, nu=None, cost=None,
@@ -215,6 +246,32 @@ def momt_solve(Lam0, Lam1, L, alpha: float = 1.0, *, tau=None, mu=None, nu=None,
                                    ctypes.byref(res), ctypes.c_void_p(st))
     _native.check(rc, ctx)
     return MatrixSolution(U, W, Phi, res.as_dict())
+
+
+def momt_tune_tau(Lam0, Lam1, L, alpha: float = 1.0, *, u_norm: int = U_L2, w_norm: int = W_L1,
+                  sample_iters: int = 1500, engine="auto", stream=None):
+    """The tau search of tune_tau for matrix OMT (momt_tune_tau; Section 7.3, Table 3)."""
+    import torch
+    Lam0 = Lam0.contiguous().float()
+    Lam1 = Lam1.contiguous().float()
+    Lh = np.ascontiguousarray(L, dtype=np.float64)
+    N, k = Lh.shape[0], Lh.shape[1]
+    kk, n = Lam0.shape[0], Lam0.shape[-1]
+    dev = Lam0.device
+    U = torch.empty((2, kk, n, n), device=dev, dtype=torch.float32)
+    W = torch.empty((N, kk, n, n), device=dev, dtype=torch.float32)
+    Phi = torch.empty((kk, n, n), device=dev, dtype=torch.float32)
+    p = _params(None, None, None, u_norm, w_norm, sample_iters, sample_iters, 0.0, 0.0, False, engine)
+    best, score = ctypes.c_double(), ctypes.c_double()
+    grid = (ctypes.c_double * _native.TAU_GRID)()
+    st = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
+    ctx = _native.context(dev.index if dev.index is not None else torch.cuda.current_device())
+    rc = _native.load().momt_tune_tau(ctx, int(n), int(k), Lam0.data_ptr(), Lam1.data_ptr(), int(N), Lh.ctypes.data,
+                                      float(alpha), ctypes.byref(p), int(sample_iters), U.data_ptr(), W.data_ptr(),
+                                      Phi.data_ptr(), ctypes.byref(best), ctypes.byref(score), grid,
+                                      ctypes.c_void_p(st))
+    _native.check(rc, ctx)
+    return best.value, score.value, list(grid)
 
 
 def momt_solve_complex(Lam0, Lam1, L, alpha: float = 1.0, *, tau=None, mu=None, nu=None, max_iters: int = 2000,
@@ -391,6 +448,23 @@ class Batch:
         _native.check(rc, ctx)
         self.results = [r.as_dict() for r in res]
         return rc
+
+    def tune_tau(self, sample_iters=1000, **kw):
+        """Per-problem dual step tau (vomt_batch_tune_tau): the whole batch runs once per
+        grid point tau_paper(n) * 10^((j-1)/2); every problem keeps its best, which is
+        stored as its tau for later solves.  Returns (taus, scores)."""
+        p = _params(None, None, None, kw.get("u_norm", U_L12), kw.get("w_norm", W_L1), sample_iters, sample_iters,
+                    0.0, 0.0, False, "batched", eps=kw.get("eps", 0.0))
+        cnt = len(self.problems)
+        taus = (ctypes.c_double * cnt)()
+        scores = (ctypes.c_double * cnt)()
+        ctx = _native.context(self.device.index)
+        _native.check(_native.load().vomt_batch_tune_tau(ctx, cnt, self.inst, self.arena.data_ptr(), ctypes.byref(p),
+                                                         int(sample_iters), taus, scores), ctx)
+        for q in range(cnt):
+            self.inst[q].tau = taus[q]
+            self.problems[q]["tau"] = taus[q]
+        return list(taus), list(scores)
 
     def tune(self, sample_iters=50, **kw):
         """Time the one-block-per-problem path with 128 / 256 / 512 threads per block and

@@ -15,6 +15,7 @@ c_int, c_double, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 P_int, P_double, P_float = ctypes.POINTER(c_int), ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_float)
 
 OK, NOT_CONVERGED = 0, 1
+TAU_GRID = 10         # VOMT_TAU_GRID
 STATUS_NAMES = {
     0: "OK", 1: "NOT_CONVERGED", -1: "BAD_ARG", -2: "MASS_MISMATCH", -3: "NEGATIVE_DENSITY",
     -4: "GRAPH", -5: "L_KERNEL", -6: "STEP_CONDITION", -7: "NONFINITE", -8: "BARRIER_TIMEOUT",
@@ -35,7 +36,7 @@ class Instance(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("tau", c_double), ("mu", c_double), ("nu", c_double), ("u_norm", c_int), ("w_norm", c_int),
                 ("max_iters", c_int), ("check_every", c_int), ("tol_gap", c_double), ("tol_res", c_double),
-                ("warm_start", c_int), ("engine", c_int), ("halo", c_int), ("eps", c_double)]
+                ("warm_start", c_int), ("engine", c_int), ("halo", c_int), ("eps", c_double), ("pitch", c_int)]
 
 
 class Result(ctypes.Structure):
@@ -78,8 +79,8 @@ SIGNATURES = {
                              ctypes.POINTER(Params), c_void_p, c_void_p, c_void_p, ctypes.POINTER(Result), c_void_p]),
     "vomt_history": (c_int, [c_void_p, P_double, c_int]),
     "vomt_set_wait_policy": (c_int, [c_void_p, c_double, c_int]),
-    "vomt_backward": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
-                              c_void_p, c_void_p, c_void_p]),
+    "vomt_backward": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                              c_void_p, c_void_p, c_void_p, c_void_p]),
     "vomt_unrolled_grad": (c_int, [c_void_p, c_int, c_void_p, c_void_p, ctypes.POINTER(Graph), c_double,
                                    ctypes.POINTER(Params), c_int, c_int, c_double, c_void_p, c_void_p, P_double,
                                    P_double, c_void_p]),
@@ -93,6 +94,14 @@ SIGNATURES = {
                                 P_double]),
     "momt_solve": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int, c_void_p, c_double,
                            ctypes.POINTER(Params), c_void_p, c_void_p, c_void_p, ctypes.POINTER(Result), c_void_p]),
+    "vomt_tune_tau": (c_int, [c_void_p, c_int, c_void_p, c_void_p, ctypes.POINTER(Graph), c_double,
+                              ctypes.POINTER(Params), c_int, c_void_p, c_void_p, c_void_p, P_double, P_double,
+                              P_double, c_void_p]),
+    "momt_tune_tau": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int, c_void_p, c_double,
+                              ctypes.POINTER(Params), c_int, c_void_p, c_void_p, c_void_p, P_double, P_double,
+                              P_double, c_void_p]),
+    "vomt_batch_tune_tau": (c_int, [c_void_p, c_int, ctypes.POINTER(Instance), c_void_p, ctypes.POINTER(Params),
+                                    c_int, P_double, P_double]),
     "vomt_solve_noalloc": (c_int, [c_int, c_void_p, c_void_p, ctypes.POINTER(Graph), c_double,
                                    ctypes.POINTER(Params), c_void_p, c_void_p, c_void_p, ctypes.POINTER(Result),
                                    c_void_p, ctypes.POINTER(ctypes.c_char_p)]),

@@ -34,10 +34,13 @@ class _TransportCost(torch.autograd.Function):
         B, k, n = r0.shape[0], r0.shape[1], r0.shape[-1]
         alphas = _alpha_tensor(alpha, B, r0.device).cpu().tolist()
         w_norm = kw.get("w_norm", W_L1)
+        taus = kw.get("taus")             # optional per-problem dual steps (e.g. from Batch.tune_tau)
+        kw = {x: v for x, v in kw.items() if x != "taus"}
         if B == 1 or kw.get("engine") != "batched":
             costs, phis, ws = [], [], []
             for q in range(B):
-                sol = solve(r0[q], r1[q], edges, alphas[q], **kw)
+                qkw = dict(kw, tau=taus[q]) if taus is not None else kw
+                sol = solve(r0[q], r1[q], edges, alphas[q], **qkw)
                 costs.append(sol.result["primal"])
                 phis.append(sol.phi)
                 ws.append(sol.w)
@@ -46,7 +49,8 @@ class _TransportCost(torch.autograd.Function):
         else:
             skw = {x: kw[x] for x in ("max_iters", "check_every", "tol_gap", "tol_res", "tau", "u_norm", "w_norm")
                    if x in kw}
-            probs = [dict(n=n, k=k, edges=edges, alpha=alphas[q]) for q in range(B)]
+            probs = [dict(n=n, k=k, edges=edges, alpha=alphas[q], tau=None if taus is None else taus[q])
+                     for q in range(B)]
             bt = Batch(probs, list(r0), list(r1), device=r0.device.index or 0)
             bt.solve(**skw)
             costs = [r["primal"] for r in bt.results]
@@ -68,7 +72,7 @@ class _TransportCost(torch.autograd.Function):
         da = torch.empty((B,), device=phi.device, dtype=torch.float32)
         cctx = _native.context(phi.device.index or 0)
         st = torch.cuda.current_stream(phi.device).cuda_stream
-        rc = _native.load().vomt_backward(cctx, B, n, k, l, w_norm, phi.data_ptr(), w.data_ptr() if l else None,
+        rc = _native.load().vomt_backward(cctx, B, n, 0, k, l, w_norm, phi.data_ptr(), w.data_ptr() if l else None,
                                           g.data_ptr(), d0.data_ptr(), d1.data_ptr(), da.data_ptr(),
                                           ctypes.c_void_p(st))
         _native.check(rc, cctx)

@@ -32,6 +32,14 @@ int ensure_buffer(vomt_ctx *ctx, void **p, size_t *cap, size_t bytes, const char
     return VOMT_OK;
 }
 
+cudaError_t copy_planes(float *dst, int dst_pitch, const float *src, int src_pitch, int n, size_t planes,
+                        cudaMemcpyKind kind, cudaStream_t st)
+{
+    if (planes == 0) return cudaSuccess;
+    return cudaMemcpy2DAsync(dst, sizeof(float) * (size_t)dst_pitch, src, sizeof(float) * (size_t)src_pitch,
+                             sizeof(float) * (size_t)n, planes * (size_t)n, kind, st);
+}
+
 int fail(vomt_ctx *ctx, int code, const char *msg)
 {
     if (ctx) ctx->err = msg;
@@ -41,31 +49,19 @@ int fail(vomt_ctx *ctx, int code, const char *msg)
 // Table 1's tuned tau (1 for the 32^2 and 64^2 grids, 3 for 128^2 and 256^2).
 static double default_tau(int n) { return n <= 64 ? 1.0 : 3.0; }
 
-struct Prepared {
-    GraphDev gd;
-    OpDev g;
-    StepDev s;
-    SolveCfg cfg;
-    vomt_params p;
-    double lmax;
-};
-
-static int prepare(vomt_ctx *ctx, int n, const vomt_graph *graph, double alpha, const vomt_params *pin,
-                   Prepared *out)
+int setup_vector(int n, const vomt_graph *graph, double alpha, const vomt_params *pin, VectorSetup *out,
+                 std::string *err)
 {
-    if (!ctx) return VOMT_ERR_BAD_ARG;
-    ctx->err.clear();
-    if (n < 2 || n > 32768) return fail(ctx, VOMT_ERR_BAD_ARG, "n must be in [2, 32768]");
-    if (!(alpha > 0.0) || !isfinite(alpha)) return fail(ctx, VOMT_ERR_BAD_ARG, "alpha must be positive");
+    if (n < 2 || n > 32768) { *err = "n must be in [2, 32768]"; return VOMT_ERR_BAD_ARG; }
+    if (!(alpha > 0.0) || !isfinite(alpha)) { *err = "alpha must be positive"; return VOMT_ERR_BAD_ARG; }
     vomt_params p;
     vomt_default_params(&p);
     if (pin) p = *pin;
-    if (p.max_iters < 0 || p.check_every < 1) return fail(ctx, VOMT_ERR_BAD_ARG, "max_iters >= 0, check_every >= 1");
-    if (p.u_norm < 0 || p.u_norm > 2 || p.w_norm < 0 || p.w_norm > 1) return fail(ctx, VOMT_ERR_BAD_ARG, "bad norm code");
-    if (p.engine < 0 || p.engine > 2) return fail(ctx, VOMT_ERR_BAD_ARG, "bad engine code");
-    if (p.halo < 0 || p.halo > 16) return fail(ctx, VOMT_ERR_BAD_ARG, "halo must be in [0, 16]");
-    if (!(p.eps >= 0.0) || !isfinite(p.eps)) return fail(ctx, VOMT_ERR_BAD_ARG, "eps must be finite and >= 0");
-    int rc = graph_to_dev(graph, &out->gd, &ctx->err);
+    if (p.max_iters < 0 || p.check_every < 1) { *err = "max_iters >= 0, check_every >= 1"; return VOMT_ERR_BAD_ARG; }
+    if (p.u_norm < 0 || p.u_norm > 2 || p.w_norm < 0 || p.w_norm > 1) { *err = "bad norm code"; return VOMT_ERR_BAD_ARG; }
+    if (!(p.eps >= 0.0) || !isfinite(p.eps)) { *err = "eps must be finite and >= 0"; return VOMT_ERR_BAD_ARG; }
+    if (p.pitch != 0 && p.pitch < n) { *err = "pitch must be 0 or >= n"; return VOMT_ERR_BAD_ARG; }
+    int rc = graph_to_dev(graph, &out->gd, err);
     if (rc) return rc;
     graph_to_op(out->gd, &out->g);
     const double tau = p.tau > 0.0 ? p.tau : default_tau(n);
@@ -75,8 +71,10 @@ static int prepare(vomt_ctx *ctx, int n, const vomt_graph *graph, double alpha, 
     const bool user = mu > 0.0 || nu > 0.0;
     if (!(mu > 0.0)) mu = out->g.l > 0 ? 1.0 / (32.0 * tau * n1 * n1) : 1.0 / (16.0 * tau * n1 * n1);
     if (!(nu > 0.0)) nu = out->g.l > 0 ? 1.0 / (4.0 * tau * lmax) : 1.0;
-    if (user && !(tau * mu * 8.0 * n1 * n1 + (out->g.l > 0 ? tau * nu * lmax : 0.0) < 1.0))
-        return fail(ctx, VOMT_ERR_STEP_CONDITION, "step sizes break 1 > tau mu 8(n-1)^2 + tau nu lambda_max(-Delta_G)");
+    if (user && !(tau * mu * 8.0 * n1 * n1 + (out->g.l > 0 ? tau * nu * lmax : 0.0) < 1.0)) {
+        *err = "step sizes break 1 > tau mu 8(n-1)^2 + tau nu lambda_max(-Delta_G)";
+        return VOMT_ERR_STEP_CONDITION;
+    }
     out->s.n = n;
     out->s.ih = (float)n1;
     out->s.mu = (float)mu;
@@ -98,6 +96,16 @@ static int prepare(vomt_ctx *ctx, int n, const vomt_graph *graph, double alpha, 
     return VOMT_OK;
 }
 
+static int prepare(vomt_ctx *ctx, int n, const vomt_graph *graph, double alpha, const vomt_params *pin,
+                   VectorSetup *out)
+{
+    if (!ctx) return VOMT_ERR_BAD_ARG;
+    ctx->err.clear();
+    if (pin && (pin->engine < 0 || pin->engine > 2)) return fail(ctx, VOMT_ERR_BAD_ARG, "bad engine code");
+    if (pin && (pin->halo < 0 || pin->halo > 16)) return fail(ctx, VOMT_ERR_BAD_ARG, "halo must be in [0, 16]");
+    return setup_vector(n, graph, alpha, pin, out, &ctx->err);
+}
+
 static int check_densities(vomt_ctx *ctx, int planes, int n, const float *rho0, const float *rho1, cudaStream_t st)
 {
     double sums[5];
@@ -105,7 +113,7 @@ static int check_densities(vomt_ctx *ctx, int planes, int n, const float *rho0, 
     if (rc) return rc;
     if (sums[4] > 0.0) return fail(ctx, VOMT_ERR_NONFINITE, "density has NaN or Inf entries");
     if (sums[2] < 0.0 || sums[3] < 0.0) return fail(ctx, VOMT_ERR_NEGATIVE_DENSITY, "density has negative entries");
-    if (fabs(sums[0] - sums[1]) > 1e-5 * fmax(fabs(sums[0]), fabs(sums[1])))
+    if (fabs(sums[0] - sums[1]) > kMassRelTol * fmax(fabs(sums[0]), fabs(sums[1])))
         return fail(ctx, VOMT_ERR_MASS_MISMATCH, "rho0 and rho1 have different total mass");
     return VOMT_OK;
 }
@@ -113,7 +121,7 @@ static int check_densities(vomt_ctx *ctx, int planes, int n, const float *rho0, 
 int prepare_vector(vomt_ctx *ctx, int n, const vomt_graph *graph, double alpha, const vomt_params *pin, OpDev *op,
                    StepDev *s, SolveCfg *cfg, vomt_params *p)
 {
-    Prepared P;
+    VectorSetup P;
     const int rc = prepare(ctx, n, graph, alpha, pin, &P);
     if (rc) return rc;
     *op = P.g;
@@ -190,13 +198,43 @@ static int solve_device(vomt_ctx *ctx, int n, const float *rho0, const float *rh
                         double alpha, const vomt_params *pin, float *u, float *w, float *phi, vomt_result *result,
                         cudaStream_t st)
 {
-    Prepared P;
+    VectorSetup P;
     int rc = prepare(ctx, n, graph, alpha, pin, &P);
     if (rc) return rc;
     if (!rho0 || !rho1 || !u || !phi || (P.g.l > 0 && !w)) return fail(ctx, VOMT_ERR_BAD_ARG, "null array");
     ctx->launches = 0;
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "cudaSetDevice");
+    const int pitch = P.p.pitch;
+    if (pitch != 0 && pitch != n) {
+        // stage the pitched arrays densely, solve, copy the outputs back
+        const size_t nn = (size_t)n * n, k = P.g.k, l = P.g.l;
+        rc = ensure_buffer(ctx, (void **)&ctx->pstage, &ctx->pstage_bytes, sizeof(float) * (5 * k + l) * nn,
+                           "pitch staging");
+        if (rc) return rc;
+        float *d0 = ctx->pstage, *d1 = d0 + k * nn, *du = d1 + k * nn, *dw = du + 2 * k * nn, *dp = dw + l * nn;
+        e = copy_planes(d0, n, rho0, pitch, n, k, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = copy_planes(d1, n, rho1, pitch, n, k, cudaMemcpyDeviceToDevice, st);
+        if (P.p.warm_start) {
+            if (e == cudaSuccess) e = copy_planes(du, n, u, pitch, n, 2 * k, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess && l) e = copy_planes(dw, n, w, pitch, n, l, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = copy_planes(dp, n, phi, pitch, n, k, cudaMemcpyDeviceToDevice, st);
+        }
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "pitched copy in");
+        vomt_params dense = P.p;
+        dense.pitch = 0;
+        dense.tau = pin && pin->tau > 0.0 ? pin->tau : 0.0;
+        dense.mu = pin ? pin->mu : 0.0;
+        dense.nu = pin ? pin->nu : 0.0;
+        const int status = solve_device(ctx, n, d0, d1, graph, alpha, &dense, du, dw, dp, result, st);
+        if (status < 0) return status;
+        e = copy_planes(u, pitch, du, n, n, 2 * k, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess && l) e = copy_planes(w, pitch, dw, n, n, l, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = copy_planes(phi, pitch, dp, n, n, k, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "pitched copy out");
+        return status;
+    }
     rc = check_densities(ctx, P.g.k, n, rho0, rho1, st);
     if (rc) return rc;
     int engine = 0;
@@ -247,6 +285,7 @@ void vomt_destroy(vomt_ctx *c)
     if (c->hstatus) cudaFreeHost(c->hstatus);
     if (c->dhist) cudaFree(c->dhist);
     if (c->stage) cudaFree(c->stage);
+    if (c->pstage) cudaFree(c->pstage);
     if (c->mstage) cudaFree(c->mstage);
     if (c->batch) batch_state_free(c->batch);
     if (c->gbuf) cudaFree(c->gbuf);
@@ -292,6 +331,7 @@ void vomt_default_params(vomt_params *p)
     p->engine = VOMT_ENGINE_AUTO;
     p->halo = 0;
     p->eps = 0.0;
+    p->pitch = 0;
 }
 
 int vomt_step_sizes(int n, const vomt_graph *g, double tau, double *mu, double *nu, double *tau_used, double *lmax_graph)
@@ -332,22 +372,29 @@ int vomt_solve_host(vomt_ctx *ctx, int n, const float *rho0, const float *rho1, 
         cudaError_t e = cudaSetDevice(ctx->device);
         if (e != cudaSuccess) return set_cuda_error(ctx, e, "cudaSetDevice");
         const size_t nn = (size_t)n * n, k = g->k, l = g->n_edges;
+        const int pitch = p && p->pitch ? p->pitch : n;
+        if (pitch < n) return fail(ctx, VOMT_ERR_BAD_ARG, "pitch must be 0 or >= n");
         const size_t need = (2 * k + 2 * k + l + k) * nn;
         int rc = ensure_buffer(ctx, (void **)&ctx->stage, &ctx->stage_floats, need * sizeof(float), "staging");
         if (rc) return rc;
         float *d0 = ctx->stage, *d1 = d0 + k * nn, *du = d1 + k * nn, *dw = du + 2 * k * nn, *dp = dw + l * nn;
         const bool warm = p && p->warm_start;
-        e = cudaMemcpyAsync(d0, rho0, k * nn * sizeof(float), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d1, rho1, k * nn * sizeof(float), cudaMemcpyHostToDevice, st);
-        if (warm && e == cudaSuccess) e = cudaMemcpyAsync(du, u, 2 * k * nn * sizeof(float), cudaMemcpyHostToDevice, st);
-        if (warm && l && e == cudaSuccess) e = cudaMemcpyAsync(dw, w, l * nn * sizeof(float), cudaMemcpyHostToDevice, st);
-        if (warm && e == cudaSuccess) e = cudaMemcpyAsync(dp, phi, k * nn * sizeof(float), cudaMemcpyHostToDevice, st);
+        const cudaMemcpyKind h2d = cudaMemcpyHostToDevice, d2h = cudaMemcpyDeviceToHost;
+        e = copy_planes(d0, n, rho0, pitch, n, k, h2d, st);
+        if (e == cudaSuccess) e = copy_planes(d1, n, rho1, pitch, n, k, h2d, st);
+        if (warm && e == cudaSuccess) e = copy_planes(du, n, u, pitch, n, 2 * k, h2d, st);
+        if (warm && l && e == cudaSuccess) e = copy_planes(dw, n, w, pitch, n, l, h2d, st);
+        if (warm && e == cudaSuccess) e = copy_planes(dp, n, phi, pitch, n, k, h2d, st);
         if (e != cudaSuccess) return set_cuda_error(ctx, e, "host to device copy");
-        int status = solve_device(ctx, n, d0, d1, g, alpha, p, du, dw, dp, result, st);
+        vomt_params dense;
+        vomt_default_params(&dense);
+        if (p) dense = *p;
+        dense.pitch = 0;
+        int status = solve_device(ctx, n, d0, d1, g, alpha, &dense, du, dw, dp, result, st);
         if (status < 0) return status;
-        e = cudaMemcpyAsync(u, du, 2 * k * nn * sizeof(float), cudaMemcpyDeviceToHost, st);
-        if (l && e == cudaSuccess) e = cudaMemcpyAsync(w, dw, l * nn * sizeof(float), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(phi, dp, k * nn * sizeof(float), cudaMemcpyDeviceToHost, st);
+        e = copy_planes(u, pitch, du, n, n, 2 * k, d2h, st);
+        if (l && e == cudaSuccess) e = copy_planes(w, pitch, dw, n, n, l, d2h, st);
+        if (e == cudaSuccess) e = copy_planes(phi, pitch, dp, n, n, k, d2h, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return set_cuda_error(ctx, e, "device to host copy");
         return status;

@@ -30,20 +30,24 @@ namespace {
 
 constexpr int AX = 32, AY = 8, AT = AX * AY;
 
-__global__ void __launch_bounds__(1024) k_envelope(int n, int k, int l, int wn, const float *__restrict__ phi,
+__global__ void __launch_bounds__(1024) k_envelope(int n, int pitch, int k, int l, int wn, const float *__restrict__ phi,
                                                    const float *__restrict__ w, const float *__restrict__ gscale,
                                                    float *__restrict__ d_rho0, float *__restrict__ d_rho1,
                                                    float *__restrict__ d_alpha)
 {
+    // logical element q = (plane * n + j) * n + i sits at (plane * n + j) * pitch + i
     const size_t nn = (size_t)n * n, cnt = (size_t)k * nn;
-    const float *P = phi + blockIdx.x * cnt;
-    const float *Wb = w + blockIdx.x * (size_t)l * nn;
+    const size_t pcnt = (size_t)k * n * pitch, pw = (size_t)n * pitch;
+    const float *P = phi + blockIdx.x * pcnt;
+    const float *Wb = w + blockIdx.x * (size_t)l * pw;
+    auto at = [n, pitch](size_t q) { return (q / (size_t)n) * (size_t)pitch + q % (size_t)n; };
     double s = 0.0, sw = 0.0;
-    for (size_t q = threadIdx.x; q < cnt; q += blockDim.x) s += P[q];
+    for (size_t q = threadIdx.x; q < cnt; q += blockDim.x) s += P[at(q)];
     for (size_t q = threadIdx.x; q < nn && l > 0; q += blockDim.x) {
         double a = 0.0;
+        const size_t o = at(q);
         for (int e = 0; e < l; ++e) {
-            const double x = Wb[e * nn + q];
+            const double x = Wb[e * pw + o];
             a += (wn == VOMT_W_L1) ? fabs(x) : x * x;
         }
         sw += (wn == VOMT_W_L1) ? a : sqrt(a);
@@ -62,9 +66,10 @@ __global__ void __launch_bounds__(1024) k_envelope(int n, int k, int l, int wn, 
     const double mean = sh[0][0] / (double)cnt;
     const float g = gscale ? gscale[blockIdx.x] : 1.0f;
     for (size_t q = threadIdx.x; q < cnt; q += blockDim.x) {
-        const float v = g * (float)((double)P[q] - mean);
-        if (d_rho1) d_rho1[blockIdx.x * cnt + q] = v;
-        if (d_rho0) d_rho0[blockIdx.x * cnt + q] = -v;
+        const size_t o = at(q);
+        const float v = g * (float)((double)P[o] - mean);
+        if (d_rho1) d_rho1[blockIdx.x * pcnt + o] = v;
+        if (d_rho0) d_rho0[blockIdx.x * pcnt + o] = -v;
     }
     if (threadIdx.x == 0 && d_alpha) d_alpha[blockIdx.x] = (float)(g * sh[1][0]);
 }
@@ -298,19 +303,21 @@ void pick_adj(int k, AdjInit *ai, AdjStep *as)
 
 using namespace vomt;
 
-extern "C" int vomt_backward(vomt_ctx *ctx, int batch, int n, int k, int n_edges, int w_norm, const float *phi,
-                             const float *w, const float *grad_scale, float *d_rho0, float *d_rho1, float *d_alpha,
-                             void *stream)
+extern "C" int vomt_backward(vomt_ctx *ctx, int batch, int n, int pitch, int k, int n_edges, int w_norm,
+                             const float *phi, const float *w, const float *grad_scale, float *d_rho0, float *d_rho1,
+                             float *d_alpha, void *stream)
 {
     if (!ctx) return VOMT_ERR_BAD_ARG;
     ctx->err.clear();
     if (batch < 1 || n < 2 || k < 1 || k > KMAX || n_edges < 0 || n_edges > LMAX || w_norm < 0 || w_norm > 1)
         return fail(ctx, VOMT_ERR_BAD_ARG, "backward: bad sizes");
+    if (pitch == 0) pitch = n;
+    if (pitch < n) return fail(ctx, VOMT_ERR_BAD_ARG, "backward: pitch must be 0 or >= n");
     if (!phi || (n_edges > 0 && !w)) return fail(ctx, VOMT_ERR_BAD_ARG, "backward: null array");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "cudaSetDevice");
-    k_envelope<<<batch, 1024, 0, (cudaStream_t)stream>>>(n, k, n_edges, w_norm, phi, w, grad_scale, d_rho0, d_rho1,
-                                                         d_alpha);
+    k_envelope<<<batch, 1024, 0, (cudaStream_t)stream>>>(n, pitch, k, n_edges, w_norm, phi, w, grad_scale, d_rho0,
+                                                         d_rho1, d_alpha);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "backward launch");
     return VOMT_OK;

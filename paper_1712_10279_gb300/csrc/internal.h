@@ -94,6 +94,10 @@ inline void set_regularisation(StepDev *s, SolveCfg *cfg, double eps, double mu,
     cfg->eps = eps;
 }
 
+// Relative tolerance of the equal-mass check of the densities (the constraint of
+// eq. (vomt) sums to zero over all cells and channels, so the totals must agree).
+constexpr double kMassRelTol = 1e-6;
+
 // ----------------------------------------------------------------- host setup
 int graph_to_dev(const vomt_graph *g, GraphDev *out, std::string *err);
 double sym_lmax(int m, const double *A);     // largest eigenvalue of a symmetric m x m matrix
@@ -134,6 +138,9 @@ struct vomt_ctx {
     // host-API staging buffers (device)
     float *stage = nullptr;
     size_t stage_floats = 0;
+    // dense copies of pitched device arrays (vomt_params.pitch)
+    float *pstage = nullptr;
+    size_t pstage_bytes = 0;
     int launches = 0;                        // kernels launched by the current call
     int last_blocks = 0, last_halo = 0, last_variant = 0;      // launch shape of the current call
     // matrix-OMT compact staging (device)
@@ -159,8 +166,26 @@ struct vomt_ctx {
 namespace vomt {
 int set_cuda_error(vomt_ctx *ctx, cudaError_t e, const char *what);
 int fail(vomt_ctx *ctx, int code, const char *msg);
+// 2-D copy of `planes` planes of n rows of n floats between row pitches (in floats).
+cudaError_t copy_planes(float *dst, int dst_pitch, const float *src, int src_pitch, int n, size_t planes,
+                        cudaMemcpyKind kind, cudaStream_t st);
 int prepare_vector(vomt_ctx *ctx, int n, const vomt_graph *graph, double alpha, const vomt_params *pin, OpDev *op,
                    StepDev *s, SolveCfg *cfg, vomt_params *p);
+// Argument checks and step sizes of a vector solve, shared by the entry points with a
+// context and the allocation-free one: parameter ranges, the channel graph (checked and
+// converted), tau (Table 1's value when p->tau <= 0), mu and nu by Section 7.2's rule
+// unless given (user steps must satisfy its condition), the step constants and the
+// check settings.  On error *err holds the message.
+struct VectorSetup {
+    GraphDev gd;
+    OpDev g;
+    StepDev s;
+    SolveCfg cfg;
+    vomt_params p;
+    double lmax;
+};
+int setup_vector(int n, const vomt_graph *graph, double alpha, const vomt_params *pin, VectorSetup *out,
+                 std::string *err);
 int check_vector_densities(vomt_ctx *ctx, int k, int n, const float *rho0, const float *rho1, cudaStream_t st);
 // 3-D solve after validation and step sizes (vector3d.cu); compact channels of g
 int solve3d_core(vomt_ctx *ctx, int n, const OpDev &g, const StepDev &s, const SolveCfg &cfg, const vomt_params &p,

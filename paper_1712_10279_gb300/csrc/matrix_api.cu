@@ -330,6 +330,39 @@ static int momt_any(int dim, vomt_ctx *ctx, int n, int k, const float *Lam0, con
         if (p.engine < 0 || p.engine > 2 || p.halo < 0 || (dim == 2 && p.halo > 16))
             return fail(ctx, VOMT_ERR_BAD_ARG, "bad engine / halo");
         if (p.eps != 0.0) return fail(ctx, VOMT_ERR_BAD_ARG, "matrix OMT takes eps = 0 (regularisation is for vector OMT)");
+        if (p.pitch != 0 && (p.pitch < n || (dim == 3 && p.pitch != n)))
+            return fail(ctx, VOMT_ERR_BAD_ARG, dim == 2 ? "pitch must be 0 or >= n" : "3-D grids take dense arrays");
+        if (p.pitch != 0 && p.pitch != n) {
+            // pitched full matrices: stage them densely, solve, copy the outputs back
+            const size_t nn = (size_t)n * n, kk = (size_t)k * k;
+            if (k < 1 || k > 8 || N < 1 || N * kk > 512) return fail(ctx, VOMT_ERR_BAD_ARG, "bad k or N");
+            int rc = ensure_buffer(ctx, (void **)&ctx->pstage, &ctx->pstage_bytes,
+                                   sizeof(float) * (5 + (size_t)N) * kk * nn, "pitch staging");
+            if (rc) return rc;
+            cudaError_t e = cudaSetDevice(ctx->device);
+            float *d0 = ctx->pstage, *d1 = d0 + kk * nn, *dU = d1 + kk * nn, *dW = dU + 2 * kk * nn;
+            float *dP = dW + (size_t)N * kk * nn;
+            const cudaMemcpyKind d2d = cudaMemcpyDeviceToDevice;
+            const int pitch = p.pitch;
+            if (e == cudaSuccess) e = copy_planes(d0, n, Lam0, pitch, n, kk, d2d, st);
+            if (e == cudaSuccess) e = copy_planes(d1, n, Lam1, pitch, n, kk, d2d, st);
+            if (p.warm_start) {
+                if (e == cudaSuccess) e = copy_planes(dU, n, U, pitch, n, 2 * kk, d2d, st);
+                if (e == cudaSuccess) e = copy_planes(dW, n, W, pitch, n, (size_t)N * kk, d2d, st);
+                if (e == cudaSuccess) e = copy_planes(dP, n, Phi, pitch, n, kk, d2d, st);
+            }
+            if (e != cudaSuccess) return set_cuda_error(ctx, e, "pitched copy in");
+            vomt_params dense = *pin;
+            dense.pitch = 0;
+            const int status = momt_any(dim, ctx, n, k, d0, d1, N, L, alpha, &dense, dU, dW, dP, result, stream);
+            if (status < 0) return status;
+            e = copy_planes(U, pitch, dU, n, n, 2 * kk, d2d, st);
+            if (e == cudaSuccess) e = copy_planes(W, pitch, dW, n, n, (size_t)N * kk, d2d, st);
+            if (e == cudaSuccess) e = copy_planes(Phi, pitch, dP, n, n, kk, d2d, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return set_cuda_error(ctx, e, "pitched copy out");
+            return status;
+        }
         OpDev op;
         double lmax = 0.0, gap = 0.0;
         int rc = quantum_to_op(k, N, L, &op, &lmax, &gap, &ctx->err);
@@ -380,7 +413,7 @@ static int momt_any(int dim, vomt_ctx *ctx, int n, int k, const float *Lam0, con
         if (bad > 0.0) return fail(ctx, VOMT_ERR_NONFINITE, "density has NaN or Inf entries");
         if (mind < 0.0) return fail(ctx, VOMT_ERR_NEGATIVE_DENSITY, "density has a negative diagonal entry");
         if (asym > 1e-5 * mabs) return fail(ctx, VOMT_ERR_BAD_ARG, "densities must be symmetric matrices");
-        if (fabs(tr0 - tr1) > 1e-5 * fmax(fabs(tr0), fabs(tr1)))
+        if (fabs(tr0 - tr1) > kMassRelTol * fmax(fabs(tr0), fabs(tr1)))
             return fail(ctx, VOMT_ERR_MASS_MISMATCH, "Lam0 and Lam1 have different total trace");
         // compact staging: rho0, rho1 (K), u (dim K), w (l), phi (K)
         const size_t need = sizeof(float) * (size_t)((3 + dim) * K + l) * nn;
@@ -454,6 +487,7 @@ extern "C" int momt_solve_complex(vomt_ctx *ctx, int n, int k, const float *Lam0
         vomt_params p;
         vomt_default_params(&p);
         if (pin) p = *pin;
+        if (p.pitch != 0 && p.pitch != n) return fail(ctx, VOMT_ERR_BAD_ARG, "complex matrix OMT takes dense arrays");
         if (p.u_norm == VOMT_U_L12) p.u_norm = VOMT_U_L2;
         if (p.u_norm != VOMT_U_L2 || p.w_norm != VOMT_W_L2)
             return fail(ctx, VOMT_ERR_BAD_ARG, "complex matrix OMT takes the Frobenius norms (u_norm L2, w_norm L2)");
@@ -503,7 +537,7 @@ extern "C" int momt_solve_complex(vomt_ctx *ctx, int n, int k, const float *Lam0
         if (bad > 0.0) return fail(ctx, VOMT_ERR_NONFINITE, "density has NaN or Inf entries");
         if (mind < 0.0) return fail(ctx, VOMT_ERR_NEGATIVE_DENSITY, "density has a negative diagonal entry");
         if (asym > 1e-5 * mabs) return fail(ctx, VOMT_ERR_BAD_ARG, "densities must be Hermitian matrices");
-        if (fabs(tr0 - tr1) > 1e-5 * fmax(fabs(tr0), fabs(tr1)))
+        if (fabs(tr0 - tr1) > kMassRelTol * fmax(fabs(tr0), fabs(tr1)))
             return fail(ctx, VOMT_ERR_MASS_MISMATCH, "Lam0 and Lam1 have different total trace");
         // compact staging: rho0, rho1 (K), u (2K), w (l), phi (K)
         const size_t need = sizeof(float) * (size_t)(5 * K + l) * nn;

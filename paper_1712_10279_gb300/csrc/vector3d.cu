@@ -588,6 +588,7 @@ extern "C" int vomt_solve3d(vomt_ctx *ctx, int n, const float *rho0, const float
         if (!rho0 || !rho1 || !u || !phi || !graph || (graph->n_edges > 0 && !w))
             return fail(ctx, VOMT_ERR_BAD_ARG, "null array");
         if (pin && pin->eps != 0.0) return fail(ctx, VOMT_ERR_BAD_ARG, "3-D grids take eps = 0");
+        if (pin && pin->pitch != 0 && pin->pitch != n) return fail(ctx, VOMT_ERR_BAD_ARG, "3-D grids take dense arrays");
         cudaStream_t st = (cudaStream_t)stream;
         cudaError_t e = cudaSetDevice(ctx->device);
         if (e != cudaSuccess) return set_cuda_error(ctx, e, "cudaSetDevice");

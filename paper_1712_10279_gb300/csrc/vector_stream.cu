@@ -736,16 +736,18 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
 // ---------------------------------------------------------------------------
 // Allocation-free variant of the streaming solve (vomt_solve_noalloc).
 //
-// Some callers cannot allocate device memory: code that runs while a CUDA
-// graph is being captured (cudaMalloc is not allowed then), applications whose
-// device memory is owned by one custom pool or allocator, and plug-ins that
-// must not grow the process's footprint after start-up.  For them this entry
-// point takes its scratch (double-buffered iterates, b = rho1 - rho0, FP64
-// partial sums, the status block) from one fixed array of
-// VOMT_NOALLOC_SCRATCH_BYTES bytes that is part of the library image: every
-// GPU that loads the library holds it until the process exits, and no call
-// ever allocates or frees memory.  Every call shares the array, so calls that
-// overlap on the GPU (other streams, other host threads) race with each other.
+// Some callers cannot allocate device memory: applications whose device memory
+// is owned by one custom pool or allocator (a cudaMalloc behind its back would
+// fragment or overcommit it), and plug-ins or long-running services that must
+// not grow the process's footprint, or risk an out-of-memory failure, after
+// start-up.  For them this entry point takes its scratch (double-buffered
+// iterates, b = rho1 - rho0, FP64 partial sums, the status block) from one
+// fixed array of VOMT_NOALLOC_SCRATCH_BYTES bytes that is part of the library
+// image: every GPU that loads the library holds it until the process exits,
+// and no call ever allocates or frees memory.  Every call shares the array, so
+// calls that overlap on the GPU (other streams, other host threads) race with
+// each other.  The call reads its stopping flag and results back while it
+// runs, so it refuses a stream that is being captured into a CUDA graph.
 // ---------------------------------------------------------------------------
 #include <mutex>
 
@@ -781,44 +783,60 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 }  // namespace
 }  // namespace vomt
 
+namespace vomt {
+namespace {
+
+// Messages of failed calls outlive the call: one per host thread.
+thread_local std::string t_noalloc_msg;
+
+int noalloc_solve(int n, const float *rho0, const float *rho1, const vomt_graph *graph, double alpha,
+                  const vomt_params *pin, float *u, float *w, float *phi, vomt_result *result, cudaStream_t st,
+                  const char **why);
+
+}  // namespace
+}  // namespace vomt
+
 extern "C" int vomt_solve_noalloc(int n, const float *rho0, const float *rho1, const vomt_graph *graph, double alpha,
                                   const vomt_params *pin, float *u, float *w, float *phi, vomt_result *result,
                                   void *stream, const char **error)
 {
-    using namespace vomt;
     const char *dummy = nullptr;
     const char **why = error ? error : &dummy;
     *why = "";
-    cudaStream_t st = (cudaStream_t)stream;
-    if (n < 2 || n > 32768) { *why = "n must be in [2, 32768]"; return VOMT_ERR_BAD_ARG; }
-    if (!(alpha > 0.0) || !isfinite(alpha)) { *why = "alpha must be positive"; return VOMT_ERR_BAD_ARG; }
-    vomt_params p;
-    vomt_default_params(&p);
-    if (pin) p = *pin;
-    if (p.max_iters < 0 || p.check_every < 1) { *why = "max_iters >= 0, check_every >= 1"; return VOMT_ERR_BAD_ARG; }
-    if (p.u_norm < 0 || p.u_norm > 2 || p.w_norm < 0 || p.w_norm > 1) { *why = "bad norm code"; return VOMT_ERR_BAD_ARG; }
-    if (!(p.eps >= 0.0) || !isfinite(p.eps)) { *why = "eps must be finite and >= 0"; return VOMT_ERR_BAD_ARG; }
-    GraphDev gd;
-    std::string gerr;
-    int rc = graph_to_dev(graph, &gd, &gerr);
-    if (rc) { *why = "invalid channel graph"; return rc; }
-    OpDev g;
-    graph_to_op(gd, &g);
-    if (!rho0 || !rho1 || !u || !phi || (g.l > 0 && !w)) { *why = "null array"; return VOMT_ERR_BAD_ARG; }
-    const double tau = p.tau > 0.0 ? p.tau : (n <= 64 ? 1.0 : 3.0);
-    const double lmax = graph_lmax(gd, graph->cost);
-    const double n1 = (double)(n - 1);
-    double mu = p.mu, nu = p.nu;
-    const bool user = mu > 0.0 || nu > 0.0;
-    if (!(mu > 0.0)) mu = g.l > 0 ? 1.0 / (32.0 * tau * n1 * n1) : 1.0 / (16.0 * tau * n1 * n1);
-    if (!(nu > 0.0)) nu = g.l > 0 ? 1.0 / (4.0 * tau * lmax) : 1.0;
-    if (user && !(tau * mu * 8.0 * n1 * n1 + (g.l > 0 ? tau * nu * lmax : 0.0) < 1.0)) {
-        *why = "step sizes break the PDHG condition";
-        return VOMT_ERR_STEP_CONDITION;
+    try {
+        return vomt::noalloc_solve(n, rho0, rho1, graph, alpha, pin, u, w, phi, result, (cudaStream_t)stream, why);
+    } catch (...) {
+        *why = "internal exception";
+        return VOMT_ERR_BAD_ARG;
     }
-    StepDev s{n, (float)n1, (float)mu, (float)nu, (float)tau, (float)alpha};
-    SolveCfg cfg{p.tol_gap, p.tol_res, mu, nu, tau, g.l > 0};
-    set_regularisation(&s, &cfg, p.eps, mu, nu);
+}
+
+namespace vomt {
+namespace {
+
+int noalloc_solve(int n, const float *rho0, const float *rho1, const vomt_graph *graph, double alpha,
+                  const vomt_params *pin, float *u, float *w, float *phi, vomt_result *result, cudaStream_t st,
+                  const char **why)
+{
+    // The call reads results back and synchronises `st` while it runs, which a stream
+    // under CUDA graph capture does not allow: refuse before any GPU work, so that the
+    // caller's capture stays intact.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) { *why = "cudaStreamIsCapturing failed"; return VOMT_ERR_CUDA; }
+    if (cap != cudaStreamCaptureStatusNone) {
+        *why = "the stream is being captured into a CUDA graph; this call synchronises its stream";
+        return VOMT_ERR_BAD_ARG;
+    }
+    VectorSetup S;
+    int rc = setup_vector(n, graph, alpha, pin, &S, &t_noalloc_msg);
+    if (rc) { *why = t_noalloc_msg.c_str(); return rc; }
+    const OpDev &g = S.g;
+    const StepDev &s = S.s;
+    const SolveCfg &cfg = S.cfg;
+    const vomt_params &p = S.p;
+    const double mu = cfg.mu, nu = cfg.nu, tau = cfg.tau;
+    if (!rho0 || !rho1 || !u || !phi || (g.l > 0 && !w)) { *why = "null array"; return VOMT_ERR_BAD_ARG; }
 
     // carve the scratch array
     const int k = g.k, l = g.l;
@@ -860,7 +878,7 @@ extern "C" int vomt_solve_noalloc(int n, const float *rho0, const float *rho1, c
     k_validate<<<vblocks, 256, 0, st>>>(count, rho0, rho1, vpart);
     ++launches;
     double hv[5 * 256];
-    cudaError_t e = cudaMemcpyAsync(hv, vpart, sizeof(double) * 5 * (size_t)vblocks, cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(hv, vpart, sizeof(double) * 5 * (size_t)vblocks, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { *why = cudaGetErrorString(e); return VOMT_ERR_CUDA; }
     double s0 = 0.0, s1 = 0.0, m0 = 1e300, m1 = 1e300, bad = 0.0;
@@ -873,7 +891,7 @@ extern "C" int vomt_solve_noalloc(int n, const float *rho0, const float *rho1, c
     }
     if (bad > 0.0) { *why = "density has NaN or Inf entries"; return VOMT_ERR_NONFINITE; }
     if (m0 < 0.0 || m1 < 0.0) { *why = "density has negative entries"; return VOMT_ERR_NEGATIVE_DENSITY; }
-    if (fabs(s0 - s1) > 1e-5 * fmax(fabs(s0), fabs(s1))) { *why = "rho0 and rho1 have different total mass"; return VOMT_ERR_MASS_MISMATCH; }
+    if (fabs(s0 - s1) > kMassRelTol * fmax(fabs(s0), fabs(s1))) { *why = "rho0 and rho1 have different total mass"; return VOMT_ERR_MASS_MISMATCH; }
 
     // the status block must start at zero; iterates and b are written by k_prepare
     e = cudaMemsetAsync(dstatus, 0, sizeof(DevStatus), st);
@@ -941,3 +959,6 @@ extern "C" int vomt_solve_noalloc(int n, const float *rho0, const float *rho1, c
     }
     return status;
 }
+
+}  // namespace
+}  // namespace vomt
