@@ -31,6 +31,11 @@ same shapes and structure:
 * ``tensor_field_pair3`` the tensor-field recipe on an n x n x n grid (angle and
                          eigenvalue fields smoothed with sigma max(1, n/12) cells),
                          matrix densities of a 3-D DTI volume's shape.
+* ``three_disk_pair``    the structure of the colour-disk example of Section 8.1
+                         (Figure 3): three disks at the same places in both
+                         images, each a pure colour, the colours permuted
+                         between the two images (a pure recolouring); total
+                         mass 1.
 * ``blob_pair3``         the blob recipe on an n x n x n grid (three blobs per
                          channel, sigma uniform in [n/12, n/5] cells, amplitude
                          uniform in [0.5, 1], 1e-3 floor; total mass 1), the
@@ -279,3 +284,18 @@ def shifted_blob_pair(n: int, k: int, shift: int, sigma: float = 1.5, margin: in
     moved = np.zeros_like(base)
     moved[:, :, shift:] = base[:, :, :n - shift]
     return base, moved
+
+
+def three_disk_pair(n: int, radius: float = 0.12,
+                    centres=((0.3, 0.3), (0.7, 0.35), (0.5, 0.7))):
+    """Three disks (centres and radius in units of the unit square) that keep their place
+    and change colour: disk d is channel d in rho0 and channel (d + 1) mod 3 in rho1."""
+    x = np.arange(n) / (n - 1)
+    X, Y = np.meshgrid(x, x)
+    rho0 = np.zeros((3, n, n))
+    rho1 = np.zeros((3, n, n))
+    for d, (cx, cy) in enumerate(centres):
+        m = (X - cx) ** 2 + (Y - cy) ** 2 <= radius ** 2
+        rho0[d][m] += 1.0
+        rho1[(d + 1) % 3][m] += 1.0
+    return rho0 / rho0.sum(), rho1 / rho1.sum()

@@ -65,6 +65,10 @@ def test_envelope_dalpha_recolor_closed_form():
 
 
 def test_envelope_directional_derivatives_match_finite_differences():
+    """32 mass-preserving directions (the differentiable configuration's count); central
+    differences (h = 1e-4) of the FP64 oracle's optimal value, each perturbed solve warm-started
+    from the unperturbed optimum and run to gap 1e-11.  V is piecewise linear in rho1 where the
+    optimal phi is not unique, so a few directions may sit on a kink."""
     n = 8
     r0, r1 = S.blob_pair(n, 3, seed=51)
     rho1 = _t(r1).requires_grad_(True)
@@ -73,15 +77,17 @@ def test_envelope_directional_derivatives_match_finite_differences():
     cost.backward()
     g = rho1.grad.cpu().numpy().astype(np.float64)
     kw = dict(alpha=1.0, tau=3.0, max_iters=600000, check_every=200, tol_gap=1e-11, tol_res=1e-11)
+    base = oracle.vomt_solve(r0, r1, K3, **kw)
+    init = {x: base[x] for x in ("ux", "uy", "w", "phi")}
     h = 1e-4
     agree = 0
-    dirs = S.mass_preserving_directions(r1, 8, seed=52)
+    dirs = S.mass_preserving_directions(r1, 32, seed=52)
     for d in dirs:
-        Vp = oracle.vomt_solve(r0, r1 + h * d, K3, **kw)["metrics"]["primal"]
-        Vm = oracle.vomt_solve(r0, r1 - h * d, K3, **kw)["metrics"]["primal"]
+        Vp = oracle.vomt_solve(r0, r1 + h * d, K3, init=init, **kw)["metrics"]["primal"]
+        Vm = oracle.vomt_solve(r0, r1 - h * d, K3, init=init, **kw)["metrics"]["primal"]
         fd = (Vp - Vm) / (2 * h)
         agree += abs(fd - np.sum(g * d)) <= 1e-2 * abs(fd) + 1e-7
-    assert agree >= 6
+    assert agree >= 28, agree
 
 
 def test_batched_forward_backward():
@@ -100,8 +106,50 @@ def test_batched_forward_backward():
     assert d.type == "cuda"
 
 
+def _kink_margin(r0, r1, T, tau, w_norm, alpha=1.0):
+    """Smallest relative distance |arg - threshold| / threshold over the T iterations of the
+    oracle's map from zero, over every shrink of Appendix B the iteration applies (per-channel
+    ||(u_x, u_y) + mu grad phi|| against mu, and |w + nu grad_G phi| or its norm against alpha nu).
+    The unrolled map is smooth wherever this stays away from 0."""
+    k, n = r0.shape[0], r0.shape[-1]
+    o = oracle.vomt_solve(r0, r1, K3, alpha, tau=tau, max_iters=1, check_every=1)
+    mu, nu = o["mu"], o["nu"]
+    st = dict(ux=np.zeros((k, n, n)), uy=np.zeros((k, n, n)), w=np.zeros((3, n, n)), phi=np.zeros((k, n, n)))
+    m = np.inf
+    for _ in range(T):
+        gx, gy = oracle.grad(st["phi"])
+        s = np.hypot(st["ux"] + mu * gx, st["uy"] + mu * gy)
+        m = min(m, float(np.min(np.abs(s - mu) / mu)))
+        x = st["w"] + nu * oracle.grad_G(st["phi"], K3)
+        a = np.abs(x) if w_norm == 0 else np.linalg.norm(x, axis=0)
+        m = min(m, float(np.min(np.abs(a - alpha * nu) / (alpha * nu))))
+        o = oracle.vomt_solve(r0, r1, K3, alpha, tau=tau, max_iters=1, check_every=1, init=st, w_norm=w_norm)
+        st = {q: o[q] for q in ("ux", "uy", "w", "phi")}
+    return m
+
+
+@pytest.mark.parametrize("n,T", [(8, 30), (16, 10)])
+@pytest.mark.parametrize("w_norm", [0, 1])
+def test_unrolled_gradient_matches_oracle_away_from_kinks(n, T, w_norm):
+    """Where no shrink argument comes near its threshold (checked in the oracle: at least 1%
+    away, while FP32 perturbs arguments by about 1e-6 relative), the FP32 reverse mode equals
+    the FP64 oracle's to the parity bar, 1e-3 relative L2."""
+    r0, r1 = S.blob_pair(n, 3, seed=41)
+    r0d, r1d = r0.astype(np.float32).astype(np.float64), r1.astype(np.float32).astype(np.float64)
+    assert _kink_margin(r0d, r1d, T, 3.0, w_norm) > 1e-2
+    J, d0, d1, da = A.unrolled_grad(_t(r0), _t(r1), K3, 1.0, T=T, ckpt=10, tau=3.0, w_norm=w_norm)
+    Jo, g1, g0, gao = oracle.unrolled_grad(r0d, r1d, K3, 1.0, T, tau=3.0, w_norm=w_norm)
+    assert J == pytest.approx(Jo, rel=1e-5)
+    assert _rel(d1.cpu().numpy().astype(np.float64), g1) < 1e-3
+    assert _rel(d0.cpu().numpy().astype(np.float64), g0) < 1e-3
+    assert da == pytest.approx(gao, rel=1e-3)
+
+
 @pytest.mark.parametrize("w_norm", [0, 1])
 def test_unrolled_gradient_matches_oracle(w_norm):
+    """16 x 16, T = 60: here some shrink argument passes within 3e-5 (relative) of its
+    threshold (_kink_margin), so FP32 rounding can put a point on the other side of a kink for
+    an iteration; the bar is 1e-2 relative L2 for this kinked case."""
     n, T = 16, 60
     r0, r1 = S.blob_pair(n, 3, seed=41)
     J, d0, d1, da = A.unrolled_grad(_t(r0), _t(r1), K3, 1.0, T=T, ckpt=20, tau=3.0, w_norm=w_norm)
