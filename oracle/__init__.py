@@ -122,7 +122,7 @@ def _load(openmp: bool = False):
             "orc_zgrad_L_point": (None, [i, i, p, p, p]),
             "orc_zdiv_L_point": (None, [i, i, p, p, p]),
             "orc_zquantum_lmax": (d, [i, i, p]),
-            "orc_zmomt_solve": (i, [i, i, i, p, p, p, d, d, d, d, i, i, d, d, p, p, p, p, p, p, i]),
+            "orc_zmomt_solve": (i, [i, i, i, p, p, p, d, i, i, d, d, d, i, i, d, d, p, p, p, p, p, p, i]),
             "orc_spectral_norm": (d, [i, p]),
             "orc_shrink_nuc": (None, [i, p, d, p]),
             "orc_vomt_unrolled_grad": (d, [i, i, i, p, p, p, p, p, d, d, d, d, i, i, p, p, p]),
@@ -581,9 +581,10 @@ def zquantum_lmax(L) -> float:
 
 
 def zmomt_solve(Lam0, Lam1, L, alpha=1.0, tau=None, mu=None, nu=None, max_iters=2000, check_every=100,
-                tol_gap=0.0, tol_res=0.0, init=None, history=False):
+                tol_gap=0.0, tol_res=0.0, init=None, history=False, u_norm=U_L2, w_norm=W_L2):
     """The M-OMT iteration of Section 7.3 on complex Hermitian densities (Section 4's complex
-    setting), Frobenius norms ||U||_2 and ||W||_2, FP64.
+    setting), FP64, with the Frobenius norms ||U||_2, ||W||_2 (u_norm U_L2, w_norm W_L2, the
+    defaults) or the entrywise ||U||_1, ||W||_1 (U_L1, W_L1: sums of the entries' moduli).
 
     Lam0, Lam1: [k*k, n, n] complex Hermitian matrices per cell.  L: [N, k, k] complex
     Hermitian.  mu defaults to 1/(32 tau (n-1)^2), nu to 1/(4 tau lambda_max(-Delta_L)).
@@ -608,8 +609,11 @@ def zmomt_solve(Lam0, Lam1, L, alpha=1.0, tau=None, mu=None, nu=None, max_iters=
     nchk = max_iters // max(check_every, 1) + 2
     hist = np.zeros((nchk, NMET))
     met = np.zeros(NMET)
-    it = _load().orc_zmomt_solve(n, k, N, _ptr(L), _ptr(Lam0), _ptr(Lam1), float(alpha), float(tau), float(mu),
-                                 float(nu), int(max_iters), int(check_every), float(tol_gap), float(tol_res),
+    if u_norm not in (U_L2, U_L1) or w_norm not in (W_L2, W_L1):
+        raise ValueError("complex matrix OMT: Frobenius or entrywise norms")
+    it = _load().orc_zmomt_solve(n, k, N, _ptr(L), _ptr(Lam0), _ptr(Lam1), float(alpha), int(u_norm), int(w_norm),
+                                 float(tau), float(mu), float(nu), int(max_iters), int(check_every),
+                                 float(tol_gap), float(tol_res),
                                  _ptr(Ux), _ptr(Uy), _ptr(W), _ptr(Phi), _ptr(met), _ptr(hist), nchk)
     out = dict(Ux=Ux, Uy=Uy, W=W, Phi=Phi, iters=it, mu=mu, nu=nu, tau=tau, metrics=dict(zip(MET_NAMES, met)))
     if history:

@@ -1847,10 +1847,41 @@ static void zshrink2(int m, const zdbl *x, double t, zdbl *out)
     for (int q = 0; q < m; ++q) out[q] = f * x[q];
 }
 
+/* Entrywise modulus shrink of m complex entries: the prox of t sum_q |z_q|, which
+ * scales each entry by max(0, 1 - t / |z_q|) (shrink_2 of Appendix B on each entry
+ * seen as a point of the plane). */
+static void zshrink1(int m, const zdbl *x, double t, zdbl *out)
+{
+    for (int q = 0; q < m; ++q) {
+        const double a = cabs(x[q]);
+        out[q] = (a > t) ? (1.0 - t / a) * x[q] : 0.0;
+    }
+}
+
+/* Norms of the complex setting (Section 6.2): the Frobenius norm ||.||_2 (square
+ * root of the summed squared moduli) or, `entrywise`, ||.||_1 (the summed moduli of
+ * the entries).  Their duals: the Frobenius norm and the largest modulus.  Codes as
+ * for real matrices: u_norm 1 = ||U||_2, 2 = ||U||_1; w_norm 1 = ||W||_2, 0 = ||W||_1. */
+static double znorm(int m, const zdbl *x, int entrywise)
+{
+    double s = 0.0;
+    if (entrywise) { for (int q = 0; q < m; ++q) s += cabs(x[q]); return s; }
+    for (int q = 0; q < m; ++q) s += zsq(x[q]);
+    return sqrt(s);
+}
+
+static double zdualnorm(int m, const zdbl *x, int entrywise)
+{
+    double s = 0.0;
+    if (entrywise) { for (int q = 0; q < m; ++q) if (cabs(x[q]) > s) s = cabs(x[q]); return s; }
+    for (int q = 0; q < m; ++q) s += zsq(x[q]);
+    return sqrt(s);
+}
+
 void orc_zmomt_metrics(int n, int k, int N, const zdbl *L, const zdbl *Lam0, const zdbl *Lam1, double alpha,
-                       double mu, double nu, double tau, const zdbl *Ux, const zdbl *Uy, const zdbl *W,
-                       const zdbl *Phi, const zdbl *pUx, const zdbl *pUy, const zdbl *pW, const zdbl *pPhi,
-                       double *out)
+                       int u_norm, int w_norm, double mu, double nu, double tau, const zdbl *Ux, const zdbl *Uy,
+                       const zdbl *W, const zdbl *Phi, const zdbl *pUx, const zdbl *pUy, const zdbl *pW,
+                       const zdbl *pPhi, double *out)
 {
     int kk = k * k;
     size_t nn = (size_t)n * n, nk = (size_t)kk * nn;
@@ -1859,10 +1890,10 @@ void orc_zmomt_metrics(int n, int k, int N, const zdbl *L, const zdbl *Lam0, con
     zdbl X[64], Z[8 * 64], Y[64];
     double P = 0.0, D = 0.0, rr = 0.0, bb = 0.0, di = 0.0, R = 0.0;
     for (size_t p = 0; p < nn; ++p) {
-        double su = 0.0, sw = 0.0;
-        for (int q = 0; q < kk; ++q) su += zsq(Ux[q * nn + p]) + zsq(Uy[q * nn + p]);
-        for (int q = 0; q < N * kk; ++q) sw += zsq(W[q * nn + p]);
-        P += sqrt(su) + alpha * sqrt(sw);
+        zdbl u2[128];                /* U_x and U_y of this point, side by side */
+        for (int q = 0; q < kk; ++q) { u2[q] = Ux[q * nn + p]; u2[kk + q] = Uy[q * nn + p]; }
+        for (int q = 0; q < N * kk; ++q) Z[q] = W[q * nn + p];
+        P += znorm(2 * kk, u2, u_norm == 2) + alpha * znorm(N * kk, Z, w_norm == 0);
     }
     for (size_t q = 0; q < nk; ++q) D += creal(Phi[q] * conj(Lam1[q] - Lam0[q]));
     zdiv(n, kk, Ux, Uy, dv);
@@ -1877,12 +1908,12 @@ void orc_zmomt_metrics(int n, int k, int N, const zdbl *L, const zdbl *Lam0, con
     }
     zgrad(n, kk, Phi, gx, gy);
     for (size_t p = 0; p < nn; ++p) {
-        double s = 0.0, w2 = 0.0;
-        for (int q = 0; q < kk; ++q) { s += zsq(gx[q * nn + p]) + zsq(gy[q * nn + p]); X[q] = Phi[q * nn + p]; }
+        zdbl g2[128];
+        for (int q = 0; q < kk; ++q) { g2[q] = gx[q * nn + p]; g2[kk + q] = gy[q * nn + p]; X[q] = Phi[q * nn + p]; }
         orc_zgrad_L_point(k, N, L, X, Z);
-        for (int q = 0; q < N * kk; ++q) w2 += zsq(Z[q]);
-        if (sqrt(s) - 1.0 > di) di = sqrt(s) - 1.0;
-        if (sqrt(w2) - alpha > di) di = sqrt(w2) - alpha;
+        const double s = zdualnorm(2 * kk, g2, u_norm == 2), w2 = zdualnorm(N * kk, Z, w_norm == 0);
+        if (s - 1.0 > di) di = s - 1.0;
+        if (w2 - alpha > di) di = w2 - alpha;
     }
     if (pUx) {
         size_t nw = (size_t)N * kk * nn;
@@ -1914,11 +1945,14 @@ void orc_zmomt_metrics(int n, int k, int N, const zdbl *L, const zdbl *Lam0, con
     free(dv); free(dl); free(gx); free(gy);
 }
 
-/* The M-OMT iteration of Section 7.3 on complex Hermitian fields, Frobenius norms. */
+/* The M-OMT iteration of Section 7.3 on complex Hermitian fields, with the
+ * Frobenius norms or the entrywise ||.||_1 (whose shrink acts on each complex entry
+ * by its modulus; Hermitian and skew-Hermitian structure is kept because an entry and
+ * its mirror have the same modulus). */
 int orc_zmomt_solve(int n, int k, int N, const zdbl *L, const zdbl *Lam0, const zdbl *Lam1, double alpha,
-                    double tau, double mu, double nu, int max_iters, int check_every, double tol_gap,
-                    double tol_res, zdbl *Ux, zdbl *Uy, zdbl *W, zdbl *Phi, double *metrics, double *history,
-                    int hist_cap)
+                    int u_norm, int w_norm, double tau, double mu, double nu, int max_iters, int check_every,
+                    double tol_gap, double tol_res, zdbl *Ux, zdbl *Uy, zdbl *W, zdbl *Phi, double *metrics,
+                    double *history, int hist_cap)
 {
     int kk = k * k;
     size_t nn = (size_t)n * n, nk = (size_t)kk * nn, nw = (size_t)N * kk * nn;
@@ -1938,14 +1972,16 @@ int orc_zmomt_solve(int n, int k, int N, const zdbl *L, const zdbl *Lam0, const 
                 v[q] = Ux[q * nn + p] + mu * gx[q * nn + p];
                 v[kk + q] = Uy[q * nn + p] + mu * gy[q * nn + p];
             }
-            zshrink2(2 * kk, v, mu, o);
+            if (u_norm == 2) zshrink1(2 * kk, v, mu, o);
+            else zshrink2(2 * kk, v, mu, o);
             for (int q = 0; q < kk; ++q) { nUx[q * nn + p] = o[q]; nUy[q * nn + p] = o[kk + q]; }
         }
         for (size_t p = 0; p < nn; ++p) {
             for (int q = 0; q < kk; ++q) X[q] = Phi[q * nn + p];
             orc_zgrad_L_point(k, N, L, X, xw);
             for (int q = 0; q < N * kk; ++q) xw[q] = W[q * nn + p] + nu * xw[q];
-            zshrink2(N * kk, xw, alpha * nu, ow);
+            if (w_norm == 0) zshrink1(N * kk, xw, alpha * nu, ow);
+            else zshrink2(N * kk, xw, alpha * nu, ow);
             for (int q = 0; q < N * kk; ++q) nW[q * nn + p] = ow[q];
         }
         for (size_t q = 0; q < nk; ++q) { bx[q] = 2.0 * nUx[q] - Ux[q]; by[q] = 2.0 * nUy[q] - Uy[q]; }
@@ -1961,7 +1997,8 @@ int orc_zmomt_solve(int n, int k, int N, const zdbl *L, const zdbl *Lam0, const 
         int check = (t % check_every == 0) || (t == max_iters);
         double m[ORC_NMET];
         if (check) {
-            orc_zmomt_metrics(n, k, N, L, Lam0, Lam1, alpha, mu, nu, tau, nUx, nUy, nW, Phi, Ux, Uy, W, pPhi, m);
+            orc_zmomt_metrics(n, k, N, L, Lam0, Lam1, alpha, u_norm, w_norm, mu, nu, tau, nUx, nUy, nW, Phi, Ux, Uy,
+                              W, pPhi, m);
             m[6] = (double)t;
             m[7] = (tol_gap > 0.0 && m[2] <= tol_gap && m[3] <= tol_res) ? 1.0 : 0.0;
             if (history && nh < hist_cap) { memcpy(history + (size_t)nh * ORC_NMET, m, sizeof m); ++nh; }

@@ -57,8 +57,9 @@ def test_real_inputs_equal_the_real_oracle(k):
     assert z["metrics"]["fp_resid"] == pytest.approx(r["metrics"]["fp_resid"], rel=1e-9)
 
 
-def test_unitary_equivariance():
-    n, k = 6, 2
+@pytest.mark.parametrize("k", [2, 3])
+def test_unitary_equivariance(k):
+    n = 6
     rng = np.random.default_rng(11)
     A0, A1 = S.hermitian_field_pair(n, k, seed=12)
     L = S.random_hermitian_L(k, 3, seed=13)
@@ -138,3 +139,74 @@ def test_iteration_keeps_structure():
     assert np.all(o["Ux"][..., -1] == 0) and np.all(o["Uy"][:, -1, :] == 0)
     R = o["history"][:, 4]
     assert np.all(np.diff(R) <= 1e-12 * R[0])
+
+
+# ---------------------------------------------------------------- the entrywise ||.||_1
+@pytest.mark.parametrize("k", [2, 3])
+def test_entrywise_norm_with_real_inputs_equals_the_real_oracle(k):
+    """||U||_1, ||W||_1 as sums of entry moduli: on real symmetric inputs with real L the
+    modulus of an entry is its absolute value, so the iterates must equal the real oracle's
+    entrywise-norm iteration (which the LP and closed-form pins fix) element by element."""
+    n = 7
+    L0, L1 = S.tensor_field_pair(n, k, seed=40 + k)
+    L0, L1 = L0 * n * n, L1 * n * n
+    L = S.random_L(k, 3, seed=41)
+    kw = dict(tau=10.0, max_iters=300, check_every=100)
+    r = oracle.momt_solve(L0, L1, L, 0.7, u_norm=oracle.U_L1, w_norm=oracle.W_L1, **kw)
+    z = oracle.zmomt_solve(L0.astype(np.complex128), L1.astype(np.complex128), L.astype(np.complex128), 0.7,
+                           u_norm=oracle.U_L1, w_norm=oracle.W_L1, **kw)
+    for key in ("Ux", "Uy", "W", "Phi"):
+        assert np.all(z[key].imag == 0.0)
+        np.testing.assert_allclose(z[key].real, r[key], rtol=0, atol=1e-12 * max(np.abs(r[key]).max(), 1e-30))
+    for m in ("primal", "dual", "rel_res", "dual_infeas"):
+        assert z["metrics"][m] == pytest.approx(r["metrics"][m], rel=1e-10, abs=1e-14), m
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_entrywise_norm_diagonal_unitary_equivariance(k):
+    """A diagonal unitary D = diag(exp(i theta_a)) multiplies entry (a, b) by
+    exp(i (theta_a - theta_b)) and keeps every modulus, so conjugating the densities and
+    the L_l by D conjugates every iterate by D.  A shrink that treated the real and
+    imaginary parts separately, or a Frobenius shrink, would break this."""
+    n = 6
+    rng = np.random.default_rng(50 + k)
+    A0, A1 = S.hermitian_field_pair(n, k, seed=51)
+    A0, A1 = A0 * n * n, A1 * n * n
+    L = S.random_hermitian_L(k, 3, seed=52)
+    D = np.diag(np.exp(1j * rng.uniform(0, 2 * np.pi, k)))
+    kw = dict(tau=10.0, max_iters=300, check_every=100, u_norm=oracle.U_L1, w_norm=oracle.W_L1)
+    a = oracle.zmomt_solve(A0, A1, L, 0.6, **kw)
+    LD = np.einsum("ab,sbc,dc->sad", D, L, D.conj())
+    b = oracle.zmomt_solve(_conj_field(D, A0), _conj_field(D, A1), LD, 0.6, **kw)
+    for key in ("Ux", "Uy", "W", "Phi"):
+        expect = _conj_field(D, a[key])
+        assert np.abs(b[key] - expect).max() <= 1e-10 * max(np.abs(expect).max(), 1e-30), key
+    assert b["metrics"]["primal"] == pytest.approx(a["metrics"]["primal"], rel=1e-10)
+    # the entrywise norm is not invariant under a general unitary: the iterates then differ
+    V = _rand_unitary(rng, k)
+    LV = np.einsum("ab,sbc,dc->sad", V, L, V.conj())
+    c = oracle.zmomt_solve(_conj_field(V, A0), _conj_field(V, A1), LV, 0.6, **kw)
+    expect = _conj_field(V, a["Phi"])
+    assert np.abs(c["Phi"] - expect).max() > 1e-6 * np.abs(expect).max()
+
+
+def test_entrywise_metrics_and_structure():
+    """With ||.||_1 the iteration keeps U, Phi Hermitian and W skew-Hermitian (an entry and
+    its mirror have equal moduli, so the entrywise shrink keeps the pairing), R does not
+    increase, and the reported primal is the summed entry moduli of U plus alpha times those
+    of W."""
+    n, k = 6, 3
+    A0, A1 = S.hermitian_field_pair(n, k, seed=61)
+    A0, A1 = A0 * n * n, A1 * n * n
+    L = S.random_hermitian_L(k, 2, seed=62)
+    alpha = 0.8
+    o = oracle.zmomt_solve(A0, A1, L, alpha, max_iters=400, check_every=50, history=True, u_norm=oracle.U_L1,
+                           w_norm=oracle.W_L1)
+    for key in ("Ux", "Uy", "Phi"):
+        assert _herm_err(o[key], k) <= 1e-12 * max(np.abs(o[key]).max(), 1e-30)
+    assert _herm_err(o["W"], k, sign=-1) <= 1e-12 * max(np.abs(o["W"]).max(), 1e-30)
+    R = o["history"][:, 4]
+    assert np.all(np.diff(R) <= 1e-12 * R[0])
+    P = np.abs(o["Ux"]).sum() + np.abs(o["Uy"]).sum() + alpha * np.abs(o["W"]).sum()
+    assert o["metrics"]["primal"] == pytest.approx(P, rel=1e-12)
+    assert np.abs(o["W"]).max() > 0.0
