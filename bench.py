@@ -53,10 +53,11 @@ BYTES_PER_GP_IT = 4 * (7 * K + 2 * len(EDGES))   # read phi,u_x,u_y,w,b; write p
 REF_TAU = 300.0             # tau of the reference arm's oracle sample (its cost per iteration does not depend on tau)
 
 
-def workload_name(alphas=ALPHAS, cap=CAP):
+def workload_name(alphas=ALPHAS, cap=CAP, tau=None):
     return ("vector OMT, 256x256 grid, k=3 colour-image densities (seed 1002), complete graph K3, "
-            "alpha in {%s}, ||u||_{1,2} ||w||_1, tau tuned per alpha (vomt_tune_tau), to rel gap and rel res "
-            "<= 1e-5, cap %d it" % (",".join("%g" % a for a in alphas), cap))
+            "alpha in {%s}, ||u||_{1,2} ||w||_1, %s, to rel gap and rel res <= 1e-5, cap %d it"
+            % (",".join("%g" % a for a in alphas),
+               "tau tuned per alpha (vomt_tune_tau)" if tau is None else "tau=%g" % tau, cap))
 
 
 WORKLOAD = workload_name()
@@ -703,7 +704,10 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
 
     alphas, cap = args.alphas, args.cap
-    taus, tune_info = tune_taus(d0, d1, alphas)
+    if args.tau is not None:
+        taus, tune_info = {a: args.tau for a in alphas}, {"fixed": args.tau}
+    else:
+        taus, tune_info = tune_taus(d0, d1, alphas)
 
     def step(results):
         for a in alphas:
@@ -780,13 +784,14 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(alphas, cap), "n": N, "k": K, "edges": l, "alphas": list(alphas),
+        "config": {"workload": workload_name(alphas, cap, args.tau), "n": N, "k": K, "edges": l, "alphas": list(alphas),
                    "tau": {"alpha=%g" % a: taus[a] for a in alphas}, "tol": TOL, "cap": cap,
                    "check_every": CHECK_EVERY, "engine": engine,
                    "l2": "flushed (512 MB write) between timed steps",
                    "parallelism": "independent replicas, one per GPU" if world > 1 else "single GPU"},
         "tau_tuning": dict(tune_info, note="vomt_tune_tau once per alpha before the warm-up (outside the timed "
-                                           "region), sample_iters=%d" % TUNE_ITERS),
+                                           "region), sample_iters=%d" % TUNE_ITERS if args.tau is None else
+                                           "tau fixed by --tau (profiler run)"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": traffic,
                      "kernel": "k_resident" if engine == "resident" else "k_step",
@@ -832,6 +837,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cap", type=int, default=CAP, help="iteration cap per solve (profiler runs only)")
     ap.add_argument("--alphas", type=float, nargs="+", default=list(ALPHAS), help="(profiler runs only)")
+    ap.add_argument("--tau", type=float, default=None,
+                    help="use this tau for every alpha instead of the tuner's (profiler runs only: fixes the "
+                         "launch sequence)")
     ap.add_argument("--only-extra", default=None,
                     help="run one named extra measurement alone and print it (profiler runs only)")
     args = ap.parse_args()

@@ -139,7 +139,8 @@ typedef struct {
     int blocks;          /* thread blocks of the main launch (resident: one tile each) */
     int halo;            /* resident engine: iterations between halo exchanges (0 otherwise) */
     int variant;         /* form of the main step kernel: 1 = inputs staged by TMA tiles,
-                            0 = per-thread loads (streaming and 3-D solves; 0 otherwise) */
+                            0 = per-thread loads (streaming and 3-D solves); for
+                            vomt_solve_batched: 1 = the solve ran as one CUDA graph launch */
 } vomt_result;
 
 /* Create a context on CUDA device `device`.  The context owns the solver's
@@ -284,7 +285,8 @@ int vomt_batch_layout(int count, vomt_instance *inst, size_t *total_floats);
 /* Solve every instance by the iteration of Section 7.2, each to its own
  * stopping point (tolerance or p->max_iters, checked every p->check_every
  * iterations, as in vomt_solve).  mu and nu follow the paper's rule per
- * instance; p->mu, p->nu and p->halo are ignored.  Two paths:
+ * instance; p->mu, p->nu and p->halo are ignored.  Both paths run as one CUDA
+ * graph launch per call where they can (results[q].variant = 1).  Two paths:
  *   one block per instance (p->engine == VOMT_ENGINE_STREAM): one persistent
  *     launch; thread blocks take instances from a device queue (largest first)
  *     and run the fused streaming step on each.  When `stream` is not the
@@ -294,7 +296,11 @@ int vomt_batch_layout(int count, vomt_instance *inst, size_t *total_floats);
  *   grouped (p->engine == VOMT_ENGINE_RESIDENT): instances of equal channel
  *     count and side form a wave; one cooperative launch per wave splits the
  *     SMs into groups of T tiles and each group runs the resident algorithm on
- *     its share of the wave, one instance after another.  Needs k <= 5 and
+ *     its share of the wave, one instance after another.  The waves' launches
+ *     are captured into one CUDA graph (on `stream`, or on a private stream of
+ *     the context when `stream` is the legacy default stream) on the first call
+ *     and replayed by later calls with the same instances, arena and
+ *     parameters.  Needs k <= 5 and
  *     p->max_iters < 2^20 - 2 (else VOMT_ERR_TOO_LARGE).
  * VOMT_ENGINE_AUTO or VOMT_ENGINE_BATCHED: the path vomt_batch_tune found
  * faster on ctx, else the one a cost model estimates faster.
@@ -372,9 +378,16 @@ int momt_solve(vomt_ctx *ctx, int n, int k, const float *Lam0, const float *Lam1
 
 /* Complex Hermitian matrix OMT: Section 4's complex setting (Hermitian densities
  * and L_l, skew-Hermitian W, the Hilbert-Schmidt product Re tr(X Y*)), iterated
- * as in Section 7.3 with the Frobenius norms ||U||_2 and ||W||_2 (p->u_norm
- * VOMT_U_L2 or the default, p->w_norm VOMT_W_L2; anything else is BAD_ARG).
- *   k = 2 (a Hermitian 2 x 2 field is 4 real coordinates), 1 <= N <= 7.
+ * as in Section 7.3.  Norms (Section 6.2, per point): p->u_norm VOMT_U_L2 (or
+ * the default) is the Frobenius norm ||U||_2 of (U_x, U_y), VOMT_U_L1 the
+ * entrywise ||U||_1 = sum of the moduli |U_ab| of both directions' entries;
+ * p->w_norm VOMT_W_L2 is ||W||_2, VOMT_W_L1 the entrywise ||W||_1 (anything else
+ * is BAD_ARG).  The entrywise shrink scales each complex entry by
+ * max(0, 1 - t / |z|) (Appendix B's shrink_2 on the entry as a point of the plane).
+ *   k = 2 (a Hermitian 2 x 2 field is 4 real coordinates), 1 <= N <= 9; or
+ *   k = 3 (9 real coordinates), 1 <= N <= 4.  3 x 3 fields and the entrywise
+ *   norms run on the resident engine only: VOMT_ENGINE_STREAM is BAD_ARG, and a
+ *   grid beyond the resident engine's reach is VOMT_ERR_TOO_LARGE.
  *   L: host, N complex k x k Hermitian matrices as (re, im) double pairs,
  *      row-major: L[((s*k + a)*k + b)*2 + {0, 1}].
  *   Lam0, Lam1: device [2][k*k][n][n] floats, the real parts then the imaginary

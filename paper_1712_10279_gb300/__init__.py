@@ -276,11 +276,12 @@ def momt_tune_tau(Lam0, Lam1, L, alpha: float = 1.0, *, u_norm: int = U_L2, w_no
 
 def momt_solve_complex(Lam0, Lam1, L, alpha: float = 1.0, *, tau=None, mu=None, nu=None, max_iters: int = 2000,
                        check_every: int = 100, tol_gap: float = 0.0, tol_res: float = 0.0, init=None, engine="auto",
-                       halo: int = 0, stream=None) -> MatrixSolution:
-    """Complex Hermitian matrix OMT (Section 4's complex setting, Section 7.3 iteration) with
-    the Frobenius norms ||U||_2, ||W||_2, on the GPU.
+                       halo: int = 0, stream=None, u_norm: int = U_L2, w_norm: int = W_L2) -> MatrixSolution:
+    """Complex Hermitian matrix OMT (Section 4's complex setting, Section 7.3 iteration) on
+    the GPU, with the Frobenius norms ||U||_2, ||W||_2 (U_L2, W_L2) or the entrywise
+    ||U||_1, ||W||_1 (U_L1, W_L1: sums of the entries' moduli).
 
-    Lam0, Lam1: CUDA complex tensors [k*k, n, n] (k = 2) of Hermitian matrices.  L: [N, k, k]
+    Lam0, Lam1: CUDA complex tensors [k*k, n, n] (k = 2 or 3) of Hermitian matrices.  L: [N, k, k]
     complex Hermitian (numpy, host).  Returns complex64 U [2, k*k, n, n], W [N, k*k, n, n],
     Phi [k*k, n, n].  The complex tensors are split into real and imaginary planes for the
     library and joined again on return (layout marshalling only).
@@ -309,7 +310,7 @@ def momt_solve_complex(Lam0, Lam1, L, alpha: float = 1.0, *, tau=None, mu=None, 
         U = torch.empty((2, 2, kk, n, n), device=dev, dtype=torch.float32)
         W = torch.empty((N, 2, kk, n, n), device=dev, dtype=torch.float32)
         Phi = torch.empty((2, kk, n, n), device=dev, dtype=torch.float32)
-    p = _params(tau, mu, nu, U_L2, W_L2, max_iters, check_every, tol_gap, tol_res, init is not None, engine, halo)
+    p = _params(tau, mu, nu, u_norm, w_norm, max_iters, check_every, tol_gap, tol_res, init is not None, engine, halo)
     res = _native.Result()
     st = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
     ctx = _native.context(dev.index if dev.index is not None else torch.cuda.current_device())

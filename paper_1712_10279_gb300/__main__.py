@@ -34,6 +34,9 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=200)
     ap.add_argument("--check-every", type=int, default=100)
     ap.add_argument("--tol", type=float, default=0.0)
+    ap.add_argument("--tau", type=float, default=None, help="dual step (default: Table 1 / Table 3 value)")
+    ap.add_argument("--norms", default="default", choices=["default", "nuclear"],
+                    help="matrix OMT: nuclear = ||U||_{1,nuc} ||W||_{1,nuc}")
     ap.add_argument("--engine", default="auto", choices=["auto", "stream", "resident"])
     ap.add_argument("--halo", type=int, default=0, help="2-D resident engine: halo; 3-D: z planes per block")
     ap.add_argument("--seed", type=int, default=1002)
@@ -76,14 +79,15 @@ def main(argv=None):
     d1 = torch.from_numpy(r1.astype(np.float32)).to(dev)
     edges = S.complete_graph(args.k)
     res, ms = None, 0.0
-    kw = dict(max_iters=args.iters, check_every=args.check_every, tol_gap=args.tol, tol_res=args.tol)
+    kw = dict(max_iters=args.iters, check_every=args.check_every, tol_gap=args.tol, tol_res=args.tol, tau=args.tau)
+    mkw = dict(u_norm=3, w_norm=2) if args.norms == "nuclear" else {}
     for _ in range(max(1, args.repeat)):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         if args.matrix and args.dim == 3:
             sol = momt_solve3d(d0, d1, L, args.alpha, zc=args.halo, **kw)
         elif args.matrix:
-            sol = momt_solve(d0, d1, L, args.alpha, engine=args.engine, halo=args.halo, **kw)
+            sol = momt_solve(d0, d1, L, args.alpha, engine=args.engine, halo=args.halo, **mkw, **kw)
         elif args.dim == 3:
             sol = solve3d(d0, d1, edges, args.alpha, zc=args.halo, **kw)
         else:

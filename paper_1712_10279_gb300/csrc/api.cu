@@ -12,6 +12,9 @@ namespace vomt {
 
 int set_cuda_error(vomt_ctx *ctx, cudaError_t e, const char *what)
 {
+    // clear a non-sticky error from the thread's last-error slot, so that it does not
+    // surface in the caller's next unrelated CUDA call
+    (void)cudaGetLastError();
     if (ctx) {
         char buf[256];
         snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
@@ -140,21 +143,24 @@ void fill_result(vomt_ctx *ctx, const SolveCfg &cfg, int engine, vomt_result *r,
 {
     const DevStatus &h = ctx->hstatus[0];
     ctx->last_checks = h.checks;
+    double met[NMET];
+    for (int q = 0; q < NMET; ++q) met[q] = h.met[q];
+    if (h.raw) finish_raw_row(met);
     if (h.error) {
         *status = h.error;
         ctx->err = h.error == VOMT_ERR_NONFINITE ? "iterate became non-finite" : "device wait timed out";
     } else if (cfg.tol_gap > 0.0) {
-        *status = h.met[7] != 0.0 ? VOMT_OK : VOMT_NOT_CONVERGED;
+        *status = met[7] != 0.0 ? VOMT_OK : VOMT_NOT_CONVERGED;
     } else {
         *status = VOMT_OK;
     }
     if (r) {
-        r->primal = h.met[0];
-        r->dual = h.met[1];
-        r->rel_gap = h.met[2];
-        r->rel_res = h.met[3];
-        r->fp_resid = h.met[4];
-        r->dual_infeas = h.met[5];
+        r->primal = met[0];
+        r->dual = met[1];
+        r->rel_gap = met[2];
+        r->rel_res = met[3];
+        r->fp_resid = met[4];
+        r->dual_infeas = met[5];
         r->iters = h.iter;
         r->mu = cfg.mu;
         r->nu = cfg.nu;
@@ -191,6 +197,11 @@ int run_engine(vomt_ctx *ctx, const OpDev &op, const StepDev &s, const SolveCfg 
             return fail(ctx, VOMT_ERR_TOO_LARGE, "grid too large for the resident engine");
         }
     }
+    // the streaming kernels exist for up to VOMT_MAX_CHANNELS channels and the public norms
+    if (op.k > KVEC || p.u_norm == U_CL1 || p.w_norm == W_CL1)
+        return fail(ctx, VOMT_ERR_TOO_LARGE,
+                    "complex 3 x 3 fields and the complex entrywise norm run on the resident engine only, and the "
+                    "grid does not fit it");
     return stream_solve(ctx, op, s, cfg, p, rho0, rho1, u, w, phi, st);
 }
 
@@ -365,7 +376,7 @@ int vomt_solve_host(vomt_ctx *ctx, int n, const float *rho0, const float *rho1, 
                     const vomt_params *p, float *u, float *w, float *phi, vomt_result *result, void *stream)
 {
     try {
-        if (!ctx || !g || n < 2 || g->k < 1 || g->k > KMAX || g->n_edges < 0 || g->n_edges > LMAX)
+        if (!ctx || !g || n < 2 || g->k < 1 || g->k > KVEC || g->n_edges < 0 || g->n_edges > LVEC)
             return fail(ctx, VOMT_ERR_BAD_ARG, "bad arguments");
         if (!rho0 || !rho1 || !u || !phi || (g->n_edges > 0 && !w)) return fail(ctx, VOMT_ERR_BAD_ARG, "null array");
         cudaStream_t st = (cudaStream_t)stream;
@@ -422,6 +433,8 @@ int vomt_history(vomt_ctx *ctx, double *out, int cap)
         cudaError_t e = cudaSetDevice(ctx->device);
         if (e == cudaSuccess) e = cudaMemcpy(out, ctx->dhist, sizeof(double) * NMET * (size_t)m, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return set_cuda_error(ctx, e, "history copy");
+        if (ctx->hist_raw)
+            for (int q = 0; q < m; ++q) finish_raw_row(out + (size_t)q * NMET);
     }
     return rows;
 }

@@ -309,7 +309,7 @@ extern "C" int vomt_backward(vomt_ctx *ctx, int batch, int n, int pitch, int k, 
 {
     if (!ctx) return VOMT_ERR_BAD_ARG;
     ctx->err.clear();
-    if (batch < 1 || n < 2 || k < 1 || k > KMAX || n_edges < 0 || n_edges > LMAX || w_norm < 0 || w_norm > 1)
+    if (batch < 1 || n < 2 || k < 1 || k > KVEC || n_edges < 0 || n_edges > LVEC || w_norm < 0 || w_norm > 1)
         return fail(ctx, VOMT_ERR_BAD_ARG, "backward: bad sizes");
     if (pitch == 0) pitch = n;
     if (pitch < n) return fail(ctx, VOMT_ERR_BAD_ARG, "backward: pitch must be 0 or >= n");

@@ -27,7 +27,7 @@ namespace {
 
 using namespace dev;
 
-constexpr int BK = 8;                      // channels per instance (vector OMT, k <= 8)
+constexpr int BK = KVEC;                   // channels per instance (vector OMT, k <= 8)
 constexpr int BL = BK * (BK - 1) / 2;
 
 struct InstDev {
@@ -443,12 +443,17 @@ struct BatchState {
     size_t gstat_bytes = 0;
     DevStatus *hgstat = nullptr;
     int hgstat_cap = 0;
+    // grouped path: the waves captured as one CUDA graph, and what it was built for
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<unsigned char> gkey;
+    long long graph_replays = 0;     // grouped solves that ran as one graph launch
 };
 
 void batch_state_free(BatchState *b)
 {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
     cudaFree(b->dinst);
     cudaFree(b->dorder);
     cudaFree(b->dqueue);
@@ -496,7 +501,7 @@ extern "C" int vomt_batch_layout(int count, vomt_instance *inst, size_t *total_f
     size_t off = 0;
     for (int q = 0; q < count; ++q) {
         const int n = inst[q].n, k = inst[q].graph.k, l = inst[q].graph.n_edges;
-        if (n < 2 || k < 1 || k > KMAX || l < 0 || l > LMAX) return VOMT_ERR_BAD_ARG;
+        if (n < 2 || k < 1 || k > KVEC || l < 0 || l > LVEC) return VOMT_ERR_BAD_ARG;
         inst[q].offset = off;
         off += (size_t)(5 * k + l) * n * n;
         off = (off + 15) & ~(size_t)15;
@@ -539,10 +544,14 @@ static int batch_prepare(vomt_ctx *ctx, int count, const vomt_instance *inst, co
         I.eps_d = p.eps;
         I.su = (float)(1.0 / (1.0 + 2.0 * mu * p.eps));
         I.sw = (float)(1.0 / (1.0 + 2.0 * nu * p.eps));
-        memcpy(I.wc, op.wc, sizeof I.wc);
-        memcpy(I.we, op.we, sizeof I.we);
-        memcpy(I.G, op.G, sizeof I.G);
-        memcpy(I.Dv, op.Dv, sizeof I.Dv);
+        // the instance table holds vector-OMT operators (k <= 8): copy entry by entry
+        for (int c = 0; c < BK; ++c) I.wc[c] = op.wc[c];
+        for (int e = 0; e < BL; ++e) I.we[e] = op.we[e];
+        for (int e = 0; e < BL; ++e)
+            for (int c = 0; c < BK; ++c) {
+                I.G[e][c] = op.G[e][c];
+                I.Dv[c][e] = op.Dv[c][e];
+            }
         I.o_rho0 = in.offset;
         I.o_rho1 = in.offset + (size_t)k * nn;
         I.o_u = in.offset + (size_t)2 * k * nn;
@@ -633,8 +642,9 @@ static double queue_estimate(const std::vector<InstDev> &h, int iters, int sms)
 }
 
 static int grouped_solve(vomt_ctx *ctx, BatchState *b, int count, const std::vector<InstDev> &h, float *arena,
-                         const vomt_params &p, std::vector<Wave> &waves, cudaStream_t st)
+                         const vomt_params &p, std::vector<Wave> &waves, cudaStream_t st, bool *as_graph)
 {
+    *as_graph = false;
     const int nm = (p.u_norm == VOMT_U_L12 && p.w_norm == VOMT_W_L1) ? 1 : 0;
     // scratch: per wave, per group two job slots of exchange words and check rows
     size_t jobs_total = 0, scratch_words = 0;
@@ -686,10 +696,13 @@ static int grouped_solve(vomt_ctx *ctx, BatchState *b, int count, const std::vec
                                  res::row_stride(EWm), EHm};
             a.g.k = I.k;
             a.g.l = I.l;
-            memcpy(a.g.wc, I.wc, sizeof I.wc);
-            memcpy(a.g.we, I.we, sizeof I.we);
-            memcpy(a.g.G, I.G, sizeof I.G);
-            memcpy(a.g.Dv, I.Dv, sizeof I.Dv);
+            for (int c = 0; c < BK; ++c) a.g.wc[c] = I.wc[c];
+            for (int e = 0; e < BL; ++e) a.g.we[e] = I.we[e];
+            for (int e = 0; e < BL; ++e)
+                for (int c = 0; c < BK; ++c) {
+                    a.g.G[e][c] = I.G[e][c];
+                    a.g.Dv[c][e] = I.Dv[c][e];
+                }
             a.s = StepDev{I.n, I.ih, I.mu, I.nu, I.tau, I.alpha};
             a.cfg = SolveCfg{p.tol_gap, p.tol_res, I.mu_d, I.nu_d, I.tau_d, I.l > 0 ? 1 : 0};
             set_regularisation(&a.s, &a.cfg, p.eps, I.mu_d, I.nu_d);
@@ -719,9 +732,32 @@ static int grouped_solve(vomt_ctx *ctx, BatchState *b, int count, const std::vec
     }
     cudaError_t e = cudaMemcpyAsync(b->gjobs, jobs.data(), sizeof(res::ResArgs) * jobs_total, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->gvalid, valid.data(), sizeof(int) * jobs_total, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(dstat, 0, sizeof(DevStatus) * count, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, ctl_bytes, st);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "grouped setup");
+    // launch shape of every wave (attributes and occupancy are set outside any capture)
+    struct WaveLaunch {
+        res::MultiKernel kern;
+        int blocks, threads, smem;
+        size_t reset_bytes;
+        res::MultiArgs m;
+    };
+    std::vector<WaveLaunch> wl(waves.size());
+    // waves that share a kernel may need different shared memory: the kernel's limit is
+    // set to the largest of its waves, once, before any launch
+    std::vector<std::pair<res::MultiKernel, int>> limits;
+    for (const Wave &w : waves) {
+        const ResidentPlan &pl = w.plan;
+        const int EWm = pl.TXm + 2 * pl.H, EHm = pl.TYm + 2 * pl.H;
+        const int smem = res::smem_layout(w.k, res::row_stride(EWm), EHm, pl.Gx * pl.Gy).total;
+        res::MultiKernel kern = res::res_multi_kernel(w.k, pl.P, nm);
+        bool found = false;
+        for (auto &lim : limits)
+            if (lim.first == kern) { lim.second = std::max(lim.second, smem); found = true; }
+        if (!found) limits.push_back({kern, smem});
+    }
+    for (const auto &lim : limits) {
+        e = cudaFuncSetAttribute((const void *)lim.first, cudaFuncAttributeMaxDynamicSharedMemorySize, lim.second);
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "grouped smem attribute");
+    }
     for (size_t wi = 0; wi < waves.size(); ++wi) {
         const Wave &w = waves[wi];
         const ResidentPlan &pl = w.plan;
@@ -729,8 +765,6 @@ static int grouped_solve(vomt_ctx *ctx, BatchState *b, int count, const std::vec
         const int EWm = pl.TXm + 2 * pl.H, EHm = pl.TYm + 2 * pl.H;
         const res::SmemLayout SL = res::smem_layout(w.k, res::row_stride(EWm), EHm, T);
         res::MultiKernel kern = res::res_multi_kernel(w.k, pl.P, nm);
-        e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SL.total);
-        if (e != cudaSuccess) return set_cuda_error(ctx, e, "grouped smem attribute");
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)kern, pl.threads, SL.total);
         if (e != cudaSuccess) return set_cuda_error(ctx, e, "grouped occupancy");
@@ -739,23 +773,76 @@ static int grouped_solve(vomt_ctx *ctx, BatchState *b, int count, const std::vec
             ctx->err = "grouped wave does not fit on the device";
             return VOMT_ERR_TOO_LARGE;
         }
+        WaveLaunch &L = wl[wi];
+        L.kern = kern;
+        L.blocks = blocks;
+        L.threads = pl.threads;
+        L.smem = SL.total;
         // exchange words of an earlier wave must not match this wave's tags
-        e = cudaMemsetAsync(b->gscratch, 0, (size_t)w.groups * 2 *
-                                                ((size_t)T * 2 * ((3 * w.k + w.k * (w.k - 1) / 2 + 1) / 2) * pl.TXm * pl.TYm * 2 +
-                                                 (size_t)2 * T * NRED * 2) * 8, st);
-        if (e != cudaSuccess) return set_cuda_error(ctx, e, "grouped reset");
-        res::MultiArgs m;
-        m.jobs = (const res::ResArgs *)b->gjobs + wave_job0[wi];
-        m.valid = (const int *)b->gvalid + wave_job0[wi];
-        m.per = w.per;
-        m.T = T;
-        m.ctl = ctl;
-        void *args[] = {&m};
-        e = cudaLaunchCooperativeKernel((const void *)kern, dim3(blocks), dim3(pl.threads), args, SL.total, st);
-        if (e != cudaSuccess) return set_cuda_error(ctx, e, "grouped launch");
-        ++ctx->launches;
+        L.reset_bytes = (size_t)w.groups * 2 *
+                        ((size_t)T * 2 * ((3 * w.k + w.k * (w.k - 1) / 2 + 1) / 2) * pl.TXm * pl.TYm * 2 +
+                         (size_t)2 * T * NRED * 2) * 8;
+        memset(&L.m, 0, sizeof L.m);
+        L.m.jobs = (const res::ResArgs *)b->gjobs + wave_job0[wi];
+        L.m.valid = (const int *)b->gvalid + wave_job0[wi];
+        L.m.per = w.per;
+        L.m.T = T;
+        L.m.ctl = ctl;
     }
-    e = cudaMemcpyAsync(b->hgstat, dstat, sizeof(DevStatus) * count, cudaMemcpyDeviceToHost, st);
+    auto enqueue = [&](cudaStream_t q) -> cudaError_t {
+        cudaError_t r = cudaMemsetAsync(dstat, 0, sizeof(DevStatus) * count, q);
+        if (r == cudaSuccess) r = cudaMemsetAsync(ctl, 0, ctl_bytes, q);
+        for (size_t wi = 0; wi < wl.size() && r == cudaSuccess; ++wi) {
+            WaveLaunch &L = wl[wi];
+            r = cudaMemsetAsync(b->gscratch, 0, L.reset_bytes, q);
+            if (r != cudaSuccess) break;
+            void *args[] = {&L.m};
+            r = cudaLaunchCooperativeKernel((const void *)L.kern, dim3(L.blocks), dim3(L.threads), args, L.smem, q);
+        }
+        if (r == cudaSuccess) r = cudaMemcpyAsync(b->hgstat, dstat, sizeof(DevStatus) * count, cudaMemcpyDeviceToHost, q);
+        return r;
+    };
+    ctx->launches += (int)wl.size();
+    // One CUDA graph holds every wave's launch; it is replayed on `st` while the job tables
+    // and the launch shapes repeat (the tables are uploaded before each replay).  Capture
+    // runs on `st`, or on the context's private stream when `st` is the legacy stream.
+    std::vector<unsigned char> key;
+    auto put = [&key](const void *p, size_t n) {
+        const unsigned char *c = (const unsigned char *)p;
+        key.insert(key.end(), c, c + n);
+    };
+    put(&count, sizeof count);
+    put(jobs.data(), sizeof(res::ResArgs) * jobs_total);
+    put(valid.data(), sizeof(int) * jobs_total);
+    for (const WaveLaunch &L : wl) put(&L, sizeof L);
+    if (!(b->gexec && key == b->gkey)) {
+        if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+        b->gkey.clear();
+        if (!st && !ctx->cap_stream) cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+        cudaStream_t cs = st ? st : ctx->cap_stream;
+        cudaGraph_t graph = nullptr;
+        e = cs ? cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) : cudaErrorInvalidResourceHandle;
+        if (e == cudaSuccess) {
+            cudaError_t r = enqueue(cs);
+            e = cudaStreamEndCapture(cs, &graph);
+            if (r != cudaSuccess) e = r;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            // capture not available: launch the waves directly
+            if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+            (void)cudaGetLastError();
+            e = enqueue(st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return set_cuda_error(ctx, e, "grouped solve");
+            return VOMT_OK;
+        }
+        b->gkey.swap(key);
+    }
+    e = cudaGraphLaunch(b->gexec, st);
+    ++b->graph_replays;
+    *as_graph = e == cudaSuccess;
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "grouped solve");
     return VOMT_OK;
@@ -818,7 +905,7 @@ extern "C" int vomt_solve_batched(vomt_ctx *ctx, int count, const vomt_instance 
             int code = 0;
             if (h[4] > 0.0) { code = VOMT_ERR_NONFINITE; snprintf(buf, sizeof buf, "instance %d: NaN or Inf density", q); }
             else if (h[2] < 0.0 || h[3] < 0.0) { code = VOMT_ERR_NEGATIVE_DENSITY; snprintf(buf, sizeof buf, "instance %d: negative density", q); }
-            else if (fabs(h[0] - h[1]) > 1e-5 * fmax(fabs(h[0]), fabs(h[1]))) { code = VOMT_ERR_MASS_MISMATCH; snprintf(buf, sizeof buf, "instance %d: different total mass", q); }
+            else if (fabs(h[0] - h[1]) > kMassRelTol * fmax(fabs(h[0]), fabs(h[1]))) { code = VOMT_ERR_MASS_MISMATCH; snprintf(buf, sizeof buf, "instance %d: different total mass", q); }
             if (code) return fail(ctx, code, buf);
         }
         // path: grouped resident waves, or one block per problem from a queue
@@ -838,7 +925,8 @@ extern "C" int vomt_solve_batched(vomt_ctx *ctx, int count, const vomt_instance 
                               queue_estimate(hinst, std::max(p.max_iters, 1), ctx->sm_count);
         }
         if (grouped) {
-            rc = grouped_solve(ctx, b, count, hinst, arena, p, waves, st);
+            bool as_graph = false;
+            rc = grouped_solve(ctx, b, count, hinst, arena, p, waves, st, &as_graph);
             if (rc) return rc;
             std::vector<int> tiles(count, 1), halo(count, 0);
             for (const Wave &w : waves)
@@ -857,12 +945,15 @@ extern "C" int vomt_solve_batched(vomt_ctx *ctx, int count, const vomt_instance 
                 else if (s_ == VOMT_NOT_CONVERGED && status == VOMT_OK) status = s_;
                 if (results) {
                     vomt_result &r = results[q];
-                    r.primal = h.met[0]; r.dual = h.met[1]; r.rel_gap = h.met[2]; r.rel_res = h.met[3];
-                    r.fp_resid = h.met[4]; r.dual_infeas = h.met[5];
+                    double met[NMET];
+                    for (int m = 0; m < NMET; ++m) met[m] = h.met[m];
+                    if (h.raw) finish_raw_row(met);
+                    r.primal = met[0]; r.dual = met[1]; r.rel_gap = met[2]; r.rel_res = met[3];
+                    r.fp_resid = met[4]; r.dual_infeas = met[5];
                     r.mu = hinst[q].mu_d; r.nu = hinst[q].nu_d; r.tau = hinst[q].tau_d;
                     r.iters = h.iter; r.status = s_; r.engine = VOMT_ENGINE_BATCHED; r.checks = h.checks;
                     r.launches = ctx->launches; r.blocks = tiles[q]; r.halo = halo[q];
-                    r.variant = 0;
+                    r.variant = as_graph ? 1 : 0;
                 }
             }
             if (status < 0) ctx->err = status == VOMT_ERR_BARRIER_TIMEOUT ? "device wait timed out"
@@ -943,7 +1034,7 @@ extern "C" int vomt_solve_batched(vomt_ctx *ctx, int count, const vomt_instance 
                 r.mu = hinst[q].mu_d; r.nu = hinst[q].nu_d; r.tau = hinst[q].tau_d;
                 r.iters = h.iter; r.status = s_; r.engine = VOMT_ENGINE_BATCHED; r.checks = h.checks;
                 r.launches = ctx->launches; r.blocks = 1; r.halo = 0;
-                r.variant = 0;
+                r.variant = st != nullptr ? 1 : 0;
             }
         }
         if (status < 0) ctx->err = "an instance produced a non-finite iterate";

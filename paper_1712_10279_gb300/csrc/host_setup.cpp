@@ -15,7 +15,7 @@ namespace vomt {
 
 int graph_to_dev(const vomt_graph *g, GraphDev *out, std::string *err)
 {
-    if (!g || g->k < 1 || g->k > KMAX || g->n_edges < 0 || g->n_edges > LMAX) {
+    if (!g || g->k < 1 || g->k > KVEC || g->n_edges < 0 || g->n_edges > LVEC) {
         *err = "graph: need 1 <= k <= 8 and 0 <= n_edges <= k(k-1)/2";
         return VOMT_ERR_BAD_ARG;
     }
@@ -275,17 +275,26 @@ int quantum_to_op(int k, int N, const double *L, OpDev *op, double *lmax, double
 // diagonal, then Re and Im of each entry above it, weights 1, 2, 2.  Both
 // reproduce Re tr(X Y*) exactly, so grad_L becomes a real-linear map G between
 // the two coordinate spaces and div_L its weighted adjoint, as in the real case.
-// k * k real channels must fit KMAX, so k = 2 (4 channels, 4 flux entries per
-// L_s); the channel count is padded to the smallest K >= 4 with
-// K(K-1)/2 >= 4N, the flux bound of the kernels' templates (padding channels
-// carry zero in every field and take no part in G).
+// The k * k real channels must fit KMAX (9), so k = 2 (4 channels, 4 flux entries
+// per L_s) or k = 3 (9 channels, 9 flux entries per L_s); the channel count is
+// padded to the smallest K >= k * k with K(K-1)/2 >= k * k * N, the flux bound of
+// the kernels' templates (padding channels carry zero in every field and take no
+// part in G): N <= 9 for k = 2, N <= 4 for k = 3.  The pairs (Re, Im) of the
+// entries above the diagonal are marked in upair / wpair for the entrywise norm.
 int hermitian_to_op(int k, int N, const double *L, OpDev *op, double *lmax, double *sym_gap, std::string *err)
 {
-    if (k != 2 || N < 1 || !L) { *err = "complex matrix OMT: k = 2 and N >= 1 with L given"; return VOMT_ERR_BAD_ARG; }
+    if (k < 2 || k > 3 || N < 1 || !L) {
+        *err = "complex matrix OMT: k = 2 or 3 and N >= 1 with L given";
+        return VOMT_ERR_BAD_ARG;
+    }
     const int kk = k * k, ks = k * k;            // real coordinates of Hermitian / skew-Hermitian
     int K = kk;
     while (K * (K - 1) / 2 < N * ks) ++K;
-    if (K > KMAX) { *err = "complex matrix OMT: too many L matrices (N <= 7)"; return VOMT_ERR_BAD_ARG; }
+    if (K > KMAX) {
+        *err = k == 2 ? "complex matrix OMT: too many L matrices (N <= 9 for 2 x 2)"
+                      : "complex matrix OMT: too many L matrices (N <= 4 for 3 x 3)";
+        return VOMT_ERR_BAD_ARG;
+    }
     typedef std::complex<double> cd;
     double scale = 0.0;
     for (int q = 0; q < 2 * N * kk; ++q) {
@@ -341,6 +350,14 @@ int hermitian_to_op(int k, int N, const double *L, OpDev *op, double *lmax, doub
     op->k = K;
     op->l = N * ks;
     for (int c = 0; c < K; ++c) op->wc[c] = c < kk ? (float)wc[c] : 1.0f;
+    // (Re, Im) pairs: coordinates k, k+2, ... of every Hermitian / skew-Hermitian block
+    for (int j = 0; j < k * (k - 1) / 2; ++j) {
+        op->upair |= 1u << (k + 2 * j);
+        for (int s = 0; s < N; ++s) {
+            const int e = s * ks + k + 2 * j;
+            op->wpair[e >> 5] |= 1u << (e & 31);
+        }
+    }
     std::vector<double> Gd((size_t)N * ks * kk, 0.0);
     for (int s = 0; s < N; ++s)
         for (int c = 0; c < kk; ++c) {

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <string>
@@ -11,8 +12,20 @@
 
 namespace vomt {
 
-constexpr int KMAX = VOMT_MAX_CHANNELS;
+// Channels and flux entries of the per-point operator: up to VOMT_MAX_CHANNELS (8)
+// colour channels for vector OMT, up to 9 real coordinates for a complex
+// Hermitian 3 x 3 field; the flux bound is K(K-1)/2.
+constexpr int KMAX = 9;
 constexpr int LMAX = KMAX * (KMAX - 1) / 2;
+constexpr int KVEC = VOMT_MAX_CHANNELS;            // vector OMT: k <= 8
+constexpr int LVEC = KVEC * (KVEC - 1) / 2;
+
+// Internal norm codes beyond the public ones: the entrywise ||.||_1 of complex
+// Hermitian / skew-Hermitian fields (Section 6.2, sum of the entries' moduli), whose
+// shrink acts jointly on the (Re, Im) coordinate pairs the operator marks (OpDev
+// upair / wpair) and entrywise on the other coordinates.
+constexpr int U_CL1 = 4;
+constexpr int W_CL1 = 3;
 
 // Channel graph as the kernels see it (passed by value as a kernel argument).
 // Edge e runs from node lo[e] to node hi[e] (lo < hi), scaled by inv_c[e] = 1/c_e.
@@ -32,6 +45,10 @@ struct GraphDev {
 // Hilbert-Schmidt products of Section 4.
 struct OpDev {
     int k, l;
+    // complex fields: bit c of upair (bit e of wpair) marks coordinate c (flux entry e)
+    // as the real part of an entry whose imaginary part is coordinate c + 1
+    uint32_t upair;
+    uint32_t wpair[2];
     float wc[KMAX];
     float we[LMAX];
     float G[LMAX][KMAX];     // (grad phi)_e = sum_c G[e][c] phi_c   (grad_G or grad_L)
@@ -74,8 +91,21 @@ struct DevStatus {
     int iter;       // iteration of the last check
     int checks;     // checks run
     int error;      // 0 or VOMT_ERR_NONFINITE / VOMT_ERR_BARRIER_TIMEOUT
+    int raw;        // 1: met[2], met[3] hold ||r||^2 and ||rho0 - rho1||^2 (finish_raw_row)
+    int reserved;
     double met[NMET];
 };
+
+// The resident engine's checks decide on the device with products and comparisons
+// only (FP64 division and square root are slow on this GPU and would sit on the
+// grid-wide critical path) and store each row as (P, D, ||r||^2, ||rho0 - rho1||^2,
+// R, dual infeasibility, t, converged); the host then forms the two ratios.
+inline void finish_raw_row(double *m)
+{
+    const double P = m[0], D = m[1], RR = m[2], BB = m[3];
+    m[2] = fabs(P - D) / fmax(fabs(P), 1e-300);
+    m[3] = sqrt(RR) / (BB > 0.0 ? sqrt(BB) : 1.0);
+}
 
 struct SolveCfg {
     double tol_gap, tol_res;
@@ -133,6 +163,7 @@ struct vomt_ctx {
     vomt::DevStatus *hstatus = nullptr;      // pinned, 2 slots
     double *dhist = nullptr;
     int hist_cap = 0;
+    bool hist_raw = false;                   // the last solve's history rows need finish_raw_row
     std::vector<double> last_hist;
     int last_checks = 0;
     // host-API staging buffers (device)

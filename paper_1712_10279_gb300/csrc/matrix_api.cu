@@ -489,8 +489,15 @@ extern "C" int momt_solve_complex(vomt_ctx *ctx, int n, int k, const float *Lam0
         if (pin) p = *pin;
         if (p.pitch != 0 && p.pitch != n) return fail(ctx, VOMT_ERR_BAD_ARG, "complex matrix OMT takes dense arrays");
         if (p.u_norm == VOMT_U_L12) p.u_norm = VOMT_U_L2;
-        if (p.u_norm != VOMT_U_L2 || p.w_norm != VOMT_W_L2)
-            return fail(ctx, VOMT_ERR_BAD_ARG, "complex matrix OMT takes the Frobenius norms (u_norm L2, w_norm L2)");
+        if ((p.u_norm != VOMT_U_L2 && p.u_norm != VOMT_U_L1) || (p.w_norm != VOMT_W_L2 && p.w_norm != VOMT_W_L1))
+            return fail(ctx, VOMT_ERR_BAD_ARG,
+                        "complex matrix OMT takes the Frobenius norms (L2) or the entrywise norms (L1) for U and W");
+        // the entrywise norms of complex fields are the modulus kind (internal codes)
+        const bool entrywise = p.u_norm == VOMT_U_L1 || p.w_norm == VOMT_W_L1;
+        if (p.u_norm == VOMT_U_L1) p.u_norm = U_CL1;
+        if (p.w_norm == VOMT_W_L1) p.w_norm = W_CL1;
+        if ((entrywise || k == 3) && p.engine == VOMT_ENGINE_STREAM)
+            return fail(ctx, VOMT_ERR_BAD_ARG, "complex 3 x 3 fields and the entrywise norms run on the resident engine");
         if (p.max_iters < 0 || p.check_every < 1) return fail(ctx, VOMT_ERR_BAD_ARG, "max_iters >= 0, check_every >= 1");
         if (p.engine < 0 || p.engine > 2 || p.halo < 0 || p.halo > 16) return fail(ctx, VOMT_ERR_BAD_ARG, "bad engine / halo");
         if (p.eps != 0.0) return fail(ctx, VOMT_ERR_BAD_ARG, "complex matrix OMT takes eps = 0");

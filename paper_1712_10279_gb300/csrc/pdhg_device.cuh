@@ -34,8 +34,19 @@ __device__ __forceinline__ float pick(const float (&a)[K], int idx)
 
 // shrink_u on one point (all channels), in place; un = VOMT_U_*; channel weights wc
 // enter the joint norm (2 for an off-diagonal matrix entry)
+// Is coordinate c the real part of a complex entry (bit c of `pairs`)?  The
+// imaginary part is coordinate c + 1.
+__device__ __forceinline__ bool pair_first(uint32_t pairs, int c) { return (pairs >> c) & 1u; }
+__device__ __forceinline__ bool pair_second(uint32_t pairs, int c) { return c > 0 && ((pairs >> (c - 1)) & 1u); }
+__device__ __forceinline__ bool wpair_first(const uint32_t (&wp)[2], int e) { return (wp[e >> 5] >> (e & 31)) & 1u; }
+__device__ __forceinline__ bool wpair_second(const uint32_t (&wp)[2], int e)
+{
+    return e > 0 && ((wp[(e - 1) >> 5] >> ((e - 1) & 31)) & 1u);
+}
+
 template <int K>
-__device__ __forceinline__ void shrink_u(float (&vx)[K], float (&vy)[K], float t, int un, const float *wc)
+__device__ __forceinline__ void shrink_u(float (&vx)[K], float (&vy)[K], float t, int un, const float *wc,
+                                         uint32_t pairs = 0u)
 {
     if (un == VOMT_U_L12) {
 #pragma unroll
@@ -55,6 +66,25 @@ __device__ __forceinline__ void shrink_u(float (&vx)[K], float (&vy)[K], float t
         // ||U_x||_nuc + ||U_y||_nuc: each direction's symmetric matrix on its own
         mat::sym_shrink_nuc<K>(vx, t);
         mat::sym_shrink_nuc<K>(vy, t);
+    } else if (un == U_CL1) {
+        // complex entrywise ||.||_1 (sum of moduli) in each direction: the prox of t |z|
+        // scales an (Re, Im) pair by its modulus (in the compact inner product the pair's
+        // weight 2 multiplies both the norm and the distance, so the threshold stays t);
+        // real coordinates (Hermitian diagonals) take the soft threshold
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            if (pair_first(pairs, c) && c + 1 < K) {
+                const float fx = shrink2_factor(vx[c] * vx[c] + vx[c + 1] * vx[c + 1], t);
+                const float fy = shrink2_factor(vy[c] * vy[c] + vy[c + 1] * vy[c + 1], t);
+                vx[c] *= fx;
+                vx[c + 1] *= fx;
+                vy[c] *= fy;
+                vy[c + 1] *= fy;
+            } else if (!pair_second(pairs, c)) {
+                vx[c] = soft(vx[c], t);
+                vy[c] = soft(vy[c], t);
+            }
+        }
     } else {
 #pragma unroll
         for (int c = 0; c < K; ++c) { vx[c] = soft(vx[c], t); vy[c] = soft(vy[c], t); }
@@ -63,9 +93,24 @@ __device__ __forceinline__ void shrink_u(float (&vx)[K], float (&vy)[K], float t
 
 // shrink_w on one point, l <= LK flux entries with weights we; wn = VOMT_W_*
 template <int LK>
-__device__ __forceinline__ void shrink_w(float (&x)[LK], int l, float t, int wn, const float *we)
+__device__ __forceinline__ void shrink_w(float (&x)[LK], int l, float t, int wn, const float *we,
+                                         const uint32_t *wpairs = nullptr)
 {
-    if (wn == VOMT_W_L1) {
+    if (wn == W_CL1) {
+        // complex entrywise ||.||_1 of the skew-Hermitian components, as in shrink_u
+        const uint32_t wp[2] = {wpairs ? wpairs[0] : 0u, wpairs ? wpairs[1] : 0u};
+#pragma unroll
+        for (int e = 0; e < LK; ++e) {
+            if (e >= l) continue;
+            if (wpair_first(wp, e) && e + 1 < LK) {
+                const float f = shrink2_factor(x[e] * x[e] + x[e + 1] * x[e + 1], t);
+                x[e] *= f;
+                x[e + 1] *= f;
+            } else if (!wpair_second(wp, e)) {
+                x[e] = soft(x[e], t);
+            }
+        }
+    } else if (wn == VOMT_W_L1) {
 #pragma unroll
         for (int e = 0; e < LK; ++e)
             if (e < l) x[e] = soft(x[e], t);

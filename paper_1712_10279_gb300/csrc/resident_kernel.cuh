@@ -463,6 +463,10 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
     int nexch = 1, checks = 0, t = 0;
     bool stop = false;
 
+    // reciprocals of the check's weights, once per solve (FP64 division is slow here)
+    const double inv_mu = 1.0 / a.cfg.mu, inv_nu = a.cfg.has_w ? 1.0 / a.cfg.nu : 0.0;
+    const double inv_tau = 1.0 / a.cfg.tau, inv4eps = a.cfg.eps > 0.0 ? 0.25 / a.cfg.eps : 0.0;
+
     float racc[P][K];
 #pragma unroll
     for (int r = 0; r < P; ++r)
@@ -501,7 +505,7 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
                     vy[c] *= a.s.su;
                 }
             }
-            shrink_u<K>(vx, vy, tu, un, a.g.wc);
+            shrink_u<K>(vx, vy, tu, un, a.g.wc, NM ? 0u : a.g.upair);
             float ubx[K], uby[K];
 #pragma unroll
             for (int c = 0; c < K; ++c) {
@@ -536,7 +540,7 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
 #pragma unroll
                 for (int e = 0; e < LKv; ++e) wx[e] *= a.s.sw;
             }
-            shrink_w<LKv>(wx, l, tw, wn, a.g.we);
+            shrink_w<LKv>(wx, l, tw, wn, a.g.we, a.g.wpair);
 #pragma unroll
             for (int c = 0; c < K; ++c) {
                 float gw = 0.0f;
@@ -668,6 +672,7 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
             lds<K>(sphi + b + ((f & 1) ? KV : 0), fx);
             lds<K>(sphi + b + ((f & 2) ? RS : 0), fy);
             float nu_pt = 0.0f, dn_u = 0.0f, q2 = 0.0f, dist = 0.0f;
+            float pux = 0.0f, puy = 0.0f, pgx = 0.0f, pgy = 0.0f;   // real parts of a complex pair
             float gxs[K], gys[K];
 #pragma unroll
             for (int c = 0; c < K; ++c) {
@@ -685,6 +690,17 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
                 gys[c] = gyy;
                 if (un == VOMT_U_NUC) {
                     // after the loop
+                } else if (!NM && un == U_CL1) {
+                    // complex entrywise: a pair's modulus (its weight 2 counts the mirror entry)
+                    if (pair_first(a.g.upair, c)) {
+                        pux = uxc; puy = uyc; pgx = gxx; pgy = gyy;
+                    } else if (pair_second(a.g.upair, c)) {
+                        nu_pt += wgt * (sqrtf(pux * pux + uxc * uxc) + sqrtf(puy * puy + uyc * uyc));
+                        dn_u = fmaxf(dn_u, fmaxf(sqrtf(pgx * pgx + gxx * gxx), sqrtf(pgy * pgy + gyy * gyy)));
+                    } else {
+                        nu_pt += wgt * (fabsf(uxc) + fabsf(uyc));
+                        dn_u = fmaxf(dn_u, fmaxf(fabsf(gxx), fabsf(gyy)));
+                    }
                 } else if (un == VOMT_U_L12) {
                     nu_pt += sqrtf(uxc * uxc + uyc * uyc);
                     const float gn = sqrtf(gxx * gxx + gyy * gyy);
@@ -716,7 +732,7 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
                 mat::sym_nuc_spec<K>(gys, n2, s2);
                 dn_u = fmaxf(s1, s2);
             }
-            float nw_pt = 0.0f, dn_w = 0.0f, wg2 = 0.0f, gg2 = 0.0f;
+            float nw_pt = 0.0f, dn_w = 0.0f, wg2 = 0.0f, gg2 = 0.0f, pw_re = 0.0f, pg_re = 0.0f;
 #pragma unroll
             for (int e = 0; e < LKv; ++e) {
                 if (e < l) {
@@ -730,6 +746,17 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
                         dn_w = fmaxf(dn_w, fabsf(ge));
                         const float o = fmaxf(fabsf(ge) - alpha, 0.0f);
                         dist += wgt * o * o;
+                    } else if (!NM && wn == W_CL1) {
+                        if (wpair_first(a.g.wpair, e)) {
+                            pw_re = we;
+                            pg_re = ge;
+                        } else if (wpair_second(a.g.wpair, e)) {
+                            nw_pt += wgt * sqrtf(pw_re * pw_re + we * we);
+                            dn_w = fmaxf(dn_w, sqrtf(pg_re * pg_re + ge * ge));
+                        } else {
+                            nw_pt += wgt * fabsf(we);
+                            dn_w = fmaxf(dn_w, fabsf(ge));
+                        }
                     } else if (wn == VOMT_W_NUC) {
                         // 3 x 3 skew components (a, b, c): ||W_s||_nuc = 2 |(a,b,c)|, spectral |(a,b,c)|
                         wg2 += we * we;
@@ -834,23 +861,29 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
         }
         __syncthreads();
         if (tid == 0) {
+            // the stop decision with products and comparisons only: rel_gap <= tol_gap is
+            // |P - D| <= tol_gap max(|P|, 1e-300), rel_res <= tol_res is
+            // ||r||^2 <= tol_res^2 ||rho0 - rho1||^2; the ratios themselves are formed on
+            // the host from the row (finish_raw_row)
             double m[NMET];
             m[0] = S[RED_P];
-            m[1] = S[RED_D] - (a.cfg.eps > 0.0 ? S[RED_DIST] / (4.0 * a.cfg.eps) : 0.0);
-            m[2] = fabs(m[0] - m[1]) / fmax(fabs(m[0]), 1e-300);
-            m[3] = sqrt(S[RED_RR]) / (S[RED_BB] > 0.0 ? sqrt(S[RED_BB]) : 1.0);
-            m[4] = S[RED_DU] / a.cfg.mu + (a.cfg.has_w ? S[RED_DW] / a.cfg.nu : 0.0) + S[RED_DP] / a.cfg.tau -
-                   2.0 * S[RED_X];
+            m[1] = S[RED_D] - S[RED_DIST] * inv4eps;
+            m[2] = S[RED_RR];
+            m[3] = S[RED_BB];
+            m[4] = S[RED_DU] * inv_mu + S[RED_DW] * inv_nu + S[RED_DP] * inv_tau - 2.0 * S[RED_X];
             m[5] = S[RED_MAX];
             m[6] = (double)t;
             bool finite = true;
             for (int q = 0; q < 6; ++q) finite = finite && isfinite(m[q]);
-            const bool conv = a.cfg.tol_gap > 0.0 && m[2] <= a.cfg.tol_gap && m[3] <= a.cfg.tol_res;
+            const double tg = a.cfg.tol_gap, tr = a.cfg.tol_res;
+            const bool conv = tg > 0.0 && fabs(m[0] - m[1]) <= tg * fmax(fabs(m[0]), 1e-300) &&
+                              m[2] <= tr * tr * (m[3] > 0.0 ? m[3] : 1.0);
             m[7] = conv ? 1.0 : 0.0;
             if (tile == 0) {
                 for (int q = 0; q < NMET; ++q) a.st->met[q] = m[q];
                 if (a.hist && checks < a.hist_cap)
                     for (int q = 0; q < NMET; ++q) a.hist[(size_t)checks * NMET + q] = m[q];
+                a.st->raw = 1;
                 a.st->checks = checks + 1;
                 a.st->iter = t;
                 if (!finite) a.st->error = VOMT_ERR_NONFINITE;
@@ -939,11 +972,16 @@ ResKernel kernel_for(int P, int NM)
     return P == 1 ? k_resident<K, 1, 0> : (P == 2 ? k_resident<K, 2, 0> : k_resident<K, 4, 0>);
 }
 
-// Grouped-batch kernel for K <= 5 channels, P in {2, 4}, NM in {0, 1}; nullptr otherwise.
+// Grouped-batch kernel for K <= 5 channels, P in {2, 4} (and P = 1 for five
+// channels, whose per-point state spills at two points per thread), NM in {0, 1};
+// nullptr otherwise.
 template <int K>
 MultiKernel multi_kernel_for(int P, int NM)
 {
     if constexpr (K <= 5) {
+        if constexpr (K == 5) {
+            if (P == 1) return NM == 1 ? k_resident_multi<K, 1, 1> : k_resident_multi<K, 1, 0>;
+        }
         if (NM == 1) return P == 2 ? k_resident_multi<K, 2, 1> : k_resident_multi<K, 4, 1>;
         return P == 2 ? k_resident_multi<K, 2, 0> : k_resident_multi<K, 4, 0>;
     } else {

@@ -464,6 +464,7 @@ namespace vomt {
 int solve3d_core(vomt_ctx *ctx, int n, const OpDev &g, const StepDev &s, const SolveCfg &cfg, const vomt_params &p,
                  int zc_user, const float *rho0, const float *rho1, float *u, float *w, float *phi, cudaStream_t st)
 {
+    ctx->hist_raw = false;           // k_finalize writes finished rows
     const int k = g.k, l = g.l;
     const size_t m = (size_t)n * n * n;
     cudaError_t e;

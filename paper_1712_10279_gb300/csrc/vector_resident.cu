@@ -17,6 +17,7 @@ ResKernel res_kernel_k3(int K, int P, int NM);
 ResKernel res_kernel_k45(int K, int P, int NM);
 ResKernel res_kernel_k6(int K, int P, int NM);
 ResKernel res_kernel_k78(int K, int P, int NM);
+ResKernel res_kernel_k9(int K, int P, int NM);
 MultiKernel res_multi_kernel_k12(int K, int P, int NM);
 MultiKernel res_multi_kernel_k3(int K, int P, int NM);
 MultiKernel res_multi_kernel_k45(int K, int P, int NM);
@@ -29,7 +30,8 @@ ResKernel res_kernel(int K, int P, int NM)
     if (K == 3) return res_kernel_k3(K, P, NM);
     if (K <= 5) return res_kernel_k45(K, P, NM);
     if (K == 6) return res_kernel_k6(K, P, NM);
-    return res_kernel_k78(K, P, NM);
+    if (K <= 8) return res_kernel_k78(K, P, NM);
+    return res_kernel_k9(K, P, NM);
 }
 
 MultiKernel res_multi_kernel(int K, int P, int NM)
@@ -38,7 +40,8 @@ MultiKernel res_multi_kernel(int K, int P, int NM)
     if (K == 3) return res_multi_kernel_k3(K, P, NM);
     if (K <= 5) return res_multi_kernel_k45(K, P, NM);
     if (K == 6) return res_multi_kernel_k6(K, P, NM);
-    return res_multi_kernel_k78(K, P, NM);
+    if (K <= 8) return res_multi_kernel_k78(K, P, NM);
+    return nullptr;
 }
 
 }  // namespace res
@@ -131,7 +134,8 @@ bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out)
 // grouped batch): each problem gets T = Gx x Gy tiles, floor(max_blocks / T)
 // problems run side by side, and the plan minimises the estimated time of the
 // whole wave (rounds of side-by-side problems x time per iteration of one).
-// Same tile rules as resident_plan; P is 2 or 4 (the grouped kernels).
+// Same tile rules as resident_plan; P is 2 or 4 (the grouped kernels), or 1 for
+// five channels when the extended tile fits one point per thread.
 bool resident_plan_wave(int n, int k, int count, int max_blocks, ResidentPlan *out)
 {
     auto smem_ok = [&](int EW, int EH, int G) {
@@ -172,7 +176,7 @@ bool resident_plan_wave(int n, int k, int count, int max_blocks, ResidentPlan *o
     }
     if (best < 0) return false;
     const int ext = (out->TXm + 2 * out->H) * (out->TYm + 2 * out->H);
-    out->P = ext <= 2 * RT ? 2 : 4;
+    out->P = (k >= 5 && ext <= RT) ? 1 : (ext <= 2 * RT ? 2 : 4);
     out->threads = (((ext + out->P - 1) / out->P + 31) / 32) * 32;
     return true;
 }
@@ -229,6 +233,7 @@ int resident_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveC
     }
     a.hist = ctx->dhist;
     a.hist_cap = ctx->hist_cap;
+    ctx->hist_raw = true;            // the kernel's check rows hold raw sums (finish_raw_row)
     a.wait_ns = ctx->wait_ns ? ctx->wait_ns : dev::kWaitBudgetNs;
     a.drop_exch = ctx->drop_exchange;
     a.tag_hi = 0u;
@@ -237,6 +242,10 @@ int resident_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveC
     if (p.u_norm == VOMT_U_L12 && p.w_norm == VOMT_W_L1) nm = 1;
     else if (p.u_norm == VOMT_U_L2 && p.w_norm == VOMT_W_L1 && (K == 3 || K == 6)) nm = 2;
     res::ResKernel kern = res::res_kernel(K, plan.P, nm);
+    if (!kern) {
+        ctx->err = "no resident kernel for this channel count and norm pair";
+        return VOMT_ERR_TOO_LARGE;
+    }
     cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SL.total);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "resident smem attribute");
     int per_sm = 0;

@@ -585,6 +585,7 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
                  const vomt_params &p, const float *rho0, const float *rho1,
                  float *u, float *w, float *phi, cudaStream_t st)
 {
+    ctx->hist_raw = false;           // k_finalize writes finished rows
     const int n = s.n, k = g.k, l = g.l;
     const size_t nn = (size_t)n * n;
     // workspace: b, then two states {phi, ux, uy, w}

@@ -104,6 +104,29 @@ def test_batched_graph_replay_and_tuner():
     _check_against_oracle(B, probs, r0s, r1s, max_iters=200, check_every=50)
 
 
+@pytest.mark.parametrize("on_side_stream", [False, True])
+def test_grouped_path_runs_as_one_graph_replay(on_side_stream):
+    """The grouped path's wave launches form one CUDA graph (captured on the caller's stream,
+    or on the context's own stream when the caller uses the legacy default stream): every
+    call reports the graph launch, the replay reproduces the captured solve bit for bit and
+    equals the oracle, and new parameters recapture."""
+    d = _dev()
+    probs, r0s, r1s = _mixed(10, seed=8)
+    B = V.Batch(probs, r0s, r1s)
+    s = torch.cuda.Stream(device=d) if on_side_stream else None
+    B.solve(max_iters=300, check_every=100, path="grouped", stream=s)        # captured
+    assert all(r["variant"] == 1 for r in B.results)
+    first = [B.phi(q).clone() for q in range(len(probs))]
+    B.solve(max_iters=300, check_every=100, path="grouped", stream=s)        # replayed
+    assert all(r["variant"] == 1 for r in B.results)
+    for q in range(len(probs)):
+        assert torch.equal(first[q], B.phi(q))
+    _check_against_oracle(B, probs, r0s, r1s, max_iters=300, check_every=100)
+    B.solve(max_iters=200, check_every=100, path="grouped", stream=s)        # new parameters
+    assert all(r["variant"] == 1 and r["iters"] == 200 for r in B.results)
+    _check_against_oracle(B, probs, r0s, r1s, max_iters=200, check_every=100)
+
+
 @pytest.mark.parametrize("path", PATHS)
 def test_batched_matches_single_solves_at_config_sizes(path):
     """Problems drawn like the 512-problem mixed configuration (sides up to 256, k in {1, 3, 5},

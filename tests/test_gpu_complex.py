@@ -1,5 +1,7 @@
 """GPU parity of complex Hermitian matrix OMT (momt_solve_complex: Section 4's complex setting,
-the Section 7.3 iteration, Frobenius norms) against the complex FP64 oracle, through the C ABI.
+the Section 7.3 iteration) against the complex FP64 oracle, through the C ABI, for 2 x 2 and
+3 x 3 fields, the Frobenius norms ||U||_2, ||W||_2 and the entrywise ||U||_1, ||W||_1 (sums of
+the entries' moduli).
 
 * fixed iteration counts from zero, n = 5, 17, 33, N = 2 and 3, both engines: relative L2
   <= 1e-3 on Phi, U and W, relative <= 1e-4 on the primal objective;
@@ -127,6 +129,70 @@ def test_unitary_conjugation_leaves_the_cost():
     assert rb["dual"] == pytest.approx(ra["dual"], rel=1e-4, abs=1e-6)
 
 
+@pytest.mark.parametrize("k,n,N", [(3, 5, 2), (3, 17, 3), (3, 12, 4), (2, 17, 3)])
+@pytest.mark.parametrize("norms", [(V.U_L2, V.W_L2), (V.U_L1, V.W_L1), (V.U_L2, V.W_L1), (V.U_L1, V.W_L2)])
+def test_fixed_iterations_3x3_and_entrywise_match_oracle(k, n, N, norms):
+    """3 x 3 fields (nine real coordinates per point, the resident engine) and the entrywise
+    norms, whose shrink scales each complex entry by its modulus, against the oracle."""
+    un, wn = norms
+    if k == 2 and norms == (V.U_L2, V.W_L2):
+        pytest.skip("covered by test_fixed_iterations_match_oracle")
+    A0, A1 = S.hermitian_field_pair(n, k, seed=70 + n + k)
+    A0, A1 = A0 * n * n, A1 * n * n
+    L = S.random_hermitian_L(k, N, seed=71 + N)
+    iters = 200
+    G, r, _ = _gpu(A0, A1, L, 0.7, max_iters=iters, check_every=50, u_norm=un, w_norm=wn)
+    assert r["iters"] == iters and r["status"] == 0 and r["engine"] == "resident"
+    o = oracle.zmomt_solve(_c(A0), _c(A1), L, 0.7, tau=r["tau"], mu=r["mu"], nu=r["nu"], max_iters=iters,
+                           check_every=50, u_norm=un, w_norm=wn)
+    assert np.abs(o["Ux"]).max() > 0 and np.abs(o["W"]).max() > 0 and np.abs(o["W"].imag).max() > 0
+    assert _rel(G["Phi"], o["Phi"]) <= 1e-3
+    assert _rel(np.stack([G["Ux"], G["Uy"]]), np.stack([o["Ux"], o["Uy"]])) <= 1e-3
+    assert _rel(G["W"], o["W"]) <= 1e-3
+    assert r["primal"] == pytest.approx(o["metrics"]["primal"], rel=1e-4)
+    assert r["dual"] == pytest.approx(o["metrics"]["dual"], rel=1e-3, abs=1e-6)
+    assert r["rel_res"] == pytest.approx(o["metrics"]["rel_res"], rel=1e-3)
+    assert r["dual_infeas"] == pytest.approx(o["metrics"]["dual_infeas"], rel=1e-3, abs=1e-6)
+
+
+def test_one_iteration_from_gpu_state_3x3_entrywise_at_64():
+    n, N, k = 64, 3, 3
+    A0, A1 = S.hermitian_field_pair(n, k, seed=17)
+    A0, A1 = A0 * n * n, A1 * n * n
+    L = S.random_hermitian_L(k, N, seed=18)
+    kw = dict(u_norm=V.U_L1, w_norm=V.W_L1)
+    G0, r0, sol = _gpu(A0, A1, L, 1.0, max_iters=100, check_every=100, **kw)
+    G, r, _ = _gpu(A0, A1, L, 1.0, max_iters=1, check_every=1, init=(sol.U.clone(), sol.W.clone(), sol.Phi.clone()),
+                   **kw)
+    o = oracle.zmomt_solve(_c(A0), _c(A1), L, 1.0, tau=r["tau"], mu=r["mu"], nu=r["nu"], max_iters=1,
+                           check_every=1, init=G0, **kw)
+    for key in ("Phi", "Ux", "Uy", "W"):
+        scale = max(np.abs(o[key]).max(), 1e-30)
+        err = np.abs(G[key] - o[key]).max() / scale
+        assert err <= 1e-5, (key, err)
+    assert r["primal"] == pytest.approx(o["metrics"]["primal"], rel=1e-5)
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_entrywise_real_inputs_give_the_real_entrywise_path(k):
+    """On real inputs the modulus of an entry is its absolute value: the complex entrywise
+    solve equals the real matrix path with ||U||_1, ||W||_1."""
+    n = 20
+    L0, L1 = S.tensor_field_pair(n, k, seed=19 + k)
+    L0, L1 = L0 * n * n, L1 * n * n
+    L = S.random_L(k, 3, seed=20)
+    G, r, _ = _gpu(L0.astype(np.complex128), L1.astype(np.complex128), L.astype(np.complex128), 0.5,
+                   max_iters=300, check_every=100, u_norm=V.U_L1, w_norm=V.W_L1)
+    d = _dev()
+    real = V.momt_solve(torch.from_numpy(L0.astype(np.float32)).to(d), torch.from_numpy(L1.astype(np.float32)).to(d),
+                        L, 0.5, u_norm=V.U_L1, w_norm=V.W_L1, max_iters=300, check_every=100)
+    torch.cuda.synchronize()
+    assert np.abs(G["Phi"].imag).max() <= 1e-6 * np.abs(G["Phi"]).max()
+    assert _rel(G["Phi"].real, real.Phi.cpu().numpy().astype(np.float64)) <= 1e-4
+    assert _rel(np.stack([G["Ux"], G["Uy"]]).real, real.U.cpu().numpy().astype(np.float64)) <= 1e-4
+    assert r["primal"] == pytest.approx(real.result["primal"], rel=1e-5)
+
+
 def test_errors():
     n = 6
     A0, A1 = _pair(n, seed=1)
@@ -138,10 +204,18 @@ def test_errors():
     with pytest.raises(V.VomtError):
         _gpu(bad, A1, L, 1.0, max_iters=1)
     with pytest.raises(V.VomtError):
-        _gpu(A0, A1, S.random_hermitian_L(2, 8, seed=3), 1.0, max_iters=1)     # N > 7
+        _gpu(A0, A1, S.random_hermitian_L(2, 10, seed=3), 1.0, max_iters=1)     # 2 x 2: N > 9
     a3, b3 = S.hermitian_field_pair(n, 3, seed=4)
     with pytest.raises(V.VomtError):
-        _gpu(a3, b3, S.random_hermitian_L(3, 2, seed=5), 1.0, max_iters=1)   # k = 3
+        _gpu(a3, b3, S.random_hermitian_L(3, 5, seed=5), 1.0, max_iters=1)   # 3 x 3: N > 4
+    with pytest.raises(V.VomtError) as ex:                                   # 3 x 3: resident engine only
+        _gpu(a3, b3, S.random_hermitian_L(3, 2, seed=5), 1.0, max_iters=1, engine="stream")
+    assert ex.value.status == -1
+    with pytest.raises(V.VomtError) as ex:                                   # entrywise: resident engine only
+        _gpu(A0, A1, L, 1.0, max_iters=1, engine="stream", u_norm=V.U_L1, w_norm=V.W_L1)
+    assert ex.value.status == -1
+    with pytest.raises(V.VomtError):
+        _gpu(A0, A1, L, 1.0, max_iters=1, u_norm=V.U_NUC)                    # no nuclear norm here
     Lnh = L.copy()
     Lnh[0, 0, 1] += 0.3                                  # L not Hermitian
     with pytest.raises(V.VomtError):
