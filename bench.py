@@ -47,7 +47,7 @@ sys.path.insert(0, ROOT)
 N, K, ALPHAS, TOL, CAP = 256, 3, (0.1, 1.0, 10.0), 1e-5, 50000
 CHECK_EVERY = 100
 TUNE_ITERS = 1000            # sample_iters of the tau tuner (about 34x that many iterations per tuning)
-UNCAPPED = 500000            # cap of the time-to-tolerance runs beyond the configured 50,000
+UNCAPPED = 2000000           # cap of the time-to-tolerance runs beyond the configured 50,000
 EDGES = [(0, 1), (0, 2), (1, 2)]
 BYTES_PER_GP_IT = 4 * (7 * K + 2 * len(EDGES))   # read phi,u_x,u_y,w,b; write phi,u_x,u_y,w (FP32)
 REF_TAU = 300.0             # tau of the reference arm's oracle sample (its cost per iteration does not depend on tau)
@@ -382,7 +382,7 @@ def extra_batched(dev, cap=20000):
     return out
 
 
-def extra_differentiable(dev, count=64, cap=50000, tol=1e-3):
+def extra_differentiable(dev, count=64, cap=150000, tol=1e-3):
     """64 colour-image pairs at 256 x 256: batched forward solve to the paper's stopping rule
     (gap 1e-3, Section 8.1) + envelope backward, and the 200-iteration unrolled gradient,
     against plain forward solves of the same pairs at the same per-pair tau and tolerance."""
