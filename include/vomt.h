@@ -343,8 +343,9 @@ int vomt_batch_set_threads(vomt_ctx *ctx, int threads);
  * is ||U||_{1,nuc} = ||U_x||_nuc + ||U_y||_nuc.  w_norm VOMT_W_L1 is ||W||_1
  * (entrywise), VOMT_W_L2 is ||W||_2 (joint Frobenius), VOMT_W_NUC is
  * ||W||_{1,nuc} = sum_s ||W_s||_nuc.  The nuclear shrink soft-thresholds the
- * singular values (Appendix B): for symmetric U through a per-point Jacobi
- * eigen-decomposition; for 3 x 3 skew W_s, whose two nonzero singular values
+ * singular values (Appendix B): for symmetric U through a per-point
+ * eigen-decomposition (one Jacobi rotation at 2 x 2, a closed form at 3 x 3);
+ * for 3 x 3 skew W_s, whose two nonzero singular values
  * are equal, it scales W_s by max(0, 1 - t / sigma).
  * Step sizes: tau <= 0 picks Table 3's value (10 for n <= 64, 30 for n <= 128,
  * else 60); mu = 1/(32 tau (n-1)^2), nu = 1/(4 tau lambda_max(-Delta_L)) with

@@ -9,15 +9,22 @@
 // k = 3 (the nuclear norms exist for matrix problems only).
 //
 // Symmetric: the singular values are |eigenvalues|, so the shrink keeps the
-// eigenvectors and maps each eigenvalue l to sign(l) max(|l| - t, 0).  The
-// eigen-decomposition is cyclic Jacobi (Golub and Van Loan, Section 8.5) in
-// FP32: one rotation is exact for 2 x 2.  For 3 x 3 the rotations act on the
-// six distinct entries only (a rotation in the (p, q) plane sets a_pq to 0,
-// moves a_pp and a_qq by -+ tan(theta) a_pq and turns the pair (a_rp, a_rq) of
-// the third index r), and four sweeps reach FP32 accuracy: cyclic Jacobi
-// converges quadratically, and in FP32 the shrink of random, clustered and
-// graded 3 x 3 matrices is within 3e-6 of the exact one after three sweeps and
-// at the rounding floor (about 1e-6 relative) after four.
+// eigenvectors and maps each eigenvalue l to sign(l) max(|l| - t, 0).  For
+// 2 x 2 the eigen-decomposition is one Jacobi rotation (Golub and Van Loan,
+// Section 8.5), which is exact.  For 3 x 3 it is closed form, in three steps:
+// (1) the eigenvalue farthest from the other two from the trigonometric
+// solution of the characteristic cubic (O. K. Smith, "Eigenvalues of a
+// symmetric 3 x 3 matrix", Comm. ACM 4 (1961) 168); it lies at least
+// sqrt(3) p from both others, p^2 = ||A - q I||_F^2 / 6, so (2) its
+// eigenvector, the longest cross product of two rows of A - l I, is
+// well conditioned; (3) the other two eigenpairs are those of the 2 x 2 block
+// of A on the plane orthogonal to that vector, by one exact Jacobi rotation.
+// The cubic alone would not do: near a double eigenvalue its two close roots
+// carry errors of order sqrt(eps) p, and the deflation removes them.  In FP32
+// the shrink of random, clustered, graded, near-scalar and exactly degenerate
+// matrices is within 6e-7 (relative to ||A||_F) of the exact FP64 shrink.
+// The dependent chain is about a fifth of that of cyclic Jacobi (twelve
+// rotations, each with two divisions and a square root).
 //
 // Skew 3 x 3 with entries (a, b, c): the singular values are theta, theta, 0
 // with theta = |(a, b, c)|, so ||W_s||_nuc = 2 theta, its dual (the spectral
@@ -45,8 +52,9 @@ __host__ __device__ constexpr int sidx(int a, int b)
     return a == b ? a : (M == 2 ? 2 : (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5)));
 }
 
-// In-place cyclic Jacobi on the symmetric M x M matrix A; V collects the
-// rotations (columns: eigenvectors), A's diagonal ends as the eigenvalues.
+// In-place Jacobi on the symmetric M x M matrix A (used for M = 2, where one
+// rotation is exact); V collects the rotations (columns: eigenvectors), A's
+// diagonal ends as the eigenvalues.
 template <int M, bool VEC>
 __device__ __forceinline__ void jacobi(float (&A)[M][M], float (&V)[M][M])
 {
@@ -56,7 +64,8 @@ __device__ __forceinline__ void jacobi(float (&A)[M][M], float (&V)[M][M])
 #pragma unroll
             for (int j = 0; j < M; ++j) V[i][j] = i == j ? 1.0f : 0.0f;
     }
-    constexpr int SWEEPS = M == 2 ? 1 : 6;
+    static_assert(M == 2, "3 x 3 matrices take the closed form eig3");
+    constexpr int SWEEPS = 1;
 #pragma unroll
     for (int sw = 0; sw < SWEEPS; ++sw) {
 #pragma unroll
@@ -103,54 +112,87 @@ __device__ __forceinline__ void unpack(const float (&x)[K], float (&A)[M][M])
         for (int b = 0; b < M; ++b) A[a][b] = x[sidx<M>(a, b)];
 }
 
-// One Jacobi rotation of a symmetric 3 x 3 matrix held as its distinct entries:
-// zeroes apq, updates app, aqq and the pair (arp, arq) of the third index r, and
-// (VEC) the columns p, q of V.
+// Closed-form eigen-decomposition of the compact symmetric 3 x 3 matrix
+// x = (a00 a11 a22 a01 a02 a12): d[0] is the eigenvalue farthest from the
+// other two with unit eigenvector v; d[1], d[2] are the eigenvalues of the
+// block of A on the plane orthogonal to v, with unit eigenvectors ga, gb
+// (written when VEC).
 template <bool VEC>
-__device__ __forceinline__ void rot3(float &app, float &aqq, float &apq, float &arp, float &arq, float (&V)[3][3],
-                                     int p, int q)
+__device__ __forceinline__ void eig3(const float (&x)[6], float (&d)[3], float (&v)[3], float (&ga)[3],
+                                     float (&gb)[3])
 {
-    if (apq == 0.0f) return;
-    const float theta = (aqq - app) / (2.0f * apq);
-    const float t = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
-    const float c = rsqrtf(fmaf(t, t, 1.0f)), s = t * c;
-    app = fmaf(-t, apq, app);
-    aqq = fmaf(t, apq, aqq);
-    apq = 0.0f;
-    const float g = arp, h = arq;
-    arp = c * g - s * h;
-    arq = s * g + c * h;
+    const float a00 = x[0], a11 = x[1], a22 = x[2], a01 = x[3], a02 = x[4], a12 = x[5];
+    const float q = (a00 + a11 + a22) * (1.0f / 3.0f);
+    const float b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+    const float off = fmaf(a01, a01, fmaf(a02, a02, a12 * a12));
+    const float p2 = fmaf(2.0f, off, fmaf(b00, b00, fmaf(b11, b11, b22 * b22))) * (1.0f / 6.0f);
+    // (1) the isolated eigenvalue: with B = (A - q I) / p, the eigenvalues are
+    // q + 2 p cos(phi + 2 pi j / 3), phi = acos(det(B) / 2) / 3 in [0, pi / 3];
+    // j = 0 (the largest) is isolated for phi <= pi / 6, else j = 1 (the smallest)
+    float li = q;
+    if (p2 > 0.0f) {
+        const float ip = rsqrtf(p2), p = p2 * ip;
+        const float c00 = b00 * ip, c11 = b11 * ip, c22 = b22 * ip, c01 = a01 * ip, c02 = a02 * ip,
+                    c12 = a12 * ip;
+        const float det = c00 * fmaf(c11, c22, -c12 * c12) - c01 * fmaf(c01, c22, -c12 * c02) +
+                          c02 * fmaf(c01, c12, -c11 * c02);
+        const float r = fminf(fmaxf(0.5f * det, -1.0f), 1.0f);
+        const float phi = acosf(r) * (1.0f / 3.0f);
+        float sn, cs;
+        sincosf(phi, &sn, &cs);
+        li = phi <= 0.52359877f ? fmaf(2.0f * p, cs, q) : fmaf(-p, fmaf(1.7320508f, sn, cs), q);
+    }
+    // (2) its eigenvector: the longest cross product of two rows of A - li I
+    const float r00 = a00 - li, r11 = a11 - li, r22 = a22 - li;
+    const float w0x = fmaf(a01, a12, -a02 * r11), w0y = fmaf(a02, a01, -r00 * a12), w0z = fmaf(r00, r11, -a01 * a01);
+    const float w1x = fmaf(a01, r22, -a02 * a12), w1y = fmaf(a02, a02, -r00 * r22), w1z = fmaf(r00, a12, -a01 * a02);
+    const float w2x = fmaf(r11, r22, -a12 * a12), w2y = fmaf(a12, a02, -a01 * r22), w2z = fmaf(a01, a12, -r11 * a02);
+    const float n0 = fmaf(w0x, w0x, fmaf(w0y, w0y, w0z * w0z));
+    const float n1 = fmaf(w1x, w1x, fmaf(w1y, w1y, w1z * w1z));
+    const float n2 = fmaf(w2x, w2x, fmaf(w2y, w2y, w2z * w2z));
+    float vx = w0x, vy = w0y, vz = w0z, nn = n0;
+    if (n1 > nn) vx = w1x, vy = w1y, vz = w1z, nn = n1;
+    if (n2 > nn) vx = w2x, vy = w2y, vz = w2z, nn = n2;
+    if (nn > 0.0f) {
+        const float in = rsqrtf(nn);
+        vx *= in, vy *= in, vz *= in;
+    } else {    // A - li I vanishes to rounding: A is scalar, any unit vector will do
+        vx = 1.0f, vy = 0.0f, vz = 0.0f;
+    }
+    // an orthonormal basis (e, g) of the plane orthogonal to v: e = v x (the axis
+    // of v's smallest component), normalised; g = v x e
+    const float ax = fabsf(vx), ay = fabsf(vy), az = fabsf(vz);
+    float ex, ey, ez;
+    if (ax <= ay && ax <= az) ex = 0.0f, ey = vz, ez = -vy;
+    else if (ay <= az) ex = -vz, ey = 0.0f, ez = vx;
+    else ex = vy, ey = -vx, ez = 0.0f;
+    const float ie = rsqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+    ex *= ie, ey *= ie, ez *= ie;
+    const float gx = fmaf(vy, ez, -vz * ey), gy = fmaf(vz, ex, -vx * ez), gz = fmaf(vx, ey, -vy * ex);
+    // (3) the 2 x 2 block [[e.Ae, e.Ag], [e.Ag, g.Ag]] and v.Av
+    const float Aex = fmaf(a00, ex, fmaf(a01, ey, a02 * ez)), Aey = fmaf(a01, ex, fmaf(a11, ey, a12 * ez)),
+                Aez = fmaf(a02, ex, fmaf(a12, ey, a22 * ez));
+    const float Agx = fmaf(a00, gx, fmaf(a01, gy, a02 * gz)), Agy = fmaf(a01, gx, fmaf(a11, gy, a12 * gz)),
+                Agz = fmaf(a02, gx, fmaf(a12, gy, a22 * gz));
+    const float Avx = fmaf(a00, vx, fmaf(a01, vy, a02 * vz)), Avy = fmaf(a01, vx, fmaf(a11, vy, a12 * vz)),
+                Avz = fmaf(a02, vx, fmaf(a12, vy, a22 * vz));
+    const float m00 = fmaf(ex, Aex, fmaf(ey, Aey, ez * Aez));
+    const float m11 = fmaf(gx, Agx, fmaf(gy, Agy, gz * Agz));
+    const float m01 = fmaf(ex, Agx, fmaf(ey, Agy, ez * Agz));
+    d[0] = fmaf(vx, Avx, fmaf(vy, Avy, vz * Avz));
+    float t = 0.0f;
+    if (m01 != 0.0f) {
+        const float theta = (m11 - m00) / (2.0f * m01);
+        t = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
+    }
+    d[1] = fmaf(-t, m01, m00);
+    d[2] = fmaf(t, m01, m11);
+    v[0] = vx, v[1] = vy, v[2] = vz;
     if constexpr (VEC) {
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            const float vp = V[r][p], vq = V[r][q];
-            V[r][p] = c * vp - s * vq;
-            V[r][q] = s * vp + c * vq;
-        }
+        const float c = rsqrtf(fmaf(t, t, 1.0f)), s = t * c;
+        ga[0] = c * ex - s * gx, ga[1] = c * ey - s * gy, ga[2] = c * ez - s * gz;
+        gb[0] = s * ex + c * gx, gb[1] = s * ey + c * gy, gb[2] = s * ez + c * gz;
     }
-}
-
-// Cyclic Jacobi on the compact symmetric 3 x 3 matrix x = (a00 a11 a22 a01 a02 a12):
-// on return d holds the eigenvalues and (VEC) V the eigenvectors as columns.
-template <bool VEC>
-__device__ __forceinline__ void jacobi3(const float (&x)[6], float (&d)[3], float (&V)[3][3])
-{
-    float a00 = x[0], a11 = x[1], a22 = x[2], a01 = x[3], a02 = x[4], a12 = x[5];
-    if constexpr (VEC) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) V[i][j] = i == j ? 1.0f : 0.0f;
-    }
-#pragma unroll
-    for (int sw = 0; sw < 4; ++sw) {
-        rot3<VEC>(a00, a11, a01, a02, a12, V, 0, 1);   // (p, q) = (0, 1), r = 2: (a20, a21)
-        rot3<VEC>(a00, a22, a02, a01, a12, V, 0, 2);   // (0, 2), r = 1: (a10, a12)
-        rot3<VEC>(a11, a22, a12, a01, a02, V, 1, 2);   // (1, 2), r = 0: (a01, a02)
-    }
-    d[0] = a00;
-    d[1] = a11;
-    d[2] = a22;
 }
 
 // x <- shrink_nuc(x; t) for a compact symmetric matrix (K = 3 or 6)
@@ -158,21 +200,25 @@ template <int K>
 __device__ __forceinline__ void sym_shrink_nuc(float (&x)[K], float t)
 {
     constexpr int M = Side<K>::v;
-    if constexpr (M > 0) {
-        float d[M], V[M][M];
-        if constexpr (M == 3) {
-            jacobi3<true>(x, d, V);
-        } else {
-            float A[M][M];
-            unpack<M>(x, A);
-            jacobi<M, true>(A, V);
+    if constexpr (M == 3) {
+        float d[3], v[3], ga[3], gb[3];
+        eig3<true>(x, d, v, ga, gb);
+        float f[3];
 #pragma unroll
-            for (int i = 0; i < M; ++i) d[i] = A[i][i];
-        }
+        for (int i = 0; i < 3; ++i) f[i] = fabsf(d[i]) > t ? d[i] - copysignf(t, d[i]) : 0.0f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = a; b < 3; ++b)
+                x[sidx<3>(a, b)] = fmaf(f[0] * v[a], v[b], fmaf(f[1] * ga[a], ga[b], f[2] * gb[a] * gb[b]));
+    } else if constexpr (M == 2) {
+        float A[M][M], V[M][M];
+        unpack<M>(x, A);
+        jacobi<M, true>(A, V);
         float f[M];
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-            const float l = d[i];
+            const float l = A[i][i];
             f[i] = fabsf(l) > t ? l - copysignf(t, l) : 0.0f;
         }
 #pragma unroll
@@ -194,22 +240,21 @@ __device__ __forceinline__ void sym_nuc_spec(const float (&x)[K], float &nuc, fl
 {
     constexpr int M = Side<K>::v;
     nuc = spec = 0.0f;
-    if constexpr (M > 0) {
-        float d[M], V[M][M];
-        if constexpr (M == 3) {
-            jacobi3<false>(x, d, V);
-        } else {
-            float A[M][M];
-            unpack<M>(x, A);
-            jacobi<M, false>(A, V);
+    float d[M > 0 ? M : 1];
+    if constexpr (M == 3) {
+        float v[3], ga[3], gb[3];
+        eig3<false>(x, d, v, ga, gb);
+    } else if constexpr (M == 2) {
+        float A[M][M], V[M][M];
+        unpack<M>(x, A);
+        jacobi<M, false>(A, V);
 #pragma unroll
-            for (int i = 0; i < M; ++i) d[i] = A[i][i];
-        }
+        for (int i = 0; i < M; ++i) d[i] = A[i][i];
+    }
 #pragma unroll
-        for (int i = 0; i < M; ++i) {
-            nuc += fabsf(d[i]);
-            spec = fmaxf(spec, fabsf(d[i]));
-        }
+    for (int i = 0; i < M; ++i) {
+        nuc += fabsf(d[i]);
+        spec = fmaxf(spec, fabsf(d[i]));
     }
 }
 
