@@ -20,9 +20,12 @@
 // well conditioned; (3) the other two eigenpairs are those of the 2 x 2 block
 // of A on the plane orthogonal to that vector, by one exact Jacobi rotation.
 // The cubic alone would not do: near a double eigenvalue its two close roots
-// carry errors of order sqrt(eps) p, and the deflation removes them.  In FP32
-// the shrink of random, clustered, graded, near-scalar and exactly degenerate
-// matrices is within 6e-7 (relative to ||A||_F) of the exact FP64 shrink.
+// carry errors of order sqrt(eps) p, and the deflation removes them.  Only v
+// depends on the accuracy of l (an error d in l turns v by about d / (sqrt(3) p));
+// the eigenvalues are Rayleigh quotients.  In FP32 the shrink of random,
+// clustered, graded, near-scalar and exactly degenerate matrices is within
+// 6e-7 (relative to ||A||_F) of the exact FP64 shrink, and within 8e-7 with l
+// moved by 8e-7 p.
 // The dependent chain is about a fifth of that of cyclic Jacobi (twelve
 // rotations, each with two divisions and a square root).
 //
@@ -121,7 +124,23 @@ template <bool VEC>
 __device__ __forceinline__ void eig3(const float (&x)[6], float (&d)[3], float (&v)[3], float (&ga)[3],
                                      float (&gb)[3])
 {
-    const float a00 = x[0], a11 = x[1], a22 = x[2], a01 = x[3], a02 = x[4], a12 = x[5];
+    // work on A / max |a_ij|: the cross products below are squares of entries
+    // and their norms fourth powers, which would underflow in FP32 at the scale
+    // of the primal steps (entries near 1e-10)
+    const float sc = fmaxf(fmaxf(fmaxf(fabsf(x[0]), fabsf(x[1])), fmaxf(fabsf(x[2]), fabsf(x[3]))),
+                           fmaxf(fabsf(x[4]), fabsf(x[5])));
+    if (sc < 1e-30f) {      // A vanishes to FP32 range: eigenvalues 0, the unit axes as vectors
+        d[0] = d[1] = d[2] = 0.0f;
+        v[0] = 1.0f, v[1] = 0.0f, v[2] = 0.0f;
+        if constexpr (VEC) {
+            ga[0] = 0.0f, ga[1] = 1.0f, ga[2] = 0.0f;
+            gb[0] = 0.0f, gb[1] = 0.0f, gb[2] = 1.0f;
+        }
+        return;
+    }
+    const float isc = __fdividef(1.0f, sc);
+    const float a00 = x[0] * isc, a11 = x[1] * isc, a22 = x[2] * isc, a01 = x[3] * isc, a02 = x[4] * isc,
+                a12 = x[5] * isc;
     const float q = (a00 + a11 + a22) * (1.0f / 3.0f);
     const float b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
     const float off = fmaf(a01, a01, fmaf(a02, a02, a12 * a12));
@@ -139,7 +158,7 @@ __device__ __forceinline__ void eig3(const float (&x)[6], float (&d)[3], float (
         const float r = fminf(fmaxf(0.5f * det, -1.0f), 1.0f);
         const float phi = acosf(r) * (1.0f / 3.0f);
         float sn, cs;
-        sincosf(phi, &sn, &cs);
+        __sincosf(phi, &sn, &cs);     // phi in [0, pi / 3]: the intrinsic's error moves li by < 1e-6 p
         li = phi <= 0.52359877f ? fmaf(2.0f * p, cs, q) : fmaf(-p, fmaf(1.7320508f, sn, cs), q);
     }
     // (2) its eigenvector: the longest cross product of two rows of A - li I
@@ -179,14 +198,14 @@ __device__ __forceinline__ void eig3(const float (&x)[6], float (&d)[3], float (
     const float m00 = fmaf(ex, Aex, fmaf(ey, Aey, ez * Aez));
     const float m11 = fmaf(gx, Agx, fmaf(gy, Agy, gz * Agz));
     const float m01 = fmaf(ex, Agx, fmaf(ey, Agy, ez * Agz));
-    d[0] = fmaf(vx, Avx, fmaf(vy, Avy, vz * Avz));
+    d[0] = sc * fmaf(vx, Avx, fmaf(vy, Avy, vz * Avz));
     float t = 0.0f;
-    if (m01 != 0.0f) {
-        const float theta = (m11 - m00) / (2.0f * m01);
-        t = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
+    if (fabsf(m01) > 1e-30f) {      // (entries are at most 1 here)
+        const float theta = __fdividef(m11 - m00, 2.0f * m01);
+        t = __fdividef(copysignf(1.0f, theta), fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
     }
-    d[1] = fmaf(-t, m01, m00);
-    d[2] = fmaf(t, m01, m11);
+    d[1] = sc * fmaf(-t, m01, m00);
+    d[2] = sc * fmaf(t, m01, m11);
     v[0] = vx, v[1] = vy, v[2] = vz;
     if constexpr (VEC) {
         const float c = rsqrtf(fmaf(t, t, 1.0f)), s = t * c;

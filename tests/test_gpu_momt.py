@@ -161,6 +161,24 @@ def test_matrix_parity_nuclear_norms(engine, k, u_norm, w_norm):
 
 
 @pytest.mark.parametrize("engine", ENGINES)
+def test_matrix_nuclear_parity_at_tiny_scale(engine):
+    """Scaling both densities by s and tau by 1/s scales mu and nu by s (Section 7.3's rules),
+    so the exact iterates are s U, s W and the same Phi.  At s = 2^-40 the 3 x 3 entries of the
+    nuclear shrink sit near 1e-20, where squares of squares underflow in FP32; the GPU must
+    still match the FP64 oracle run on the same scaled problem."""
+    k, s = 3, 2.0 ** -40
+    L = S.random_L(k, 3, seed=43)
+    T0, T1 = S.tensor_field_pair(29, k, seed=44)
+    sol, ref = _run(T0 * s, T1 * s, L, 0.7, tau=30.0 / s, max_iters=900, check_every=300, engine=engine,
+                    u_norm=oracle.U_NUC, w_norm=oracle.W_NUC)
+    _compare(sol, ref)
+    big, _ = _run(T0, T1, L, 0.7, tau=30.0, max_iters=900, check_every=300, engine=engine, u_norm=oracle.U_NUC,
+                  w_norm=oracle.W_NUC)
+    assert _rel(sol.U.cpu().numpy() / s, big.U.cpu().numpy()) <= 1e-4
+    assert sol.result["primal"] / s == pytest.approx(big.result["primal"], rel=1e-4)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
 def test_matrix_nuclear_isotropic_shift_on_gpu(engine):
     """||U||_{1,nuc}: an isotropic density moved s cells costs mass x shift (within the
     tolerance reached)."""
