@@ -304,8 +304,9 @@ __device__ __forceinline__ bool poll_pairs(int cnt, uint32_t tag, ResCtl *ctl, u
 
 // ------------------------------------------------------------------ the kernel
 // NM = 1: the norms are the vector default pair (||u||_{1,2}, ||w||_1), fixed at
-// compile time; NM = 2: the matrix default pair (||U||_2, ||W||_1); NM = 0: the
-// norms are read from the arguments.
+// compile time; NM = 2: the matrix default pair (||U||_2, ||W||_1); NM = 3: both
+// nuclear norms (||U||_{1,nuc}, ||W||_{1,nuc}; 3 x 3 matrices); NM = 0: the norms
+// are read from the arguments.
 template <int K, int P, int NM>
 __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, const int NT, const uint32_t tag_hi)
 {
@@ -344,8 +345,8 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int k = a.g.k, l = a.g.l, F = 3 * K + l, F2 = (F + 1) / 2;
-    const int un = NM == 1 ? (int)VOMT_U_L12 : (NM == 2 ? (int)VOMT_U_L2 : a.un);
-    const int wn = NM ? (int)VOMT_W_L1 : a.wn;
+    const int un = NM == 1 ? (int)VOMT_U_L12 : (NM == 2 ? (int)VOMT_U_L2 : (NM == 3 ? (int)VOMT_U_NUC : a.un));
+    const int wn = NM == 3 ? (int)VOMT_W_NUC : (NM ? (int)VOMT_W_L1 : a.wn);
     const float mu = a.s.mu, nu = a.s.nu, tau = a.s.tau, ih = a.s.ih, alpha = a.s.alpha;
     const float muih = mu * ih;
     const int T = a.max_iters, CE = a.check_every;
@@ -401,30 +402,36 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
     }
     __syncthreads();
 
-    // ---- halo exchange number e: publish the tile's band, receive the ring
-    auto exchange = [&](int e) -> bool {
+    // ---- publish band point r for halo exchange number e (its tagged word pairs)
+    auto publish_point = [&](int r, int e) {
+        if (a.drop_exch > 0 && e == a.drop_exch && tile == 0) return;
         const uint32_t tag = tag_hi + (uint32_t)e + 1u;
         const int par = e & 1;
-        const bool publish = !(a.drop_exch > 0 && e == a.drop_exch && tile == 0);
+        const int lx = (pxy[r] & 0xffff) - fr.x0, ly = (pxy[r] >> 16) - fr.y0;
+        float vals[2 * F2MAX];
 #pragma unroll
-        for (int r = 0; r < P; ++r) {
-            if (!pband[r] || !publish) continue;
-            const int lx = (pxy[r] & 0xffff) - fr.x0, ly = (pxy[r] >> 16) - fr.y0;
-            float vals[2 * F2MAX];
+        for (int q = 0; q < 2 * F2MAX; ++q) vals[q] = 0.0f;
 #pragma unroll
-            for (int q = 0; q < 2 * F2MAX; ++q) vals[q] = 0.0f;
-#pragma unroll
-            for (int c = 0; c < K; ++c) {
-                vals[c] = ph[r][c];
-                vals[K + c] = ux[r][c];
-                vals[2 * K + c] = uy[r][c];
-            }
-#pragma unroll
-            for (int e2 = 0; e2 < LKv; ++e2) vals[3 * K + e2] = w[r][e2];
-#pragma unroll
-            for (int j = 0; j < F2MAX; ++j)
-                if (j < F2) st_tagged2(xpair(tile, par, j, ly, lx), vals[2 * j], vals[2 * j + 1], tag);
+        for (int c = 0; c < K; ++c) {
+            vals[c] = ph[r][c];
+            vals[K + c] = ux[r][c];
+            vals[2 * K + c] = uy[r][c];
         }
+#pragma unroll
+        for (int e2 = 0; e2 < LKv; ++e2) vals[3 * K + e2] = w[r][e2];
+#pragma unroll
+        for (int j = 0; j < F2MAX; ++j)
+            if (j < F2) st_tagged2(xpair(tile, par, j, ly, lx), vals[2 * j], vals[2 * j + 1], tag);
+    };
+
+    // ---- halo exchange number e: publish the tile's band (unless the last step
+    // already did), receive the ring
+    auto exchange = [&](int e, bool published) -> bool {
+        const uint32_t tag = tag_hi + (uint32_t)e + 1u;
+        const int par = e & 1;
+#pragma unroll
+        for (int r = 0; r < P; ++r)
+            if (pband[r] && !published) publish_point(r, e);
         bool ok = true;
 #pragma unroll
         for (int r = 0; r < P; ++r) {
@@ -457,7 +464,7 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
 #pragma unroll
     for (int r = 0; r < P; ++r)
         if (ptile[r]) sts<K>(sphi + sb[r], ph[r]);
-    if (!exchange(0)) dec[0] = 1;
+    if (!exchange(0, false)) dec[0] = 1;
     __syncthreads();
     bool aborted = dec[0] != 0;
     int nexch = 1, checks = 0, t = 0;
@@ -466,6 +473,8 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
     // reciprocals of the check's weights, once per solve (FP64 division is slow here)
     const double inv_mu = 1.0 / a.cfg.mu, inv_nu = a.cfg.has_w ? 1.0 / a.cfg.nu : 0.0;
     const double inv_tau = 1.0 / a.cfg.tau, inv4eps = a.cfg.eps > 0.0 ? 0.25 / a.cfg.eps : 0.0;
+    const bool use_tol = a.cfg.tol_gap > 0.0;
+    const double tol_g = a.cfg.tol_gap, tol_r2 = a.cfg.tol_res * a.cfg.tol_res;
 
     float racc[P][K];
 #pragma unroll
@@ -480,7 +489,13 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
     // <dphi, div du + div_G dw>, where du on the points left of and below the tile
     // comes from the same phase-1 arithmetic their own tile does.
     float fdu = 0.0f, fdw = 0.0f, fdp = 0.0f, fdx = 0.0f;
-    auto step = [&](auto last_tag, int nR, int nRp) {
+    // pub_e >= 0: the last step before halo exchange pub_e.  With six and more
+    // channels (EARLY) each band point publishes as soon as its phi is final, so
+    // that its many stores drain while the rest of the tile finishes the step
+    // (measured: 3 x 3 matrices at 128^2 gain 2-3%; at three channels the extra
+    // code in the step costs more than the overlap gains)
+    constexpr bool EARLY = K >= 6;
+    auto step = [&](auto last_tag, int nR, int nRp, int pub_e) {
         constexpr bool LAST = decltype(last_tag)::value;
 #pragma unroll
         for (int r = 0; r < P; ++r) {
@@ -595,6 +610,7 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
                 ph[r][c] = np;
             }
             sts<K>(sphi + b, ph[r]);
+            if (EARLY && pub_e >= 0 && pband[r]) publish_point(r, pub_e);
             if constexpr (LAST) {
                 float dxo[K], dxl[K], dyo[K], dyd[K], dg[K];
                 lds<K>(sdx + b, dxo);
@@ -628,15 +644,16 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
         for (int s = 1; s <= hb; ++s) {
             const int rr = min(hb - s, R);      // ring width of the region this step updates
             const int nR = cntR[rr], nRp = cntRp[rr];
+            const int pub_e = s == hb ? nexch : -1;
             if (s == hb && check_after)
-                step(std::integral_constant<bool, true>(), nR, nRp);
+                step(std::integral_constant<bool, true>(), nR, nRp, pub_e);
             else
-                step(std::integral_constant<bool, false>(), nR, nRp);
+                step(std::integral_constant<bool, false>(), nR, nRp, pub_e);
         }
         t = t_end;
         // ---- refresh the ring
         if (hb > 0) {
-            if (!exchange(nexch)) dec[0] = 1;
+            if (!exchange(nexch, EARLY)) dec[0] = 1;
             ++nexch;
             __syncthreads();
             if (dec[0]) { aborted = true; break; }
@@ -820,15 +837,30 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
         const int cpar = checks & 1;
         const uint32_t ctag = tag_hi + (uint32_t)checks + 1u;
         const int words = NT * NRED * 2;
-        if (tid < NRED) {
-            double acc = tid == RED_MAX ? (double)redf[tid * 2] : (double)redf[tid * 2] + (double)redf[tid * 2 + 1];
-            for (int q = 1; q < nw; ++q) {
-                const double x_ = (double)redf[(q * NRED + tid) * 2], y_ = (double)redf[(q * NRED + tid) * 2 + 1];
-                acc = (tid == RED_MAX) ? fmax(acc, x_) : acc + (x_ + y_);
+        // the block's row: warp q sums slot q over the warps' (hi, lo) pairs, lane j
+        // taking warp j, then a butterfly over the lanes.  An FP64 instruction costs a
+        // whole warp's issue on this GPU whatever its active lanes, so the few FP64
+        // instructions are spread over the warps (the maximum stays in FP32: exact)
+        for (int q = wid; q < NRED; q += nw) {
+            double acc = 0.0;
+            if (q == RED_MAX) {
+                float mx = 0.0f;
+                for (int j = lane; j < nw; j += 32) mx = fmaxf(mx, redf[(j * NRED + q) * 2]);
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+                acc = (double)mx;
+            } else {
+                for (int j = lane; j < nw; j += 32)
+                    acc += (double)redf[(j * NRED + q) * 2] + (double)redf[(j * NRED + q) * 2 + 1];
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1)
+                    if (off < nw) acc += __shfl_xor_sync(0xffffffffu, acc, off);
             }
-            unsigned long long *dst = a.rows + (size_t)cpar * words + ((size_t)tile * NRED + tid) * 2;
-            st_tagged(dst, __int_as_float(__double2hiint(acc)), ctag);
-            st_tagged(dst + 1, __int_as_float(__double2loint(acc)), ctag);
+            if (lane == 0) {
+                unsigned long long *dst = a.rows + (size_t)cpar * words + ((size_t)tile * NRED + q) * 2;
+                st_tagged(dst, __int_as_float(__double2hiint(acc)), ctag);
+                st_tagged(dst + 1, __int_as_float(__double2loint(acc)), ctag);
+            }
         }
         // every block gathers every row (one L2 round trip) ...
         {
@@ -867,17 +899,23 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
             // the host from the row (finish_raw_row)
             double m[NMET];
             m[0] = S[RED_P];
-            m[1] = S[RED_D] - S[RED_DIST] * inv4eps;
+            m[1] = fma(-S[RED_DIST], inv4eps, S[RED_D]);
             m[2] = S[RED_RR];
             m[3] = S[RED_BB];
-            m[4] = S[RED_DU] * inv_mu + S[RED_DW] * inv_nu + S[RED_DP] * inv_tau - 2.0 * S[RED_X];
+            m[4] = fma(S[RED_DU], inv_mu, fma(S[RED_DW], inv_nu, fma(S[RED_DP], inv_tau, -2.0 * S[RED_X])));
             m[5] = S[RED_MAX];
             m[6] = (double)t;
+            // finiteness, magnitudes and comparisons of non-negative values on the
+            // bit patterns (integer instructions; IEEE order of non-negative doubles is
+            // the order of their bits)
             bool finite = true;
-            for (int q = 0; q < 6; ++q) finite = finite && isfinite(m[q]);
-            const double tg = a.cfg.tol_gap, tr = a.cfg.tol_res;
-            const bool conv = tg > 0.0 && fabs(m[0] - m[1]) <= tg * fmax(fabs(m[0]), 1e-300) &&
-                              m[2] <= tr * tr * (m[3] > 0.0 ? m[3] : 1.0);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) finite = finite && (((uint32_t)__double2hiint(m[q]) & 0x7ff00000u) != 0x7ff00000u);
+            const auto mag = [](double x) { return (long long)((unsigned long long)__double_as_longlong(x) << 1 >> 1); };
+            const long long p_mag = mag(m[0]), tiny = mag(1e-300);
+            const double scale = __longlong_as_double(p_mag > tiny ? p_mag : tiny);
+            const double bb = mag(m[3]) > 0 ? m[3] : 1.0;
+            const bool conv = use_tol && mag(m[0] - m[1]) <= mag(tol_g * scale) && mag(m[2]) <= mag(tol_r2 * bb);
             m[7] = conv ? 1.0 : 0.0;
             if (tile == 0) {
                 for (int q = 0; q < NMET; ++q) a.st->met[q] = m[q];
@@ -967,6 +1005,9 @@ ResKernel kernel_for(int P, int NM)
 {
     if constexpr (K == 3 || K == 6) {     // compact 2 x 2 and 3 x 3 matrices
         if (NM == 2) return P == 1 ? k_resident<K, 1, 2> : (P == 2 ? k_resident<K, 2, 2> : k_resident<K, 4, 2>);
+    }
+    if constexpr (K == 6) {               // 3 x 3 matrices, both nuclear norms
+        if (NM == 3) return P == 1 ? k_resident<K, 1, 3> : (P == 2 ? k_resident<K, 2, 3> : k_resident<K, 4, 3>);
     }
     if (NM == 1) return P == 1 ? k_resident<K, 1, 1> : (P == 2 ? k_resident<K, 2, 1> : k_resident<K, 4, 1>);
     return P == 1 ? k_resident<K, 1, 0> : (P == 2 ? k_resident<K, 2, 0> : k_resident<K, 4, 0>);

@@ -241,6 +241,7 @@ int resident_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveC
     int nm = 0;
     if (p.u_norm == VOMT_U_L12 && p.w_norm == VOMT_W_L1) nm = 1;
     else if (p.u_norm == VOMT_U_L2 && p.w_norm == VOMT_W_L1 && (K == 3 || K == 6)) nm = 2;
+    else if (p.u_norm == VOMT_U_NUC && p.w_norm == VOMT_W_NUC && K == 6) nm = 3;
     res::ResKernel kern = res::res_kernel(K, plan.P, nm);
     if (!kern) {
         ctx->err = "no resident kernel for this channel count and norm pair";
