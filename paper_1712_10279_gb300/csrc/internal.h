@@ -234,6 +234,7 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
 struct ResidentPlan {
     int Gx, Gy, TXm, TYm, H, threads, P;
     double est_ns;      // estimated ns per iteration (a wave plan: of the whole wave, all its rounds)
+    int lb;             // launch bound of the single-problem kernel (0: res_threads(k))
 };
 // Fixed-order sum of per-block FP64 partials (NRED per block), the stopping
 // decision and the history row (one block of 256 threads; vector_stream.cu).

@@ -5,10 +5,10 @@
 namespace vomt {
 namespace res {
 
-ResKernel res_kernel_k12(int K, int P, int NM)
+ResKernel res_kernel_k12(int K, int P, int NM, int LB, int LF)
 {
-    if (K == 1) return kernel_for<1>(P, NM);
-    if (K == 2) return kernel_for<2>(P, NM);
+    if (K == 1) return kernel_for<1>(P, NM, LB, LF);
+    if (K == 2) return kernel_for<2>(P, NM, LB, LF);
     return nullptr;
 }
 

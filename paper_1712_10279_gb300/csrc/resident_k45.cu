@@ -5,10 +5,10 @@
 namespace vomt {
 namespace res {
 
-ResKernel res_kernel_k45(int K, int P, int NM)
+ResKernel res_kernel_k45(int K, int P, int NM, int LB, int LF)
 {
-    if (K == 4) return kernel_for<4>(P, NM);
-    if (K == 5) return kernel_for<5>(P, NM);
+    if (K == 4) return kernel_for<4>(P, NM, LB, LF);
+    if (K == 5) return kernel_for<5>(P, NM, LB, LF);
     return nullptr;
 }
 

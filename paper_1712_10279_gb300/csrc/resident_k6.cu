@@ -5,9 +5,9 @@
 namespace vomt {
 namespace res {
 
-ResKernel res_kernel_k6(int K, int P, int NM)
+ResKernel res_kernel_k6(int K, int P, int NM, int LB, int LF)
 {
-    if (K == 6) return kernel_for<6>(P, NM);
+    if (K == 6) return kernel_for<6>(P, NM, LB, LF);
     return nullptr;
 }
 

@@ -5,10 +5,10 @@
 namespace vomt {
 namespace res {
 
-ResKernel res_kernel_k78(int K, int P, int NM)
+ResKernel res_kernel_k78(int K, int P, int NM, int LB, int LF)
 {
-    if (K == 7) return kernel_for<7>(P, NM);
-    if (K == 8) return kernel_for<8>(P, NM);
+    if (K == 7) return kernel_for<7>(P, NM, LB, LF);
+    if (K == 8) return kernel_for<8>(P, NM, LB, LF);
     return nullptr;
 }
 

@@ -7,8 +7,10 @@
 namespace vomt {
 namespace res {
 
-ResKernel res_kernel_k9(int K, int P, int NM)
+ResKernel res_kernel_k9(int K, int P, int NM, int LB, int LF)
 {
+    (void)LB;
+    (void)LF;
     if (K != 9 || NM != 0) return nullptr;
     return P == 1 ? k_resident<9, 1, 0> : (P == 2 ? k_resident<9, 2, 0> : k_resident<9, 4, 0>);
 }

@@ -306,11 +306,14 @@ __device__ __forceinline__ bool poll_pairs(int cnt, uint32_t tag, ResCtl *ctl, u
 // NM = 1: the norms are the vector default pair (||u||_{1,2}, ||w||_1), fixed at
 // compile time; NM = 2: the matrix default pair (||U||_2, ||W||_1); NM = 3: both
 // nuclear norms (||U||_{1,nuc}, ||W||_{1,nuc}; 3 x 3 matrices); NM = 0: the norms
-// are read from the arguments.
-template <int K, int P, int NM>
+// are read from the arguments.  LF > 0 fixes the number of flux entries per point
+// at compile time (9 for 3 x 3 matrices with three L matrices: the flux loops then
+// run over 9 entries instead of the 15 that a 3 x 3 problem may have); LF = 0
+// reads it from the operator.
+template <int K, int P, int NM, int LF = 0>
 __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, const int NT, const uint32_t tag_hi)
 {
-    constexpr int LKv = LK<K>::v;
+    constexpr int LKv = LF > 0 ? LF : LK<K>::v;
     constexpr int FMAX = 3 * K + LKv;
     constexpr int F2MAX = (FMAX + 1) / 2;
     constexpr int KV = kv_of(K);
@@ -344,7 +347,7 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
     const int RS = G.EWs * KV;             // one row of a shared array, in floats
 
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int k = a.g.k, l = a.g.l, F = 3 * K + l, F2 = (F + 1) / 2;
+    const int k = a.g.k, l = LF > 0 ? LF : a.g.l, F = 3 * K + l, F2 = (F + 1) / 2;
     const int un = NM == 1 ? (int)VOMT_U_L12 : (NM == 2 ? (int)VOMT_U_L2 : (NM == 3 ? (int)VOMT_U_NUC : a.un));
     const int wn = NM == 3 ? (int)VOMT_W_NUC : (NM ? (int)VOMT_W_L1 : a.wn);
     const float mu = a.s.mu, nu = a.s.nu, tau = a.s.tau, ih = a.s.ih, alpha = a.s.alpha;
@@ -629,6 +632,116 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
         __syncthreads();
     };
 
+    // ---- the tile's iterate to the caller's arrays: at the end, and at every check
+    // whose stop decision is deferred (the arrays then hold that check's iterate)
+    auto write_out = [&]() {
+#pragma unroll
+        for (int r = 0; r < P; ++r) {
+            if (!ptile[r]) continue;
+            const int x = pxy[r] & 0xffff, y = pxy[r] >> 16;
+            const size_t p = (size_t)y * n + x;
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                a.phi[c * nn + p] = ph[r][c];
+                a.u[c * nn + p] = ux[r][c];
+                a.u[(k + c) * nn + p] = uy[r][c];
+            }
+#pragma unroll
+            for (int e = 0; e < LKv; ++e)
+                if (e < l) a.w[e * nn + p] = w[r][e];
+        }
+    };
+
+    // ---- stop decision of check number idx (the iterate after iteration tc): every
+    // block gathers every block's row (one L2 round trip), sums the rows in a fixed
+    // order and decides; block 0 records the metric row.  dec[2] = 1 stops.  Returns
+    // false if a wait ran out (the solve is then aborted).
+    auto decide = [&](int idx, int tc) -> bool {
+        const int cpar = idx & 1;
+        const uint32_t ctag = tag_hi + (uint32_t)idx + 1u;
+        const int words = NT * NRED * 2;
+        const int lane = tid & 31, wid = tid >> 5, nw = (nthr + 31) >> 5;
+        {
+            const int mine = tid < words ? (words - tid + nthr - 1) / nthr : 0;
+            const bool ok = poll_words<8>(
+                mine, ctag, a.ctl, a.wait_ns,
+                [&](int j) { return a.rows + (size_t)cpar * words + (size_t)tid + (size_t)j * nthr; },
+                [&](int j, uint32_t bits) {
+                    const int widx = tid + j * nthr;
+                    ((uint32_t *)rtab)[(widx >> 1) * 2 + ((widx & 1) ? 0 : 1)] = bits;
+                });
+            if (!ok) dec[0] = 1;
+        }
+        __syncthreads();
+        if (dec[0]) return false;
+        // fixed-order sum: lane j takes rows j, j + 32, ..., then a butterfly over the
+        // lanes (every lane ends with the same sum, in every block)
+        for (int q = wid; q < NRED; q += nw) {
+            double acc = 0.0;
+            for (int b = lane; b < NT; b += 32) {
+                const double x_ = rtab[b * NRED + q];
+                acc = (q == RED_MAX) ? fmax(acc, x_) : acc + x_;
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const double o = __shfl_xor_sync(0xffffffffu, acc, off);
+                acc = (q == RED_MAX) ? fmax(acc, o) : acc + o;
+            }
+            if (lane == 0) S[q] = acc;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            // the stop decision with products and comparisons only: rel_gap <= tol_gap is
+            // |P - D| <= tol_gap max(|P|, 1e-300), rel_res <= tol_res is
+            // ||r||^2 <= tol_res^2 ||rho0 - rho1||^2; the ratios themselves are formed on
+            // the host from the row (finish_raw_row)
+            double m[NMET];
+            m[0] = S[RED_P];
+            m[1] = fma(-S[RED_DIST], inv4eps, S[RED_D]);
+            m[2] = S[RED_RR];
+            m[3] = S[RED_BB];
+            m[4] = fma(S[RED_DU], inv_mu, fma(S[RED_DW], inv_nu, fma(S[RED_DP], inv_tau, -2.0 * S[RED_X])));
+            m[5] = S[RED_MAX];
+            m[6] = (double)tc;
+            // finiteness, magnitudes and comparisons of non-negative values on the
+            // bit patterns (integer instructions; IEEE order of non-negative doubles is
+            // the order of their bits)
+            bool finite = true;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) finite = finite && (((uint32_t)__double2hiint(m[q]) & 0x7ff00000u) != 0x7ff00000u);
+            const auto mag = [](double x) { return (long long)((unsigned long long)__double_as_longlong(x) << 1 >> 1); };
+            const long long p_mag = mag(m[0]), tiny = mag(1e-300);
+            const double scale = __longlong_as_double(p_mag > tiny ? p_mag : tiny);
+            const double bb = mag(m[3]) > 0 ? m[3] : 1.0;
+            const bool conv = use_tol && mag(m[0] - m[1]) <= mag(tol_g * scale) && mag(m[2]) <= mag(tol_r2 * bb);
+            m[7] = conv ? 1.0 : 0.0;
+            if (tile == 0) {
+                for (int q = 0; q < NMET; ++q) a.st->met[q] = m[q];
+                if (a.hist && idx < a.hist_cap)
+                    for (int q = 0; q < NMET; ++q) a.hist[(size_t)idx * NMET + q] = m[q];
+                a.st->raw = 1;
+                a.st->checks = idx + 1;
+                a.st->iter = tc;
+                if (!finite) a.st->error = VOMT_ERR_NONFINITE;
+                if (conv || !finite) a.st->stop = 1;
+            }
+            dec[2] = (conv || !finite || tc >= T) ? 1 : 0;
+        }
+        __syncthreads();
+        return true;
+    };
+
+    // A check before the last iteration publishes its row and saves the iterate to
+    // the caller's arrays, and the iteration runs on; the rows are gathered and the
+    // stop decision taken after the next halo exchange, when every block's row has
+    // long arrived, so that no block waits for the slowest one.  If that decision
+    // stops, the solve ends with the saved iterate (the extra iterations are
+    // discarded).  Rows alternate between two slots: a block publishes the row of
+    // check c + 1 only after its decision of check c, which needed every row of c,
+    // so no slot is overwritten before every block has read it.
+    int pend = -1, pend_t = 0;
+    bool saved = false;
+
     while (!aborted && !stop) {
         // a block of iterations runs to the next check (or the end) or H iterations
         int hb = 0;
@@ -657,6 +770,11 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
             ++nexch;
             __syncthreads();
             if (dec[0]) { aborted = true; break; }
+        }
+        if (pend >= 0) {
+            if (!decide(pend, pend_t)) { aborted = true; break; }
+            pend = -1;
+            if (dec[2]) { saved = true; break; }
         }
         if (!check_after) continue;
 
@@ -862,74 +980,13 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
                 st_tagged(dst + 1, __int_as_float(__double2loint(acc)), ctag);
             }
         }
-        // every block gathers every row (one L2 round trip) ...
-        {
-            const int mine = tid < words ? (words - tid + nthr - 1) / nthr : 0;
-            const bool ok = poll_words<8>(
-                mine, ctag, a.ctl, a.wait_ns,
-                [&](int j) { return a.rows + (size_t)cpar * words + (size_t)tid + (size_t)j * nthr; },
-                [&](int j, uint32_t bits) {
-                    const int widx = tid + j * nthr;
-                    ((uint32_t *)rtab)[(widx >> 1) * 2 + ((widx & 1) ? 0 : 1)] = bits;
-                });
-            if (!ok) dec[0] = 1;
+        if (R > 0 && t < T) {      // a halo exchange comes before the decision
+            write_out();
+            pend = checks++;
+            pend_t = t;
+            continue;
         }
-        __syncthreads();
-        if (dec[0]) { aborted = true; break; }
-        // ... and sums them in a fixed order: lane j takes rows j, j + 32, ..., then a
-        // butterfly over the lanes (every lane ends with the same sum, in every block)
-        for (int q = wid; q < NRED; q += nw) {
-            double acc = 0.0;
-            for (int b = lane; b < NT; b += 32) {
-                const double x_ = rtab[b * NRED + q];
-                acc = (q == RED_MAX) ? fmax(acc, x_) : acc + x_;
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const double o = __shfl_xor_sync(0xffffffffu, acc, off);
-                acc = (q == RED_MAX) ? fmax(acc, o) : acc + o;
-            }
-            if (lane == 0) S[q] = acc;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            // the stop decision with products and comparisons only: rel_gap <= tol_gap is
-            // |P - D| <= tol_gap max(|P|, 1e-300), rel_res <= tol_res is
-            // ||r||^2 <= tol_res^2 ||rho0 - rho1||^2; the ratios themselves are formed on
-            // the host from the row (finish_raw_row)
-            double m[NMET];
-            m[0] = S[RED_P];
-            m[1] = fma(-S[RED_DIST], inv4eps, S[RED_D]);
-            m[2] = S[RED_RR];
-            m[3] = S[RED_BB];
-            m[4] = fma(S[RED_DU], inv_mu, fma(S[RED_DW], inv_nu, fma(S[RED_DP], inv_tau, -2.0 * S[RED_X])));
-            m[5] = S[RED_MAX];
-            m[6] = (double)t;
-            // finiteness, magnitudes and comparisons of non-negative values on the
-            // bit patterns (integer instructions; IEEE order of non-negative doubles is
-            // the order of their bits)
-            bool finite = true;
-#pragma unroll
-            for (int q = 0; q < 6; ++q) finite = finite && (((uint32_t)__double2hiint(m[q]) & 0x7ff00000u) != 0x7ff00000u);
-            const auto mag = [](double x) { return (long long)((unsigned long long)__double_as_longlong(x) << 1 >> 1); };
-            const long long p_mag = mag(m[0]), tiny = mag(1e-300);
-            const double scale = __longlong_as_double(p_mag > tiny ? p_mag : tiny);
-            const double bb = mag(m[3]) > 0 ? m[3] : 1.0;
-            const bool conv = use_tol && mag(m[0] - m[1]) <= mag(tol_g * scale) && mag(m[2]) <= mag(tol_r2 * bb);
-            m[7] = conv ? 1.0 : 0.0;
-            if (tile == 0) {
-                for (int q = 0; q < NMET; ++q) a.st->met[q] = m[q];
-                if (a.hist && checks < a.hist_cap)
-                    for (int q = 0; q < NMET; ++q) a.hist[(size_t)checks * NMET + q] = m[q];
-                a.st->raw = 1;
-                a.st->checks = checks + 1;
-                a.st->iter = t;
-                if (!finite) a.st->error = VOMT_ERR_NONFINITE;
-                if (conv || !finite) a.st->stop = 1;
-            }
-            dec[2] = (conv || !finite || t >= T) ? 1 : 0;
-        }
-        __syncthreads();
+        if (!decide(checks, t)) { aborted = true; break; }
         ++checks;
         stop = dec[2] != 0;
     }
@@ -940,29 +997,21 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
         }
         return;
     }
-    // ---- final iterate of the tile to the caller's arrays
-#pragma unroll
-    for (int r = 0; r < P; ++r) {
-        if (!ptile[r]) continue;
-        const int x = pxy[r] & 0xffff, y = pxy[r] >> 16;
-        const size_t p = (size_t)y * n + x;
-#pragma unroll
-        for (int c = 0; c < K; ++c) {
-            a.phi[c * nn + p] = ph[r][c];
-            a.u[c * nn + p] = ux[r][c];
-            a.u[(k + c) * nn + p] = uy[r][c];
-        }
-#pragma unroll
-        for (int e = 0; e < LKv; ++e)
-            if (e < l) a.w[e * nn + p] = w[r][e];
-    }
+    // ---- final iterate of the tile to the caller's arrays (unless a deferred
+    // decision stopped the solve: its check's iterate is there already)
+    if (!saved) write_out();
 }
 
 // One problem: the grid is its tiles.
-template <int K, int P, int NM>
-__global__ void __launch_bounds__(res_threads(K), 1) k_resident(const __grid_constant__ ResArgs a)
+// LB: the launch bound (most threads of a block).  A block of 384 threads (12
+// warps, three per SM sub-partition) lets a thread hold 170 registers, 512 only
+// 128 (four warps on some sub-partition): two points per thread need about 170
+// to be processed side by side, so extended tiles of at most 768 points take the
+// 384-thread form.
+template <int K, int P, int NM, int LB = res_threads(K), int LF = 0>
+__global__ void __launch_bounds__(LB, 1) k_resident(const __grid_constant__ ResArgs a)
 {
-    resident_body<K, P, NM>(a, (int)blockIdx.x, (int)gridDim.x, 0u);
+    resident_body<K, P, NM, LF>(a, (int)blockIdx.x, (int)gridDim.x, 0u);
 }
 
 // Many problems of one shape (grouped batch): the grid is `groups` groups of T
@@ -998,11 +1047,30 @@ __global__ void __launch_bounds__(res_threads(K), 1) k_resident_multi(const __gr
 using ResKernel = void (*)(ResArgs);
 using MultiKernel = void (*)(MultiArgs);
 
-// Kernel for K channels, P points per thread and the norm mode NM (one per
-// instantiation unit; the host picks through res_kernel).
+// Kernel for K channels, P points per thread, the norm mode NM, the launch bound
+// LB and the fixed flux count LF (one per instantiation unit; the host picks
+// through res_kernel).  LB = 384 with two points per thread exists for up to four
+// channels; LF = 9 for 3 x 3 matrices with the matrix or the nuclear norms and one
+// or two points per thread; every other request takes LB = res_threads(K), LF = 0.
 template <int K>
-ResKernel kernel_for(int P, int NM)
+ResKernel kernel_for(int P, int NM, int LB, int LF)
 {
+    if constexpr (K <= 4) {
+        if (P == 2 && LB == 384) {
+            if constexpr (K == 3) {
+                if (NM == 2) return k_resident<K, 2, 2, 384>;
+            }
+            return NM == 1 ? k_resident<K, 2, 1, 384> : k_resident<K, 2, 0, 384>;
+        }
+    }
+    if constexpr (K == 6) {
+        if (LF == 9 && P <= 2) {
+            if (NM == 2) return P == 1 ? k_resident<K, 1, 2, 384, 9> : k_resident<K, 2, 2, 384, 9>;
+            if (NM == 3) return P == 1 ? k_resident<K, 1, 3, 384, 9> : k_resident<K, 2, 3, 384, 9>;
+        }
+    }
+    (void)LB;
+    (void)LF;
     if constexpr (K == 3 || K == 6) {     // compact 2 x 2 and 3 x 3 matrices
         if (NM == 2) return P == 1 ? k_resident<K, 1, 2> : (P == 2 ? k_resident<K, 2, 2> : k_resident<K, 4, 2>);
     }
@@ -1032,7 +1100,7 @@ MultiKernel multi_kernel_for(int P, int NM)
     }
 }
 
-ResKernel res_kernel(int K, int P, int NM);
+ResKernel res_kernel(int K, int P, int NM, int LB, int LF);
 MultiKernel res_multi_kernel(int K, int P, int NM);
 
 // Shared memory of the grouped kernel beyond the dynamic layout (the job copy).

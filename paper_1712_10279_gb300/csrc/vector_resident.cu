@@ -12,26 +12,26 @@
 namespace vomt {
 namespace res {
 
-ResKernel res_kernel_k12(int K, int P, int NM);
-ResKernel res_kernel_k3(int K, int P, int NM);
-ResKernel res_kernel_k45(int K, int P, int NM);
-ResKernel res_kernel_k6(int K, int P, int NM);
-ResKernel res_kernel_k78(int K, int P, int NM);
-ResKernel res_kernel_k9(int K, int P, int NM);
+ResKernel res_kernel_k12(int K, int P, int NM, int LB, int LF);
+ResKernel res_kernel_k3(int K, int P, int NM, int LB, int LF);
+ResKernel res_kernel_k45(int K, int P, int NM, int LB, int LF);
+ResKernel res_kernel_k6(int K, int P, int NM, int LB, int LF);
+ResKernel res_kernel_k78(int K, int P, int NM, int LB, int LF);
+ResKernel res_kernel_k9(int K, int P, int NM, int LB, int LF);
 MultiKernel res_multi_kernel_k12(int K, int P, int NM);
 MultiKernel res_multi_kernel_k3(int K, int P, int NM);
 MultiKernel res_multi_kernel_k45(int K, int P, int NM);
 MultiKernel res_multi_kernel_k6(int K, int P, int NM);
 MultiKernel res_multi_kernel_k78(int K, int P, int NM);
 
-ResKernel res_kernel(int K, int P, int NM)
+ResKernel res_kernel(int K, int P, int NM, int LB, int LF)
 {
-    if (K <= 2) return res_kernel_k12(K, P, NM);
-    if (K == 3) return res_kernel_k3(K, P, NM);
-    if (K <= 5) return res_kernel_k45(K, P, NM);
-    if (K == 6) return res_kernel_k6(K, P, NM);
-    if (K <= 8) return res_kernel_k78(K, P, NM);
-    return res_kernel_k9(K, P, NM);
+    if (K <= 2) return res_kernel_k12(K, P, NM, LB, LF);
+    if (K == 3) return res_kernel_k3(K, P, NM, LB, LF);
+    if (K <= 5) return res_kernel_k45(K, P, NM, LB, LF);
+    if (K == 6) return res_kernel_k6(K, P, NM, LB, LF);
+    if (K <= 8) return res_kernel_k78(K, P, NM, LB, LF);
+    return res_kernel_k9(K, P, NM, LB, LF);
 }
 
 MultiKernel res_multi_kernel(int K, int P, int NM)
@@ -53,6 +53,10 @@ using res::HMAX;
 constexpr int TMAX = 64;              // longest tile side
 constexpr int SMEM_MAX = 227 * 1024;
 
+// Largest extended tile of the 384-thread form of the two-point kernel (up to
+// four channels; 170 registers a thread).
+constexpr int LIGHT384_POINTS = 768;
+
 // Estimated nanoseconds per iteration (see resident_plan).  Constants fitted to
 // GB300 measurements of this kernel at k = 3: 3.5 ns per point of the region a
 // step updates (arithmetic, shared-memory traffic and the two barriers of a
@@ -60,13 +64,20 @@ constexpr int SMEM_MAX = 227 * 1024;
 // the tagged stores and polls), and 30% more per point when a thread owns
 // four points (register spills).  With five and more channels (`heavy`, 384
 // threads) two points per thread already spill: 30% more there, 60% at four.
-double plan_cost(int TX, int TY, int H, int G, int rt = RES_THREADS, bool heavy = false)
+// With three or four channels (`k34`), two points per thread run in the
+// 384-thread form up to 768 points; beyond that, in 512-thread blocks at 128
+// registers, where their state spills and the steps measured 19% slower
+// (256^2, k = 3).  One and two channels fit 128 registers at two points and
+// take no such charge.  One point per thread stays the cheapest where it fits
+// (128^2, k = 3: 0.92 us per iteration at one point against 1.23 at two).
+double plan_cost(int TX, int TY, int H, int G, int rt = RES_THREADS, bool heavy = false, bool k34 = false)
 {
-    const double per_pt = 3.5;
     auto spill = [&](int ext) {
+        if (k34 && ext > LIGHT384_POINTS && ext <= 2 * rt) return 1.19;
         if (ext <= (heavy ? rt : 2 * rt)) return 1.0;
         return heavy && ext > 2 * rt ? 1.6 : 1.3;
     };
+    const double per_pt = 3.5;
     if (G == 1) return per_pt * TX * TY * spill(TX * TY);
     double pts = 0.0;
     for (int s = 1; s <= H; ++s) pts += (double)(TX + 2 * (H - s) + 1) * (TY + 2 * (H - s) + 1);
@@ -89,7 +100,7 @@ bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out)
         return res::smem_layout(k, res::row_stride(EW), EH, G).total <= SMEM_MAX;
     };
     const int RT = res::res_threads(k), max_points = 4 * RT;
-    const bool heavy = RT < RES_THREADS;
+    const bool heavy = RT < RES_THREADS, k34 = k >= 3 && k <= 4;
     double best = -1.0;
     for (int Gx = 1; Gx <= n && Gx <= max_blocks; ++Gx) {
         const int TX = (n + Gx - 1) / Gx, TXmin = n / Gx;
@@ -100,7 +111,7 @@ bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out)
             const int G = Gx * Gy;
             if (G == 1) {
                 if (TX * TY > max_points || !smem_ok(TX, TY, 1)) continue;
-                const double cost = plan_cost(TX, TY, 0, 1, RT, heavy);
+                const double cost = plan_cost(TX, TY, 0, 1, RT, heavy, k34);
                 if (best < 0 || cost < best) {
                     best = cost;
                     *out = ResidentPlan{Gx, Gy, TX, TY, 0, 0, 0, cost};
@@ -112,7 +123,7 @@ bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out)
                 if (H > TXmin || H > TYmin) break;
                 const int EW = TX + 2 * H, EH = TY + 2 * H;
                 if (EW * EH > max_points || !smem_ok(EW, EH, G)) break;
-                const double cost = plan_cost(TX, TY, H, G, RT, heavy);
+                const double cost = plan_cost(TX, TY, H, G, RT, heavy, k34);
                 if (best < 0 || cost < best) {
                     best = cost;
                     *out = ResidentPlan{Gx, Gy, TX, TY, H, 0, 0, cost};
@@ -123,10 +134,12 @@ bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out)
     if (best < 0) return false;
     const int EW = out->TXm + 2 * out->H, EH = out->TYm + 2 * out->H;
     // P points per thread, the fewest that fit RT threads, spread evenly over
-    // round_up(ext / P, 32) threads.
+    // round_up(ext / P, 32) threads; two points on at most 384 threads take the
+    // 384-thread form (up to four channels)
     const int ext = EW * EH;
     out->P = ext <= RT ? 1 : (ext <= 2 * RT ? 2 : 4);
     out->threads = (((ext + out->P - 1) / out->P + 31) / 32) * 32;
+    out->lb = (k <= 4 && out->P == 2 && ext <= LIGHT384_POINTS) ? 384 : RT;
     return true;
 }
 
@@ -242,7 +255,9 @@ int resident_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveC
     if (p.u_norm == VOMT_U_L12 && p.w_norm == VOMT_W_L1) nm = 1;
     else if (p.u_norm == VOMT_U_L2 && p.w_norm == VOMT_W_L1 && (K == 3 || K == 6)) nm = 2;
     else if (p.u_norm == VOMT_U_NUC && p.w_norm == VOMT_W_NUC && K == 6) nm = 3;
-    res::ResKernel kern = res::res_kernel(K, plan.P, nm);
+    // 3 x 3 matrices with three L matrices: the flux count fixed at compile time
+    const int lf = (K == 6 && g.l == 9 && (nm == 2 || nm == 3)) ? 9 : 0;
+    res::ResKernel kern = res::res_kernel(K, plan.P, nm, plan.lb > 0 ? plan.lb : res::res_threads(K), lf);
     if (!kern) {
         ctx->err = "no resident kernel for this channel count and norm pair";
         return VOMT_ERR_TOO_LARGE;
