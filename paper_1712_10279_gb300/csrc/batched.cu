@@ -613,7 +613,7 @@ static bool grouped_plan(vomt_ctx *ctx, int count, const std::vector<InstDev> &h
         w.groups = std::min((int)w.insts.size(), ctx->sm_count / T);
         w.per = ((int)w.insts.size() + w.groups - 1) / w.groups;
         const int nm = (p.u_norm == VOMT_U_L12 && p.w_norm == VOMT_W_L1) ? 1 : 0;
-        if (!res::res_multi_kernel(w.k, w.plan.P, nm)) return false;
+        if (!res::res_multi_kernel(w.k, w.plan.P, nm, w.plan.lb)) return false;
     }
     return true;
 }
@@ -734,9 +734,14 @@ static int grouped_solve(vomt_ctx *ctx, BatchState *b, int count, const std::vec
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->gvalid, valid.data(), sizeof(int) * jobs_total, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "grouped setup");
     // launch shape of every wave (attributes and occupancy are set outside any capture)
+    // A wave whose problems each take every tile of the GPU (one group) runs them one after
+    // the other as launches of the single-problem kernel, whose arguments sit in the constant
+    // bank (the grouped kernel reads each problem's operator from shared memory).
     struct WaveLaunch {
         res::MultiKernel kern;
-        int blocks, threads, smem;
+        res::ResKernel single;
+        int blocks, threads, smem, jobs;
+        size_t job0;
         size_t reset_bytes;
         res::MultiArgs m;
     };
@@ -748,7 +753,7 @@ static int grouped_solve(vomt_ctx *ctx, BatchState *b, int count, const std::vec
         const ResidentPlan &pl = w.plan;
         const int EWm = pl.TXm + 2 * pl.H, EHm = pl.TYm + 2 * pl.H;
         const int smem = res::smem_layout(w.k, res::row_stride(EWm), EHm, pl.Gx * pl.Gy).total;
-        res::MultiKernel kern = res::res_multi_kernel(w.k, pl.P, nm);
+        res::MultiKernel kern = res::res_multi_kernel(w.k, pl.P, nm, pl.lb);
         bool found = false;
         for (auto &lim : limits)
             if (lim.first == kern) { lim.second = std::max(lim.second, smem); found = true; }
@@ -758,13 +763,30 @@ static int grouped_solve(vomt_ctx *ctx, BatchState *b, int count, const std::vec
         e = cudaFuncSetAttribute((const void *)lim.first, cudaFuncAttributeMaxDynamicSharedMemorySize, lim.second);
         if (e != cudaSuccess) return set_cuda_error(ctx, e, "grouped smem attribute");
     }
+    std::vector<std::pair<res::ResKernel, int>> single_limits;
+    for (const Wave &w : waves) {
+        if (w.groups != 1) continue;
+        const ResidentPlan &pl = w.plan;
+        const int EWm = pl.TXm + 2 * pl.H, EHm = pl.TYm + 2 * pl.H;
+        const int smem = res::smem_layout(w.k, res::row_stride(EWm), EHm, pl.Gx * pl.Gy).total;
+        res::ResKernel kern = res::res_kernel(w.k, pl.P, nm, pl.lb > 0 ? pl.lb : res::res_threads(w.k), 0);
+        if (!kern) continue;
+        bool found = false;
+        for (auto &lim : single_limits)
+            if (lim.first == kern) { lim.second = std::max(lim.second, smem); found = true; }
+        if (!found) single_limits.push_back({kern, smem});
+    }
+    for (const auto &lim : single_limits) {
+        e = cudaFuncSetAttribute((const void *)lim.first, cudaFuncAttributeMaxDynamicSharedMemorySize, lim.second);
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "grouped smem attribute");
+    }
     for (size_t wi = 0; wi < waves.size(); ++wi) {
         const Wave &w = waves[wi];
         const ResidentPlan &pl = w.plan;
         const int T = pl.Gx * pl.Gy;
         const int EWm = pl.TXm + 2 * pl.H, EHm = pl.TYm + 2 * pl.H;
         const res::SmemLayout SL = res::smem_layout(w.k, res::row_stride(EWm), EHm, T);
-        res::MultiKernel kern = res::res_multi_kernel(w.k, pl.P, nm);
+        res::MultiKernel kern = res::res_multi_kernel(w.k, pl.P, nm, pl.lb);
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)kern, pl.threads, SL.total);
         if (e != cudaSuccess) return set_cuda_error(ctx, e, "grouped occupancy");
@@ -775,9 +797,21 @@ static int grouped_solve(vomt_ctx *ctx, BatchState *b, int count, const std::vec
         }
         WaveLaunch &L = wl[wi];
         L.kern = kern;
+        L.single = nullptr;
         L.blocks = blocks;
         L.threads = pl.threads;
         L.smem = SL.total;
+        L.jobs = (int)w.insts.size();
+        L.job0 = wave_job0[wi];
+        if (w.groups == 1) {
+            res::ResKernel sk = res::res_kernel(w.k, pl.P, nm, pl.lb > 0 ? pl.lb : res::res_threads(w.k), 0);
+            int per_sm1 = 0;
+            if (sk && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, (const void *)sk, pl.threads, SL.total) ==
+                          cudaSuccess &&
+                per_sm1 >= 1 && blocks <= per_sm1 * ctx->sm_count)
+                L.single = sk;
+            (void)cudaGetLastError();
+        }
         // exchange words of an earlier wave must not match this wave's tags
         L.reset_bytes = (size_t)w.groups * 2 *
                         ((size_t)T * 2 * ((3 * w.k + w.k * (w.k - 1) / 2 + 1) / 2) * pl.TXm * pl.TYm * 2 +
@@ -796,13 +830,23 @@ static int grouped_solve(vomt_ctx *ctx, BatchState *b, int count, const std::vec
             WaveLaunch &L = wl[wi];
             r = cudaMemsetAsync(b->gscratch, 0, L.reset_bytes, q);
             if (r != cudaSuccess) break;
+            if (L.single) {
+                // one problem at a time on every tile; consecutive problems alternate exchange
+                // slots and carry their own tag prefixes, as in the grouped kernel
+                for (int j = 0; j < L.jobs && r == cudaSuccess; ++j) {
+                    void *args[] = {&jobs[L.job0 + (size_t)j]};
+                    r = cudaLaunchCooperativeKernel((const void *)L.single, dim3(L.blocks), dim3(L.threads), args,
+                                                    L.smem, q);
+                }
+                continue;
+            }
             void *args[] = {&L.m};
             r = cudaLaunchCooperativeKernel((const void *)L.kern, dim3(L.blocks), dim3(L.threads), args, L.smem, q);
         }
         if (r == cudaSuccess) r = cudaMemcpyAsync(b->hgstat, dstat, sizeof(DevStatus) * count, cudaMemcpyDeviceToHost, q);
         return r;
     };
-    ctx->launches += (int)wl.size();
+    for (const WaveLaunch &L : wl) ctx->launches += L.single ? L.jobs : 1;
     // One CUDA graph holds every wave's launch; it is replayed on `st` while the job tables
     // and the launch shapes repeat (the tables are uploaded before each replay).  Capture
     // runs on `st`, or on the context's private stream when `st` is the legacy stream.

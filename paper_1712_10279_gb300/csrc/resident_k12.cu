@@ -12,10 +12,10 @@ ResKernel res_kernel_k12(int K, int P, int NM, int LB, int LF)
     return nullptr;
 }
 
-MultiKernel res_multi_kernel_k12(int K, int P, int NM)
+MultiKernel res_multi_kernel_k12(int K, int P, int NM, int LB)
 {
-    if (K == 1) return multi_kernel_for<1>(P, NM);
-    if (K == 2) return multi_kernel_for<2>(P, NM);
+    if (K == 1) return multi_kernel_for<1>(P, NM, LB);
+    if (K == 2) return multi_kernel_for<2>(P, NM, LB);
     return nullptr;
 }
 

@@ -11,9 +11,9 @@ ResKernel res_kernel_k3(int K, int P, int NM, int LB, int LF)
     return nullptr;
 }
 
-MultiKernel res_multi_kernel_k3(int K, int P, int NM)
+MultiKernel res_multi_kernel_k3(int K, int P, int NM, int LB)
 {
-    if (K == 3) return multi_kernel_for<3>(P, NM);
+    if (K == 3) return multi_kernel_for<3>(P, NM, LB);
     return nullptr;
 }
 

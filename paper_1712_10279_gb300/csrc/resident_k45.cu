@@ -12,10 +12,10 @@ ResKernel res_kernel_k45(int K, int P, int NM, int LB, int LF)
     return nullptr;
 }
 
-MultiKernel res_multi_kernel_k45(int K, int P, int NM)
+MultiKernel res_multi_kernel_k45(int K, int P, int NM, int LB)
 {
-    if (K == 4) return multi_kernel_for<4>(P, NM);
-    if (K == 5) return multi_kernel_for<5>(P, NM);
+    if (K == 4) return multi_kernel_for<4>(P, NM, LB);
+    if (K == 5) return multi_kernel_for<5>(P, NM, LB);
     return nullptr;
 }
 

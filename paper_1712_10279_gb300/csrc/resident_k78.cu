@@ -12,10 +12,10 @@ ResKernel res_kernel_k78(int K, int P, int NM, int LB, int LF)
     return nullptr;
 }
 
-MultiKernel res_multi_kernel_k78(int K, int P, int NM)
+MultiKernel res_multi_kernel_k78(int K, int P, int NM, int LB)
 {
-    if (K == 7) return multi_kernel_for<7>(P, NM);
-    if (K == 8) return multi_kernel_for<8>(P, NM);
+    if (K == 7) return multi_kernel_for<7>(P, NM, LB);
+    if (K == 8) return multi_kernel_for<8>(P, NM, LB);
     return nullptr;
 }
 

@@ -1002,7 +1002,8 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
     if (!saved) write_out();
 }
 
-// One problem: the grid is its tiles.
+// One problem: the grid is its tiles.  Its tags carry the prefix a.tag_hi (0 for
+// a lone solve; the grouped batch gives each problem its own).
 // LB: the launch bound (most threads of a block).  A block of 384 threads (12
 // warps, three per SM sub-partition) lets a thread hold 170 registers, 512 only
 // 128 (four warps on some sub-partition): two points per thread need about 170
@@ -1011,7 +1012,7 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
 template <int K, int P, int NM, int LB = res_threads(K), int LF = 0>
 __global__ void __launch_bounds__(LB, 1) k_resident(const __grid_constant__ ResArgs a)
 {
-    resident_body<K, P, NM, LF>(a, (int)blockIdx.x, (int)gridDim.x, 0u);
+    resident_body<K, P, NM, LF>(a, (int)blockIdx.x, (int)gridDim.x, a.tag_hi);
 }
 
 // Many problems of one shape (grouped batch): the grid is `groups` groups of T
@@ -1027,8 +1028,8 @@ struct MultiArgs {
     ResCtl *ctl;
 };
 
-template <int K, int P, int NM>
-__global__ void __launch_bounds__(res_threads(K), 1) k_resident_multi(const __grid_constant__ MultiArgs m)
+template <int K, int P, int NM, int LB = res_threads(K)>
+__global__ void __launch_bounds__(LB, 1) k_resident_multi(const __grid_constant__ MultiArgs m)
 {
     __shared__ __align__(16) ResArgs sa;
     const int g = (int)blockIdx.x / m.T, t = (int)blockIdx.x % m.T;
@@ -1082,12 +1083,16 @@ ResKernel kernel_for(int P, int NM, int LB, int LF)
 }
 
 // Grouped-batch kernel for K <= 5 channels, P in {2, 4} (and P = 1 for five
-// channels, whose per-point state spills at two points per thread), NM in {0, 1};
-// nullptr otherwise.
+// channels, whose per-point state spills at two points per thread), NM in {0, 1},
+// and the 384-thread form of P = 2 (LB = 384) for up to four channels; nullptr
+// otherwise.
 template <int K>
-MultiKernel multi_kernel_for(int P, int NM)
+MultiKernel multi_kernel_for(int P, int NM, int LB)
 {
     if constexpr (K <= 5) {
+        if constexpr (K <= 4) {
+            if (P == 2 && LB == 384) return NM == 1 ? k_resident_multi<K, 2, 1, 384> : k_resident_multi<K, 2, 0, 384>;
+        }
         if constexpr (K == 5) {
             if (P == 1) return NM == 1 ? k_resident_multi<K, 1, 1> : k_resident_multi<K, 1, 0>;
         }
@@ -1096,12 +1101,13 @@ MultiKernel multi_kernel_for(int P, int NM)
     } else {
         (void)P;
         (void)NM;
+        (void)LB;
         return nullptr;
     }
 }
 
 ResKernel res_kernel(int K, int P, int NM, int LB, int LF);
-MultiKernel res_multi_kernel(int K, int P, int NM);
+MultiKernel res_multi_kernel(int K, int P, int NM, int LB);
 
 // Shared memory of the grouped kernel beyond the dynamic layout (the job copy).
 constexpr int MULTI_STATIC_SMEM = (int)((sizeof(ResArgs) + 15) / 16 * 16);

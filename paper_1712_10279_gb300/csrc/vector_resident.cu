@@ -18,11 +18,11 @@ ResKernel res_kernel_k45(int K, int P, int NM, int LB, int LF);
 ResKernel res_kernel_k6(int K, int P, int NM, int LB, int LF);
 ResKernel res_kernel_k78(int K, int P, int NM, int LB, int LF);
 ResKernel res_kernel_k9(int K, int P, int NM, int LB, int LF);
-MultiKernel res_multi_kernel_k12(int K, int P, int NM);
-MultiKernel res_multi_kernel_k3(int K, int P, int NM);
-MultiKernel res_multi_kernel_k45(int K, int P, int NM);
-MultiKernel res_multi_kernel_k6(int K, int P, int NM);
-MultiKernel res_multi_kernel_k78(int K, int P, int NM);
+MultiKernel res_multi_kernel_k12(int K, int P, int NM, int LB);
+MultiKernel res_multi_kernel_k3(int K, int P, int NM, int LB);
+MultiKernel res_multi_kernel_k45(int K, int P, int NM, int LB);
+MultiKernel res_multi_kernel_k6(int K, int P, int NM, int LB);
+MultiKernel res_multi_kernel_k78(int K, int P, int NM, int LB);
 
 ResKernel res_kernel(int K, int P, int NM, int LB, int LF)
 {
@@ -34,13 +34,13 @@ ResKernel res_kernel(int K, int P, int NM, int LB, int LF)
     return res_kernel_k9(K, P, NM, LB, LF);
 }
 
-MultiKernel res_multi_kernel(int K, int P, int NM)
+MultiKernel res_multi_kernel(int K, int P, int NM, int LB)
 {
-    if (K <= 2) return res_multi_kernel_k12(K, P, NM);
-    if (K == 3) return res_multi_kernel_k3(K, P, NM);
-    if (K <= 5) return res_multi_kernel_k45(K, P, NM);
-    if (K == 6) return res_multi_kernel_k6(K, P, NM);
-    if (K <= 8) return res_multi_kernel_k78(K, P, NM);
+    if (K <= 2) return res_multi_kernel_k12(K, P, NM, LB);
+    if (K == 3) return res_multi_kernel_k3(K, P, NM, LB);
+    if (K <= 5) return res_multi_kernel_k45(K, P, NM, LB);
+    if (K == 6) return res_multi_kernel_k6(K, P, NM, LB);
+    if (K <= 8) return res_multi_kernel_k78(K, P, NM, LB);
     return nullptr;
 }
 
@@ -67,13 +67,15 @@ constexpr int LIGHT384_POINTS = 768;
 // With three or four channels (`k34`), two points per thread run in the
 // 384-thread form up to 768 points; beyond that, in 512-thread blocks at 128
 // registers, where their state spills and the steps measured 19% slower
-// (256^2, k = 3).  One and two channels fit 128 registers at two points and
+// (256^2, k = 3); four points per thread spill more and measured 39% slower
+// again (1.65 in all).  One and two channels fit 128 registers at two points and
 // take no such charge.  One point per thread stays the cheapest where it fits
 // (128^2, k = 3: 0.92 us per iteration at one point against 1.23 at two).
 double plan_cost(int TX, int TY, int H, int G, int rt = RES_THREADS, bool heavy = false, bool k34 = false)
 {
     auto spill = [&](int ext) {
         if (k34 && ext > LIGHT384_POINTS && ext <= 2 * rt) return 1.19;
+        if (k34 && ext > 2 * rt) return 1.65;
         if (ext <= (heavy ? rt : 2 * rt)) return 1.0;
         return heavy && ext > 2 * rt ? 1.6 : 1.3;
     };
@@ -147,15 +149,16 @@ bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out)
 // grouped batch): each problem gets T = Gx x Gy tiles, floor(max_blocks / T)
 // problems run side by side, and the plan minimises the estimated time of the
 // whole wave (rounds of side-by-side problems x time per iteration of one).
-// Same tile rules as resident_plan; P is 2 or 4 (the grouped kernels), or 1 for
-// five channels when the extended tile fits one point per thread.
+// Same tile rules as resident_plan; P is 2 or 4 (the grouped kernels; two points
+// in 384-thread blocks up to 768 points at up to four channels), or 1 for five
+// channels when the extended tile fits one point per thread.
 bool resident_plan_wave(int n, int k, int count, int max_blocks, ResidentPlan *out)
 {
     auto smem_ok = [&](int EW, int EH, int G) {
         return res::smem_layout(k, res::row_stride(EW), EH, G).total <= SMEM_MAX - res::MULTI_STATIC_SMEM;
     };
     const int RT = res::res_threads(k), max_points = 4 * RT;
-    const bool heavy = res::res_threads(k) < RES_THREADS;
+    const bool heavy = res::res_threads(k) < RES_THREADS, k34 = k >= 3 && k <= 4;
     double best = -1.0;
     for (int Gx = 1; Gx <= n && Gx <= max_blocks; ++Gx) {
         const int TX = (n + Gx - 1) / Gx, TXmin = n / Gx;
@@ -168,7 +171,7 @@ bool resident_plan_wave(int n, int k, int count, int max_blocks, ResidentPlan *o
             const double rounds = (double)((count + side - 1) / side);
             if (G == 1) {
                 if (TX * TY > max_points || !smem_ok(TX, TY, 1)) continue;
-                const double cost = rounds * plan_cost(TX, TY, 0, 1, RT, heavy);
+                const double cost = rounds * plan_cost(TX, TY, 0, 1, RT, heavy, k34);
                 if (best < 0 || cost < best) {
                     best = cost;
                     *out = ResidentPlan{Gx, Gy, TX, TY, 0, 0, 0, cost};
@@ -179,7 +182,7 @@ bool resident_plan_wave(int n, int k, int count, int max_blocks, ResidentPlan *o
                 if (H > TXmin || H > TYmin) break;
                 const int EW = TX + 2 * H, EH = TY + 2 * H;
                 if (EW * EH > max_points || !smem_ok(EW, EH, G)) break;
-                const double cost = rounds * plan_cost(TX, TY, H, G, RT, heavy);
+                const double cost = rounds * plan_cost(TX, TY, H, G, RT, heavy, k34);
                 if (best < 0 || cost < best) {
                     best = cost;
                     *out = ResidentPlan{Gx, Gy, TX, TY, H, 0, 0, cost};
@@ -191,6 +194,7 @@ bool resident_plan_wave(int n, int k, int count, int max_blocks, ResidentPlan *o
     const int ext = (out->TXm + 2 * out->H) * (out->TYm + 2 * out->H);
     out->P = (k >= 5 && ext <= RT) ? 1 : (ext <= 2 * RT ? 2 : 4);
     out->threads = (((ext + out->P - 1) / out->P + 31) / 32) * 32;
+    out->lb = (k <= 4 && out->P == 2 && ext <= LIGHT384_POINTS) ? 384 : RT;
     return true;
 }
 
