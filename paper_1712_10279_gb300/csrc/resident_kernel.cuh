@@ -107,6 +107,7 @@ struct SmemLayout {
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
+__host__ __device__ inline int align128(int x) { return (x + 127) & ~127; }
 
 __host__ __device__ inline SmemLayout smem_layout(int K, int EWs, int EHm, int G)
 {
@@ -118,17 +119,33 @@ __host__ __device__ inline SmemLayout smem_layout(int K, int EWs, int EHm, int G
     L.dec = o; o += 16;
     L.rtab = o; o += align16(G * NRED * 8);
     L.cnt = o; o += align16(2 * (HMAX + 2) * 4);
-    L.sphi = o; o += align16(plane);
-    L.sux = o; o += align16(plane);
-    L.suy = o; o += align16(plane);
-    L.sdx = o; o += align16(plane);
-    L.sdy = o; o += align16(plane);
-    L.sdg = o; o += align16(plane);
+    o = align128(o);           // the point arrays start on 128-byte boundaries (half_swap)
+    L.sphi = o; o += align128(plane);
+    L.sux = o; o += align128(plane);
+    L.suy = o; o += align128(plane);
+    L.sdx = o; o += align128(plane);
+    L.sdy = o; o += align128(plane);
+    L.sdg = o; o += align128(plane);
     L.total = o;
     return L;
 }
 
 // ---------------------------------------------------------------- small helpers
+// A point's record of 8 floats (5 to 8 channels) holds two 16-byte halves.  Eight
+// lanes of a warp reading the same half of eight consecutive records would touch
+// every bank group twice; so the halves are swapped in every other group of four
+// records (bit 2 of the record index, bit 7 of the shared-memory byte address with
+// 128-byte aligned arrays), which spreads any eight consecutive records over all
+// eight bank groups.
+template <int KV>
+__device__ __forceinline__ int half_swap(const float *p)
+{
+    if constexpr (KV == 8)
+        return (int)((__cvta_generic_to_shared(p) >> 5) & 4u);   // 4 floats where the halves swap
+    else
+        return 0;
+}
+
 // K channel values of one point from / to a shared-memory array (vector accesses)
 template <int K>
 __device__ __forceinline__ void lds(const float *p, float (&v)[K])
@@ -142,9 +159,10 @@ __device__ __forceinline__ void lds(const float *p, float (&v)[K])
         t[0] = a.x;
         t[1] = a.y;
     } else {
+        const int sw = half_swap<KV>(p);
 #pragma unroll
         for (int j = 0; j < KV / 4; ++j) {
-            const float4 a = *reinterpret_cast<const float4 *>(p + 4 * j);
+            const float4 a = *reinterpret_cast<const float4 *>(p + ((4 * j) ^ sw));
             t[4 * j] = a.x;
             t[4 * j + 1] = a.y;
             t[4 * j + 2] = a.z;
@@ -169,9 +187,11 @@ __device__ __forceinline__ void sts(float *p, const float (&v)[K])
     } else if constexpr (KV == 2) {
         *reinterpret_cast<float2 *>(p) = make_float2(t[0], t[1]);
     } else {
+        const int sw = half_swap<KV>(p);
 #pragma unroll
         for (int j = 0; j < KV / 4; ++j)
-            *reinterpret_cast<float4 *>(p + 4 * j) = make_float4(t[4 * j], t[4 * j + 1], t[4 * j + 2], t[4 * j + 3]);
+            *reinterpret_cast<float4 *>(p + ((4 * j) ^ sw)) =
+                make_float4(t[4 * j], t[4 * j + 1], t[4 * j + 2], t[4 * j + 3]);
     }
 }
 
@@ -317,7 +337,7 @@ __device__ __forceinline__ void resident_body(const ResArgs &a, const int tile, 
     constexpr int FMAX = 3 * K + LKv;
     constexpr int F2MAX = (FMAX + 1) / 2;
     constexpr int KV = kv_of(K);
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const ResGeom G = a.geo;
     const int n = G.n, H = G.H, R = G.R;
     const size_t nn = (size_t)n * n;
@@ -1110,7 +1130,7 @@ ResKernel res_kernel(int K, int P, int NM, int LB, int LF);
 MultiKernel res_multi_kernel(int K, int P, int NM, int LB);
 
 // Shared memory of the grouped kernel beyond the dynamic layout (the job copy).
-constexpr int MULTI_STATIC_SMEM = (int)((sizeof(ResArgs) + 15) / 16 * 16);
+constexpr int MULTI_STATIC_SMEM = (int)((sizeof(ResArgs) + 127) / 128 * 128);
 
 }  // namespace res
 }  // namespace vomt
