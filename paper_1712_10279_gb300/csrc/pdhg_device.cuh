@@ -11,16 +11,21 @@
 namespace vomt {
 namespace dev {
 
-// factor of shrink_2 (Appendix B): 1 - t/s for s = sqrt(s2) > t, else 0
+// factor of shrink_2 (Appendix B): 1 - t/s for s = sqrt(s2) > t, else 0, as
+// max(1 - t / s, 0): the factor is positive exactly when s > t, and at s2 = 0 the
+// reciprocal square root is +inf, so 1 - t/s is -inf (or NaN for t = 0, which
+// fmaxf also maps to 0)
 __device__ __forceinline__ float shrink2_factor(float s2, float t)
 {
-    return (s2 > t * t) ? (1.0f - t * rsqrtf(s2)) : 0.0f;
+    return fmaxf(1.0f - t * rsqrtf(s2), 0.0f);
 }
 
-// shrink_1 (Appendix B): soft threshold
+// shrink_1 (Appendix B): soft threshold sign(x) max(|x| - t, 0), as x minus x
+// clamped to [-t, t] (the same single rounding of x -+ t where |x| > t, exactly 0
+// elsewhere)
 __device__ __forceinline__ float soft(float x, float t)
 {
-    return (fabsf(x) > t) ? (x - copysignf(t, x)) : 0.0f;
+    return x - fminf(fmaxf(x, -t), t);
 }
 
 template <int K>

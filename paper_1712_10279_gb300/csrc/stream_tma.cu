@@ -25,6 +25,7 @@
 
 #include "internal.h"
 #include "matrix_norms.cuh"
+#include "pdhg_device.cuh"
 #include "stream_tma.h"
 
 namespace vomt {
@@ -54,15 +55,9 @@ __host__ __device__ inline TmaSmem tma_smem(int K, int l)
     return S;
 }
 
-__device__ __forceinline__ float shrink2_factor(float s2, float t)
-{
-    return (s2 > t * t) ? (1.0f - t * rsqrtf(s2)) : 0.0f;
-}
-
-__device__ __forceinline__ float soft(float x, float t)
-{
-    return (fabsf(x) > t) ? (x - copysignf(t, x)) : 0.0f;
-}
+// shrink_2 factor and soft threshold of Appendix B (pdhg_device.cuh)
+using dev::shrink2_factor;
+using dev::soft;
 
 template <int K, int UN>
 __device__ __forceinline__ void shrink_u(float (&vx)[K], float (&vy)[K], float t, const float *wc)

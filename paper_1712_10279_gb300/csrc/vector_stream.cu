@@ -11,6 +11,7 @@
 
 #include "internal.h"
 #include "matrix_norms.cuh"
+#include "pdhg_device.cuh"
 #include "stream_tma.h"
 
 namespace vomt {
@@ -25,17 +26,9 @@ struct StateOut {
     float *phi, *ux, *uy, *w;
 };
 
-// factor of shrink_2 (Appendix B): 1 - t/s for s = sqrt(s2) > t, else 0
-__device__ __forceinline__ float shrink2_factor(float s2, float t)
-{
-    return (s2 > t * t) ? (1.0f - t * rsqrtf(s2)) : 0.0f;
-}
-
-// shrink_1 (Appendix B): soft threshold
-__device__ __forceinline__ float soft(float x, float t)
-{
-    return (fabsf(x) > t) ? (x - copysignf(t, x)) : 0.0f;
-}
+// shrink_2 factor and soft threshold of Appendix B (pdhg_device.cuh)
+using dev::shrink2_factor;
+using dev::soft;
 
 template <int K>
 __device__ __forceinline__ float pick(const float (&a)[K], int idx)
