@@ -65,16 +65,17 @@ constexpr int LIGHT384_POINTS = 768;
 // four points (register spills).  With five and more channels (`heavy`, 384
 // threads) two points per thread already spill: 30% more there, 60% at four.
 // With three or four channels (`k34`), two points per thread run in the
-// 384-thread form up to 768 points; beyond that, in 512-thread blocks at 128
-// registers, where their state spills and the steps measured 19% slower
-// (256^2, k = 3); four points per thread spill more and measured 39% slower
-// again (1.65 in all).  One and two channels fit 128 registers at two points and
-// take no such charge.  One point per thread stays the cheapest where it fits
-// (128^2, k = 3: 0.92 us per iteration at one point against 1.23 at two).
+// 384-thread form up to 768 points and in 512-thread blocks at 128 registers
+// beyond (at 256^2, k = 3 the two cost the same per iteration: H = 3 in the
+// 384-thread form, 31.9 ms per 20,000 iterations, against H = 4 in the 512-thread
+// form, 31.6 ms); four points per thread spill: 20,000 iterations at 256^2 took
+// 45.7 ms against 33.0 at two (H = 4, 128 registers), the steps about 60% longer,
+// so their steps are charged 65% more.  One point per thread stays
+// the cheapest where it fits (128^2, k = 3: 0.92 us per iteration at one point
+// against 1.23 at two).
 double plan_cost(int TX, int TY, int H, int G, int rt = RES_THREADS, bool heavy = false, bool k34 = false)
 {
     auto spill = [&](int ext) {
-        if (k34 && ext > LIGHT384_POINTS && ext <= 2 * rt) return 1.19;
         if (k34 && ext > 2 * rt) return 1.65;
         if (ext <= (heavy ? rt : 2 * rt)) return 1.0;
         return heavy && ext > 2 * rt ? 1.6 : 1.3;
