@@ -236,9 +236,15 @@ struct ResidentPlan {
     double est_ns;      // estimated ns per iteration (a wave plan: of the whole wave, all its rounds)
     int lb;             // launch bound of the single-problem kernel (0: res_threads(k))
 };
+// Blocks of a streaming check (k_metrics, k_metrics3): the check's kernel loops
+// over the grid with at most this many blocks (four per SM on a GB300), which
+// bounds the FP64 rows k_finalize sums.
+constexpr int kMetricBlocks = 608;
 // Fixed-order sum of per-block FP64 partials (NRED per block), the stopping
-// decision and the history row (one block of 256 threads; vector_stream.cu).
-// t < 0: the iteration is the last check's plus -t (replayed graphs).
+// decision and the history row (one block of kFinThreads threads, one warp per
+// slot; vector_stream.cu).  t < 0: the iteration is the last check's plus -t
+// (replayed graphs).
+constexpr int kFinThreads = 32 * NRED;
 __global__ void k_finalize(const double *__restrict__ partials, int nblocks, SolveCfg cfg, int t, DevStatus *st,
                            double *hist, int hist_cap);
 

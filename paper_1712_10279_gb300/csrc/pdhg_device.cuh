@@ -143,6 +143,85 @@ __device__ __forceinline__ void shrink_w(float (&x)[LK], int l, float t, int wn,
     }
 }
 
+// ---------------------------------------------------------------- check sums
+// Error-free sum (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ float two_sum(float a, float b, float &e)
+{
+    const float s = a + b;
+    const float bv = s - a;
+    e = (a - (s - bv)) + (b - bv);
+    return s;
+}
+
+// One thread's share of a convergence check: each sum slot is a pair of FP32
+// numbers (hi, lo) that TwoSum keeps equal to the exact running sum up to the
+// rounding of lo (about twice FP32 precision); the maximum slot is a plain FP32
+// maximum (exact).  FP64 arithmetic runs at a small fraction of the FP32 rate on
+// this GPU, so FP64 is kept for the sums across warps and blocks.
+struct CheckAcc {
+    float hi[NRED], lo[NRED];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int q = 0; q < NRED; ++q) hi[q] = lo[q] = 0.0f;
+    }
+    __device__ __forceinline__ void add(int q, float x)
+    {
+        float e;
+        hi[q] = two_sum(hi[q], x, e);
+        lo[q] += e;
+    }
+    // an FP64 term: its FP32 head through TwoSum, the remainder into lo
+    __device__ __forceinline__ void add_d(int q, double x)
+    {
+        const float h = __double2float_rn(x);
+        add(q, h);
+        lo[q] += __double2float_rn(x - (double)h);
+    }
+    __device__ __forceinline__ void max(int q, float x) { hi[q] = fmaxf(hi[q], x); }
+};
+
+// The block's FP64 row of a check (NRED slots) from every thread's CheckAcc: warp
+// sums of the (hi, lo) pairs in FP32 with TwoSum (fixed order), then the warps'
+// pairs summed in FP64 by one thread per slot, in warp order.  NTH threads per
+// block, numbered x fastest; every thread must call it.
+template <int NTH>
+__device__ __forceinline__ void block_sum_store(CheckAcc &a, double *dst)
+{
+    constexpr int NW = NTH / 32;
+    __shared__ float sh[NW][NRED][2];
+    const int tid = (int)(threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z));
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int q = 0; q < NRED; ++q) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float oh = __shfl_down_sync(0xffffffffu, a.hi[q], off);
+            const float ol = __shfl_down_sync(0xffffffffu, a.lo[q], off);
+            if (q == RED_MAX) {
+                a.hi[q] = fmaxf(a.hi[q], oh);
+            } else {
+                float e;
+                a.hi[q] = two_sum(a.hi[q], oh, e);
+                a.lo[q] = a.lo[q] + (ol + e);
+            }
+        }
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NRED; ++q) {
+            sh[wid][q][0] = a.hi[q];
+            sh[wid][q][1] = a.lo[q];
+        }
+    __syncthreads();
+    if (tid < NRED) {
+        double s = 0.0;
+        for (int w = 0; w < NW; ++w)
+            s = (tid == RED_MAX) ? fmax(s, (double)sh[w][tid][0]) : s + ((double)sh[w][tid][0] + (double)sh[w][tid][1]);
+        dst[tid] = s;
+    }
+}
+
 // ---------------------------------------------------------------- exchange words
 // A 64-bit word carries one FP32 value in its low half and a 32-bit tag (the
 // iteration it belongs to, plus one) in its high half.  Aligned 64-bit stores

@@ -195,15 +195,6 @@ __device__ __forceinline__ void sts(float *p, const float (&v)[K])
     }
 }
 
-// Error-free sum (Knuth's TwoSum): s + e == a + b exactly.
-__device__ __forceinline__ float two_sum(float a, float b, float &e)
-{
-    const float s = a + b;
-    const float bv = s - a;
-    e = (a - (s - bv)) + (b - bv);
-    return s;
-}
-
 // ih * ((ux - xl) + (uy - yd)) + gb with the rounding errors of the
 // differences, their sum, the product and the final sum carried along (the
 // compensated evaluation of Ogita, Rump and Oishi, "Accurate sum and dot

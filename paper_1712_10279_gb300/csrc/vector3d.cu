@@ -238,7 +238,9 @@ __global__ void __launch_bounds__(MT, K <= 4 ? 2 : 1) k_step3m(S3In in, S3Out ou
 }
 
 // FP64 block partials of one convergence check (slots RED_*): per-point terms in
-// FP32 (the constraint residual in FP64), summed per block in FP64.
+// FP32 (the constraint residual in FP64), summed per thread and warp in pairs of
+// FP32 numbers with TwoSum and per block in FP64 (CheckAcc, block_sum_store).
+// At most kMetricBlocks blocks loop over the volume's points.
 template <int K, int UN, int WN>
 __global__ void __launch_bounds__(T3) k_metrics3(S3In cur, S3In prv, const float *__restrict__ b, OpDev g,
                                                  StepDev s, double *__restrict__ partials,
@@ -248,11 +250,9 @@ __global__ void __launch_bounds__(T3) k_metrics3(S3In cur, S3In prv, const float
     constexpr int LK = LK3<K>::v;
     const int n = s.n;
     const size_t m = (size_t)n * n * n;
-    const size_t p = (size_t)blockIdx.x * T3 + threadIdx.x;
-    double v[NRED];
-#pragma unroll
-    for (int q = 0; q < NRED; ++q) v[q] = 0.0;
-    if (p < m) {
+    CheckAcc acc;
+    acc.zero();
+    for (size_t p = (size_t)blockIdx.x * T3 + threadIdx.x; p < m; p += (size_t)gridDim.x * T3) {
         const int x = (int)(p % n), y = (int)((p / n) % n), z = (int)(p / ((size_t)n * n));
         const long SX = 1, SY = n, SZ = (long)n * n;
         const bool hx = x < n - 1, hy = y < n - 1, hz = z < n - 1, lx = x > 0, ly = y > 0, lz = z > 0;
@@ -343,43 +343,26 @@ __global__ void __launch_bounds__(T3) k_metrics3(S3In cur, S3In prv, const float
             }
         }
         if (WN == VOMT_W_L2) { nw_pt = sqrtf(nw_pt); dn_w = sqrtf(dn_w); }
+        double rr = 0.0;
 #pragma unroll
         for (int c = 0; c < K; ++c) {
             const double rc = rdiv[c] + (double)gwb[c];
-            v[RED_RR] += (double)g.wc[c] * rc * rc;
+            rr += (double)g.wc[c] * rc * rc;
             fx += g.wc[c] * dph[c] * ddiv[c];
         }
-        v[RED_P] = (double)(nu_pt + alpha * nw_pt);
-        v[RED_D] = (double)fd;
-        v[RED_BB] = (double)fbb;
-        v[RED_DU] = (double)fdu;
-        v[RED_DW] = (double)fdw;
-        v[RED_DP] = (double)fdp;
-        v[RED_X] = (double)fx;
+        acc.add_d(RED_RR, rr);
+        acc.add(RED_P, nu_pt + alpha * nw_pt);
+        acc.add(RED_D, fd);
+        acc.add(RED_BB, fbb);
+        acc.add(RED_DU, fdu);
+        acc.add(RED_DW, fdw);
+        acc.add(RED_DP, fdp);
+        acc.add(RED_X, fx);
         float di = fmaxf(dn_u - 1.0f, 0.0f);
         if (g.l > 0) di = fmaxf(di, dn_w - alpha);
-        v[RED_MAX] = (double)di;
+        acc.max(RED_MAX, di);
     }
-    // fixed-order block reduction
-    __shared__ double sh[T3 / 32][NRED];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < NRED; ++q) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const double o = __shfl_down_sync(0xffffffffu, v[q], off);
-            v[q] = (q == RED_MAX) ? fmax(v[q], o) : v[q] + o;
-        }
-    }
-    if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < NRED; ++q) sh[wid][q] = v[q];
-    __syncthreads();
-    if (wid == 0 && lane < NRED) {
-        double a = sh[0][lane];
-        for (int w2 = 1; w2 < T3 / 32; ++w2) a = (lane == RED_MAX) ? fmax(a, sh[w2][lane]) : a + sh[w2][lane];
-        partials[(size_t)blockIdx.x * NRED + lane] = a;
-    }
+    block_sum_store<T3>(acc, partials + (size_t)blockIdx.x * NRED);
 }
 
 __global__ void k_prepare3(size_t m, int k, int l, const float *__restrict__ rho0, const float *__restrict__ rho1,
@@ -483,7 +466,8 @@ int solve3d_core(vomt_ctx *ctx, int n, const OpDev &g, const StepDev &s, const S
                       base + (size_t)4 * k * m};
         si[q] = S3In{so[q].phi, so[q].ux, so[q].uy, so[q].uz, so[q].w};
     }
-    const int nblocks = (int)((m + T3 - 1) / T3);     // checks: one point per thread
+    const int nblocks = (int)((m + T3 - 1) / T3);
+    const int mblocks = nblocks < kMetricBlocks ? nblocks : kMetricBlocks;     // blocks of a check
     rc = ensure_buffer(ctx, (void **)&ctx->partials, &ctx->partials_cap, sizeof(double) * (size_t)nblocks * NRED,
                        "partials");
     if (rc) return rc;
@@ -522,8 +506,8 @@ int solve3d_core(vomt_ctx *ctx, int n, const OpDev &g, const StepDev &s, const S
     const dim3 mgrid((n + MX - 1) / MX, (n + MY - 1) / MY, (n + zc - 1) / zc);
     ctx->last_blocks = (int)(mgrid.x * mgrid.y * mgrid.z);
     auto check = [&](int t, int cur) {
-        L.metrics<<<nblocks, T3, 0, st>>>(si[cur], si[cur ^ 1], b, g, s, ctx->partials, ctx->dstatus);
-        k_finalize<<<1, 256, 0, st>>>(ctx->partials, nblocks, cfg, t, ctx->dstatus, ctx->dhist, ctx->hist_cap);
+        L.metrics<<<mblocks, T3, 0, st>>>(si[cur], si[cur ^ 1], b, g, s, ctx->partials, ctx->dstatus);
+        k_finalize<<<1, kFinThreads, 0, st>>>(ctx->partials, mblocks, cfg, t, ctx->dstatus, ctx->dhist, ctx->hist_cap);
         ctx->launches += 2;
     };
     if (p.max_iters == 0) check(0, 0);

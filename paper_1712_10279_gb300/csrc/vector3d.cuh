@@ -16,6 +16,8 @@ namespace v3 {
 
 using dev::shrink2_factor;
 using dev::soft;
+using dev::CheckAcc;
+using dev::block_sum_store;
 
 // a block owns an MX x MY column of the grid and marches through a chunk of z
 constexpr int MX = 32, MY = 8, MT = MX * MY;

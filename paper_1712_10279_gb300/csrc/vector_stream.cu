@@ -29,6 +29,8 @@ struct StateOut {
 // shrink_2 factor and soft threshold of Appendix B (pdhg_device.cuh)
 using dev::shrink2_factor;
 using dev::soft;
+using dev::CheckAcc;
+using dev::block_sum_store;
 
 template <int K>
 __device__ __forceinline__ float pick(const float (&a)[K], int idx)
@@ -211,29 +213,6 @@ __global__ void __launch_bounds__(NT) k_step(StateIn in, StateOut out, const flo
 }
 
 // ----------------------------------------------------------------- metrics
-__device__ __forceinline__ void block_reduce_store(double (&v)[NRED], double *dst)
-{
-    __shared__ double sh[NT / 32][NRED];
-    const int lane = (threadIdx.y * BX + threadIdx.x) & 31, wid = (threadIdx.y * BX + threadIdx.x) >> 5;
-#pragma unroll
-    for (int q = 0; q < NRED; ++q) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            double o = __shfl_down_sync(0xffffffffu, v[q], off);
-            v[q] = (q == RED_MAX) ? fmax(v[q], o) : v[q] + o;
-        }
-    }
-    if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < NRED; ++q) sh[wid][q] = v[q];
-    __syncthreads();
-    if (wid == 0 && lane < NRED) {
-        double a = sh[0][lane];
-        for (int w = 1; w < NT / 32; ++w) a = (lane == RED_MAX) ? fmax(a, sh[w][lane]) : a + sh[w][lane];
-        dst[lane] = a;
-    }
-}
-
 template <int K, int UN, int WN>
 __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const float *__restrict__ b,
                                                  OpDev g, StepDev s, double *__restrict__ partials,
@@ -242,11 +221,14 @@ __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const 
     if (st->stop) return;
     constexpr int LK = LKOf<K>::v;
     const int n = s.n;
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    double v[NRED];
-#pragma unroll
-    for (int q = 0; q < NRED; ++q) v[q] = 0.0;
+    // the grid's BX x BY tiles, visited by the blocks in turn (at most kMetricBlocks
+    // blocks, so that k_finalize sums few rows)
+    const int gxb = (n + BX - 1) / BX, ntile = gxb * ((n + BY - 1) / BY);
+    CheckAcc acc;
+    acc.zero();
+    for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int i = (tile % gxb) * BX + threadIdx.x;
+    const int j = (tile / gxb) * BY + threadIdx.y;
     if (i < n && j < n) {
         // Per-point terms in FP32 (each rounding is relative 2^-24), converted once
         // per point and accumulated in FP64 (FP64 arithmetic is scarce on this
@@ -359,26 +341,31 @@ __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const 
             const float o = fmaxf(dn_w - alpha, 0.0f);
             if (g.l > 0) dist += o * o;
         }
+        double rr = 0.0;
 #pragma unroll
         for (int c = 0; c < K; ++c) {
             const double rc = rdiv[c] + (double)gwb[c];
-            v[RED_RR] += (double)g.wc[c] * rc * rc;
+            rr += (double)g.wc[c] * rc * rc;
             fx += g.wc[c] * dph[c] * ddiv[c];
         }
-        v[RED_P] = (double)(nu_pt + alpha * nw_pt) + (s.reg ? (double)(s.eps * q2) : 0.0);
-        v[RED_DIST] = s.reg ? (double)dist : 0.0;
-        v[RED_D] = (double)fd;
-        v[RED_BB] = (double)fbb;
-        v[RED_DU] = (double)fdu;
-        v[RED_DW] = (double)fdw;
-        v[RED_DP] = (double)fdp;
-        v[RED_X] = (double)fx;
+        acc.add_d(RED_RR, rr);
+        acc.add(RED_P, nu_pt + alpha * nw_pt);
+        if (s.reg) {
+            acc.add(RED_P, s.eps * q2);
+            acc.add(RED_DIST, dist);
+        }
+        acc.add(RED_D, fd);
+        acc.add(RED_BB, fbb);
+        acc.add(RED_DU, fdu);
+        acc.add(RED_DW, fdw);
+        acc.add(RED_DP, fdp);
+        acc.add(RED_X, fx);
         float di = fmaxf(dn_u - 1.0f, 0.0f);
         if (g.l > 0) di = fmaxf(di, dn_w - alpha);
-        v[RED_MAX] = (double)di;
+        acc.max(RED_MAX, di);
     }
-    const int blk = blockIdx.y * gridDim.x + blockIdx.x;
-    block_reduce_store(v, partials + (size_t)blk * NRED);
+    }
+    block_sum_store<NT>(acc, partials + (size_t)blockIdx.x * NRED);
 }
 
 // ----------------------------------------------------------------- setup / copy
@@ -491,25 +478,24 @@ __global__ void k_finalize(const double *__restrict__ partials, int nblocks, Sol
                            DevStatus *st, double *hist, int hist_cap)
 {
     if (st->stop) return;
-    __shared__ double sh[256];
     __shared__ double S[NRED];
-    for (int q = 0; q < NRED; ++q) {
+    // warp q sums slot q: lane j takes rows j, j + 32, ..., then a butterfly over
+    // the lanes (a fixed order, so the same sum on every run)
+    const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+    if (q < NRED) {
         double a = 0.0;
-        for (int bk = threadIdx.x; bk < nblocks; bk += blockDim.x) {
-            double x = partials[(size_t)bk * NRED + q];
+        for (int bk = lane; bk < nblocks; bk += 32) {
+            const double x = partials[(size_t)bk * NRED + q];
             a = (q == RED_MAX) ? fmax(a, x) : a + x;
         }
-        sh[threadIdx.x] = a;
-        __syncthreads();
-        for (int off = 128; off > 0; off >>= 1) {
-            if (threadIdx.x < off)
-                sh[threadIdx.x] = (q == RED_MAX) ? fmax(sh[threadIdx.x], sh[threadIdx.x + off])
-                                                 : sh[threadIdx.x] + sh[threadIdx.x + off];
-            __syncthreads();
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double o = __shfl_xor_sync(0xffffffffu, a, off);
+            a = (q == RED_MAX) ? fmax(a, o) : a + o;
         }
-        if (threadIdx.x == 0) S[q] = sh[0];
-        __syncthreads();
+        if (lane == 0) S[q] = a;
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
         if (t < 0) t = st->iter - t;       // in a replayed graph: the last check's iteration plus -t
         double P = S[RED_P], D = S[RED_D] - (cfg.eps > 0.0 ? S[RED_DIST] / (4.0 * cfg.eps) : 0.0);
@@ -596,6 +582,7 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
     }
     const dim3 blk(BX, BY), grd((n + BX - 1) / BX, (n + BY - 1) / BY);
     const int nblocks = (int)(grd.x * grd.y);
+    const int mblocks = nblocks < kMetricBlocks ? nblocks : kMetricBlocks;     // blocks of a check
     ctx->last_blocks = nblocks;
     rc = ensure_buffer(ctx, (void **)&ctx->partials, &ctx->partials_cap, sizeof(double) * (size_t)nblocks * NRED,
                        "partials");
@@ -625,13 +612,13 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
         ctx->last_variant = 1;
     }
     auto check = [&](int t, int cur) {
-        L.metrics<<<grd, blk, 0, st>>>(si[cur], si[cur ^ 1], b, g, s, ctx->partials, ctx->dstatus);
-        k_finalize<<<1, 256, 0, st>>>(ctx->partials, nblocks, cfg, t, ctx->dstatus, ctx->dhist, ctx->hist_cap);
+        L.metrics<<<mblocks, blk, 0, st>>>(si[cur], si[cur ^ 1], b, g, s, ctx->partials, ctx->dstatus);
+        k_finalize<<<1, kFinThreads, 0, st>>>(ctx->partials, mblocks, cfg, t, ctx->dstatus, ctx->dhist, ctx->hist_cap);
         ctx->launches += 2;
     };
     if (p.max_iters == 0) {
-        L.metrics<<<grd, blk, 0, st>>>(si[0], si[0], b, g, s, ctx->partials, ctx->dstatus);
-        k_finalize<<<1, 256, 0, st>>>(ctx->partials, nblocks, cfg, 0, ctx->dstatus, ctx->dhist, ctx->hist_cap);
+        L.metrics<<<mblocks, blk, 0, st>>>(si[0], si[0], b, g, s, ctx->partials, ctx->dstatus);
+        k_finalize<<<1, kFinThreads, 0, st>>>(ctx->partials, mblocks, cfg, 0, ctx->dstatus, ctx->dhist, ctx->hist_cap);
         ctx->launches += 2;
     }
     const bool tol_mode = cfg.tol_gap > 0.0;
@@ -653,9 +640,9 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
                 else
                     L.step<<<grd, blk, 0, ctx->cap_stream>>>(si[cur ^ 1], so[cur], b, g, s, ctx->dstatus);
                 if (tt % p.check_every == 0) {
-                    L.metrics<<<grd, blk, 0, ctx->cap_stream>>>(si[cur], si[cur ^ 1], b, g, s, ctx->partials,
+                    L.metrics<<<mblocks, blk, 0, ctx->cap_stream>>>(si[cur], si[cur ^ 1], b, g, s, ctx->partials,
                                                                  ctx->dstatus);
-                    k_finalize<<<1, 256, 0, ctx->cap_stream>>>(ctx->partials, nblocks, cfg, -p.check_every,
+                    k_finalize<<<1, kFinThreads, 0, ctx->cap_stream>>>(ctx->partials, mblocks, cfg, -p.check_every,
                                                                 ctx->dstatus, ctx->dhist, ctx->hist_cap);
                 }
             }
@@ -837,6 +824,7 @@ int noalloc_solve(int n, const float *rho0, const float *rho1, const vomt_graph 
     const size_t nn = (size_t)n * n;
     const dim3 blk(BX, BY), grd((n + BX - 1) / BX, (n + BY - 1) / BY);
     const int nblocks = (int)(grd.x * grd.y);
+    const int mblocks = nblocks < kMetricBlocks ? nblocks : kMetricBlocks;     // blocks of a check
     const size_t count = (size_t)k * nn;
     const int vblocks = (int)((count + 255) / 256 < 256 ? (count + 255) / 256 : 256);
     const size_t off_status = 0;
@@ -895,8 +883,8 @@ int noalloc_solve(int n, const float *rho0, const float *rho1, const vomt_graph 
     ++launches;
     Launchers L = pick(k, p.u_norm, p.w_norm);
     if (p.max_iters == 0) {
-        L.metrics<<<grd, blk, 0, st>>>(si[0], si[0], b, g, s, partials, dstatus);
-        k_finalize<<<1, 256, 0, st>>>(partials, nblocks, cfg, 0, dstatus, nullptr, 0);
+        L.metrics<<<mblocks, blk, 0, st>>>(si[0], si[0], b, g, s, partials, dstatus);
+        k_finalize<<<1, kFinThreads, 0, st>>>(partials, mblocks, cfg, 0, dstatus, nullptr, 0);
         launches += 2;
     }
     const bool tol_mode = cfg.tol_gap > 0.0;
@@ -910,8 +898,8 @@ int noalloc_solve(int n, const float *rho0, const float *rho1, const vomt_graph 
             L.step<<<grd, blk, 0, st>>>(si[cur ^ 1], so[cur], b, g, s, dstatus);
             ++launches;
             if (tt % p.check_every == 0 || tt == p.max_iters) {
-                L.metrics<<<grd, blk, 0, st>>>(si[cur], si[cur ^ 1], b, g, s, partials, dstatus);
-                k_finalize<<<1, 256, 0, st>>>(partials, nblocks, cfg, tt, dstatus, nullptr, 0);
+                L.metrics<<<mblocks, blk, 0, st>>>(si[cur], si[cur ^ 1], b, g, s, partials, dstatus);
+                k_finalize<<<1, kFinThreads, 0, st>>>(partials, mblocks, cfg, tt, dstatus, nullptr, 0);
                 launches += 2;
             }
         }
