@@ -55,7 +55,7 @@ constexpr int SMEM_MAX = 227 * 1024;
 
 // Largest extended tile of the 384-thread form of the two-point kernel (up to
 // four channels; 170 registers a thread).
-constexpr int LIGHT384_POINTS = 768;
+constexpr int kTwoPoint384Max = 768;
 
 // Estimated nanoseconds per iteration (see resident_plan).  Constants fitted to
 // GB300 measurements of this kernel at k = 3: 3.5 ns per point of the region a
@@ -142,7 +142,7 @@ bool resident_plan(int n, int k, int max_blocks, int force_H, ResidentPlan *out)
     const int ext = EW * EH;
     out->P = ext <= RT ? 1 : (ext <= 2 * RT ? 2 : 4);
     out->threads = (((ext + out->P - 1) / out->P + 31) / 32) * 32;
-    out->lb = (k <= 4 && out->P == 2 && ext <= LIGHT384_POINTS) ? 384 : RT;
+    out->lb = (k <= 4 && out->P == 2 && ext <= kTwoPoint384Max) ? 384 : RT;
     return true;
 }
 
@@ -195,7 +195,7 @@ bool resident_plan_wave(int n, int k, int count, int max_blocks, ResidentPlan *o
     const int ext = (out->TXm + 2 * out->H) * (out->TYm + 2 * out->H);
     out->P = (k >= 5 && ext <= RT) ? 1 : (ext <= 2 * RT ? 2 : 4);
     out->threads = (((ext + out->P - 1) / out->P + 31) / 32) * 32;
-    out->lb = (k <= 4 && out->P == 2 && ext <= LIGHT384_POINTS) ? 384 : RT;
+    out->lb = (k <= 4 && out->P == 2 && ext <= kTwoPoint384Max) ? 384 : RT;
     return true;
 }
 
