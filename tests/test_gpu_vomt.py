@@ -207,6 +207,22 @@ def test_resident_matches_stream_closely_at_256():
     assert abs(a.result["primal"] - b.result["primal"]) <= 1e-5 * a.result["primal"]
 
 
+@pytest.mark.parametrize("n,k", [(190, 3), (200, 2), (176, 4), (160, 1)])
+def test_resident_two_point_384_thread_form_matches_oracle(n, k):
+    """Sizes whose default tile plan puts two points on each of at most 384 threads (the
+    384-thread form of the resident kernel, ring widths 4 and 5, ragged tiles): iterates and
+    the check history equal the oracle's at a fixed iteration count."""
+    rng = np.random.default_rng(3 * n + k)
+    edges = S.random_connected_graph(rng, k, 0.6)
+    r0, r1 = S.blob_pair(n, k, seed=n + 11 * k)
+    sol = _gpu(r0, r1, edges, 0.7, max_iters=150, check_every=50, engine="resident")
+    assert sol.result["engine"] == "resident" and sol.result["iters"] == 150
+    ref = _oracle(r0, r1, edges, 0.7, max_iters=150, check_every=50, history=True)
+    _compare(sol, ref)
+    h = V.history()
+    np.testing.assert_allclose(h[:, 0], ref["history"][:, 0], rtol=1e-4)
+
+
 @pytest.mark.parametrize("halo", [1, 2, 3, 5, 8])
 @pytest.mark.parametrize("n,k", [(64, 3), (130, 2), (256, 3), (97, 5)])
 def test_resident_halo_widths_match_oracle(halo, n, k):
