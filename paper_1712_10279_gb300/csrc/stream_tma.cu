@@ -145,7 +145,6 @@ template <int K, int UN, int WN>
 __global__ void __launch_bounds__(NTH) k_step_tma(const __grid_constant__ TmaMapsDev maps, float *__restrict__ out,
                                                   OpDev g, StepDev s, DevStatus *st)
 {
-    if (st->stop) return;
     constexpr int LK = LKT<K>::v;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) unsigned long long mbar;
@@ -161,6 +160,11 @@ __global__ void __launch_bounds__(NTH) k_step_tma(const __grid_constant__ TmaMap
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    // launched as a programmatic dependent of the previous step or check: everything
+    // above ran while that kernel drained; from here on its writes are complete and
+    // visible (a no-op for a normal launch)
+    cudaGridDependencySynchronize();
+    if (st->stop) return;
     if (tid == 0) {
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(SL.bytes) : "memory");
         tma_load_3d(smem_u32(sphi), &maps.phi, x0 - 4, y0 - 1, 0, mb);
@@ -391,10 +395,24 @@ TmaPlan *tma_plan_create(int n, int k, int l, int un, int wn, const float *state
 void tma_plan_destroy(TmaPlan *pl) { delete pl; }
 
 void tma_launch_step(const TmaPlan *pl, int in_state, float *out_state, const OpDev &g, const StepDev &s,
-                     DevStatus *st, cudaStream_t stream)
+                     DevStatus *st, cudaStream_t stream, bool pdl)
 {
     const dim3 grd((s.n + TX - 1) / TX, (s.n + TY - 1) / TY);
-    pl->kern<<<grd, NTH, pl->smem, stream>>>(pl->maps[in_state], out_state, g, s, st);
+    if (!pdl) {
+        pl->kern<<<grd, NTH, pl->smem, stream>>>(pl->maps[in_state], out_state, g, s, st);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = grd;
+    cfg.blockDim = dim3(NTH);
+    cfg.dynamicSmemBytes = pl->smem;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, pl->kern, pl->maps[in_state], out_state, g, s, st);
 }
 
 }  // namespace vomt

@@ -20,7 +20,9 @@ TmaPlan *tma_plan_create(int n, int k, int l, int un, int wn, const float *state
 void tma_plan_destroy(TmaPlan *pl);
 
 // One iteration from state `in_state` (0 or 1) into the state at out_state.
+// pdl: launch as a programmatic dependent of the previous kernel on the stream (its
+// blocks are scheduled while that kernel drains and wait for its writes in the kernel)
 void tma_launch_step(const TmaPlan *pl, int in_state, float *out_state, const OpDev &g, const StepDev &s,
-                     DevStatus *st, cudaStream_t stream);
+                     DevStatus *st, cudaStream_t stream, bool pdl = false);
 
 }  // namespace vomt

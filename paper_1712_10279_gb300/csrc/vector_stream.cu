@@ -110,6 +110,7 @@ template <int K, int UN, int WN>
 __global__ void __launch_bounds__(NT) k_step(StateIn in, StateOut out, const float *__restrict__ b,
                                               OpDev g, StepDev s, const DevStatus *__restrict__ st)
 {
+    cudaGridDependencySynchronize();      // after the previous kernel (no-op for a normal launch)
     if (st->stop) return;
     constexpr int LK = LKOf<K>::v;
     const int n = s.n;
@@ -218,6 +219,7 @@ __global__ void __launch_bounds__(NT) k_metrics(StateIn cur, StateIn prv, const 
                                                  OpDev g, StepDev s, double *__restrict__ partials,
                                                  const DevStatus *__restrict__ st)
 {
+    cudaGridDependencySynchronize();
     if (st->stop) return;
     constexpr int LK = LKOf<K>::v;
     const int n = s.n;
@@ -477,6 +479,7 @@ Launchers pick(int k, int un, int wn)
 __global__ void k_finalize(const double *__restrict__ partials, int nblocks, SolveCfg cfg, int t,
                            DevStatus *st, double *hist, int hist_cap)
 {
+    cudaGridDependencySynchronize();
     if (st->stop) return;
     __shared__ double S[NRED];
     // warp q sums slot q: lane j takes rows j, j + 32, ..., then a butterfly over
@@ -519,6 +522,27 @@ __global__ void k_finalize(const double *__restrict__ partials, int nblocks, Sol
         if (!finite) { st->error = VOMT_ERR_NONFINITE; st->stop = 1; }
         if (conv) st->stop = 1;
     }
+}
+
+// Launch as a programmatic dependent of the previous kernel on the stream: the
+// kernel's blocks may be scheduled while that kernel drains, and each of the
+// streaming kernels waits in cudaGridDependencySynchronize() before it reads
+// what the previous one wrote.  The iterations of a solve are chains of short
+// kernels, so this hides part of the gap between them.
+template <typename... Exp, typename... Act>
+static cudaError_t launch_pdl(void (*kern)(Exp...), dim3 grid, dim3 block, cudaStream_t st, Act... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 // One fused iteration (Section 7.2) from the state at `in` to the state at
@@ -612,8 +636,10 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
         ctx->last_variant = 1;
     }
     auto check = [&](int t, int cur) {
-        L.metrics<<<mblocks, blk, 0, st>>>(si[cur], si[cur ^ 1], b, g, s, ctx->partials, ctx->dstatus);
-        k_finalize<<<1, kFinThreads, 0, st>>>(ctx->partials, mblocks, cfg, t, ctx->dstatus, ctx->dhist, ctx->hist_cap);
+        launch_pdl(L.metrics, dim3(mblocks), blk, st, si[cur], si[cur ^ 1], (const float *)b, g, s, ctx->partials,
+                   (const DevStatus *)ctx->dstatus);
+        launch_pdl(k_finalize, dim3(1), dim3(kFinThreads), st, (const double *)ctx->partials, mblocks, cfg, t,
+                   ctx->dstatus, ctx->dhist, ctx->hist_cap);
         ctx->launches += 2;
     };
     if (p.max_iters == 0) {
@@ -636,14 +662,15 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
             for (int tt = 1; tt <= G; ++tt) {
                 const int cur = tt & 1;
                 if (tp)
-                    tma_launch_step(tp, cur ^ 1, so[cur].phi, g, s, ctx->dstatus, ctx->cap_stream);
+                    tma_launch_step(tp, cur ^ 1, so[cur].phi, g, s, ctx->dstatus, ctx->cap_stream, true);
                 else
-                    L.step<<<grd, blk, 0, ctx->cap_stream>>>(si[cur ^ 1], so[cur], b, g, s, ctx->dstatus);
+                    launch_pdl(L.step, grd, blk, ctx->cap_stream, si[cur ^ 1], so[cur], (const float *)b, g, s,
+                               (const DevStatus *)ctx->dstatus);
                 if (tt % p.check_every == 0) {
-                    L.metrics<<<mblocks, blk, 0, ctx->cap_stream>>>(si[cur], si[cur ^ 1], b, g, s, ctx->partials,
-                                                                 ctx->dstatus);
-                    k_finalize<<<1, kFinThreads, 0, ctx->cap_stream>>>(ctx->partials, mblocks, cfg, -p.check_every,
-                                                                ctx->dstatus, ctx->dhist, ctx->hist_cap);
+                    launch_pdl(L.metrics, dim3(mblocks), blk, ctx->cap_stream, si[cur], si[cur ^ 1], (const float *)b, g,
+                               s, ctx->partials, (const DevStatus *)ctx->dstatus);
+                    launch_pdl(k_finalize, dim3(1), dim3(kFinThreads), ctx->cap_stream, (const double *)ctx->partials,
+                               mblocks, cfg, -p.check_every, ctx->dstatus, ctx->dhist, ctx->hist_cap);
                 }
             }
             if (cudaStreamEndCapture(ctx->cap_stream, &graph) != cudaSuccess ||
@@ -674,9 +701,10 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
         for (int tt = t + 1; tt <= end; ++tt) {
             const int cur = tt & 1;
             if (tp)
-                tma_launch_step(tp, cur ^ 1, so[cur].phi, g, s, ctx->dstatus, st);
+                tma_launch_step(tp, cur ^ 1, so[cur].phi, g, s, ctx->dstatus, st, true);
             else
-                L.step<<<grd, blk, 0, st>>>(si[cur ^ 1], so[cur], b, g, s, ctx->dstatus);
+                launch_pdl(L.step, grd, blk, st, si[cur ^ 1], so[cur], (const float *)b, g, s,
+                           (const DevStatus *)ctx->dstatus);
             ctx->launches += 1;
             if (tt % p.check_every == 0 || tt == p.max_iters) check(tt, cur);
         }
