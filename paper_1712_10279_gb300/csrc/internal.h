@@ -236,6 +236,29 @@ struct ResidentPlan {
     double est_ns;      // estimated ns per iteration (a wave plan: of the whole wave, all its rounds)
     int lb;             // launch bound of the single-problem kernel (0: res_threads(k))
 };
+// Launch as a programmatic dependent of the previous kernel on the stream: the
+// kernel's blocks may be scheduled while that kernel drains, and each of the
+// streaming kernels (2-D and 3-D steps, checks, k_finalize) waits in
+// cudaGridDependencySynchronize() before it reads what the previous one wrote.
+// An iteration is a chain of short kernels, so this hides part of the gap
+// between them.
+template <typename... Exp, typename... Act>
+inline cudaError_t launch_pdl(void (*kern)(Exp...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Act... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Blocks of a streaming check (k_metrics, k_metrics3): the check's kernel loops
 // over the grid with at most this many blocks (four per SM on a GB300), which
 // bounds the FP64 rows k_finalize sums.

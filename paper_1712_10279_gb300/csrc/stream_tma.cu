@@ -402,17 +402,7 @@ void tma_launch_step(const TmaPlan *pl, int in_state, float *out_state, const Op
         pl->kern<<<grd, NTH, pl->smem, stream>>>(pl->maps[in_state], out_state, g, s, st);
         return;
     }
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.gridDim = grd;
-    cfg.blockDim = dim3(NTH);
-    cfg.dynamicSmemBytes = pl->smem;
-    cfg.stream = stream;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, pl->kern, pl->maps[in_state], out_state, g, s, st);
+    launch_pdl(pl->kern, grd, dim3(NTH), pl->smem, stream, pl->maps[in_state], out_state, g, s, st);
 }
 
 }  // namespace vomt

@@ -66,6 +66,7 @@ template <int K, int UN, int WN>
 __global__ void __launch_bounds__(MT, K <= 4 ? 2 : 1) k_step3m(S3In in, S3Out out, const float *__restrict__ b, OpDev g,
                                                  StepDev s, const DevStatus *__restrict__ st, int zc)
 {
+    cudaGridDependencySynchronize();      // after the previous kernel (no-op for a normal launch)
     if (st->stop) return;
     constexpr int LK = LK3<K>::v;
     constexpr int PF = (HP + MT - 1) / MT;
@@ -246,6 +247,7 @@ __global__ void __launch_bounds__(T3) k_metrics3(S3In cur, S3In prv, const float
                                                  StepDev s, double *__restrict__ partials,
                                                  const DevStatus *__restrict__ st)
 {
+    cudaGridDependencySynchronize();      // after the previous kernel (no-op for a normal launch)
     if (st->stop) return;
     constexpr int LK = LK3<K>::v;
     const int n = s.n;
@@ -506,8 +508,10 @@ int solve3d_core(vomt_ctx *ctx, int n, const OpDev &g, const StepDev &s, const S
     const dim3 mgrid((n + MX - 1) / MX, (n + MY - 1) / MY, (n + zc - 1) / zc);
     ctx->last_blocks = (int)(mgrid.x * mgrid.y * mgrid.z);
     auto check = [&](int t, int cur) {
-        L.metrics<<<mblocks, T3, 0, st>>>(si[cur], si[cur ^ 1], b, g, s, ctx->partials, ctx->dstatus);
-        k_finalize<<<1, kFinThreads, 0, st>>>(ctx->partials, mblocks, cfg, t, ctx->dstatus, ctx->dhist, ctx->hist_cap);
+        launch_pdl(L.metrics, dim3(mblocks), dim3(T3), 0, st, si[cur], si[cur ^ 1], (const float *)b, g, s,
+                   ctx->partials, (const DevStatus *)ctx->dstatus);
+        launch_pdl(k_finalize, dim3(1), dim3(kFinThreads), 0, st, (const double *)ctx->partials, mblocks, cfg, t,
+                   ctx->dstatus, ctx->dhist, ctx->hist_cap);
         ctx->launches += 2;
     };
     if (p.max_iters == 0) check(0, 0);
@@ -525,7 +529,8 @@ int solve3d_core(vomt_ctx *ctx, int n, const OpDev &g, const StepDev &s, const S
             if (tp)
                 tma3_launch_step(tp, cur ^ 1, so[cur], g, s, ctx->dstatus, zc, st);
             else
-                L.step<<<mgrid, MT, L.smem, st>>>(si[cur ^ 1], so[cur], b, g, s, ctx->dstatus, zc);
+                launch_pdl(L.step, mgrid, dim3(MT), (size_t)L.smem, st, si[cur ^ 1], so[cur], (const float *)b, g, s,
+                           (const DevStatus *)ctx->dstatus, zc);
             ctx->launches += 1;
             if (tt % p.check_every == 0 || tt == p.max_iters) check(tt, cur);
         }

@@ -128,7 +128,6 @@ template <int K, int UN, int WN>
 __global__ void __launch_bounds__(NT3, blocks_per_sm(K)) k_step3t(const __grid_constant__ Maps3 maps, const float *__restrict__ in,
                                                  S3Out out, OpDev g, StepDev s, DevStatus *st, int zc)
 {
-    if (st->stop) return;
     constexpr int NS = nstages(K), LK = LK3<K>::v;
     constexpr int PL = BYP * BXH, UL = BYU * BXU, WL = MY * MX;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -154,6 +153,11 @@ __global__ void __launch_bounds__(NT3, blocks_per_sm(K)) k_step3t(const __grid_c
         abort_flag = 0;
     }
     __syncthreads();
+    // launched as a programmatic dependent of the previous step or check: the setup
+    // above ran while that kernel drained; from here on its writes are complete and
+    // visible (a no-op for a normal launch)
+    cudaGridDependencySynchronize();
+    if (st->stop) return;
     // plane p lives in stage (p - z0) % NS; its use of that stage has phase parity ((p - z0) / NS) & 1
     auto issue = [&](int p) {
         const int q = (p - z0) % NS;
@@ -451,7 +455,7 @@ void tma3_launch_step(const Tma3Plan *pl, int in_state, S3Out out, const OpDev &
 {
     const int n = s.n;
     const dim3 grd((n + MX - 1) / MX, (n + MY - 1) / MY, (n + zc - 1) / zc);
-    pl->kern<<<grd, NT3, pl->smem, stream>>>(pl->maps[in_state], pl->in[in_state], out, g, s, st, zc);
+    launch_pdl(pl->kern, grd, dim3(NT3), pl->smem, stream, pl->maps[in_state], pl->in[in_state], out, g, s, st, zc);
 }
 
 }  // namespace vomt

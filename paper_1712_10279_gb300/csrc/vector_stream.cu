@@ -524,27 +524,6 @@ __global__ void k_finalize(const double *__restrict__ partials, int nblocks, Sol
     }
 }
 
-// Launch as a programmatic dependent of the previous kernel on the stream: the
-// kernel's blocks may be scheduled while that kernel drains, and each of the
-// streaming kernels waits in cudaGridDependencySynchronize() before it reads
-// what the previous one wrote.  The iterations of a solve are chains of short
-// kernels, so this hides part of the gap between them.
-template <typename... Exp, typename... Act>
-static cudaError_t launch_pdl(void (*kern)(Exp...), dim3 grid, dim3 block, cudaStream_t st, Act... args)
-{
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, args...);
-}
-
 // One fused iteration (Section 7.2) from the state at `in` to the state at
 // `out`; each state is contiguous planes phi [k], u_x [k], u_y [k], w [l].
 void launch_step(const OpDev &g, const StepDev &s, int un, int wn, const float *in, float *out, const float *b,
@@ -636,9 +615,9 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
         ctx->last_variant = 1;
     }
     auto check = [&](int t, int cur) {
-        launch_pdl(L.metrics, dim3(mblocks), blk, st, si[cur], si[cur ^ 1], (const float *)b, g, s, ctx->partials,
+        launch_pdl(L.metrics, dim3(mblocks), blk, 0, st, si[cur], si[cur ^ 1], (const float *)b, g, s, ctx->partials,
                    (const DevStatus *)ctx->dstatus);
-        launch_pdl(k_finalize, dim3(1), dim3(kFinThreads), st, (const double *)ctx->partials, mblocks, cfg, t,
+        launch_pdl(k_finalize, dim3(1), dim3(kFinThreads), 0, st, (const double *)ctx->partials, mblocks, cfg, t,
                    ctx->dstatus, ctx->dhist, ctx->hist_cap);
         ctx->launches += 2;
     };
@@ -664,12 +643,12 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
                 if (tp)
                     tma_launch_step(tp, cur ^ 1, so[cur].phi, g, s, ctx->dstatus, ctx->cap_stream, true);
                 else
-                    launch_pdl(L.step, grd, blk, ctx->cap_stream, si[cur ^ 1], so[cur], (const float *)b, g, s,
+                    launch_pdl(L.step, grd, blk, 0, ctx->cap_stream, si[cur ^ 1], so[cur], (const float *)b, g, s,
                                (const DevStatus *)ctx->dstatus);
                 if (tt % p.check_every == 0) {
-                    launch_pdl(L.metrics, dim3(mblocks), blk, ctx->cap_stream, si[cur], si[cur ^ 1], (const float *)b, g,
+                    launch_pdl(L.metrics, dim3(mblocks), blk, 0, ctx->cap_stream, si[cur], si[cur ^ 1], (const float *)b, g,
                                s, ctx->partials, (const DevStatus *)ctx->dstatus);
-                    launch_pdl(k_finalize, dim3(1), dim3(kFinThreads), ctx->cap_stream, (const double *)ctx->partials,
+                    launch_pdl(k_finalize, dim3(1), dim3(kFinThreads), 0, ctx->cap_stream, (const double *)ctx->partials,
                                mblocks, cfg, -p.check_every, ctx->dstatus, ctx->dhist, ctx->hist_cap);
                 }
             }
@@ -703,7 +682,7 @@ int stream_solve(vomt_ctx *ctx, const OpDev &g, const StepDev &s, const SolveCfg
             if (tp)
                 tma_launch_step(tp, cur ^ 1, so[cur].phi, g, s, ctx->dstatus, st, true);
             else
-                launch_pdl(L.step, grd, blk, st, si[cur ^ 1], so[cur], (const float *)b, g, s,
+                launch_pdl(L.step, grd, blk, 0, st, si[cur ^ 1], so[cur], (const float *)b, g, s,
                            (const DevStatus *)ctx->dstatus);
             ctx->launches += 1;
             if (tt % p.check_every == 0 || tt == p.max_iters) check(tt, cur);
